@@ -1,0 +1,114 @@
+"""GB300 Jacobi–Davidson eigensolver for the 3D Anderson model of localization.
+
+Python binding of the C ABI declared in ``include/anderson_jd.h``.  The
+binding only marshals arguments: every step of the computation runs in the
+library's CUDA kernels (and its native host setup code).  PyTorch supplies
+device memory and streams; tensors passed in must live on the CUDA device
+that was current when the handle was created.
+"""
+import ctypes
+
+import numpy as np
+
+from . import _ffi
+from ._ffi import (JD_EBREAKDOWN, JD_EDEVICE, JD_EINVAL, JD_ENOCONV, JD_ENOMEM, JD_ESETUP, JD_FP32,
+                   JD_FP64, JD_HARDWALL, JD_OK, JD_PERIODIC, JDError)
+
+__all__ = ["Anderson", "JDError", "JD_PERIODIC", "JD_HARDWALL", "JD_FP64", "JD_FP32", "library_path"]
+
+
+def library_path():
+    return _ffi.LIB_PATH
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _precision_of(t):
+    import torch
+    if t.dtype == torch.float64:
+        return JD_FP64
+    if t.dtype == torch.float32:
+        return JD_FP32
+    raise TypeError("only float64 and float32 tensors are supported, got %s" % t.dtype)
+
+
+def _dev_ptr(t, what):
+    if not t.is_cuda:
+        raise ValueError("%s must be a CUDA tensor" % what)
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % what)
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Anderson:
+    """An L^3 Anderson lattice (Eq. (1)) with box disorder of width W.
+
+    The potential is generated on the current CUDA device from ``seed``.
+    """
+
+    def __init__(self, L, W, seed, bc=JD_PERIODIC):
+        h = ctypes.c_void_p()
+        _ffi.call("anderson_create", int(L), float(W), ctypes.c_uint64(int(seed) & (2 ** 64 - 1)), int(bc),
+                  ctypes.byref(h))
+        self._h = h
+        self.L, self.W, self.seed, self.bc = int(L), float(W), int(seed), int(bc)
+        n = ctypes.c_int64()
+        _ffi.call("anderson_size", self._h, ctypes.byref(n))
+        self.n = n.value
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise ValueError("handle is closed")
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            _ffi.lib().anderson_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def norm(self):
+        v = ctypes.c_double()
+        _ffi.call("anderson_norm", self.handle, ctypes.byref(v))
+        return v.value
+
+    def potential(self):
+        out = np.empty(self.n, dtype=np.float64)
+        _ffi.call("anderson_potential", self.handle, out.ctypes.data_as(ctypes.c_void_p))
+        return out
+
+    def apply(self, x, shift=0.0, out=None, stream=None):
+        """y = (A - shift I) x.  ``x`` is a CUDA tensor of shape (n,) or
+        (m, n) (m vectors, one per row, i.e. an n x m column-major block),
+        float64 or float32."""
+        import torch
+        if x.shape[-1] != self.n:
+            raise ValueError("last dimension must be n = %d" % self.n)
+        m = 1 if x.dim() == 1 else x.shape[0]
+        if out is None:
+            out = torch.empty_like(x)
+        prec = _precision_of(x)
+        if out.dtype != x.dtype or out.shape != x.shape:
+            raise ValueError("out must match x in dtype and shape")
+        _ffi.call("anderson_apply", self.handle, float(shift), _dev_ptr(x, "x"), _dev_ptr(out, "out"), int(m),
+                  prec, _stream_handle(stream))
+        return out

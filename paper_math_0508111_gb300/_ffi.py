@@ -1,0 +1,69 @@
+"""ctypes declarations of the C ABI in ``include/anderson_jd.h``.
+
+Loading fails loudly when the shared library has not been built: there is no
+fallback implementation.
+"""
+import ctypes
+import os
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libanderson_jd.so")
+
+c_int, c_double, c_void_p, c_int64, c_uint64 = (ctypes.c_int, ctypes.c_double, ctypes.c_void_p,
+                                                ctypes.c_int64, ctypes.c_uint64)
+P = ctypes.POINTER
+
+JD_OK, JD_EINVAL, JD_ENOMEM, JD_ENOCONV, JD_EBREAKDOWN, JD_EDEVICE, JD_ESETUP = 0, -1, -2, -3, -4, -5, -6
+JD_PERIODIC, JD_HARDWALL = 0, 1
+JD_FP64, JD_FP32 = 0, 1
+
+ERROR_NAMES = {JD_EINVAL: "JD_EINVAL", JD_ENOMEM: "JD_ENOMEM", JD_ENOCONV: "JD_ENOCONV",
+               JD_EBREAKDOWN: "JD_EBREAKDOWN", JD_EDEVICE: "JD_EDEVICE", JD_ESETUP: "JD_ESETUP"}
+
+
+class JDError(RuntimeError):
+    def __init__(self, code, func, msg):
+        super().__init__("%s failed with %s: %s" % (func, ERROR_NAMES.get(code, str(code)), msg))
+        self.code = code
+
+
+# (name, restype, argtypes) of every exported function
+SIGNATURES = [
+    ("jd_last_error", ctypes.c_char_p, []),
+    ("jd_version", c_int, []),
+    ("anderson_create", c_int, [c_int, c_double, c_uint64, c_int, P(c_void_p)]),
+    ("anderson_destroy", c_int, [c_void_p]),
+    ("anderson_size", c_int, [c_void_p, P(c_int64)]),
+    ("anderson_potential", c_int, [c_void_p, c_void_p]),
+    ("anderson_norm", c_int, [c_void_p, P(c_double)]),
+    ("anderson_apply", c_int, [c_void_p, c_double, c_void_p, c_void_p, c_int, c_int, c_void_p]),
+]
+
+_lib = None
+
+
+def lib():
+    """The loaded library (loaded on first use)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError("libanderson_jd.so is not built; run `python -m paper_math_0508111_gb300.build` "
+                              "(or __graft_entry__.build()).  There is no non-CUDA fallback.")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, res, args in SIGNATURES:
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def check(code, func):
+    if code != JD_OK:
+        msg = lib().jd_last_error().decode(errors="replace")
+        raise JDError(code, func, msg)
+    return code
+
+
+def call(name, *args):
+    return check(getattr(lib(), name)(*args), name)
