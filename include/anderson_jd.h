@@ -115,6 +115,117 @@ int anderson_norm(anderson_t h, double* norm);
 int anderson_apply(anderson_t h, double shift, const void* x, void* y, int m,
                    int precision, void* stream);
 
+/* ======================================================================== *
+ *  Preconditioner K ~ A - sigma I (Sections 5 and 6)                        *
+ * ======================================================================== */
+typedef struct ildl_s* ildl_t;
+
+/* Parameters of the multilevel incomplete LDL^T.  Defaults in brackets. */
+typedef struct {
+  double kappa;   /* bound on ||L^{-1}|| of each level (inverse-based pivoting,
+                     Section 6.2); pivots that would exceed it are postponed
+                     to the next level [5, the value used in Section 7]      */
+  double drop;    /* drop tolerance epsilon: entries of L and of the Schur
+                     complement below epsilon/kappa in modulus are dropped
+                     (Section 6.2); < 0 selects 1/sqrt(n) (Section 7), 0
+                     disables dropping [-1]                                  */
+  double gamma;   /* couplings below gamma (scaled matrix, entries <= 1) are
+                     ignored when each level's independent set of pivots is
+                     chosen, and dropped between pivots of the same level;
+                     0 = exact independence [0.02]                           */
+  int max_levels; /* maximum number of sparse levels [96]                    */
+  int n_dense;    /* the remaining Schur complement is factored densely once
+                     it has at most this many rows [1000]                    */
+  int matching;   /* 1: maximum-product matching, 1x1/2x2 cycle split and
+                     symmetric dual scaling per level (Sections 5.1, 5.2);
+                     0: row-max scaling and 1x1 pivots only [1]              */
+} ildl_params;
+
+/* Fill *p with the defaults above. */
+int ildl_params_default(ildl_params* p);
+
+/* Sizes and statistics of a factor. */
+typedef struct {
+  int n;             /* order                                               */
+  int levels;        /* sparse levels (each one parallel step of the solves)*/
+  int n_dense;       /* order of the trailing dense block                   */
+  int n_2x2;         /* number of 2x2 pivots                                */
+  int64_t nnz_L;     /* stored entries of the strictly lower factor L       */
+  int64_t nnz_A;     /* stored entries of the input matrix                  */
+  double fill;       /* nnz(L D L^T)/nnz(A) = (2 nnz_L + nnz(D))/nnz(A),
+                        the measure of Table 5                              */
+  double setup_ms;   /* wall time of the host construction                  */
+  double match_ms;   /* of which: matchings and scalings                    */
+} ildl_info_t;
+
+/*
+ * ildl_setup_csr -- build the preconditioner of a symmetric matrix on the
+ * host (no GPU needed).  The matrix is given in CSR with both triangles:
+ * rowptr[n+1] (int64), col[nnz] (int32, sorted within each row), val[nnz].
+ * The factor is an approximation K = P^T S^{-1} L D L^T S^{-1} P of the
+ * matrix (see ildl_export).  Errors: JD_EINVAL, JD_ENOMEM, JD_ESETUP
+ * (singular dense block or no usable pivot).
+ */
+int ildl_setup_csr(int n, const int64_t* rowptr, const int* col, const double* val,
+                   const ildl_params* p, ildl_t* out);
+
+/*
+ * ildl_matching -- the first setup step on its own (Sections 5.1, 5.2):
+ * maximum-product matching of a symmetric CSR matrix (Eqs. (5.1)-(5.2)),
+ * the symmetric scaling from its dual potentials, and the split of the
+ * matching's cycles into 1x1 and 2x2 groups.  Host only.
+ *   match_col[n]  row matched to column j (the permutation sigma)
+ *   scale[n]      D with |d_i a_ij d_j| <= 1 and matched entries == 1
+ *   partner[n]    2x2 partner of row i within its group, or -1 (1x1)
+ * Returns JD_OK, or JD_EINVAL; a structurally singular matrix is matched
+ * as far as possible (the leftover rows are paired in index order).
+ */
+int ildl_matching(int n, const int64_t* rowptr, const int* col, const double* val, int* match_col,
+                  double* scale, int* partner);
+
+/*
+ * ildl_create -- build the preconditioner of A - sigma I for the lattice h
+ * (host construction from the lattice's potential), then upload it to the
+ * device of h in binary64 and binary32.  Synchronous.
+ */
+int ildl_create(anderson_t h, double sigma, const ildl_params* p, ildl_t* out);
+
+/* Statistics of a factor. */
+int ildl_info(ildl_t f, ildl_info_t* info);
+
+/*
+ * ildl_export -- copy the factor to caller-owned host arrays.  With
+ * m = info.n, d = info.n_dense, nl = info.levels, nnz = info.nnz_L:
+ *   perm[m]          position p holds original index perm[p]
+ *   scale[m]         S
+ *   level_ptr[nl+2]  positions of level l are [level_ptr[l], level_ptr[l+1]);
+ *                    the dense block is [level_ptr[nl], level_ptr[nl+1]=m)
+ *   Lptr[m+1], Lcol[nnz], Lval[nnz]   strictly lower L, CSR by positions
+ *   dinv_d[m], dinv_o[m], partner[m]  D^{-1}: for a 1x1 pivot at p,
+ *                    (D^{-1} y)_p = dinv_d[p] y_p; for a 2x2 pivot (p, q=partner[p]),
+ *                    (D^{-1} y)_p = dinv_d[p] y_p + dinv_o[p] y_q; unused on
+ *                    dense positions
+ *   dense_inv[d*d]   inverse of the dense block, row-major
+ * so that K^{-1} b = P^T S L^{-T} D^{-1} L^{-1} S P b with (P b)[p] = b[perm[p]].
+ * Any pointer may be NULL to skip that array.
+ */
+int ildl_export(ildl_t f, int* perm, double* scale, int* level_ptr, int64_t* Lptr, int* Lcol,
+                double* Lval, double* dinv_d, double* dinv_o, int* partner, double* dense_inv);
+
+/*
+ * ildl_apply -- x = K^{-1} b on the device (created by ildl_create): one
+ * gather/scale pass, one parallel step per level of L (forward), the block
+ * diagonal and dense solves, one parallel step per level of L^T (backward),
+ * and one scatter/scale pass.
+ *   b, x       device pointers, n elements each, distinct; binary64 for
+ *              JD_FP64, binary32 for JD_FP32.
+ * Errors: JD_EINVAL (no device copy, bad precision), JD_EDEVICE.
+ */
+int ildl_apply(ildl_t f, const void* b, void* x, int precision, void* stream);
+
+/* Release the factor (host and device parts).  NULL is a no-op. */
+int ildl_destroy(ildl_t f);
+
 #ifdef __cplusplus
 }
 #endif

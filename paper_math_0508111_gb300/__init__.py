@@ -14,7 +14,7 @@ from . import _ffi
 from ._ffi import (JD_EBREAKDOWN, JD_EDEVICE, JD_EINVAL, JD_ENOCONV, JD_ENOMEM, JD_ESETUP, JD_FP32,
                    JD_FP64, JD_HARDWALL, JD_OK, JD_PERIODIC, JDError)
 
-__all__ = ["Anderson", "JDError", "JD_PERIODIC", "JD_HARDWALL", "JD_FP64", "JD_FP32", "library_path"]
+__all__ = ["Anderson", "Preconditioner", "ildl_params", "JDError", "JD_PERIODIC", "JD_HARDWALL", "JD_FP64", "JD_FP32", "library_path"]
 
 
 def library_path():
@@ -112,3 +112,115 @@ class Anderson:
         _ffi.call("anderson_apply", self.handle, float(shift), _dev_ptr(x, "x"), _dev_ptr(out, "out"), int(m),
                   prec, _stream_handle(stream))
         return out
+
+
+def ildl_params(**kw):
+    """Preconditioner parameters (defaults of ildl_params_default) with
+    keyword overrides: kappa, drop, gamma, max_levels, n_dense, matching."""
+    p = _ffi.IldlParams()
+    _ffi.call("ildl_params_default", ctypes.byref(p))
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise TypeError("unknown preconditioner parameter %r" % k)
+        setattr(p, k, v)
+    return p
+
+
+def matching(indptr, indices, data):
+    """Sections 5.1-5.2 on a symmetric CSR matrix (host): returns
+    (match_col, scale, partner) as numpy arrays."""
+    indptr = np.ascontiguousarray(indptr, dtype=np.int64)
+    indices = np.ascontiguousarray(indices, dtype=np.int32)
+    data = np.ascontiguousarray(data, dtype=np.float64)
+    n = len(indptr) - 1
+    mc = np.empty(n, np.int32)
+    sc = np.empty(n)
+    pt = np.empty(n, np.int32)
+    vp = ctypes.c_void_p
+    _ffi.call("ildl_matching", int(n), indptr.ctypes.data_as(vp), indices.ctypes.data_as(vp),
+              data.ctypes.data_as(vp), mc.ctypes.data_as(vp), sc.ctypes.data_as(vp), pt.ctypes.data_as(vp))
+    return mc, sc, pt
+
+
+class Preconditioner:
+    """Multilevel incomplete LDL^T K ~ A - sigma I (Sections 5-6).
+
+    ``Preconditioner.from_lattice(h, sigma)`` builds it for a lattice and
+    uploads it to the device; ``Preconditioner.from_csr(...)`` builds the
+    host factor of any symmetric CSR matrix (no GPU needed)."""
+
+    def __init__(self, handle):
+        self._h = handle
+
+    @classmethod
+    def from_lattice(cls, lattice, sigma, **params):
+        h = ctypes.c_void_p()
+        p = ildl_params(**params)
+        _ffi.call("ildl_create", lattice.handle, float(sigma), ctypes.byref(p), ctypes.byref(h))
+        return cls(h)
+
+    @classmethod
+    def from_csr(cls, indptr, indices, data, **params):
+        indptr = np.ascontiguousarray(indptr, dtype=np.int64)
+        indices = np.ascontiguousarray(indices, dtype=np.int32)
+        data = np.ascontiguousarray(data, dtype=np.float64)
+        n = len(indptr) - 1
+        h = ctypes.c_void_p()
+        p = ildl_params(**params)
+        _ffi.call("ildl_setup_csr", int(n), indptr.ctypes.data_as(ctypes.c_void_p),
+                  indices.ctypes.data_as(ctypes.c_void_p), data.ctypes.data_as(ctypes.c_void_p),
+                  ctypes.byref(p), ctypes.byref(h))
+        return cls(h)
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise ValueError("handle is closed")
+        return self._h
+
+    def info(self):
+        i = _ffi.IldlInfo()
+        _ffi.call("ildl_info", self.handle, ctypes.byref(i))
+        return {f: getattr(i, f) for f, _ in i._fields_}
+
+    def export(self):
+        """The factor as numpy arrays (see ildl_export in the header)."""
+        inf = self.info()
+        n, nl, nd, nnz = inf["n"], inf["levels"], inf["n_dense"], inf["nnz_L"]
+        out = dict(perm=np.empty(n, np.int32), scale=np.empty(n), level_ptr=np.empty(nl + 2, np.int32),
+                   Lptr=np.empty(n + 1, np.int64), Lcol=np.empty(max(nnz, 1), np.int32),
+                   Lval=np.empty(max(nnz, 1)), dinv_d=np.empty(n), dinv_o=np.empty(n),
+                   partner=np.empty(n, np.int32), dense_inv=np.empty(max(nd * nd, 1)))
+        ptrs = [out[k].ctypes.data_as(ctypes.c_void_p) for k in
+                ["perm", "scale", "level_ptr", "Lptr", "Lcol", "Lval", "dinv_d", "dinv_o", "partner", "dense_inv"]]
+        _ffi.call("ildl_export", self.handle, *ptrs)
+        out["Lcol"], out["Lval"] = out["Lcol"][:nnz], out["Lval"][:nnz]
+        out["dense_inv"] = out["dense_inv"][:nd * nd].reshape(nd, nd)
+        out.update(inf)
+        return out
+
+    def apply(self, b, out=None, stream=None):
+        """x = K^{-1} b for a CUDA tensor b (float64 or float32, length n)."""
+        import torch
+        if out is None:
+            out = torch.empty_like(b)
+        _ffi.call("ildl_apply", self.handle, _dev_ptr(b, "b"), _dev_ptr(out, "out"), _precision_of(b),
+                  _stream_handle(stream))
+        return out
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            _ffi.lib().ildl_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

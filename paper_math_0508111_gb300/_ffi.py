@@ -27,6 +27,16 @@ class JDError(RuntimeError):
         self.code = code
 
 
+class IldlParams(ctypes.Structure):
+    _fields_ = [("kappa", c_double), ("drop", c_double), ("gamma", c_double), ("max_levels", c_int),
+                ("n_dense", c_int), ("matching", c_int)]
+
+
+class IldlInfo(ctypes.Structure):
+    _fields_ = [("n", c_int), ("levels", c_int), ("n_dense", c_int), ("n_2x2", c_int), ("nnz_L", c_int64),
+                ("nnz_A", c_int64), ("fill", c_double), ("setup_ms", c_double), ("match_ms", c_double)]
+
+
 # (name, restype, argtypes) of every exported function
 SIGNATURES = [
     ("jd_last_error", ctypes.c_char_p, []),
@@ -37,6 +47,14 @@ SIGNATURES = [
     ("anderson_potential", c_int, [c_void_p, c_void_p]),
     ("anderson_norm", c_int, [c_void_p, P(c_double)]),
     ("anderson_apply", c_int, [c_void_p, c_double, c_void_p, c_void_p, c_int, c_int, c_void_p]),
+    ("ildl_params_default", c_int, [P(IldlParams)]),
+    ("ildl_setup_csr", c_int, [c_int, c_void_p, c_void_p, c_void_p, P(IldlParams), P(c_void_p)]),
+    ("ildl_matching", c_int, [c_int, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    ("ildl_create", c_int, [c_void_p, c_double, P(IldlParams), P(c_void_p)]),
+    ("ildl_info", c_int, [c_void_p, P(IldlInfo)]),
+    ("ildl_export", c_int, [c_void_p] + [c_void_p] * 10),
+    ("ildl_apply", c_int, [c_void_p, c_void_p, c_void_p, c_int, c_void_p]),
+    ("ildl_destroy", c_int, [c_void_p]),
 ]
 
 _lib = None

@@ -2,12 +2,9 @@
 // 7-point stencil y = (A - shift I) x.
 //
 // Section 3.1 notes that the matrix-vector product can be coded directly with
-// only the diagonal stored.  Here the product is a z-marching stencil: each
-// CTA owns a TX x TY column of the lattice and walks a chunk of z-planes,
-// keeping the (z-1, z, z+1) values of its column in registers and staging
-// the current plane (plus a one-site halo, wrapped for periodic boundaries)
-// in shared memory.  Every x value is read from HBM once per sweep, every
-// y written once: 24 bytes per site in binary64, 12 in binary32.
+// only the diagonal stored.  Here it is a z-marching stencil (see
+// stencil_kernel below): every x value is read from HBM once per sweep and
+// every y written once, 24 bytes per site in binary64 and 12 in binary32.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -57,108 +54,145 @@ __global__ void max_abs_kernel(const double* __restrict__ v, int64_t n,
   if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(m));
 }
 
-constexpr int TX = 32;  // tile width (x, contiguous in memory)
-constexpr int TY = 8;   // tile height (y)
+// Row-marching stencil.  A warp owns one x-segment of 32*V sites of a lattice
+// row (fixed y) and walks a chunk of z-planes, keeping the segment's values at
+// z-1, z and z+1 in registers; lane l holds sites seg*32V + l + 32v, so every
+// load instruction of the warp is one contiguous, coalesced run.  The x+-1 and
+// y+-1 neighbours are re-read through L1 (the eight warps of a CTA own eight
+// consecutive rows), so each x value comes from HBM once per sweep.
+constexpr int kWarps = 8;
 
 template <typename T>
-__device__ __forceinline__ T load_site(const T* __restrict__ x, int L, int64_t LL,
-                                       int wx, int wy, int z, bool inside_xy,
-                                       bool periodic) {
-  if (periodic) {
-    z = (z < 0) ? z + L : (z >= L ? z - L : z);
-  } else if (z < 0 || z >= L || !inside_xy) {
-    return T(0);
-  }
-  return __ldg(x + (int64_t)z * LL + (int64_t)wy * L + wx);
+__device__ __forceinline__ T ldv(const T* __restrict__ p, int64_t i, bool ok) {
+  return ok ? __ldg(p + i) : T(0);
 }
 
-// y = (eps - shift) x + hop * (sum of the six neighbours), one vector per
-// blockIdx.z.  Tiles of TX x TY sites in (x, y); blockIdx.y picks a chunk of
-// `zchunk` planes.
-template <typename T>
-__global__ void __launch_bounds__(TX * TY)
+template <typename T, int V>
+__global__ void __launch_bounds__(32 * kWarps)
 stencil_kernel(const T* __restrict__ eps, const T* __restrict__ xin, T* __restrict__ yout,
-               int L, int ntx, int zchunk, T shift, T hop, int periodic_i, int64_t n) {
-  __shared__ T tile[TY + 2][TX + 2];
+               int L, int nseg, int zchunk, T shift, T hop, int periodic_i, int64_t n) {
   const bool periodic = periodic_i != 0;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int w = blockIdx.x * kWarps + warp;
+  if (w >= L * nseg) return;
+  const int yy = w / nseg, seg = w - yy * nseg;
+  const int z0 = blockIdx.y * zchunk;
+  const int z1 = min(z0 + zchunk, L);
   const int64_t LL = (int64_t)L * L;
   const T* __restrict__ x = xin + (int64_t)blockIdx.z * n;
   T* __restrict__ y = yout + (int64_t)blockIdx.z * n;
-  const int tx0 = (blockIdx.x % ntx) * TX;
-  const int ty0 = (blockIdx.x / ntx) * TY;
-  const int z0 = blockIdx.y * zchunk;
-  const int z1 = min(z0 + zchunk, L);
-  if (z0 >= L) return;
-  const int lx = threadIdx.x, ly = threadIdx.y;
-  const int gx = tx0 + lx, gy = ty0 + ly;
-  const bool own = gx < L && gy < L;
-  // coordinates this thread's register column holds (wrapped for periodic,
-  // zero outside for hard walls)
-  const int wx = periodic ? gx % L : gx;
-  const int wy = periodic ? gy % L : gy;
-  const bool in_xy = periodic || own;
 
-  // halo perimeter: cells of the (TY+2) x (TX+2) frame, filled by the first
-  // threads of the block
-  const int tid = ly * TX + lx;
-  constexpr int kPerim = 2 * (TX + 2) + 2 * TY;
-  int hr = 0, hc = 0;
-  if (tid < kPerim) {
-    if (tid < TX + 2) { hr = 0; hc = tid; }
-    else if (tid < 2 * (TX + 2)) { hr = TY + 1; hc = tid - (TX + 2); }
-    else { int k = tid - 2 * (TX + 2); hr = 1 + (k >> 1); hc = (k & 1) ? TX + 1 : 0; }
+  int xi[V], xl[V], xr[V];
+  bool ok[V], okl[V], okr[V];
+#pragma unroll
+  for (int v = 0; v < V; ++v) {
+    xi[v] = seg * 32 * V + lane + 32 * v;
+    ok[v] = xi[v] < L;
+    xl[v] = xi[v] - 1;
+    xr[v] = xi[v] + 1;
+    okl[v] = ok[v] && (periodic || xl[v] >= 0);
+    okr[v] = ok[v] && (periodic || xr[v] < L);
+    if (xl[v] < 0) xl[v] += L;
+    if (xr[v] >= L) xr[v] -= L;
   }
-  int hx = tx0 + hc - 1, hy = ty0 + hr - 1;
-  bool h_in = true;
-  if (periodic) {
-    hx = (hx + L) % L;
-    hy = (hy + L) % L;
-  } else {
-    h_in = hx >= 0 && hx < L && hy >= 0 && hy < L;
-  }
+  int ym = yy - 1, yp = yy + 1;
+  const bool okym = periodic || ym >= 0, okyp = periodic || yp < L;
+  if (ym < 0) ym += L;
+  if (yp >= L) yp -= L;
 
-  T prev = load_site(x, L, LL, wx, wy, z0 - 1, in_xy, periodic);
-  T cur = load_site(x, L, LL, wx, wy, z0, in_xy, periodic);
-  T next;
-  for (int z = z0; z < z1; ++z) {
-    next = load_site(x, L, LL, wx, wy, z + 1, in_xy, periodic);
-    tile[ly + 1][lx + 1] = cur;
-    if (tid < kPerim) tile[hr][hc] = load_site(x, L, LL, hx, hy, z, h_in, periodic);
-    __syncthreads();
-    if (own) {
-      const int64_t s = (int64_t)z * LL + (int64_t)gy * L + gx;
-      T nb = tile[ly + 1][lx] + tile[ly + 1][lx + 2];
-      nb += tile[ly][lx + 1] + tile[ly + 2][lx + 1];
-      nb += prev + next;
-      y[s] = (__ldg(eps + s) - shift) * cur + hop * nb;
+  // Software pipeline: x of planes z-1, z, z+1 are consumed at step z while
+  // plane z+2 (x) and z+1 (eps) are in flight; planes further ahead are
+  // prefetched into L2 so that the register loads hit L2 rather than HBM.
+  auto wrapz = [&](int z, bool& okz) {
+    okz = periodic || (z >= 0 && z < L);
+    if (z < 0) z += L;
+    if (z >= L) z -= L;
+    return z;
+  };
+  T xm[V], xc[V], xp[V], xpp[V], ec[V], en[V];
+  {
+    bool o1, o2, o3;
+    const int za = wrapz(z0 - 1, o1), zb = wrapz(z0 + 1, o2);
+    const int64_t bm = (int64_t)za * LL + (int64_t)yy * L, b0 = (int64_t)z0 * LL + (int64_t)yy * L;
+    const int64_t bp = (int64_t)zb * LL + (int64_t)yy * L;
+    (void)o3;
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      xm[v] = ldv(x, bm + xi[v], ok[v] && o1);
+      xc[v] = ldv(x, b0 + xi[v], ok[v]);
+      xp[v] = ldv(x, bp + xi[v], ok[v] && o2);
+      ec[v] = ldv(eps, b0 + xi[v], ok[v]);
     }
-    __syncthreads();
-    prev = cur;
-    cur = next;
+  }
+  constexpr int kPrefetch = 6;
+  for (int z = z0; z < z1; ++z) {
+    bool okpp, oke, okf;
+    const int zpp = wrapz(z + 2, okpp);
+    const int ze = wrapz(z + 1, oke);
+    const int zf = wrapz(z + kPrefetch, okf);
+    const int64_t row = (int64_t)z * LL + (int64_t)yy * L;
+    const int64_t rowpp = (int64_t)zpp * LL + (int64_t)yy * L;
+    const int64_t rowe = (int64_t)ze * LL + (int64_t)yy * L;
+    const int64_t rowf = (int64_t)zf * LL + (int64_t)yy * L;
+    const int64_t rowym = (int64_t)z * LL + (int64_t)ym * L;
+    const int64_t rowyp = (int64_t)z * LL + (int64_t)yp * L;
+    const bool more = z + 1 < z1;  // planes beyond this chunk are not needed
+    T nb[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      xpp[v] = ldv(x, rowpp + xi[v], ok[v] && okpp && (z + 2 <= z1));
+      en[v] = ldv(eps, rowe + xi[v], ok[v] && oke && more);
+      if (ok[v] && okf && z + kPrefetch <= z1) {
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(x + rowf + xi[v]));
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(eps + rowf + xi[v]));
+      }
+      nb[v] = ldv(x, row + xl[v], okl[v]) + ldv(x, row + xr[v], okr[v]);
+      nb[v] += ldv(x, rowym + xi[v], ok[v] && okym) + ldv(x, rowyp + xi[v], ok[v] && okyp);
+    }
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      if (ok[v]) y[row + xi[v]] = (ec[v] - shift) * xc[v] + hop * (nb[v] + xm[v] + xp[v]);
+      xm[v] = xc[v];
+      xc[v] = xp[v];
+      xp[v] = xpp[v];
+      ec[v] = en[v];
+    }
   }
 }
 
 }  // namespace
 
-template <typename T>
-int stencil_apply(const anderson_s* h, T shift, const T* x, T* y, int m, cudaStream_t stream) {
-  if (m == 0) return JD_OK;
-  const int L = h->L;
-  const int ntx = ceil_div(L, TX), nty = ceil_div(L, TY);
-  const int tiles = ntx * nty;
+template <typename T, int V>
+static void launch_stencil(const T* eps, const T* x, T* y, int L, int m, T shift, T hop,
+                           int periodic, int64_t n, cudaStream_t stream) {
+  const int nseg = ceil_div(L, 32 * V);
+  const int units = L * nseg;
+  const int bx = ceil_div(units, kWarps);
+  // enough CTAs to fill every SM several times over; z-chunks split the rest
   const int target = 8 * sm_count();
-  int nchunk = ceil_div(target, tiles);
+  int nchunk = ceil_div(target, (int64_t)bx * m);
   if (nchunk > L) nchunk = L;
   if (nchunk < 1) nchunk = 1;
   const int zchunk = ceil_div(L, nchunk);
   nchunk = ceil_div(L, zchunk);
+  dim3 grid(bx, nchunk, m);
+  stencil_kernel<T, V><<<grid, 32 * kWarps, 0, stream>>>(eps, x, y, L, nseg, zchunk, shift, hop,
+                                                         periodic, n);
+}
+
+template <typename T>
+int stencil_apply(const anderson_s* h, T shift, const T* x, T* y, int m, cudaStream_t stream) {
+  if (m == 0) return JD_OK;
   if (m > 65535) return fail(JD_EINVAL, "anderson_apply: at most 65535 vectors per call");
-  dim3 grid(tiles, nchunk, m), block(TX, TY);
   const T* eps = nullptr;
   if constexpr (sizeof(T) == 8) eps = reinterpret_cast<const T*>(h->eps64);
   else eps = reinterpret_cast<const T*>(h->eps32);
-  stencil_kernel<T><<<grid, block, 0, stream>>>(eps, x, y, L, ntx, zchunk, shift, (T)h->hop,
-                                                h->bc == JD_PERIODIC ? 1 : 0, h->n);
+  const int L = h->L, per = h->bc == JD_PERIODIC ? 1 : 0;
+  const T hop = (T)h->hop;
+  if (L <= 32) launch_stencil<T, 1>(eps, x, y, L, m, shift, hop, per, h->n, stream);
+  else if (L <= 64) launch_stencil<T, 2>(eps, x, y, L, m, shift, hop, per, h->n, stream);
+  else if (L <= 96) launch_stencil<T, 3>(eps, x, y, L, m, shift, hop, per, h->n, stream);
+  else launch_stencil<T, 4>(eps, x, y, L, m, shift, hop, per, h->n, stream);
   AJD_CHECK_LAUNCH();
   return JD_OK;
 }

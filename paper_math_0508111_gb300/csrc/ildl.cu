@@ -1,0 +1,484 @@
+// Device part of the multilevel incomplete LDL^T preconditioner: upload of
+// the host factor and the application x = K^{-1} b.
+//
+// K^{-1} b = P^T S L^{-T} D^{-1} L^{-1} S P b.  Positions are ordered level by
+// level and every level's pivots are mutually independent, so the forward
+// solve with L is one parallel sweep per level (each row of level l only
+// reads rows of earlier levels) and the backward solve with L^T is one
+// parallel sweep per level in reverse.  The gather/scale P, S is fused into
+// the forward sweeps, the block diagonal D^{-1} (1x1 and 2x2 pivots) and the
+// scatter into the backward sweeps, and the trailing dense block is one
+// matrix-vector product with its stored inverse.  Every stored entry of L is
+// read exactly once per sweep, so the apply streams 2 * nnz(L) * (value +
+// index) bytes plus a few vectors.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <new>
+
+#include "anderson_impl.cuh"
+#include "ildl_impl.cuh"
+#include "ildl_setup.h"
+
+namespace ajd {
+namespace {
+
+constexpr int kRowThreads = 256;
+
+// Forward sweep of one level: w[p] = s[p] b[perm[p]] - sum_q L[p,q] w[q]
+// for positions p in [p0, p1); G threads per row.
+template <typename T, int G>
+__global__ void __launch_bounds__(kRowThreads)
+fwd_level_kernel(const int* __restrict__ ptr, const int* __restrict__ col, const T* __restrict__ val,
+                 const T* __restrict__ scale, const int* __restrict__ perm, const T* __restrict__ b,
+                 T* __restrict__ w, int p0, int p1) {
+  const int lane = threadIdx.x % G;
+  const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; ; t += nthreads) {
+    const int64_t rr = t / G;
+    const int p = p0 + (int)rr;
+    const bool active = p < p1;
+    if (__all_sync(0xffffffffu, !active)) break;
+    T acc = T(0);
+    if (active) {
+      const int e = ptr[p + 1];
+      for (int q = ptr[p] + lane; q < e; q += G) acc += val[q] * w[col[q]];
+    }
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, G);
+    if (active && lane == 0) w[p] = scale[p] * b[perm[p]] - acc;
+  }
+}
+
+// Level 0 has no entries of L: w[p] = s[p] b[perm[p]].
+template <typename T>
+__global__ void gather_kernel(const T* __restrict__ scale, const int* __restrict__ perm,
+                              const T* __restrict__ b, T* __restrict__ w, int p0, int p1) {
+  for (int p = p0 + blockIdx.x * blockDim.x + threadIdx.x; p < p1; p += gridDim.x * blockDim.x)
+    w[p] = scale[p] * b[perm[p]];
+}
+
+// Dense trailing block: z[d0 + r] = sum_c Dinv[r][c] w[d0 + c], also
+// scattered to the output: out[perm[d0 + r]] = s[d0 + r] z[d0 + r].
+// One warp per row.
+template <typename T>
+__global__ void dense_kernel(const T* __restrict__ dinv, int nd, int d0, const T* __restrict__ w,
+                             T* __restrict__ z, const T* __restrict__ scale, const int* __restrict__ perm,
+                             T* __restrict__ out) {
+  const int lane = threadIdx.x & 31;
+  const int warps = (gridDim.x * blockDim.x) >> 5;
+  for (int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < nd; r += warps) {
+    const T* row = dinv + (int64_t)r * nd;
+    T acc = T(0);
+    for (int c = lane; c < nd; c += 32) acc += row[c] * w[d0 + c];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) {
+      z[d0 + r] = acc;
+      out[perm[d0 + r]] = scale[d0 + r] * acc;
+    }
+  }
+}
+
+// Backward sweep of one level: z[p] = (D^{-1} w)_p - sum_q L^T[p,q] z[q],
+// out[perm[p]] = s[p] z[p].
+template <typename T, int G>
+__global__ void __launch_bounds__(kRowThreads)
+bwd_level_kernel(const int* __restrict__ ptr, const int* __restrict__ col, const T* __restrict__ val,
+                 const T* __restrict__ dd, const T* __restrict__ dof, const int* __restrict__ partner,
+                 const T* __restrict__ w, T* __restrict__ z, const T* __restrict__ scale,
+                 const int* __restrict__ perm, T* __restrict__ out, int p0, int p1) {
+  const int lane = threadIdx.x % G;
+  const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; ; t += nthreads) {
+    const int p = p0 + (int)(t / G);
+    const bool active = p < p1;
+    if (__all_sync(0xffffffffu, !active)) break;
+    T acc = T(0);
+    if (active) {
+      const int e = ptr[p + 1];
+      for (int q = ptr[p] + lane; q < e; q += G) acc += val[q] * z[col[q]];
+    }
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, G);
+    if (active && lane == 0) {
+      const int pp = partner[p];
+      T d = dd[p] * w[p];
+      if (pp >= 0) d += dof[p] * w[pp];
+      const T zp = d - acc;
+      z[p] = zp;
+      out[perm[p]] = scale[p] * zp;
+    }
+  }
+}
+
+template <typename T>
+void free_dev(DevFactor<T>& d) {
+  cudaFree(d.perm);
+  cudaFree(d.scale);
+  cudaFree(d.Lptr);
+  cudaFree(d.Lcol);
+  cudaFree(d.Lval);
+  cudaFree(d.Uptr);
+  cudaFree(d.Ucol);
+  cudaFree(d.Uval);
+  cudaFree(d.dd);
+  cudaFree(d.dof);
+  cudaFree(d.partner);
+  cudaFree(d.dense);
+  cudaFree(d.w);
+  cudaFree(d.z);
+  d = DevFactor<T>();
+}
+
+template <typename S, typename D>
+int upload(D** dst, const std::vector<S>& src) {
+  *dst = nullptr;
+  if (src.empty()) return JD_OK;
+  std::vector<D> tmp(src.begin(), src.end());
+  cudaError_t e = cudaMalloc(dst, tmp.size() * sizeof(D));
+  if (e != cudaSuccess) return fail(e == cudaErrorMemoryAllocation ? JD_ENOMEM : JD_EDEVICE, "ildl upload: %s", cudaGetErrorString(e));
+  AJD_CUDA(cudaMemcpy(*dst, tmp.data(), tmp.size() * sizeof(D), cudaMemcpyHostToDevice));
+  return JD_OK;
+}
+
+template <typename T>
+int upload_factor(const HostFactor& F, DevFactor<T>& d) {
+  if (F.Lcol.size() >= (size_t)1 << 31) return fail(JD_ENOMEM, "ildl: factor has more than 2^31 entries");
+  std::vector<int> lp(F.Lptr.begin(), F.Lptr.end()), up(F.Uptr.begin(), F.Uptr.end());
+  AJD_TRY(upload(&d.perm, F.perm));
+  AJD_TRY(upload(&d.scale, F.scale));
+  AJD_TRY(upload(&d.Lptr, lp));
+  AJD_TRY(upload(&d.Lcol, F.Lcol));
+  AJD_TRY(upload(&d.Lval, F.Lval));
+  AJD_TRY(upload(&d.Uptr, up));
+  AJD_TRY(upload(&d.Ucol, F.Ucol));
+  AJD_TRY(upload(&d.Uval, F.Uval));
+  AJD_TRY(upload(&d.dd, F.dinv_d));
+  AJD_TRY(upload(&d.dof, F.dinv_o));
+  AJD_TRY(upload(&d.partner, F.partner));
+  AJD_TRY(upload(&d.dense, F.dense_inv));
+  AJD_CUDA(cudaMalloc(&d.w, std::max<size_t>(1, F.n) * sizeof(T)));
+  AJD_CUDA(cudaMalloc(&d.z, std::max<size_t>(1, F.n) * sizeof(T)));
+  d.ready = true;
+  return JD_OK;
+}
+
+template <typename T, int G>
+void launch_fwd(const DevFactor<T>& d, const T* b, int p0, int p1, cudaStream_t s) {
+  const int64_t threads = (int64_t)(p1 - p0) * G;
+  const int blocks = (int)std::min<int64_t>((threads + kRowThreads - 1) / kRowThreads, 32 * sm_count());
+  fwd_level_kernel<T, G><<<blocks, kRowThreads, 0, s>>>(d.Lptr, d.Lcol, d.Lval, d.scale, d.perm, b, d.w, p0, p1);
+}
+
+template <typename T, int G>
+void launch_bwd(const DevFactor<T>& d, T* out, int p0, int p1, cudaStream_t s) {
+  const int64_t threads = (int64_t)(p1 - p0) * G;
+  const int blocks = (int)std::min<int64_t>((threads + kRowThreads - 1) / kRowThreads, 32 * sm_count());
+  bwd_level_kernel<T, G><<<blocks, kRowThreads, 0, s>>>(d.Uptr, d.Ucol, d.Uval, d.dd, d.dof, d.partner, d.w, d.z,
+                                                       d.scale, d.perm, out, p0, p1);
+}
+
+}  // namespace
+
+template <typename T>
+int ildl_apply_dev(const ildl_s* f, const T* b, T* out, cudaStream_t s) {
+  const DevFactor<T>& d = f->dev<T>();
+  if (!d.ready) return fail(JD_EINVAL, "ildl_apply: factor has no device copy (use ildl_create)");
+  const HostFactor& F = f->F;
+  const int nl = F.nlev;
+  const std::vector<int>& lp = F.level_ptr;
+  if (F.n == 0) return JD_OK;
+  // forward: level 0 is a pure gather; levels 1..nl-1 and the dense rows read
+  // earlier levels
+  {
+    const int p0 = lp[0], p1 = lp[1];
+    if (p1 > p0) {
+      const int blocks = std::min(ceil_div(p1 - p0, 256), 16 * sm_count());
+      gather_kernel<T><<<blocks, 256, 0, s>>>(d.scale, d.perm, b, d.w, p0, p1);
+    }
+  }
+  for (int l = 1; l <= nl; ++l) {
+    const int p0 = lp[l], p1 = lp[l + 1];
+    if (p1 <= p0) continue;
+    const int64_t nnz = F.Lptr[p1] - F.Lptr[p0];
+    const double avg = (double)nnz / (p1 - p0);
+    if (avg > 24) launch_fwd<T, 16>(d, b, p0, p1, s);
+    else if (avg > 6) launch_fwd<T, 8>(d, b, p0, p1, s);
+    else launch_fwd<T, 4>(d, b, p0, p1, s);
+  }
+  AJD_CHECK_LAUNCH();
+  if (F.n_dense > 0) {
+    const int d0 = lp[nl];
+    const int blocks = std::min(ceil_div((int64_t)F.n_dense * 32, 256), 8 * sm_count());
+    dense_kernel<T><<<blocks, 256, 0, s>>>(d.dense, F.n_dense, d0, d.w, d.z, d.scale, d.perm, out);
+  }
+  for (int l = nl - 1; l >= 0; --l) {
+    const int p0 = lp[l], p1 = lp[l + 1];
+    if (p1 <= p0) continue;
+    const int64_t nnz = F.Uptr[p1] - F.Uptr[p0];
+    const double avg = (double)nnz / (p1 - p0);
+    if (avg > 24) launch_bwd<T, 16>(d, out, p0, p1, s);
+    else if (avg > 6) launch_bwd<T, 8>(d, out, p0, p1, s);
+    else launch_bwd<T, 4>(d, out, p0, p1, s);
+  }
+  AJD_CHECK_LAUNCH();
+  return JD_OK;
+}
+
+template int ildl_apply_dev<double>(const ildl_s*, const double*, double*, cudaStream_t);
+template int ildl_apply_dev<float>(const ildl_s*, const float*, float*, cudaStream_t);
+
+int ildl_upload_all(ildl_s* f) {
+  AJD_TRY(upload_factor<double>(f->F, f->d64));
+  AJD_TRY(upload_factor<float>(f->F, f->d32));
+  return JD_OK;
+}
+
+void ildl_free_device(ildl_s* f) {
+  free_dev(f->d64);
+  free_dev(f->d32);
+}
+
+// CSR of A - sigma I for a lattice (host, from the binary64 potential).
+int lattice_csr(const anderson_s* h, const std::vector<double>& eps, double sigma, SymCsr& A) {
+  const int L = h->L;
+  const int64_t n = h->n;
+  const bool per = h->bc == JD_PERIODIC;
+  A.n = (int)n;
+  A.ptr.assign(n + 1, 0);
+  A.col.clear();
+  A.val.clear();
+  A.col.reserve(7 * n);
+  A.val.reserve(7 * n);
+  int nb[7];
+  double nv[7];
+  for (int64_t s = 0; s < n; ++s) {
+    const int x = (int)(s % L), y = (int)((s / L) % L), z = (int)(s / ((int64_t)L * L));
+    int k = 0;
+    auto add = [&](int xx, int yy, int zz) {
+      if (per) {
+        xx = (xx + L) % L;
+        yy = (yy + L) % L;
+        zz = (zz + L) % L;
+      } else if (xx < 0 || xx >= L || yy < 0 || yy >= L || zz < 0 || zz >= L) {
+        return;
+      }
+      nb[k] = (int)(xx + (int64_t)L * (yy + (int64_t)L * zz));
+      nv[k] = h->hop;
+      ++k;
+    };
+    add(x - 1, y, z);
+    add(x + 1, y, z);
+    add(x, y - 1, z);
+    add(x, y + 1, z);
+    add(x, y, z - 1);
+    add(x, y, z + 1);
+    nb[k] = (int)s;
+    nv[k] = eps[s] - sigma;
+    ++k;
+    // sort by column (insertion sort on 7 entries)
+    for (int a = 1; a < k; ++a)
+      for (int b = a; b > 0 && nb[b] < nb[b - 1]; --b) {
+        std::swap(nb[b], nb[b - 1]);
+        std::swap(nv[b], nv[b - 1]);
+      }
+    for (int a = 0; a < k; ++a) {
+      A.col.push_back(nb[a]);
+      A.val.push_back(nv[a]);
+    }
+    A.ptr[s + 1] = (int64_t)A.col.size();
+  }
+  return JD_OK;
+}
+
+}  // namespace ajd
+
+using namespace ajd;
+
+extern "C" int ildl_params_default(ildl_params* p) {
+  if (!p) return fail(JD_EINVAL, "ildl_params_default: NULL");
+  p->kappa = 5.0;
+  p->drop = -1.0;
+  p->gamma = 0.02;
+  p->max_levels = 96;
+  p->n_dense = 1000;
+  p->matching = 1;
+  return JD_OK;
+}
+
+static int check_params(const ildl_params* p, ildl_params& out) {
+  if (p) out = *p;
+  else ildl_params_default(&out);
+  if (!(out.kappa > 1.0)) return fail(JD_EINVAL, "ildl: kappa must be > 1");
+  if (!std::isfinite(out.drop) && out.drop > 0) return fail(JD_EINVAL, "ildl: drop must be finite");
+  if (!(out.gamma >= 0.0) || out.gamma >= 1.0) return fail(JD_EINVAL, "ildl: gamma must be in [0, 1)");
+  if (out.max_levels < 1 || out.n_dense < 1 || out.n_dense > 6000)
+    return fail(JD_EINVAL, "ildl: max_levels >= 1 and 1 <= n_dense <= 6000 required");
+  return JD_OK;
+}
+
+extern "C" int ildl_setup_csr(int n, const int64_t* rowptr, const int* col, const double* val,
+                              const ildl_params* p, ildl_t* out) {
+  if (!out) return fail(JD_EINVAL, "ildl_setup_csr: out is NULL");
+  *out = nullptr;
+  if (n <= 0 || !rowptr || !col || !val) return fail(JD_EINVAL, "ildl_setup_csr: bad matrix arguments");
+  ildl_params prm;
+  AJD_TRY(check_params(p, prm));
+  try {
+    SymCsr A;
+    A.n = n;
+    A.ptr.assign(rowptr, rowptr + n + 1);
+    if (A.ptr[0] != 0) return fail(JD_EINVAL, "ildl_setup_csr: rowptr[0] must be 0");
+    const int64_t nnz = A.ptr[n];
+    A.col.assign(col, col + nnz);
+    A.val.assign(val, val + nnz);
+    // ensure sorted rows with a diagonal entry
+    SymCsr B;
+    B.n = n;
+    B.ptr.assign(n + 1, 0);
+    for (int i = 0; i < n; ++i) {
+      bool has_diag = false;
+      int prev = -1;
+      for (int64_t q = A.ptr[i]; q < A.ptr[i + 1]; ++q) {
+        const int c = A.col[q];
+        if (c < 0 || c >= n || c <= prev) return fail(JD_EINVAL, "ildl_setup_csr: row %d not sorted/unique or out of range", i);
+        if (c > i && !has_diag) { B.col.push_back(i); B.val.push_back(0.0); has_diag = true; }
+        if (c == i) has_diag = true;
+        B.col.push_back(c);
+        B.val.push_back(A.val[q]);
+        prev = c;
+      }
+      if (!has_diag) { B.col.push_back(i); B.val.push_back(0.0); }
+      B.ptr[i + 1] = (int64_t)B.col.size();
+    }
+    ildl_s* f = new ildl_s();
+    int rc = build_ildl(B, prm, f->F);
+    if (rc != JD_OK) {
+      delete f;
+      return rc;
+    }
+    *out = f;
+    return JD_OK;
+  } catch (const std::bad_alloc&) {
+    return fail(JD_ENOMEM, "ildl_setup_csr: out of host memory");
+  }
+}
+
+extern "C" int ildl_matching(int n, const int64_t* rowptr, const int* col, const double* val, int* match_col,
+                             double* scale, int* partner) {
+  if (n <= 0 || !rowptr || !col || !val || !match_col || !scale || !partner)
+    return fail(JD_EINVAL, "ildl_matching: bad arguments");
+  try {
+    SymCsr A;
+    A.n = n;
+    A.ptr.assign(rowptr, rowptr + n + 1);
+    A.col.assign(col, col + A.ptr[n]);
+    A.val.assign(val, val + A.ptr[n]);
+    std::vector<int> mc;
+    std::vector<double> u, v, rmax;
+    max_product_matching(A, mc, u, v, rmax);
+    SymCsr S = A;
+    for (int i = 0; i < n; ++i) {
+      scale[i] = std::sqrt(std::exp(u[i] + v[i]) / rmax[i]);
+      match_col[i] = mc[i];
+    }
+    for (int i = 0; i < n; ++i)
+      for (int64_t p = S.ptr[i]; p < S.ptr[i + 1]; ++p) S.val[p] *= scale[i] * scale[S.col[p]];
+    std::vector<std::pair<int, int>> groups;
+    split_cycles(S, mc, groups);
+    for (int i = 0; i < n; ++i) partner[i] = -1;
+    for (const auto& g : groups)
+      if (g.second >= 0) {
+        partner[g.first] = g.second;
+        partner[g.second] = g.first;
+      }
+    return JD_OK;
+  } catch (const std::bad_alloc&) {
+    return fail(JD_ENOMEM, "ildl_matching: out of host memory");
+  }
+}
+
+extern "C" int ildl_create(anderson_t h, double sigma, const ildl_params* p, ildl_t* out) {
+  if (!out || !h) return fail(JD_EINVAL, "ildl_create: NULL argument");
+  *out = nullptr;
+  if (!std::isfinite(sigma)) return fail(JD_EINVAL, "ildl_create: sigma must be finite");
+  ildl_params prm;
+  AJD_TRY(check_params(p, prm));
+  try {
+    std::vector<double> eps(h->n);
+    AJD_CUDA(cudaMemcpy(eps.data(), h->eps64, h->n * sizeof(double), cudaMemcpyDeviceToHost));
+    SymCsr A;
+    lattice_csr(h, eps, sigma, A);
+    ildl_s* f = new ildl_s();
+    f->device = h->device;
+    int rc = build_ildl(A, prm, f->F);
+    if (rc == JD_OK) rc = ildl_upload_all(f);
+    if (rc != JD_OK) {
+      ildl_free_device(f);
+      delete f;
+      return rc;
+    }
+    *out = f;
+    return JD_OK;
+  } catch (const std::bad_alloc&) {
+    return fail(JD_ENOMEM, "ildl_create: out of host memory");
+  }
+}
+
+extern "C" int ildl_info(ildl_t f, ildl_info_t* info) {
+  if (!f || !info) return fail(JD_EINVAL, "ildl_info: NULL argument");
+  const HostFactor& F = f->F;
+  info->n = F.n;
+  info->levels = F.nlev;
+  info->n_dense = F.n_dense;
+  info->n_2x2 = F.n_2x2;
+  info->nnz_L = (int64_t)F.Lcol.size();
+  info->nnz_A = F.nnz_A;
+  const double nnzD = (double)(F.n - F.n_dense) + 2.0 * F.n_2x2 + (double)F.n_dense * F.n_dense;
+  info->fill = F.nnz_A > 0 ? (2.0 * (double)F.Lcol.size() + nnzD) / (double)F.nnz_A : 0.0;
+  info->setup_ms = F.t_total_ms;
+  info->match_ms = F.t_match_ms;
+  return JD_OK;
+}
+
+extern "C" int ildl_export(ildl_t f, int* perm, double* scale, int* level_ptr, int64_t* Lptr, int* Lcol,
+                           double* Lval, double* dinv_d, double* dinv_o, int* partner, double* dense_inv) {
+  if (!f) return fail(JD_EINVAL, "ildl_export: NULL handle");
+  const HostFactor& F = f->F;
+  if (perm) std::copy(F.perm.begin(), F.perm.end(), perm);
+  if (scale) std::copy(F.scale.begin(), F.scale.end(), scale);
+  if (level_ptr) std::copy(F.level_ptr.begin(), F.level_ptr.end(), level_ptr);
+  if (Lptr) std::copy(F.Lptr.begin(), F.Lptr.end(), Lptr);
+  if (Lcol) std::copy(F.Lcol.begin(), F.Lcol.end(), Lcol);
+  if (Lval) std::copy(F.Lval.begin(), F.Lval.end(), Lval);
+  if (dinv_d) std::copy(F.dinv_d.begin(), F.dinv_d.end(), dinv_d);
+  if (dinv_o) std::copy(F.dinv_o.begin(), F.dinv_o.end(), dinv_o);
+  if (partner) std::copy(F.partner.begin(), F.partner.end(), partner);
+  if (dense_inv) std::copy(F.dense_inv.begin(), F.dense_inv.end(), dense_inv);
+  return JD_OK;
+}
+
+extern "C" int ildl_apply(ildl_t f, const void* b, void* x, int precision, void* stream) {
+  if (!f || !b || !x) return fail(JD_EINVAL, "ildl_apply: NULL argument");
+  if (b == x) return fail(JD_EINVAL, "ildl_apply: b and x must be distinct");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (precision == JD_FP64)
+    return ildl_apply_dev<double>(f, static_cast<const double*>(b), static_cast<double*>(x), s);
+  if (precision == JD_FP32)
+    return ildl_apply_dev<float>(f, static_cast<const float*>(b), static_cast<float*>(x), s);
+  return fail(JD_EINVAL, "ildl_apply: unknown precision %d", precision);
+}
+
+extern "C" int ildl_destroy(ildl_t f) {
+  if (!f) return JD_OK;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (f->d64.ready || f->d32.ready) {
+    cudaSetDevice(f->device);
+    ildl_free_device(f);
+    cudaSetDevice(dev);
+  }
+  delete f;
+  return JD_OK;
+}

@@ -1,0 +1,48 @@
+// Internal state of a preconditioner handle.
+#pragma once
+#include "common.cuh"
+#include "ildl_setup.h"
+
+namespace ajd {
+
+// Device copy of a HostFactor in one precision.
+template <typename T>
+struct DevFactor {
+  bool ready = false;
+  int* perm = nullptr;
+  T* scale = nullptr;
+  int* Lptr = nullptr;
+  int* Lcol = nullptr;
+  T* Lval = nullptr;
+  int* Uptr = nullptr;
+  int* Ucol = nullptr;
+  T* Uval = nullptr;
+  T* dd = nullptr;
+  T* dof = nullptr;
+  int* partner = nullptr;
+  T* dense = nullptr;
+  T* w = nullptr;  // work vectors in position space
+  T* z = nullptr;
+};
+
+}  // namespace ajd
+
+struct ildl_s {
+  ajd::HostFactor F;
+  int device = 0;
+  ajd::DevFactor<double> d64;
+  ajd::DevFactor<float> d32;
+  template <typename T>
+  const ajd::DevFactor<T>& dev() const {
+    if constexpr (sizeof(T) == 8) return d64;
+    else return d32;
+  }
+};
+
+namespace ajd {
+
+// x = K^{-1} b on `stream` (device pointers, n elements).
+template <typename T>
+int ildl_apply_dev(const ildl_s* f, const T* b, T* out, cudaStream_t stream);
+
+}  // namespace ajd

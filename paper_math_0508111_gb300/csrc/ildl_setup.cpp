@@ -1,0 +1,813 @@
+// Host construction of the multilevel incomplete LDL^T preconditioner.
+//
+// Per level (Section 6.3: reordering, scaling and factorization are applied
+// recursively to the Schur complement of the postponed part):
+//   1. maximum-product matching (Section 5.1, Eqs. (5.1)-(5.2)) by a sparse
+//      shortest-augmenting-path assignment solver with dual potentials;
+//   2. symmetric scaling from the duals (entries <= 1 in modulus, matched
+//      entries equal to 1; Section 4.2) and the split of the matching's
+//      cycles into 1x1 and 2x2 candidate pivots (Section 5.2);
+//   3. the 1x1 / 2x2 choice by the d1/d2 block diagonal dominance rule and
+//      inverse-based pivoting: a pivot is only taken if the level's
+//      ||L^{-1}||_1 stays <= kappa, otherwise it is postponed (Section 6.2);
+//   4. ordering: instead of AMD on the compressed graph (Section 5.3), an
+//      independent set of the compressed graph's candidates (couplings below
+//      gamma ignored) is eliminated, best pivots first.  Each level's block of
+//      pivots is then block diagonal, so every level is ONE parallel step of
+//      the triangular solves on the GPU;
+//   5. the level's column block of L is dropped at epsilon/kappa (Section
+//      6.2) and the Schur complement S = C - L D L^T formed explicitly and
+//      dropped the same way; the recursion continues on S until it is small
+//      enough to be factored densely.
+// The levels are finally concatenated into one global unit lower triangular
+// L (rows ordered level by level), one block diagonal D and one scaling.
+#include "ildl_setup.h"
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <limits>
+#include <numeric>
+#include <queue>
+#include <utility>
+#include <cstdio>
+#include <cstdlib>
+
+namespace ajd {
+
+int fail(int code, const char* fmt, ...);
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+double ms_since(Clock::time_point t0) {
+  return std::chrono::duration<double, std::milli>(Clock::now() - t0).count();
+}
+
+constexpr double kInf = std::numeric_limits<double>::infinity();
+
+double lookup(const SymCsr& S, int i, int j) {
+  const int* b = S.col.data() + S.ptr[i];
+  const int* e = S.col.data() + S.ptr[i + 1];
+  const int* p = std::lower_bound(b, e, j);
+  return (p != e && *p == j) ? S.val[p - S.col.data()] : 0.0;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Section 5.1: maximise prod_i |a_{sigma(i) i}| <=> minimise sum c_{sigma(i) i}
+// with c_ij = log a_i - log |a_ij|, a_i = max_j |a_ij|.  Sparse Kuhn–Munkres:
+// a zero-reduced-cost greedy start, then one Dijkstra shortest augmenting
+// path per unmatched row over reduced costs c_ij - u_i - v_j >= 0.
+// ---------------------------------------------------------------------------
+int max_product_matching(const SymCsr& A, std::vector<int>& match_col, std::vector<double>& u,
+                         std::vector<double>& v, std::vector<double>& rowmax) {
+  const int n = A.n;
+  rowmax.assign(n, 0.0);
+  for (int i = 0; i < n; ++i)
+    for (int64_t p = A.ptr[i]; p < A.ptr[i + 1]; ++p) rowmax[i] = std::max(rowmax[i], std::fabs(A.val[p]));
+  std::vector<double> logmax(n);
+  for (int i = 0; i < n; ++i) {
+    if (rowmax[i] == 0.0) rowmax[i] = 1.0;
+    logmax[i] = std::log(rowmax[i]);
+  }
+  // cost of entry p (row i, column col[p]); +inf for explicit zeros
+  std::vector<double> cost(A.val.size());
+  for (int i = 0; i < n; ++i)
+    for (int64_t p = A.ptr[i]; p < A.ptr[i + 1]; ++p) {
+      const double a = std::fabs(A.val[p]);
+      cost[p] = a > 0.0 ? logmax[i] - std::log(a) : kInf;
+    }
+  // v_j = min_i c_ij: by symmetry column j's entries are row j's entries,
+  // with the cost taken in the row of the other index.
+  v.assign(n, kInf);
+  for (int j = 0; j < n; ++j)
+    for (int64_t p = A.ptr[j]; p < A.ptr[j + 1]; ++p) {
+      const int i = A.col[p];
+      const double a = std::fabs(A.val[p]);
+      if (a > 0.0) v[j] = std::min(v[j], logmax[i] - std::log(a));
+    }
+  for (int j = 0; j < n; ++j)
+    if (v[j] == kInf) v[j] = 0.0;
+  u.assign(n, kInf);
+  for (int i = 0; i < n; ++i) {
+    for (int64_t p = A.ptr[i]; p < A.ptr[i + 1]; ++p)
+      if (cost[p] < kInf) u[i] = std::min(u[i], cost[p] - v[A.col[p]]);
+    if (u[i] == kInf) u[i] = 0.0;
+  }
+  match_col.assign(n, -1);
+  std::vector<int> match_row(n, -1);
+  // greedy start on zero reduced costs, preferring the diagonal
+  for (int i = 0; i < n; ++i) {
+    int best = -1;
+    for (int64_t p = A.ptr[i]; p < A.ptr[i + 1]; ++p) {
+      const int j = A.col[p];
+      if (match_col[j] >= 0 || cost[p] == kInf) continue;
+      if (cost[p] - u[i] - v[j] <= 1e-13 * (1.0 + std::fabs(u[i]) + std::fabs(v[j]))) {
+        if (best < 0 || j == i) best = j;
+        if (j == i) break;
+      }
+    }
+    if (best >= 0) {
+      match_row[i] = best;
+      match_col[best] = i;
+    }
+  }
+  // shortest augmenting paths
+  std::vector<double> dist(n, kInf);
+  std::vector<int> pred(n, -1);
+  std::vector<char> scanned(n, 0);
+  std::vector<int> touched, scanned_list, tree_rows;
+  std::vector<double> tree_d;
+  using Item = std::pair<double, int>;
+  std::priority_queue<Item, std::vector<Item>, std::greater<Item>> heap;
+  int unmatched = 0;
+  for (int s = 0; s < n; ++s) {
+    if (match_row[s] >= 0) continue;
+    touched.clear();
+    scanned_list.clear();
+    tree_rows.clear();
+    tree_d.clear();
+    while (!heap.empty()) heap.pop();
+    int i = s;
+    double di = 0.0;
+    tree_rows.push_back(s);
+    tree_d.push_back(0.0);
+    int sink = -1;
+    for (;;) {
+      for (int64_t p = A.ptr[i]; p < A.ptr[i + 1]; ++p) {
+        const int j = A.col[p];
+        if (scanned[j] || cost[p] == kInf) continue;
+        const double nd = di + std::max(0.0, cost[p] - u[i] - v[j]);
+        if (nd < dist[j]) {
+          if (dist[j] == kInf) touched.push_back(j);
+          dist[j] = nd;
+          pred[j] = i;
+          heap.push({nd, j});
+        }
+      }
+      int jmin = -1;
+      while (!heap.empty()) {
+        Item it = heap.top();
+        heap.pop();
+        if (!scanned[it.second] && it.first == dist[it.second]) {
+          jmin = it.second;
+          break;
+        }
+      }
+      if (jmin < 0) break;  // no augmenting path from s
+      scanned[jmin] = 1;
+      scanned_list.push_back(jmin);
+      if (match_col[jmin] < 0) {
+        sink = jmin;
+        break;
+      }
+      i = match_col[jmin];
+      di = dist[jmin];
+      tree_rows.push_back(i);
+      tree_d.push_back(di);
+    }
+    if (sink >= 0) {
+      const double D = dist[sink];
+      for (size_t t = 0; t < tree_rows.size(); ++t) u[tree_rows[t]] += D - tree_d[t];
+      for (int j : scanned_list) v[j] += dist[j] - D;
+      int j = sink;
+      for (;;) {
+        const int r = pred[j];
+        const int jprev = match_row[r];
+        match_row[r] = j;
+        match_col[j] = r;
+        if (r == s) break;
+        j = jprev;
+      }
+    } else {
+      ++unmatched;
+    }
+    for (int j : touched) {
+      dist[j] = kInf;
+      pred[j] = -1;
+    }
+    for (int j : scanned_list) scanned[j] = 0;
+  }
+  if (unmatched) {
+    // structurally singular: pair the leftover rows and columns in index
+    // order and give them neutral duals (scaling then reduces to 1/sqrt(a_i))
+    std::vector<int> fr, fc;
+    for (int i = 0; i < n; ++i)
+      if (match_row[i] < 0) fr.push_back(i);
+    for (int j = 0; j < n; ++j)
+      if (match_col[j] < 0) fc.push_back(j);
+    for (size_t t = 0; t < fr.size() && t < fc.size(); ++t) {
+      match_col[fc[t]] = fr[t];
+      u[fr[t]] = 0.0;
+      v[fc[t]] = 0.0;
+    }
+  }
+  return unmatched;
+}
+
+// ---------------------------------------------------------------------------
+// Section 5.2: split the cycles of j -> match_col[j] into 2-cycles and at most
+// one 1-cycle per odd cycle.  Consecutive cycle members always share a
+// matched entry, so every 2x2 block contains one.  Readings: an even cycle
+// takes whichever of its two splits has the larger product of |off-diagonal|
+// entries (ties: fewer nonzeros in the merged rows, then the split that
+// starts at the cycle's first member); an odd cycle keeps as 1x1 the member
+// with the largest |diagonal| (ties: lowest index).
+// ---------------------------------------------------------------------------
+void split_cycles(const SymCsr& S, const std::vector<int>& match_col,
+                  std::vector<std::pair<int, int>>& groups) {
+  const int n = S.n;
+  groups.clear();
+  std::vector<char> seen(n, 0);
+  std::vector<int> cyc;
+  auto union_nnz = [&](int a, int b) {
+    int64_t pa = S.ptr[a], pb = S.ptr[b], cnt = 0;
+    while (pa < S.ptr[a + 1] || pb < S.ptr[b + 1]) {
+      if (pb >= S.ptr[b + 1] || (pa < S.ptr[a + 1] && S.col[pa] < S.col[pb])) ++pa;
+      else if (pa >= S.ptr[a + 1] || S.col[pb] < S.col[pa]) ++pb;
+      else { ++pa; ++pb; }
+      ++cnt;
+    }
+    return cnt;
+  };
+  for (int j0 = 0; j0 < n; ++j0) {
+    if (seen[j0]) continue;
+    cyc.clear();
+    int j = j0;
+    do {
+      seen[j] = 1;
+      cyc.push_back(j);
+      j = match_col[j];
+    } while (j != j0 && j >= 0 && !seen[j]);
+    const int len = (int)cyc.size();
+    if (len == 1) {
+      groups.push_back({cyc[0], -1});
+    } else if (len == 2) {
+      groups.push_back({std::min(cyc[0], cyc[1]), std::max(cyc[0], cyc[1])});
+    } else if (len % 2 == 0) {
+      double score[2] = {0.0, 0.0};
+      int64_t nnz[2] = {0, 0};
+      for (int opt = 0; opt < 2; ++opt)
+        for (int k = opt; k < len + opt; k += 2) {
+          const int a = cyc[k % len], b = cyc[(k + 1) % len];
+          score[opt] += std::log(std::fabs(lookup(S, a, b)) + 1e-300);
+          nnz[opt] += union_nnz(a, b);
+        }
+      int opt = 0;
+      if (score[1] > score[0] || (score[1] == score[0] && nnz[1] < nnz[0])) opt = 1;
+      for (int k = opt; k < len + opt; k += 2) {
+        const int a = cyc[k % len], b = cyc[(k + 1) % len];
+        groups.push_back({std::min(a, b), std::max(a, b)});
+      }
+    } else {
+      int t = 0;
+      for (int k = 1; k < len; ++k) {
+        const double dk = std::fabs(lookup(S, cyc[k], cyc[k])), dt = std::fabs(lookup(S, cyc[t], cyc[t]));
+        if (dk > dt || (dk == dt && cyc[k] < cyc[t])) t = k;
+      }
+      groups.push_back({cyc[t], -1});
+      for (int k = 1; k < len; k += 2) {
+        const int a = cyc[(t + k) % len], b = cyc[(t + k + 1) % len];
+        groups.push_back({std::min(a, b), std::max(a, b)});
+      }
+    }
+  }
+}
+
+namespace {
+
+struct Cand {
+  int a, b;   // nodes (b = -1 for 1x1)
+  double q;   // max column 1-norm of the would-be L block
+};
+
+struct Trip {
+  int r, c;   // original indices
+  double v;
+};
+
+// Gauss–Jordan inverse with partial pivoting (row-major, in place on a copy).
+bool dense_inverse(int m, std::vector<double>& M, std::vector<double>& inv) {
+  inv.assign((size_t)m * m, 0.0);
+  for (int i = 0; i < m; ++i) inv[(size_t)i * m + i] = 1.0;
+  for (int c = 0; c < m; ++c) {
+    int piv = c;
+    double best = std::fabs(M[(size_t)c * m + c]);
+    for (int r = c + 1; r < m; ++r) {
+      const double a = std::fabs(M[(size_t)r * m + c]);
+      if (a > best) { best = a; piv = r; }
+    }
+    if (!(best > 0.0) || !std::isfinite(best)) return false;
+    if (piv != c) {
+      for (int k = 0; k < m; ++k) {
+        std::swap(M[(size_t)c * m + k], M[(size_t)piv * m + k]);
+        std::swap(inv[(size_t)c * m + k], inv[(size_t)piv * m + k]);
+      }
+    }
+    const double d = 1.0 / M[(size_t)c * m + c];
+    double* Mc = &M[(size_t)c * m];
+    double* Ic = &inv[(size_t)c * m];
+    for (int k = 0; k < m; ++k) { Mc[k] *= d; Ic[k] *= d; }
+    for (int r = 0; r < m; ++r) {
+      if (r == c) continue;
+      const double f = M[(size_t)r * m + c];
+      if (f == 0.0) continue;
+      double* Mr = &M[(size_t)r * m];
+      double* Ir = &inv[(size_t)r * m];
+      for (int k = 0; k < m; ++k) { Mr[k] -= f * Mc[k]; Ir[k] -= f * Ic[k]; }
+    }
+  }
+  // symmetrise (the exact inverse of a symmetric matrix is symmetric)
+  for (int i = 0; i < m; ++i)
+    for (int j = i + 1; j < m; ++j) {
+      const double s = 0.5 * (inv[(size_t)i * m + j] + inv[(size_t)j * m + i]);
+      inv[(size_t)i * m + j] = inv[(size_t)j * m + i] = s;
+    }
+  return true;
+}
+
+}  // namespace
+
+int build_ildl(const SymCsr& A, const ildl_params& prm, HostFactor& F) {
+  const auto t_start = Clock::now();
+  const int n = A.n;
+  if (n <= 0) return fail(JD_EINVAL, "ildl: empty matrix");
+  const double kappa = prm.kappa > 1.0 ? prm.kappa : 5.0;
+  const double eps_drop = prm.drop < 0.0 ? 1.0 / std::sqrt((double)n) : prm.drop;
+  const double tau = eps_drop / kappa;
+
+  const double gamma = prm.gamma > 0.0 ? prm.gamma : 0.0;
+  const int max_levels = prm.max_levels > 0 ? prm.max_levels : 64;
+  const int n_dense = prm.n_dense > 0 ? prm.n_dense : 1000;
+  constexpr int kDenseHardMax = 6000;
+
+  F = HostFactor();
+  F.n = n;
+  F.nnz_A = (int64_t)A.col.size();
+
+  SymCsr S = A;
+  std::vector<int> gid(n);
+  std::iota(gid.begin(), gid.end(), 0);
+  std::vector<double> cum(n, 1.0);
+
+  std::vector<int> order;          // original ids in elimination order
+  order.reserve(n);
+  std::vector<int> level_ptr{0};
+  std::vector<double> dd(n, 0.0), dof(n, 0.0);
+  std::vector<int> part(n, -1);    // partner original id
+  std::vector<double> sc(n, 1.0);  // final scaling of each original node
+  std::vector<Trip> trips;
+  double t_match = 0.0;
+
+  const bool verbose = std::getenv("AJD_SETUP_VERBOSE") != nullptr;
+  int level = 0;
+  for (;; ++level) {
+    const auto t_level = Clock::now();
+    const int m = S.n;
+    if (m == 0) break;
+    if (m <= n_dense || (level >= max_levels && m <= kDenseHardMax)) break;
+    if (level >= 4 * max_levels) return fail(JD_ESETUP, "ildl: %d rows left after %d levels", m, level);
+
+    // 1-2. matching, scaling, candidate groups
+    auto tm = Clock::now();
+    std::vector<int> mc;
+    std::vector<double> u, v, rmax;
+    std::vector<double> d(m);
+    std::vector<std::pair<int, int>> groups;
+    if (prm.matching) {
+      max_product_matching(S, mc, u, v, rmax);
+      for (int i = 0; i < m; ++i) d[i] = std::sqrt(std::exp(u[i] + v[i]) / rmax[i]);
+      if (level == 0)
+        for (int j = 0; j < m; ++j) F.n_matched_offdiag += (mc[j] != j);
+    } else {
+      for (int i = 0; i < m; ++i) {
+        double r = 0.0;
+        for (int64_t p = S.ptr[i]; p < S.ptr[i + 1]; ++p) r = std::max(r, std::fabs(S.val[p]));
+        d[i] = r > 0.0 ? 1.0 / std::sqrt(r) : 1.0;
+      }
+    }
+    for (int i = 0; i < m; ++i) {
+      cum[i] *= d[i];
+      for (int64_t p = S.ptr[i]; p < S.ptr[i + 1]; ++p) S.val[p] *= d[i] * d[S.col[p]];
+    }
+    if (prm.matching) {
+      split_cycles(S, mc, groups);
+    } else {
+      groups.reserve(m);
+      for (int i = 0; i < m; ++i) groups.push_back({i, -1});
+    }
+    const double tm_ms = ms_since(tm);
+    t_match += tm_ms;
+    const auto t_cand = Clock::now();
+
+    // 3. candidates: d1 = sum_{k != i} |s_ki| / |s_ii| (the 1-norm of the
+    // would-be L column); d2 = sum_k ||(s_ki, s_kj) B^{-1}||_1 for a 2x2 block
+    std::vector<double> diag(m), offsum(m);
+    for (int i = 0; i < m; ++i) {
+      double o = 0.0, dg = 0.0;
+      for (int64_t p = S.ptr[i]; p < S.ptr[i + 1]; ++p) {
+        if (S.col[p] == i) dg = S.val[p];
+        else o += std::fabs(S.val[p]);
+      }
+      diag[i] = dg;
+      offsum[i] = o;
+    }
+    auto d1_of = [&](int i) { return diag[i] != 0.0 ? offsum[i] / std::fabs(diag[i]) : kInf; };
+    std::vector<Cand> cands;
+    cands.reserve(m);
+    for (const auto& g : groups) {
+      if (g.second < 0) {
+        cands.push_back({g.first, -1, d1_of(g.first)});
+        continue;
+      }
+      const int i = g.first, j = g.second;
+      const double sij = 0.5 * (lookup(S, i, j) + lookup(S, j, i));
+      const double a = diag[i], c = diag[j];
+      const double det = a * c - sij * sij;
+      const double d1 = std::min(d1_of(i), d1_of(j));
+      bool use2 = false;
+      double q2 = kInf;
+      if (std::fabs(det) > 1e-300 && std::isfinite(det)) {
+        const double i00 = c / det, i01 = -sij / det, i11 = a / det;
+        double cs1 = 0.0, cs2 = 0.0, d2 = 0.0;
+        int64_t pa = S.ptr[i], pb = S.ptr[j];
+        const int64_t ea = S.ptr[i + 1], eb = S.ptr[j + 1];
+        while (pa < ea || pb < eb) {
+          int k;
+          double ski = 0.0, skj = 0.0;
+          if (pb >= eb || (pa < ea && S.col[pa] < S.col[pb])) { k = S.col[pa]; ski = S.val[pa++]; }
+          else if (pa >= ea || S.col[pb] < S.col[pa]) { k = S.col[pb]; skj = S.val[pb++]; }
+          else { k = S.col[pa]; ski = S.val[pa++]; skj = S.val[pb++]; }
+          if (k == i || k == j) continue;
+          const double r1 = ski * i00 + skj * i01, r2 = ski * i01 + skj * i11;
+          cs1 += std::fabs(r1);
+          cs2 += std::fabs(r2);
+          d2 += std::fabs(r1) + std::fabs(r2);
+        }
+        if (d2 < d1) {  // Section 6.2: 2x2 update only if d2 < d1
+          use2 = true;
+          q2 = std::max(cs1, cs2);
+        }
+      }
+      if (use2) {
+        cands.push_back({i, j, q2});
+      } else {
+        cands.push_back({i, -1, d1_of(i)});
+        cands.push_back({j, -1, d1_of(j)});
+      }
+    }
+    std::stable_sort(cands.begin(), cands.end(), [](const Cand& x, const Cand& y) {
+      if (x.q != y.q) return x.q < y.q;
+      return x.a < y.a;
+    });
+
+    // 4. independent set of pivots, best first; inverse-based acceptance
+    // 1 + q <= kappa (||L^{-1}||_1 of this level)
+    std::vector<char> blocked(m, 0), inB(m, 0);
+    std::vector<int> acc;  // indices into cands
+    auto block_nbrs = [&](int x) {
+      blocked[x] = 1;
+      for (int64_t p = S.ptr[x]; p < S.ptr[x + 1]; ++p)
+        if (std::fabs(S.val[p]) > gamma) blocked[S.col[p]] = 1;
+    };
+    auto try_accept = [&](double qmax) {
+      for (size_t t = 0; t < cands.size(); ++t) {
+        const Cand& cd = cands[t];
+        if (!(cd.q <= qmax)) break;
+        if (blocked[cd.a] || (cd.b >= 0 && blocked[cd.b])) continue;
+        acc.push_back((int)t);
+        inB[cd.a] = 1;
+        if (cd.b >= 0) inB[cd.b] = 1;
+        block_nbrs(cd.a);
+        if (cd.b >= 0) block_nbrs(cd.b);
+      }
+    };
+    try_accept(kappa - 1.0);
+    if ((int64_t)acc.size() * 200 < m) {
+      // the level would stall: accept every remaining independent candidate
+      // with a finite pivot (recorded as a relaxed level)
+      ++F.n_relaxed;
+      try_accept(std::numeric_limits<double>::max());
+    }
+    if (acc.empty()) return fail(JD_ESETUP, "ildl: no usable pivot at level %d (%d rows)", level, m);
+
+    const double tc_ms = ms_since(t_cand);
+    const auto t_lf = Clock::now();
+    // 5. local numbering: B in accepted order, C in index order
+    std::vector<int> blk_of(m, -1), cidx(m, -1);
+    std::vector<double> binv(3 * acc.size());  // symmetric 2x2 (or 1x1) inverse per block
+    std::vector<double> bmat(3 * acc.size());
+    const int level_start = (int)order.size();
+    for (size_t b = 0; b < acc.size(); ++b) {
+      const Cand& cd = cands[acc[b]];
+      blk_of[cd.a] = (int)b;
+      if (cd.b < 0) {
+        const double piv = diag[cd.a];
+        bmat[3 * b] = piv;
+        binv[3 * b] = 1.0 / piv;
+        binv[3 * b + 1] = binv[3 * b + 2] = 0.0;
+        order.push_back(gid[cd.a]);
+        sc[gid[cd.a]] = cum[cd.a];
+        dd[gid[cd.a]] = 1.0 / piv;
+        dof[gid[cd.a]] = 0.0;
+        part[gid[cd.a]] = -1;
+      } else {
+        blk_of[cd.b] = (int)b;
+        const double a = diag[cd.a], c = diag[cd.b];
+        const double s = 0.5 * (lookup(S, cd.a, cd.b) + lookup(S, cd.b, cd.a));
+        const double det = a * c - s * s;
+        bmat[3 * b] = a;
+        bmat[3 * b + 1] = s;
+        bmat[3 * b + 2] = c;
+        binv[3 * b] = c / det;
+        binv[3 * b + 1] = -s / det;
+        binv[3 * b + 2] = a / det;
+        order.push_back(gid[cd.a]);
+        order.push_back(gid[cd.b]);
+        sc[gid[cd.a]] = cum[cd.a];
+        sc[gid[cd.b]] = cum[cd.b];
+        dd[gid[cd.a]] = c / det;
+        dd[gid[cd.b]] = a / det;
+        dof[gid[cd.a]] = dof[gid[cd.b]] = -s / det;
+        part[gid[cd.a]] = gid[cd.b];
+        part[gid[cd.b]] = gid[cd.a];
+        ++F.n_2x2;
+      }
+    }
+    level_ptr.push_back((int)order.size());
+    F.level_sizes.push_back((int)order.size() - level_start);
+    int mc_n = 0;
+    std::vector<int> cnodes;
+    for (int i = 0; i < m; ++i)
+      if (!inB[i]) { cidx[i] = mc_n++; cnodes.push_back(i); }
+
+    // 6. L_F = F D_B^{-1} row by row (rows: C nodes), dropped at tau.
+    // Entries: (C row, B node, value) with the B node's block.
+    std::vector<int64_t> lptr(mc_n + 1, 0);
+    std::vector<int> lnode;    // B node (local index)
+    std::vector<double> lval;
+    {
+      std::vector<double> fa(acc.size(), 0.0), fb(acc.size(), 0.0);
+      std::vector<int> touched;
+      for (int r = 0; r < mc_n; ++r) {
+        const int k = cnodes[r];
+        touched.clear();
+        for (int64_t p = S.ptr[k]; p < S.ptr[k + 1]; ++p) {
+          const int x = S.col[p];
+          if (!inB[x]) continue;
+          const int b = blk_of[x];
+          const Cand& cd = cands[acc[b]];
+          if (fa[b] == 0.0 && fb[b] == 0.0) touched.push_back(b);
+          if (x == cd.a) fa[b] += S.val[p];
+          else fb[b] += S.val[p];
+        }
+        std::sort(touched.begin(), touched.end());
+        for (int b : touched) {
+          const Cand& cd = cands[acc[b]];
+          if (cd.b < 0) {
+            const double l = fa[b] * binv[3 * b];
+            if (std::fabs(l) >= tau && l != 0.0) { lnode.push_back(cd.a); lval.push_back(l); }
+          } else {
+            const double l1 = fa[b] * binv[3 * b] + fb[b] * binv[3 * b + 1];
+            const double l2 = fa[b] * binv[3 * b + 1] + fb[b] * binv[3 * b + 2];
+            if (std::fabs(l1) >= tau && l1 != 0.0) { lnode.push_back(cd.a); lval.push_back(l1); }
+            if (std::fabs(l2) >= tau && l2 != 0.0) { lnode.push_back(cd.b); lval.push_back(l2); }
+          }
+          fa[b] = fb[b] = 0.0;
+        }
+        lptr[r + 1] = (int64_t)lnode.size();
+      }
+    }
+    for (int r = 0; r < mc_n; ++r) {
+      const int k = cnodes[r];
+      for (int64_t p = lptr[r]; p < lptr[r + 1]; ++p)
+        trips.push_back({gid[k], gid[lnode[p]], lval[p] / cum[k]});
+    }
+
+    const double tl_ms = ms_since(t_lf);
+    const auto t_schur = Clock::now();
+    // 7. Schur complement S' = S_CC - L_F D_B L_F^T (upper triangle, then
+    // mirrored so that S' is exactly symmetric), dropped at tau off the
+    // diagonal.  Column access to L_F per B block:
+    std::vector<int64_t> cptr(acc.size() + 1, 0);
+    for (int64_t p = 0; p < (int64_t)lnode.size(); ++p) cptr[blk_of[lnode[p]] + 1]++;
+    for (size_t b = 0; b < acc.size(); ++b) cptr[b + 1] += cptr[b];
+    std::vector<int> crow(lnode.size());
+    std::vector<double> c1(lnode.size(), 0.0), c2(lnode.size(), 0.0);
+    {
+      // one record per (block, C row): values for node a and node b
+      std::vector<int64_t> fillp(cptr.begin(), cptr.end() - 1);
+      std::vector<int64_t> last_slot(acc.size(), -1);
+      std::vector<int> last_row(acc.size(), -1);
+      for (int r = 0; r < mc_n; ++r)
+        for (int64_t p = lptr[r]; p < lptr[r + 1]; ++p) {
+          const int b = blk_of[lnode[p]];
+          int64_t slot;
+          if (last_row[b] == r) slot = last_slot[b];
+          else { slot = fillp[b]++; last_row[b] = r; last_slot[b] = slot; crow[slot] = r; }
+          if (lnode[p] == cands[acc[b]].a) c1[slot] = lval[p];
+          else c2[slot] = lval[p];
+        }
+      // compact: records per block are fillp[b] - cptr[b]
+      std::vector<int64_t> nptr(acc.size() + 1, 0);
+      for (size_t b = 0; b < acc.size(); ++b) nptr[b + 1] = nptr[b] + (fillp[b] - cptr[b]);
+      std::vector<int> crow2(nptr.back());
+      std::vector<double> c12(nptr.back()), c22(nptr.back());
+      for (size_t b = 0; b < acc.size(); ++b)
+        for (int64_t t = 0; t < fillp[b] - cptr[b]; ++t) {
+          crow2[nptr[b] + t] = crow[cptr[b] + t];
+          c12[nptr[b] + t] = c1[cptr[b] + t];
+          c22[nptr[b] + t] = c2[cptr[b] + t];
+        }
+      cptr.swap(nptr);
+      crow.swap(crow2);
+      c1.swap(c12);
+      c2.swap(c22);
+    }
+    SymCsr U;  // upper triangle of S'
+    U.n = mc_n;
+    U.ptr.assign(mc_n + 1, 0);
+    {
+      std::vector<double> accv(mc_n, 0.0);
+      std::vector<char> mark(mc_n, 0);
+      std::vector<int> cols;
+      std::vector<int> rowblocks;
+      for (int r = 0; r < mc_n; ++r) {
+        const int k = cnodes[r];
+        cols.clear();
+        for (int64_t p = S.ptr[k]; p < S.ptr[k + 1]; ++p) {
+          const int c = cidx[S.col[p]];
+          if (c < r) continue;  // B columns have cidx -1
+          if (!mark[c]) { mark[c] = 1; cols.push_back(c); }
+          accv[c] += S.val[p];
+        }
+        if (!mark[r]) { mark[r] = 1; cols.push_back(r); }
+        // blocks in row r of L_F with their (l_a, l_b) values
+        rowblocks.clear();
+        for (int64_t p = lptr[r]; p < lptr[r + 1]; ++p) {
+          const int b = blk_of[lnode[p]];
+          if (rowblocks.empty() || rowblocks.back() != b) rowblocks.push_back(b);
+        }
+        for (int b : rowblocks) {
+          // find this row's record in block b's column list (rows ascending)
+          const int* cb = crow.data() + cptr[b];
+          const int* ce = crow.data() + cptr[b + 1];
+          const int64_t me = std::lower_bound(cb, ce, r) - crow.data();
+          const double la = c1[me], lb = c2[me];
+          double wa, wb;  // (l_a, l_b) * D_b
+          if (cands[acc[b]].b < 0) { wa = la * bmat[3 * b]; wb = 0.0; }
+          else {
+            wa = la * bmat[3 * b] + lb * bmat[3 * b + 1];
+            wb = la * bmat[3 * b + 1] + lb * bmat[3 * b + 2];
+          }
+          for (int64_t t = me; t < cptr[b + 1]; ++t) {
+            const int q = crow[t];  // q >= r because rows are ascending
+            if (!mark[q]) { mark[q] = 1; cols.push_back(q); }
+            accv[q] -= wa * c1[t] + wb * c2[t];
+          }
+        }
+        std::sort(cols.begin(), cols.end());
+        for (int c : cols) {
+          const double val = accv[c];
+          if (c == r || std::fabs(val) >= tau) {
+            U.col.push_back(c);
+            U.val.push_back(val);
+          }
+          accv[c] = 0.0;
+          mark[c] = 0;
+        }
+        U.ptr[r + 1] = (int64_t)U.col.size();
+      }
+    }
+    // mirror U into a full symmetric CSR
+    SymCsr Sn;
+    Sn.n = mc_n;
+    Sn.ptr.assign(mc_n + 1, 0);
+    for (int r = 0; r < mc_n; ++r)
+      for (int64_t p = U.ptr[r]; p < U.ptr[r + 1]; ++p) {
+        Sn.ptr[r + 1]++;
+        if (U.col[p] != r) Sn.ptr[U.col[p] + 1]++;
+      }
+    for (int r = 0; r < mc_n; ++r) Sn.ptr[r + 1] += Sn.ptr[r];
+    Sn.col.resize(Sn.ptr[mc_n]);
+    Sn.val.resize(Sn.ptr[mc_n]);
+    {
+      std::vector<int64_t> fp(Sn.ptr.begin(), Sn.ptr.end() - 1);
+      // lower entries first (rows ascending give ascending columns), then upper
+      for (int r = 0; r < mc_n; ++r)
+        for (int64_t p = U.ptr[r]; p < U.ptr[r + 1]; ++p)
+          if (U.col[p] != r) {
+            const int c = U.col[p];
+            Sn.col[fp[c]] = r;
+            Sn.val[fp[c]++] = U.val[p];
+          }
+      for (int r = 0; r < mc_n; ++r)
+        for (int64_t p = U.ptr[r]; p < U.ptr[r + 1]; ++p) {
+          Sn.col[fp[r]] = U.col[p];
+          Sn.val[fp[r]++] = U.val[p];
+        }
+    }
+    // next level's numbering
+    std::vector<int> gid2(mc_n);
+    std::vector<double> cum2(mc_n);
+    for (int r = 0; r < mc_n; ++r) {
+      gid2[r] = gid[cnodes[r]];
+      cum2[r] = cum[cnodes[r]];
+    }
+    gid.swap(gid2);
+    cum.swap(cum2);
+    if (verbose)
+      std::fprintf(stderr, "ildl level %d: m=%d B=%zu C=%d nnzS'/row=%.1f nnzLF=%zu | match %.1f cand %.1f LF %.1f schur %.1f total %.1f ms\n",
+                   level, m, acc.size(), mc_n, mc_n ? (double)Sn.col.size() / mc_n : 0.0, lnode.size(), tm_ms, tc_ms, tl_ms,
+                   ms_since(t_schur), ms_since(t_level));
+    S = std::move(Sn);
+  }
+  const int nlev = level;
+  const int nd = S.n;
+  // trailing dense block
+  std::vector<double> dense_inv;
+  if (nd > 0) {
+    std::vector<double> M((size_t)nd * nd, 0.0);
+    for (int i = 0; i < nd; ++i)
+      for (int64_t p = S.ptr[i]; p < S.ptr[i + 1]; ++p) M[(size_t)i * nd + S.col[p]] = S.val[p];
+    const auto t_dense = Clock::now();
+    if (!dense_inverse(nd, M, dense_inv))
+      return fail(JD_ESETUP, "ildl: the final dense block (%d rows) is singular", nd);
+    if (verbose) std::fprintf(stderr, "ildl dense block %d rows: %.1f ms\n", nd, ms_since(t_dense));
+    for (int i = 0; i < nd; ++i) {
+      order.push_back(gid[i]);
+      sc[gid[i]] = cum[i];
+    }
+  }
+  level_ptr.push_back((int)order.size());
+  if ((int)order.size() != n) return fail(JD_ESETUP, "ildl: internal error, %zu of %d rows ordered", order.size(), n);
+
+  // global assembly in position space
+  std::vector<int> pos(n);
+  for (int p = 0; p < n; ++p) pos[order[p]] = p;
+  F.nlev = nlev;
+  F.n_dense = nd;
+  F.perm = order;
+  F.scale.resize(n);
+  for (int p = 0; p < n; ++p) F.scale[p] = sc[order[p]];
+  F.level_ptr = level_ptr;
+  F.Lptr.assign(n + 1, 0);
+  for (const Trip& t : trips) F.Lptr[pos[t.r] + 1]++;
+  for (int p = 0; p < n; ++p) F.Lptr[p + 1] += F.Lptr[p];
+  F.Lcol.resize(trips.size());
+  F.Lval.resize(trips.size());
+  {
+    std::vector<int64_t> fp(F.Lptr.begin(), F.Lptr.end() - 1);
+    for (const Trip& t : trips) {
+      const int r = pos[t.r];
+      F.Lcol[fp[r]] = pos[t.c];
+      F.Lval[fp[r]++] = t.v * sc[t.r];
+    }
+    std::vector<std::pair<int, double>> tmp;
+    for (int r = 0; r < n; ++r) {
+      tmp.clear();
+      for (int64_t q = F.Lptr[r]; q < F.Lptr[r + 1]; ++q) tmp.push_back({F.Lcol[q], F.Lval[q]});
+      std::sort(tmp.begin(), tmp.end());
+      for (size_t k = 0; k < tmp.size(); ++k) {
+        F.Lcol[F.Lptr[r] + k] = tmp[k].first;
+        F.Lval[F.Lptr[r] + k] = tmp[k].second;
+      }
+    }
+  }
+  trips.clear();
+  trips.shrink_to_fit();
+  // transpose (rows of L^T = columns of L), entries ordered by row
+  F.Uptr.assign(n + 1, 0);
+  for (int64_t q = 0; q < (int64_t)F.Lcol.size(); ++q) F.Uptr[F.Lcol[q] + 1]++;
+  for (int p = 0; p < n; ++p) F.Uptr[p + 1] += F.Uptr[p];
+  F.Ucol.resize(F.Lcol.size());
+  F.Uval.resize(F.Lcol.size());
+  {
+    std::vector<int64_t> fp(F.Uptr.begin(), F.Uptr.end() - 1);
+    for (int r = 0; r < n; ++r)
+      for (int64_t q = F.Lptr[r]; q < F.Lptr[r + 1]; ++q) {
+        const int c = F.Lcol[q];
+        F.Ucol[fp[c]] = r;
+        F.Uval[fp[c]++] = F.Lval[q];
+      }
+  }
+  F.dinv_d.assign(n, 0.0);
+  F.dinv_o.assign(n, 0.0);
+  F.partner.assign(n, -1);
+  for (int p = 0; p < n - nd; ++p) {
+    const int o = order[p];
+    F.dinv_d[p] = dd[o];
+    F.dinv_o[p] = dof[o];
+    F.partner[p] = part[o] >= 0 ? pos[part[o]] : -1;
+  }
+  F.dense_inv.swap(dense_inv);
+  F.t_match_ms = t_match;
+  F.t_total_ms = ms_since(t_start);
+  F.t_factor_ms = F.t_total_ms - t_match;
+  return JD_OK;
+}
+
+}  // namespace ajd

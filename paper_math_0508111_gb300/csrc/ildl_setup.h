@@ -1,0 +1,69 @@
+// Host-side construction of the multilevel incomplete LDL^T preconditioner
+// (Sections 5 and 6).  Pure C++ (no CUDA), so it also runs without a GPU.
+#pragma once
+#include <cstdint>
+#include <vector>
+
+#include "anderson_jd.h"
+
+namespace ajd {
+
+// Symmetric sparse matrix, both triangles stored, rows sorted by column,
+// diagonal entry always present (possibly zero).
+struct SymCsr {
+  int n = 0;
+  std::vector<int64_t> ptr;
+  std::vector<int> col;
+  std::vector<double> val;
+};
+
+// The factor in global (level-ordered) position space:
+//   K^{-1} b = P^T S L^{-T} D^{-1} L^{-1} S P b,
+// (P b)[p] = b[perm[p]], S = diag(scale), L unit lower triangular, D block
+// diagonal with 1x1/2x2 blocks on levels 0..nlev-1 and one dense block of
+// size n_dense on the trailing positions.
+struct HostFactor {
+  int n = 0;
+  int nlev = 0;                   // number of sparse levels
+  int n_dense = 0;                // size of the trailing dense block
+  std::vector<int> perm;          // position -> original index
+  std::vector<double> scale;      // S
+  std::vector<int> level_ptr;     // nlev + 2 entries: sparse levels, then the dense block
+  std::vector<int64_t> Lptr;      // strictly lower part of L, CSR by rows
+  std::vector<int> Lcol;
+  std::vector<double> Lval;
+  std::vector<int64_t> Uptr;      // L^T, CSR by rows (= L by columns)
+  std::vector<int> Ucol;
+  std::vector<double> Uval;
+  std::vector<double> dinv_d;     // per position: diagonal of D^{-1} block
+  std::vector<double> dinv_o;     // per position: off-diagonal of D^{-1} block
+  std::vector<int> partner;       // per position: 2x2 partner position or -1
+  std::vector<double> dense_inv;  // n_dense^2, row-major, symmetric
+  // statistics
+  int n_2x2 = 0;
+  int n_matched_offdiag = 0;      // rows matched off the diagonal at level 0
+  int n_relaxed = 0;              // levels where pivot acceptance was relaxed
+  int64_t nnz_A = 0;
+  double t_match_ms = 0, t_factor_ms = 0, t_total_ms = 0;
+  std::vector<int> level_sizes;   // rows eliminated per sparse level
+};
+
+// Build the preconditioner of A (symmetric, e.g. A - sigma I).  Returns
+// JD_OK or JD_ESETUP / JD_EINVAL with jd_last_error() set.
+int build_ildl(const SymCsr& A, const ildl_params& p, HostFactor& F);
+
+// Maximum-product transversal of Section 5.1 (Eqs. (5.1)-(5.2)): on return
+// match_col[j] is the row matched to column j, u and v are the dual
+// potentials of the assignment problem with costs c_ij = log a_i - log|a_ij|,
+// a_i = max_j |a_ij|.  Returns the number of unmatched columns (0 when a
+// perfect matching exists).
+int max_product_matching(const SymCsr& A, std::vector<int>& match_col, std::vector<double>& u,
+                         std::vector<double>& v, std::vector<double>& rowmax);
+
+// Split the cycles of the permutation j -> match_col[j] into 1- and 2-cycles
+// (Section 5.2).  `sdiag` and the scaled matrix decide the splits.  Returns
+// groups as pairs (a, b) with b = -1 for singletons.
+void split_cycles(const SymCsr& S, const std::vector<int>& match_col,
+                  std::vector<std::pair<int, int>>& groups);
+
+}  // namespace ajd

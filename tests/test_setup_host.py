@@ -1,0 +1,134 @@
+"""The library's host-side preconditioner construction (Sections 5-6), run on
+the CPU and checked against the oracle."""
+import numpy as np
+import pytest
+
+from oracle import krylov, lattice, matching, rng
+from oracle.lattice import HARDWALL, PERIODIC
+
+
+@pytest.fixture(scope="module")
+def ajd():
+    from paper_math_0508111_gb300 import build
+    build.build()
+    import paper_math_0508111_gb300 as ajd
+    return ajd
+
+
+def _csr(L, W, seed, bc, sigma):
+    eps = rng.potential(L, W, seed)
+    A = lattice.assemble(L, eps, bc, shift=sigma).tocsr()
+    A.sort_indices()
+    return A, eps
+
+
+@pytest.mark.parametrize("L,bc,sigma,match", [(6, PERIODIC, 0.0, 1), (6, HARDWALL, 0.7, 1), (7, PERIODIC, -1.0, 1),
+                                              (6, PERIODIC, 0.0, 0)])
+def test_exact_without_dropping(ajd, L, bc, sigma, match):
+    """With no dropping, no weak couplings ignored and kappa = inf the
+    multilevel LDL^T is a complete factorization: K = A - sigma I."""
+    A, _ = _csr(L, 16.5, 2, bc, sigma)
+    P = ajd.Preconditioner.from_csr(A.indptr, A.indices, A.data, drop=0.0, kappa=1e300, gamma=0.0,
+                                    n_dense=20, matching=match)
+    F = P.export()
+    assert F["levels"] >= 2
+    g = np.random.default_rng(0)
+    for _ in range(3):
+        x = g.standard_normal(A.shape[0])
+        assert np.linalg.norm(matching.apply_factor(F, A @ x) - x) <= 1e-9 * np.linalg.norm(x)
+
+
+def test_factor_structure(ajd):
+    A, _ = _csr(12, 16.5, 1, PERIODIC, 0.0)
+    F = ajd.Preconditioner.from_csr(A.indptr, A.indices, A.data, n_dense=100).export()
+    n = A.shape[0]
+    assert sorted(F["perm"]) == list(range(n))
+    lp = F["level_ptr"]
+    assert lp[0] == 0 and lp[-1] == n and np.all(np.diff(lp) >= 0)
+    assert lp[-1] - lp[-2] == F["n_dense"]
+    # each row only references earlier levels (one parallel step per level)
+    lev = np.searchsorted(lp, np.arange(n), side="right") - 1
+    for p in range(n):
+        cols = F["Lcol"][F["Lptr"][p]:F["Lptr"][p + 1]]
+        assert np.all(cols < lp[lev[p]])
+    # 2x2 partners sit in the same level and point at each other
+    pt = F["partner"]
+    for p in range(lp[-2]):
+        if pt[p] >= 0:
+            assert pt[pt[p]] == p and lev[pt[p]] == lev[p]
+    # dense inverse is symmetric
+    Dn = F["dense_inv"]
+    assert np.allclose(Dn, Dn.T)
+
+
+def test_preconditioner_quality_default(ajd):
+    """Default parameters: SQMR (oracle) preconditioned by the library's K
+    solves (A - sigma I) x = b at L = 12 in few iterations, versus
+    thousands unpreconditioned."""
+    A, _ = _csr(12, 16.5, 1, PERIODIC, 0.0)
+    F = ajd.Preconditioner.from_csr(A.indptr, A.indices, A.data, n_dense=200).export()
+    b = np.random.default_rng(3).standard_normal(A.shape[0])
+    x, k, _ = krylov.sqmr(lambda v: A @ v, lambda v: matching.apply_factor(F, v), b, 1e-8, 400)
+    assert k < 80
+    assert np.linalg.norm(A @ x - b) <= 1e-7 * np.linalg.norm(b)
+
+
+def test_symmetry_of_K(ajd):
+    A, _ = _csr(5, 16.5, 4, PERIODIC, 0.2)
+    F = ajd.Preconditioner.from_csr(A.indptr, A.indices, A.data, n_dense=10).export()
+    g = np.random.default_rng(1)
+    a, b = g.standard_normal(125), g.standard_normal(125)
+    assert a @ matching.apply_factor(F, b) == pytest.approx(b @ matching.apply_factor(F, a), rel=1e-11)
+
+
+@pytest.mark.parametrize("L,W,sigma", [(6, 16.5, 0.0), (8, 12.0, 0.5), (5, 2.0, 0.0)])
+def test_matching_optimal_and_scaled(ajd, L, W, sigma):
+    """The library's matching has the optimal product (unique even when the
+    permutation is not), its scaling puts every entry in [-1, 1], and its
+    1x1/2x2 groups are matched pairs."""
+    A, _ = _csr(L, W, 5, PERIODIC, sigma)
+    mc, sc, pt = ajd.matching(A.indptr, A.indices, A.data)
+    n = A.shape[0]
+    assert sorted(mc) == list(range(n))
+    Ad = A.toarray()
+    vals = np.abs(Ad[mc, np.arange(n)])
+    assert np.all(vals > 0)
+    _, _, _, total = matching.max_product_assignment(Ad)
+    c = matching.costs(Ad)
+    assert c[mc, np.arange(n)].sum() == pytest.approx(total, abs=1e-9)
+    S = sc[:, None] * Ad * sc[None, :]
+    assert np.abs(S).max() <= 1 + 1e-12
+    for i in range(n):
+        if pt[i] >= 0:
+            j = pt[i]
+            assert pt[j] == i
+            assert mc[i] == j or mc[j] == i
+
+
+def test_matching_fig4_structure(ajd):
+    """A 6x6 symmetric matrix whose largest entries follow the matching of
+    Figure 3 (rows 4,1,5,2,3,6 on the diagonal of P_M A) and whose
+    diagonal inside the 3-cycle is largest at row 1: the library returns the
+    cycle form and split of Figure 4."""
+    n = 6
+    A = np.full((n, n), 0.0)
+    pm = [3, 0, 4, 1, 2, 5]  # 0-based rows matched to columns 0..5
+    for col, row in enumerate(pm):
+        A[row, col] = A[col, row] = 4.0
+    A[0, 0], A[1, 1], A[3, 3] = 0.5, 0.1, 0.2
+    A[2, 2], A[4, 4] = 0.1, 0.1
+    A[5, 5] = 3.0
+    import scipy.sparse as sp
+    C = sp.csr_matrix(A)
+    C.sort_indices()
+    mc, sc, pt = ajd.matching(C.indptr, C.indices, C.data)
+    cyc = sorted(sorted(c) for c in matching.cycles(mc))
+    assert cyc == [[0, 1, 3], [2, 4], [5]]
+    assert pt[0] == -1 and pt[1] == 3 and pt[3] == 1 and pt[2] == 4 and pt[5] == -1
+
+
+def test_setup_rejects_bad_input(ajd):
+    with pytest.raises(ajd.JDError):
+        ajd.Preconditioner.from_csr(np.array([0, 1]), np.array([0]), np.array([1.0]), kappa=0.5)
+    with pytest.raises(ajd.JDError):
+        ajd.Preconditioner.from_csr(np.array([0, 2, 3]), np.array([1, 0, 1]), np.array([1.0, 2.0, 1.0]))
