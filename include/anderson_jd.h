@@ -226,6 +226,82 @@ int ildl_apply(ildl_t f, const void* b, void* x, int precision, void* stream);
 /* Release the factor (host and device parts).  NULL is a no-op. */
 int ildl_destroy(ildl_t f);
 
+/* ======================================================================== *
+ *  Jacobi–Davidson eigensolver (Section 4.2)                                *
+ * ======================================================================== */
+
+/* Solver parameters.  Zero fields select the defaults in brackets. */
+typedef struct {
+  int jmin;           /* search space size kept at a restart [max(2k, 10)]     */
+  int jmax;           /* search space size that triggers a restart [jmin+15]   */
+  int max_outer;      /* outer (expansion) steps before JD_ENOCONV [3000]      */
+  int max_inner;      /* SQMR iterations per correction equation [60]          */
+  double inner_decay; /* the correction equation is solved to relative
+                         residual max(inner_decay^j, inner_floor), j = outer
+                         steps spent on the current Ritz pair [0.7]            */
+  double inner_floor; /* [1e-7]                                                */
+  double switch_tol;  /* correction shift: sigma while ||r|| > switch_tol*||A||,
+                         the Ritz value theta afterwards [1e-3]                */
+  int precision;      /* inner solve (stencil, preconditioner, SQMR) in
+                         JD_FP64 or JD_FP32; the outer residual, Ritz
+                         projection and orthogonalisation are always
+                         binary64 [JD_FP64]                                   */
+  uint64_t seed;      /* start vector seed (0 = derived from the lattice seed)*/
+  ildl_params ildl;   /* preconditioner parameters (zeroed = defaults)       */
+  ildl_t precond;     /* optional prebuilt preconditioner of A - sigma I
+                         (from ildl_create with the same sigma); NULL = build
+                         one inside the call and time it as setup           */
+} jd_params;
+
+/* Counters of one solve (the observables of Tables 3-5). */
+typedef struct {
+  int nconv;           /* eigenpairs that met the tolerance                   */
+  int outer_its;       /* Jacobi–Davidson expansion steps                     */
+  int inner_its;       /* total SQMR iterations                               */
+  int restarts;        /* search space restarts                               */
+  double setup_ms;     /* preconditioner construction (host) and upload       */
+  double solve_ms;     /* everything after the setup                          */
+  double max_residual; /* max ||A x - lambda x||_2 / ||A|| over returned pairs */
+  double orth_error;   /* max |X^T X - I| over returned pairs                 */
+  ildl_info_t ildl;    /* preconditioner statistics                           */
+} jd_stats;
+
+/* Fill *p with the defaults (all fields zero except ildl = ildl defaults). */
+int jd_params_default(jd_params* p);
+
+/*
+ * jd_solve -- the k eigenpairs of A (the lattice h) nearest sigma.
+ *
+ * Jacobi–Davidson (Section 4.2): the search space V is expanded by the
+ * approximate solution of the correction equation (4.1),
+ *   (I - Q~Q~^T)(A - theta^ I)(I - Q~Q~^T) z = -r,  Q~ = [Q, u],
+ * obtained by simplified QMR with the projected preconditioner
+ * K^{-1} - W (Q~^T W)^{-1} W^T, W = K^{-1} Q~, K ~ A - sigma I the
+ * multilevel ILDL^T; each new vector is orthogonalised against [Q, V]
+ * (classical Gram–Schmidt, twice), the Ritz pair of [V]^T A [V] nearest sigma
+ * is selected, and it is locked into Q once ||A u - theta u|| <= tol*||A||
+ * (||A|| = 6 + max|eps|).  A final Rayleigh–Ritz step on Q returns the
+ * eigenvalues.
+ *
+ *   sigma   target shift (finite).
+ *   k       number of eigenpairs, 1 <= k <= 64 and k < n.
+ *   tol     relative residual tolerance, > 0 (e.g. 1e-8).
+ *   p       parameters or NULL for defaults.
+ *   evals   caller buffer of k doubles (host or device pointer).
+ *   evecs   caller buffer of n*k doubles, column-major (host or device
+ *           pointer), or NULL to skip the eigenvectors.
+ *   st      optional statistics.
+ *   stream  cudaStream_t or NULL.  The call is synchronous.
+ * Results are ordered by |lambda - sigma| ascending (ties: lambda
+ * ascending); each eigenvector has unit 2-norm and its largest-modulus
+ * component (lowest index on ties) positive.
+ * Errors: JD_EINVAL, JD_ENOMEM, JD_EDEVICE, JD_ESETUP; JD_ENOCONV when
+ * max_outer steps did not converge all k pairs -- evals/evecs then hold the
+ * st->nconv converged pairs first.
+ */
+int jd_solve(anderson_t h, double sigma, int k, double tol, const jd_params* p, double* evals,
+             double* evecs, jd_stats* st, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -14,7 +14,7 @@ from . import _ffi
 from ._ffi import (JD_EBREAKDOWN, JD_EDEVICE, JD_EINVAL, JD_ENOCONV, JD_ENOMEM, JD_ESETUP, JD_FP32,
                    JD_FP64, JD_HARDWALL, JD_OK, JD_PERIODIC, JDError)
 
-__all__ = ["Anderson", "Preconditioner", "ildl_params", "JDError", "JD_PERIODIC", "JD_HARDWALL", "JD_FP64", "JD_FP32", "library_path"]
+__all__ = ["Anderson", "Preconditioner", "ildl_params", "jd_params", "solve", "JDError", "JD_PERIODIC", "JD_HARDWALL", "JD_FP64", "JD_FP32", "library_path"]
 
 
 def library_path():
@@ -224,3 +224,50 @@ class Preconditioner:
 
     def __exit__(self, *exc):
         self.close()
+
+
+def jd_params(precision=JD_FP64, precond=None, ildl=None, **kw):
+    """Solver parameters: defaults of jd_params_default with keyword
+    overrides (jmin, jmax, max_outer, max_inner, inner_decay, inner_floor,
+    switch_tol, seed); ``ildl`` is a dict of preconditioner overrides and
+    ``precond`` an optional prebuilt :class:`Preconditioner`."""
+    p = _ffi.JdParams()
+    _ffi.call("jd_params_default", ctypes.byref(p))
+    p.precision = int(precision)
+    for k, v in kw.items():
+        if not hasattr(p, k) or k in ("ildl", "precond", "precision"):
+            raise TypeError("unknown solver parameter %r" % k)
+        setattr(p, k, v)
+    if ildl:
+        for k, v in ildl.items():
+            setattr(p.ildl, k, v)
+    if precond is not None:
+        p.precond = precond.handle
+    return p
+
+
+def _stats_dict(st):
+    d = {f: getattr(st, f) for f, _ in st._fields_ if f != "ildl"}
+    d["ildl"] = {f: getattr(st.ildl, f) for f, _ in st.ildl._fields_}
+    return d
+
+
+def solve(lattice, sigma, k, tol, precision=JD_FP64, vectors=True, stream=None, raise_on_noconv=True, **params):
+    """The k eigenpairs of the lattice's matrix nearest sigma (jd_solve).
+
+    Returns (evals, evecs, stats): evals has shape (k,), evecs shape (n, k)
+    (numpy, host), stats a dict of the solver counters.  Extra keyword
+    arguments go to :func:`jd_params`."""
+    p = jd_params(precision=precision, **params)
+    ev = np.zeros(int(k))
+    X = np.zeros((int(k), lattice.n)) if vectors else None
+    st = _ffi.JdStats()
+    vp = ctypes.c_void_p
+    rc = _ffi.lib().jd_solve(lattice.handle, float(sigma), int(k), float(tol), ctypes.byref(p),
+                             ev.ctypes.data_as(vp), X.ctypes.data_as(vp) if vectors else None, ctypes.byref(st),
+                             _stream_handle(stream) if stream is not None else None)
+    if rc != JD_OK and (rc != JD_ENOCONV or raise_on_noconv):
+        _ffi.check(rc, "jd_solve")
+    stats = _stats_dict(st)
+    stats["status"] = rc
+    return ev, (X.T if vectors else None), stats

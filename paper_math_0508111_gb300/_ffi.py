@@ -37,6 +37,18 @@ class IldlInfo(ctypes.Structure):
                 ("nnz_A", c_int64), ("fill", c_double), ("setup_ms", c_double), ("match_ms", c_double)]
 
 
+class JdParams(ctypes.Structure):
+    _fields_ = [("jmin", c_int), ("jmax", c_int), ("max_outer", c_int), ("max_inner", c_int),
+                ("inner_decay", c_double), ("inner_floor", c_double), ("switch_tol", c_double),
+                ("precision", c_int), ("seed", c_uint64), ("ildl", IldlParams), ("precond", c_void_p)]
+
+
+class JdStats(ctypes.Structure):
+    _fields_ = [("nconv", c_int), ("outer_its", c_int), ("inner_its", c_int), ("restarts", c_int),
+                ("setup_ms", c_double), ("solve_ms", c_double), ("max_residual", c_double),
+                ("orth_error", c_double), ("ildl", IldlInfo)]
+
+
 # (name, restype, argtypes) of every exported function
 SIGNATURES = [
     ("jd_last_error", ctypes.c_char_p, []),
@@ -55,6 +67,9 @@ SIGNATURES = [
     ("ildl_export", c_int, [c_void_p] + [c_void_p] * 10),
     ("ildl_apply", c_int, [c_void_p, c_void_p, c_void_p, c_int, c_void_p]),
     ("ildl_destroy", c_int, [c_void_p]),
+    ("jd_params_default", c_int, [P(JdParams)]),
+    ("jd_solve", c_int, [c_void_p, c_double, c_int, c_double, P(JdParams), c_void_p, c_void_p, P(JdStats),
+                         c_void_p]),
 ]
 
 _lib = None

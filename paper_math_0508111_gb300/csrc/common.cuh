@@ -33,8 +33,8 @@ int fail(int code, const char* fmt, ...);
 // Propagate a non-zero status code.
 #define AJD_TRY(expr)                                                         \
   do {                                                                        \
-    int s_ = (expr);                                                          \
-    if (s_ != JD_OK) return s_;                                               \
+    int ajd_rc_ = (expr);                                                     \
+    if (ajd_rc_ != JD_OK) return ajd_rc_;                                     \
   } while (0)
 
 #define AJD_CHECK_LAUNCH() AJD_CUDA(cudaGetLastError())

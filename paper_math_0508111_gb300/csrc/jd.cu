@@ -1,0 +1,1014 @@
+// Jacobi–Davidson for the k eigenpairs of the Anderson matrix nearest sigma
+// (Section 4.2), with the correction equation (4.1) solved by simplified QMR
+// and the multilevel ILDL^T preconditioner of Sections 5-6.
+//
+// Division of work: every O(n) operation runs in the kernels of this file
+// (or the stencil and preconditioner kernels): Gram–Schmidt, the Rayleigh
+// quotient matrix H = V^T A V, Ritz vectors, residuals, restarts and every
+// SQMR step.  The m x m (m <= 64) symmetric eigenproblem of H is solved by a
+// one-CTA Jacobi kernel.  The host only sequences the steps and reads a few
+// scalars back once per outer step (Ritz value, residual norm, convergence
+// flags).  The outer quantities are binary64; the inner solve runs in the
+// precision the caller selects.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "anderson_impl.cuh"
+#include "ildl_impl.cuh"
+
+namespace ajd {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kMaxCols = 160;  // columns of one multi-dot (k + jmax + 2)
+constexpr int kMaxM = 64;      // largest Rayleigh–Ritz problem
+
+int vec_blocks(int64_t n) {
+  return (int)std::max<int64_t>(1, std::min<int64_t>((n + kThreads * 4 - 1) / (kThreads * 4), 4 * sm_count()));
+}
+
+template <typename T>
+struct Cols {
+  const T* p = nullptr;
+  int64_t ld = 0;
+  int c = 0;
+};
+
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x < 32) {
+    t = threadIdx.x < (blockDim.x >> 5) ? sh[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  }
+  return t;  // valid in thread 0
+}
+
+// partial[b*ncols + j] = block b's share of (column j of [X1 X2 extra])^T v
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+multidot_kernel(Cols<T> X1, Cols<T> X2, const T* __restrict__ extra, const T* __restrict__ v, int64_t n,
+                double* __restrict__ partial, int ncols, const int* done) {
+  if (done && *done) return;
+  __shared__ double sh[kThreads / 32];
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (int j = 0; j < ncols; ++j) {
+    const T* x;
+    if (j < X1.c) x = X1.p + (int64_t)j * X1.ld;
+    else if (j < X1.c + X2.c) x = X2.p + (int64_t)(j - X1.c) * X2.ld;
+    else x = extra;
+    T acc = T(0);
+    for (int64_t i = i0; i < n; i += stride) acc += x[i] * v[i];
+    const double s = block_sum((double)acc, sh);
+    if (threadIdx.x == 0) partial[(int64_t)blockIdx.x * ncols + j] = s;
+  }
+}
+
+// out[j] = sum_b partial[b*ncols + j] (fixed order, deterministic)
+__global__ void reduce_partials_kernel(const double* __restrict__ partial, int nblocks, int ncols,
+                                       double* __restrict__ out, const int* done) {
+  if (done && *done) return;
+  for (int j = threadIdx.x; j < ncols; j += blockDim.x) {
+    double s = 0.0;
+    for (int b = 0; b < nblocks; ++b) s += partial[(int64_t)b * ncols + j];
+    out[j] = s;
+  }
+}
+
+// v -= X1 h1 + X2 h2 (h from device memory), optionally y = alpha_scale * v
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+multiaxpy_kernel(Cols<T> X1, Cols<T> X2, const double* __restrict__ h, T* __restrict__ v, int64_t n) {
+  __shared__ double hs[kMaxCols];
+  const int c = X1.c + X2.c;
+  for (int j = threadIdx.x; j < c; j += blockDim.x) hs[j] = h[j];
+  __syncthreads();
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    T acc = v[i];
+    for (int j = 0; j < X1.c; ++j) acc -= X1.p[(int64_t)j * X1.ld + i] * (T)hs[j];
+    for (int j = 0; j < X2.c; ++j) acc -= X2.p[(int64_t)j * X2.ld + i] * (T)hs[X1.c + j];
+    v[i] = acc;
+  }
+}
+
+// out_j = sum_k X[:, k] Y[k, j] for j < mo (Y column-major with leading dim ldy);
+// outputs in tiles of 8 so each row's X values are re-read from L1
+__global__ void __launch_bounds__(kThreads)
+lincomb_kernel(const double* __restrict__ X, int64_t ldx, int m, const double* __restrict__ Y, int ldy,
+               int mo, double* __restrict__ out, int64_t ldo, int64_t n) {
+  __shared__ double ys[kMaxM * kMaxM];
+  for (int t = threadIdx.x; t < m * mo; t += blockDim.x) {
+    const int k = t % m, j = t / m;
+    ys[j * m + k] = Y[(int64_t)j * ldy + k];
+  }
+  __syncthreads();
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    for (int j0 = 0; j0 < mo; j0 += 8) {
+      double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+      const int jn = min(8, mo - j0);
+      for (int k = 0; k < m; ++k) {
+        const double x = X[(int64_t)k * ldx + i];
+#pragma unroll
+        for (int jj = 0; jj < 8; ++jj)
+          if (jj < jn) acc[jj] = fma(x, ys[(j0 + jj) * m + k], acc[jj]);
+      }
+#pragma unroll
+      for (int jj = 0; jj < 8; ++jj)
+        if (jj < jn) out[(int64_t)(j0 + jj) * ldo + i] = acc[jj];
+    }
+  }
+}
+
+// y = a * x with a = scal[ia] (or 1/sqrt(scal[ia]) when inv_sqrt)
+__global__ void scale_copy_kernel(const double* __restrict__ x, double* __restrict__ y, int64_t n,
+                                  const double* __restrict__ scal, int ia, int inv_sqrt) {
+  double a = scal[ia];
+  if (inv_sqrt) a = 1.0 / sqrt(a);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = a * x[i];
+}
+
+// r = Au - theta u with theta = scal[0]
+__global__ void residual_kernel(const double* __restrict__ Au, const double* __restrict__ u,
+                                const double* __restrict__ theta, double* __restrict__ r, int64_t n) {
+  const double th = *theta;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    r[i] = Au[i] - th * u[i];
+}
+
+template <typename S, typename D>
+__global__ void convert_kernel(const S* __restrict__ x, D* __restrict__ y, int64_t n, double a) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = (D)(a * (double)x[i]);
+}
+
+// start vector: uniform in [-1/2, 1/2) from SplitMix64 (counter form)
+__global__ void random_kernel(double* __restrict__ v, int64_t n, uint64_t seed) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    uint64_t z = seed + ((uint64_t)i + 1ull) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    v[i] = (double)(z >> 11) * 0x1.0p-53 - 0.5;
+  }
+}
+
+// H[:, col] and H[col, :] from the dot results (symmetric), ld = ldh
+__global__ void set_h_column_kernel(double* __restrict__ H, int ldh, int col, const double* __restrict__ d) {
+  for (int i = threadIdx.x; i <= col; i += blockDim.x) {
+    double v = d[i];
+    H[(int64_t)col * ldh + i] = v;
+    H[(int64_t)i * ldh + col] = v;
+  }
+}
+
+// H = diag(theta[sel[0..m)])
+__global__ void set_h_diag_kernel(double* __restrict__ H, int ldh, int m, const double* __restrict__ theta, int off) {
+  for (int t = threadIdx.x; t < m * m; t += blockDim.x) {
+    const int i = t % m, j = t / m;
+    H[(int64_t)j * ldh + i] = (i == j) ? theta[off + i] : 0.0;
+  }
+}
+
+// Symmetric eigenproblem of H (m x m, m <= kMaxM) by the cyclic Jacobi method
+// with the round-robin (tournament) ordering, m/2 rotations per round applied
+// in parallel.  Output: theta[j] and Y[:, j] ordered by |theta - sigma|
+// (ties: theta ascending).
+__global__ void __launch_bounds__(kThreads)
+rr_eig_kernel(const double* __restrict__ H, int ldh, int m, double sigma, double* __restrict__ theta,
+              double* __restrict__ Y, int ldy) {
+  extern __shared__ double smem[];
+  const int mp = (m + 1) & ~1;  // padded to even
+  double* A = smem;             // mp x mp, column-major
+  double* V = A + mp * mp;      // mp x mp
+  double* cs = V + mp * mp;     // cos/sin per pair
+  int* pr = reinterpret_cast<int*>(cs + mp);  // pairs
+  __shared__ double red[kThreads / 32];
+  __shared__ int stop;
+  for (int t = threadIdx.x; t < mp * mp; t += blockDim.x) {
+    const int i = t % mp, j = t / mp;
+    A[t] = (i < m && j < m) ? 0.5 * (H[(int64_t)j * ldh + i] + H[(int64_t)i * ldh + j]) : 0.0;
+    V[t] = (i == j) ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  const int half = mp / 2;
+  for (int sweep = 0; sweep < 40; ++sweep) {
+    double off = 0.0, fro = 0.0;
+    for (int t = threadIdx.x; t < mp * mp; t += blockDim.x) {
+      const int i = t % mp, j = t / mp;
+      fro += A[t] * A[t];
+      if (i != j) off += A[t] * A[t];
+    }
+    off = block_sum(off, red);
+    __syncthreads();
+    fro = block_sum(fro, red);
+    if (threadIdx.x == 0) stop = (off <= 1e-30 * fro) || fro == 0.0;
+    __syncthreads();
+    if (stop) break;
+    for (int round = 0; round < mp - 1; ++round) {
+      // pairs of the circle method: index 0 fixed, others rotate
+      for (int k = threadIdx.x; k < half; k += blockDim.x) {
+        auto pos = [&](int q) { return q == 0 ? 0 : ((q - 1 + round) % (mp - 1)) + 1; };
+        int p = pos(k), q = pos(mp - 1 - k);
+        if (p > q) { int tmp = p; p = q; q = tmp; }
+        pr[2 * k] = p;
+        pr[2 * k + 1] = q;
+        const double apq = A[q * mp + p];
+        double c = 1.0, s = 0.0;
+        if (p < m && q < m && apq != 0.0) {
+          const double tau = (A[q * mp + q] - A[p * mp + p]) / (2.0 * apq);
+          double t;
+          if (fabs(tau) > 1e150) t = 0.5 / tau;
+          else t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+          c = 1.0 / sqrt(1.0 + t * t);
+          s = t * c;
+        }
+        cs[2 * k] = c;
+        cs[2 * k + 1] = s;
+      }
+      __syncthreads();
+      // columns: A <- A J, V <- V J
+      for (int t = threadIdx.x; t < half * mp; t += blockDim.x) {
+        const int k = t / mp, i = t % mp;
+        const int p = pr[2 * k], q = pr[2 * k + 1];
+        const double c = cs[2 * k], s = cs[2 * k + 1];
+        const double ap = A[p * mp + i], aq = A[q * mp + i];
+        A[p * mp + i] = c * ap - s * aq;
+        A[q * mp + i] = s * ap + c * aq;
+        const double vp = V[p * mp + i], vq = V[q * mp + i];
+        V[p * mp + i] = c * vp - s * vq;
+        V[q * mp + i] = s * vp + c * vq;
+      }
+      __syncthreads();
+      // rows: A <- J^T A
+      for (int t = threadIdx.x; t < half * mp; t += blockDim.x) {
+        const int k = t / mp, j = t % mp;
+        const int p = pr[2 * k], q = pr[2 * k + 1];
+        const double c = cs[2 * k], s = cs[2 * k + 1];
+        const double ap = A[j * mp + p], aq = A[j * mp + q];
+        A[j * mp + p] = c * ap - s * aq;
+        A[j * mp + q] = s * ap + c * aq;
+      }
+      __syncthreads();
+    }
+  }
+  // order by |theta - sigma|, then theta: rank of each eigenvalue
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    const double ti = A[i * mp + i], di = fabs(ti - sigma);
+    int rank = 0;
+    for (int j = 0; j < m; ++j) {
+      const double tj = A[j * mp + j], dj = fabs(tj - sigma);
+      if (dj < di || (dj == di && (tj < ti || (tj == ti && j < i)))) ++rank;
+    }
+    theta[rank] = ti;
+    for (int r = 0; r < m; ++r) Y[(int64_t)rank * ldy + r] = V[i * mp + r];
+  }
+}
+
+// ---------------------------------------------------------------- SQMR ---
+// scalar slots of the inner solver (double)
+enum {
+  S_RHO = 0, S_SIGMA, S_ALPHA, S_THETA, S_TAU, S_CD, S_CQ, S_BETA, S_BNORM, S_TOL, S_IT,
+  S_NSCAL
+};
+
+// Projected matrix-vector step: after t = (A - theta^ I) q, dots[0..c) =
+// Qt^T t and dots[c] = q^T t.  Then:
+//   alpha = rho / sigma;  r -= alpha (t - Qt h);  partial ||r||^2
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+sqmr_update_r_kernel(Cols<T> Qt, const double* __restrict__ dots, const T* __restrict__ t, T* __restrict__ r,
+                     int64_t n, double* __restrict__ scal, double* __restrict__ partial, const int* done) {
+  if (*done) return;
+  __shared__ double hs[kMaxCols];
+  __shared__ double sh[kThreads / 32];
+  const int c = Qt.c;
+  for (int j = threadIdx.x; j < c; j += blockDim.x) hs[j] = dots[j];
+  __syncthreads();
+  const double sigma = dots[c];
+  const T alpha = (T)(scal[S_RHO] / sigma);
+  T acc = T(0);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    T ti = t[i];
+    for (int j = 0; j < c; ++j) ti -= Qt.p[(int64_t)j * Qt.ld + i] * (T)hs[j];
+    const T ri = r[i] - alpha * ti;
+    r[i] = ri;
+    acc += ri * ri;
+  }
+  const double s = block_sum((double)acc, sh);
+  if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+// After ||r||^2: theta_k, c_k, tau_k and the convergence test (one thread).
+__global__ void sqmr_scalar_theta_kernel(const double* __restrict__ partial, int nblocks,
+                                         const double* __restrict__ dots, int c, double* __restrict__ scal,
+                                         int* done, int* breakdown) {
+  if (*done) return;
+  double rr = 0.0;
+  for (int b = 0; b < nblocks; ++b) rr += partial[b];
+  const double sigma = dots[c];
+  if (sigma == 0.0 || !isfinite(sigma)) {
+    *breakdown = 1;
+    *done = 1;
+    return;
+  }
+  const double alpha = scal[S_RHO] / sigma;
+  const double theta_old = scal[S_THETA];
+  const double theta = sqrt(rr) / scal[S_TAU];
+  const double c2 = 1.0 / (1.0 + theta * theta);
+  const double tau = scal[S_TAU] * theta * sqrt(c2);
+  scal[S_ALPHA] = alpha;
+  scal[S_SIGMA] = sigma;
+  scal[S_CD] = c2 * theta_old * theta_old;
+  scal[S_CQ] = c2 * alpha;
+  scal[S_THETA] = theta;
+  scal[S_TAU] = tau;
+  const double it = scal[S_IT] + 1.0;
+  scal[S_IT] = it;
+  if (sqrt(it + 1.0) * tau <= scal[S_TOL] || !isfinite(tau)) *done = 2;  // 2: stop after x update
+}
+
+// d = cd d + cq q ; x += d
+template <typename T>
+__global__ void sqmr_update_dx_kernel(T* __restrict__ d, T* __restrict__ x, const T* __restrict__ q, int64_t n,
+                                      const double* __restrict__ scal, const int* done) {
+  if (*done == 1) return;
+  const T cd = (T)scal[S_CD], cq = (T)scal[S_CQ];
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const T di = cd * d[i] + cq * q[i];
+    d[i] = di;
+    x[i] += di;
+  }
+}
+
+__global__ void sqmr_mark_done_kernel(int* done) {
+  if (*done == 2) *done = 1;
+}
+
+// g = Minv (Qt^T y) (small, one thread block)
+__global__ void small_matvec_kernel(const double* __restrict__ Minv, int c, const double* __restrict__ g,
+                                    double* __restrict__ out, const int* done) {
+  if (done && *done) return;
+  for (int i = threadIdx.x; i < c; i += blockDim.x) {
+    double s = 0.0;
+    for (int j = 0; j < c; ++j) s += Minv[(int64_t)j * c + i] * g[j];
+    out[i] = s;
+  }
+}
+
+// u = y - W gg ; partial r^T u
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+sqmr_update_u_kernel(Cols<T> W, const double* __restrict__ gg, const T* __restrict__ y, const T* __restrict__ r,
+                     T* __restrict__ u, int64_t n, double* __restrict__ partial, const int* done) {
+  if (done && *done) return;
+  __shared__ double hs[kMaxCols];
+  __shared__ double sh[kThreads / 32];
+  for (int j = threadIdx.x; j < W.c; j += blockDim.x) hs[j] = gg[j];
+  __syncthreads();
+  T acc = T(0);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    T ui = y[i];
+    for (int j = 0; j < W.c; ++j) ui -= W.p[(int64_t)j * W.ld + i] * (T)hs[j];
+    u[i] = ui;
+    acc += r[i] * ui;
+  }
+  const double s = block_sum((double)acc, sh);
+  if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+// rho' = r^T u ; beta = rho'/rho (first call: just rho)
+__global__ void sqmr_scalar_beta_kernel(const double* __restrict__ partial, int nblocks, double* __restrict__ scal,
+                                        int first, int* done, int* breakdown) {
+  if (*done) return;
+  double rho = 0.0;
+  for (int b = 0; b < nblocks; ++b) rho += partial[b];
+  if (first) {
+    scal[S_BETA] = 0.0;
+  } else {
+    if (scal[S_RHO] == 0.0) {
+      *breakdown = 1;
+      *done = 1;
+      return;
+    }
+    scal[S_BETA] = rho / scal[S_RHO];
+  }
+  scal[S_RHO] = rho;
+  if (rho == 0.0 || !isfinite(rho)) {
+    *breakdown = 1;
+    *done = 1;
+  }
+}
+
+// q = u + beta q
+template <typename T>
+__global__ void sqmr_update_q_kernel(const T* __restrict__ u, T* __restrict__ q, int64_t n,
+                                     const double* __restrict__ scal, const int* done) {
+  if (*done) return;
+  const T beta = (T)scal[S_BETA];
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    q[i] = u[i] + beta * q[i];
+}
+
+// init: r = b, x = d = 0, partial ||r||^2
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+sqmr_init_kernel(const T* __restrict__ b, T* __restrict__ r, T* __restrict__ x, T* __restrict__ d, int64_t n,
+                 double* __restrict__ partial) {
+  __shared__ double sh[kThreads / 32];
+  T acc = T(0);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const T bi = b[i];
+    r[i] = bi;
+    x[i] = T(0);
+    d[i] = T(0);
+    acc += bi * bi;
+  }
+  const double s = block_sum((double)acc, sh);
+  if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+__global__ void sqmr_scalar_init_kernel(const double* __restrict__ partial, int nblocks, double* __restrict__ scal,
+                                        double rel_tol, int* done, int* breakdown) {
+  double rr = 0.0;
+  for (int b = 0; b < nblocks; ++b) rr += partial[b];
+  const double bn = sqrt(rr);
+  for (int i = 0; i < S_NSCAL; ++i) scal[i] = 0.0;
+  scal[S_TAU] = bn;
+  scal[S_BNORM] = bn;
+  scal[S_TOL] = rel_tol * bn;
+  *breakdown = 0;
+  *done = (bn == 0.0 || !isfinite(bn)) ? 1 : 0;
+}
+
+// Sign convention of an eigenvector: the largest |x_i| (lowest index on
+// ties).  Pass 1: max |x| via an atomic max on the IEEE bits (monotone for
+// non-negative doubles); pass 2: smallest index attaining it.
+__global__ void max_abs_bits_kernel(const double* __restrict__ x, int64_t n, unsigned long long* out) {
+  unsigned long long best = 0ull;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(fabs(x[i]));
+    best = b > best ? b : best;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long v = __shfl_xor_sync(0xffffffffu, best, o);
+    best = v > best ? v : best;
+  }
+  if ((threadIdx.x & 31) == 0) atomicMax(out, best);
+}
+
+__global__ void first_index_kernel(const double* __restrict__ x, int64_t n, const unsigned long long* bits,
+                                   unsigned long long* out) {
+  const double m = __longlong_as_double((long long)*bits);
+  unsigned long long best = ~0ull;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    if (fabs(x[i]) == m && (unsigned long long)i < best) best = (unsigned long long)i;
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long v = __shfl_xor_sync(0xffffffffu, best, o);
+    best = v < best ? v : best;
+  }
+  if ((threadIdx.x & 31) == 0) atomicMin(out, best);
+}
+
+}  // namespace
+
+// ------------------------------------------------------------ the solver ---
+class JdSolver {
+ public:
+  JdSolver(anderson_s* h, ildl_s* pc, const jd_params& p, double sigma, int k, double tol, cudaStream_t s)
+      : h_(h), pc_(pc), p_(p), sigma_(sigma), k_(k), tol_(tol), s_(s) {}
+  ~JdSolver() { release(); }
+
+  int run(double* evals, double* evecs, jd_stats* st);
+
+ private:
+  anderson_s* h_;
+  ildl_s* pc_;
+  jd_params p_;
+  double sigma_;
+  int k_;
+  double tol_;
+  cudaStream_t s_;
+  int64_t n_ = 0, ld_ = 0;
+  int jmin_ = 0, jmax_ = 0;
+  double normA_ = 0.0;
+  // binary64 buffers
+  double *V_ = nullptr, *AV_ = nullptr, *Vt_ = nullptr, *AVt_ = nullptr, *Q_ = nullptr;
+  double *t_ = nullptr, *u_ = nullptr, *Au_ = nullptr, *r_ = nullptr;
+  double *H_ = nullptr, *theta_ = nullptr, *Y_ = nullptr, *dots_ = nullptr, *partial_ = nullptr, *scal_ = nullptr;
+  double *Minv_ = nullptr, *gg_ = nullptr;
+  int* flags_ = nullptr;  // [0] done, [1] breakdown
+  unsigned long long* amax_ = nullptr;  // [0] max bits, [1] first index
+  // inner-precision buffers (allocated as bytes)
+  void *Qt_ = nullptr, *W_ = nullptr, *xb_ = nullptr, *rb_ = nullptr, *qb_ = nullptr, *db_ = nullptr,
+       *tb_ = nullptr, *yb_ = nullptr, *ub_ = nullptr, *bb_ = nullptr;
+  double* host_ = nullptr;  // pinned readback area
+  int nb_ = 0;              // blocks of vector kernels
+  std::vector<double> Mq_;  // cached Q^T W_Q block (host, kc x kc)
+  int inner_total_ = 0;
+
+  int alloc();
+  void release();
+  int dot_cols(Cols<double> X1, Cols<double> X2, const double* extra, const double* v, double* out);
+  int cgs2(int kc, int m, double* t, double* nrm_host);
+  int rr(int m);
+  template <typename T>
+  int correction(int kc, double theta_hat, double rel_tol, int* its);
+  int finalize(int kc, double* lam, double* evals, double* evecs, jd_stats* st);
+  int sync_read(const double* dev, int cnt, double* host);
+};
+
+int JdSolver::alloc() {
+  n_ = h_->n;
+  ld_ = (n_ + 31) & ~(int64_t)31;
+  nb_ = vec_blocks(n_);
+  const size_t vb = (size_t)ld_ * sizeof(double);
+  auto A = [&](void** p, size_t bytes) -> int {
+    cudaError_t e = cudaMalloc(p, std::max<size_t>(bytes, 16));
+    if (e != cudaSuccess)
+      return fail(e == cudaErrorMemoryAllocation ? JD_ENOMEM : JD_EDEVICE, "jd_solve: cudaMalloc: %s", cudaGetErrorString(e));
+    return JD_OK;
+  };
+  AJD_TRY(A((void**)&V_, vb * jmax_));
+  AJD_TRY(A((void**)&AV_, vb * jmax_));
+  AJD_TRY(A((void**)&Vt_, vb * jmax_));
+  AJD_TRY(A((void**)&AVt_, vb * jmax_));
+  AJD_TRY(A((void**)&Q_, vb * k_));
+  AJD_TRY(A((void**)&t_, vb));
+  AJD_TRY(A((void**)&u_, vb));
+  AJD_TRY(A((void**)&Au_, vb));
+  AJD_TRY(A((void**)&r_, vb));
+  AJD_TRY(A((void**)&H_, sizeof(double) * kMaxM * kMaxM));
+  AJD_TRY(A((void**)&theta_, sizeof(double) * kMaxM));
+  AJD_TRY(A((void**)&Y_, sizeof(double) * kMaxM * kMaxM));
+  AJD_TRY(A((void**)&dots_, sizeof(double) * kMaxCols));
+  AJD_TRY(A((void**)&partial_, sizeof(double) * (size_t)nb_ * kMaxCols));
+  AJD_TRY(A((void**)&scal_, sizeof(double) * 64));
+  AJD_TRY(A((void**)&Minv_, sizeof(double) * (k_ + 1) * (k_ + 1)));
+  AJD_TRY(A((void**)&gg_, sizeof(double) * (k_ + 1)));
+  AJD_TRY(A((void**)&flags_, sizeof(int) * 4));
+  AJD_TRY(A((void**)&amax_, 2 * sizeof(unsigned long long)));
+  const size_t eb = p_.precision == JD_FP32 ? sizeof(float) : sizeof(double);
+  const size_t pb = (size_t)ld_ * eb;
+  AJD_TRY(A(&Qt_, pb * (k_ + 1)));
+  AJD_TRY(A(&W_, pb * (k_ + 1)));
+  for (void** b : {&xb_, &rb_, &qb_, &db_, &tb_, &yb_, &ub_, &bb_}) AJD_TRY(A(b, pb));
+  AJD_CUDA(cudaMallocHost(&host_, sizeof(double) * (kMaxM * kMaxM + 256)));
+  return JD_OK;
+}
+
+void JdSolver::release() {
+  for (void* p : {(void*)V_, (void*)AV_, (void*)Vt_, (void*)AVt_, (void*)Q_, (void*)t_, (void*)u_, (void*)Au_,
+                  (void*)r_, (void*)H_, (void*)theta_, (void*)Y_, (void*)dots_, (void*)partial_, (void*)scal_,
+                  (void*)Minv_, (void*)gg_, (void*)flags_, (void*)amax_, Qt_, W_, xb_, rb_, qb_, db_, tb_, yb_, ub_, bb_})
+    if (p) cudaFree(p);
+  if (host_) cudaFreeHost(host_);
+  V_ = nullptr;
+  host_ = nullptr;
+}
+
+int JdSolver::sync_read(const double* dev, int cnt, double* host) {
+  AJD_CUDA(cudaMemcpyAsync(host_, dev, sizeof(double) * cnt, cudaMemcpyDeviceToHost, s_));
+  AJD_CUDA(cudaStreamSynchronize(s_));
+  std::memcpy(host, host_, sizeof(double) * cnt);
+  return JD_OK;
+}
+
+int JdSolver::dot_cols(Cols<double> X1, Cols<double> X2, const double* extra, const double* v, double* out) {
+  const int nc = X1.c + X2.c + (extra ? 1 : 0);
+  if (nc == 0) return JD_OK;
+  multidot_kernel<double><<<nb_, kThreads, 0, s_>>>(X1, X2, extra, v, n_, partial_, nc, nullptr);
+  reduce_partials_kernel<<<1, 128, 0, s_>>>(partial_, nb_, nc, out, nullptr);
+  AJD_CHECK_LAUNCH();
+  return JD_OK;
+}
+
+// t <- (I - [Q V][Q V]^T)^2 t; returns ||t|| (device scal[0] and host)
+int JdSolver::cgs2(int kc, int m, double* t, double* nrm_host) {
+  Cols<double> Xq{Q_, ld_, kc}, Xv{V_, ld_, m};
+  for (int pass = 0; pass < 2; ++pass) {
+    if (kc + m == 0) break;
+    AJD_TRY(dot_cols(Xq, Xv, nullptr, t, dots_));
+    multiaxpy_kernel<double><<<nb_, kThreads, 0, s_>>>(Xq, Xv, dots_, t, n_);
+  }
+  AJD_TRY(dot_cols(Cols<double>{t, ld_, 1}, Cols<double>{}, nullptr, t, scal_));
+  double nn;
+  AJD_TRY(sync_read(scal_, 1, &nn));
+  *nrm_host = std::sqrt(std::max(nn, 0.0));
+  return JD_OK;
+}
+
+int JdSolver::rr(int m) {
+  const int mp = (m + 1) & ~1;
+  const size_t sm = sizeof(double) * (2 * mp * mp + mp) + sizeof(int) * mp;
+  static bool attr = false;
+  if (!attr) {
+    AJD_CUDA(cudaFuncSetAttribute(rr_eig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)(sizeof(double) * (2 * kMaxM * kMaxM + kMaxM) + sizeof(int) * kMaxM)));
+    attr = true;
+  }
+  rr_eig_kernel<<<1, kThreads, sm, s_>>>(H_, kMaxM, m, sigma_, theta_, Y_, kMaxM);
+  AJD_CHECK_LAUNCH();
+  return JD_OK;
+}
+
+template <typename T>
+int JdSolver::correction(int kc, double theta_hat, double rel_tol, int* its) {
+  const int c = kc + 1;
+  T* Qt = static_cast<T*>(Qt_);
+  T* W = static_cast<T*>(W_);
+  T *x = static_cast<T*>(xb_), *r = static_cast<T*>(rb_), *q = static_cast<T*>(qb_), *d = static_cast<T*>(db_);
+  T *t = static_cast<T*>(tb_), *y = static_cast<T*>(yb_), *u = static_cast<T*>(ub_), *b = static_cast<T*>(bb_);
+  int* done = flags_;
+  int* brk = flags_ + 1;
+  const int bl = nb_;
+  // Qt[:, kc] = u, W[:, kc] = K^{-1} u  (Q columns and their W are cached)
+  convert_kernel<double, T><<<bl, kThreads, 0, s_>>>(u_, Qt + (int64_t)kc * ld_, n_, 1.0);
+  AJD_TRY(ildl_apply_dev<T>(pc_, Qt + (int64_t)kc * ld_, W + (int64_t)kc * ld_, s_));
+  // M = Qt^T W (c x c): only row/column kc are new
+  {
+    multidot_kernel<T><<<bl, kThreads, 0, s_>>>(Cols<T>{Qt, ld_, c}, Cols<T>{}, nullptr, W + (int64_t)kc * ld_, n_,
+                                                partial_, c, nullptr);
+    reduce_partials_kernel<<<1, 128, 0, s_>>>(partial_, bl, c, dots_, nullptr);
+    std::vector<double> col(c);
+    AJD_TRY(sync_read(dots_, c, col.data()));
+    // assemble M (host) from the cached Q block and the new column, invert
+    std::vector<double> M((size_t)c * c), Mi((size_t)c * c, 0.0);
+    for (int i = 0; i < kc; ++i)
+      for (int j = 0; j < kc; ++j) M[(size_t)j * c + i] = Mq_[(size_t)j * kc + i];
+    for (int i = 0; i < c; ++i) {
+      M[(size_t)kc * c + i] = col[i];
+      M[(size_t)i * c + kc] = col[i];
+    }
+    // Gauss–Jordan with partial pivoting (c <= 65)
+    std::vector<double> A = M;
+    for (int i = 0; i < c; ++i) Mi[(size_t)i * c + i] = 1.0;
+    for (int cc = 0; cc < c; ++cc) {
+      int pv = cc;
+      for (int rr2 = cc + 1; rr2 < c; ++rr2)
+        if (std::fabs(A[(size_t)cc * c + rr2]) > std::fabs(A[(size_t)cc * c + pv])) pv = rr2;
+      if (A[(size_t)cc * c + pv] == 0.0) return fail(JD_EBREAKDOWN, "jd: Q~^T K^{-1} Q~ is singular");
+      for (int j = 0; j < c; ++j) {
+        std::swap(A[(size_t)j * c + cc], A[(size_t)j * c + pv]);
+        std::swap(Mi[(size_t)j * c + cc], Mi[(size_t)j * c + pv]);
+      }
+      const double inv = 1.0 / A[(size_t)cc * c + cc];
+      for (int j = 0; j < c; ++j) {
+        A[(size_t)j * c + cc] *= inv;
+        Mi[(size_t)j * c + cc] *= inv;
+      }
+      for (int rr2 = 0; rr2 < c; ++rr2) {
+        if (rr2 == cc) continue;
+        const double f = A[(size_t)cc * c + rr2];
+        if (f == 0.0) continue;
+        for (int j = 0; j < c; ++j) {
+          A[(size_t)j * c + rr2] -= f * A[(size_t)j * c + cc];
+          Mi[(size_t)j * c + rr2] -= f * Mi[(size_t)j * c + cc];
+        }
+      }
+    }
+    AJD_CUDA(cudaMemcpyAsync(Minv_, Mi.data(), sizeof(double) * c * c, cudaMemcpyHostToDevice, s_));
+  }
+  // rhs b = -r (binary64 residual, already orthogonal to Q and u)
+  convert_kernel<double, T><<<bl, kThreads, 0, s_>>>(r_, b, n_, -1.0);
+  Cols<T> QtC{Qt, ld_, c}, WC{W, ld_, c};
+  // init: r = b, x = d = 0, tau = ||b||; u = P b; q = u; rho = r^T u
+  sqmr_init_kernel<T><<<bl, kThreads, 0, s_>>>(b, r, x, d, n_, partial_);
+  sqmr_scalar_init_kernel<<<1, 1, 0, s_>>>(partial_, bl, scal_, rel_tol, done, brk);
+  auto precond = [&]() -> int {
+    AJD_TRY(ildl_apply_dev<T>(pc_, r, y, s_));
+    multidot_kernel<T><<<bl, kThreads, 0, s_>>>(QtC, Cols<T>{}, nullptr, y, n_, partial_, c, done);
+    reduce_partials_kernel<<<1, 128, 0, s_>>>(partial_, bl, c, dots_, done);
+    small_matvec_kernel<<<1, 64, 0, s_>>>(Minv_, c, dots_, gg_, done);
+    sqmr_update_u_kernel<T><<<bl, kThreads, 0, s_>>>(WC, gg_, y, r, u, n_, partial_, done);
+    return JD_OK;
+  };
+  AJD_TRY(precond());
+  sqmr_scalar_beta_kernel<<<1, 1, 0, s_>>>(partial_, bl, scal_, 1, done, brk);
+  sqmr_update_q_kernel<T><<<bl, kThreads, 0, s_>>>(u, q, n_, scal_, done);  // q = u (beta = 0)
+  const int maxit = p_.max_inner;
+  int it = 0;
+  const int chunk = 4;
+  while (it < maxit) {
+    const int nstep = std::min(chunk, maxit - it);
+    for (int s = 0; s < nstep; ++s) {
+      AJD_TRY(stencil_apply<T>(h_, (T)theta_hat, q, t, 1, s_));
+      multidot_kernel<T><<<bl, kThreads, 0, s_>>>(QtC, Cols<T>{}, q, t, n_, partial_, c + 1, done);
+      reduce_partials_kernel<<<1, 128, 0, s_>>>(partial_, bl, c + 1, dots_, done);
+      sqmr_update_r_kernel<T><<<bl, kThreads, 0, s_>>>(QtC, dots_, t, r, n_, scal_, partial_, done);
+      sqmr_scalar_theta_kernel<<<1, 1, 0, s_>>>(partial_, bl, dots_, c, scal_, done, brk);
+      sqmr_update_dx_kernel<T><<<bl, kThreads, 0, s_>>>(d, x, q, n_, scal_, done);
+      sqmr_mark_done_kernel<<<1, 1, 0, s_>>>(done);
+      AJD_TRY(precond());
+      sqmr_scalar_beta_kernel<<<1, 1, 0, s_>>>(partial_, bl, scal_, 0, done, brk);
+      sqmr_update_q_kernel<T><<<bl, kThreads, 0, s_>>>(u, q, n_, scal_, done);
+    }
+    AJD_CHECK_LAUNCH();
+    it += nstep;
+    double sc[S_NSCAL];
+    int fl[2];
+    AJD_CUDA(cudaMemcpyAsync(host_, scal_, sizeof(double) * S_NSCAL, cudaMemcpyDeviceToHost, s_));
+    AJD_CUDA(cudaMemcpyAsync(host_ + S_NSCAL, flags_, sizeof(int) * 2, cudaMemcpyDeviceToHost, s_));
+    AJD_CUDA(cudaStreamSynchronize(s_));
+    std::memcpy(sc, host_, sizeof(sc));
+    std::memcpy(fl, host_ + S_NSCAL, sizeof(fl));
+    if (fl[0]) {
+      it = (int)sc[S_IT];
+      break;
+    }
+  }
+  *its = it;
+  // t (binary64) = x, then the caller orthogonalises it
+  convert_kernel<T, double><<<bl, kThreads, 0, s_>>>(x, t_, n_, 1.0);
+  AJD_CHECK_LAUNCH();
+  return JD_OK;
+}
+
+int JdSolver::run(double* evals, double* evecs, jd_stats* st) {
+  using Clock = std::chrono::steady_clock;
+  const auto t0 = Clock::now();
+  normA_ = 6.0 + h_->max_abs_eps;
+  const int64_t n = h_->n;
+  jmin_ = p_.jmin > 0 ? p_.jmin : std::max(2 * k_, 10);
+  jmax_ = p_.jmax > 0 ? p_.jmax : jmin_ + 15;
+  jmax_ = (int)std::min<int64_t>(std::min<int64_t>(jmax_, kMaxM), n - k_);
+  jmin_ = std::min(jmin_, jmax_ - 1);
+  if (jmax_ < 2 || jmin_ < 1) return fail(JD_EINVAL, "jd_solve: lattice too small for k = %d", k_);
+  if (k_ + jmax_ + 2 > kMaxCols) return fail(JD_EINVAL, "jd_solve: k + jmax too large");
+  AJD_TRY(alloc());
+  Mq_.clear();
+  const uint64_t seed = p_.seed ? p_.seed : (h_->seed ^ 0xD1B54A32D192ED03ull);
+  random_kernel<<<nb_, kThreads, 0, s_>>>(t_, n, seed);
+  AJD_CUDA(cudaMemsetAsync(H_, 0, sizeof(double) * kMaxM * kMaxM, s_));
+  int m = 0, kc = 0, outer = 0, restarts = 0, steps_on_pair = 0;
+  std::vector<double> lam;
+  double theta0 = sigma_, rnorm = 0.0;
+  int status = JD_OK;
+  uint64_t reseed = seed;
+  while (true) {
+    // --- expand: orthogonalise t against [Q V], append
+    double nrm = 0.0;
+    AJD_TRY(cgs2(kc, m, t_, &nrm));
+    int tries = 0;
+    while (!(nrm > 1e-10) && tries < 3) {  // t in span: take a fresh random direction
+      random_kernel<<<nb_, kThreads, 0, s_>>>(t_, n, ++reseed);
+      AJD_TRY(cgs2(kc, m, t_, &nrm));
+      ++tries;
+    }
+    if (!(nrm > 0.0)) return fail(JD_EBREAKDOWN, "jd_solve: cannot expand the search space");
+    scale_copy_kernel<<<nb_, kThreads, 0, s_>>>(t_, V_ + (int64_t)m * ld_, n, scal_, 0, 1);
+    AJD_TRY(stencil_apply<double>(h_, 0.0, V_ + (int64_t)m * ld_, AV_ + (int64_t)m * ld_, 1, s_));
+    AJD_TRY(dot_cols(Cols<double>{V_, ld_, m + 1}, Cols<double>{}, nullptr, AV_ + (int64_t)m * ld_, dots_));
+    set_h_column_kernel<<<1, 128, 0, s_>>>(H_, kMaxM, m, dots_);
+    ++m;
+    ++outer;
+    // --- Rayleigh–Ritz, selection, locking
+    bool finished = false;
+    while (true) {
+      AJD_TRY(rr(m));
+      double th[kMaxM];
+      AJD_TRY(sync_read(theta_, m, th));
+      theta0 = th[0];
+      // u = V y1, Au = AV y1, r = Au - theta u, r -= Q Q^T r
+      lincomb_kernel<<<nb_, kThreads, 0, s_>>>(V_, ld_, m, Y_, kMaxM, 1, u_, ld_, n);
+      lincomb_kernel<<<nb_, kThreads, 0, s_>>>(AV_, ld_, m, Y_, kMaxM, 1, Au_, ld_, n);
+      residual_kernel<<<nb_, kThreads, 0, s_>>>(Au_, u_, theta_, r_, n);
+      AJD_TRY(dot_cols(Cols<double>{r_, ld_, 1}, Cols<double>{}, nullptr, r_, scal_ + 1));
+      double rr2;
+      AJD_TRY(sync_read(scal_ + 1, 1, &rr2));
+      rnorm = std::sqrt(std::max(rr2, 0.0));
+      if (kc > 0) {
+        Cols<double> Xq{Q_, ld_, kc};
+        AJD_TRY(dot_cols(Xq, Cols<double>{}, nullptr, r_, dots_));
+        multiaxpy_kernel<double><<<nb_, kThreads, 0, s_>>>(Xq, Cols<double>{}, dots_, r_, n);
+      }
+      if (rnorm <= tol_ * normA_ && m >= 1) {
+        // lock u
+        AJD_CUDA(cudaMemcpyAsync(Q_ + (int64_t)kc * ld_, u_, sizeof(double) * n, cudaMemcpyDeviceToDevice, s_));
+        lam.push_back(theta0);
+        // cache W = K^{-1} q and the Q^T W block for the projected preconditioner
+        {
+          const int c = kc + 1;
+          if (p_.precision == JD_FP32) {
+            float* Qt = static_cast<float*>(Qt_);
+            float* W = static_cast<float*>(W_);
+            convert_kernel<double, float><<<nb_, kThreads, 0, s_>>>(u_, Qt + (int64_t)kc * ld_, n, 1.0);
+            AJD_TRY(ildl_apply_dev<float>(pc_, Qt + (int64_t)kc * ld_, W + (int64_t)kc * ld_, s_));
+            multidot_kernel<float><<<nb_, kThreads, 0, s_>>>(Cols<float>{Qt, ld_, c}, Cols<float>{}, nullptr,
+                                                             W + (int64_t)kc * ld_, n, partial_, c, nullptr);
+          } else {
+            double* Qt = static_cast<double*>(Qt_);
+            double* W = static_cast<double*>(W_);
+            convert_kernel<double, double><<<nb_, kThreads, 0, s_>>>(u_, Qt + (int64_t)kc * ld_, n, 1.0);
+            AJD_TRY(ildl_apply_dev<double>(pc_, Qt + (int64_t)kc * ld_, W + (int64_t)kc * ld_, s_));
+            multidot_kernel<double><<<nb_, kThreads, 0, s_>>>(Cols<double>{Qt, ld_, c}, Cols<double>{}, nullptr,
+                                                              W + (int64_t)kc * ld_, n, partial_, c, nullptr);
+          }
+          reduce_partials_kernel<<<1, 128, 0, s_>>>(partial_, nb_, c, dots_, nullptr);
+          std::vector<double> col(c);
+          AJD_TRY(sync_read(dots_, c, col.data()));
+          std::vector<double> Mn((size_t)c * c);
+          for (int i = 0; i < kc; ++i)
+            for (int j = 0; j < kc; ++j) Mn[(size_t)j * c + i] = Mq_[(size_t)j * kc + i];
+          for (int i = 0; i < c; ++i) {
+            Mn[(size_t)kc * c + i] = col[i];
+            Mn[(size_t)i * c + kc] = col[i];
+          }
+          Mq_.swap(Mn);
+        }
+        ++kc;
+        steps_on_pair = 0;
+        if (kc == k_) {
+          finished = true;
+          break;
+        }
+        // deflate: keep the other Ritz vectors
+        if (m > 1) {
+          lincomb_kernel<<<nb_, kThreads, 0, s_>>>(V_, ld_, m, Y_ + kMaxM, kMaxM, m - 1, Vt_, ld_, n);
+          lincomb_kernel<<<nb_, kThreads, 0, s_>>>(AV_, ld_, m, Y_ + kMaxM, kMaxM, m - 1, AVt_, ld_, n);
+          std::swap(V_, Vt_);
+          std::swap(AV_, AVt_);
+          set_h_diag_kernel<<<1, 256, 0, s_>>>(H_, kMaxM, m - 1, theta_, 1);
+          --m;
+          continue;
+        }
+        m = 0;
+        random_kernel<<<nb_, kThreads, 0, s_>>>(t_, n, ++reseed);
+        break;
+      }
+      break;
+    }
+    if (finished) break;
+    if (m == 0) continue;  // search space emptied: expand with the random t
+    if (outer >= p_.max_outer) {
+      status = fail(JD_ENOCONV, "jd_solve: %d of %d eigenpairs after %d outer steps (residual %.3e)", kc, k_, outer,
+                    rnorm / normA_);
+      break;
+    }
+    // --- restart
+    if (m >= jmax_) {
+      lincomb_kernel<<<nb_, kThreads, 0, s_>>>(V_, ld_, m, Y_, kMaxM, jmin_, Vt_, ld_, n);
+      lincomb_kernel<<<nb_, kThreads, 0, s_>>>(AV_, ld_, m, Y_, kMaxM, jmin_, AVt_, ld_, n);
+      std::swap(V_, Vt_);
+      std::swap(AV_, AVt_);
+      set_h_diag_kernel<<<1, 256, 0, s_>>>(H_, kMaxM, jmin_, theta_, 0);
+      m = jmin_;
+      ++restarts;
+    }
+    // --- correction equation
+    const double theta_hat = rnorm > p_.switch_tol * normA_ ? sigma_ : theta0;
+    const double rel = std::max(std::pow(p_.inner_decay, steps_on_pair + 1), p_.inner_floor);
+    int its = 0;
+    if (p_.precision == JD_FP32) AJD_TRY(correction<float>(kc, theta_hat, rel, &its));
+    else AJD_TRY(correction<double>(kc, theta_hat, rel, &its));
+    inner_total_ += its;
+    ++steps_on_pair;
+  }
+  if (st) {
+    st->outer_its = outer;
+    st->inner_its = inner_total_;
+    st->restarts = restarts;
+  }
+  const int rc = finalize(kc, lam.data(), evals, evecs, st);
+  if (st) st->solve_ms = std::chrono::duration<double, std::milli>(Clock::now() - t0).count();
+  if (rc != JD_OK) return rc;
+  return status;
+}
+
+// Final Rayleigh–Ritz on the locked vectors, residuals, ordering, signs,
+// copy-out.
+int JdSolver::finalize(int kc, double* lam, double* evals, double* evecs, jd_stats* st) {
+  (void)lam;
+  if (st) st->nconv = kc;
+  if (kc == 0) return JD_OK;
+  const int64_t n = n_;
+  // A Q into AV_ (columns 0..kc), H = Q^T A Q
+  AJD_TRY(stencil_apply<double>(h_, 0.0, Q_, AV_, 1, s_));
+  for (int j = 1; j < kc; ++j)
+    AJD_TRY(stencil_apply<double>(h_, 0.0, Q_ + (int64_t)j * ld_, AV_ + (int64_t)j * ld_, 1, s_));
+  for (int j = 0; j < kc; ++j) {
+    AJD_TRY(dot_cols(Cols<double>{Q_, ld_, j + 1}, Cols<double>{}, nullptr, AV_ + (int64_t)j * ld_, dots_));
+    set_h_column_kernel<<<1, 128, 0, s_>>>(H_, kMaxM, j, dots_);
+  }
+  AJD_TRY(rr(kc));
+  double th[kMaxM];
+  AJD_TRY(sync_read(theta_, kc, th));
+  lincomb_kernel<<<nb_, kThreads, 0, s_>>>(Q_, ld_, kc, Y_, kMaxM, kc, Vt_, ld_, n);
+  lincomb_kernel<<<nb_, kThreads, 0, s_>>>(AV_, ld_, kc, Y_, kMaxM, kc, AVt_, ld_, n);
+  double max_res = 0.0;
+  std::vector<double> signs(kc);
+  for (int j = 0; j < kc; ++j) {
+    double* x = Vt_ + (int64_t)j * ld_;
+    double* ax = AVt_ + (int64_t)j * ld_;
+    AJD_TRY(dot_cols(Cols<double>{x, ld_, 1}, Cols<double>{}, nullptr, x, dots_));
+    residual_kernel<<<nb_, kThreads, 0, s_>>>(ax, x, theta_ + j, r_, n);
+    AJD_TRY(dot_cols(Cols<double>{r_, ld_, 1}, Cols<double>{}, nullptr, r_, dots_ + 1));
+    AJD_CUDA(cudaMemsetAsync(amax_, 0, sizeof(unsigned long long), s_));
+    AJD_CUDA(cudaMemsetAsync(amax_ + 1, 0xFF, sizeof(unsigned long long), s_));
+    max_abs_bits_kernel<<<nb_, kThreads, 0, s_>>>(x, n, amax_);
+    first_index_kernel<<<nb_, kThreads, 0, s_>>>(x, n, amax_, amax_ + 1);
+    double nn[2];
+    AJD_TRY(sync_read(dots_, 2, nn));
+    unsigned long long key = 0;
+    AJD_CUDA(cudaMemcpy(&key, amax_ + 1, sizeof(key), cudaMemcpyDeviceToHost));
+    const int64_t imax = (int64_t)key;
+    double xv = 0.0;
+    AJD_CUDA(cudaMemcpy(&xv, x + imax, sizeof(double), cudaMemcpyDeviceToHost));
+    const double nrm = std::sqrt(nn[0]);
+    max_res = std::max(max_res, std::sqrt(std::max(nn[1], 0.0)) / nrm / normA_);
+    signs[j] = (xv < 0 ? -1.0 : 1.0) / nrm;
+  }
+  // output (already ordered by |theta - sigma| by the eigen kernel)
+  AJD_CUDA(cudaMemcpyAsync(evals, theta_, sizeof(double) * kc, cudaMemcpyDefault, s_));
+  double orth = 0.0;
+  for (int j = 0; j < kc; ++j) {
+    double* x = Vt_ + (int64_t)j * ld_;
+    AJD_CUDA(cudaMemcpyAsync(scal_ + 8, &signs[j], sizeof(double), cudaMemcpyHostToDevice, s_));
+    scale_copy_kernel<<<nb_, kThreads, 0, s_>>>(x, x, n, scal_, 8, 0);
+    AJD_CUDA(cudaStreamSynchronize(s_));
+  }
+  for (int j = 0; j < kc; ++j) {
+    AJD_TRY(dot_cols(Cols<double>{Vt_, ld_, kc}, Cols<double>{}, nullptr, Vt_ + (int64_t)j * ld_, dots_));
+    double g[kMaxM];
+    AJD_TRY(sync_read(dots_, kc, g));
+    for (int i = 0; i < kc; ++i) orth = std::max(orth, std::fabs(g[i] - (i == j ? 1.0 : 0.0)));
+  }
+  if (evecs) {
+    for (int j = 0; j < kc; ++j)
+      AJD_CUDA(cudaMemcpyAsync(evecs + (int64_t)j * n, Vt_ + (int64_t)j * ld_, sizeof(double) * n, cudaMemcpyDefault, s_));
+  }
+  AJD_CUDA(cudaStreamSynchronize(s_));
+  if (st) {
+    st->max_residual = max_res;
+    st->orth_error = orth;
+  }
+  return JD_OK;
+}
+
+}  // namespace ajd
+
+using namespace ajd;
+
+extern "C" int jd_params_default(jd_params* p) {
+  if (!p) return fail(JD_EINVAL, "jd_params_default: NULL");
+  std::memset(p, 0, sizeof(*p));
+  p->max_outer = 3000;
+  p->max_inner = 60;
+  p->inner_decay = 0.7;
+  p->inner_floor = 1e-7;
+  p->switch_tol = 1e-3;
+  p->precision = JD_FP64;
+  ildl_params_default(&p->ildl);
+  return JD_OK;
+}
+
+extern "C" int jd_solve(anderson_t h, double sigma, int k, double tol, const jd_params* p, double* evals,
+                        double* evecs, jd_stats* st, void* stream) {
+  if (!h || !evals) return fail(JD_EINVAL, "jd_solve: NULL handle or evals");
+  if (!std::isfinite(sigma)) return fail(JD_EINVAL, "jd_solve: sigma must be finite");
+  if (k < 1 || k > 64 || (int64_t)k >= h->n) return fail(JD_EINVAL, "jd_solve: need 1 <= k <= 64 and k < n");
+  if (!(tol > 0.0)) return fail(JD_EINVAL, "jd_solve: tol must be > 0");
+  jd_params prm;
+  jd_params_default(&prm);
+  if (p) {
+    prm = *p;
+    jd_params d;
+    jd_params_default(&d);
+    if (prm.max_outer <= 0) prm.max_outer = d.max_outer;
+    if (prm.max_inner <= 0) prm.max_inner = d.max_inner;
+    if (!(prm.inner_decay > 0.0 && prm.inner_decay < 1.0)) prm.inner_decay = d.inner_decay;
+    if (!(prm.inner_floor > 0.0)) prm.inner_floor = d.inner_floor;
+    if (!(prm.switch_tol > 0.0)) prm.switch_tol = d.switch_tol;
+    if (prm.ildl.kappa == 0.0 && prm.ildl.max_levels == 0 && prm.ildl.n_dense == 0) prm.ildl = d.ildl;
+  }
+  if (prm.precision != JD_FP64 && prm.precision != JD_FP32) return fail(JD_EINVAL, "jd_solve: unknown precision");
+  if (st) std::memset(st, 0, sizeof(*st));
+  using Clock = std::chrono::steady_clock;
+  const auto t0 = Clock::now();
+  ildl_t pc = prm.precond;
+  bool own = false;
+  if (!pc) {
+    AJD_TRY(ildl_create(h, sigma, &prm.ildl, &pc));
+    own = true;
+  }
+  if (st) {
+    st->setup_ms = std::chrono::duration<double, std::milli>(Clock::now() - t0).count();
+    ildl_info(pc, &st->ildl);
+  }
+  int rc;
+  {
+    JdSolver solver(h, pc, prm, sigma, k, tol, reinterpret_cast<cudaStream_t>(stream));
+    rc = solver.run(evals, evecs, st);
+  }
+  if (own) ildl_destroy(pc);
+  return rc;
+}

@@ -1,0 +1,139 @@
+"""GPU parity of the preconditioner apply and of the Jacobi–Davidson
+eigenpairs against the CPU oracle."""
+import numpy as np
+import pytest
+
+from oracle import eig, lanczos, lattice, matching, rng
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def ajd():
+    import paper_math_0508111_gb300 as ajd
+    assert torch.cuda.is_available()
+    return ajd
+
+
+@pytest.mark.parametrize("L,bc,sigma,nd", [(10, 0, 0.0, 1000), (20, 0, 0.3, 1000), (33, 1, -0.5, 300), (16, 0, 1.0, 50)])
+def test_ildl_apply_matches_oracle(ajd, L, bc, sigma, nd):
+    """x = K^{-1} b on the GPU equals the plain definition applied by the
+    oracle to the same factor (binary64 and binary32)."""
+    with ajd.Anderson(L, 16.5, 1, bc) as h:
+        P = ajd.Preconditioner.from_lattice(h, sigma, n_dense=nd)
+        F = P.export()
+        b = np.random.default_rng(0).standard_normal(h.n)
+        want = matching.apply_factor(F, b)
+        scale = np.abs(want).max()
+        x64 = P.apply(torch.tensor(b, device="cuda")).cpu().numpy()
+        assert np.abs(x64 - want).max() <= 1e-12 * scale
+        x32 = P.apply(torch.tensor(b, device="cuda", dtype=torch.float32)).double().cpu().numpy()
+        assert np.abs(x32 - want).max() <= 2e-5 * scale
+        P.close()
+
+
+def _check_pairs(L, W, seed, bc, sigma, k, ev, X, st, tol, oracle="dense"):
+    eps = rng.potential(L, W, seed)
+    A = lattice.assemble(L, eps, bc)
+    nA = lattice.norm_bound(eps)
+    if oracle == "dense":
+        w_all, V_all = np.linalg.eigh(A.toarray())
+        o = eig.order_nearest(w_all, sigma)
+        wl, Vl = w_all[o[:k]], eig.normalize_sign(V_all[:, o[:k]])
+        dist = np.sort(np.abs(w_all - sigma))
+    else:
+        wl, Vl, _ = lanczos.shift_invert_nearest(A, sigma, k + 1, norm_a=nA)
+        dist = np.sort(np.abs(wl - sigma))
+        wl, Vl = wl[:k], Vl[:, :k]
+    assert st["nconv"] == k and st["status"] == 0
+    # eigenvalues: |dlambda| <= 1e-10 ||A||
+    assert np.abs(ev - wl).max() <= 1e-10 * nA, (ev, wl)
+    # residuals measured by the oracle's matrix
+    res = np.linalg.norm(A @ X - X * ev, axis=0) / nA
+    assert res.max() <= 2 * tol
+    assert st["max_residual"] <= 2 * tol
+    # orthonormality
+    assert np.abs(X.T @ X - np.eye(k)).max() <= 1e-12
+    # eigenvectors: angle to the oracle's, bounded by max(1e-6, 2 ||r|| / gap)
+    full = np.sort(np.abs(np.concatenate([dist])))
+    for j in range(k):
+        gaps = np.abs(wl - wl[j])
+        gaps[j] = np.inf
+        gap = min(gaps.min(), abs(dist[k] - dist[k - 1]) if len(dist) > k else np.inf)
+        cosang = min(1.0, abs(X[:, j] @ Vl[:, j]))
+        sinang = np.sqrt(max(0.0, 1 - cosang * cosang))
+        assert sinang <= max(1e-6, 2 * res[j] * nA / gap), (j, sinang)
+    # sign convention
+    for j in range(k):
+        i = int(np.argmax(np.abs(X[:, j])))
+        assert X[i, j] > 0
+    assert np.all(np.diff(np.abs(ev - sigma)) >= 0)
+    return full
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_jd_tiny_config(ajd, precision):
+    """L = 10, W = 16.5, periodic, 5 eigenpairs nearest 0."""
+    L, W, seed, sigma, k, tol = 10, 16.5, 1, 0.0, 5, 1e-12
+    with ajd.Anderson(L, W, seed) as h:
+        ev, X, st = ajd.solve(h, sigma, k, tol, precision=precision)
+    _check_pairs(L, W, seed, 0, sigma, k, ev, X, st, tol)
+
+
+@pytest.mark.parametrize("L,W,seed,bc,sigma,k,prec", [
+    (8, 16.5, 2, 1, 0.5, 3, 0),
+    (12, 12.0, 3, 0, -1.0, 10, 1),
+    (9, 21.0, 4, 0, 0.0, 1, 0),
+    (11, 16.5, 5, 1, 2.0, 6, 1),
+    (6, 8.0, 6, 0, 0.25, 4, 0),
+])
+def test_jd_dense_oracle_cases(ajd, L, W, seed, bc, sigma, k, prec):
+    tol = 1e-12
+    with ajd.Anderson(L, W, seed, bc) as h:
+        ev, X, st = ajd.solve(h, sigma, k, tol, precision=prec)
+    _check_pairs(L, W, seed, bc, sigma, k, ev, X, st, tol)
+
+
+@pytest.mark.parametrize("L,sigma,prec", [(20, 0.0, 1), (24, 1.0, 0), (27, -0.5, 1)])
+def test_jd_shift_invert_oracle(ajd, L, sigma, prec):
+    """Mid sizes against the shift-and-invert Lanczos oracle."""
+    W, seed, k, tol = 16.5, 1, 5, 1e-11
+    with ajd.Anderson(L, W, seed) as h:
+        ev, X, st = ajd.solve(h, sigma, k, tol, precision=prec)
+    _check_pairs(L, W, seed, 0, sigma, k, ev, X, st, tol, oracle="lanczos")
+
+
+def test_jd_degenerate_zero_disorder(ajd):
+    """W = 0: eigenvalues of the closed form, degenerate clusters; compare
+    eigenvalues and check the returned vectors are eigenvectors."""
+    L, k = 4, 4
+    with ajd.Anderson(L, 0.0, 1) as h:
+        ev, X, st = ajd.solve(h, 1.0, k, 1e-11)
+    A = lattice.assemble(L, np.zeros(L ** 3))
+    spec = lattice.closed_form_spectrum(L)
+    o = eig.order_nearest(spec, 1.0)
+    # the cluster at distance 1 (lambda = 0 and 2) straddles k: compare distances
+    assert np.allclose(np.abs(ev - 1.0), np.abs(spec[o[:k]] - 1.0), atol=1e-10)
+    assert np.linalg.norm(A @ X - X * ev, axis=0).max() <= 1e-10 * 6
+
+
+def test_jd_small_lattice_and_errors(ajd):
+    with ajd.Anderson(3, 16.5, 1) as h:
+        ev, X, st = ajd.solve(h, 0.0, 2, 1e-12)
+        _check_pairs(3, 16.5, 1, 0, 0.0, 2, ev, X, st, 1e-12)
+        with pytest.raises(ajd.JDError):
+            ajd.solve(h, 0.0, 27, 1e-8)
+        with pytest.raises(ajd.JDError):
+            ajd.solve(h, 0.0, 2, 0.0)
+        with pytest.raises(ajd.JDError):
+            ajd.solve(h, float("nan"), 2, 1e-8)
+
+
+def test_jd_noconv_reports_prefix(ajd):
+    """A too-small outer budget returns JD_ENOCONV with the converged prefix."""
+    with ajd.Anderson(12, 16.5, 1) as h:
+        ev, X, st = ajd.solve(h, 0.0, 5, 1e-12, max_outer=12, raise_on_noconv=False)
+    assert st["status"] == ajd.JD_ENOCONV
+    assert 0 <= st["nconv"] < 5
