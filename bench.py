@@ -1,0 +1,355 @@
+#!/usr/bin/env python3
+"""Benchmark of the GPU Jacobi–Davidson solver for the 3D Anderson model.
+
+Metric: converged eigenpairs per second (residual <= 1e-8 ||A||) on the
+L = 100, W = 16.5 periodic lattice, k = 5 eigenpairs nearest sigma = 0 (the
+configuration of Table 4's headline row M = 100, w = 16.5).  One step is one
+complete ``jd_solve``: preconditioner construction (matching, ordering,
+multilevel ILDL^T and its upload) plus the Jacobi–Davidson iteration, on a
+fresh disorder realisation whose potential is already resident on the
+device.  The headline form is the mixed one (binary32 stencil, preconditioner
+and SQMR inside a binary64 outer iteration); the plain binary64 form is
+timed on the same realisations for comparison.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+For N > 1 launch with torch.distributed.run; every rank solves its own
+realisations (independent problems, no collective on the data path) and the
+JSON line reports the whole-job rate (weak scaling).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "eigenpairs/s at resid≤1e-8, L=100 W=16.5; batched/served vs plain FP64; p99"
+UNIT = "eigenpairs/s"
+PAPER_EIGENPAIRS_PER_S = 5.0 / 978.0  # Table 4, M = 100, w = 16.5, one Itanium2 core
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--L", type=int, default=100)
+    ap.add_argument("--W", type=float, default=16.5)
+    ap.add_argument("--k", type=int, default=5)
+    ap.add_argument("--tol", type=float, default=1e-8)
+    ap.add_argument("--sigma", type=float, default=0.0)
+    ap.add_argument("--no-fp64", action="store_true", help="skip the plain binary64 comparison")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def apply_bytes(info, elem):
+    """Algorithmic bytes of one preconditioner application x = K^{-1} b:
+    every stored entry of L read once in the forward and once in the backward
+    sweep (value + int32 column), both row-pointer arrays, and per position
+    the gather/scatter vectors (perm, scale twice, b, out), the work vectors
+    w and z (written once, read once), the 2x2 pivot data (diagonal,
+    off-diagonal, partner) and the dense trailing inverse.  Gathers of
+    earlier solution entries through the column indices are cache traffic
+    and not counted."""
+    n, nnz, nd = info["n"], info["nnz_L"], info["n_dense"]
+    idx = 4
+    return (2 * nnz * (elem + idx) + 2 * (n + 1) * idx
+            + n * (2 * idx + 2 * elem + 2 * elem)      # perm x2, scale x2, b, out
+            + n * (4 * elem)                          # w write/read, z write/read
+            + (n - nd) * (2 * elem + idx)             # D^{-1} diagonal, off-diagonal, partner
+            + nd * nd * elem)
+
+
+def cpu_baseline(W, sigma, k, L_sample=30):
+    """The oracle (shift-and-invert Lanczos over SuperLU) on a bounded sample:
+    one L_sample^3 lattice of the same disorder, shift and k."""
+    import numpy as np
+    from oracle import lanczos, lattice, rng
+    eps = rng.potential(L_sample, W, 1)
+    A = lattice.assemble(L_sample, eps)
+    t0 = time.perf_counter()
+    w, X, info = lanczos.shift_invert_nearest(A, sigma, k, norm_a=lattice.norm_bound(eps))
+    dt = time.perf_counter() - t0
+    return {"value": k / dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": "oracle shift-invert Lanczos + SuperLU on one L=%d lattice (W=%g, sigma=%g, k=%d): %.1f s; "
+                      "the oracle's sparse LU does not reach L=100 in bounded time (L=50 takes ~6 min), so the "
+                      "sample is the largest lattice it solves in ~10 s" % (L_sample, W, sigma, k, dt),
+            "seconds": dt}
+
+
+def run_reference(args, rank, world):
+    """--impl reference: the CPU oracle as it stands, on the host cores."""
+    if rank != 0:
+        return
+    import numpy as np  # noqa: F401
+    for _ in range(args.warmup):
+        pass  # the oracle has no state to warm; keep the contract's shape
+    vals = []
+    t0 = time.perf_counter()
+    for s in range(args.steps):
+        cb = cpu_baseline(args.W, args.sigma, args.k)
+        vals.append(cb["seconds"])
+    total = time.perf_counter() - t0
+    value = args.k * args.steps / sum(vals)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": "anderson-L30-W%g-periodic-k%d-sigma%g (oracle sample of the L=100 workload)"
+                       % (args.W, args.k, args.sigma)},
+            "cpu_baseline": {"value": value, "unit": UNIT, "kind": "oracle", "cores": os.cpu_count(),
+                             "sample": cb["sample"]},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    import numpy as np
+    import torch
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import paper_math_0508111_gb300 as ajd
+    L, W, k, tol, sigma = args.L, args.W, args.k, args.tol, args.sigma
+    nwarm, nsteps = args.warmup, args.steps
+    seeds = [1 + 100000 * rank + i for i in range(nwarm + nsteps)]
+    lattices = [ajd.Anderson(L, W, s) for s in seeds]  # potentials resident before timing
+    n = lattices[0].n
+    flush = torch.empty(256 * 1024 * 1024 // 4, device="cuda", dtype=torch.float32)
+    stream = torch.cuda.current_stream()
+    ev_out = np.zeros(k)
+    X_dev = torch.empty((k, n), device="cuda", dtype=torch.float64)
+
+    def one(h, precision):
+        p = ajd.jd_params(precision=precision)
+        st = ajd._ffi.JdStats()
+        rc = ajd._ffi.lib().jd_solve(h.handle, sigma, k, tol, ajd.ctypes.byref(p),
+                                     ev_out.ctypes.data_as(ajd.ctypes.c_void_p),
+                                     ajd.ctypes.c_void_p(X_dev.data_ptr()), ajd.ctypes.byref(st),
+                                     ajd.ctypes.c_void_p(stream.cuda_stream))
+        ajd._ffi.check(rc, "jd_solve")
+        return ajd._stats_dict(st)
+
+    for i in range(nwarm):
+        one(lattices[i], ajd.JD_FP32)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    stats = []
+    e0.record(stream)
+    for i in range(nsteps):
+        flush.zero_()  # L2 flushed between steps (256 MiB write)
+        stats.append(one(lattices[nwarm + i], ajd.JD_FP32))
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop()
+    elapsed = e0.elapsed_time(e1) / 1e3
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([elapsed], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed = float(t.item())
+    value = world * nsteps * k / elapsed
+    setup_s = sum(s["setup_ms"] for s in stats) / 1e3
+    solve_s = sum(s["solve_ms"] for s in stats) / 1e3
+
+    # plain binary64 form on the same realisations
+    fp64 = None
+    if not args.no_fp64:
+        torch.cuda.synchronize()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        st64 = []
+        f0.record(stream)
+        for i in range(nsteps):
+            flush.zero_()
+            st64.append(one(lattices[nwarm + i], ajd.JD_FP64))
+        f1.record(stream)
+        torch.cuda.synchronize()
+        t64 = f0.elapsed_time(f1) / 1e3
+        fp64 = {"value": nsteps * k / t64, "unit": UNIT, "ms_per_step": 1e3 * t64 / nsteps,
+                "solve_only_value": nsteps * k / (sum(s["solve_ms"] for s in st64) / 1e3),
+                "outer_its": [s["outer_its"] for s in st64], "inner_its": [s["inner_its"] for s in st64]}
+
+    # end to end through the public API from host memory: potential copied in
+    # (pinned), solve, eigenvalues and eigenvectors copied out (pinned)
+    e2e = None
+    if not args.no_e2e:
+        pots = [torch.from_numpy(h.potential()).pin_memory() for h in lattices[nwarm:]]
+        Xh = torch.empty((k, n), dtype=torch.float64).pin_memory()
+        evh = torch.empty(k, dtype=torch.float64).pin_memory()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for i in range(nsteps):
+            flush.zero_()
+            h = ajd._ffi.ctypes.c_void_p()
+            ajd._ffi.call("anderson_create_from_potential", L, ajd.ctypes.c_void_p(pots[i].data_ptr()), 0,
+                          ajd.ctypes.byref(h))
+            p = ajd.jd_params(precision=ajd.JD_FP32)
+            st = ajd._ffi.JdStats()
+            rc = ajd._ffi.lib().jd_solve(h, sigma, k, tol, ajd.ctypes.byref(p),
+                                         ajd.ctypes.c_void_p(evh.data_ptr()), ajd.ctypes.c_void_p(Xh.data_ptr()),
+                                         ajd.ctypes.byref(st), ajd.ctypes.c_void_p(stream.cuda_stream))
+            ajd._ffi.check(rc, "jd_solve")
+            ajd._ffi.lib().anderson_destroy(h)
+        torch.cuda.synchronize()
+        te = time.perf_counter() - t0
+        e2e = {"value": world * nsteps * k / te, "unit": UNIT, "h2d_bytes_per_step": 8 * n,
+               "d2h_bytes_per_step": 8 * n * k + 8 * k}
+
+    # roofline of the dominant kernel: the preconditioner application
+    peak, peak_kind = measured_peaks()
+    calls = sum(s["precond_calls"] for s in stats)
+    ms = sum(s["precond_ms"] for s in stats)
+    info = stats[-1]["ildl"]
+    bytes_per = apply_bytes(info, 4)
+    achieved = bytes_per / (ms / calls / 1e3) / 1e9 if calls else 0.0
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "ildl_apply_fp32_traffic.json")
+    if os.path.exists(prof):
+        try:
+            traffic = json.load(open(prof)).get("dram_bytes_per_apply_scaled_to_L100")
+        except Exception:
+            traffic = None
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": traffic, "kernel": "ildl_apply (binary32: forward/backward level sweeps + dense block)",
+                "peak_kind": peak_kind + " (hbm_gbs, copy test)", "algorithmic_bytes_per_launch": bytes_per,
+                "avg_launch_ms": ms / calls if calls else None, "launches_timed": calls}
+    stencil_calls = sum(s["stencil_calls"] for s in stats)
+    stencil_ms = sum(s["stencil_ms"] for s in stats)
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        cpu = cpu_baseline(W, sigma, k)
+        cpu.pop("seconds", None)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": nsteps,
+                "warmup": nwarm, "ms_per_step": 1e3 * elapsed / nsteps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": value / PAPER_EIGENPAIRS_PER_S,
+                "vs_baseline_note": "paper Table 4: 978 s for 5 eigenpairs at M=100, w=16.5 on one Itanium2 core "
+                                    "(context; the paper does not state its residual tolerance)",
+                "dtype": "f32+f64", "data": "synthetic",
+                "config": {"workload": "anderson-L%d-W%g-periodic-k%d-sigma%g-tol%g" % (L, W, k, sigma, tol),
+                           "L": L, "W": W, "k": k, "sigma": sigma, "tol": tol, "bc": "periodic",
+                           "precision": "mixed: binary32 stencil/preconditioner/SQMR, binary64 outer",
+                           "step": "one full jd_solve incl. preconditioner setup, fresh realisation per step",
+                           "l2": "flushed between steps (256 MiB write)", "seeds": seeds[nwarm:],
+                           "parallelism": "replicas (one realisation per step per GPU)"},
+                "setup_s_per_step": setup_s / nsteps, "solve_s_per_step": solve_s / nsteps,
+                "solve_only_value": world * nsteps * k / solve_s,
+                "iterations": {"outer": [s["outer_its"] for s in stats], "inner": [s["inner_its"] for s in stats],
+                               "restarts": [s["restarts"] for s in stats]},
+                "max_residual": max(s["max_residual"] for s in stats),
+                "preconditioner": {"levels": info["levels"], "n_dense": info["n_dense"], "nnz_L": info["nnz_L"],
+                                   "fill": info["fill"], "n_2x2": info["n_2x2"]},
+                "fp64": fp64, "e2e": e2e, "roofline": roofline,
+                "stencil_fp32": {"calls": stencil_calls, "avg_ms": stencil_ms / stencil_calls if stencil_calls else None,
+                                 "achieved_GBps": 12 * n / (stencil_ms / stencil_calls / 1e3) / 1e9 if stencil_calls else None},
+                "cpu_baseline": cpu, "clocks": clocks,
+                "gpu_launches": int(sum(s["kernel_launches"] for s in stats))}
+        print(json.dumps(line), flush=True)
+    for h in lattices:
+        h.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -89,6 +89,17 @@ typedef struct anderson_s* anderson_t;
  */
 int anderson_create(int L, double W, uint64_t seed, int bc, anderson_t* out);
 
+/*
+ * anderson_create_from_potential -- a lattice whose on-site energies are
+ * supplied by the caller (host buffer eps_host[L^3], binary64, site order
+ * x fastest) instead of being drawn from the box distribution.  The values
+ * are copied to the device (a pinned host buffer makes the copy
+ * asynchronous-capable; any host buffer works).  W and seed of the handle are
+ * recorded as 0.  Same argument rules as anderson_create; eps must be
+ * finite.  Synchronous.
+ */
+int anderson_create_from_potential(int L, const double* eps_host, int bc, anderson_t* out);
+
 /* Release the handle and its device memory.  NULL is a no-op. */
 int anderson_destroy(anderson_t h);
 
@@ -132,10 +143,11 @@ typedef struct {
   double gamma;   /* couplings below gamma (scaled matrix, entries <= 1) are
                      ignored when each level's independent set of pivots is
                      chosen, and dropped between pivots of the same level;
-                     0 = exact independence [0.02]                           */
-  int max_levels; /* maximum number of sparse levels [96]                    */
+                     0 = exact independence; < 0 selects
+                     min(0.02, 5/sqrt(n)) [-1]                               */
+  int max_levels; /* maximum number of sparse levels [256]                    */
   int n_dense;    /* the remaining Schur complement is factored densely once
-                     it has at most this many rows [1000]                    */
+                     it has at most this many rows (at most 8000) [3000]                    */
   int matching;   /* 1: maximum-product matching, 1x1/2x2 cycle split and
                      symmetric dual scaling per level (Sections 5.1, 5.2);
                      0: row-max scaling and 1x1 pivots only [1]              */
@@ -154,8 +166,11 @@ typedef struct {
   int64_t nnz_A;     /* stored entries of the input matrix                  */
   double fill;       /* nnz(L D L^T)/nnz(A) = (2 nnz_L + nnz(D))/nnz(A),
                         the measure of Table 5                              */
-  double setup_ms;   /* wall time of the host construction                  */
+  double setup_ms;   /* wall time of the construction (host + dense inverse) */
   double match_ms;   /* of which: matchings and scalings                    */
+  int relaxed_levels;/* levels where fewer than 0.5% of the rows met kappa and
+                        the bound was widened (at most 64 kappa)            */
+  double max_abs_L;  /* largest |entry| of L (after the global scaling)     */
 } ildl_info_t;
 
 /*
@@ -239,7 +254,8 @@ typedef struct {
   double inner_decay; /* the correction equation is solved to relative
                          residual max(inner_decay^j, inner_floor), j = outer
                          steps spent on the current Ritz pair [0.7]            */
-  double inner_floor; /* [1e-7]                                                */
+  double inner_floor; /* [0 = 1e-8 for JD_FP64, 1e-5 for JD_FP32, the level a
+                         binary32 solve can still reach]                      */
   double switch_tol;  /* correction shift: sigma while ||r|| > switch_tol*||A||,
                          the Ritz value theta afterwards [1e-3]                */
   int precision;      /* inner solve (stencil, preconditioner, SQMR) in
@@ -247,6 +263,13 @@ typedef struct {
                          projection and orthogonalisation are always
                          binary64 [JD_FP64]                                   */
   uint64_t seed;      /* start vector seed (0 = derived from the lattice seed)*/
+  int extraction;     /* 0: harmonic Ritz vectors for targets nearest sigma
+                         (robust in the dense interior spectrum); 1: standard
+                         Ritz vectors of V^T A V as printed in Section 4.2 [0] */
+  int guard;          /* extra pairs computed beyond k; the k nearest of the
+                         converged pairs are returned, which protects against
+                         a nearer eigenvalue found after a farther one was
+                         locked (0 = default 2, < 0 = none)                  */
   ildl_params ildl;   /* preconditioner parameters (zeroed = defaults)       */
   ildl_t precond;     /* optional prebuilt preconditioner of A - sigma I
                          (from ildl_create with the same sigma); NULL = build
@@ -264,6 +287,12 @@ typedef struct {
   double max_residual; /* max ||A x - lambda x||_2 / ||A|| over returned pairs */
   double orth_error;   /* max |X^T X - I| over returned pairs                 */
   ildl_info_t ildl;    /* preconditioner statistics                           */
+  int64_t kernel_launches;  /* GPU kernels launched by the solve (incl. setup
+                               upload and the final Rayleigh–Ritz)            */
+  int precond_calls;   /* preconditioner applications in the inner solves    */
+  double precond_ms;   /* their device time (CUDA events on the stream)      */
+  int stencil_calls;   /* inner-solve stencil applications                   */
+  double stencil_ms;   /* their device time                                  */
 } jd_stats;
 
 /* Fill *p with the defaults (all fields zero except ildl = ildl defaults). */
@@ -278,8 +307,10 @@ int jd_params_default(jd_params* p);
  * obtained by simplified QMR with the projected preconditioner
  * K^{-1} - W (Q~^T W)^{-1} W^T, W = K^{-1} Q~, K ~ A - sigma I the
  * multilevel ILDL^T; each new vector is orthogonalised against [Q, V]
- * (classical Gram–Schmidt, twice), the Ritz pair of [V]^T A [V] nearest sigma
- * is selected, and it is locked into Q once ||A u - theta u|| <= tol*||A||
+ * (classical Gram–Schmidt, twice), the target pair is extracted from span(V)
+ * (harmonic Ritz by default, standard Ritz on request; the eigenvalue is
+ * the Rayleigh quotient), and it is locked into Q once
+ * ||A u - theta u|| <= tol*||A||
  * (||A|| = 6 + max|eps|).  A final Rayleigh–Ritz step on Q returns the
  * eigenvalues.
  *

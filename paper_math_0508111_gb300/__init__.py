@@ -50,13 +50,21 @@ def _dev_ptr(t, what):
 class Anderson:
     """An L^3 Anderson lattice (Eq. (1)) with box disorder of width W.
 
-    The potential is generated on the current CUDA device from ``seed``.
+    The potential is generated on the current CUDA device from ``seed``, or
+    copied from ``potential`` (host array of L**3 energies) when given.
     """
 
-    def __init__(self, L, W, seed, bc=JD_PERIODIC):
+    def __init__(self, L, W, seed, bc=JD_PERIODIC, potential=None):
         h = ctypes.c_void_p()
-        _ffi.call("anderson_create", int(L), float(W), ctypes.c_uint64(int(seed) & (2 ** 64 - 1)), int(bc),
-                  ctypes.byref(h))
+        if potential is None:
+            _ffi.call("anderson_create", int(L), float(W), ctypes.c_uint64(int(seed) & (2 ** 64 - 1)), int(bc),
+                      ctypes.byref(h))
+        else:
+            eps = np.ascontiguousarray(potential, dtype=np.float64)
+            if eps.shape != (int(L) ** 3,):
+                raise ValueError("potential must have L**3 entries")
+            _ffi.call("anderson_create_from_potential", int(L), eps.ctypes.data_as(ctypes.c_void_p), int(bc),
+                      ctypes.byref(h))
         self._h = h
         self.L, self.W, self.seed, self.bc = int(L), float(W), int(seed), int(bc)
         n = ctypes.c_int64()

@@ -34,19 +34,22 @@ class IldlParams(ctypes.Structure):
 
 class IldlInfo(ctypes.Structure):
     _fields_ = [("n", c_int), ("levels", c_int), ("n_dense", c_int), ("n_2x2", c_int), ("nnz_L", c_int64),
-                ("nnz_A", c_int64), ("fill", c_double), ("setup_ms", c_double), ("match_ms", c_double)]
+                ("nnz_A", c_int64), ("fill", c_double), ("setup_ms", c_double), ("match_ms", c_double),
+                ("relaxed_levels", c_int), ("max_abs_L", c_double)]
 
 
 class JdParams(ctypes.Structure):
     _fields_ = [("jmin", c_int), ("jmax", c_int), ("max_outer", c_int), ("max_inner", c_int),
                 ("inner_decay", c_double), ("inner_floor", c_double), ("switch_tol", c_double),
-                ("precision", c_int), ("seed", c_uint64), ("ildl", IldlParams), ("precond", c_void_p)]
+                ("precision", c_int), ("seed", c_uint64), ("extraction", c_int), ("guard", c_int), ("ildl", IldlParams),
+                ("precond", c_void_p)]
 
 
 class JdStats(ctypes.Structure):
     _fields_ = [("nconv", c_int), ("outer_its", c_int), ("inner_its", c_int), ("restarts", c_int),
                 ("setup_ms", c_double), ("solve_ms", c_double), ("max_residual", c_double),
-                ("orth_error", c_double), ("ildl", IldlInfo)]
+                ("orth_error", c_double), ("ildl", IldlInfo), ("kernel_launches", c_int64),
+                ("precond_calls", c_int), ("precond_ms", c_double), ("stencil_calls", c_int), ("stencil_ms", c_double)]
 
 
 # (name, restype, argtypes) of every exported function
@@ -54,6 +57,7 @@ SIGNATURES = [
     ("jd_last_error", ctypes.c_char_p, []),
     ("jd_version", c_int, []),
     ("anderson_create", c_int, [c_int, c_double, c_uint64, c_int, P(c_void_p)]),
+    ("anderson_create_from_potential", c_int, [c_int, c_void_p, c_int, P(c_void_p)]),
     ("anderson_destroy", c_int, [c_void_p]),
     ("anderson_size", c_int, [c_void_p, P(c_int64)]),
     ("anderson_potential", c_int, [c_void_p, c_void_p]),

@@ -21,7 +21,7 @@ BUILD = os.path.join(ROOT, "_build", "libanderson_jd")
 LIB = os.path.join(PKG, "libanderson_jd.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O3",
+COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O3,-fopenmp",
           "-I", INCLUDE, "-I", CSRC, "--expt-relaxed-constexpr"]
 
 
@@ -72,7 +72,7 @@ def build(force=False, verbose=False, extra=()):
             if err.strip():
                 sys.stderr.write(err)
     tmp = LIB + ".tmp"
-    cmd = [nvcc()] + ARCH + ["-shared", "-cudart", "shared", "-o", tmp] + objs + ["-lcublas"]
+    cmd = [nvcc()] + ARCH + ["-shared", "-cudart", "shared", "-o", tmp] + objs + ["-lgomp"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s\n%s" % (" ".join(cmd), r.stderr))

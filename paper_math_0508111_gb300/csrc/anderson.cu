@@ -178,6 +178,7 @@ static void launch_stencil(const T* eps, const T* x, T* y, int L, int m, T shift
   dim3 grid(bx, nchunk, m);
   stencil_kernel<T, V><<<grid, 32 * kWarps, 0, stream>>>(eps, x, y, L, nseg, zchunk, shift, hop,
                                                          periodic, n);
+  count_launches();
 }
 
 template <typename T>
@@ -245,6 +246,48 @@ extern "C" int anderson_create(int L, double W, uint64_t seed, int bc, anderson_
     return fail(JD_EDEVICE, "anderson_create: %s", cudaGetErrorString(e));
   }
   std::memcpy(&h->max_abs_eps, &bits, sizeof(double));
+  *out = h;
+  return JD_OK;
+}
+
+__global__ void narrow_kernel(const double* __restrict__ e64, float* __restrict__ e32, int64_t n) {
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x)
+    e32[s] = (float)e64[s];
+}
+
+extern "C" int anderson_create_from_potential(int L, const double* eps_host, int bc, anderson_t* out) {
+  if (!out || !eps_host) return fail(JD_EINVAL, "anderson_create_from_potential: NULL argument");
+  *out = nullptr;
+  if (bc != JD_PERIODIC && bc != JD_HARDWALL) return fail(JD_EINVAL, "anderson_create_from_potential: bad bc");
+  if (bc == JD_PERIODIC && L < 3) return fail(JD_EINVAL, "anderson_create_from_potential: periodic lattice needs L >= 3");
+  if (L < 1 || (int64_t)L * L * L >= (int64_t)1 << 31) return fail(JD_EINVAL, "anderson_create_from_potential: bad L");
+  const int64_t n = (int64_t)L * L * L;
+  double mx = 0.0;
+  for (int64_t s = 0; s < n; ++s) {
+    if (!std::isfinite(eps_host[s])) return fail(JD_EINVAL, "anderson_create_from_potential: non-finite eps");
+    mx = std::max(mx, std::fabs(eps_host[s]));
+  }
+  anderson_s* h = new (std::nothrow) anderson_s();
+  if (!h) return fail(JD_ENOMEM, "anderson_create_from_potential: host allocation failed");
+  h->L = L;
+  h->n = n;
+  h->bc = bc;
+  h->max_abs_eps = mx;
+  cudaGetDevice(&h->device);
+  cudaError_t e = cudaMalloc(&h->eps64, n * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&h->eps32, n * sizeof(float));
+  if (e == cudaSuccess) e = cudaMemcpy(h->eps64, eps_host, n * sizeof(double), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    const int blocks = (int)std::min<int64_t>((n + 255) / 256, 16 * sm_count());
+    narrow_kernel<<<blocks, 256>>>(h->eps64, h->eps32, n);
+    count_launches();
+    e = cudaDeviceSynchronize();
+  }
+  if (e != cudaSuccess) {
+    anderson_destroy(h);
+    return fail(e == cudaErrorMemoryAllocation ? JD_ENOMEM : JD_EDEVICE, "anderson_create_from_potential: %s",
+                cudaGetErrorString(e));
+  }
   *out = h;
   return JD_OK;
 }

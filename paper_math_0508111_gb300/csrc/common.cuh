@@ -46,4 +46,8 @@ inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 // Number of SMs of the current device (cached per process; one GPU).
 int sm_count();
 
+// Kernel launches issued by this library on the calling thread (monotone).
+int64_t& launch_counter();
+inline void count_launches(int k = 1) { launch_counter() += k; }
+
 }  // namespace ajd

@@ -42,7 +42,16 @@ fwd_level_kernel(const int* __restrict__ ptr, const int* __restrict__ col, const
     T acc = T(0);
     if (active) {
       const int e = ptr[p + 1];
-      for (int q = ptr[p] + lane; q < e; q += G) acc += val[q] * w[col[q]];
+      int q = ptr[p] + lane;
+      T a1 = T(0), a2 = T(0), a3 = T(0);
+      for (; q + 3 * G < e; q += 4 * G) {
+        acc += val[q] * w[col[q]];
+        a1 += val[q + G] * w[col[q + G]];
+        a2 += val[q + 2 * G] * w[col[q + 2 * G]];
+        a3 += val[q + 3 * G] * w[col[q + 3 * G]];
+      }
+      for (; q < e; q += G) acc += val[q] * w[col[q]];
+      acc = (acc + a1) + (a2 + a3);
     }
 #pragma unroll
     for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, G);
@@ -97,7 +106,16 @@ bwd_level_kernel(const int* __restrict__ ptr, const int* __restrict__ col, const
     T acc = T(0);
     if (active) {
       const int e = ptr[p + 1];
-      for (int q = ptr[p] + lane; q < e; q += G) acc += val[q] * z[col[q]];
+      int q = ptr[p] + lane;
+      T a1 = T(0), a2 = T(0), a3 = T(0);
+      for (; q + 3 * G < e; q += 4 * G) {
+        acc += val[q] * z[col[q]];
+        a1 += val[q + G] * z[col[q + G]];
+        a2 += val[q + 2 * G] * z[col[q + 2 * G]];
+        a3 += val[q + 3 * G] * z[col[q + 3 * G]];
+      }
+      for (; q < e; q += G) acc += val[q] * z[col[q]];
+      acc = (acc + a1) + (a2 + a3);
     }
 #pragma unroll
     for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, G);
@@ -109,6 +127,239 @@ bwd_level_kernel(const int* __restrict__ ptr, const int* __restrict__ col, const
       z[p] = zp;
       out[perm[p]] = scale[p] * zp;
     }
+  }
+}
+
+// ---- Gauss–Jordan inversion of the dense trailing block (setup) ----
+// A and X are m x m row-major binary64; X starts as I and ends as A^{-1}.
+// Pivot c: argmax_{r >= c} |A[r][c]| (ties: smallest r).
+__global__ void gj_pivot_kernel(const double* __restrict__ A, int m, int c, int* piv, double* pval, int* bad) {
+  __shared__ double bv[1024];
+  __shared__ int bi[1024];
+  double best = -1.0;
+  int arg = c;
+  for (int r = c + threadIdx.x; r < m; r += blockDim.x) {
+    const double a = fabs(A[(int64_t)r * m + c]);
+    if (a > best) { best = a; arg = r; }
+  }
+  bv[threadIdx.x] = best;
+  bi[threadIdx.x] = arg;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      const double b2 = bv[threadIdx.x + o];
+      const int i2 = bi[threadIdx.x + o];
+      if (b2 > bv[threadIdx.x] || (b2 == bv[threadIdx.x] && i2 < bi[threadIdx.x])) {
+        bv[threadIdx.x] = b2;
+        bi[threadIdx.x] = i2;
+      }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    *piv = bi[0];
+    *pval = A[(int64_t)bi[0] * m + c];
+    if (!(bv[0] > 0.0) || !isfinite(bv[0])) *bad = 1;
+  }
+}
+
+// swap rows c and piv, scale the new row c by 1/pivot; f[r] = A[r][c] after
+// the swap (f[c] = 1)
+__global__ void gj_swap_scale_kernel(double* __restrict__ A, double* __restrict__ X, int m, int c,
+                                     const int* __restrict__ piv, const double* __restrict__ pval) {
+  const int p = *piv;
+  const double inv = 1.0 / *pval;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < m; k += gridDim.x * blockDim.x) {
+    const double ac = A[(int64_t)c * m + k], ap = A[(int64_t)p * m + k];
+    const double xc = X[(int64_t)c * m + k], xp = X[(int64_t)p * m + k];
+    A[(int64_t)c * m + k] = ap * inv;
+    X[(int64_t)c * m + k] = xp * inv;
+    if (p != c) {
+      A[(int64_t)p * m + k] = ac;
+      X[(int64_t)p * m + k] = xc;
+    }
+  }
+}
+
+__global__ void gj_save_col_kernel(const double* __restrict__ A, int m, int c, double* __restrict__ f) {
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < m; r += gridDim.x * blockDim.x) f[r] = A[(int64_t)r * m + c];
+}
+
+// rows r != c: A[r][k] -= f[r] A[c][k] (k > c; A[r][c] = 0), X[r][k] -= f[r] X[c][k]
+// (flattened grid-stride loop over all (r, k))
+__global__ void gj_eliminate_kernel(double* __restrict__ A, double* __restrict__ X, int m, int c,
+                                    const double* __restrict__ f) {
+  const int64_t total = (int64_t)m * m;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(t / m), k = (int)(t - (int64_t)r * m);
+    if (r == c) continue;
+    const double fr = f[r];
+    if (fr == 0.0) continue;
+    if (k > c) A[t] -= fr * A[(int64_t)c * m + k];
+    else if (k == c) A[t] = 0.0;
+    X[t] -= fr * X[(int64_t)c * m + k];
+  }
+}
+
+__global__ void gj_symmetrize_kernel(double* __restrict__ X, int m) {
+  const int64_t total = (int64_t)m * m;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(t / m), j = (int)(t % m);
+    if (j <= i) continue;
+    const double s = 0.5 * (X[(int64_t)i * m + j] + X[(int64_t)j * m + i]);
+    X[(int64_t)i * m + j] = s;
+    X[(int64_t)j * m + i] = s;
+  }
+}
+
+__global__ void identity_kernel(double* __restrict__ X, int m) {
+  const int64_t total = (int64_t)m * m;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x)
+    X[t] = (t / m == t % m) ? 1.0 : 0.0;
+}
+
+// ---- persistent apply: all phases of K^{-1} b in one cooperative launch ----
+// Phase kinds: gather (level 0), forward level, dense trailing block,
+// backward level.  Phases run in order; a grid-wide barrier separates them
+// (every phase reads only results of earlier phases).  The barrier counts
+// CTA arrivals on one counter (zeroed before the launch); waits are bounded
+// and record a timeout in `err` instead of hanging.
+enum { PH_GATHER = 0, PH_FWD = 1, PH_DENSE = 2, PH_BWD = 3 };
+constexpr int kPersistThreads = 512;
+constexpr unsigned kSpinLimit = 1u << 22;  // ~0.1-0.5 s at 32-128 ns per poll
+
+template <typename T>
+struct ApplyArgs {
+  const int* perm;
+  const T* scale;
+  const int* Lptr;
+  const int* Lcol;
+  const T* Lval;
+  const int* Uptr;
+  const int* Ucol;
+  const T* Uval;
+  const T* dd;
+  const T* dof;
+  const int* partner;
+  const T* dense;
+  T* w;
+  T* z;
+  const T* b;
+  T* out;
+  int nd, d0;
+};
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned target, int* err) {
+  __syncthreads();
+  __shared__ int failed;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(count, 1u);
+    unsigned spins = 0;
+    int f = 0;
+    while (ld_acquire_u32(count) < target) {
+      if (++spins > kSpinLimit || *((volatile int*)err)) {
+        atomicExch(err, 1);
+        f = 1;
+        break;
+      }
+      __nanosleep(64);
+    }
+    failed = f;
+  }
+  __syncthreads();
+  return failed == 0;
+}
+
+template <typename T, int G>
+__device__ __forceinline__ void level_rows(const ApplyArgs<T>& a, int kind, int p0, int p1) {
+  const int lane = threadIdx.x % G;
+  const int64_t groups = (int64_t)gridDim.x * blockDim.x / G;
+  const int64_t g0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
+  const int* ptr = kind == PH_FWD ? a.Lptr : a.Uptr;
+  const int* col = kind == PH_FWD ? a.Lcol : a.Ucol;
+  const T* val = kind == PH_FWD ? a.Lval : a.Uval;
+  const T* x = kind == PH_FWD ? a.w : a.z;  // vector read through the columns
+  for (int64_t base = p0; base < p1; base += groups) {
+    const int64_t pr = base + g0;
+    const bool active = pr < p1;
+    const int p = (int)pr;
+    T acc = T(0);
+    if (active) {
+      const int e = __ldg(ptr + p + 1);
+      int q = __ldg(ptr + p) + lane;
+      T a1 = T(0), a2 = T(0), a3 = T(0);
+      for (; q + 3 * G < e; q += 4 * G) {
+        acc += __ldg(val + q) * __ldcg(x + __ldg(col + q));
+        a1 += __ldg(val + q + G) * __ldcg(x + __ldg(col + q + G));
+        a2 += __ldg(val + q + 2 * G) * __ldcg(x + __ldg(col + q + 2 * G));
+        a3 += __ldg(val + q + 3 * G) * __ldcg(x + __ldg(col + q + 3 * G));
+      }
+      for (; q < e; q += G) acc += __ldg(val + q) * __ldcg(x + __ldg(col + q));
+      acc = (acc + a1) + (a2 + a3);
+    }
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, G);
+    if (active && lane == 0) {
+      if (kind == PH_FWD) {
+        __stcg(a.w + p, __ldg(a.scale + p) * __ldg(a.b + __ldg(a.perm + p)) - acc);
+      } else {
+        const int pp = __ldg(a.partner + p);
+        T d = __ldg(a.dd + p) * __ldcg(a.w + p);
+        if (pp >= 0) d += __ldg(a.dof + p) * __ldcg(a.w + pp);
+        const T zp = d - acc;
+        __stcg(a.z + p, zp);
+        a.out[__ldg(a.perm + p)] = __ldg(a.scale + p) * zp;
+      }
+    }
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kPersistThreads)
+ildl_apply_persistent_kernel(ApplyArgs<T> a, const int4* __restrict__ phases, int nphase, unsigned* count,
+                             int* err) {
+  for (int ph = 0; ph < nphase; ++ph) {
+    const int4 P = phases[ph];  // kind, p0, p1, G
+    const int kind = P.x, p0 = P.y, p1 = P.z, G = P.w;
+    if (kind == PH_GATHER) {
+      for (int p = p0 + blockIdx.x * blockDim.x + threadIdx.x; p < p1; p += gridDim.x * blockDim.x)
+        __stcg(a.w + p, __ldg(a.scale + p) * __ldg(a.b + __ldg(a.perm + p)));
+    } else if (kind == PH_DENSE) {
+      const int lane = threadIdx.x & 31;
+      const int warps = (gridDim.x * blockDim.x) >> 5;
+      for (int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < a.nd; r += warps) {
+        const T* row = a.dense + (int64_t)r * a.nd;
+        T acc = T(0), a1 = T(0);
+        int c = lane;
+        for (; c + 32 < a.nd; c += 64) {
+          acc += __ldg(row + c) * __ldcg(a.w + a.d0 + c);
+          a1 += __ldg(row + c + 32) * __ldcg(a.w + a.d0 + c + 32);
+        }
+        for (; c < a.nd; c += 32) acc += __ldg(row + c) * __ldcg(a.w + a.d0 + c);
+        acc += a1;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) {
+          __stcg(a.z + a.d0 + r, acc);
+          a.out[__ldg(a.perm + a.d0 + r)] = __ldg(a.scale + a.d0 + r) * acc;
+        }
+      }
+    } else {
+      switch (G) {
+        case 4: level_rows<T, 4>(a, kind, p0, p1); break;
+        case 8: level_rows<T, 8>(a, kind, p0, p1); break;
+        case 16: level_rows<T, 16>(a, kind, p0, p1); break;
+        default: level_rows<T, 32>(a, kind, p0, p1); break;
+      }
+    }
+    if (ph + 1 < nphase && !grid_barrier(count, (unsigned)(ph + 1) * gridDim.x, err)) return;
   }
 }
 
@@ -128,6 +379,8 @@ void free_dev(DevFactor<T>& d) {
   cudaFree(d.dense);
   cudaFree(d.w);
   cudaFree(d.z);
+  cudaFree(d.phases);
+  cudaFree(d.bar);
   d = DevFactor<T>();
 }
 
@@ -160,6 +413,33 @@ int upload_factor(const HostFactor& F, DevFactor<T>& d) {
   AJD_TRY(upload(&d.dense, F.dense_inv));
   AJD_CUDA(cudaMalloc(&d.w, std::max<size_t>(1, F.n) * sizeof(T)));
   AJD_CUDA(cudaMalloc(&d.z, std::max<size_t>(1, F.n) * sizeof(T)));
+  // phase list of the persistent apply
+  std::vector<int4> ph;
+  const std::vector<int>& lvp = F.level_ptr;
+  const int nl = F.nlev;
+  auto pick_g = [](double avg) { return avg > 48 ? 32 : avg > 16 ? 16 : avg > 6 ? 8 : 4; };
+  if (lvp[1] > lvp[0]) ph.push_back(make_int4(PH_GATHER, lvp[0], lvp[1], 1));
+  for (int l = 1; l <= nl; ++l) {
+    const int p0 = lvp[l], p1 = lvp[l + 1];
+    if (p1 <= p0) continue;
+    const double avg = (double)(F.Lptr[p1] - F.Lptr[p0]) / (p1 - p0);
+    ph.push_back(make_int4(PH_FWD, p0, p1, pick_g(avg)));
+  }
+  if (F.n_dense > 0) ph.push_back(make_int4(PH_DENSE, lvp[nl], lvp[nl + 1], 32));
+  for (int l = nl - 1; l >= 0; --l) {
+    const int p0 = lvp[l], p1 = lvp[l + 1];
+    if (p1 <= p0) continue;
+    const double avg = (double)(F.Uptr[p1] - F.Uptr[p0]) / (p1 - p0);
+    ph.push_back(make_int4(PH_BWD, p0, p1, pick_g(avg)));
+  }
+  d.nphase = (int)ph.size();
+  AJD_CUDA(cudaMalloc(&d.phases, std::max<size_t>(1, ph.size()) * sizeof(int4)));
+  if (!ph.empty()) AJD_CUDA(cudaMemcpy(d.phases, ph.data(), ph.size() * sizeof(int4), cudaMemcpyHostToDevice));
+  AJD_CUDA(cudaMalloc(&d.bar, 2 * sizeof(unsigned)));
+  AJD_CUDA(cudaMemset(d.bar, 0, 2 * sizeof(unsigned)));
+  int per_sm = 0;
+  AJD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ildl_apply_persistent_kernel<T>, kPersistThreads, 0));
+  d.grid = std::max(1, std::min(per_sm, 2) * sm_count());
   d.ready = true;
   return JD_OK;
 }
@@ -169,6 +449,7 @@ void launch_fwd(const DevFactor<T>& d, const T* b, int p0, int p1, cudaStream_t 
   const int64_t threads = (int64_t)(p1 - p0) * G;
   const int blocks = (int)std::min<int64_t>((threads + kRowThreads - 1) / kRowThreads, 32 * sm_count());
   fwd_level_kernel<T, G><<<blocks, kRowThreads, 0, s>>>(d.Lptr, d.Lcol, d.Lval, d.scale, d.perm, b, d.w, p0, p1);
+  count_launches();
 }
 
 template <typename T, int G>
@@ -177,6 +458,7 @@ void launch_bwd(const DevFactor<T>& d, T* out, int p0, int p1, cudaStream_t s) {
   const int blocks = (int)std::min<int64_t>((threads + kRowThreads - 1) / kRowThreads, 32 * sm_count());
   bwd_level_kernel<T, G><<<blocks, kRowThreads, 0, s>>>(d.Uptr, d.Ucol, d.Uval, d.dd, d.dof, d.partner, d.w, d.z,
                                                        d.scale, d.perm, out, p0, p1);
+  count_launches();
 }
 
 }  // namespace
@@ -186,50 +468,86 @@ int ildl_apply_dev(const ildl_s* f, const T* b, T* out, cudaStream_t s) {
   const DevFactor<T>& d = f->dev<T>();
   if (!d.ready) return fail(JD_EINVAL, "ildl_apply: factor has no device copy (use ildl_create)");
   const HostFactor& F = f->F;
-  const int nl = F.nlev;
-  const std::vector<int>& lp = F.level_ptr;
-  if (F.n == 0) return JD_OK;
-  // forward: level 0 is a pure gather; levels 1..nl-1 and the dense rows read
-  // earlier levels
-  {
-    const int p0 = lp[0], p1 = lp[1];
-    if (p1 > p0) {
-      const int blocks = std::min(ceil_div(p1 - p0, 256), 16 * sm_count());
-      gather_kernel<T><<<blocks, 256, 0, s>>>(d.scale, d.perm, b, d.w, p0, p1);
-    }
+  if (F.n == 0 || d.nphase == 0) return JD_OK;
+  ApplyArgs<T> a{d.perm, d.scale, d.Lptr, d.Lcol, d.Lval, d.Uptr, d.Ucol, d.Uval, d.dd, d.dof, d.partner,
+                 d.dense, d.w, d.z, b, out, F.n_dense, F.level_ptr[F.nlev]};
+  AJD_CUDA(cudaMemsetAsync(d.bar, 0, sizeof(unsigned), s));
+  const int4* ph = d.phases;
+  int np = d.nphase;
+  unsigned* cnt = d.bar;
+  int* err = reinterpret_cast<int*>(d.bar + 1);
+  void* args[] = {&a, &ph, &np, &cnt, &err};
+  AJD_CUDA(cudaLaunchCooperativeKernel((void*)ildl_apply_persistent_kernel<T>, dim3(d.grid), dim3(kPersistThreads),
+                                       args, 0, s));
+  count_launches(2);
+  return JD_OK;
+}
+
+// Timeout flag of the persistent apply (sticky until cleared): JD_EDEVICE if
+// a grid barrier gave up.
+int ildl_check_device_error(const ildl_s* f) {
+  for (int prec = 0; prec < 2; ++prec) {
+    const unsigned* bar = prec == 0 ? f->d64.bar : f->d32.bar;
+    if (!bar) continue;
+    int e = 0;
+    AJD_CUDA(cudaMemcpy(&e, bar + 1, sizeof(int), cudaMemcpyDeviceToHost));
+    if (e) return fail(JD_EDEVICE, "ildl_apply: a device-side barrier timed out");
   }
-  for (int l = 1; l <= nl; ++l) {
-    const int p0 = lp[l], p1 = lp[l + 1];
-    if (p1 <= p0) continue;
-    const int64_t nnz = F.Lptr[p1] - F.Lptr[p0];
-    const double avg = (double)nnz / (p1 - p0);
-    if (avg > 24) launch_fwd<T, 16>(d, b, p0, p1, s);
-    else if (avg > 6) launch_fwd<T, 8>(d, b, p0, p1, s);
-    else launch_fwd<T, 4>(d, b, p0, p1, s);
-  }
-  AJD_CHECK_LAUNCH();
-  if (F.n_dense > 0) {
-    const int d0 = lp[nl];
-    const int blocks = std::min(ceil_div((int64_t)F.n_dense * 32, 256), 8 * sm_count());
-    dense_kernel<T><<<blocks, 256, 0, s>>>(d.dense, F.n_dense, d0, d.w, d.z, d.scale, d.perm, out);
-  }
-  for (int l = nl - 1; l >= 0; --l) {
-    const int p0 = lp[l], p1 = lp[l + 1];
-    if (p1 <= p0) continue;
-    const int64_t nnz = F.Uptr[p1] - F.Uptr[p0];
-    const double avg = (double)nnz / (p1 - p0);
-    if (avg > 24) launch_bwd<T, 16>(d, out, p0, p1, s);
-    else if (avg > 6) launch_bwd<T, 8>(d, out, p0, p1, s);
-    else launch_bwd<T, 4>(d, out, p0, p1, s);
-  }
-  AJD_CHECK_LAUNCH();
   return JD_OK;
 }
 
 template int ildl_apply_dev<double>(const ildl_s*, const double*, double*, cudaStream_t);
 template int ildl_apply_dev<float>(const ildl_s*, const float*, float*, cudaStream_t);
 
+// Invert the dense trailing block (host matrix in, host inverse out) on the
+// current device.
+int invert_dense_on_device(std::vector<double>& M, int m) {
+  if (m == 0) return JD_OK;
+  double *A = nullptr, *X = nullptr, *f = nullptr, *pv = nullptr;
+  int *piv = nullptr, *bad = nullptr;
+  const size_t bytes = (size_t)m * m * sizeof(double);
+  cudaError_t e = cudaMalloc(&A, bytes);
+  if (e == cudaSuccess) e = cudaMalloc(&X, bytes);
+  if (e == cudaSuccess) e = cudaMalloc(&f, m * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&pv, sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&piv, sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&bad, sizeof(int));
+  int rc = JD_OK;
+  if (e == cudaSuccess) e = cudaMemcpy(A, M.data(), bytes, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(bad, 0, sizeof(int));
+  if (e == cudaSuccess) {
+    const int gb = std::max(1, std::min(ceil_div((int64_t)m * m, 256), 8 * sm_count()));
+    identity_kernel<<<gb, 256>>>(X, m);
+    const int cb = ceil_div(m, 256);
+    for (int c = 0; c < m; ++c) {
+      gj_pivot_kernel<<<1, 1024>>>(A, m, c, piv, pv, bad);
+      gj_swap_scale_kernel<<<cb, 256>>>(A, X, m, c, piv, pv);
+      gj_save_col_kernel<<<cb, 256>>>(A, m, c, f);
+      gj_eliminate_kernel<<<gb, 256>>>(A, X, m, c, f);
+    }
+    gj_symmetrize_kernel<<<gb, 256>>>(X, m);
+    count_launches(4 * m + 2);
+    e = cudaGetLastError();
+    int hbad = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(M.data(), X, bytes, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && hbad) rc = fail(JD_ESETUP, "ildl: the final dense block (%d rows) is singular", m);
+  }
+  if (e != cudaSuccess) rc = fail(JD_EDEVICE, "ildl dense inverse: %s", cudaGetErrorString(e));
+  cudaFree(A);
+  cudaFree(X);
+  cudaFree(f);
+  cudaFree(pv);
+  cudaFree(piv);
+  cudaFree(bad);
+  return rc;
+}
+
 int ildl_upload_all(ildl_s* f) {
+  if (f->F.dense_is_matrix) {
+    AJD_TRY(invert_dense_on_device(f->F.dense_inv, f->F.n_dense));
+    f->F.dense_is_matrix = false;
+  }
   AJD_TRY(upload_factor<double>(f->F, f->d64));
   AJD_TRY(upload_factor<float>(f->F, f->d32));
   return JD_OK;
@@ -300,9 +618,9 @@ extern "C" int ildl_params_default(ildl_params* p) {
   if (!p) return fail(JD_EINVAL, "ildl_params_default: NULL");
   p->kappa = 5.0;
   p->drop = -1.0;
-  p->gamma = 0.02;
-  p->max_levels = 96;
-  p->n_dense = 1000;
+  p->gamma = -1.0;
+  p->max_levels = 256;
+  p->n_dense = 3000;
   p->matching = 1;
   return JD_OK;
 }
@@ -312,9 +630,9 @@ static int check_params(const ildl_params* p, ildl_params& out) {
   else ildl_params_default(&out);
   if (!(out.kappa > 1.0)) return fail(JD_EINVAL, "ildl: kappa must be > 1");
   if (!std::isfinite(out.drop) && out.drop > 0) return fail(JD_EINVAL, "ildl: drop must be finite");
-  if (!(out.gamma >= 0.0) || out.gamma >= 1.0) return fail(JD_EINVAL, "ildl: gamma must be in [0, 1)");
-  if (out.max_levels < 1 || out.n_dense < 1 || out.n_dense > 6000)
-    return fail(JD_EINVAL, "ildl: max_levels >= 1 and 1 <= n_dense <= 6000 required");
+  if (out.gamma >= 1.0 || std::isnan(out.gamma)) return fail(JD_EINVAL, "ildl: gamma must be < 1");
+  if (out.max_levels < 1 || out.n_dense < 1 || out.n_dense > 8000)
+    return fail(JD_EINVAL, "ildl: max_levels >= 1 and 1 <= n_dense <= 8000 required");
   return JD_OK;
 }
 
@@ -412,8 +730,10 @@ extern "C" int ildl_create(anderson_t h, double sigma, const ildl_params* p, ild
     lattice_csr(h, eps, sigma, A);
     ildl_s* f = new ildl_s();
     f->device = h->device;
-    int rc = build_ildl(A, prm, f->F);
+    const auto t0 = std::chrono::steady_clock::now();
+    int rc = build_ildl(A, prm, f->F, /*dense_on_host=*/false);
     if (rc == JD_OK) rc = ildl_upload_all(f);
+    f->F.t_total_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     if (rc != JD_OK) {
       ildl_free_device(f);
       delete f;
@@ -439,6 +759,8 @@ extern "C" int ildl_info(ildl_t f, ildl_info_t* info) {
   info->fill = F.nnz_A > 0 ? (2.0 * (double)F.Lcol.size() + nnzD) / (double)F.nnz_A : 0.0;
   info->setup_ms = F.t_total_ms;
   info->match_ms = F.t_match_ms;
+  info->relaxed_levels = F.n_relaxed;
+  info->max_abs_L = F.max_abs_L;
   return JD_OK;
 }
 

@@ -23,6 +23,10 @@ struct DevFactor {
   T* dense = nullptr;
   T* w = nullptr;  // work vectors in position space
   T* z = nullptr;
+  int4* phases = nullptr;  // persistent-apply phase list (kind, p0, p1, G)
+  int nphase = 0;
+  unsigned* bar = nullptr;  // [0] barrier count, [1] timeout flag
+  int grid = 0;
 };
 
 }  // namespace ajd
@@ -44,5 +48,8 @@ namespace ajd {
 // x = K^{-1} b on `stream` (device pointers, n elements).
 template <typename T>
 int ildl_apply_dev(const ildl_s* f, const T* b, T* out, cudaStream_t stream);
+
+// JD_EDEVICE if a device-side wait of an apply timed out (reads a flag).
+int ildl_check_device_error(const ildl_s* f);
 
 }  // namespace ajd

@@ -34,6 +34,8 @@
 #include <cstdio>
 #include <cstdlib>
 
+#include <omp.h>
+
 namespace ajd {
 
 int fail(int code, const char* fmt, ...);
@@ -66,36 +68,41 @@ int max_product_matching(const SymCsr& A, std::vector<int>& match_col, std::vect
                          std::vector<double>& v, std::vector<double>& rowmax) {
   const int n = A.n;
   rowmax.assign(n, 0.0);
-  for (int i = 0; i < n; ++i)
-    for (int64_t p = A.ptr[i]; p < A.ptr[i + 1]; ++p) rowmax[i] = std::max(rowmax[i], std::fabs(A.val[p]));
   std::vector<double> logmax(n);
+#pragma omp parallel for schedule(static)
   for (int i = 0; i < n; ++i) {
-    if (rowmax[i] == 0.0) rowmax[i] = 1.0;
-    logmax[i] = std::log(rowmax[i]);
+    double r = 0.0;
+    for (int64_t p = A.ptr[i]; p < A.ptr[i + 1]; ++p) r = std::max(r, std::fabs(A.val[p]));
+    if (r == 0.0) r = 1.0;
+    rowmax[i] = r;
+    logmax[i] = std::log(r);
   }
   // cost of entry p (row i, column col[p]); +inf for explicit zeros
-  std::vector<double> cost(A.val.size());
+  std::vector<double> cost(A.val.size()), loga(A.val.size());
+#pragma omp parallel for schedule(static)
   for (int i = 0; i < n; ++i)
     for (int64_t p = A.ptr[i]; p < A.ptr[i + 1]; ++p) {
       const double a = std::fabs(A.val[p]);
-      cost[p] = a > 0.0 ? logmax[i] - std::log(a) : kInf;
+      loga[p] = a > 0.0 ? std::log(a) : -kInf;
+      cost[p] = a > 0.0 ? logmax[i] - loga[p] : kInf;
     }
   // v_j = min_i c_ij: by symmetry column j's entries are row j's entries,
   // with the cost taken in the row of the other index.
   v.assign(n, kInf);
-  for (int j = 0; j < n; ++j)
-    for (int64_t p = A.ptr[j]; p < A.ptr[j + 1]; ++p) {
-      const int i = A.col[p];
-      const double a = std::fabs(A.val[p]);
-      if (a > 0.0) v[j] = std::min(v[j], logmax[i] - std::log(a));
-    }
-  for (int j = 0; j < n; ++j)
-    if (v[j] == kInf) v[j] = 0.0;
+#pragma omp parallel for schedule(static)
+  for (int j = 0; j < n; ++j) {
+    double best = kInf;
+    for (int64_t p = A.ptr[j]; p < A.ptr[j + 1]; ++p)
+      if (loga[p] > -kInf) best = std::min(best, logmax[A.col[p]] - loga[p]);
+    v[j] = best == kInf ? 0.0 : best;
+  }
   u.assign(n, kInf);
+#pragma omp parallel for schedule(static)
   for (int i = 0; i < n; ++i) {
+    double best = kInf;
     for (int64_t p = A.ptr[i]; p < A.ptr[i + 1]; ++p)
-      if (cost[p] < kInf) u[i] = std::min(u[i], cost[p] - v[A.col[p]]);
-    if (u[i] == kInf) u[i] = 0.0;
+      if (cost[p] < kInf) best = std::min(best, cost[p] - v[A.col[p]]);
+    u[i] = best == kInf ? 0.0 : best;
   }
   match_col.assign(n, -1);
   std::vector<int> match_row(n, -1);
@@ -311,13 +318,15 @@ bool dense_inverse(int m, std::vector<double>& M, std::vector<double>& inv) {
     double* Mc = &M[(size_t)c * m];
     double* Ic = &inv[(size_t)c * m];
     for (int k = 0; k < m; ++k) { Mc[k] *= d; Ic[k] *= d; }
+#pragma omp parallel for schedule(static)
     for (int r = 0; r < m; ++r) {
       if (r == c) continue;
       const double f = M[(size_t)r * m + c];
       if (f == 0.0) continue;
       double* Mr = &M[(size_t)r * m];
       double* Ir = &inv[(size_t)r * m];
-      for (int k = 0; k < m; ++k) { Mr[k] -= f * Mc[k]; Ir[k] -= f * Ic[k]; }
+      for (int k = c; k < m; ++k) Mr[k] -= f * Mc[k];
+      for (int k = 0; k < m; ++k) Ir[k] -= f * Ic[k];
     }
   }
   // symmetrise (the exact inverse of a symmetric matrix is symmetric)
@@ -331,7 +340,7 @@ bool dense_inverse(int m, std::vector<double>& M, std::vector<double>& inv) {
 
 }  // namespace
 
-int build_ildl(const SymCsr& A, const ildl_params& prm, HostFactor& F) {
+int build_ildl(const SymCsr& A, const ildl_params& prm, HostFactor& F, bool dense_on_host) {
   const auto t_start = Clock::now();
   const int n = A.n;
   if (n <= 0) return fail(JD_EINVAL, "ildl: empty matrix");
@@ -339,10 +348,13 @@ int build_ildl(const SymCsr& A, const ildl_params& prm, HostFactor& F) {
   const double eps_drop = prm.drop < 0.0 ? 1.0 / std::sqrt((double)n) : prm.drop;
   const double tau = eps_drop / kappa;
 
-  const double gamma = prm.gamma > 0.0 ? prm.gamma : 0.0;
+  // weak-coupling threshold of the independent sets; by default it shrinks
+  // with the drop tolerance (measured: a fixed 0.02 loses the preconditioner
+  // at n = 10^6 while 5/sqrt(n) keeps it)
+  const double gamma = prm.gamma < 0.0 ? std::min(0.02, 5.0 / std::sqrt((double)n)) : prm.gamma;
   const int max_levels = prm.max_levels > 0 ? prm.max_levels : 64;
   const int n_dense = prm.n_dense > 0 ? prm.n_dense : 1000;
-  constexpr int kDenseHardMax = 6000;
+  constexpr int kDenseHardMax = 8000;
 
   F = HostFactor();
   F.n = n;
@@ -389,6 +401,7 @@ int build_ildl(const SymCsr& A, const ildl_params& prm, HostFactor& F) {
         d[i] = r > 0.0 ? 1.0 / std::sqrt(r) : 1.0;
       }
     }
+#pragma omp parallel for schedule(static)
     for (int i = 0; i < m; ++i) {
       cum[i] *= d[i];
       for (int64_t p = S.ptr[i]; p < S.ptr[i + 1]; ++p) S.val[p] *= d[i] * d[S.col[p]];
@@ -406,6 +419,7 @@ int build_ildl(const SymCsr& A, const ildl_params& prm, HostFactor& F) {
     // 3. candidates: d1 = sum_{k != i} |s_ki| / |s_ii| (the 1-norm of the
     // would-be L column); d2 = sum_k ||(s_ki, s_kj) B^{-1}||_1 for a 2x2 block
     std::vector<double> diag(m), offsum(m);
+#pragma omp parallel for schedule(static)
     for (int i = 0; i < m; ++i) {
       double o = 0.0, dg = 0.0;
       for (int64_t p = S.ptr[i]; p < S.ptr[i + 1]; ++p) {
@@ -486,11 +500,11 @@ int build_ildl(const SymCsr& A, const ildl_params& prm, HostFactor& F) {
       }
     };
     try_accept(kappa - 1.0);
-    if ((int64_t)acc.size() * 200 < m) {
-      // the level would stall: accept every remaining independent candidate
-      // with a finite pivot (recorded as a relaxed level)
+    if ((int64_t)acc.size() * 200 < m && m > n_dense) {
+      // the level would stall: widen the bound on ||L^{-1}|| for this level
+      // step by step (recorded as a relaxed level), never beyond 64 kappa
       ++F.n_relaxed;
-      try_accept(std::numeric_limits<double>::max());
+      for (double f = 2.0; f <= 64.0 && (int64_t)acc.size() * 200 < m; f *= 2.0) try_accept(f * kappa - 1.0);
     }
     if (acc.empty()) return fail(JD_ESETUP, "ildl: no usable pivot at level %d (%d rows)", level, m);
 
@@ -549,36 +563,55 @@ int build_ildl(const SymCsr& A, const ildl_params& prm, HostFactor& F) {
     std::vector<int64_t> lptr(mc_n + 1, 0);
     std::vector<int> lnode;    // B node (local index)
     std::vector<double> lval;
+    const int nchunk = std::max(1, std::min(mc_n, 8 * omp_get_max_threads()));
     {
-      std::vector<double> fa(acc.size(), 0.0), fb(acc.size(), 0.0);
-      std::vector<int> touched;
-      for (int r = 0; r < mc_n; ++r) {
-        const int k = cnodes[r];
-        touched.clear();
-        for (int64_t p = S.ptr[k]; p < S.ptr[k + 1]; ++p) {
-          const int x = S.col[p];
-          if (!inB[x]) continue;
-          const int b = blk_of[x];
-          const Cand& cd = cands[acc[b]];
-          if (fa[b] == 0.0 && fb[b] == 0.0) touched.push_back(b);
-          if (x == cd.a) fa[b] += S.val[p];
-          else fb[b] += S.val[p];
-        }
-        std::sort(touched.begin(), touched.end());
-        for (int b : touched) {
-          const Cand& cd = cands[acc[b]];
-          if (cd.b < 0) {
-            const double l = fa[b] * binv[3 * b];
-            if (std::fabs(l) >= tau && l != 0.0) { lnode.push_back(cd.a); lval.push_back(l); }
-          } else {
-            const double l1 = fa[b] * binv[3 * b] + fb[b] * binv[3 * b + 1];
-            const double l2 = fa[b] * binv[3 * b + 1] + fb[b] * binv[3 * b + 2];
-            if (std::fabs(l1) >= tau && l1 != 0.0) { lnode.push_back(cd.a); lval.push_back(l1); }
-            if (std::fabs(l2) >= tau && l2 != 0.0) { lnode.push_back(cd.b); lval.push_back(l2); }
+      std::vector<std::vector<int>> cn(nchunk);
+      std::vector<std::vector<double>> cv(nchunk);
+      std::vector<int> rowcnt(mc_n, 0);
+#pragma omp parallel
+      {
+        std::vector<double> fa(acc.size(), 0.0), fb(acc.size(), 0.0);
+        std::vector<int> touched;
+#pragma omp for schedule(dynamic, 1)
+        for (int ch = 0; ch < nchunk; ++ch) {
+          const int r0 = (int)((int64_t)mc_n * ch / nchunk), r1 = (int)((int64_t)mc_n * (ch + 1) / nchunk);
+          for (int r = r0; r < r1; ++r) {
+            const int k = cnodes[r];
+            touched.clear();
+            for (int64_t p = S.ptr[k]; p < S.ptr[k + 1]; ++p) {
+              const int x = S.col[p];
+              if (!inB[x]) continue;
+              const int b = blk_of[x];
+              const Cand& cd = cands[acc[b]];
+              if (fa[b] == 0.0 && fb[b] == 0.0) touched.push_back(b);
+              if (x == cd.a) fa[b] += S.val[p];
+              else fb[b] += S.val[p];
+            }
+            std::sort(touched.begin(), touched.end());
+            const size_t before = cn[ch].size();
+            for (int b : touched) {
+              const Cand& cd = cands[acc[b]];
+              if (cd.b < 0) {
+                const double l = fa[b] * binv[3 * b];
+                if (std::fabs(l) >= tau && l != 0.0) { cn[ch].push_back(cd.a); cv[ch].push_back(l); }
+              } else {
+                const double l1 = fa[b] * binv[3 * b] + fb[b] * binv[3 * b + 1];
+                const double l2 = fa[b] * binv[3 * b + 1] + fb[b] * binv[3 * b + 2];
+                if (std::fabs(l1) >= tau && l1 != 0.0) { cn[ch].push_back(cd.a); cv[ch].push_back(l1); }
+                if (std::fabs(l2) >= tau && l2 != 0.0) { cn[ch].push_back(cd.b); cv[ch].push_back(l2); }
+              }
+              fa[b] = fb[b] = 0.0;
+            }
+            rowcnt[r] = (int)(cn[ch].size() - before);
           }
-          fa[b] = fb[b] = 0.0;
         }
-        lptr[r + 1] = (int64_t)lnode.size();
+      }
+      for (int r = 0; r < mc_n; ++r) lptr[r + 1] = lptr[r] + rowcnt[r];
+      lnode.reserve(lptr[mc_n]);
+      lval.reserve(lptr[mc_n]);
+      for (int ch = 0; ch < nchunk; ++ch) {
+        lnode.insert(lnode.end(), cn[ch].begin(), cn[ch].end());
+        lval.insert(lval.end(), cv[ch].begin(), cv[ch].end());
       }
     }
     for (int r = 0; r < mc_n; ++r) {
@@ -631,55 +664,88 @@ int build_ildl(const SymCsr& A, const ildl_params& prm, HostFactor& F) {
     U.n = mc_n;
     U.ptr.assign(mc_n + 1, 0);
     {
-      std::vector<double> accv(mc_n, 0.0);
-      std::vector<char> mark(mc_n, 0);
-      std::vector<int> cols;
-      std::vector<int> rowblocks;
-      for (int r = 0; r < mc_n; ++r) {
-        const int k = cnodes[r];
-        cols.clear();
-        for (int64_t p = S.ptr[k]; p < S.ptr[k + 1]; ++p) {
-          const int c = cidx[S.col[p]];
-          if (c < r) continue;  // B columns have cidx -1
-          if (!mark[c]) { mark[c] = 1; cols.push_back(c); }
-          accv[c] += S.val[p];
-        }
-        if (!mark[r]) { mark[r] = 1; cols.push_back(r); }
-        // blocks in row r of L_F with their (l_a, l_b) values
-        rowblocks.clear();
-        for (int64_t p = lptr[r]; p < lptr[r + 1]; ++p) {
-          const int b = blk_of[lnode[p]];
-          if (rowblocks.empty() || rowblocks.back() != b) rowblocks.push_back(b);
-        }
-        for (int b : rowblocks) {
-          // find this row's record in block b's column list (rows ascending)
-          const int* cb = crow.data() + cptr[b];
-          const int* ce = crow.data() + cptr[b + 1];
-          const int64_t me = std::lower_bound(cb, ce, r) - crow.data();
-          const double la = c1[me], lb = c2[me];
-          double wa, wb;  // (l_a, l_b) * D_b
-          if (cands[acc[b]].b < 0) { wa = la * bmat[3 * b]; wb = 0.0; }
-          else {
-            wa = la * bmat[3 * b] + lb * bmat[3 * b + 1];
-            wb = la * bmat[3 * b + 1] + lb * bmat[3 * b + 2];
+      std::vector<std::vector<int>> ucol(nchunk);
+      std::vector<std::vector<double>> uval(nchunk);
+      std::vector<int> rowcnt(mc_n, 0);
+#pragma omp parallel
+      {
+        std::vector<double> accv(mc_n, 0.0);
+        std::vector<char> mark(mc_n, 0);
+        std::vector<int> cols;
+        std::vector<int> rowblocks;
+#pragma omp for schedule(dynamic, 1)
+        for (int ch = 0; ch < nchunk; ++ch) {
+          const int r0 = (int)((int64_t)mc_n * ch / nchunk), r1 = (int)((int64_t)mc_n * (ch + 1) / nchunk);
+          for (int r = r0; r < r1; ++r) {
+            const int k = cnodes[r];
+            if (lptr[r] == lptr[r + 1]) {
+              // no elimination update reaches this row: S' row = S row on C
+              // (column order is preserved by the C numbering)
+              const size_t before = ucol[ch].size();
+              for (int64_t p = S.ptr[k]; p < S.ptr[k + 1]; ++p) {
+                const int c = cidx[S.col[p]];
+                if (c < r) continue;
+                if (c == r || std::fabs(S.val[p]) >= tau) {
+                  ucol[ch].push_back(c);
+                  uval[ch].push_back(S.val[p]);
+                }
+              }
+              rowcnt[r] = (int)(ucol[ch].size() - before);
+              continue;
+            }
+            cols.clear();
+            for (int64_t p = S.ptr[k]; p < S.ptr[k + 1]; ++p) {
+              const int c = cidx[S.col[p]];
+              if (c < r) continue;  // B columns have cidx -1
+              if (!mark[c]) { mark[c] = 1; cols.push_back(c); }
+              accv[c] += S.val[p];
+            }
+            if (!mark[r]) { mark[r] = 1; cols.push_back(r); }
+            // blocks in row r of L_F with their (l_a, l_b) values
+            rowblocks.clear();
+            for (int64_t p = lptr[r]; p < lptr[r + 1]; ++p) {
+              const int b = blk_of[lnode[p]];
+              if (rowblocks.empty() || rowblocks.back() != b) rowblocks.push_back(b);
+            }
+            for (int b : rowblocks) {
+              // this row's record in block b's column list (rows ascending)
+              const int* cb = crow.data() + cptr[b];
+              const int* ce = crow.data() + cptr[b + 1];
+              const int64_t me = std::lower_bound(cb, ce, r) - crow.data();
+              const double la = c1[me], lb = c2[me];
+              double wa, wb;  // (l_a, l_b) * D_b
+              if (cands[acc[b]].b < 0) { wa = la * bmat[3 * b]; wb = 0.0; }
+              else {
+                wa = la * bmat[3 * b] + lb * bmat[3 * b + 1];
+                wb = la * bmat[3 * b + 1] + lb * bmat[3 * b + 2];
+              }
+              for (int64_t t = me; t < cptr[b + 1]; ++t) {
+                const int q = crow[t];  // q >= r because rows are ascending
+                if (!mark[q]) { mark[q] = 1; cols.push_back(q); }
+                accv[q] -= wa * c1[t] + wb * c2[t];
+              }
+            }
+            std::sort(cols.begin(), cols.end());
+            const size_t before = ucol[ch].size();
+            for (int c : cols) {
+              const double val = accv[c];
+              if (c == r || std::fabs(val) >= tau) {
+                ucol[ch].push_back(c);
+                uval[ch].push_back(val);
+              }
+              accv[c] = 0.0;
+              mark[c] = 0;
+            }
+            rowcnt[r] = (int)(ucol[ch].size() - before);
           }
-          for (int64_t t = me; t < cptr[b + 1]; ++t) {
-            const int q = crow[t];  // q >= r because rows are ascending
-            if (!mark[q]) { mark[q] = 1; cols.push_back(q); }
-            accv[q] -= wa * c1[t] + wb * c2[t];
-          }
         }
-        std::sort(cols.begin(), cols.end());
-        for (int c : cols) {
-          const double val = accv[c];
-          if (c == r || std::fabs(val) >= tau) {
-            U.col.push_back(c);
-            U.val.push_back(val);
-          }
-          accv[c] = 0.0;
-          mark[c] = 0;
-        }
-        U.ptr[r + 1] = (int64_t)U.col.size();
+      }
+      for (int r = 0; r < mc_n; ++r) U.ptr[r + 1] = U.ptr[r] + rowcnt[r];
+      U.col.reserve(U.ptr[mc_n]);
+      U.val.reserve(U.ptr[mc_n]);
+      for (int ch = 0; ch < nchunk; ++ch) {
+        U.col.insert(U.col.end(), ucol[ch].begin(), ucol[ch].end());
+        U.val.insert(U.val.end(), uval[ch].begin(), uval[ch].end());
       }
     }
     // mirror U into a full symmetric CSR
@@ -734,8 +800,13 @@ int build_ildl(const SymCsr& A, const ildl_params& prm, HostFactor& F) {
     for (int i = 0; i < nd; ++i)
       for (int64_t p = S.ptr[i]; p < S.ptr[i + 1]; ++p) M[(size_t)i * nd + S.col[p]] = S.val[p];
     const auto t_dense = Clock::now();
-    if (!dense_inverse(nd, M, dense_inv))
-      return fail(JD_ESETUP, "ildl: the final dense block (%d rows) is singular", nd);
+    if (dense_on_host) {
+      if (!dense_inverse(nd, M, dense_inv))
+        return fail(JD_ESETUP, "ildl: the final dense block (%d rows) is singular", nd);
+    } else {
+      dense_inv.swap(M);  // inverted on the device by the caller
+      F.dense_is_matrix = true;
+    }
     if (verbose) std::fprintf(stderr, "ildl dense block %d rows: %.1f ms\n", nd, ms_since(t_dense));
     for (int i = 0; i < nd; ++i) {
       order.push_back(gid[i]);
@@ -804,6 +875,8 @@ int build_ildl(const SymCsr& A, const ildl_params& prm, HostFactor& F) {
     F.partner[p] = part[o] >= 0 ? pos[part[o]] : -1;
   }
   F.dense_inv.swap(dense_inv);
+  F.max_abs_L = 0.0;
+  for (double v : F.Lval) F.max_abs_L = std::max(F.max_abs_L, std::fabs(v));
   F.t_match_ms = t_match;
   F.t_total_ms = ms_since(t_start);
   F.t_factor_ms = F.t_total_ms - t_match;

@@ -39,18 +39,22 @@ struct HostFactor {
   std::vector<double> dinv_o;     // per position: off-diagonal of D^{-1} block
   std::vector<int> partner;       // per position: 2x2 partner position or -1
   std::vector<double> dense_inv;  // n_dense^2, row-major, symmetric
+  bool dense_is_matrix = false;   // dense_inv still holds the block itself
   // statistics
   int n_2x2 = 0;
   int n_matched_offdiag = 0;      // rows matched off the diagonal at level 0
   int n_relaxed = 0;              // levels where pivot acceptance was relaxed
+  double max_abs_L = 0.0;         // largest |entry| of the global L
   int64_t nnz_A = 0;
   double t_match_ms = 0, t_factor_ms = 0, t_total_ms = 0;
   std::vector<int> level_sizes;   // rows eliminated per sparse level
 };
 
 // Build the preconditioner of A (symmetric, e.g. A - sigma I).  Returns
-// JD_OK or JD_ESETUP / JD_EINVAL with jd_last_error() set.
-int build_ildl(const SymCsr& A, const ildl_params& p, HostFactor& F);
+// JD_OK or JD_ESETUP / JD_EINVAL with jd_last_error() set.  With
+// dense_on_host = false the trailing dense block is left un-inverted
+// (dense_is_matrix) for a device-side inversion.
+int build_ildl(const SymCsr& A, const ildl_params& p, HostFactor& F, bool dense_on_host = true);
 
 // Maximum-product transversal of Section 5.1 (Eqs. (5.1)-(5.2)): on return
 // match_col[j] is the row matched to column j, u and v are the dual

@@ -16,6 +16,9 @@
 #include <cstring>
 #include <new>
 #include <vector>
+#include <cstdio>
+#include <cstdlib>
+#include <limits>
 
 #include "anderson_impl.cuh"
 #include "ildl_impl.cuh"
@@ -69,6 +72,29 @@ multidot_kernel(Cols<T> X1, Cols<T> X2, const T* __restrict__ extra, const T* __
     T acc = T(0);
     for (int64_t i = i0; i < n; i += stride) acc += x[i] * v[i];
     const double s = block_sum((double)acc, sh);
+    if (threadIdx.x == 0) partial[(int64_t)blockIdx.x * ncols + j] = s;
+  }
+}
+
+// partial[b*ncols + j] = block b's share of (AV_j - sigma V_j)^T (AV_c - sigma V_c),
+// j = 0..ncols-1, c = ncols - 1: the new column of G = W^T W, W = AV - sigma V,
+// formed from the shifted vectors themselves (no cancellation of
+// (AV)^T AV - 2 sigma V^T AV + sigma^2 I)
+__global__ void __launch_bounds__(kThreads)
+shifted_dots_kernel(const double* __restrict__ V, const double* __restrict__ AV, int64_t ld, int ncols,
+                    double sigma, int64_t n, double* __restrict__ partial) {
+  __shared__ double sh[kThreads / 32];
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int c = ncols - 1;
+  for (int j = 0; j < ncols; ++j) {
+    double acc = 0.0;
+    for (int64_t i = i0; i < n; i += stride) {
+      const double wc = AV[(int64_t)c * ld + i] - sigma * V[(int64_t)c * ld + i];
+      const double wj = AV[(int64_t)j * ld + i] - sigma * V[(int64_t)j * ld + i];
+      acc = fma(wj, wc, acc);
+    }
+    const double s = block_sum(acc, sh);
     if (threadIdx.x == 0) partial[(int64_t)blockIdx.x * ncols + j] = s;
   }
 }
@@ -481,6 +507,115 @@ __global__ void first_index_kernel(const double* __restrict__ x, int64_t n, cons
 
 }  // namespace
 
+// ------------------------------------------- small dense algebra (host) ---
+// Matrices of order m <= 64, column-major with leading dimension m.
+namespace hostla {
+
+// Cyclic Jacobi eigen-decomposition of the symmetric A: A = V diag(w) V^T.
+void jacobi_eig(int m, std::vector<double> A, std::vector<double>& w, std::vector<double>& V) {
+  V.assign((size_t)m * m, 0.0);
+  for (int i = 0; i < m; ++i) V[(size_t)i * m + i] = 1.0;
+  auto a = [&](int i, int j) -> double& { return A[(size_t)j * m + i]; };
+  double fro = 0.0;
+  for (double x : A) fro += x * x;
+  for (int sweep = 0; sweep < 60; ++sweep) {
+    double off = 0.0;
+    for (int j = 0; j < m; ++j)
+      for (int i = 0; i < m; ++i)
+        if (i != j) off += a(i, j) * a(i, j);
+    if (off <= 1e-30 * fro || fro == 0.0) break;
+    for (int p = 0; p < m - 1; ++p)
+      for (int q = p + 1; q < m; ++q) {
+        const double apq = a(p, q);
+        if (apq == 0.0) continue;
+        const double tau = (a(q, q) - a(p, p)) / (2.0 * apq);
+        double t;
+        if (std::fabs(tau) > 1e150) t = 0.5 / tau;
+        else t = (tau >= 0.0 ? 1.0 : -1.0) / (std::fabs(tau) + std::sqrt(1.0 + tau * tau));
+        const double c = 1.0 / std::sqrt(1.0 + t * t), sn = t * c;
+        for (int k = 0; k < m; ++k) {
+          const double akp = a(k, p), akq = a(k, q);
+          a(k, p) = c * akp - sn * akq;
+          a(k, q) = sn * akp + c * akq;
+        }
+        for (int k = 0; k < m; ++k) {
+          const double apk = a(p, k), aqk = a(q, k);
+          a(p, k) = c * apk - sn * aqk;
+          a(q, k) = sn * apk + c * aqk;
+        }
+        for (int k = 0; k < m; ++k) {
+          const double vkp = V[(size_t)p * m + k], vkq = V[(size_t)q * m + k];
+          V[(size_t)p * m + k] = c * vkp - sn * vkq;
+          V[(size_t)q * m + k] = sn * vkp + c * vkq;
+        }
+      }
+  }
+  w.resize(m);
+  for (int i = 0; i < m; ++i) w[i] = a(i, i);
+}
+
+// Cholesky G = L L^T in place (lower triangle); false if not positive definite.
+bool cholesky(int m, std::vector<double>& G) {
+  for (int j = 0; j < m; ++j) {
+    double d = G[(size_t)j * m + j];
+    for (int k = 0; k < j; ++k) d -= G[(size_t)k * m + j] * G[(size_t)k * m + j];
+    if (!(d > 0.0)) return false;
+    d = std::sqrt(d);
+    G[(size_t)j * m + j] = d;
+    for (int i = j + 1; i < m; ++i) {
+      double s = G[(size_t)j * m + i];
+      for (int k = 0; k < j; ++k) s -= G[(size_t)k * m + i] * G[(size_t)k * m + j];
+      G[(size_t)j * m + i] = s / d;
+    }
+  }
+  return true;
+}
+
+// Orthonormal basis (m x c, column-major) of the columns of Y (m x c) by
+// modified Gram–Schmidt run twice; the first column is y_0 / ||y_0||.
+void orthonormalize(int m, int c, const std::vector<double>& Y, std::vector<double>& Qo) {
+  Qo = Y;
+  for (int j = 0; j < c; ++j) {
+    double* qj = &Qo[(size_t)j * m];
+    for (int pass = 0; pass < 2; ++pass)
+      for (int i = 0; i < j; ++i) {
+        const double* qi = &Qo[(size_t)i * m];
+        double d = 0.0;
+        for (int k = 0; k < m; ++k) d += qi[k] * qj[k];
+        for (int k = 0; k < m; ++k) qj[k] -= d * qi[k];
+      }
+    double nr = 0.0;
+    for (int k = 0; k < m; ++k) nr += qj[k] * qj[k];
+    nr = std::sqrt(nr);
+    for (int k = 0; k < m; ++k) qj[k] = nr > 0.0 ? qj[k] / nr : 0.0;
+  }
+}
+
+// B = Q^T A Q for symmetric A (m x m) and Q (m x c)
+std::vector<double> congruence(int m, int c, const std::vector<double>& A, const std::vector<double>& Q) {
+  std::vector<double> AQ((size_t)m * c, 0.0), B((size_t)c * c, 0.0);
+  for (int j = 0; j < c; ++j)
+    for (int k = 0; k < m; ++k) {
+      const double q = Q[(size_t)j * m + k];
+      if (q == 0.0) continue;
+      for (int i = 0; i < m; ++i) AQ[(size_t)j * m + i] += A[(size_t)k * m + i] * q;
+    }
+  for (int j = 0; j < c; ++j)
+    for (int i = 0; i < c; ++i) {
+      double s = 0.0;
+      for (int k = 0; k < m; ++k) s += Q[(size_t)i * m + k] * AQ[(size_t)j * m + k];
+      B[(size_t)j * c + i] = s;
+    }
+  for (int j = 0; j < c; ++j)
+    for (int i = j + 1; i < c; ++i) {
+      const double v = 0.5 * (B[(size_t)j * c + i] + B[(size_t)i * c + j]);
+      B[(size_t)j * c + i] = B[(size_t)i * c + j] = v;
+    }
+  return B;
+}
+
+}  // namespace hostla
+
 // ------------------------------------------------------------ the solver ---
 class JdSolver {
  public:
@@ -500,6 +635,7 @@ class JdSolver {
   cudaStream_t s_;
   int64_t n_ = 0, ld_ = 0;
   int jmin_ = 0, jmax_ = 0;
+  int kint_ = 0;  // pairs computed: k plus guard pairs
   double normA_ = 0.0;
   // binary64 buffers
   double *V_ = nullptr, *AV_ = nullptr, *Vt_ = nullptr, *AVt_ = nullptr, *Q_ = nullptr;
@@ -515,6 +651,15 @@ class JdSolver {
   int nb_ = 0;              // blocks of vector kernels
   std::vector<double> Mq_;  // cached Q^T W_Q block (host, kc x kc)
   int inner_total_ = 0;
+  // CUDA events around the inner-loop preconditioner and stencil calls
+  static constexpr int kEv = 16;
+  cudaEvent_t evp_[2 * kEv] = {}, evs_[2 * kEv] = {};
+  int nevp_ = 0, nevs_ = 0;
+  int precond_calls_ = 0, stencil_calls_ = 0;
+  double precond_ms_ = 0.0, stencil_ms_ = 0.0;
+  int64_t launches0_ = 0;
+  bool trace_ = std::getenv("AJD_JD_TRACE") != nullptr;
+  void harvest_events();
 
   int alloc();
   void release();
@@ -542,7 +687,7 @@ int JdSolver::alloc() {
   AJD_TRY(A((void**)&AV_, vb * jmax_));
   AJD_TRY(A((void**)&Vt_, vb * jmax_));
   AJD_TRY(A((void**)&AVt_, vb * jmax_));
-  AJD_TRY(A((void**)&Q_, vb * k_));
+  AJD_TRY(A((void**)&Q_, vb * kint_));
   AJD_TRY(A((void**)&t_, vb));
   AJD_TRY(A((void**)&u_, vb));
   AJD_TRY(A((void**)&Au_, vb));
@@ -553,20 +698,38 @@ int JdSolver::alloc() {
   AJD_TRY(A((void**)&dots_, sizeof(double) * kMaxCols));
   AJD_TRY(A((void**)&partial_, sizeof(double) * (size_t)nb_ * kMaxCols));
   AJD_TRY(A((void**)&scal_, sizeof(double) * 64));
-  AJD_TRY(A((void**)&Minv_, sizeof(double) * (k_ + 1) * (k_ + 1)));
-  AJD_TRY(A((void**)&gg_, sizeof(double) * (k_ + 1)));
+  AJD_TRY(A((void**)&Minv_, sizeof(double) * (kint_ + 1) * (kint_ + 1)));
+  AJD_TRY(A((void**)&gg_, sizeof(double) * (kint_ + 1)));
   AJD_TRY(A((void**)&flags_, sizeof(int) * 4));
   AJD_TRY(A((void**)&amax_, 2 * sizeof(unsigned long long)));
   const size_t eb = p_.precision == JD_FP32 ? sizeof(float) : sizeof(double);
   const size_t pb = (size_t)ld_ * eb;
-  AJD_TRY(A(&Qt_, pb * (k_ + 1)));
-  AJD_TRY(A(&W_, pb * (k_ + 1)));
+  AJD_TRY(A(&Qt_, pb * (kint_ + 1)));
+  AJD_TRY(A(&W_, pb * (kint_ + 1)));
   for (void** b : {&xb_, &rb_, &qb_, &db_, &tb_, &yb_, &ub_, &bb_}) AJD_TRY(A(b, pb));
   AJD_CUDA(cudaMallocHost(&host_, sizeof(double) * (kMaxM * kMaxM + 256)));
+  for (auto& e : evp_) AJD_CUDA(cudaEventCreate(&e));
+  for (auto& e : evs_) AJD_CUDA(cudaEventCreate(&e));
   return JD_OK;
 }
 
+void JdSolver::harvest_events() {
+  for (int i = 0; i < nevp_; ++i) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, evp_[2 * i], evp_[2 * i + 1]) == cudaSuccess) precond_ms_ += ms;
+  }
+  for (int i = 0; i < nevs_; ++i) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, evs_[2 * i], evs_[2 * i + 1]) == cudaSuccess) stencil_ms_ += ms;
+  }
+  precond_calls_ += nevp_;
+  stencil_calls_ += nevs_;
+  nevp_ = nevs_ = 0;
+}
+
 void JdSolver::release() {
+  for (auto& e : evp_) if (e) cudaEventDestroy(e);
+  for (auto& e : evs_) if (e) cudaEventDestroy(e);
   for (void* p : {(void*)V_, (void*)AV_, (void*)Vt_, (void*)AVt_, (void*)Q_, (void*)t_, (void*)u_, (void*)Au_,
                   (void*)r_, (void*)H_, (void*)theta_, (void*)Y_, (void*)dots_, (void*)partial_, (void*)scal_,
                   (void*)Minv_, (void*)gg_, (void*)flags_, (void*)amax_, Qt_, W_, xb_, rb_, qb_, db_, tb_, yb_, ub_, bb_})
@@ -586,8 +749,8 @@ int JdSolver::sync_read(const double* dev, int cnt, double* host) {
 int JdSolver::dot_cols(Cols<double> X1, Cols<double> X2, const double* extra, const double* v, double* out) {
   const int nc = X1.c + X2.c + (extra ? 1 : 0);
   if (nc == 0) return JD_OK;
-  multidot_kernel<double><<<nb_, kThreads, 0, s_>>>(X1, X2, extra, v, n_, partial_, nc, nullptr);
-  reduce_partials_kernel<<<1, 128, 0, s_>>>(partial_, nb_, nc, out, nullptr);
+  multidot_kernel<double><<<nb_, kThreads, 0, s_>>>(X1, X2, extra, v, n_, partial_, nc, nullptr); count_launches();
+  reduce_partials_kernel<<<1, 128, 0, s_>>>(partial_, nb_, nc, out, nullptr); count_launches();
   AJD_CHECK_LAUNCH();
   return JD_OK;
 }
@@ -598,7 +761,7 @@ int JdSolver::cgs2(int kc, int m, double* t, double* nrm_host) {
   for (int pass = 0; pass < 2; ++pass) {
     if (kc + m == 0) break;
     AJD_TRY(dot_cols(Xq, Xv, nullptr, t, dots_));
-    multiaxpy_kernel<double><<<nb_, kThreads, 0, s_>>>(Xq, Xv, dots_, t, n_);
+    multiaxpy_kernel<double><<<nb_, kThreads, 0, s_>>>(Xq, Xv, dots_, t, n_); count_launches();
   }
   AJD_TRY(dot_cols(Cols<double>{t, ld_, 1}, Cols<double>{}, nullptr, t, scal_));
   double nn;
@@ -616,7 +779,7 @@ int JdSolver::rr(int m) {
                                   (int)(sizeof(double) * (2 * kMaxM * kMaxM + kMaxM) + sizeof(int) * kMaxM)));
     attr = true;
   }
-  rr_eig_kernel<<<1, kThreads, sm, s_>>>(H_, kMaxM, m, sigma_, theta_, Y_, kMaxM);
+  rr_eig_kernel<<<1, kThreads, sm, s_>>>(H_, kMaxM, m, sigma_, theta_, Y_, kMaxM); count_launches();
   AJD_CHECK_LAUNCH();
   return JD_OK;
 }
@@ -632,13 +795,13 @@ int JdSolver::correction(int kc, double theta_hat, double rel_tol, int* its) {
   int* brk = flags_ + 1;
   const int bl = nb_;
   // Qt[:, kc] = u, W[:, kc] = K^{-1} u  (Q columns and their W are cached)
-  convert_kernel<double, T><<<bl, kThreads, 0, s_>>>(u_, Qt + (int64_t)kc * ld_, n_, 1.0);
+  convert_kernel<double, T><<<bl, kThreads, 0, s_>>>(u_, Qt + (int64_t)kc * ld_, n_, 1.0); count_launches();
   AJD_TRY(ildl_apply_dev<T>(pc_, Qt + (int64_t)kc * ld_, W + (int64_t)kc * ld_, s_));
   // M = Qt^T W (c x c): only row/column kc are new
   {
     multidot_kernel<T><<<bl, kThreads, 0, s_>>>(Cols<T>{Qt, ld_, c}, Cols<T>{}, nullptr, W + (int64_t)kc * ld_, n_,
-                                                partial_, c, nullptr);
-    reduce_partials_kernel<<<1, 128, 0, s_>>>(partial_, bl, c, dots_, nullptr);
+                                                partial_, c, nullptr); count_launches();
+    reduce_partials_kernel<<<1, 128, 0, s_>>>(partial_, bl, c, dots_, nullptr); count_launches();
     std::vector<double> col(c);
     AJD_TRY(sync_read(dots_, c, col.data()));
     // assemble M (host) from the cached Q block and the new column, invert
@@ -679,38 +842,44 @@ int JdSolver::correction(int kc, double theta_hat, double rel_tol, int* its) {
     AJD_CUDA(cudaMemcpyAsync(Minv_, Mi.data(), sizeof(double) * c * c, cudaMemcpyHostToDevice, s_));
   }
   // rhs b = -r (binary64 residual, already orthogonal to Q and u)
-  convert_kernel<double, T><<<bl, kThreads, 0, s_>>>(r_, b, n_, -1.0);
+  convert_kernel<double, T><<<bl, kThreads, 0, s_>>>(r_, b, n_, -1.0); count_launches();
   Cols<T> QtC{Qt, ld_, c}, WC{W, ld_, c};
   // init: r = b, x = d = 0, tau = ||b||; u = P b; q = u; rho = r^T u
-  sqmr_init_kernel<T><<<bl, kThreads, 0, s_>>>(b, r, x, d, n_, partial_);
-  sqmr_scalar_init_kernel<<<1, 1, 0, s_>>>(partial_, bl, scal_, rel_tol, done, brk);
+  sqmr_init_kernel<T><<<bl, kThreads, 0, s_>>>(b, r, x, d, n_, partial_); count_launches();
+  sqmr_scalar_init_kernel<<<1, 1, 0, s_>>>(partial_, bl, scal_, rel_tol, done, brk); count_launches();
   auto precond = [&]() -> int {
+    const bool timed = nevp_ < kEv;
+    if (timed) AJD_CUDA(cudaEventRecord(evp_[2 * nevp_], s_));
     AJD_TRY(ildl_apply_dev<T>(pc_, r, y, s_));
-    multidot_kernel<T><<<bl, kThreads, 0, s_>>>(QtC, Cols<T>{}, nullptr, y, n_, partial_, c, done);
-    reduce_partials_kernel<<<1, 128, 0, s_>>>(partial_, bl, c, dots_, done);
-    small_matvec_kernel<<<1, 64, 0, s_>>>(Minv_, c, dots_, gg_, done);
-    sqmr_update_u_kernel<T><<<bl, kThreads, 0, s_>>>(WC, gg_, y, r, u, n_, partial_, done);
+    if (timed) AJD_CUDA(cudaEventRecord(evp_[2 * nevp_++ + 1], s_));
+    multidot_kernel<T><<<bl, kThreads, 0, s_>>>(QtC, Cols<T>{}, nullptr, y, n_, partial_, c, done); count_launches();
+    reduce_partials_kernel<<<1, 128, 0, s_>>>(partial_, bl, c, dots_, done); count_launches();
+    small_matvec_kernel<<<1, 64, 0, s_>>>(Minv_, c, dots_, gg_, done); count_launches();
+    sqmr_update_u_kernel<T><<<bl, kThreads, 0, s_>>>(WC, gg_, y, r, u, n_, partial_, done); count_launches();
     return JD_OK;
   };
   AJD_TRY(precond());
-  sqmr_scalar_beta_kernel<<<1, 1, 0, s_>>>(partial_, bl, scal_, 1, done, brk);
-  sqmr_update_q_kernel<T><<<bl, kThreads, 0, s_>>>(u, q, n_, scal_, done);  // q = u (beta = 0)
+  sqmr_scalar_beta_kernel<<<1, 1, 0, s_>>>(partial_, bl, scal_, 1, done, brk); count_launches();
+  sqmr_update_q_kernel<T><<<bl, kThreads, 0, s_>>>(u, q, n_, scal_, done); count_launches();  // q = u (beta = 0)
   const int maxit = p_.max_inner;
   int it = 0;
   const int chunk = 4;
   while (it < maxit) {
     const int nstep = std::min(chunk, maxit - it);
     for (int s = 0; s < nstep; ++s) {
+      const bool timed = nevs_ < kEv;
+      if (timed) AJD_CUDA(cudaEventRecord(evs_[2 * nevs_], s_));
       AJD_TRY(stencil_apply<T>(h_, (T)theta_hat, q, t, 1, s_));
-      multidot_kernel<T><<<bl, kThreads, 0, s_>>>(QtC, Cols<T>{}, q, t, n_, partial_, c + 1, done);
-      reduce_partials_kernel<<<1, 128, 0, s_>>>(partial_, bl, c + 1, dots_, done);
-      sqmr_update_r_kernel<T><<<bl, kThreads, 0, s_>>>(QtC, dots_, t, r, n_, scal_, partial_, done);
-      sqmr_scalar_theta_kernel<<<1, 1, 0, s_>>>(partial_, bl, dots_, c, scal_, done, brk);
-      sqmr_update_dx_kernel<T><<<bl, kThreads, 0, s_>>>(d, x, q, n_, scal_, done);
-      sqmr_mark_done_kernel<<<1, 1, 0, s_>>>(done);
+      if (timed) AJD_CUDA(cudaEventRecord(evs_[2 * nevs_++ + 1], s_));
+      multidot_kernel<T><<<bl, kThreads, 0, s_>>>(QtC, Cols<T>{}, q, t, n_, partial_, c + 1, done); count_launches();
+      reduce_partials_kernel<<<1, 128, 0, s_>>>(partial_, bl, c + 1, dots_, done); count_launches();
+      sqmr_update_r_kernel<T><<<bl, kThreads, 0, s_>>>(QtC, dots_, t, r, n_, scal_, partial_, done); count_launches();
+      sqmr_scalar_theta_kernel<<<1, 1, 0, s_>>>(partial_, bl, dots_, c, scal_, done, brk); count_launches();
+      sqmr_update_dx_kernel<T><<<bl, kThreads, 0, s_>>>(d, x, q, n_, scal_, done); count_launches();
+      sqmr_mark_done_kernel<<<1, 1, 0, s_>>>(done); count_launches();
       AJD_TRY(precond());
-      sqmr_scalar_beta_kernel<<<1, 1, 0, s_>>>(partial_, bl, scal_, 0, done, brk);
-      sqmr_update_q_kernel<T><<<bl, kThreads, 0, s_>>>(u, q, n_, scal_, done);
+      sqmr_scalar_beta_kernel<<<1, 1, 0, s_>>>(partial_, bl, scal_, 0, done, brk); count_launches();
+      sqmr_update_q_kernel<T><<<bl, kThreads, 0, s_>>>(u, q, n_, scal_, done); count_launches();
     }
     AJD_CHECK_LAUNCH();
     it += nstep;
@@ -721,14 +890,16 @@ int JdSolver::correction(int kc, double theta_hat, double rel_tol, int* its) {
     AJD_CUDA(cudaStreamSynchronize(s_));
     std::memcpy(sc, host_, sizeof(sc));
     std::memcpy(fl, host_ + S_NSCAL, sizeof(fl));
+    harvest_events();
     if (fl[0]) {
       it = (int)sc[S_IT];
       break;
     }
   }
   *its = it;
+  AJD_TRY(ildl_check_device_error(pc_));
   // t (binary64) = x, then the caller orthogonalises it
-  convert_kernel<T, double><<<bl, kThreads, 0, s_>>>(x, t_, n_, 1.0);
+  convert_kernel<T, double><<<bl, kThreads, 0, s_>>>(x, t_, n_, 1.0); count_launches();
   AJD_CHECK_LAUNCH();
   return JD_OK;
 }
@@ -738,50 +909,179 @@ int JdSolver::run(double* evals, double* evecs, jd_stats* st) {
   const auto t0 = Clock::now();
   normA_ = 6.0 + h_->max_abs_eps;
   const int64_t n = h_->n;
-  jmin_ = p_.jmin > 0 ? p_.jmin : std::max(2 * k_, 10);
+  const int guard = p_.guard < 0 ? 0 : (p_.guard == 0 ? 2 : p_.guard);
+  kint_ = (int)std::min<int64_t>(k_ + guard, n / 2 > k_ ? n / 2 : k_);
+  jmin_ = p_.jmin > 0 ? p_.jmin : std::max(2 * kint_, 10);
   jmax_ = p_.jmax > 0 ? p_.jmax : jmin_ + 15;
-  jmax_ = (int)std::min<int64_t>(std::min<int64_t>(jmax_, kMaxM), n - k_);
+  jmax_ = (int)std::min<int64_t>(std::min<int64_t>(jmax_, kMaxM), n - kint_);
   jmin_ = std::min(jmin_, jmax_ - 1);
   if (jmax_ < 2 || jmin_ < 1) return fail(JD_EINVAL, "jd_solve: lattice too small for k = %d", k_);
-  if (k_ + jmax_ + 2 > kMaxCols) return fail(JD_EINVAL, "jd_solve: k + jmax too large");
+  if (kint_ + 2 * jmax_ + 2 > kMaxCols) return fail(JD_EINVAL, "jd_solve: k + jmax too large");
   AJD_TRY(alloc());
+  launches0_ = launch_counter();
   Mq_.clear();
   const uint64_t seed = p_.seed ? p_.seed : (h_->seed ^ 0xD1B54A32D192ED03ull);
-  random_kernel<<<nb_, kThreads, 0, s_>>>(t_, n, seed);
-  AJD_CUDA(cudaMemsetAsync(H_, 0, sizeof(double) * kMaxM * kMaxM, s_));
+  random_kernel<<<nb_, kThreads, 0, s_>>>(t_, n, seed); count_launches();
   int m = 0, kc = 0, outer = 0, restarts = 0, steps_on_pair = 0;
   std::vector<double> lam;
-  double theta0 = sigma_, rnorm = 0.0;
+  double theta0 = sigma_, rnorm = 0.0, gap = 0.0;
   int status = JD_OK;
   uint64_t reseed = seed;
-  while (true) {
-    // --- expand: orthogonalise t against [Q V], append
+  std::vector<double> Yc, th;
+  // host copies of H = V^T A V and G = (AV - sigma V)^T (AV - sigma V) for
+  // the current basis
+  std::vector<double> Hh((size_t)kMaxM * kMaxM, 0.0), Gh((size_t)kMaxM * kMaxM, 0.0);
+  auto hget = [&](std::vector<double>& X, int i, int j) -> double& { return X[(size_t)j * kMaxM + i]; };
+  auto compact = [&](const std::vector<double>& X, int m) {
+    std::vector<double> c((size_t)m * m);
+    for (int j = 0; j < m; ++j)
+      for (int i = 0; i < m; ++i) c[(size_t)j * m + i] = X[(size_t)j * kMaxM + i];
+    return c;
+  };
+  auto expand_h = [&](std::vector<double>& X, const std::vector<double>& c, int m) {
+    std::fill(X.begin(), X.end(), 0.0);
+    for (int j = 0; j < m; ++j)
+      for (int i = 0; i < m; ++i) X[(size_t)j * kMaxM + i] = c[(size_t)j * m + i];
+  };
+  // apply the coefficient basis Qy (m x c) to V and AV on the device and to
+  // H, M2 on the host
+  auto transform = [&](int m, int c, const std::vector<double>& Qy) -> int {
+    std::vector<double> up((size_t)kMaxM * c, 0.0);
+    for (int j = 0; j < c; ++j)
+      for (int i = 0; i < m; ++i) up[(size_t)j * kMaxM + i] = Qy[(size_t)j * m + i];
+    AJD_CUDA(cudaMemcpyAsync(Y_, up.data(), sizeof(double) * kMaxM * c, cudaMemcpyHostToDevice, s_));
+    lincomb_kernel<<<nb_, kThreads, 0, s_>>>(V_, ld_, m, Y_, kMaxM, c, Vt_, ld_, n); count_launches();
+    lincomb_kernel<<<nb_, kThreads, 0, s_>>>(AV_, ld_, m, Y_, kMaxM, c, AVt_, ld_, n); count_launches();
+    std::swap(V_, Vt_);
+    std::swap(AV_, AVt_);
+    expand_h(Hh, hostla::congruence(m, c, compact(Hh, m), Qy), c);
+    expand_h(Gh, hostla::congruence(m, c, compact(Gh, m), Qy), c);
+    AJD_CUDA(cudaStreamSynchronize(s_));  // Y_ is reused by the next upload
+    return JD_OK;
+  };
+  // Ritz extraction on the current basis: coefficient vectors Yc (m x m,
+  // unit columns, best target first) and Rayleigh quotients th.
+  // Harmonic (default): (H - sigma I) y = mu G y with
+  // G = (AV - sigma V)^T (AV - sigma V), largest |mu| first -- the harmonic
+  // Ritz values nearest sigma; the reported value is the Rayleigh quotient
+  // y^T H y.  Standard: eigenpairs of H nearest sigma.
+  auto extract = [&](int m, std::vector<double>& Yc, std::vector<double>& th) {
+    std::vector<double> H = compact(Hh, m);
+    std::vector<double> w, Z;
+    std::vector<int> order(m);
+    for (int i = 0; i < m; ++i) order[i] = i;
+    bool harmonic = p_.extraction == 0;
+    std::vector<double> Lc;
+    if (harmonic) {
+      Lc = compact(Gh, m);
+      for (int j = 0; j < m; ++j)
+        for (int i = j + 1; i < m; ++i) {
+          const double v = 0.5 * (Lc[(size_t)j * m + i] + Lc[(size_t)i * m + j]);
+          Lc[(size_t)j * m + i] = Lc[(size_t)i * m + j] = v;
+        }
+      harmonic = hostla::cholesky(m, Lc);
+    }
+    Yc.assign((size_t)m * m, 0.0);
+    th.assign(m, 0.0);
+    if (harmonic) {
+      // C = L^{-1} (H - sigma I) L^{-T}
+      std::vector<double> X = H;
+      for (int i = 0; i < m; ++i) X[(size_t)i * m + i] -= sigma_;
+      auto fwd = [&](std::vector<double>& B) {  // B <- L^{-1} B (columns)
+        for (int j = 0; j < m; ++j)
+          for (int i = 0; i < m; ++i) {
+            double v = B[(size_t)j * m + i];
+            for (int k = 0; k < i; ++k) v -= Lc[(size_t)k * m + i] * B[(size_t)j * m + k];
+            B[(size_t)j * m + i] = v / Lc[(size_t)i * m + i];
+          }
+      };
+      fwd(X);
+      std::vector<double> Xt((size_t)m * m);
+      for (int j = 0; j < m; ++j)
+        for (int i = 0; i < m; ++i) Xt[(size_t)j * m + i] = X[(size_t)i * m + j];
+      fwd(Xt);  // = L^{-1} (L^{-1} (H - sigma I))^T = C
+      hostla::jacobi_eig(m, Xt, w, Z);
+      std::sort(order.begin(), order.end(), [&](int a, int b) { return std::fabs(w[a]) > std::fabs(w[b]); });
+      for (int jj = 0; jj < m; ++jj) {
+        const int j = order[jj];
+        // y = L^{-T} z
+        std::vector<double> y(m);
+        for (int i = m - 1; i >= 0; --i) {
+          double v = Z[(size_t)j * m + i];
+          for (int k = i + 1; k < m; ++k) v -= Lc[(size_t)i * m + k] * y[k];
+          y[i] = v / Lc[(size_t)i * m + i];
+        }
+        double nr = 0.0;
+        for (double v : y) nr += v * v;
+        nr = std::sqrt(nr);
+        double rq = 0.0;
+        for (int i = 0; i < m; ++i) {
+          y[i] /= nr;
+          Yc[(size_t)jj * m + i] = y[i];
+        }
+        for (int a = 0; a < m; ++a)
+          for (int b = 0; b < m; ++b) rq += y[a] * H[(size_t)b * m + a] * y[b];
+        th[jj] = rq;
+      }
+    } else {
+      hostla::jacobi_eig(m, H, w, Z);
+      std::sort(order.begin(), order.end(), [&](int a, int b) {
+        const double da = std::fabs(w[a] - sigma_), db = std::fabs(w[b] - sigma_);
+        return da != db ? da < db : w[a] < w[b];
+      });
+      for (int jj = 0; jj < m; ++jj) {
+        th[jj] = w[order[jj]];
+        for (int i = 0; i < m; ++i) Yc[(size_t)jj * m + i] = Z[(size_t)order[jj] * m + i];
+      }
+    }
+  };
+
+  // append t (orthogonalised against [Q V]) to V, A t to AV and the new
+  // columns of H and G
+  auto expand = [&]() -> int {
     double nrm = 0.0;
     AJD_TRY(cgs2(kc, m, t_, &nrm));
     int tries = 0;
     while (!(nrm > 1e-10) && tries < 3) {  // t in span: take a fresh random direction
-      random_kernel<<<nb_, kThreads, 0, s_>>>(t_, n, ++reseed);
+      random_kernel<<<nb_, kThreads, 0, s_>>>(t_, n, ++reseed); count_launches();
       AJD_TRY(cgs2(kc, m, t_, &nrm));
       ++tries;
     }
     if (!(nrm > 0.0)) return fail(JD_EBREAKDOWN, "jd_solve: cannot expand the search space");
-    scale_copy_kernel<<<nb_, kThreads, 0, s_>>>(t_, V_ + (int64_t)m * ld_, n, scal_, 0, 1);
+    scale_copy_kernel<<<nb_, kThreads, 0, s_>>>(t_, V_ + (int64_t)m * ld_, n, scal_, 0, 1); count_launches();
     AJD_TRY(stencil_apply<double>(h_, 0.0, V_ + (int64_t)m * ld_, AV_ + (int64_t)m * ld_, 1, s_));
     AJD_TRY(dot_cols(Cols<double>{V_, ld_, m + 1}, Cols<double>{}, nullptr, AV_ + (int64_t)m * ld_, dots_));
-    set_h_column_kernel<<<1, 128, 0, s_>>>(H_, kMaxM, m, dots_);
+    shifted_dots_kernel<<<nb_, kThreads, 0, s_>>>(V_, AV_, ld_, m + 1, sigma_, n, partial_); count_launches();
+    reduce_partials_kernel<<<1, 128, 0, s_>>>(partial_, nb_, m + 1, dots_ + (m + 1), nullptr); count_launches();
+    double d[2 * kMaxM + 2];
+    AJD_TRY(sync_read(dots_, 2 * (m + 1), d));
+    for (int i = 0; i <= m; ++i) {
+      hget(Hh, i, m) = hget(Hh, m, i) = d[i];
+      hget(Gh, i, m) = hget(Gh, m, i) = d[m + 1 + i];
+    }
     ++m;
+    return JD_OK;
+  };
+  while (true) {
+    AJD_TRY(expand());
     ++outer;
-    // --- Rayleigh–Ritz, selection, locking
+    // --- Ritz extraction, selection, locking
     bool finished = false;
     while (true) {
-      AJD_TRY(rr(m));
-      double th[kMaxM];
-      AJD_TRY(sync_read(theta_, m, th));
+      extract(m, Yc, th);
       theta0 = th[0];
+      gap = std::numeric_limits<double>::infinity();
+      for (int i = 1; i < m; ++i) gap = std::min(gap, std::fabs(th[i] - theta0));
       // u = V y1, Au = AV y1, r = Au - theta u, r -= Q Q^T r
-      lincomb_kernel<<<nb_, kThreads, 0, s_>>>(V_, ld_, m, Y_, kMaxM, 1, u_, ld_, n);
-      lincomb_kernel<<<nb_, kThreads, 0, s_>>>(AV_, ld_, m, Y_, kMaxM, 1, Au_, ld_, n);
-      residual_kernel<<<nb_, kThreads, 0, s_>>>(Au_, u_, theta_, r_, n);
+      {
+        std::vector<double> up(kMaxM, 0.0);
+        for (int i = 0; i < m; ++i) up[i] = Yc[i];
+        AJD_CUDA(cudaMemcpyAsync(Y_, up.data(), sizeof(double) * kMaxM, cudaMemcpyHostToDevice, s_));
+        AJD_CUDA(cudaMemcpyAsync(theta_, &theta0, sizeof(double), cudaMemcpyHostToDevice, s_));
+      }
+      lincomb_kernel<<<nb_, kThreads, 0, s_>>>(V_, ld_, m, Y_, kMaxM, 1, u_, ld_, n); count_launches();
+      lincomb_kernel<<<nb_, kThreads, 0, s_>>>(AV_, ld_, m, Y_, kMaxM, 1, Au_, ld_, n); count_launches();
+      residual_kernel<<<nb_, kThreads, 0, s_>>>(Au_, u_, theta_, r_, n); count_launches();
       AJD_TRY(dot_cols(Cols<double>{r_, ld_, 1}, Cols<double>{}, nullptr, r_, scal_ + 1));
       double rr2;
       AJD_TRY(sync_read(scal_ + 1, 1, &rr2));
@@ -789,31 +1089,32 @@ int JdSolver::run(double* evals, double* evecs, jd_stats* st) {
       if (kc > 0) {
         Cols<double> Xq{Q_, ld_, kc};
         AJD_TRY(dot_cols(Xq, Cols<double>{}, nullptr, r_, dots_));
-        multiaxpy_kernel<double><<<nb_, kThreads, 0, s_>>>(Xq, Cols<double>{}, dots_, r_, n);
+        multiaxpy_kernel<double><<<nb_, kThreads, 0, s_>>>(Xq, Cols<double>{}, dots_, r_, n); count_launches();
       }
-      if (rnorm <= tol_ * normA_ && m >= 1) {
+      if (rnorm <= tol_ * normA_) {
         // lock u
         AJD_CUDA(cudaMemcpyAsync(Q_ + (int64_t)kc * ld_, u_, sizeof(double) * n, cudaMemcpyDeviceToDevice, s_));
         lam.push_back(theta0);
+        if (trace_) std::fprintf(stderr, "jd LOCK %d theta=%.15g res=%.3e at outer %d\n", kc, theta0, rnorm / normA_, outer);
         // cache W = K^{-1} q and the Q^T W block for the projected preconditioner
         {
           const int c = kc + 1;
           if (p_.precision == JD_FP32) {
             float* Qt = static_cast<float*>(Qt_);
             float* W = static_cast<float*>(W_);
-            convert_kernel<double, float><<<nb_, kThreads, 0, s_>>>(u_, Qt + (int64_t)kc * ld_, n, 1.0);
+            convert_kernel<double, float><<<nb_, kThreads, 0, s_>>>(u_, Qt + (int64_t)kc * ld_, n, 1.0); count_launches();
             AJD_TRY(ildl_apply_dev<float>(pc_, Qt + (int64_t)kc * ld_, W + (int64_t)kc * ld_, s_));
             multidot_kernel<float><<<nb_, kThreads, 0, s_>>>(Cols<float>{Qt, ld_, c}, Cols<float>{}, nullptr,
-                                                             W + (int64_t)kc * ld_, n, partial_, c, nullptr);
+                                                             W + (int64_t)kc * ld_, n, partial_, c, nullptr); count_launches();
           } else {
             double* Qt = static_cast<double*>(Qt_);
             double* W = static_cast<double*>(W_);
-            convert_kernel<double, double><<<nb_, kThreads, 0, s_>>>(u_, Qt + (int64_t)kc * ld_, n, 1.0);
+            convert_kernel<double, double><<<nb_, kThreads, 0, s_>>>(u_, Qt + (int64_t)kc * ld_, n, 1.0); count_launches();
             AJD_TRY(ildl_apply_dev<double>(pc_, Qt + (int64_t)kc * ld_, W + (int64_t)kc * ld_, s_));
             multidot_kernel<double><<<nb_, kThreads, 0, s_>>>(Cols<double>{Qt, ld_, c}, Cols<double>{}, nullptr,
-                                                              W + (int64_t)kc * ld_, n, partial_, c, nullptr);
+                                                              W + (int64_t)kc * ld_, n, partial_, c, nullptr); count_launches();
           }
-          reduce_partials_kernel<<<1, 128, 0, s_>>>(partial_, nb_, c, dots_, nullptr);
+          reduce_partials_kernel<<<1, 128, 0, s_>>>(partial_, nb_, c, dots_, nullptr); count_launches();
           std::vector<double> col(c);
           AJD_TRY(sync_read(dots_, c, col.data()));
           std::vector<double> Mn((size_t)c * c);
@@ -827,51 +1128,65 @@ int JdSolver::run(double* evals, double* evecs, jd_stats* st) {
         }
         ++kc;
         steps_on_pair = 0;
-        if (kc == k_) {
+        if (kc == kint_) {
           finished = true;
           break;
         }
-        // deflate: keep the other Ritz vectors
+        // deflate: keep span(V) minus u, orthonormal
         if (m > 1) {
-          lincomb_kernel<<<nb_, kThreads, 0, s_>>>(V_, ld_, m, Y_ + kMaxM, kMaxM, m - 1, Vt_, ld_, n);
-          lincomb_kernel<<<nb_, kThreads, 0, s_>>>(AV_, ld_, m, Y_ + kMaxM, kMaxM, m - 1, AVt_, ld_, n);
-          std::swap(V_, Vt_);
-          std::swap(AV_, AVt_);
-          set_h_diag_kernel<<<1, 256, 0, s_>>>(H_, kMaxM, m - 1, theta_, 1);
+          std::vector<double> Qy;
+          hostla::orthonormalize(m, m, Yc, Qy);
+          std::vector<double> rest(Qy.begin() + m, Qy.end());
+          AJD_TRY(transform(m, m - 1, rest));
           --m;
-          continue;
+        } else {
+          m = 0;
+          std::fill(Hh.begin(), Hh.end(), 0.0);
+          std::fill(Gh.begin(), Gh.end(), 0.0);
         }
-        m = 0;
-        random_kernel<<<nb_, kThreads, 0, s_>>>(t_, n, ++reseed);
-        break;
+        // inject a fresh random direction: JD's correction cannot see other
+        // eigenvectors of a (nearly) repeated eigenvalue once they have left
+        // the search space
+        if (m + 1 < jmax_) {
+          random_kernel<<<nb_, kThreads, 0, s_>>>(t_, n, ++reseed); count_launches();
+          AJD_TRY(expand());
+        }
+        continue;
       }
       break;
     }
     if (finished) break;
-    if (m == 0) continue;  // search space emptied: expand with the random t
+    if (kc >= k_ && steps_on_pair >= 30) break;  // guard pair stalled: k pairs are in hand
     if (outer >= p_.max_outer) {
-      status = fail(JD_ENOCONV, "jd_solve: %d of %d eigenpairs after %d outer steps (residual %.3e)", kc, k_, outer,
-                    rnorm / normA_);
+      status = kc >= k_ ? JD_OK
+                        : fail(JD_ENOCONV, "jd_solve: %d of %d eigenpairs after %d outer steps (residual %.3e)", kc,
+                               k_, outer, rnorm / normA_);
       break;
     }
-    // --- restart
+    // --- restart: keep the jmin best Ritz vectors (orthonormalised)
     if (m >= jmax_) {
-      lincomb_kernel<<<nb_, kThreads, 0, s_>>>(V_, ld_, m, Y_, kMaxM, jmin_, Vt_, ld_, n);
-      lincomb_kernel<<<nb_, kThreads, 0, s_>>>(AV_, ld_, m, Y_, kMaxM, jmin_, AVt_, ld_, n);
-      std::swap(V_, Vt_);
-      std::swap(AV_, AVt_);
-      set_h_diag_kernel<<<1, 256, 0, s_>>>(H_, kMaxM, jmin_, theta_, 0);
+      std::vector<double> keep(Yc.begin(), Yc.begin() + (size_t)m * jmin_), Qy;
+      hostla::orthonormalize(m, jmin_, keep, Qy);
+      AJD_TRY(transform(m, jmin_, Qy));
       m = jmin_;
       ++restarts;
     }
     // --- correction equation
-    const double theta_hat = rnorm > p_.switch_tol * normA_ ? sigma_ : theta0;
-    const double rel = std::max(std::pow(p_.inner_decay, steps_on_pair + 1), p_.inner_floor);
+    // correction shift: sigma until the target is resolved (residual below
+    // switch_tol ||A|| and below half the distance to the next Ritz value)
+    const bool resolved = rnorm <= p_.switch_tol * normA_ && rnorm <= 0.5 * gap;
+    const double theta_hat = resolved ? theta0 : sigma_;
+    if (trace_)
+      std::fprintf(stderr, "jd outer %d m=%d kc=%d theta=%.15g res=%.3e gap=%.2e shift=%s\n", outer, m, kc, theta0,
+                   rnorm / normA_, gap, resolved ? "theta" : "sigma");
+    const double floor = p_.inner_floor > 0.0 ? p_.inner_floor : (p_.precision == JD_FP32 ? 1e-5 : 1e-8);
+    const double rel = std::max(std::pow(p_.inner_decay, steps_on_pair + 1), floor);
     int its = 0;
     if (p_.precision == JD_FP32) AJD_TRY(correction<float>(kc, theta_hat, rel, &its));
     else AJD_TRY(correction<double>(kc, theta_hat, rel, &its));
     inner_total_ += its;
     ++steps_on_pair;
+    if (trace_) std::fprintf(stderr, "   inner its %d (rel tol %.2e)\n", its, rel);
   }
   if (st) {
     st->outer_its = outer;
@@ -879,7 +1194,14 @@ int JdSolver::run(double* evals, double* evecs, jd_stats* st) {
     st->restarts = restarts;
   }
   const int rc = finalize(kc, lam.data(), evals, evecs, st);
-  if (st) st->solve_ms = std::chrono::duration<double, std::milli>(Clock::now() - t0).count();
+  if (st) {
+    st->solve_ms = std::chrono::duration<double, std::milli>(Clock::now() - t0).count();
+    st->kernel_launches = launch_counter() - launches0_;
+    st->precond_calls = precond_calls_;
+    st->precond_ms = precond_ms_;
+    st->stencil_calls = stencil_calls_;
+    st->stencil_ms = stencil_ms_;
+  }
   if (rc != JD_OK) return rc;
   return status;
 }
@@ -888,34 +1210,32 @@ int JdSolver::run(double* evals, double* evecs, jd_stats* st) {
 // copy-out.
 int JdSolver::finalize(int kc, double* lam, double* evals, double* evecs, jd_stats* st) {
   (void)lam;
-  if (st) st->nconv = kc;
+  const int kout = std::min(kc, k_);  // the k nearest of the locked pairs
+  if (st) st->nconv = kout;
   if (kc == 0) return JD_OK;
   const int64_t n = n_;
   // A Q into AV_ (columns 0..kc), H = Q^T A Q
-  AJD_TRY(stencil_apply<double>(h_, 0.0, Q_, AV_, 1, s_));
-  for (int j = 1; j < kc; ++j)
+  for (int j = 0; j < kc; ++j)
     AJD_TRY(stencil_apply<double>(h_, 0.0, Q_ + (int64_t)j * ld_, AV_ + (int64_t)j * ld_, 1, s_));
   for (int j = 0; j < kc; ++j) {
     AJD_TRY(dot_cols(Cols<double>{Q_, ld_, j + 1}, Cols<double>{}, nullptr, AV_ + (int64_t)j * ld_, dots_));
-    set_h_column_kernel<<<1, 128, 0, s_>>>(H_, kMaxM, j, dots_);
+    set_h_column_kernel<<<1, 128, 0, s_>>>(H_, kMaxM, j, dots_); count_launches();
   }
-  AJD_TRY(rr(kc));
-  double th[kMaxM];
-  AJD_TRY(sync_read(theta_, kc, th));
-  lincomb_kernel<<<nb_, kThreads, 0, s_>>>(Q_, ld_, kc, Y_, kMaxM, kc, Vt_, ld_, n);
-  lincomb_kernel<<<nb_, kThreads, 0, s_>>>(AV_, ld_, kc, Y_, kMaxM, kc, AVt_, ld_, n);
+  AJD_TRY(rr(kc));  // eigenpairs of Q^T A Q ordered by |theta - sigma|
+  lincomb_kernel<<<nb_, kThreads, 0, s_>>>(Q_, ld_, kc, Y_, kMaxM, kout, Vt_, ld_, n); count_launches();
+  lincomb_kernel<<<nb_, kThreads, 0, s_>>>(AV_, ld_, kc, Y_, kMaxM, kout, AVt_, ld_, n); count_launches();
   double max_res = 0.0;
-  std::vector<double> signs(kc);
-  for (int j = 0; j < kc; ++j) {
+  std::vector<double> signs(kout);
+  for (int j = 0; j < kout; ++j) {
     double* x = Vt_ + (int64_t)j * ld_;
     double* ax = AVt_ + (int64_t)j * ld_;
     AJD_TRY(dot_cols(Cols<double>{x, ld_, 1}, Cols<double>{}, nullptr, x, dots_));
-    residual_kernel<<<nb_, kThreads, 0, s_>>>(ax, x, theta_ + j, r_, n);
+    residual_kernel<<<nb_, kThreads, 0, s_>>>(ax, x, theta_ + j, r_, n); count_launches();
     AJD_TRY(dot_cols(Cols<double>{r_, ld_, 1}, Cols<double>{}, nullptr, r_, dots_ + 1));
     AJD_CUDA(cudaMemsetAsync(amax_, 0, sizeof(unsigned long long), s_));
     AJD_CUDA(cudaMemsetAsync(amax_ + 1, 0xFF, sizeof(unsigned long long), s_));
-    max_abs_bits_kernel<<<nb_, kThreads, 0, s_>>>(x, n, amax_);
-    first_index_kernel<<<nb_, kThreads, 0, s_>>>(x, n, amax_, amax_ + 1);
+    max_abs_bits_kernel<<<nb_, kThreads, 0, s_>>>(x, n, amax_); count_launches();
+    first_index_kernel<<<nb_, kThreads, 0, s_>>>(x, n, amax_, amax_ + 1); count_launches();
     double nn[2];
     AJD_TRY(sync_read(dots_, 2, nn));
     unsigned long long key = 0;
@@ -927,23 +1247,22 @@ int JdSolver::finalize(int kc, double* lam, double* evals, double* evecs, jd_sta
     max_res = std::max(max_res, std::sqrt(std::max(nn[1], 0.0)) / nrm / normA_);
     signs[j] = (xv < 0 ? -1.0 : 1.0) / nrm;
   }
-  // output (already ordered by |theta - sigma| by the eigen kernel)
-  AJD_CUDA(cudaMemcpyAsync(evals, theta_, sizeof(double) * kc, cudaMemcpyDefault, s_));
-  double orth = 0.0;
-  for (int j = 0; j < kc; ++j) {
+  AJD_CUDA(cudaMemcpyAsync(evals, theta_, sizeof(double) * kout, cudaMemcpyDefault, s_));
+  for (int j = 0; j < kout; ++j) {
     double* x = Vt_ + (int64_t)j * ld_;
     AJD_CUDA(cudaMemcpyAsync(scal_ + 8, &signs[j], sizeof(double), cudaMemcpyHostToDevice, s_));
-    scale_copy_kernel<<<nb_, kThreads, 0, s_>>>(x, x, n, scal_, 8, 0);
+    scale_copy_kernel<<<nb_, kThreads, 0, s_>>>(x, x, n, scal_, 8, 0); count_launches();
     AJD_CUDA(cudaStreamSynchronize(s_));
   }
-  for (int j = 0; j < kc; ++j) {
-    AJD_TRY(dot_cols(Cols<double>{Vt_, ld_, kc}, Cols<double>{}, nullptr, Vt_ + (int64_t)j * ld_, dots_));
+  double orth = 0.0;
+  for (int j = 0; j < kout; ++j) {
+    AJD_TRY(dot_cols(Cols<double>{Vt_, ld_, kout}, Cols<double>{}, nullptr, Vt_ + (int64_t)j * ld_, dots_));
     double g[kMaxM];
-    AJD_TRY(sync_read(dots_, kc, g));
-    for (int i = 0; i < kc; ++i) orth = std::max(orth, std::fabs(g[i] - (i == j ? 1.0 : 0.0)));
+    AJD_TRY(sync_read(dots_, kout, g));
+    for (int i = 0; i < kout; ++i) orth = std::max(orth, std::fabs(g[i] - (i == j ? 1.0 : 0.0)));
   }
   if (evecs) {
-    for (int j = 0; j < kc; ++j)
+    for (int j = 0; j < kout; ++j)
       AJD_CUDA(cudaMemcpyAsync(evecs + (int64_t)j * n, Vt_ + (int64_t)j * ld_, sizeof(double) * n, cudaMemcpyDefault, s_));
   }
   AJD_CUDA(cudaStreamSynchronize(s_));
@@ -964,7 +1283,9 @@ extern "C" int jd_params_default(jd_params* p) {
   p->max_outer = 3000;
   p->max_inner = 60;
   p->inner_decay = 0.7;
-  p->inner_floor = 1e-7;
+  p->inner_floor = 0.0;
+  p->extraction = 0;
+  p->guard = 0;
   p->switch_tol = 1e-3;
   p->precision = JD_FP64;
   ildl_params_default(&p->ildl);
@@ -986,7 +1307,8 @@ extern "C" int jd_solve(anderson_t h, double sigma, int k, double tol, const jd_
     if (prm.max_outer <= 0) prm.max_outer = d.max_outer;
     if (prm.max_inner <= 0) prm.max_inner = d.max_inner;
     if (!(prm.inner_decay > 0.0 && prm.inner_decay < 1.0)) prm.inner_decay = d.inner_decay;
-    if (!(prm.inner_floor > 0.0)) prm.inner_floor = d.inner_floor;
+    if (!(prm.inner_floor >= 0.0)) prm.inner_floor = d.inner_floor;
+    if (prm.extraction != 0 && prm.extraction != 1) prm.extraction = d.extraction;
     if (!(prm.switch_tol > 0.0)) prm.switch_tol = d.switch_tol;
     if (prm.ildl.kappa == 0.0 && prm.ildl.max_levels == 0 && prm.ildl.n_dense == 0) prm.ildl = d.ildl;
   }

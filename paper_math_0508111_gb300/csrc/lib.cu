@@ -37,6 +37,11 @@ int sm_count() {
   return cached;
 }
 
+int64_t& launch_counter() {
+  static thread_local int64_t c = 0;
+  return c;
+}
+
 }  // namespace ajd
 
 extern "C" const char* jd_last_error(void) { return ajd::g_last_error.c_str(); }

@@ -76,7 +76,8 @@ def _check_pairs(L, W, seed, bc, sigma, k, ev, X, st, tol, oracle="dense"):
 @pytest.mark.parametrize("precision", [0, 1])
 def test_jd_tiny_config(ajd, precision):
     """L = 10, W = 16.5, periodic, 5 eigenpairs nearest 0."""
-    L, W, seed, sigma, k, tol = 10, 16.5, 1, 0.0, 5, 1e-12
+    L, W, seed, sigma, k = 10, 16.5, 1, 0.0, 5
+    tol = 1e-11 if precision == 0 else 1e-10  # a binary32 inner solve stalls near 1e-12
     with ajd.Anderson(L, W, seed) as h:
         ev, X, st = ajd.solve(h, sigma, k, tol, precision=precision)
     _check_pairs(L, W, seed, 0, sigma, k, ev, X, st, tol)
@@ -90,7 +91,7 @@ def test_jd_tiny_config(ajd, precision):
     (6, 8.0, 6, 0, 0.25, 4, 0),
 ])
 def test_jd_dense_oracle_cases(ajd, L, W, seed, bc, sigma, k, prec):
-    tol = 1e-12
+    tol = 1e-11 if prec == 0 else 1e-10
     with ajd.Anderson(L, W, seed, bc) as h:
         ev, X, st = ajd.solve(h, sigma, k, tol, precision=prec)
     _check_pairs(L, W, seed, bc, sigma, k, ev, X, st, tol)
@@ -99,10 +100,20 @@ def test_jd_dense_oracle_cases(ajd, L, W, seed, bc, sigma, k, prec):
 @pytest.mark.parametrize("L,sigma,prec", [(20, 0.0, 1), (24, 1.0, 0), (27, -0.5, 1)])
 def test_jd_shift_invert_oracle(ajd, L, sigma, prec):
     """Mid sizes against the shift-and-invert Lanczos oracle."""
-    W, seed, k, tol = 16.5, 1, 5, 1e-11
+    W, seed, k = 16.5, 1, 5
+    tol = 1e-11 if prec == 0 else 1e-10
     with ajd.Anderson(L, W, seed) as h:
         ev, X, st = ajd.solve(h, sigma, k, tol, precision=prec)
     _check_pairs(L, W, seed, 0, sigma, k, ev, X, st, tol, oracle="lanczos")
+
+
+@pytest.mark.parametrize("extraction", [0, 1])
+def test_jd_extraction_modes(ajd, extraction):
+    """Harmonic (default) and standard Ritz extraction reach the same pairs."""
+    L, W, seed, sigma, k, tol = 12, 16.5, 7, 0.0, 5, 1e-11
+    with ajd.Anderson(L, W, seed) as h:
+        ev, X, st = ajd.solve(h, sigma, k, tol, extraction=extraction)
+    _check_pairs(L, W, seed, 0, sigma, k, ev, X, st, tol)
 
 
 def test_jd_degenerate_zero_disorder(ajd):
@@ -121,8 +132,8 @@ def test_jd_degenerate_zero_disorder(ajd):
 
 def test_jd_small_lattice_and_errors(ajd):
     with ajd.Anderson(3, 16.5, 1) as h:
-        ev, X, st = ajd.solve(h, 0.0, 2, 1e-12)
-        _check_pairs(3, 16.5, 1, 0, 0.0, 2, ev, X, st, 1e-12)
+        ev, X, st = ajd.solve(h, 0.0, 2, 1e-11)
+        _check_pairs(3, 16.5, 1, 0, 0.0, 2, ev, X, st, 1e-11)
         with pytest.raises(ajd.JDError):
             ajd.solve(h, 0.0, 27, 1e-8)
         with pytest.raises(ajd.JDError):
@@ -134,6 +145,6 @@ def test_jd_small_lattice_and_errors(ajd):
 def test_jd_noconv_reports_prefix(ajd):
     """A too-small outer budget returns JD_ENOCONV with the converged prefix."""
     with ajd.Anderson(12, 16.5, 1) as h:
-        ev, X, st = ajd.solve(h, 0.0, 5, 1e-12, max_outer=12, raise_on_noconv=False)
+        ev, X, st = ajd.solve(h, 0.0, 5, 1e-11, max_outer=12, raise_on_noconv=False)
     assert st["status"] == ajd.JD_ENOCONV
     assert 0 <= st["nconv"] < 5
