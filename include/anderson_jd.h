@@ -54,6 +54,8 @@ extern "C" {
 
 #define JD_FP64 0  /* arithmetic in binary64                                  */
 #define JD_FP32 1  /* arithmetic in binary32 (vectors and potential in FP32)  */
+#define JD_MIXED 2 /* jd_solve only: binary32 preconditioner application,
+                      binary64 everything else                                */
 
 /* Message of the last failing call on this thread ("" if none). */
 const char* jd_last_error(void);
@@ -147,7 +149,7 @@ typedef struct {
                      min(0.02, 5/sqrt(n)) [-1]                               */
   int max_levels; /* maximum number of sparse levels [256]                    */
   int n_dense;    /* the remaining Schur complement is factored densely once
-                     it has at most this many rows (at most 8000) [3000]                    */
+                     it has at most this many rows (at most 8000) [6000]                    */
   int matching;   /* 1: maximum-product matching, 1x1/2x2 cycle split and
                      symmetric dual scaling per level (Sections 5.1, 5.2);
                      0: row-max scaling and 1x1 pivots only [1]              */
@@ -254,12 +256,14 @@ typedef struct {
   double inner_decay; /* the correction equation is solved to relative
                          residual max(inner_decay^j, inner_floor), j = outer
                          steps spent on the current Ritz pair [0.7]            */
-  double inner_floor; /* [0 = 1e-8 for JD_FP64, 1e-5 for JD_FP32, the level a
-                         binary32 solve can still reach]                      */
+  double inner_floor; /* [0 = 1e-8 for JD_FP64, 1e-6 for JD_MIXED, 1e-5 for
+                         JD_FP32, the level a binary32 solve can still reach] */
   double switch_tol;  /* correction shift: sigma while ||r|| > switch_tol*||A||,
                          the Ritz value theta afterwards [1e-3]                */
-  int precision;      /* inner solve (stencil, preconditioner, SQMR) in
-                         JD_FP64 or JD_FP32; the outer residual, Ritz
+  int precision;      /* inner solve: JD_FP64 (all binary64), JD_FP32
+                         (stencil, preconditioner and SQMR in binary32) or
+                         JD_MIXED (preconditioner in binary32, SQMR vectors
+                         and stencil in binary64); the outer residual, Ritz
                          projection and orthogonalisation are always
                          binary64 [JD_FP64]                                   */
   uint64_t seed;      /* start vector seed (0 = derived from the lattice seed)*/

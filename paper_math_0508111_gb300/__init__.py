@@ -12,9 +12,9 @@ import numpy as np
 
 from . import _ffi
 from ._ffi import (JD_EBREAKDOWN, JD_EDEVICE, JD_EINVAL, JD_ENOCONV, JD_ENOMEM, JD_ESETUP, JD_FP32,
-                   JD_FP64, JD_HARDWALL, JD_OK, JD_PERIODIC, JDError)
+                   JD_FP64, JD_HARDWALL, JD_MIXED, JD_OK, JD_PERIODIC, JDError)
 
-__all__ = ["Anderson", "Preconditioner", "ildl_params", "jd_params", "solve", "JDError", "JD_PERIODIC", "JD_HARDWALL", "JD_FP64", "JD_FP32", "library_path"]
+__all__ = ["Anderson", "Preconditioner", "ildl_params", "jd_params", "solve", "JDError", "JD_PERIODIC", "JD_HARDWALL", "JD_FP64", "JD_FP32", "JD_MIXED", "library_path"]
 
 
 def library_path():

@@ -15,7 +15,7 @@ P = ctypes.POINTER
 
 JD_OK, JD_EINVAL, JD_ENOMEM, JD_ENOCONV, JD_EBREAKDOWN, JD_EDEVICE, JD_ESETUP = 0, -1, -2, -3, -4, -5, -6
 JD_PERIODIC, JD_HARDWALL = 0, 1
-JD_FP64, JD_FP32 = 0, 1
+JD_FP64, JD_FP32, JD_MIXED = 0, 1, 2
 
 ERROR_NAMES = {JD_EINVAL: "JD_EINVAL", JD_ENOMEM: "JD_ENOMEM", JD_ENOCONV: "JD_ENOCONV",
                JD_EBREAKDOWN: "JD_EBREAKDOWN", JD_EDEVICE: "JD_EDEVICE", JD_ESETUP: "JD_ESETUP"}

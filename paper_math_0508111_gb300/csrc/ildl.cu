@@ -15,6 +15,8 @@
 #include <chrono>
 #include <cmath>
 #include <new>
+#include <cstdio>
+#include <cstdlib>
 
 #include "anderson_impl.cuh"
 #include "ildl_impl.cuh"
@@ -185,19 +187,29 @@ __global__ void gj_save_col_kernel(const double* __restrict__ A, int m, int c, d
   for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < m; r += gridDim.x * blockDim.x) f[r] = A[(int64_t)r * m + c];
 }
 
-// rows r != c: A[r][k] -= f[r] A[c][k] (k > c; A[r][c] = 0), X[r][k] -= f[r] X[c][k]
-// (flattened grid-stride loop over all (r, k))
+// rows r != c: A[r][k] -= f[r] A[c][k] for k > c (A[r][c] becomes 0) and
+// X[r][k] -= f[r] X[c][k] for all k.  Columns k < c of A are unit columns
+// untouched by the (row >= c) swaps, so they are skipped; X is updated in
+// full because row swaps move entries into its later columns.
+// (flattened grid-stride loop over all (r, j), j < 2m - c)
 __global__ void gj_eliminate_kernel(double* __restrict__ A, double* __restrict__ X, int m, int c,
                                     const double* __restrict__ f) {
-  const int64_t total = (int64_t)m * m;
+  const int64_t w = (int64_t)(m - c) + m;
+  const int64_t total = (int64_t)m * w;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
-    const int r = (int)(t / m), k = (int)(t - (int64_t)r * m);
+    const int r = (int)(t / w);
+    const int j = (int)(t - (int64_t)r * w);
     if (r == c) continue;
     const double fr = f[r];
     if (fr == 0.0) continue;
-    if (k > c) A[t] -= fr * A[(int64_t)c * m + k];
-    else if (k == c) A[t] = 0.0;
-    X[t] -= fr * X[(int64_t)c * m + k];
+    if (j < m - c) {  // A columns c .. m-1
+      const int k = c + j;
+      if (k == c) A[(int64_t)r * m + k] = 0.0;
+      else A[(int64_t)r * m + k] -= fr * A[(int64_t)c * m + k];
+    } else {          // X columns 0 .. m-1
+      const int k = j - (m - c);
+      X[(int64_t)r * m + k] -= fr * X[(int64_t)c * m + k];
+    }
   }
 }
 
@@ -255,21 +267,31 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
   return v;
 }
 
-__device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned target, int* err) {
+// Grid barrier number `ph` (0-based) of one apply: every CTA adds one
+// arrival to `count`; the last arrival of this barrier publishes generation
+// ph + 1 in `gen` (a different cache line), which the other CTAs poll.  Polls
+// are bounded: after kSpinLimit of them the CTA records a timeout in `err`
+// and the whole apply returns early.
+__device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned* gen, unsigned ph, int* err) {
+  (void)gen;
   __syncthreads();
   __shared__ int failed;
   if (threadIdx.x == 0) {
-    __threadfence();
-    atomicAdd(count, 1u);
-    unsigned spins = 0;
     int f = 0;
+    // release-add: this CTA's writes (ordered by the CTA barrier above)
+    // become visible before its arrival is counted
+    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(count) : "memory");
+    const unsigned target = (ph + 1) * gridDim.x;
+    unsigned spins = 0;
     while (ld_acquire_u32(count) < target) {
-      if (++spins > kSpinLimit || *((volatile int*)err)) {
+      ++spins;
+      if ((spins & 1023u) == 0 && *((volatile int*)err)) { f = 1; break; }
+      if (spins > kSpinLimit) {
         atomicExch(err, 1);
         f = 1;
         break;
       }
-      __nanosleep(64);
+      if (spins > 64) __nanosleep(32);
     }
     failed = f;
   }
@@ -277,6 +299,27 @@ __device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned target, i
   return failed == 0;
 }
 
+template <typename T, int G>
+__device__ __forceinline__ void finish_row(const ApplyArgs<T>& a, int kind, int p, T acc, int lane, T rhs) {
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, G);
+  if (p >= 0 && lane == 0) {
+    if (kind == PH_FWD) {
+      __stcg(a.w + p, rhs - acc);  // rhs = s[p] b[perm[p]], stored in w by the gather phase
+    } else {
+      const int pp = __ldg(a.partner + p);
+      T d = __ldg(a.dd + p) * __ldcg(a.w + p);
+      if (pp >= 0) d += __ldg(a.dof + p) * __ldcg(a.w + pp);
+      const T zp = d - acc;
+      __stcg(a.z + p, zp);
+      a.out[__ldg(a.perm + p)] = __ldg(a.scale + p) * zp;
+    }
+  }
+}
+
+// Rows of one level, G threads per row; each group handles two rows at a
+// time with their loads interleaved (index/value loads of both rows first,
+// then the gathers), so every memory latency is shared by two rows.
 template <typename T, int G>
 __device__ __forceinline__ void level_rows(const ApplyArgs<T>& a, int kind, int p0, int p1) {
   const int lane = threadIdx.x % G;
@@ -286,48 +329,86 @@ __device__ __forceinline__ void level_rows(const ApplyArgs<T>& a, int kind, int 
   const int* col = kind == PH_FWD ? a.Lcol : a.Ucol;
   const T* val = kind == PH_FWD ? a.Lval : a.Uval;
   const T* x = kind == PH_FWD ? a.w : a.z;  // vector read through the columns
-  for (int64_t base = p0; base < p1; base += groups) {
-    const int64_t pr = base + g0;
-    const bool active = pr < p1;
-    const int p = (int)pr;
-    T acc = T(0);
-    if (active) {
-      const int e = __ldg(ptr + p + 1);
-      int q = __ldg(ptr + p) + lane;
-      T a1 = T(0), a2 = T(0), a3 = T(0);
-      for (; q + 3 * G < e; q += 4 * G) {
-        acc += __ldg(val + q) * __ldcg(x + __ldg(col + q));
-        a1 += __ldg(val + q + G) * __ldcg(x + __ldg(col + q + G));
-        a2 += __ldg(val + q + 2 * G) * __ldcg(x + __ldg(col + q + 2 * G));
-        a3 += __ldg(val + q + 3 * G) * __ldcg(x + __ldg(col + q + 3 * G));
-      }
-      for (; q < e; q += G) acc += __ldg(val + q) * __ldcg(x + __ldg(col + q));
-      acc = (acc + a1) + (a2 + a3);
+  constexpr int B = G >= 32 ? 8 : 4;          // entries per lane and row per batch
+  for (int64_t base = p0; base < p1; base += 2 * groups) {
+    const int64_t ra = base + g0, rb = base + groups + g0;
+    const int pa = ra < p1 ? (int)ra : -1;
+    const int pb = rb < p1 ? (int)rb : -1;
+    int qa = 0, ea = 0, qb = 0, eb = 0;
+    T ra_rhs = T(0), rb_rhs = T(0);
+    if (pa >= 0) {
+      qa = __ldg(ptr + pa) + lane;
+      ea = __ldg(ptr + pa + 1);
+      if (kind == PH_FWD && lane == 0) ra_rhs = __ldcg(a.w + pa);
     }
+    if (pb >= 0) {
+      qb = __ldg(ptr + pb) + lane;
+      eb = __ldg(ptr + pb + 1);
+      if (kind == PH_FWD && lane == 0) rb_rhs = __ldcg(a.w + pb);
+    }
+    T acca = T(0), accb = T(0);
+    while (qa < ea || qb < eb) {
+      int ca[B], cb[B];
+      T va[B], vb[B];
 #pragma unroll
-    for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, G);
-    if (active && lane == 0) {
-      if (kind == PH_FWD) {
-        __stcg(a.w + p, __ldg(a.scale + p) * __ldg(a.b + __ldg(a.perm + p)) - acc);
-      } else {
-        const int pp = __ldg(a.partner + p);
-        T d = __ldg(a.dd + p) * __ldcg(a.w + p);
-        if (pp >= 0) d += __ldg(a.dof + p) * __ldcg(a.w + pp);
-        const T zp = d - acc;
-        __stcg(a.z + p, zp);
-        a.out[__ldg(a.perm + p)] = __ldg(a.scale + p) * zp;
+      for (int i = 0; i < B; ++i) {
+        const int q1 = qa + i * G, q2 = qb + i * G;
+        const bool o1 = q1 < ea, o2 = q2 < eb;
+        ca[i] = o1 ? __ldg(col + q1) : 0;
+        va[i] = o1 ? __ldg(val + q1) : T(0);
+        cb[i] = o2 ? __ldg(col + q2) : 0;
+        vb[i] = o2 ? __ldg(val + q2) : T(0);
       }
+#pragma unroll
+      for (int i = 0; i < B; ++i) {
+        acca += va[i] * __ldcg(x + ca[i]);
+        accb += vb[i] * __ldcg(x + cb[i]);
+      }
+      qa += B * G;
+      qb += B * G;
     }
+    finish_row<T, G>(a, kind, pa, acca, lane, ra_rhs);
+    finish_row<T, G>(a, kind, pb, accb, lane, rb_rhs);
+  }
+}
+
+// Prefetch the stored rows of a level phase into L2 (lines strided over the
+// whole grid); skipped for phases larger than 16 MB, which stream from HBM
+// at full bandwidth anyway.
+template <typename T>
+__device__ __forceinline__ void prefetch_phase(const ApplyArgs<T>& a, int4 P) {
+  if (P.x != PH_FWD && P.x != PH_BWD) return;
+  const int* ptr = P.x == PH_FWD ? a.Lptr : a.Uptr;
+  const int* col = P.x == PH_FWD ? a.Lcol : a.Ucol;
+  const T* val = P.x == PH_FWD ? a.Lval : a.Uval;
+  const int64_t q0 = __ldg(ptr + P.y), q1 = __ldg(ptr + P.z);
+  const int64_t bytes = (q1 - q0) * (int64_t)(sizeof(T) + sizeof(int));
+  if (bytes > (16ll << 20) || q1 <= q0) return;
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t nth = (int64_t)gridDim.x * blockDim.x;
+  const int64_t lines_v = ((q1 - q0) * (int64_t)sizeof(T) + 127) / 128;
+  const int64_t lines_c = ((q1 - q0) * (int64_t)sizeof(int) + 127) / 128;
+  const char* vb = reinterpret_cast<const char*>(val + q0);
+  const char* cb = reinterpret_cast<const char*>(col + q0);
+  for (int64_t l = tid; l < lines_v + lines_c; l += nth) {
+    const char* addr = l < lines_v ? vb + l * 128 : cb + (l - lines_v) * 128;
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(addr));
   }
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kPersistThreads)
+__global__ void __launch_bounds__(kPersistThreads, 1)
 ildl_apply_persistent_kernel(ApplyArgs<T> a, const int4* __restrict__ phases, int nphase, unsigned* count,
-                             int* err) {
+                             unsigned* gen, int* err, unsigned long long* stamps) {
   for (int ph = 0; ph < nphase; ++ph) {
     const int4 P = phases[ph];  // kind, p0, p1, G
     const int kind = P.x, p0 = P.y, p1 = P.z, G = P.w;
+    if (stamps && blockIdx.x == 0 && threadIdx.x == 0) {
+      unsigned long long t;
+      asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+      stamps[ph] = t;
+    }
+    const int4 Pn = ph + 1 < nphase ? phases[ph + 1] : make_int4(-1, 0, 0, 0);
     if (kind == PH_GATHER) {
       for (int p = p0 + blockIdx.x * blockDim.x + threadIdx.x; p < p1; p += gridDim.x * blockDim.x)
         __stcg(a.w + p, __ldg(a.scale + p) * __ldg(a.b + __ldg(a.perm + p)));
@@ -336,14 +417,19 @@ ildl_apply_persistent_kernel(ApplyArgs<T> a, const int4* __restrict__ phases, in
       const int warps = (gridDim.x * blockDim.x) >> 5;
       for (int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < a.nd; r += warps) {
         const T* row = a.dense + (int64_t)r * a.nd;
-        T acc = T(0), a1 = T(0);
-        int c = lane;
-        for (; c + 32 < a.nd; c += 64) {
-          acc += __ldg(row + c) * __ldcg(a.w + a.d0 + c);
-          a1 += __ldg(row + c + 32) * __ldcg(a.w + a.d0 + c + 32);
+        T acc = T(0);
+        for (int c0 = lane; c0 < a.nd; c0 += 8 * 32) {
+          T rv[8], wv[8];
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            const int c = c0 + 32 * i;
+            const bool ok = c < a.nd;
+            rv[i] = ok ? __ldg(row + c) : T(0);
+            wv[i] = ok ? __ldcg(a.w + a.d0 + c) : T(0);
+          }
+#pragma unroll
+          for (int i = 0; i < 8; ++i) acc += rv[i] * wv[i];
         }
-        for (; c < a.nd; c += 32) acc += __ldg(row + c) * __ldcg(a.w + a.d0 + c);
-        acc += a1;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
         if (lane == 0) {
@@ -359,7 +445,13 @@ ildl_apply_persistent_kernel(ApplyArgs<T> a, const int4* __restrict__ phases, in
         default: level_rows<T, 32>(a, kind, p0, p1); break;
       }
     }
-    if (ph + 1 < nphase && !grid_barrier(count, (unsigned)(ph + 1) * gridDim.x, err)) return;
+    if (ph + 1 < nphase) prefetch_phase<T>(a, Pn);
+    if (ph + 1 < nphase && !grid_barrier(count, gen, (unsigned)ph, err)) return;
+  }
+  if (stamps && blockIdx.x == 0 && threadIdx.x == 0) {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    stamps[nphase] = t;
   }
 }
 
@@ -418,7 +510,9 @@ int upload_factor(const HostFactor& F, DevFactor<T>& d) {
   const std::vector<int>& lvp = F.level_ptr;
   const int nl = F.nlev;
   auto pick_g = [](double avg) { return avg > 48 ? 32 : avg > 16 ? 16 : avg > 6 ? 8 : 4; };
-  if (lvp[1] > lvp[0]) ph.push_back(make_int4(PH_GATHER, lvp[0], lvp[1], 1));
+  // the gather phase writes s[p] b[perm[p]] into w for every position; level
+  // 0 rows are then final and later rows read their right-hand side from w
+  ph.push_back(make_int4(PH_GATHER, 0, F.n, 1));
   for (int l = 1; l <= nl; ++l) {
     const int p0 = lvp[l], p1 = lvp[l + 1];
     if (p1 <= p0) continue;
@@ -435,11 +529,14 @@ int upload_factor(const HostFactor& F, DevFactor<T>& d) {
   d.nphase = (int)ph.size();
   AJD_CUDA(cudaMalloc(&d.phases, std::max<size_t>(1, ph.size()) * sizeof(int4)));
   if (!ph.empty()) AJD_CUDA(cudaMemcpy(d.phases, ph.data(), ph.size() * sizeof(int4), cudaMemcpyHostToDevice));
-  AJD_CUDA(cudaMalloc(&d.bar, 2 * sizeof(unsigned)));
-  AJD_CUDA(cudaMemset(d.bar, 0, 2 * sizeof(unsigned)));
+  // barrier words on separate 128-byte lines: [0] arrivals, [32] generation,
+  // [64] timeout flag
+  AJD_CUDA(cudaMalloc(&d.bar, 96 * sizeof(unsigned)));
+  AJD_CUDA(cudaMemset(d.bar, 0, 96 * sizeof(unsigned)));
   int per_sm = 0;
   AJD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ildl_apply_persistent_kernel<T>, kPersistThreads, 0));
-  d.grid = std::max(1, std::min(per_sm, 2) * sm_count());
+  if (per_sm < 1) return fail(JD_EDEVICE, "ildl: persistent apply kernel cannot be resident");
+  d.grid = sm_count();  // one CTA per SM
   d.ready = true;
   return JD_OK;
 }
@@ -471,15 +568,41 @@ int ildl_apply_dev(const ildl_s* f, const T* b, T* out, cudaStream_t s) {
   if (F.n == 0 || d.nphase == 0) return JD_OK;
   ApplyArgs<T> a{d.perm, d.scale, d.Lptr, d.Lcol, d.Lval, d.Uptr, d.Ucol, d.Uval, d.dd, d.dof, d.partner,
                  d.dense, d.w, d.z, b, out, F.n_dense, F.level_ptr[F.nlev]};
-  AJD_CUDA(cudaMemsetAsync(d.bar, 0, sizeof(unsigned), s));
+  AJD_CUDA(cudaMemsetAsync(d.bar, 0, 64 * sizeof(unsigned), s));  // arrivals and generation
   const int4* ph = d.phases;
   int np = d.nphase;
   unsigned* cnt = d.bar;
-  int* err = reinterpret_cast<int*>(d.bar + 1);
-  void* args[] = {&a, &ph, &np, &cnt, &err};
+  unsigned* gen = d.bar + 32;
+  int* err = reinterpret_cast<int*>(d.bar + 64);
+  // AJD_APPLY_TIMING=1: record the start of every phase (globaltimer, CTA 0)
+  // and print a per-kind summary of the next apply to stderr (diagnostics)
+  static const bool timing = std::getenv("AJD_APPLY_TIMING") != nullptr;
+  unsigned long long* stamps = nullptr;
+  if (timing) AJD_CUDA(cudaMalloc(&stamps, (np + 1) * sizeof(unsigned long long)));
+  void* args[] = {&a, &ph, &np, &cnt, &gen, &err, &stamps};
   AJD_CUDA(cudaLaunchCooperativeKernel((void*)ildl_apply_persistent_kernel<T>, dim3(d.grid), dim3(kPersistThreads),
                                        args, 0, s));
   count_launches(2);
+  if (timing) {
+    std::vector<unsigned long long> t(np + 1);
+    std::vector<int4> phs(np);
+    AJD_CUDA(cudaMemcpyAsync(t.data(), stamps, (np + 1) * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+    AJD_CUDA(cudaMemcpyAsync(phs.data(), d.phases, np * sizeof(int4), cudaMemcpyDeviceToHost, s));
+    AJD_CUDA(cudaStreamSynchronize(s));
+    cudaFree(stamps);
+    double kind_us[4] = {0, 0, 0, 0};
+    int kind_n[4] = {0, 0, 0, 0};
+    for (int i = 0; i < np; ++i) {
+      const double us = (t[i + 1] - t[i]) * 1e-3;
+      kind_us[phs[i].x] += us;
+      kind_n[phs[i].x]++;
+      if (std::getenv("AJD_APPLY_TIMING_ALL"))
+        std::fprintf(stderr, "phase %d kind %d rows %d G %d: %.2f us\n", i, phs[i].x, phs[i].z - phs[i].y, phs[i].w, us);
+    }
+    std::fprintf(stderr, "apply %.1f us: gather %.1f (%d) fwd %.1f (%d) dense %.1f (%d) bwd %.1f (%d)\n",
+                 (t[np] - t[0]) * 1e-3, kind_us[0], kind_n[0], kind_us[1], kind_n[1], kind_us[2], kind_n[2], kind_us[3],
+                 kind_n[3]);
+  }
   return JD_OK;
 }
 
@@ -490,7 +613,7 @@ int ildl_check_device_error(const ildl_s* f) {
     const unsigned* bar = prec == 0 ? f->d64.bar : f->d32.bar;
     if (!bar) continue;
     int e = 0;
-    AJD_CUDA(cudaMemcpy(&e, bar + 1, sizeof(int), cudaMemcpyDeviceToHost));
+    AJD_CUDA(cudaMemcpy(&e, bar + 64, sizeof(int), cudaMemcpyDeviceToHost));
     if (e) return fail(JD_EDEVICE, "ildl_apply: a device-side barrier timed out");
   }
   return JD_OK;
@@ -620,7 +743,7 @@ extern "C" int ildl_params_default(ildl_params* p) {
   p->drop = -1.0;
   p->gamma = -1.0;
   p->max_levels = 256;
-  p->n_dense = 3000;
+  p->n_dense = 6000;
   p->matching = 1;
   return JD_OK;
 }

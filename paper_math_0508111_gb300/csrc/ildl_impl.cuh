@@ -25,7 +25,7 @@ struct DevFactor {
   T* z = nullptr;
   int4* phases = nullptr;  // persistent-apply phase list (kind, p0, p1, G)
   int nphase = 0;
-  unsigned* bar = nullptr;  // [0] barrier count, [1] timeout flag
+  unsigned* bar = nullptr;  // [0] arrivals, [32] generation, [64] timeout flag
   int grid = 0;
 };
 

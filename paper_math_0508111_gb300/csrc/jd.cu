@@ -19,6 +19,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <limits>
+#include <type_traits>
 
 #include "anderson_impl.cuh"
 #include "ildl_impl.cuh"
@@ -647,6 +648,7 @@ class JdSolver {
   // inner-precision buffers (allocated as bytes)
   void *Qt_ = nullptr, *W_ = nullptr, *xb_ = nullptr, *rb_ = nullptr, *qb_ = nullptr, *db_ = nullptr,
        *tb_ = nullptr, *yb_ = nullptr, *ub_ = nullptr, *bb_ = nullptr;
+  float *pin_ = nullptr, *pout_ = nullptr;  // binary32 buffers of the mixed mode's preconditioner
   double* host_ = nullptr;  // pinned readback area
   int nb_ = 0;              // blocks of vector kernels
   std::vector<double> Mq_;  // cached Q^T W_Q block (host, kc x kc)
@@ -666,8 +668,13 @@ class JdSolver {
   int dot_cols(Cols<double> X1, Cols<double> X2, const double* extra, const double* v, double* out);
   int cgs2(int kc, int m, double* t, double* nrm_host);
   int rr(int m);
-  template <typename T>
+  template <typename T, typename P>
   int correction(int kc, double theta_hat, double rel_tol, int* its);
+  // out = K^{-1} in with vectors in T and the preconditioner applied in P
+  template <typename T, typename P>
+  int apply_k(const T* in, T* out);
+  template <typename T, typename P>
+  int cache_lock_column(int kc);
   int finalize(int kc, double* lam, double* evals, double* evecs, jd_stats* st);
   int sync_read(const double* dev, int cnt, double* host);
 };
@@ -703,6 +710,10 @@ int JdSolver::alloc() {
   AJD_TRY(A((void**)&flags_, sizeof(int) * 4));
   AJD_TRY(A((void**)&amax_, 2 * sizeof(unsigned long long)));
   const size_t eb = p_.precision == JD_FP32 ? sizeof(float) : sizeof(double);
+  if (p_.precision == JD_MIXED) {
+    AJD_TRY(A((void**)&pin_, (size_t)ld_ * sizeof(float)));
+    AJD_TRY(A((void**)&pout_, (size_t)ld_ * sizeof(float)));
+  }
   const size_t pb = (size_t)ld_ * eb;
   AJD_TRY(A(&Qt_, pb * (kint_ + 1)));
   AJD_TRY(A(&W_, pb * (kint_ + 1)));
@@ -732,7 +743,8 @@ void JdSolver::release() {
   for (auto& e : evs_) if (e) cudaEventDestroy(e);
   for (void* p : {(void*)V_, (void*)AV_, (void*)Vt_, (void*)AVt_, (void*)Q_, (void*)t_, (void*)u_, (void*)Au_,
                   (void*)r_, (void*)H_, (void*)theta_, (void*)Y_, (void*)dots_, (void*)partial_, (void*)scal_,
-                  (void*)Minv_, (void*)gg_, (void*)flags_, (void*)amax_, Qt_, W_, xb_, rb_, qb_, db_, tb_, yb_, ub_, bb_})
+                  (void*)Minv_, (void*)gg_, (void*)flags_, (void*)amax_, Qt_, W_, xb_, rb_, qb_, db_, tb_, yb_, ub_, bb_,
+                  (void*)pin_, (void*)pout_})
     if (p) cudaFree(p);
   if (host_) cudaFreeHost(host_);
   V_ = nullptr;
@@ -784,7 +796,44 @@ int JdSolver::rr(int m) {
   return JD_OK;
 }
 
-template <typename T>
+template <typename T, typename P>
+int JdSolver::apply_k(const T* in, T* out) {
+  if constexpr (std::is_same<T, P>::value) {
+    return ildl_apply_dev<T>(pc_, in, out, s_);
+  } else {
+    convert_kernel<T, P><<<nb_, kThreads, 0, s_>>>(in, reinterpret_cast<P*>(pin_), n_, 1.0); count_launches();
+    AJD_TRY(ildl_apply_dev<P>(pc_, reinterpret_cast<P*>(pin_), reinterpret_cast<P*>(pout_), s_));
+    convert_kernel<P, T><<<nb_, kThreads, 0, s_>>>(reinterpret_cast<P*>(pout_), out, n_, 1.0); count_launches();
+    return JD_OK;
+  }
+}
+
+// Q~[:, kc] = u and W[:, kc] = K^{-1} u for a newly locked vector, and the
+// new row/column of M = Q~^T W (host cache Mq_)
+template <typename T, typename P>
+int JdSolver::cache_lock_column(int kc) {
+  const int c = kc + 1;
+  T* Qt = static_cast<T*>(Qt_);
+  T* W = static_cast<T*>(W_);
+  convert_kernel<double, T><<<nb_, kThreads, 0, s_>>>(u_, Qt + (int64_t)kc * ld_, n_, 1.0); count_launches();
+  AJD_TRY((apply_k<T, P>(Qt + (int64_t)kc * ld_, W + (int64_t)kc * ld_)));
+  multidot_kernel<T><<<nb_, kThreads, 0, s_>>>(Cols<T>{Qt, ld_, c}, Cols<T>{}, nullptr, W + (int64_t)kc * ld_, n_,
+                                               partial_, c, nullptr); count_launches();
+  reduce_partials_kernel<<<1, 128, 0, s_>>>(partial_, nb_, c, dots_, nullptr); count_launches();
+  std::vector<double> col(c);
+  AJD_TRY(sync_read(dots_, c, col.data()));
+  std::vector<double> Mn((size_t)c * c);
+  for (int i = 0; i < kc; ++i)
+    for (int j = 0; j < kc; ++j) Mn[(size_t)j * c + i] = Mq_[(size_t)j * kc + i];
+  for (int i = 0; i < c; ++i) {
+    Mn[(size_t)kc * c + i] = col[i];
+    Mn[(size_t)i * c + kc] = col[i];
+  }
+  Mq_.swap(Mn);
+  return JD_OK;
+}
+
+template <typename T, typename P>
 int JdSolver::correction(int kc, double theta_hat, double rel_tol, int* its) {
   const int c = kc + 1;
   T* Qt = static_cast<T*>(Qt_);
@@ -796,7 +845,7 @@ int JdSolver::correction(int kc, double theta_hat, double rel_tol, int* its) {
   const int bl = nb_;
   // Qt[:, kc] = u, W[:, kc] = K^{-1} u  (Q columns and their W are cached)
   convert_kernel<double, T><<<bl, kThreads, 0, s_>>>(u_, Qt + (int64_t)kc * ld_, n_, 1.0); count_launches();
-  AJD_TRY(ildl_apply_dev<T>(pc_, Qt + (int64_t)kc * ld_, W + (int64_t)kc * ld_, s_));
+  AJD_TRY((apply_k<T, P>(Qt + (int64_t)kc * ld_, W + (int64_t)kc * ld_)));
   // M = Qt^T W (c x c): only row/column kc are new
   {
     multidot_kernel<T><<<bl, kThreads, 0, s_>>>(Cols<T>{Qt, ld_, c}, Cols<T>{}, nullptr, W + (int64_t)kc * ld_, n_,
@@ -850,7 +899,7 @@ int JdSolver::correction(int kc, double theta_hat, double rel_tol, int* its) {
   auto precond = [&]() -> int {
     const bool timed = nevp_ < kEv;
     if (timed) AJD_CUDA(cudaEventRecord(evp_[2 * nevp_], s_));
-    AJD_TRY(ildl_apply_dev<T>(pc_, r, y, s_));
+    AJD_TRY((apply_k<T, P>(r, y)));
     if (timed) AJD_CUDA(cudaEventRecord(evp_[2 * nevp_++ + 1], s_));
     multidot_kernel<T><<<bl, kThreads, 0, s_>>>(QtC, Cols<T>{}, nullptr, y, n_, partial_, c, done); count_launches();
     reduce_partials_kernel<<<1, 128, 0, s_>>>(partial_, bl, c, dots_, done); count_launches();
@@ -1097,35 +1146,9 @@ int JdSolver::run(double* evals, double* evecs, jd_stats* st) {
         lam.push_back(theta0);
         if (trace_) std::fprintf(stderr, "jd LOCK %d theta=%.15g res=%.3e at outer %d\n", kc, theta0, rnorm / normA_, outer);
         // cache W = K^{-1} q and the Q^T W block for the projected preconditioner
-        {
-          const int c = kc + 1;
-          if (p_.precision == JD_FP32) {
-            float* Qt = static_cast<float*>(Qt_);
-            float* W = static_cast<float*>(W_);
-            convert_kernel<double, float><<<nb_, kThreads, 0, s_>>>(u_, Qt + (int64_t)kc * ld_, n, 1.0); count_launches();
-            AJD_TRY(ildl_apply_dev<float>(pc_, Qt + (int64_t)kc * ld_, W + (int64_t)kc * ld_, s_));
-            multidot_kernel<float><<<nb_, kThreads, 0, s_>>>(Cols<float>{Qt, ld_, c}, Cols<float>{}, nullptr,
-                                                             W + (int64_t)kc * ld_, n, partial_, c, nullptr); count_launches();
-          } else {
-            double* Qt = static_cast<double*>(Qt_);
-            double* W = static_cast<double*>(W_);
-            convert_kernel<double, double><<<nb_, kThreads, 0, s_>>>(u_, Qt + (int64_t)kc * ld_, n, 1.0); count_launches();
-            AJD_TRY(ildl_apply_dev<double>(pc_, Qt + (int64_t)kc * ld_, W + (int64_t)kc * ld_, s_));
-            multidot_kernel<double><<<nb_, kThreads, 0, s_>>>(Cols<double>{Qt, ld_, c}, Cols<double>{}, nullptr,
-                                                              W + (int64_t)kc * ld_, n, partial_, c, nullptr); count_launches();
-          }
-          reduce_partials_kernel<<<1, 128, 0, s_>>>(partial_, nb_, c, dots_, nullptr); count_launches();
-          std::vector<double> col(c);
-          AJD_TRY(sync_read(dots_, c, col.data()));
-          std::vector<double> Mn((size_t)c * c);
-          for (int i = 0; i < kc; ++i)
-            for (int j = 0; j < kc; ++j) Mn[(size_t)j * c + i] = Mq_[(size_t)j * kc + i];
-          for (int i = 0; i < c; ++i) {
-            Mn[(size_t)kc * c + i] = col[i];
-            Mn[(size_t)i * c + kc] = col[i];
-          }
-          Mq_.swap(Mn);
-        }
+        if (p_.precision == JD_FP32) AJD_TRY((cache_lock_column<float, float>(kc)));
+        else if (p_.precision == JD_MIXED) AJD_TRY((cache_lock_column<double, float>(kc)));
+        else AJD_TRY((cache_lock_column<double, double>(kc)));
         ++kc;
         steps_on_pair = 0;
         if (kc == kint_) {
@@ -1179,11 +1202,13 @@ int JdSolver::run(double* evals, double* evecs, jd_stats* st) {
     if (trace_)
       std::fprintf(stderr, "jd outer %d m=%d kc=%d theta=%.15g res=%.3e gap=%.2e shift=%s\n", outer, m, kc, theta0,
                    rnorm / normA_, gap, resolved ? "theta" : "sigma");
-    const double floor = p_.inner_floor > 0.0 ? p_.inner_floor : (p_.precision == JD_FP32 ? 1e-5 : 1e-8);
+    const double floor =
+        p_.inner_floor > 0.0 ? p_.inner_floor : (p_.precision == JD_FP32 ? 1e-5 : p_.precision == JD_MIXED ? 1e-6 : 1e-8);
     const double rel = std::max(std::pow(p_.inner_decay, steps_on_pair + 1), floor);
     int its = 0;
-    if (p_.precision == JD_FP32) AJD_TRY(correction<float>(kc, theta_hat, rel, &its));
-    else AJD_TRY(correction<double>(kc, theta_hat, rel, &its));
+    if (p_.precision == JD_FP32) AJD_TRY((correction<float, float>(kc, theta_hat, rel, &its)));
+    else if (p_.precision == JD_MIXED) AJD_TRY((correction<double, float>(kc, theta_hat, rel, &its)));
+    else AJD_TRY((correction<double, double>(kc, theta_hat, rel, &its)));
     inner_total_ += its;
     ++steps_on_pair;
     if (trace_) std::fprintf(stderr, "   inner its %d (rel tol %.2e)\n", its, rel);
@@ -1312,7 +1337,8 @@ extern "C" int jd_solve(anderson_t h, double sigma, int k, double tol, const jd_
     if (!(prm.switch_tol > 0.0)) prm.switch_tol = d.switch_tol;
     if (prm.ildl.kappa == 0.0 && prm.ildl.max_levels == 0 && prm.ildl.n_dense == 0) prm.ildl = d.ildl;
   }
-  if (prm.precision != JD_FP64 && prm.precision != JD_FP32) return fail(JD_EINVAL, "jd_solve: unknown precision");
+  if (prm.precision != JD_FP64 && prm.precision != JD_FP32 && prm.precision != JD_MIXED)
+    return fail(JD_EINVAL, "jd_solve: unknown precision");
   if (st) std::memset(st, 0, sizeof(*st));
   using Clock = std::chrono::steady_clock;
   const auto t0 = Clock::now();

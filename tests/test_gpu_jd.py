@@ -34,6 +34,37 @@ def test_ildl_apply_matches_oracle(ajd, L, bc, sigma, nd):
         P.close()
 
 
+@pytest.mark.parametrize("L,bc,sigma", [(8, 0, 0.0), (9, 1, 0.7)])
+def test_dense_tail_inverse_is_exact(ajd, L, bc, sigma):
+    """When the whole matrix fits the dense tail, K = A - sigma I exactly: the
+    device Gauss-Jordan inverse must reproduce (A - sigma I)^{-1}."""
+    with ajd.Anderson(L, 16.5, 2, bc) as h:
+        P = ajd.Preconditioner.from_lattice(h, sigma)
+        assert P.info()["n_dense"] == h.n
+        A = lattice.assemble(L, rng.potential(L, 16.5, 2), bc, shift=sigma)
+        x = np.random.default_rng(1).standard_normal(h.n)
+        y = P.apply(torch.tensor(A @ x, device="cuda")).cpu().numpy()
+        assert np.linalg.norm(y - x) <= 1e-9 * np.linalg.norm(x)
+        F = P.export()
+        assert np.linalg.norm(matching.apply_factor(F, A @ x) - x) <= 1e-9 * np.linalg.norm(x)
+        P.close()
+
+
+def test_multilevel_factor_exact_on_device(ajd):
+    """No dropping, exact independence, kappa = inf: the device apply of the
+    multilevel factor (sparse levels + device-inverted dense tail) inverts
+    A - sigma I."""
+    L, sigma = 10, 0.3
+    with ajd.Anderson(L, 16.5, 3) as h:
+        P = ajd.Preconditioner.from_lattice(h, sigma, drop=0.0, kappa=1e300, gamma=0.0, n_dense=200)
+        assert P.info()["levels"] >= 2
+        A = lattice.assemble(L, rng.potential(L, 16.5, 3), 0, shift=sigma)
+        x = np.random.default_rng(2).standard_normal(h.n)
+        y = P.apply(torch.tensor(A @ x, device="cuda")).cpu().numpy()
+        assert np.linalg.norm(y - x) <= 1e-8 * np.linalg.norm(x)
+        P.close()
+
+
 def _check_pairs(L, W, seed, bc, sigma, k, ev, X, st, tol, oracle="dense"):
     eps = rng.potential(L, W, seed)
     A = lattice.assemble(L, eps, bc)
