@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--k", type=int, default=5)
     ap.add_argument("--tol", type=float, default=1e-8)
     ap.add_argument("--sigma", type=float, default=0.0)
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp32", "fp64"],
+                    help="inner-solve precision of the headline form")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain binary64 comparison")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
@@ -215,8 +217,9 @@ def main():
         ajd._ffi.check(rc, "jd_solve")
         return ajd._stats_dict(st)
 
+    head = {"mixed": ajd.JD_MIXED, "fp32": ajd.JD_FP32, "fp64": ajd.JD_FP64}[args.precision]
     for i in range(nwarm):
-        one(lattices[i], ajd.JD_FP32)
+        one(lattices[i], head)
 
     def barrier():
         if world > 1:
@@ -233,7 +236,7 @@ def main():
     e0.record(stream)
     for i in range(nsteps):
         flush.zero_()  # L2 flushed between steps (256 MiB write)
-        stats.append(one(lattices[nwarm + i], ajd.JD_FP32))
+        stats.append(one(lattices[nwarm + i], head))
     e1.record(stream)
     torch.cuda.synchronize()
     barrier()
@@ -280,7 +283,7 @@ def main():
             h = ajd._ffi.ctypes.c_void_p()
             ajd._ffi.call("anderson_create_from_potential", L, ajd.ctypes.c_void_p(pots[i].data_ptr()), 0,
                           ajd.ctypes.byref(h))
-            p = ajd.jd_params(precision=ajd.JD_FP32)
+            p = ajd.jd_params(precision=head)
             st = ajd._ffi.JdStats()
             rc = ajd._ffi.lib().jd_solve(h, sigma, k, tol, ajd.ctypes.byref(p),
                                          ajd.ctypes.c_void_p(evh.data_ptr()), ajd.ctypes.c_void_p(Xh.data_ptr()),
@@ -297,7 +300,7 @@ def main():
     calls = sum(s["precond_calls"] for s in stats)
     ms = sum(s["precond_ms"] for s in stats)
     info = stats[-1]["ildl"]
-    bytes_per = apply_bytes(info, 4)
+    bytes_per = apply_bytes(info, 8 if args.precision == "fp64" else 4)
     achieved = bytes_per / (ms / calls / 1e3) / 1e9 if calls else 0.0
     traffic = None
     prof = os.path.join(ROOT, "profiles", "ildl_apply_fp32_traffic.json")
@@ -307,7 +310,8 @@ def main():
         except Exception:
             traffic = None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": traffic, "kernel": "ildl_apply (binary32: forward/backward level sweeps + dense block)",
+                "traffic": traffic, "kernel": "ildl_apply_persistent_kernel (one cooperative launch: gather, "
+                                               "forward level sweeps, dense tail, backward level sweeps)",
                 "peak_kind": peak_kind + " (hbm_gbs, copy test)", "algorithmic_bytes_per_launch": bytes_per,
                 "avg_launch_ms": ms / calls if calls else None, "launches_timed": calls}
     stencil_calls = sum(s["stencil_calls"] for s in stats)
@@ -324,10 +328,12 @@ def main():
                 "scaling": "weak", "vs_baseline": value / PAPER_EIGENPAIRS_PER_S,
                 "vs_baseline_note": "paper Table 4: 978 s for 5 eigenpairs at M=100, w=16.5 on one Itanium2 core "
                                     "(context; the paper does not state its residual tolerance)",
-                "dtype": "f32+f64", "data": "synthetic",
+                "dtype": {"mixed": "f32+f64", "fp32": "f32+f64", "fp64": "f64"}[args.precision], "data": "synthetic",
                 "config": {"workload": "anderson-L%d-W%g-periodic-k%d-sigma%g-tol%g" % (L, W, k, sigma, tol),
                            "L": L, "W": W, "k": k, "sigma": sigma, "tol": tol, "bc": "periodic",
-                           "precision": "mixed: binary32 stencil/preconditioner/SQMR, binary64 outer",
+                           "precision": {"mixed": "mixed: binary32 preconditioner, binary64 vectors/stencil/outer",
+                                         "fp32": "binary32 inner solve (stencil, preconditioner, SQMR), binary64 outer",
+                                         "fp64": "binary64 throughout"}[args.precision],
                            "step": "one full jd_solve incl. preconditioner setup, fresh realisation per step",
                            "l2": "flushed between steps (256 MiB write)", "seeds": seeds[nwarm:],
                            "parallelism": "replicas (one realisation per step per GPU)"},

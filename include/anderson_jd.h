@@ -150,9 +150,10 @@ typedef struct {
   int max_levels; /* maximum number of sparse levels [256]                    */
   int n_dense;    /* the remaining Schur complement is factored densely once
                      it has at most this many rows (at most 8000) [6000]                    */
-  int matching;   /* 1: maximum-product matching, 1x1/2x2 cycle split and
-                     symmetric dual scaling per level (Sections 5.1, 5.2);
-                     0: row-max scaling and 1x1 pivots only [1]              */
+  int matching;   /* levels that use the maximum-product matching, 1x1/2x2
+                     cycle split and symmetric dual scaling (Sections 5.1,
+                     5.2); deeper levels use row-max scaling and 1x1
+                     candidates; 0 = none, < 0 = every level [-1]            */
 } ildl_params;
 
 /* Fill *p with the defaults above. */
@@ -235,7 +236,8 @@ int ildl_export(ildl_t f, int* perm, double* scale, int* level_ptr, int64_t* Lpt
  * diagonal and dense solves, one parallel step per level of L^T (backward),
  * and one scatter/scale pass.
  *   b, x       device pointers, n elements each, distinct; binary64 for
- *              JD_FP64, binary32 for JD_FP32.
+ *              JD_FP64 and JD_MIXED (binary32 factor, binary64 vectors and
+ *              sums), binary32 for JD_FP32.
  * Errors: JD_EINVAL (no device copy, bad precision), JD_EDEVICE.
  */
 int ildl_apply(ildl_t f, const void* b, void* x, int precision, void* stream);

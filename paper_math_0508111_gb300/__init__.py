@@ -207,13 +207,19 @@ class Preconditioner:
         out.update(inf)
         return out
 
-    def apply(self, b, out=None, stream=None):
-        """x = K^{-1} b for a CUDA tensor b (float64 or float32, length n)."""
+    def apply(self, b, out=None, stream=None, mixed=False):
+        """x = K^{-1} b for a CUDA tensor b (float64 or float32, length n).
+        ``mixed=True`` (float64 b) applies the binary32 factor with binary64
+        vectors and sums."""
         import torch
         if out is None:
             out = torch.empty_like(b)
-        _ffi.call("ildl_apply", self.handle, _dev_ptr(b, "b"), _dev_ptr(out, "out"), _precision_of(b),
-                  _stream_handle(stream))
+        prec = _precision_of(b)
+        if mixed:
+            if prec != JD_FP64:
+                raise TypeError("mixed apply takes float64 vectors")
+            prec = JD_MIXED
+        _ffi.call("ildl_apply", self.handle, _dev_ptr(b, "b"), _dev_ptr(out, "out"), prec, _stream_handle(stream))
         return out
 
     def close(self):

@@ -240,24 +240,27 @@ enum { PH_GATHER = 0, PH_FWD = 1, PH_DENSE = 2, PH_BWD = 3 };
 constexpr int kPersistThreads = 512;
 constexpr unsigned kSpinLimit = 1u << 22;  // ~0.1-0.5 s at 32-128 ns per poll
 
-template <typename T>
+// V: type of the stored factor values; X: type of the vectors and of the
+// accumulation (V = X for the binary64 and binary32 applies; V = float,
+// X = double for the mixed apply: binary32 factor traffic, binary64 sums).
+template <typename V, typename X>
 struct ApplyArgs {
   const int* perm;
-  const T* scale;
+  const V* scale;
   const int* Lptr;
   const int* Lcol;
-  const T* Lval;
+  const V* Lval;
   const int* Uptr;
   const int* Ucol;
-  const T* Uval;
-  const T* dd;
-  const T* dof;
+  const V* Uval;
+  const V* dd;
+  const V* dof;
   const int* partner;
-  const T* dense;
-  T* w;
-  T* z;
-  const T* b;
-  T* out;
+  const V* dense;
+  X* w;
+  X* z;
+  const X* b;
+  X* out;
   int nd, d0;
 };
 
@@ -299,8 +302,8 @@ __device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned* gen, uns
   return failed == 0;
 }
 
-template <typename T, int G>
-__device__ __forceinline__ void finish_row(const ApplyArgs<T>& a, int kind, int p, T acc, int lane, T rhs) {
+template <typename V, typename X, int G>
+__device__ __forceinline__ void finish_row(const ApplyArgs<V, X>& a, int kind, int p, X acc, int lane, X rhs) {
 #pragma unroll
   for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, G);
   if (p >= 0 && lane == 0) {
@@ -308,11 +311,11 @@ __device__ __forceinline__ void finish_row(const ApplyArgs<T>& a, int kind, int 
       __stcg(a.w + p, rhs - acc);  // rhs = s[p] b[perm[p]], stored in w by the gather phase
     } else {
       const int pp = __ldg(a.partner + p);
-      T d = __ldg(a.dd + p) * __ldcg(a.w + p);
-      if (pp >= 0) d += __ldg(a.dof + p) * __ldcg(a.w + pp);
-      const T zp = d - acc;
+      X d = (X)__ldg(a.dd + p) * __ldcg(a.w + p);
+      if (pp >= 0) d += (X)__ldg(a.dof + p) * __ldcg(a.w + pp);
+      const X zp = d - acc;
       __stcg(a.z + p, zp);
-      a.out[__ldg(a.perm + p)] = __ldg(a.scale + p) * zp;
+      a.out[__ldg(a.perm + p)] = (X)__ldg(a.scale + p) * zp;
     }
   }
 }
@@ -320,22 +323,22 @@ __device__ __forceinline__ void finish_row(const ApplyArgs<T>& a, int kind, int 
 // Rows of one level, G threads per row; each group handles two rows at a
 // time with their loads interleaved (index/value loads of both rows first,
 // then the gathers), so every memory latency is shared by two rows.
-template <typename T, int G>
-__device__ __forceinline__ void level_rows(const ApplyArgs<T>& a, int kind, int p0, int p1) {
+template <typename V, typename X, int G>
+__device__ __forceinline__ void level_rows(const ApplyArgs<V, X>& a, int kind, int p0, int p1) {
   const int lane = threadIdx.x % G;
   const int64_t groups = (int64_t)gridDim.x * blockDim.x / G;
   const int64_t g0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
   const int* ptr = kind == PH_FWD ? a.Lptr : a.Uptr;
   const int* col = kind == PH_FWD ? a.Lcol : a.Ucol;
-  const T* val = kind == PH_FWD ? a.Lval : a.Uval;
-  const T* x = kind == PH_FWD ? a.w : a.z;  // vector read through the columns
-  constexpr int B = G >= 32 ? 8 : 4;          // entries per lane and row per batch
+  const V* val = kind == PH_FWD ? a.Lval : a.Uval;
+  const X* x = kind == PH_FWD ? a.w : a.z;  // vector read through the columns
+  constexpr int B = G >= 32 ? 8 : 4;        // entries per lane and row per batch
   for (int64_t base = p0; base < p1; base += 2 * groups) {
     const int64_t ra = base + g0, rb = base + groups + g0;
     const int pa = ra < p1 ? (int)ra : -1;
     const int pb = rb < p1 ? (int)rb : -1;
     int qa = 0, ea = 0, qb = 0, eb = 0;
-    T ra_rhs = T(0), rb_rhs = T(0);
+    X ra_rhs = X(0), rb_rhs = X(0);
     if (pa >= 0) {
       qa = __ldg(ptr + pa) + lane;
       ea = __ldg(ptr + pa + 1);
@@ -346,47 +349,47 @@ __device__ __forceinline__ void level_rows(const ApplyArgs<T>& a, int kind, int 
       eb = __ldg(ptr + pb + 1);
       if (kind == PH_FWD && lane == 0) rb_rhs = __ldcg(a.w + pb);
     }
-    T acca = T(0), accb = T(0);
+    X acca = X(0), accb = X(0);
     while (qa < ea || qb < eb) {
       int ca[B], cb[B];
-      T va[B], vb[B];
+      V va[B], vb[B];
 #pragma unroll
       for (int i = 0; i < B; ++i) {
         const int q1 = qa + i * G, q2 = qb + i * G;
         const bool o1 = q1 < ea, o2 = q2 < eb;
         ca[i] = o1 ? __ldg(col + q1) : 0;
-        va[i] = o1 ? __ldg(val + q1) : T(0);
+        va[i] = o1 ? __ldg(val + q1) : V(0);
         cb[i] = o2 ? __ldg(col + q2) : 0;
-        vb[i] = o2 ? __ldg(val + q2) : T(0);
+        vb[i] = o2 ? __ldg(val + q2) : V(0);
       }
 #pragma unroll
       for (int i = 0; i < B; ++i) {
-        acca += va[i] * __ldcg(x + ca[i]);
-        accb += vb[i] * __ldcg(x + cb[i]);
+        acca += (X)va[i] * __ldcg(x + ca[i]);
+        accb += (X)vb[i] * __ldcg(x + cb[i]);
       }
       qa += B * G;
       qb += B * G;
     }
-    finish_row<T, G>(a, kind, pa, acca, lane, ra_rhs);
-    finish_row<T, G>(a, kind, pb, accb, lane, rb_rhs);
+    finish_row<V, X, G>(a, kind, pa, acca, lane, ra_rhs);
+    finish_row<V, X, G>(a, kind, pb, accb, lane, rb_rhs);
   }
 }
 
 // Prefetch the stored rows of a level phase into L2 (lines strided over the
 // whole grid); skipped for phases larger than 16 MB, which stream from HBM
 // at full bandwidth anyway.
-template <typename T>
-__device__ __forceinline__ void prefetch_phase(const ApplyArgs<T>& a, int4 P) {
+template <typename V, typename X>
+__device__ __forceinline__ void prefetch_phase(const ApplyArgs<V, X>& a, int4 P) {
   if (P.x != PH_FWD && P.x != PH_BWD) return;
   const int* ptr = P.x == PH_FWD ? a.Lptr : a.Uptr;
   const int* col = P.x == PH_FWD ? a.Lcol : a.Ucol;
-  const T* val = P.x == PH_FWD ? a.Lval : a.Uval;
+  const V* val = P.x == PH_FWD ? a.Lval : a.Uval;
   const int64_t q0 = __ldg(ptr + P.y), q1 = __ldg(ptr + P.z);
-  const int64_t bytes = (q1 - q0) * (int64_t)(sizeof(T) + sizeof(int));
+  const int64_t bytes = (q1 - q0) * (int64_t)(sizeof(V) + sizeof(int));
   if (bytes > (16ll << 20) || q1 <= q0) return;
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t nth = (int64_t)gridDim.x * blockDim.x;
-  const int64_t lines_v = ((q1 - q0) * (int64_t)sizeof(T) + 127) / 128;
+  const int64_t lines_v = ((q1 - q0) * (int64_t)sizeof(V) + 127) / 128;
   const int64_t lines_c = ((q1 - q0) * (int64_t)sizeof(int) + 127) / 128;
   const char* vb = reinterpret_cast<const char*>(val + q0);
   const char* cb = reinterpret_cast<const char*>(col + q0);
@@ -396,9 +399,9 @@ __device__ __forceinline__ void prefetch_phase(const ApplyArgs<T>& a, int4 P) {
   }
 }
 
-template <typename T>
+template <typename V, typename X>
 __global__ void __launch_bounds__(kPersistThreads, 1)
-ildl_apply_persistent_kernel(ApplyArgs<T> a, const int4* __restrict__ phases, int nphase, unsigned* count,
+ildl_apply_persistent_kernel(ApplyArgs<V, X> a, const int4* __restrict__ phases, int nphase, unsigned* count,
                              unsigned* gen, int* err, unsigned long long* stamps) {
   for (int ph = 0; ph < nphase; ++ph) {
     const int4 P = phases[ph];  // kind, p0, p1, G
@@ -411,41 +414,42 @@ ildl_apply_persistent_kernel(ApplyArgs<T> a, const int4* __restrict__ phases, in
     const int4 Pn = ph + 1 < nphase ? phases[ph + 1] : make_int4(-1, 0, 0, 0);
     if (kind == PH_GATHER) {
       for (int p = p0 + blockIdx.x * blockDim.x + threadIdx.x; p < p1; p += gridDim.x * blockDim.x)
-        __stcg(a.w + p, __ldg(a.scale + p) * __ldg(a.b + __ldg(a.perm + p)));
+        __stcg(a.w + p, (X)__ldg(a.scale + p) * __ldg(a.b + __ldg(a.perm + p)));
     } else if (kind == PH_DENSE) {
       const int lane = threadIdx.x & 31;
       const int warps = (gridDim.x * blockDim.x) >> 5;
       for (int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < a.nd; r += warps) {
-        const T* row = a.dense + (int64_t)r * a.nd;
-        T acc = T(0);
+        const V* row = a.dense + (int64_t)r * a.nd;
+        X acc = X(0);
         for (int c0 = lane; c0 < a.nd; c0 += 8 * 32) {
-          T rv[8], wv[8];
+          V rv[8];
+          X wv[8];
 #pragma unroll
           for (int i = 0; i < 8; ++i) {
             const int c = c0 + 32 * i;
             const bool ok = c < a.nd;
-            rv[i] = ok ? __ldg(row + c) : T(0);
-            wv[i] = ok ? __ldcg(a.w + a.d0 + c) : T(0);
+            rv[i] = ok ? __ldg(row + c) : V(0);
+            wv[i] = ok ? __ldcg(a.w + a.d0 + c) : X(0);
           }
 #pragma unroll
-          for (int i = 0; i < 8; ++i) acc += rv[i] * wv[i];
+          for (int i = 0; i < 8; ++i) acc += (X)rv[i] * wv[i];
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
         if (lane == 0) {
           __stcg(a.z + a.d0 + r, acc);
-          a.out[__ldg(a.perm + a.d0 + r)] = __ldg(a.scale + a.d0 + r) * acc;
+          a.out[__ldg(a.perm + a.d0 + r)] = (X)__ldg(a.scale + a.d0 + r) * acc;
         }
       }
     } else {
       switch (G) {
-        case 4: level_rows<T, 4>(a, kind, p0, p1); break;
-        case 8: level_rows<T, 8>(a, kind, p0, p1); break;
-        case 16: level_rows<T, 16>(a, kind, p0, p1); break;
-        default: level_rows<T, 32>(a, kind, p0, p1); break;
+        case 4: level_rows<V, X, 4>(a, kind, p0, p1); break;
+        case 8: level_rows<V, X, 8>(a, kind, p0, p1); break;
+        case 16: level_rows<V, X, 16>(a, kind, p0, p1); break;
+        default: level_rows<V, X, 32>(a, kind, p0, p1); break;
       }
     }
-    if (ph + 1 < nphase) prefetch_phase<T>(a, Pn);
+    if (ph + 1 < nphase) prefetch_phase<V, X>(a, Pn);
     if (ph + 1 < nphase && !grid_barrier(count, gen, (unsigned)ph, err)) return;
   }
   if (stamps && blockIdx.x == 0 && threadIdx.x == 0) {
@@ -473,6 +477,8 @@ void free_dev(DevFactor<T>& d) {
   cudaFree(d.z);
   cudaFree(d.phases);
   cudaFree(d.bar);
+  cudaFree(d.w64);
+  cudaFree(d.z64);
   d = DevFactor<T>();
 }
 
@@ -505,6 +511,10 @@ int upload_factor(const HostFactor& F, DevFactor<T>& d) {
   AJD_TRY(upload(&d.dense, F.dense_inv));
   AJD_CUDA(cudaMalloc(&d.w, std::max<size_t>(1, F.n) * sizeof(T)));
   AJD_CUDA(cudaMalloc(&d.z, std::max<size_t>(1, F.n) * sizeof(T)));
+  if (sizeof(T) == 4) {  // binary64 work vectors of the mixed apply
+    AJD_CUDA(cudaMalloc(&d.w64, std::max<size_t>(1, F.n) * sizeof(double)));
+    AJD_CUDA(cudaMalloc(&d.z64, std::max<size_t>(1, F.n) * sizeof(double)));
+  }
   // phase list of the persistent apply
   std::vector<int4> ph;
   const std::vector<int>& lvp = F.level_ptr;
@@ -534,7 +544,7 @@ int upload_factor(const HostFactor& F, DevFactor<T>& d) {
   AJD_CUDA(cudaMalloc(&d.bar, 96 * sizeof(unsigned)));
   AJD_CUDA(cudaMemset(d.bar, 0, 96 * sizeof(unsigned)));
   int per_sm = 0;
-  AJD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ildl_apply_persistent_kernel<T>, kPersistThreads, 0));
+  AJD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ildl_apply_persistent_kernel<T, double>, kPersistThreads, 0));
   if (per_sm < 1) return fail(JD_EDEVICE, "ildl: persistent apply kernel cannot be resident");
   d.grid = sm_count();  // one CTA per SM
   d.ready = true;
@@ -560,14 +570,14 @@ void launch_bwd(const DevFactor<T>& d, T* out, int p0, int p1, cudaStream_t s) {
 
 }  // namespace
 
-template <typename T>
-int ildl_apply_dev(const ildl_s* f, const T* b, T* out, cudaStream_t s) {
-  const DevFactor<T>& d = f->dev<T>();
+// One persistent apply with factor values V and vectors X.
+template <typename V, typename X>
+int launch_apply(const ildl_s* f, const DevFactor<V>& d, X* w, X* z, const X* b, X* out, cudaStream_t s) {
   if (!d.ready) return fail(JD_EINVAL, "ildl_apply: factor has no device copy (use ildl_create)");
   const HostFactor& F = f->F;
   if (F.n == 0 || d.nphase == 0) return JD_OK;
-  ApplyArgs<T> a{d.perm, d.scale, d.Lptr, d.Lcol, d.Lval, d.Uptr, d.Ucol, d.Uval, d.dd, d.dof, d.partner,
-                 d.dense, d.w, d.z, b, out, F.n_dense, F.level_ptr[F.nlev]};
+  ApplyArgs<V, X> a{d.perm, d.scale, d.Lptr, d.Lcol, d.Lval, d.Uptr, d.Ucol, d.Uval, d.dd, d.dof, d.partner,
+                    d.dense, w, z, b, out, F.n_dense, F.level_ptr[F.nlev]};
   AJD_CUDA(cudaMemsetAsync(d.bar, 0, 64 * sizeof(unsigned), s));  // arrivals and generation
   const int4* ph = d.phases;
   int np = d.nphase;
@@ -580,8 +590,8 @@ int ildl_apply_dev(const ildl_s* f, const T* b, T* out, cudaStream_t s) {
   unsigned long long* stamps = nullptr;
   if (timing) AJD_CUDA(cudaMalloc(&stamps, (np + 1) * sizeof(unsigned long long)));
   void* args[] = {&a, &ph, &np, &cnt, &gen, &err, &stamps};
-  AJD_CUDA(cudaLaunchCooperativeKernel((void*)ildl_apply_persistent_kernel<T>, dim3(d.grid), dim3(kPersistThreads),
-                                       args, 0, s));
+  AJD_CUDA(cudaLaunchCooperativeKernel((void*)ildl_apply_persistent_kernel<V, X>, dim3(d.grid),
+                                       dim3(kPersistThreads), args, 0, s));
   count_launches(2);
   if (timing) {
     std::vector<unsigned long long> t(np + 1);
@@ -604,6 +614,18 @@ int ildl_apply_dev(const ildl_s* f, const T* b, T* out, cudaStream_t s) {
                  kind_n[3]);
   }
   return JD_OK;
+}
+
+template <typename T>
+int ildl_apply_dev(const ildl_s* f, const T* b, T* out, cudaStream_t s) {
+  const DevFactor<T>& d = f->dev<T>();
+  return launch_apply<T, T>(f, d, d.w, d.z, b, out, s);
+}
+
+int ildl_apply_dev_mixed(const ildl_s* f, const double* b, double* out, cudaStream_t s) {
+  const DevFactor<float>& d = f->d32;
+  if (!d.w64) return fail(JD_EINVAL, "ildl_apply: no mixed-precision work vectors");
+  return launch_apply<float, double>(f, d, d.w64, d.z64, b, out, s);
 }
 
 // Timeout flag of the persistent apply (sticky until cleared): JD_EDEVICE if
@@ -744,7 +766,7 @@ extern "C" int ildl_params_default(ildl_params* p) {
   p->gamma = -1.0;
   p->max_levels = 256;
   p->n_dense = 6000;
-  p->matching = 1;
+  p->matching = -1;
   return JD_OK;
 }
 
@@ -912,6 +934,8 @@ extern "C" int ildl_apply(ildl_t f, const void* b, void* x, int precision, void*
     return ildl_apply_dev<double>(f, static_cast<const double*>(b), static_cast<double*>(x), s);
   if (precision == JD_FP32)
     return ildl_apply_dev<float>(f, static_cast<const float*>(b), static_cast<float*>(x), s);
+  if (precision == JD_MIXED)
+    return ildl_apply_dev_mixed(f, static_cast<const double*>(b), static_cast<double*>(x), s);
   return fail(JD_EINVAL, "ildl_apply: unknown precision %d", precision);
 }
 
@@ -927,3 +951,4 @@ extern "C" int ildl_destroy(ildl_t f) {
   delete f;
   return JD_OK;
 }
+

@@ -27,6 +27,8 @@ struct DevFactor {
   int nphase = 0;
   unsigned* bar = nullptr;  // [0] arrivals, [32] generation, [64] timeout flag
   int grid = 0;
+  double* w64 = nullptr;  // binary64 work vectors of the mixed apply (float factor)
+  double* z64 = nullptr;
 };
 
 }  // namespace ajd
@@ -48,6 +50,9 @@ namespace ajd {
 // x = K^{-1} b on `stream` (device pointers, n elements).
 template <typename T>
 int ildl_apply_dev(const ildl_s* f, const T* b, T* out, cudaStream_t stream);
+
+// x = K^{-1} b with the binary32 factor, binary64 vectors and sums.
+int ildl_apply_dev_mixed(const ildl_s* f, const double* b, double* out, cudaStream_t stream);
 
 // JD_EDEVICE if a device-side wait of an apply timed out (reads a flag).
 int ildl_check_device_error(const ildl_s* f);

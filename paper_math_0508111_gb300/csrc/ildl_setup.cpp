@@ -35,6 +35,7 @@
 #include <cstdlib>
 
 #include <omp.h>
+#include <parallel/algorithm>
 
 namespace ajd {
 
@@ -389,7 +390,8 @@ int build_ildl(const SymCsr& A, const ildl_params& prm, HostFactor& F, bool dens
     std::vector<double> u, v, rmax;
     std::vector<double> d(m);
     std::vector<std::pair<int, int>> groups;
-    if (prm.matching) {
+    const bool use_matching = prm.matching != 0 && (prm.matching < 0 || level < prm.matching);
+    if (use_matching) {
       max_product_matching(S, mc, u, v, rmax);
       for (int i = 0; i < m; ++i) d[i] = std::sqrt(std::exp(u[i] + v[i]) / rmax[i]);
       if (level == 0)
@@ -406,7 +408,7 @@ int build_ildl(const SymCsr& A, const ildl_params& prm, HostFactor& F, bool dens
       cum[i] *= d[i];
       for (int64_t p = S.ptr[i]; p < S.ptr[i + 1]; ++p) S.val[p] *= d[i] * d[S.col[p]];
     }
-    if (prm.matching) {
+    if (use_matching) {
       split_cycles(S, mc, groups);
     } else {
       groups.reserve(m);
@@ -473,7 +475,7 @@ int build_ildl(const SymCsr& A, const ildl_params& prm, HostFactor& F, bool dens
         cands.push_back({j, -1, d1_of(j)});
       }
     }
-    std::stable_sort(cands.begin(), cands.end(), [](const Cand& x, const Cand& y) {
+    __gnu_parallel::stable_sort(cands.begin(), cands.end(), [](const Cand& x, const Cand& y) {
       if (x.q != y.q) return x.q < y.q;
       return x.a < y.a;
     });

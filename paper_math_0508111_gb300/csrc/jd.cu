@@ -648,7 +648,6 @@ class JdSolver {
   // inner-precision buffers (allocated as bytes)
   void *Qt_ = nullptr, *W_ = nullptr, *xb_ = nullptr, *rb_ = nullptr, *qb_ = nullptr, *db_ = nullptr,
        *tb_ = nullptr, *yb_ = nullptr, *ub_ = nullptr, *bb_ = nullptr;
-  float *pin_ = nullptr, *pout_ = nullptr;  // binary32 buffers of the mixed mode's preconditioner
   double* host_ = nullptr;  // pinned readback area
   int nb_ = 0;              // blocks of vector kernels
   std::vector<double> Mq_;  // cached Q^T W_Q block (host, kc x kc)
@@ -710,10 +709,7 @@ int JdSolver::alloc() {
   AJD_TRY(A((void**)&flags_, sizeof(int) * 4));
   AJD_TRY(A((void**)&amax_, 2 * sizeof(unsigned long long)));
   const size_t eb = p_.precision == JD_FP32 ? sizeof(float) : sizeof(double);
-  if (p_.precision == JD_MIXED) {
-    AJD_TRY(A((void**)&pin_, (size_t)ld_ * sizeof(float)));
-    AJD_TRY(A((void**)&pout_, (size_t)ld_ * sizeof(float)));
-  }
+
   const size_t pb = (size_t)ld_ * eb;
   AJD_TRY(A(&Qt_, pb * (kint_ + 1)));
   AJD_TRY(A(&W_, pb * (kint_ + 1)));
@@ -743,8 +739,7 @@ void JdSolver::release() {
   for (auto& e : evs_) if (e) cudaEventDestroy(e);
   for (void* p : {(void*)V_, (void*)AV_, (void*)Vt_, (void*)AVt_, (void*)Q_, (void*)t_, (void*)u_, (void*)Au_,
                   (void*)r_, (void*)H_, (void*)theta_, (void*)Y_, (void*)dots_, (void*)partial_, (void*)scal_,
-                  (void*)Minv_, (void*)gg_, (void*)flags_, (void*)amax_, Qt_, W_, xb_, rb_, qb_, db_, tb_, yb_, ub_, bb_,
-                  (void*)pin_, (void*)pout_})
+                  (void*)Minv_, (void*)gg_, (void*)flags_, (void*)amax_, Qt_, W_, xb_, rb_, qb_, db_, tb_, yb_, ub_, bb_})
     if (p) cudaFree(p);
   if (host_) cudaFreeHost(host_);
   V_ = nullptr;
@@ -801,10 +796,8 @@ int JdSolver::apply_k(const T* in, T* out) {
   if constexpr (std::is_same<T, P>::value) {
     return ildl_apply_dev<T>(pc_, in, out, s_);
   } else {
-    convert_kernel<T, P><<<nb_, kThreads, 0, s_>>>(in, reinterpret_cast<P*>(pin_), n_, 1.0); count_launches();
-    AJD_TRY(ildl_apply_dev<P>(pc_, reinterpret_cast<P*>(pin_), reinterpret_cast<P*>(pout_), s_));
-    convert_kernel<P, T><<<nb_, kThreads, 0, s_>>>(reinterpret_cast<P*>(pout_), out, n_, 1.0); count_launches();
-    return JD_OK;
+    // binary32 factor, binary64 vectors and accumulation
+    return ildl_apply_dev_mixed(pc_, in, out, s_);
   }
 }
 

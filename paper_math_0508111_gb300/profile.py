@@ -1,0 +1,85 @@
+"""Small, repeatable workloads for timing and profiling single kernels.
+
+    python -m paper_math_0508111_gb300.profile apply   [--L 70] [--reps 5]
+    python -m paper_math_0508111_gb300.profile stencil [--L 256] [--reps 20]
+
+``apply`` builds the preconditioner of A - 0 I for an L^3 lattice (W = 16.5,
+seed 1) and times its application in binary32, binary32-with-binary64
+vectors and binary64 (3 warm-up applications each, then ``reps`` timed ones,
+CUDA events on the current stream).  ``stencil`` times y = A x in binary64
+and binary32 with the L2 flushed before every repetition.  Both print one
+JSON line per case.  Run them under ncu with ``-k regex:persistent`` or
+``-k regex:stencil`` to capture the kernel of interest.
+"""
+import argparse
+import json
+
+import torch
+
+import paper_math_0508111_gb300 as ajd
+
+
+def _time(fn, reps, flush=None):
+    s = torch.cuda.current_stream()
+    ts = []
+    for _ in range(reps):
+        if flush is not None:
+            flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(s)
+        fn()
+        b.record(s)
+        b.synchronize()
+        ts.append(a.elapsed_time(b))
+    ts.sort()
+    return ts[len(ts) // 2]
+
+
+def apply_case(L, reps):
+    h = ajd.Anderson(L, 16.5, 1)
+    P = ajd.Preconditioner.from_lattice(h, 0.0)
+    info = P.info()
+    print(json.dumps({"case": "setup", "L": L, **info}), flush=True)
+    for name, dt in [("fp32", torch.float32), ("fp64", torch.float64)]:
+        b = torch.randn(h.n, device="cuda", dtype=dt)
+        x = torch.empty_like(b)
+        for _ in range(3):
+            P.apply(b, out=x)
+        ms = _time(lambda: P.apply(b, out=x), reps)
+        print(json.dumps({"case": "apply", "precision": name, "L": L, "ms": ms}), flush=True)
+    b = torch.randn(h.n, device="cuda", dtype=torch.float64)
+    x = torch.empty_like(b)
+    for _ in range(3):
+        P.apply(b, out=x, mixed=True)
+    ms = _time(lambda: P.apply(b, out=x, mixed=True), reps)
+    print(json.dumps({"case": "apply", "precision": "mixed", "L": L, "ms": ms}), flush=True)
+
+
+def stencil_case(L, reps):
+    h = ajd.Anderson(L, 16.5, 1)
+    flush = torch.empty(256 * 1024 * 1024 // 4, device="cuda", dtype=torch.float32)
+    for name, dt, nbytes in [("fp64", torch.float64, 24), ("fp32", torch.float32, 12)]:
+        x = torch.randn(h.n, device="cuda", dtype=dt)
+        y = torch.empty_like(x)
+        for _ in range(3):
+            h.apply(x, out=y)
+        ms = _time(lambda: h.apply(x, out=y), reps, flush)
+        print(json.dumps({"case": "stencil", "precision": name, "L": L, "ms": ms,
+                          "GBps": nbytes * h.n / (ms * 1e-3) / 1e9}), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("what", choices=["apply", "stencil"])
+    ap.add_argument("--L", type=int, default=None)
+    ap.add_argument("--reps", type=int, default=None)
+    a = ap.parse_args()
+    if a.what == "apply":
+        apply_case(a.L or 70, a.reps or 5)
+    else:
+        stencil_case(a.L or 256, a.reps or 20)
+
+
+if __name__ == "__main__":
+    main()

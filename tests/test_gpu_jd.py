@@ -31,6 +31,8 @@ def test_ildl_apply_matches_oracle(ajd, L, bc, sigma, nd):
         assert np.abs(x64 - want).max() <= 1e-12 * scale
         x32 = P.apply(torch.tensor(b, device="cuda", dtype=torch.float32)).double().cpu().numpy()
         assert np.abs(x32 - want).max() <= 2e-5 * scale
+        xm = P.apply(torch.tensor(b, device="cuda"), mixed=True).cpu().numpy()
+        assert np.abs(xm - want).max() <= 2e-5 * scale
         P.close()
 
 
