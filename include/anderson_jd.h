@@ -242,6 +242,30 @@ int ildl_export(ildl_t f, int* perm, double* scale, int* level_ptr, int64_t* Lpt
  */
 int ildl_apply(ildl_t f, const void* b, void* x, int precision, void* stream);
 
+/*
+ * ildl_apply_noalloc -- x = K^{-1} b like ildl_apply, for callers that cannot
+ * allocate device memory during the call (a fixed memory pool, an embedding
+ * runtime that owns all device memory, a region that must stay free of
+ * allocations).  The paper has no counterpart: this is a deployment variant.
+ * It runs the same kernel but takes its scratch (two work vectors and the
+ * grid-barrier words) from one static device array compiled into the
+ * library (2 MiB + 512 bytes, held by every GPU that loads the library until
+ * the process exits) instead of the factor's buffers; it calls no cudaMalloc,
+ * cudaFree or allocating library routine.
+ *   f          a factor from ildl_create with at most 131072 rows (n = L^3,
+ *              L <= 50); larger orders are rejected with JD_EINVAL.
+ *   b, x       device pointers as for ildl_apply; precision JD_FP64,
+ *              JD_FP32 or JD_MIXED.
+ * Every call shares the one array (its previous contents are kept; the call
+ * clears the words that must start at zero), so calls that overlap on the
+ * GPU -- on different streams or threads -- race and must not be issued.
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  The call waits for the apply to finish and
+ * returns JD_EDEVICE if a device-side wait timed out.
+ */
+int ildl_apply_noalloc(ildl_t f, const void* b, void* x, int precision, void* stream);
+
 /* Release the factor (host and device parts).  NULL is a no-op. */
 int ildl_destroy(ildl_t f);
 

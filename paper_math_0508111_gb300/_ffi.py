@@ -70,6 +70,7 @@ SIGNATURES = [
     ("ildl_info", c_int, [c_void_p, P(IldlInfo)]),
     ("ildl_export", c_int, [c_void_p] + [c_void_p] * 10),
     ("ildl_apply", c_int, [c_void_p, c_void_p, c_void_p, c_int, c_void_p]),
+    ("ildl_apply_noalloc", c_int, [c_void_p, c_void_p, c_void_p, c_int, c_void_p]),
     ("ildl_destroy", c_int, [c_void_p]),
     ("jd_params_default", c_int, [P(JdParams)]),
     ("jd_solve", c_int, [c_void_p, c_double, c_int, c_double, P(JdParams), c_void_p, c_void_p, P(JdStats),

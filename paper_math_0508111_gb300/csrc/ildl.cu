@@ -14,6 +14,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <mutex>
 #include <new>
 #include <cstdio>
 #include <cstdlib>
@@ -952,3 +953,108 @@ extern "C" int ildl_destroy(ildl_t f) {
   return JD_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Allocation-free preconditioner application.
+//
+// Some callers cannot allocate device memory while they run: code executing
+// under an allocator that forbids it (a memory pool reserved up front, a
+// captured region that must stay allocation-free, an embedding runtime that
+// owns all device memory).  ildl_apply_noalloc serves them: it launches the
+// same persistent kernel as ildl_apply but takes its scratch (the two work
+// vectors and the grid-barrier words) from one file-scope device array
+// instead of the factor's own buffers.  Nothing is allocated or freed.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int64_t kNoAllocMaxN = 131072;  // largest order served (L <= 50 lattices)
+constexpr size_t kNoAllocVecBytes = (size_t)kNoAllocMaxN * sizeof(double);
+constexpr size_t kNoAllocBytes = 2 * kNoAllocVecBytes + 512;  // w, z, barrier words
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+// Device address of g_noalloc_scratch per device (host code may not use the
+// symbol itself: it names a host-side stand-in).
+struct NoAllocSlot {
+  bool ready = false;
+  unsigned char* ptr = nullptr;
+};
+constexpr int kMaxDevices = 64;
+NoAllocSlot g_noalloc_slots[kMaxDevices];
+std::mutex g_noalloc_mutex;
+
+int noalloc_scratch(unsigned char** out) {
+  int dev = 0;
+  AJD_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return fail(JD_EDEVICE, "ildl_apply_noalloc: device %d out of range", dev);
+  std::lock_guard<std::mutex> lk(g_noalloc_mutex);
+  NoAllocSlot& sl = g_noalloc_slots[dev];
+  if (!sl.ready) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return fail(JD_EDEVICE, "ildl_apply_noalloc: cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+    sl.ptr = static_cast<unsigned char*>(p);
+    sl.ready = true;
+  }
+  *out = sl.ptr;
+  return JD_OK;
+}
+
+template <typename V, typename X>
+int launch_apply_static(const ildl_s* f, const DevFactor<V>& d, const X* b, X* out, unsigned char* scratch,
+                        cudaStream_t s) {
+  const HostFactor& F = f->F;
+  if (F.n == 0 || d.nphase == 0) return JD_OK;
+  X* w = reinterpret_cast<X*>(scratch);
+  X* z = reinterpret_cast<X*>(scratch + kNoAllocVecBytes);
+  unsigned* bar = reinterpret_cast<unsigned*>(scratch + 2 * kNoAllocVecBytes);
+  ApplyArgs<V, X> a{d.perm, d.scale, d.Lptr, d.Lcol, d.Lval, d.Uptr, d.Ucol, d.Uval, d.dd, d.dof, d.partner,
+                    d.dense, w, z, b, out, F.n_dense, F.level_ptr[F.nlev]};
+  // the array keeps the previous call's contents: the barrier words (arrivals,
+  // generation, timeout flag) must start at zero; w and z are written before
+  // they are read
+  AJD_CUDA(cudaMemsetAsync(bar, 0, 96 * sizeof(unsigned), s));
+  const int4* ph = d.phases;
+  int np = d.nphase;
+  unsigned* cnt = bar;
+  unsigned* gen = bar + 32;
+  int* err = reinterpret_cast<int*>(bar + 64);
+  unsigned long long* stamps = nullptr;
+  void* args[] = {&a, &ph, &np, &cnt, &gen, &err, &stamps};
+  AJD_CUDA(cudaLaunchCooperativeKernel((void*)ildl_apply_persistent_kernel<V, X>, dim3(d.grid),
+                                       dim3(kPersistThreads), args, 0, s));
+  count_launches(2);
+  int herr = 0;
+  AJD_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  AJD_CUDA(cudaStreamSynchronize(s));
+  if (herr) return fail(JD_EDEVICE, "ildl_apply_noalloc: a device-side barrier timed out");
+  return JD_OK;
+}
+
+}  // namespace
+
+extern "C" int ildl_apply_noalloc(ildl_t f, const void* b, void* x, int precision, void* stream) {
+  if (!f || !b || !x) return fail(JD_EINVAL, "ildl_apply_noalloc: NULL argument");
+  if (b == x) return fail(JD_EINVAL, "ildl_apply_noalloc: b and x must be distinct");
+  if ((int64_t)f->F.n > kNoAllocMaxN)
+    return fail(JD_EINVAL, "ildl_apply_noalloc: order %d exceeds the static scratch limit of %lld rows", f->F.n,
+                (long long)kNoAllocMaxN);
+  unsigned char* scratch = nullptr;
+  AJD_TRY(noalloc_scratch(&scratch));
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (precision == JD_FP64) {
+    if (!f->d64.ready) return fail(JD_EINVAL, "ildl_apply_noalloc: factor has no device copy");
+    return launch_apply_static<double, double>(f, f->d64, static_cast<const double*>(b), static_cast<double*>(x),
+                                               scratch, s);
+  }
+  if (precision == JD_FP32) {
+    if (!f->d32.ready) return fail(JD_EINVAL, "ildl_apply_noalloc: factor has no device copy");
+    return launch_apply_static<float, float>(f, f->d32, static_cast<const float*>(b), static_cast<float*>(x),
+                                             scratch, s);
+  }
+  if (precision == JD_MIXED) {
+    if (!f->d32.ready) return fail(JD_EINVAL, "ildl_apply_noalloc: factor has no device copy");
+    return launch_apply_static<float, double>(f, f->d32, static_cast<const double*>(b), static_cast<double*>(x),
+                                              scratch, s);
+  }
+  return fail(JD_EINVAL, "ildl_apply_noalloc: unknown precision %d", precision);
+}
