@@ -363,6 +363,27 @@ int jd_params_default(jd_params* p);
 int jd_solve(anderson_t h, double sigma, int k, double tol, const jd_params* p, double* evals,
              double* evecs, jd_stats* st, void* stream);
 
+/*
+ * jd_solve_batch -- jd_solve for nprob independent problems (disorder
+ * realisations, shifts, k; the paper's physics needs "many realizations",
+ * Section 3), pipelined: `setup_threads` host threads build the
+ * preconditioners of later problems (the host part of the setup, each with
+ * its share of the OpenMP threads, and the device part on its own stream)
+ * while the calling thread solves earlier problems on `stream`.  At most
+ * setup_threads + 1 factors are alive at once.
+ *   hs[nprob], sigma[nprob], k[nprob]   the problems (each as for jd_solve);
+ *   evals[i]   caller buffer of k[i] doubles; evecs NULL or evecs[i] a buffer
+ *              of n_i * k[i] doubles (host or device pointers);
+ *   stats      NULL or nprob entries; setup_ms is each problem's build time.
+ *   setup_threads  concurrent builds (0 = 2).
+ * p->precond must be NULL.  Returns JD_OK, JD_ENOCONV if some problem did
+ * not converge (its stats say how far it got; the others complete), or the
+ * first fatal error (the remaining problems are abandoned).
+ */
+int jd_solve_batch(const anderson_t* hs, int nprob, const double* sigma, const int* k, double tol,
+                   const jd_params* p, double* const* evals, double* const* evecs, jd_stats* stats,
+                   int setup_threads, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

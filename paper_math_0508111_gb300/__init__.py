@@ -285,3 +285,34 @@ def solve(lattice, sigma, k, tol, precision=JD_FP64, vectors=True, stream=None, 
     stats = _stats_dict(st)
     stats["status"] = rc
     return ev, (X.T if vectors else None), stats
+
+
+def solve_batch(lattices, sigmas, ks, tol, precision=JD_FP64, vectors=True, setup_threads=2, stream=None,
+                raise_on_noconv=True, **params):
+    """Independent problems through jd_solve_batch: later problems'
+    preconditioners are built on host threads while earlier ones solve.
+
+    ``sigmas`` and ``ks`` are scalars or one entry per lattice.  Returns a
+    list of (evals, evecs, stats) like :func:`solve`."""
+    m = len(lattices)
+    sig = np.broadcast_to(np.asarray(sigmas, dtype=np.float64), (m,)).copy()
+    kk = np.broadcast_to(np.asarray(ks, dtype=np.int32), (m,)).copy()
+    p = jd_params(precision=precision, **params)
+    evs = [np.zeros(int(kk[i])) for i in range(m)]
+    Xs = [np.zeros((int(kk[i]), lat.n)) for i, lat in enumerate(lattices)] if vectors else None
+    vp = ctypes.c_void_p
+    hs = (vp * max(m, 1))(*[lat.handle for lat in lattices])
+    ep = (vp * max(m, 1))(*[e.ctypes.data for e in evs])
+    xp = (vp * max(m, 1))(*[x.ctypes.data for x in Xs]) if vectors else None
+    sts = (_ffi.JdStats * max(m, 1))()
+    rc = _ffi.lib().jd_solve_batch(hs, m, sig.ctypes.data_as(vp), kk.ctypes.data_as(vp), float(tol),
+                                   ctypes.byref(p), ep, xp, sts, int(setup_threads),
+                                   _stream_handle(stream) if stream is not None else None)
+    if rc != JD_OK and (rc != JD_ENOCONV or raise_on_noconv):
+        _ffi.check(rc, "jd_solve_batch")
+    out = []
+    for i in range(m):
+        stats = _stats_dict(sts[i])
+        stats["status"] = JD_OK if stats["nconv"] >= kk[i] else JD_ENOCONV
+        out.append((evs[i], (Xs[i].T if vectors else None), stats))
+    return out

@@ -75,6 +75,8 @@ SIGNATURES = [
     ("jd_params_default", c_int, [P(JdParams)]),
     ("jd_solve", c_int, [c_void_p, c_double, c_int, c_double, P(JdParams), c_void_p, c_void_p, P(JdStats),
                          c_void_p]),
+    ("jd_solve_batch", c_int, [c_void_p, c_int, c_void_p, c_void_p, c_double, P(JdParams), c_void_p, c_void_p,
+                               c_void_p, c_int, c_void_p]),
 ]
 
 _lib = None

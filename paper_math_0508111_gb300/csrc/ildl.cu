@@ -484,32 +484,33 @@ void free_dev(DevFactor<T>& d) {
 }
 
 template <typename S, typename D>
-int upload(D** dst, const std::vector<S>& src) {
+int upload(D** dst, const std::vector<S>& src, cudaStream_t st) {
   *dst = nullptr;
   if (src.empty()) return JD_OK;
   std::vector<D> tmp(src.begin(), src.end());
   cudaError_t e = cudaMalloc(dst, tmp.size() * sizeof(D));
   if (e != cudaSuccess) return fail(e == cudaErrorMemoryAllocation ? JD_ENOMEM : JD_EDEVICE, "ildl upload: %s", cudaGetErrorString(e));
-  AJD_CUDA(cudaMemcpy(*dst, tmp.data(), tmp.size() * sizeof(D), cudaMemcpyHostToDevice));
+  AJD_CUDA(cudaMemcpyAsync(*dst, tmp.data(), tmp.size() * sizeof(D), cudaMemcpyHostToDevice, st));
+  AJD_CUDA(cudaStreamSynchronize(st));  // tmp is released on return
   return JD_OK;
 }
 
 template <typename T>
-int upload_factor(const HostFactor& F, DevFactor<T>& d) {
+int upload_factor(const HostFactor& F, DevFactor<T>& d, cudaStream_t st) {
   if (F.Lcol.size() >= (size_t)1 << 31) return fail(JD_ENOMEM, "ildl: factor has more than 2^31 entries");
   std::vector<int> lp(F.Lptr.begin(), F.Lptr.end()), up(F.Uptr.begin(), F.Uptr.end());
-  AJD_TRY(upload(&d.perm, F.perm));
-  AJD_TRY(upload(&d.scale, F.scale));
-  AJD_TRY(upload(&d.Lptr, lp));
-  AJD_TRY(upload(&d.Lcol, F.Lcol));
-  AJD_TRY(upload(&d.Lval, F.Lval));
-  AJD_TRY(upload(&d.Uptr, up));
-  AJD_TRY(upload(&d.Ucol, F.Ucol));
-  AJD_TRY(upload(&d.Uval, F.Uval));
-  AJD_TRY(upload(&d.dd, F.dinv_d));
-  AJD_TRY(upload(&d.dof, F.dinv_o));
-  AJD_TRY(upload(&d.partner, F.partner));
-  AJD_TRY(upload(&d.dense, F.dense_inv));
+  AJD_TRY(upload(&d.perm, F.perm, st));
+  AJD_TRY(upload(&d.scale, F.scale, st));
+  AJD_TRY(upload(&d.Lptr, lp, st));
+  AJD_TRY(upload(&d.Lcol, F.Lcol, st));
+  AJD_TRY(upload(&d.Lval, F.Lval, st));
+  AJD_TRY(upload(&d.Uptr, up, st));
+  AJD_TRY(upload(&d.Ucol, F.Ucol, st));
+  AJD_TRY(upload(&d.Uval, F.Uval, st));
+  AJD_TRY(upload(&d.dd, F.dinv_d, st));
+  AJD_TRY(upload(&d.dof, F.dinv_o, st));
+  AJD_TRY(upload(&d.partner, F.partner, st));
+  AJD_TRY(upload(&d.dense, F.dense_inv, st));
   AJD_CUDA(cudaMalloc(&d.w, std::max<size_t>(1, F.n) * sizeof(T)));
   AJD_CUDA(cudaMalloc(&d.z, std::max<size_t>(1, F.n) * sizeof(T)));
   if (sizeof(T) == 4) {  // binary64 work vectors of the mixed apply
@@ -539,11 +540,15 @@ int upload_factor(const HostFactor& F, DevFactor<T>& d) {
   }
   d.nphase = (int)ph.size();
   AJD_CUDA(cudaMalloc(&d.phases, std::max<size_t>(1, ph.size()) * sizeof(int4)));
-  if (!ph.empty()) AJD_CUDA(cudaMemcpy(d.phases, ph.data(), ph.size() * sizeof(int4), cudaMemcpyHostToDevice));
+  if (!ph.empty()) {
+    AJD_CUDA(cudaMemcpyAsync(d.phases, ph.data(), ph.size() * sizeof(int4), cudaMemcpyHostToDevice, st));
+    AJD_CUDA(cudaStreamSynchronize(st));
+  }
   // barrier words on separate 128-byte lines: [0] arrivals, [32] generation,
   // [64] timeout flag
   AJD_CUDA(cudaMalloc(&d.bar, 96 * sizeof(unsigned)));
-  AJD_CUDA(cudaMemset(d.bar, 0, 96 * sizeof(unsigned)));
+  AJD_CUDA(cudaMemsetAsync(d.bar, 0, 96 * sizeof(unsigned), st));
+  AJD_CUDA(cudaStreamSynchronize(st));
   int per_sm = 0;
   AJD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ildl_apply_persistent_kernel<T, double>, kPersistThreads, 0));
   if (per_sm < 1) return fail(JD_EDEVICE, "ildl: persistent apply kernel cannot be resident");
@@ -647,7 +652,7 @@ template int ildl_apply_dev<float>(const ildl_s*, const float*, float*, cudaStre
 
 // Invert the dense trailing block (host matrix in, host inverse out) on the
 // current device.
-int invert_dense_on_device(std::vector<double>& M, int m) {
+int invert_dense_on_device(std::vector<double>& M, int m, cudaStream_t st) {
   if (m == 0) return JD_OK;
   double *A = nullptr, *X = nullptr, *f = nullptr, *pv = nullptr;
   int *piv = nullptr, *bad = nullptr;
@@ -659,24 +664,25 @@ int invert_dense_on_device(std::vector<double>& M, int m) {
   if (e == cudaSuccess) e = cudaMalloc(&piv, sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc(&bad, sizeof(int));
   int rc = JD_OK;
-  if (e == cudaSuccess) e = cudaMemcpy(A, M.data(), bytes, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemset(bad, 0, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemcpyAsync(A, M.data(), bytes, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(bad, 0, sizeof(int), st);
   if (e == cudaSuccess) {
     const int gb = std::max(1, std::min(ceil_div((int64_t)m * m, 256), 8 * sm_count()));
-    identity_kernel<<<gb, 256>>>(X, m);
+    identity_kernel<<<gb, 256, 0, st>>>(X, m);
     const int cb = ceil_div(m, 256);
     for (int c = 0; c < m; ++c) {
-      gj_pivot_kernel<<<1, 1024>>>(A, m, c, piv, pv, bad);
-      gj_swap_scale_kernel<<<cb, 256>>>(A, X, m, c, piv, pv);
-      gj_save_col_kernel<<<cb, 256>>>(A, m, c, f);
-      gj_eliminate_kernel<<<gb, 256>>>(A, X, m, c, f);
+      gj_pivot_kernel<<<1, 1024, 0, st>>>(A, m, c, piv, pv, bad);
+      gj_swap_scale_kernel<<<cb, 256, 0, st>>>(A, X, m, c, piv, pv);
+      gj_save_col_kernel<<<cb, 256, 0, st>>>(A, m, c, f);
+      gj_eliminate_kernel<<<gb, 256, 0, st>>>(A, X, m, c, f);
     }
-    gj_symmetrize_kernel<<<gb, 256>>>(X, m);
+    gj_symmetrize_kernel<<<gb, 256, 0, st>>>(X, m);
     count_launches(4 * m + 2);
     e = cudaGetLastError();
     int hbad = 0;
-    if (e == cudaSuccess) e = cudaMemcpy(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost);
-    if (e == cudaSuccess) e = cudaMemcpy(M.data(), X, bytes, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(M.data(), X, bytes, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e == cudaSuccess && hbad) rc = fail(JD_ESETUP, "ildl: the final dense block (%d rows) is singular", m);
   }
   if (e != cudaSuccess) rc = fail(JD_EDEVICE, "ildl dense inverse: %s", cudaGetErrorString(e));
@@ -689,13 +695,13 @@ int invert_dense_on_device(std::vector<double>& M, int m) {
   return rc;
 }
 
-int ildl_upload_all(ildl_s* f) {
+int ildl_upload_all(ildl_s* f, cudaStream_t st) {
   if (f->F.dense_is_matrix) {
-    AJD_TRY(invert_dense_on_device(f->F.dense_inv, f->F.n_dense));
+    AJD_TRY(invert_dense_on_device(f->F.dense_inv, f->F.n_dense, st));
     f->F.dense_is_matrix = false;
   }
-  AJD_TRY(upload_factor<double>(f->F, f->d64));
-  AJD_TRY(upload_factor<float>(f->F, f->d32));
+  AJD_TRY(upload_factor<double>(f->F, f->d64, st));
+  AJD_TRY(upload_factor<float>(f->F, f->d32, st));
   return JD_OK;
 }
 
@@ -863,7 +869,10 @@ extern "C" int ildl_matching(int n, const int64_t* rowptr, const int* col, const
   }
 }
 
-extern "C" int ildl_create(anderson_t h, double sigma, const ildl_params* p, ildl_t* out) {
+namespace ajd {
+// ildl_create with the device work (potential download, dense inverse,
+// upload) on `st`
+int ildl_create_on_stream(anderson_t h, double sigma, const ildl_params* p, ildl_t* out, cudaStream_t st) {
   if (!out || !h) return fail(JD_EINVAL, "ildl_create: NULL argument");
   *out = nullptr;
   if (!std::isfinite(sigma)) return fail(JD_EINVAL, "ildl_create: sigma must be finite");
@@ -871,14 +880,15 @@ extern "C" int ildl_create(anderson_t h, double sigma, const ildl_params* p, ild
   AJD_TRY(check_params(p, prm));
   try {
     std::vector<double> eps(h->n);
-    AJD_CUDA(cudaMemcpy(eps.data(), h->eps64, h->n * sizeof(double), cudaMemcpyDeviceToHost));
+    AJD_CUDA(cudaMemcpyAsync(eps.data(), h->eps64, h->n * sizeof(double), cudaMemcpyDeviceToHost, st));
+    AJD_CUDA(cudaStreamSynchronize(st));
     SymCsr A;
     lattice_csr(h, eps, sigma, A);
     ildl_s* f = new ildl_s();
     f->device = h->device;
     const auto t0 = std::chrono::steady_clock::now();
     int rc = build_ildl(A, prm, f->F, /*dense_on_host=*/false);
-    if (rc == JD_OK) rc = ildl_upload_all(f);
+    if (rc == JD_OK) rc = ildl_upload_all(f, st);
     f->F.t_total_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     if (rc != JD_OK) {
       ildl_free_device(f);
@@ -890,6 +900,11 @@ extern "C" int ildl_create(anderson_t h, double sigma, const ildl_params* p, ild
   } catch (const std::bad_alloc&) {
     return fail(JD_ENOMEM, "ildl_create: out of host memory");
   }
+}
+}  // namespace ajd
+
+extern "C" int ildl_create(anderson_t h, double sigma, const ildl_params* p, ildl_t* out) {
+  return ajd::ildl_create_on_stream(h, sigma, p, out, 0);
 }
 
 extern "C" int ildl_info(ildl_t f, ildl_info_t* info) {

@@ -54,6 +54,9 @@ int ildl_apply_dev(const ildl_s* f, const T* b, T* out, cudaStream_t stream);
 // x = K^{-1} b with the binary32 factor, binary64 vectors and sums.
 int ildl_apply_dev_mixed(const ildl_s* f, const double* b, double* out, cudaStream_t stream);
 
+// ildl_create with its device work on stream `st`.
+int ildl_create_on_stream(anderson_t h, double sigma, const ildl_params* p, ildl_t* out, cudaStream_t st);
+
 // JD_EDEVICE if a device-side wait of an apply timed out (reads a flag).
 int ildl_check_device_error(const ildl_s* f);
 

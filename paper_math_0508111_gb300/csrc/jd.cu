@@ -20,6 +20,13 @@
 #include <cstdlib>
 #include <limits>
 #include <type_traits>
+#include <atomic>
+#include <condition_variable>
+#include <mutex>
+#include <string>
+#include <thread>
+
+#include <omp.h>
 
 #include "anderson_impl.cuh"
 #include "ildl_impl.cuh"
@@ -1310,6 +1317,8 @@ extern "C" int jd_params_default(jd_params* p) {
   return JD_OK;
 }
 
+static int normalize_params(const jd_params* p, jd_params& prm);
+
 extern "C" int jd_solve(anderson_t h, double sigma, int k, double tol, const jd_params* p, double* evals,
                         double* evecs, jd_stats* st, void* stream) {
   if (!h || !evals) return fail(JD_EINVAL, "jd_solve: NULL handle or evals");
@@ -1317,21 +1326,7 @@ extern "C" int jd_solve(anderson_t h, double sigma, int k, double tol, const jd_
   if (k < 1 || k > 64 || (int64_t)k >= h->n) return fail(JD_EINVAL, "jd_solve: need 1 <= k <= 64 and k < n");
   if (!(tol > 0.0)) return fail(JD_EINVAL, "jd_solve: tol must be > 0");
   jd_params prm;
-  jd_params_default(&prm);
-  if (p) {
-    prm = *p;
-    jd_params d;
-    jd_params_default(&d);
-    if (prm.max_outer <= 0) prm.max_outer = d.max_outer;
-    if (prm.max_inner <= 0) prm.max_inner = d.max_inner;
-    if (!(prm.inner_decay > 0.0 && prm.inner_decay < 1.0)) prm.inner_decay = d.inner_decay;
-    if (!(prm.inner_floor >= 0.0)) prm.inner_floor = d.inner_floor;
-    if (prm.extraction != 0 && prm.extraction != 1) prm.extraction = d.extraction;
-    if (!(prm.switch_tol > 0.0)) prm.switch_tol = d.switch_tol;
-    if (prm.ildl.kappa == 0.0 && prm.ildl.max_levels == 0 && prm.ildl.n_dense == 0) prm.ildl = d.ildl;
-  }
-  if (prm.precision != JD_FP64 && prm.precision != JD_FP32 && prm.precision != JD_MIXED)
-    return fail(JD_EINVAL, "jd_solve: unknown precision");
+  AJD_TRY(normalize_params(p, prm));
   if (st) std::memset(st, 0, sizeof(*st));
   using Clock = std::chrono::steady_clock;
   const auto t0 = Clock::now();
@@ -1352,4 +1347,129 @@ extern "C" int jd_solve(anderson_t h, double sigma, int k, double tol, const jd_
   }
   if (own) ildl_destroy(pc);
   return rc;
+}
+
+static int normalize_params(const jd_params* p, jd_params& prm) {
+  jd_params_default(&prm);
+  if (p) {
+    prm = *p;
+    jd_params d;
+    jd_params_default(&d);
+    if (prm.max_outer <= 0) prm.max_outer = d.max_outer;
+    if (prm.max_inner <= 0) prm.max_inner = d.max_inner;
+    if (!(prm.inner_decay > 0.0 && prm.inner_decay < 1.0)) prm.inner_decay = d.inner_decay;
+    if (!(prm.inner_floor >= 0.0)) prm.inner_floor = d.inner_floor;
+    if (prm.extraction != 0 && prm.extraction != 1) prm.extraction = d.extraction;
+    if (!(prm.switch_tol > 0.0)) prm.switch_tol = d.switch_tol;
+    if (prm.ildl.kappa == 0.0 && prm.ildl.max_levels == 0 && prm.ildl.n_dense == 0) prm.ildl = d.ildl;
+  }
+  if (prm.precision != JD_FP64 && prm.precision != JD_FP32 && prm.precision != JD_MIXED)
+    return fail(JD_EINVAL, "jd_solve: unknown precision");
+  return JD_OK;
+}
+
+// ------------------------------------------------------------ batches ---
+// Independent problems, pipelined: `setup_threads` host threads build the
+// preconditioners of problems i+1, i+2, ... (host C++ with OpenMP, device
+// upload on their own streams) while the calling thread solves problem i
+// on `stream`.  At most setup_threads + 1 factors are alive at any time.
+extern "C" int jd_solve_batch(const anderson_t* hs, int nprob, const double* sigma, const int* k, double tol,
+                              const jd_params* p, double* const* evals, double* const* evecs, jd_stats* stats,
+                              int setup_threads, void* stream) {
+  if (nprob < 0 || (nprob > 0 && (!hs || !sigma || !k || !evals)))
+    return fail(JD_EINVAL, "jd_solve_batch: bad arguments");
+  if (!(tol > 0.0)) return fail(JD_EINVAL, "jd_solve_batch: tol must be > 0");
+  for (int i = 0; i < nprob; ++i) {
+    if (!hs[i] || !evals[i] || !std::isfinite(sigma[i]) || k[i] < 1 || k[i] > 64 || (int64_t)k[i] >= hs[i]->n)
+      return fail(JD_EINVAL, "jd_solve_batch: bad problem %d", i);
+  }
+  if (nprob == 0) return JD_OK;
+  jd_params prm;
+  AJD_TRY(normalize_params(p, prm));
+  if (prm.precond) return fail(JD_EINVAL, "jd_solve_batch: a prebuilt preconditioner is per problem; pass NULL");
+  if (stats) std::memset(stats, 0, sizeof(jd_stats) * nprob);
+  const int nthr = std::max(1, std::min(setup_threads > 0 ? setup_threads : 2, nprob));
+  const int omp_total = std::max(1, omp_get_max_threads());
+  const int omp_each = std::max(1, omp_total / nthr);
+  int dev = 0;
+  AJD_CUDA(cudaGetDevice(&dev));
+
+  std::vector<ildl_t> pcs(nprob, nullptr);
+  std::vector<int> setup_rc(nprob, JD_OK);
+  std::vector<std::string> setup_msg(nprob);
+  std::vector<double> setup_ms(nprob, 0.0);
+  std::vector<char> ready(nprob, 0);
+  std::mutex mu;
+  std::condition_variable cv;
+  std::atomic<int> next{0};
+  int solved = 0;  // guarded by mu
+  bool abort_all = false;
+
+  auto worker = [&]() {
+    cudaSetDevice(dev);
+    omp_set_num_threads(omp_each);
+    cudaStream_t st = nullptr;
+    cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    for (;;) {
+      const int i = next.fetch_add(1);
+      if (i >= nprob) break;
+      {
+        std::unique_lock<std::mutex> lk(mu);  // bound the factors alive
+        cv.wait(lk, [&] { return abort_all || i <= solved + nthr; });
+        if (abort_all) break;
+      }
+      const auto t0 = std::chrono::steady_clock::now();
+      ildl_t pc = nullptr;
+      const int rc = ildl_create_on_stream(hs[i], sigma[i], &prm.ildl, &pc, st);
+      const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+      std::lock_guard<std::mutex> lk(mu);
+      pcs[i] = pc;
+      setup_rc[i] = rc;
+      if (rc != JD_OK) setup_msg[i] = jd_last_error();
+      setup_ms[i] = ms;
+      ready[i] = 1;
+      cv.notify_all();
+    }
+    if (st) cudaStreamDestroy(st);
+  };
+  std::vector<std::thread> pool;
+  for (int t = 0; t < nthr; ++t) pool.emplace_back(worker);
+
+  int status = JD_OK;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  for (int i = 0; i < nprob; ++i) {
+    {
+      std::unique_lock<std::mutex> lk(mu);
+      cv.wait(lk, [&] { return ready[i] != 0; });
+    }
+    jd_stats* st = stats ? &stats[i] : nullptr;
+    int rc = setup_rc[i];
+    if (rc == JD_OK) {
+      if (st) {
+        st->setup_ms = setup_ms[i];
+        ildl_info(pcs[i], &st->ildl);
+      }
+      JdSolver solver(hs[i], pcs[i], prm, sigma[i], k[i], tol, s);
+      rc = solver.run(evals[i], evecs ? evecs[i] : nullptr, st);
+      ildl_destroy(pcs[i]);
+      pcs[i] = nullptr;
+    } else {
+      set_error_msg("%s", setup_msg[i].c_str());
+    }
+    {
+      std::lock_guard<std::mutex> lk(mu);
+      ++solved;
+      if (rc != JD_OK && rc != JD_ENOCONV) abort_all = true;
+      cv.notify_all();
+    }
+    if (rc != JD_OK && status == JD_OK) status = rc;
+    if (rc != JD_OK && rc != JD_ENOCONV) {
+      // fatal: stop the pipeline; release what the workers built
+      for (auto& t : pool) t.join();
+      for (auto& pc : pcs) ildl_destroy(pc);
+      return fail(rc, "jd_solve_batch: problem %d: %s", i, jd_last_error());
+    }
+  }
+  for (auto& t : pool) t.join();
+  return status;
 }

@@ -56,3 +56,18 @@ def test_argument_validation_without_gpu(built_lib):
     assert L.anderson_create(1300, 1.0, 1, _ffi.JD_HARDWALL, ctypes.byref(h)) == _ffi.JD_EINVAL
     assert L.anderson_destroy(None) == _ffi.JD_OK
     assert L.jd_version() >= 100
+
+
+def test_batch_argument_validation_without_gpu(built_lib):
+    """jd_solve_batch rejects bad arguments before touching a device."""
+    from paper_math_0508111_gb300 import _ffi
+    L = _ffi.lib()
+    assert L.jd_solve_batch(None, 0, None, None, 1e-8, None, None, None, None, 0, None) == _ffi.JD_OK
+    assert L.jd_solve_batch(None, 2, None, None, 1e-8, None, None, None, None, 0, None) == _ffi.JD_EINVAL
+    assert L.jd_solve_batch(None, -1, None, None, 1e-8, None, None, None, None, 0, None) == _ffi.JD_EINVAL
+    hs = (ctypes.c_void_p * 1)(None)
+    sig = (ctypes.c_double * 1)(0.0)
+    kk = (ctypes.c_int * 1)(1)
+    ev = (ctypes.c_void_p * 1)(None)
+    assert L.jd_solve_batch(hs, 1, sig, kk, 1e-8, None, ev, None, None, 0, None) == _ffi.JD_EINVAL
+    assert b"problem 0" in L.jd_last_error()

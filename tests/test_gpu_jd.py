@@ -181,3 +181,31 @@ def test_jd_noconv_reports_prefix(ajd):
         ev, X, st = ajd.solve(h, 0.0, 5, 1e-11, max_outer=12, raise_on_noconv=False)
     assert st["status"] == ajd.JD_ENOCONV
     assert 0 <= st["nconv"] < 5
+
+
+@pytest.mark.parametrize("threads,prec", [(1, 0), (3, 2)])
+def test_jd_batch_matches_single_solves(ajd, threads, prec):
+    """The pipelined batch returns, per problem, the pairs of the oracle and
+    of a single jd_solve of the same problem."""
+    cases = [(10, 16.5, 11, 0, 0.0, 4), (12, 12.0, 12, 1, -1.0, 3), (8, 16.5, 13, 0, 0.5, 5),
+             (11, 21.0, 14, 0, 1.5, 2), (9, 16.5, 15, 1, 0.0, 6)]
+    tol = 1e-11 if prec == 0 else 1e-10
+    hs = [ajd.Anderson(L, W, s, bc) for (L, W, s, bc, _, _) in cases]
+    try:
+        out = ajd.solve_batch(hs, [c[4] for c in cases], [c[5] for c in cases], tol, precision=prec,
+                              setup_threads=threads)
+        for (L, W, s, bc, sigma, k), h, (ev, X, st) in zip(cases, hs, out):
+            _check_pairs(L, W, s, bc, sigma, k, ev, X, st, tol)
+            assert st["setup_ms"] > 0
+            ev1, _, _ = ajd.solve(h, sigma, k, tol, precision=prec)
+            assert np.abs(ev - ev1).max() <= 1e-10 * (6 + W / 2)
+    finally:
+        for h in hs:
+            h.close()
+
+
+def test_jd_batch_empty_and_errors(ajd):
+    assert ajd.solve_batch([], 0.0, 1, 1e-8) == []
+    with ajd.Anderson(4, 16.5, 1) as h:
+        with pytest.raises(ajd.JDError):
+            ajd.solve_batch([h, h], [0.0, 0.0], [2, 64], 1e-8)
