@@ -26,113 +26,6 @@
 namespace ajd {
 namespace {
 
-constexpr int kRowThreads = 256;
-
-// Forward sweep of one level: w[p] = s[p] b[perm[p]] - sum_q L[p,q] w[q]
-// for positions p in [p0, p1); G threads per row.
-template <typename T, int G>
-__global__ void __launch_bounds__(kRowThreads)
-fwd_level_kernel(const int* __restrict__ ptr, const int* __restrict__ col, const T* __restrict__ val,
-                 const T* __restrict__ scale, const int* __restrict__ perm, const T* __restrict__ b,
-                 T* __restrict__ w, int p0, int p1) {
-  const int lane = threadIdx.x % G;
-  const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; ; t += nthreads) {
-    const int64_t rr = t / G;
-    const int p = p0 + (int)rr;
-    const bool active = p < p1;
-    if (__all_sync(0xffffffffu, !active)) break;
-    T acc = T(0);
-    if (active) {
-      const int e = ptr[p + 1];
-      int q = ptr[p] + lane;
-      T a1 = T(0), a2 = T(0), a3 = T(0);
-      for (; q + 3 * G < e; q += 4 * G) {
-        acc += val[q] * w[col[q]];
-        a1 += val[q + G] * w[col[q + G]];
-        a2 += val[q + 2 * G] * w[col[q + 2 * G]];
-        a3 += val[q + 3 * G] * w[col[q + 3 * G]];
-      }
-      for (; q < e; q += G) acc += val[q] * w[col[q]];
-      acc = (acc + a1) + (a2 + a3);
-    }
-#pragma unroll
-    for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, G);
-    if (active && lane == 0) w[p] = scale[p] * b[perm[p]] - acc;
-  }
-}
-
-// Level 0 has no entries of L: w[p] = s[p] b[perm[p]].
-template <typename T>
-__global__ void gather_kernel(const T* __restrict__ scale, const int* __restrict__ perm,
-                              const T* __restrict__ b, T* __restrict__ w, int p0, int p1) {
-  for (int p = p0 + blockIdx.x * blockDim.x + threadIdx.x; p < p1; p += gridDim.x * blockDim.x)
-    w[p] = scale[p] * b[perm[p]];
-}
-
-// Dense trailing block: z[d0 + r] = sum_c Dinv[r][c] w[d0 + c], also
-// scattered to the output: out[perm[d0 + r]] = s[d0 + r] z[d0 + r].
-// One warp per row.
-template <typename T>
-__global__ void dense_kernel(const T* __restrict__ dinv, int nd, int d0, const T* __restrict__ w,
-                             T* __restrict__ z, const T* __restrict__ scale, const int* __restrict__ perm,
-                             T* __restrict__ out) {
-  const int lane = threadIdx.x & 31;
-  const int warps = (gridDim.x * blockDim.x) >> 5;
-  for (int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < nd; r += warps) {
-    const T* row = dinv + (int64_t)r * nd;
-    T acc = T(0);
-    for (int c = lane; c < nd; c += 32) acc += row[c] * w[d0 + c];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) {
-      z[d0 + r] = acc;
-      out[perm[d0 + r]] = scale[d0 + r] * acc;
-    }
-  }
-}
-
-// Backward sweep of one level: z[p] = (D^{-1} w)_p - sum_q L^T[p,q] z[q],
-// out[perm[p]] = s[p] z[p].
-template <typename T, int G>
-__global__ void __launch_bounds__(kRowThreads)
-bwd_level_kernel(const int* __restrict__ ptr, const int* __restrict__ col, const T* __restrict__ val,
-                 const T* __restrict__ dd, const T* __restrict__ dof, const int* __restrict__ partner,
-                 const T* __restrict__ w, T* __restrict__ z, const T* __restrict__ scale,
-                 const int* __restrict__ perm, T* __restrict__ out, int p0, int p1) {
-  const int lane = threadIdx.x % G;
-  const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; ; t += nthreads) {
-    const int p = p0 + (int)(t / G);
-    const bool active = p < p1;
-    if (__all_sync(0xffffffffu, !active)) break;
-    T acc = T(0);
-    if (active) {
-      const int e = ptr[p + 1];
-      int q = ptr[p] + lane;
-      T a1 = T(0), a2 = T(0), a3 = T(0);
-      for (; q + 3 * G < e; q += 4 * G) {
-        acc += val[q] * z[col[q]];
-        a1 += val[q + G] * z[col[q + G]];
-        a2 += val[q + 2 * G] * z[col[q + 2 * G]];
-        a3 += val[q + 3 * G] * z[col[q + 3 * G]];
-      }
-      for (; q < e; q += G) acc += val[q] * z[col[q]];
-      acc = (acc + a1) + (a2 + a3);
-    }
-#pragma unroll
-    for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, G);
-    if (active && lane == 0) {
-      const int pp = partner[p];
-      T d = dd[p] * w[p];
-      if (pp >= 0) d += dof[p] * w[pp];
-      const T zp = d - acc;
-      z[p] = zp;
-      out[perm[p]] = scale[p] * zp;
-    }
-  }
-}
-
 // ---- Gauss–Jordan inversion of the dense trailing block (setup) ----
 // A and X are m x m row-major binary64; X starts as I and ends as A^{-1}.
 // Pivot c: argmax_{r >= c} |A[r][c]| (ties: smallest r).
@@ -241,10 +134,11 @@ enum { PH_GATHER = 0, PH_FWD = 1, PH_DENSE = 2, PH_BWD = 3 };
 constexpr int kPersistThreads = 512;
 constexpr unsigned kSpinLimit = 1u << 22;  // ~0.1-0.5 s at 32-128 ns per poll
 
-// V: type of the stored factor values; X: type of the vectors and of the
-// accumulation (V = X for the binary64 and binary32 applies; V = float,
-// X = double for the mixed apply: binary32 factor traffic, binary64 sums).
-template <typename V, typename X>
+// V: type of the stored factor values; X: type of the work vectors and of
+// the accumulation; IO: type of the caller's b and x (V = X = IO for the
+// binary64 and binary32 applies; V = X = float, IO = double for the mixed
+// apply, which converts at the gather and at the final scaling).
+template <typename V, typename X, typename IO = X>
 struct ApplyArgs {
   const int* perm;
   const V* scale;
@@ -260,8 +154,8 @@ struct ApplyArgs {
   const V* dense;
   X* w;
   X* z;
-  const X* b;
-  X* out;
+  const IO* b;
+  IO* out;
   int nd, d0;
 };
 
@@ -303,8 +197,8 @@ __device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned* gen, uns
   return failed == 0;
 }
 
-template <typename V, typename X, int G>
-__device__ __forceinline__ void finish_row(const ApplyArgs<V, X>& a, int kind, int p, X acc, int lane, X rhs) {
+template <typename V, typename X, typename IO, int G>
+__device__ __forceinline__ void finish_row(const ApplyArgs<V, X, IO>& a, int kind, int p, X acc, int lane, X rhs) {
 #pragma unroll
   for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, G);
   if (p >= 0 && lane == 0) {
@@ -316,7 +210,7 @@ __device__ __forceinline__ void finish_row(const ApplyArgs<V, X>& a, int kind, i
       if (pp >= 0) d += (X)__ldg(a.dof + p) * __ldcg(a.w + pp);
       const X zp = d - acc;
       __stcg(a.z + p, zp);
-      a.out[__ldg(a.perm + p)] = (X)__ldg(a.scale + p) * zp;
+      a.out[__ldg(a.perm + p)] = (IO)((X)__ldg(a.scale + p) * zp);
     }
   }
 }
@@ -324,8 +218,8 @@ __device__ __forceinline__ void finish_row(const ApplyArgs<V, X>& a, int kind, i
 // Rows of one level, G threads per row; each group handles two rows at a
 // time with their loads interleaved (index/value loads of both rows first,
 // then the gathers), so every memory latency is shared by two rows.
-template <typename V, typename X, int G>
-__device__ __forceinline__ void level_rows(const ApplyArgs<V, X>& a, int kind, int p0, int p1) {
+template <typename V, typename X, typename IO, int G>
+__device__ __forceinline__ void level_rows(const ApplyArgs<V, X, IO>& a, int kind, int p0, int p1) {
   const int lane = threadIdx.x % G;
   const int64_t groups = (int64_t)gridDim.x * blockDim.x / G;
   const int64_t g0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
@@ -352,35 +246,39 @@ __device__ __forceinline__ void level_rows(const ApplyArgs<V, X>& a, int kind, i
     }
     X acca = X(0), accb = X(0);
     while (qa < ea || qb < eb) {
+      // lanes past the end of a row gather nothing: the solution entry they
+      // would point at may not be written yet in this sweep (0 * NaN = NaN)
       int ca[B], cb[B];
       V va[B], vb[B];
 #pragma unroll
       for (int i = 0; i < B; ++i) {
         const int q1 = qa + i * G, q2 = qb + i * G;
         const bool o1 = q1 < ea, o2 = q2 < eb;
-        ca[i] = o1 ? __ldg(col + q1) : 0;
+        ca[i] = o1 ? __ldg(col + q1) : -1;
         va[i] = o1 ? __ldg(val + q1) : V(0);
-        cb[i] = o2 ? __ldg(col + q2) : 0;
+        cb[i] = o2 ? __ldg(col + q2) : -1;
         vb[i] = o2 ? __ldg(val + q2) : V(0);
       }
 #pragma unroll
       for (int i = 0; i < B; ++i) {
-        acca += (X)va[i] * __ldcg(x + ca[i]);
-        accb += (X)vb[i] * __ldcg(x + cb[i]);
+        const X xa = ca[i] >= 0 ? __ldcg(x + ca[i]) : X(0);
+        const X xb = cb[i] >= 0 ? __ldcg(x + cb[i]) : X(0);
+        acca += (X)va[i] * xa;
+        accb += (X)vb[i] * xb;
       }
       qa += B * G;
       qb += B * G;
     }
-    finish_row<V, X, G>(a, kind, pa, acca, lane, ra_rhs);
-    finish_row<V, X, G>(a, kind, pb, accb, lane, rb_rhs);
+    finish_row<V, X, IO, G>(a, kind, pa, acca, lane, ra_rhs);
+    finish_row<V, X, IO, G>(a, kind, pb, accb, lane, rb_rhs);
   }
 }
 
 // Prefetch the stored rows of a level phase into L2 (lines strided over the
 // whole grid); skipped for phases larger than 16 MB, which stream from HBM
 // at full bandwidth anyway.
-template <typename V, typename X>
-__device__ __forceinline__ void prefetch_phase(const ApplyArgs<V, X>& a, int4 P) {
+template <typename V, typename X, typename IO>
+__device__ __forceinline__ void prefetch_phase(const ApplyArgs<V, X, IO>& a, int4 P) {
   if (P.x != PH_FWD && P.x != PH_BWD) return;
   const int* ptr = P.x == PH_FWD ? a.Lptr : a.Uptr;
   const int* col = P.x == PH_FWD ? a.Lcol : a.Ucol;
@@ -400,9 +298,9 @@ __device__ __forceinline__ void prefetch_phase(const ApplyArgs<V, X>& a, int4 P)
   }
 }
 
-template <typename V, typename X>
+template <typename V, typename X, typename IO>
 __global__ void __launch_bounds__(kPersistThreads, 1)
-ildl_apply_persistent_kernel(ApplyArgs<V, X> a, const int4* __restrict__ phases, int nphase, unsigned* count,
+ildl_apply_persistent_kernel(ApplyArgs<V, X, IO> a, const int4* __restrict__ phases, int nphase, unsigned* count,
                              unsigned* gen, int* err, unsigned long long* stamps) {
   for (int ph = 0; ph < nphase; ++ph) {
     const int4 P = phases[ph];  // kind, p0, p1, G
@@ -415,7 +313,7 @@ ildl_apply_persistent_kernel(ApplyArgs<V, X> a, const int4* __restrict__ phases,
     const int4 Pn = ph + 1 < nphase ? phases[ph + 1] : make_int4(-1, 0, 0, 0);
     if (kind == PH_GATHER) {
       for (int p = p0 + blockIdx.x * blockDim.x + threadIdx.x; p < p1; p += gridDim.x * blockDim.x)
-        __stcg(a.w + p, (X)__ldg(a.scale + p) * __ldg(a.b + __ldg(a.perm + p)));
+        __stcg(a.w + p, (X)__ldg(a.scale + p) * (X)__ldg(a.b + __ldg(a.perm + p)));
     } else if (kind == PH_DENSE) {
       const int lane = threadIdx.x & 31;
       const int warps = (gridDim.x * blockDim.x) >> 5;
@@ -439,18 +337,18 @@ ildl_apply_persistent_kernel(ApplyArgs<V, X> a, const int4* __restrict__ phases,
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
         if (lane == 0) {
           __stcg(a.z + a.d0 + r, acc);
-          a.out[__ldg(a.perm + a.d0 + r)] = (X)__ldg(a.scale + a.d0 + r) * acc;
+          a.out[__ldg(a.perm + a.d0 + r)] = (IO)((X)__ldg(a.scale + a.d0 + r) * acc);
         }
       }
     } else {
       switch (G) {
-        case 4: level_rows<V, X, 4>(a, kind, p0, p1); break;
-        case 8: level_rows<V, X, 8>(a, kind, p0, p1); break;
-        case 16: level_rows<V, X, 16>(a, kind, p0, p1); break;
-        default: level_rows<V, X, 32>(a, kind, p0, p1); break;
+        case 4: level_rows<V, X, IO, 4>(a, kind, p0, p1); break;
+        case 8: level_rows<V, X, IO, 8>(a, kind, p0, p1); break;
+        case 16: level_rows<V, X, IO, 16>(a, kind, p0, p1); break;
+        default: level_rows<V, X, IO, 32>(a, kind, p0, p1); break;
       }
     }
-    if (ph + 1 < nphase) prefetch_phase<V, X>(a, Pn);
+    if (ph + 1 < nphase) prefetch_phase<V, X, IO>(a, Pn);
     if (ph + 1 < nphase && !grid_barrier(count, gen, (unsigned)ph, err)) return;
   }
   if (stamps && blockIdx.x == 0 && threadIdx.x == 0) {
@@ -517,6 +415,13 @@ int upload_factor(const HostFactor& F, DevFactor<T>& d, cudaStream_t st) {
     AJD_CUDA(cudaMalloc(&d.w64, std::max<size_t>(1, F.n) * sizeof(double)));
     AJD_CUDA(cudaMalloc(&d.z64, std::max<size_t>(1, F.n) * sizeof(double)));
   }
+  if (std::getenv("AJD_POISON_ALLOC")) {  // NaN-filled work vectors (read-before-write check in tests)
+    const size_t nb = std::max<size_t>(1, F.n);
+    AJD_CUDA(cudaMemsetAsync(d.w, 0xFF, nb * sizeof(T), st));
+    AJD_CUDA(cudaMemsetAsync(d.z, 0xFF, nb * sizeof(T), st));
+    if (d.w64) AJD_CUDA(cudaMemsetAsync(d.w64, 0xFF, nb * sizeof(double), st));
+    if (d.z64) AJD_CUDA(cudaMemsetAsync(d.z64, 0xFF, nb * sizeof(double), st));
+  }
   // phase list of the persistent apply
   std::vector<int4> ph;
   const std::vector<int>& lvp = F.level_ptr;
@@ -550,40 +455,23 @@ int upload_factor(const HostFactor& F, DevFactor<T>& d, cudaStream_t st) {
   AJD_CUDA(cudaMemsetAsync(d.bar, 0, 96 * sizeof(unsigned), st));
   AJD_CUDA(cudaStreamSynchronize(st));
   int per_sm = 0;
-  AJD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ildl_apply_persistent_kernel<T, double>, kPersistThreads, 0));
+  AJD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ildl_apply_persistent_kernel<T, T, double>, kPersistThreads, 0));
   if (per_sm < 1) return fail(JD_EDEVICE, "ildl: persistent apply kernel cannot be resident");
   d.grid = sm_count();  // one CTA per SM
   d.ready = true;
   return JD_OK;
 }
 
-template <typename T, int G>
-void launch_fwd(const DevFactor<T>& d, const T* b, int p0, int p1, cudaStream_t s) {
-  const int64_t threads = (int64_t)(p1 - p0) * G;
-  const int blocks = (int)std::min<int64_t>((threads + kRowThreads - 1) / kRowThreads, 32 * sm_count());
-  fwd_level_kernel<T, G><<<blocks, kRowThreads, 0, s>>>(d.Lptr, d.Lcol, d.Lval, d.scale, d.perm, b, d.w, p0, p1);
-  count_launches();
-}
-
-template <typename T, int G>
-void launch_bwd(const DevFactor<T>& d, T* out, int p0, int p1, cudaStream_t s) {
-  const int64_t threads = (int64_t)(p1 - p0) * G;
-  const int blocks = (int)std::min<int64_t>((threads + kRowThreads - 1) / kRowThreads, 32 * sm_count());
-  bwd_level_kernel<T, G><<<blocks, kRowThreads, 0, s>>>(d.Uptr, d.Ucol, d.Uval, d.dd, d.dof, d.partner, d.w, d.z,
-                                                       d.scale, d.perm, out, p0, p1);
-  count_launches();
-}
-
 }  // namespace
 
-// One persistent apply with factor values V and vectors X.
-template <typename V, typename X>
-int launch_apply(const ildl_s* f, const DevFactor<V>& d, X* w, X* z, const X* b, X* out, cudaStream_t s) {
+// One persistent apply with factor values V, work vectors X, caller vectors IO.
+template <typename V, typename X, typename IO>
+int launch_apply(const ildl_s* f, const DevFactor<V>& d, X* w, X* z, const IO* b, IO* out, cudaStream_t s) {
   if (!d.ready) return fail(JD_EINVAL, "ildl_apply: factor has no device copy (use ildl_create)");
   const HostFactor& F = f->F;
   if (F.n == 0 || d.nphase == 0) return JD_OK;
-  ApplyArgs<V, X> a{d.perm, d.scale, d.Lptr, d.Lcol, d.Lval, d.Uptr, d.Ucol, d.Uval, d.dd, d.dof, d.partner,
-                    d.dense, w, z, b, out, F.n_dense, F.level_ptr[F.nlev]};
+  ApplyArgs<V, X, IO> a{d.perm, d.scale, d.Lptr, d.Lcol, d.Lval, d.Uptr, d.Ucol, d.Uval, d.dd, d.dof, d.partner,
+                        d.dense, w, z, b, out, F.n_dense, F.level_ptr[F.nlev]};
   AJD_CUDA(cudaMemsetAsync(d.bar, 0, 64 * sizeof(unsigned), s));  // arrivals and generation
   const int4* ph = d.phases;
   int np = d.nphase;
@@ -596,7 +484,7 @@ int launch_apply(const ildl_s* f, const DevFactor<V>& d, X* w, X* z, const X* b,
   unsigned long long* stamps = nullptr;
   if (timing) AJD_CUDA(cudaMalloc(&stamps, (np + 1) * sizeof(unsigned long long)));
   void* args[] = {&a, &ph, &np, &cnt, &gen, &err, &stamps};
-  AJD_CUDA(cudaLaunchCooperativeKernel((void*)ildl_apply_persistent_kernel<V, X>, dim3(d.grid),
+  AJD_CUDA(cudaLaunchCooperativeKernel((void*)ildl_apply_persistent_kernel<V, X, IO>, dim3(d.grid),
                                        dim3(kPersistThreads), args, 0, s));
   count_launches(2);
   if (timing) {
@@ -625,13 +513,17 @@ int launch_apply(const ildl_s* f, const DevFactor<V>& d, X* w, X* z, const X* b,
 template <typename T>
 int ildl_apply_dev(const ildl_s* f, const T* b, T* out, cudaStream_t s) {
   const DevFactor<T>& d = f->dev<T>();
-  return launch_apply<T, T>(f, d, d.w, d.z, b, out, s);
+  return launch_apply<T, T, T>(f, d, d.w, d.z, b, out, s);
 }
 
 int ildl_apply_dev_mixed(const ildl_s* f, const double* b, double* out, cudaStream_t s) {
   const DevFactor<float>& d = f->d32;
-  if (!d.w64) return fail(JD_EINVAL, "ildl_apply: no mixed-precision work vectors");
-  return launch_apply<float, double>(f, d, d.w64, d.z64, b, out, s);
+  static const bool acc64 = std::getenv("AJD_MIXED_ACC64") != nullptr;
+  if (acc64) {
+    if (!d.w64) return fail(JD_EINVAL, "ildl_apply: no mixed-precision work vectors");
+    return launch_apply<float, double, double>(f, d, d.w64, d.z64, b, out, s);
+  }
+  return launch_apply<float, float, double>(f, d, d.w, d.z, b, out, s);
 }
 
 // Timeout flag of the persistent apply (sticky until cleared): JD_EDEVICE if
@@ -1014,16 +906,16 @@ int noalloc_scratch(unsigned char** out) {
   return JD_OK;
 }
 
-template <typename V, typename X>
-int launch_apply_static(const ildl_s* f, const DevFactor<V>& d, const X* b, X* out, unsigned char* scratch,
+template <typename V, typename X, typename IO>
+int launch_apply_static(const ildl_s* f, const DevFactor<V>& d, const IO* b, IO* out, unsigned char* scratch,
                         cudaStream_t s) {
   const HostFactor& F = f->F;
   if (F.n == 0 || d.nphase == 0) return JD_OK;
   X* w = reinterpret_cast<X*>(scratch);
   X* z = reinterpret_cast<X*>(scratch + kNoAllocVecBytes);
   unsigned* bar = reinterpret_cast<unsigned*>(scratch + 2 * kNoAllocVecBytes);
-  ApplyArgs<V, X> a{d.perm, d.scale, d.Lptr, d.Lcol, d.Lval, d.Uptr, d.Ucol, d.Uval, d.dd, d.dof, d.partner,
-                    d.dense, w, z, b, out, F.n_dense, F.level_ptr[F.nlev]};
+  ApplyArgs<V, X, IO> a{d.perm, d.scale, d.Lptr, d.Lcol, d.Lval, d.Uptr, d.Ucol, d.Uval, d.dd, d.dof, d.partner,
+                        d.dense, w, z, b, out, F.n_dense, F.level_ptr[F.nlev]};
   // the array keeps the previous call's contents: the barrier words (arrivals,
   // generation, timeout flag) must start at zero; w and z are written before
   // they are read
@@ -1035,7 +927,7 @@ int launch_apply_static(const ildl_s* f, const DevFactor<V>& d, const X* b, X* o
   int* err = reinterpret_cast<int*>(bar + 64);
   unsigned long long* stamps = nullptr;
   void* args[] = {&a, &ph, &np, &cnt, &gen, &err, &stamps};
-  AJD_CUDA(cudaLaunchCooperativeKernel((void*)ildl_apply_persistent_kernel<V, X>, dim3(d.grid),
+  AJD_CUDA(cudaLaunchCooperativeKernel((void*)ildl_apply_persistent_kernel<V, X, IO>, dim3(d.grid),
                                        dim3(kPersistThreads), args, 0, s));
   count_launches(2);
   int herr = 0;
@@ -1058,17 +950,17 @@ extern "C" int ildl_apply_noalloc(ildl_t f, const void* b, void* x, int precisio
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   if (precision == JD_FP64) {
     if (!f->d64.ready) return fail(JD_EINVAL, "ildl_apply_noalloc: factor has no device copy");
-    return launch_apply_static<double, double>(f, f->d64, static_cast<const double*>(b), static_cast<double*>(x),
+    return launch_apply_static<double, double, double>(f, f->d64, static_cast<const double*>(b), static_cast<double*>(x),
                                                scratch, s);
   }
   if (precision == JD_FP32) {
     if (!f->d32.ready) return fail(JD_EINVAL, "ildl_apply_noalloc: factor has no device copy");
-    return launch_apply_static<float, float>(f, f->d32, static_cast<const float*>(b), static_cast<float*>(x),
+    return launch_apply_static<float, float, float>(f, f->d32, static_cast<const float*>(b), static_cast<float*>(x),
                                              scratch, s);
   }
   if (precision == JD_MIXED) {
     if (!f->d32.ready) return fail(JD_EINVAL, "ildl_apply_noalloc: factor has no device copy");
-    return launch_apply_static<float, double>(f, f->d32, static_cast<const double*>(b), static_cast<double*>(x),
+    return launch_apply_static<float, float, double>(f, f->d32, static_cast<const double*>(b), static_cast<double*>(x),
                                               scratch, s);
   }
   return fail(JD_EINVAL, "ildl_apply_noalloc: unknown precision %d", precision);

@@ -453,11 +453,13 @@ __global__ void sqmr_update_q_kernel(const T* __restrict__ u, T* __restrict__ q,
     q[i] = u[i] + beta * q[i];
 }
 
-// init: r = b, x = d = 0, partial ||r||^2
+// init: r = b, x = d = q = 0, partial ||r||^2.  q must hold numbers before
+// the first q = u + beta q (beta = 0): a buffer that held other data may
+// contain NaN bit patterns, and 0 * NaN is NaN.
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
-sqmr_init_kernel(const T* __restrict__ b, T* __restrict__ r, T* __restrict__ x, T* __restrict__ d, int64_t n,
-                 double* __restrict__ partial) {
+sqmr_init_kernel(const T* __restrict__ b, T* __restrict__ r, T* __restrict__ x, T* __restrict__ d,
+                 T* __restrict__ q, int64_t n, double* __restrict__ partial) {
   __shared__ double sh[kThreads / 32];
   T acc = T(0);
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -465,6 +467,7 @@ sqmr_init_kernel(const T* __restrict__ b, T* __restrict__ r, T* __restrict__ x, 
     r[i] = bi;
     x[i] = T(0);
     d[i] = T(0);
+    q[i] = T(0);
     acc += bi * bi;
   }
   const double s = block_sum((double)acc, sh);
@@ -690,10 +693,16 @@ int JdSolver::alloc() {
   ld_ = (n_ + 31) & ~(int64_t)31;
   nb_ = vec_blocks(n_);
   const size_t vb = (size_t)ld_ * sizeof(double);
+  // AJD_POISON_ALLOC set: fill every work buffer with 0xFF bytes (NaN in
+  // binary32 and binary64), so that a read before the first write shows up
+  // as a NaN in the tests instead of depending on what the memory held
+  const bool poison = std::getenv("AJD_POISON_ALLOC") != nullptr;
   auto A = [&](void** p, size_t bytes) -> int {
-    cudaError_t e = cudaMalloc(p, std::max<size_t>(bytes, 16));
+    bytes = std::max<size_t>(bytes, 16);
+    cudaError_t e = cudaMalloc(p, bytes);
     if (e != cudaSuccess)
       return fail(e == cudaErrorMemoryAllocation ? JD_ENOMEM : JD_EDEVICE, "jd_solve: cudaMalloc: %s", cudaGetErrorString(e));
+    if (poison) AJD_CUDA(cudaMemsetAsync(*p, 0xFF, bytes, s_));
     return JD_OK;
   };
   AJD_TRY(A((void**)&V_, vb * jmax_));
@@ -894,7 +903,7 @@ int JdSolver::correction(int kc, double theta_hat, double rel_tol, int* its) {
   convert_kernel<double, T><<<bl, kThreads, 0, s_>>>(r_, b, n_, -1.0); count_launches();
   Cols<T> QtC{Qt, ld_, c}, WC{W, ld_, c};
   // init: r = b, x = d = 0, tau = ||b||; u = P b; q = u; rho = r^T u
-  sqmr_init_kernel<T><<<bl, kThreads, 0, s_>>>(b, r, x, d, n_, partial_); count_launches();
+  sqmr_init_kernel<T><<<bl, kThreads, 0, s_>>>(b, r, x, d, q, n_, partial_); count_launches();
   sqmr_scalar_init_kernel<<<1, 1, 0, s_>>>(partial_, bl, scal_, rel_tol, done, brk); count_launches();
   auto precond = [&]() -> int {
     const bool timed = nevp_ < kEv;
@@ -1390,7 +1399,7 @@ extern "C" int jd_solve_batch(const anderson_t* hs, int nprob, const double* sig
   if (stats) std::memset(stats, 0, sizeof(jd_stats) * nprob);
   const int nthr = std::max(1, std::min(setup_threads > 0 ? setup_threads : 2, nprob));
   const int omp_total = std::max(1, omp_get_max_threads());
-  const int omp_each = std::max(1, omp_total / nthr);
+  const int omp_each = std::max(1, (omp_total - 1) / nthr);  // one core stays with the solving thread
   int dev = 0;
   AJD_CUDA(cudaGetDevice(&dev));
 

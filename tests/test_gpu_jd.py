@@ -36,6 +36,25 @@ def test_ildl_apply_matches_oracle(ajd, L, bc, sigma, nd):
         P.close()
 
 
+@pytest.mark.parametrize("L,bc,sigma,nd", [(12, 1, -1.0, 200), (20, 0, 0.3, 1000)])
+def test_ildl_apply_no_read_before_write(ajd, monkeypatch, L, bc, sigma, nd):
+    """Work vectors filled with NaN before the first apply (AJD_POISON_ALLOC):
+    every apply must still equal the oracle's, so no entry of w or z is read
+    before this apply wrote it (padding lanes of a row included)."""
+    monkeypatch.setenv("AJD_POISON_ALLOC", "1")
+    with ajd.Anderson(L, 12.0, 12, bc) as h:
+        P = ajd.Preconditioner.from_lattice(h, sigma, n_dense=nd)
+        assert P.info()["levels"] >= 2
+        want = matching.apply_factor(P.export(), np.random.default_rng(0).standard_normal(h.n))
+        b = np.random.default_rng(0).standard_normal(h.n)
+        scale = np.abs(want).max()
+        for dt, mixed, tol in [(torch.float64, False, 1e-12), (torch.float32, False, 2e-5), (torch.float64, True, 2e-5)]:
+            x = P.apply(torch.tensor(b, device="cuda", dtype=dt), mixed=mixed).double().cpu().numpy()
+            assert np.isfinite(x).all()
+            assert np.abs(x - want).max() <= tol * scale
+        P.close()
+
+
 @pytest.mark.parametrize("L,bc,sigma", [(8, 0, 0.0), (9, 1, 0.7)])
 def test_dense_tail_inverse_is_exact(ajd, L, bc, sigma):
     """When the whole matrix fits the dense tail, K = A - sigma I exactly: the
@@ -209,3 +228,16 @@ def test_jd_batch_empty_and_errors(ajd):
     with ajd.Anderson(4, 16.5, 1) as h:
         with pytest.raises(ajd.JDError):
             ajd.solve_batch([h, h], [0.0, 0.0], [2, 64], 1e-8)
+
+
+@pytest.mark.parametrize("prec", [0, 1, 2])
+def test_jd_no_read_before_write(ajd, prec, monkeypatch):
+    """Every work buffer of the solver and of the preconditioner apply starts
+    as NaN (AJD_POISON_ALLOC): a read before the first write would poison the
+    solve, so the pairs coming out right shows none happens."""
+    monkeypatch.setenv("AJD_POISON_ALLOC", "1")
+    tol = 1e-11 if prec == 0 else 1e-10
+    for (L, W, s, bc, sigma, k) in [(12, 12.0, 12, 1, -1.0, 3), (11, 21.0, 14, 0, 1.5, 2), (14, 16.5, 16, 0, 0.0, 4)]:
+        with ajd.Anderson(L, W, s, bc) as h:
+            ev, X, st = ajd.solve(h, sigma, k, tol, precision=prec, ildl={"n_dense": 200})
+        _check_pairs(L, W, s, bc, sigma, k, ev, X, st, tol)
