@@ -18,6 +18,7 @@
 #include <new>
 #include <cstdio>
 #include <cstdlib>
+#include <type_traits>
 
 #include "anderson_impl.cuh"
 #include "ildl_impl.cuh"
@@ -136,8 +137,18 @@ constexpr unsigned kSpinLimit = 1u << 22;  // ~0.1-0.5 s at 32-128 ns per poll
 
 // V: type of the stored factor values; X: type of the work vectors and of
 // the accumulation; IO: type of the caller's b and x (V = X = IO for the
-// binary64 and binary32 applies; V = X = float, IO = double for the mixed
-// apply, which converts at the gather and at the final scaling).
+// binary64 and binary32 applies; V = hi32_t, X = IO = double for the mixed
+// apply: half the factor bytes, binary64 arithmetic).
+// Load a stored value and widen it to the arithmetic type X.
+template <typename X, typename V>
+__device__ __forceinline__ X ldw(const V* p) {
+  return (X)__ldg(p);
+}
+template <>
+__device__ __forceinline__ double ldw<double, hi32_t>(const hi32_t* p) {
+  return __hiloint2double((int)__ldg(&p->u), 0);
+}
+
 template <typename V, typename X, typename IO = X>
 struct ApplyArgs {
   const int* perm;
@@ -206,11 +217,11 @@ __device__ __forceinline__ void finish_row(const ApplyArgs<V, X, IO>& a, int kin
       __stcg(a.w + p, rhs - acc);  // rhs = s[p] b[perm[p]], stored in w by the gather phase
     } else {
       const int pp = __ldg(a.partner + p);
-      X d = (X)__ldg(a.dd + p) * __ldcg(a.w + p);
-      if (pp >= 0) d += (X)__ldg(a.dof + p) * __ldcg(a.w + pp);
+      X d = ldw<X>(a.dd + p) * __ldcg(a.w + p);
+      if (pp >= 0) d += ldw<X>(a.dof + p) * __ldcg(a.w + pp);
       const X zp = d - acc;
       __stcg(a.z + p, zp);
-      a.out[__ldg(a.perm + p)] = (IO)((X)__ldg(a.scale + p) * zp);
+      a.out[__ldg(a.perm + p)] = (IO)(ldw<X>(a.scale + p) * zp);
     }
   }
 }
@@ -244,31 +255,38 @@ __device__ __forceinline__ void level_rows(const ApplyArgs<V, X, IO>& a, int kin
       eb = __ldg(ptr + pb + 1);
       if (kind == PH_FWD && lane == 0) rb_rhs = __ldcg(a.w + pb);
     }
-    X acca = X(0), accb = X(0);
+    // two partial sums per row halve the dependent chain of FMAs
+    X acca = X(0), accb = X(0), acca2 = X(0), accb2 = X(0);
     while (qa < ea || qb < eb) {
       // lanes past the end of a row gather nothing: the solution entry they
       // would point at may not be written yet in this sweep (0 * NaN = NaN)
       int ca[B], cb[B];
-      V va[B], vb[B];
+      X va[B], vb[B];
 #pragma unroll
       for (int i = 0; i < B; ++i) {
         const int q1 = qa + i * G, q2 = qb + i * G;
         const bool o1 = q1 < ea, o2 = q2 < eb;
         ca[i] = o1 ? __ldg(col + q1) : -1;
-        va[i] = o1 ? __ldg(val + q1) : V(0);
+        va[i] = o1 ? ldw<X>(val + q1) : X(0);
         cb[i] = o2 ? __ldg(col + q2) : -1;
-        vb[i] = o2 ? __ldg(val + q2) : V(0);
+        vb[i] = o2 ? ldw<X>(val + q2) : X(0);
       }
 #pragma unroll
-      for (int i = 0; i < B; ++i) {
-        const X xa = ca[i] >= 0 ? __ldcg(x + ca[i]) : X(0);
-        const X xb = cb[i] >= 0 ? __ldcg(x + cb[i]) : X(0);
-        acca += (X)va[i] * xa;
-        accb += (X)vb[i] * xb;
+      for (int i = 0; i < B; i += 2) {
+        const X xa0 = ca[i] >= 0 ? __ldcg(x + ca[i]) : X(0);
+        const X xb0 = cb[i] >= 0 ? __ldcg(x + cb[i]) : X(0);
+        const X xa1 = ca[i + 1] >= 0 ? __ldcg(x + ca[i + 1]) : X(0);
+        const X xb1 = cb[i + 1] >= 0 ? __ldcg(x + cb[i + 1]) : X(0);
+        acca += va[i] * xa0;
+        accb += vb[i] * xb0;
+        acca2 += va[i + 1] * xa1;
+        accb2 += vb[i + 1] * xb1;
       }
       qa += B * G;
       qb += B * G;
     }
+    acca += acca2;
+    accb += accb2;
     finish_row<V, X, IO, G>(a, kind, pa, acca, lane, ra_rhs);
     finish_row<V, X, IO, G>(a, kind, pb, accb, lane, rb_rhs);
   }
@@ -313,31 +331,34 @@ ildl_apply_persistent_kernel(ApplyArgs<V, X, IO> a, const int4* __restrict__ pha
     const int4 Pn = ph + 1 < nphase ? phases[ph + 1] : make_int4(-1, 0, 0, 0);
     if (kind == PH_GATHER) {
       for (int p = p0 + blockIdx.x * blockDim.x + threadIdx.x; p < p1; p += gridDim.x * blockDim.x)
-        __stcg(a.w + p, (X)__ldg(a.scale + p) * (X)__ldg(a.b + __ldg(a.perm + p)));
+        __stcg(a.w + p, ldw<X>(a.scale + p) * (X)__ldg(a.b + __ldg(a.perm + p)));
     } else if (kind == PH_DENSE) {
       const int lane = threadIdx.x & 31;
       const int warps = (gridDim.x * blockDim.x) >> 5;
       for (int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < a.nd; r += warps) {
         const V* row = a.dense + (int64_t)r * a.nd;
-        X acc = X(0);
+        X acc = X(0), acc2 = X(0);
         for (int c0 = lane; c0 < a.nd; c0 += 8 * 32) {
-          V rv[8];
-          X wv[8];
+          X rv[8], wv[8];
 #pragma unroll
           for (int i = 0; i < 8; ++i) {
             const int c = c0 + 32 * i;
             const bool ok = c < a.nd;
-            rv[i] = ok ? __ldg(row + c) : V(0);
+            rv[i] = ok ? ldw<X>(row + c) : X(0);
             wv[i] = ok ? __ldcg(a.w + a.d0 + c) : X(0);
           }
 #pragma unroll
-          for (int i = 0; i < 8; ++i) acc += (X)rv[i] * wv[i];
+          for (int i = 0; i < 8; i += 2) {
+            acc += rv[i] * wv[i];
+            acc2 += rv[i + 1] * wv[i + 1];
+          }
         }
+        acc += acc2;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
         if (lane == 0) {
           __stcg(a.z + a.d0 + r, acc);
-          a.out[__ldg(a.perm + a.d0 + r)] = (IO)((X)__ldg(a.scale + a.d0 + r) * acc);
+          a.out[__ldg(a.perm + a.d0 + r)] = (IO)(ldw<X>(a.scale + a.d0 + r) * acc);
         }
       }
     } else {
@@ -409,18 +430,22 @@ int upload_factor(const HostFactor& F, DevFactor<T>& d, cudaStream_t st) {
   AJD_TRY(upload(&d.dof, F.dinv_o, st));
   AJD_TRY(upload(&d.partner, F.partner, st));
   AJD_TRY(upload(&d.dense, F.dense_inv, st));
-  AJD_CUDA(cudaMalloc(&d.w, std::max<size_t>(1, F.n) * sizeof(T)));
-  AJD_CUDA(cudaMalloc(&d.z, std::max<size_t>(1, F.n) * sizeof(T)));
-  if (sizeof(T) == 4) {  // binary64 work vectors of the mixed apply
-    AJD_CUDA(cudaMalloc(&d.w64, std::max<size_t>(1, F.n) * sizeof(double)));
-    AJD_CUDA(cudaMalloc(&d.z64, std::max<size_t>(1, F.n) * sizeof(double)));
-  }
-  if (std::getenv("AJD_POISON_ALLOC")) {  // NaN-filled work vectors (read-before-write check in tests)
-    const size_t nb = std::max<size_t>(1, F.n);
-    AJD_CUDA(cudaMemsetAsync(d.w, 0xFF, nb * sizeof(T), st));
-    AJD_CUDA(cudaMemsetAsync(d.z, 0xFF, nb * sizeof(T), st));
-    if (d.w64) AJD_CUDA(cudaMemsetAsync(d.w64, 0xFF, nb * sizeof(double), st));
-    if (d.z64) AJD_CUDA(cudaMemsetAsync(d.z64, 0xFF, nb * sizeof(double), st));
+  const size_t nb = std::max<size_t>(1, F.n);
+  const bool poison = std::getenv("AJD_POISON_ALLOC") != nullptr;  // NaN-filled work vectors (tests)
+  if constexpr (std::is_same<T, hi32_t>::value) {  // binary64 work vectors of the mixed apply
+    AJD_CUDA(cudaMalloc(&d.w64, nb * sizeof(double)));
+    AJD_CUDA(cudaMalloc(&d.z64, nb * sizeof(double)));
+    if (poison) {
+      AJD_CUDA(cudaMemsetAsync(d.w64, 0xFF, nb * sizeof(double), st));
+      AJD_CUDA(cudaMemsetAsync(d.z64, 0xFF, nb * sizeof(double), st));
+    }
+  } else {
+    AJD_CUDA(cudaMalloc(&d.w, nb * sizeof(T)));
+    AJD_CUDA(cudaMalloc(&d.z, nb * sizeof(T)));
+    if (poison) {
+      AJD_CUDA(cudaMemsetAsync(d.w, 0xFF, nb * sizeof(T), st));
+      AJD_CUDA(cudaMemsetAsync(d.z, 0xFF, nb * sizeof(T), st));
+    }
   }
   // phase list of the persistent apply
   std::vector<int4> ph;
@@ -455,7 +480,8 @@ int upload_factor(const HostFactor& F, DevFactor<T>& d, cudaStream_t st) {
   AJD_CUDA(cudaMemsetAsync(d.bar, 0, 96 * sizeof(unsigned), st));
   AJD_CUDA(cudaStreamSynchronize(st));
   int per_sm = 0;
-  AJD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ildl_apply_persistent_kernel<T, T, double>, kPersistThreads, 0));
+  using XT = typename std::conditional<std::is_same<T, hi32_t>::value, double, T>::type;
+  AJD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ildl_apply_persistent_kernel<T, XT, XT>, kPersistThreads, 0));
   if (per_sm < 1) return fail(JD_EDEVICE, "ildl: persistent apply kernel cannot be resident");
   d.grid = sm_count();  // one CTA per SM
   d.ready = true;
@@ -517,20 +543,16 @@ int ildl_apply_dev(const ildl_s* f, const T* b, T* out, cudaStream_t s) {
 }
 
 int ildl_apply_dev_mixed(const ildl_s* f, const double* b, double* out, cudaStream_t s) {
-  const DevFactor<float>& d = f->d32;
-  static const bool acc64 = std::getenv("AJD_MIXED_ACC64") != nullptr;
-  if (acc64) {
-    if (!d.w64) return fail(JD_EINVAL, "ildl_apply: no mixed-precision work vectors");
-    return launch_apply<float, double, double>(f, d, d.w64, d.z64, b, out, s);
-  }
-  return launch_apply<float, float, double>(f, d, d.w, d.z, b, out, s);
+  const DevFactor<hi32_t>& d = f->dh;
+  if (!d.w64) return fail(JD_EINVAL, "ildl_apply: no mixed-precision work vectors");
+  return launch_apply<hi32_t, double, double>(f, d, d.w64, d.z64, b, out, s);
 }
 
 // Timeout flag of the persistent apply (sticky until cleared): JD_EDEVICE if
 // a grid barrier gave up.
 int ildl_check_device_error(const ildl_s* f) {
-  for (int prec = 0; prec < 2; ++prec) {
-    const unsigned* bar = prec == 0 ? f->d64.bar : f->d32.bar;
+  for (int prec = 0; prec < 3; ++prec) {
+    const unsigned* bar = prec == 0 ? f->d64.bar : prec == 1 ? f->d32.bar : f->dh.bar;
     if (!bar) continue;
     int e = 0;
     AJD_CUDA(cudaMemcpy(&e, bar + 64, sizeof(int), cudaMemcpyDeviceToHost));
@@ -594,12 +616,14 @@ int ildl_upload_all(ildl_s* f, cudaStream_t st) {
   }
   AJD_TRY(upload_factor<double>(f->F, f->d64, st));
   AJD_TRY(upload_factor<float>(f->F, f->d32, st));
+  AJD_TRY(upload_factor<hi32_t>(f->F, f->dh, st));
   return JD_OK;
 }
 
 void ildl_free_device(ildl_s* f) {
   free_dev(f->d64);
   free_dev(f->d32);
+  free_dev(f->dh);
 }
 
 // CSR of A - sigma I for a lattice (host, from the binary64 potential).
@@ -851,7 +875,7 @@ extern "C" int ildl_destroy(ildl_t f) {
   if (!f) return JD_OK;
   int dev = 0;
   cudaGetDevice(&dev);
-  if (f->d64.ready || f->d32.ready) {
+  if (f->d64.ready || f->d32.ready || f->dh.ready) {
     cudaSetDevice(f->device);
     ildl_free_device(f);
     cudaSetDevice(dev);
@@ -959,8 +983,8 @@ extern "C" int ildl_apply_noalloc(ildl_t f, const void* b, void* x, int precisio
                                              scratch, s);
   }
   if (precision == JD_MIXED) {
-    if (!f->d32.ready) return fail(JD_EINVAL, "ildl_apply_noalloc: factor has no device copy");
-    return launch_apply_static<float, float, double>(f, f->d32, static_cast<const double*>(b), static_cast<double*>(x),
+    if (!f->dh.ready) return fail(JD_EINVAL, "ildl_apply_noalloc: factor has no device copy");
+    return launch_apply_static<hi32_t, double, double>(f, f->dh, static_cast<const double*>(b), static_cast<double*>(x),
                                               scratch, s);
   }
   return fail(JD_EINVAL, "ildl_apply_noalloc: unknown precision %d", precision);

@@ -1,9 +1,27 @@
 // Internal state of a preconditioner handle.
 #pragma once
+#include <cstring>
+
 #include "common.cuh"
 #include "ildl_setup.h"
 
 namespace ajd {
+
+// A binary64 value stored as its upper 32 bits (sign, 11-bit exponent, 20
+// mantissa bits), rounded to nearest-even from the full value: half the
+// bytes of a binary64 entry, the full binary64 range, 21 significant bits,
+// and widening back to binary64 is a register move (no conversion
+// instruction).  Used for the factor values of the mixed apply.
+struct hi32_t {
+  unsigned u = 0;
+  hi32_t() = default;
+  explicit hi32_t(double x) {
+    uint64_t b;
+    std::memcpy(&b, &x, sizeof(b));
+    b += 0x7FFFFFFFull + ((b >> 32) & 1ull);  // round the dropped low word, ties to even
+    u = (unsigned)(b >> 32);
+  }
+};
 
 // Device copy of a HostFactor in one precision.
 template <typename T>
@@ -27,7 +45,7 @@ struct DevFactor {
   int nphase = 0;
   unsigned* bar = nullptr;  // [0] arrivals, [32] generation, [64] timeout flag
   int grid = 0;
-  double* w64 = nullptr;  // binary64 work vectors of the mixed apply (float factor)
+  double* w64 = nullptr;  // binary64 work vectors of the mixed apply (hi32_t factor)
   double* z64 = nullptr;
 };
 
@@ -38,6 +56,7 @@ struct ildl_s {
   int device = 0;
   ajd::DevFactor<double> d64;
   ajd::DevFactor<float> d32;
+  ajd::DevFactor<ajd::hi32_t> dh;  // mixed apply: binary64 sums over hi32_t values
   template <typename T>
   const ajd::DevFactor<T>& dev() const {
     if constexpr (sizeof(T) == 8) return d64;
@@ -51,7 +70,8 @@ namespace ajd {
 template <typename T>
 int ildl_apply_dev(const ildl_s* f, const T* b, T* out, cudaStream_t stream);
 
-// x = K^{-1} b with the binary32 factor, binary64 vectors and sums.
+// x = K^{-1} b with the factor values stored as hi32_t, binary64 vectors
+// and sums.
 int ildl_apply_dev_mixed(const ildl_s* f, const double* b, double* out, cudaStream_t stream);
 
 // ildl_create with its device work on stream `st`.
