@@ -53,7 +53,13 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain binary64 comparison")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
-    ap.add_argument("--setup-threads", type=int, default=2,
+    ap.add_argument("--serve-requests", type=int, default=32,
+                    help="requests of the serving sample (0 skips it)")
+    ap.add_argument("--serve-rate", type=float, default=1.5, help="Poisson arrival rate of the serving sample, 1/s")
+    ap.add_argument("--serve-lmax", type=int, default=48, help="largest lattice of the serving sample")
+    ap.add_argument("--serve-slots", type=int, default=4)
+    ap.add_argument("--serve-setup-threads", type=int, default=3)
+    ap.add_argument("--setup-threads", type=int, default=4,
                     help="concurrent preconditioner builds in the pipelined batch")
     return ap.parse_args()
 
@@ -145,6 +151,51 @@ def apply_bytes(info, elem):
             + n * (4 * elem)                          # w write/read, z write/read
             + (n - nd) * (2 * elem + idx)             # D^{-1} diagonal, off-diagonal, partner
             + nd * nd * elem)
+
+
+def serving_sample(ajd, args, precision):
+    """Requests arriving as a Poisson stream (driver seed 7): L uniform in
+    {16..serve_lmax}, W uniform in [8, 24], sigma uniform in [-2, 2], k in
+    {1, 5, 10}, request r on disorder seed 10^6 + r, periodic, tol as the
+    headline.  Each is submitted to a jd_server at its arrival time and
+    polled until done; reports eigenpairs/s over the whole sample and the
+    latency percentiles (submission to completion)."""
+    import numpy as np
+    g = np.random.default_rng(7)
+    reqs, t = [], 0.0
+    for r in range(args.serve_requests):
+        t += g.exponential(1.0 / args.serve_rate)
+        reqs.append((t, int(g.integers(16, args.serve_lmax + 1)), float(g.uniform(8.0, 24.0)), 10 ** 6 + r,
+                     float(g.uniform(-2.0, 2.0)), int(g.choice([1, 5, 10]))))
+    lat, pairs, failed = [], 0, 0
+    with ajd.Server(slots=args.serve_slots, setup_threads=args.serve_setup_threads, precision=precision) as srv:
+        start = time.perf_counter()
+        pending, i = {}, 0
+        while i < len(reqs) or pending:
+            now = time.perf_counter() - start
+            while i < len(reqs) and reqs[i][0] <= now:
+                _, L, W, seed, sigma, k = reqs[i]
+                pending[srv.submit(L, W, seed, sigma, k, args.tol)] = k
+                i += 1
+            for tk in list(pending):
+                out = srv.poll(tk, raise_on_error=False)
+                if out is not None:
+                    st = out[2]
+                    lat.append(st["latency_ms"])
+                    pairs += st["nconv"]
+                    failed += st["status"] not in (0, ajd.JD_ENOCONV)
+                    del pending[tk]
+            time.sleep(0.002)
+        elapsed = time.perf_counter() - start
+        info = srv.info()
+    lat = np.sort(np.array(lat))
+    return {"value": pairs / elapsed, "unit": UNIT, "requests": len(reqs), "failed": failed,
+            "p50_latency_ms": float(np.percentile(lat, 50)), "p99_latency_ms": float(np.percentile(lat, 99)),
+            "max_latency_ms": float(lat[-1]), "seconds": elapsed, "peak_concurrent_solves": info["peak_solving"],
+            "slots": args.serve_slots, "setup_threads": args.serve_setup_threads,
+            "sample": "%d Poisson arrivals at %.2f/s, L~U{16..%d}, W~U[8,24], sigma~U[-2,2], k in {1,5,10}, seeds "
+                      "1e6+r, tol %g (a bounded sample of the 4096-request L<=120 stream)"
+                      % (len(reqs), args.serve_rate, args.serve_lmax, args.tol)}
 
 
 def cpu_baseline(W, sigma, k, L_sample=30):
@@ -345,6 +396,10 @@ def main():
     stencil_calls = sum(s["stencil_calls"] for s in stats)
     stencil_ms = sum(s["stencil_ms"] for s in stats)
 
+    serving = None
+    if args.serve_requests > 0:
+        serving = serving_sample(ajd, args, head)
+
     cpu = None
     if rank == 0 and not args.no_cpu:
         cpu = cpu_baseline(W, sigma, k)
@@ -376,7 +431,7 @@ def main():
                 "max_residual": max(s["max_residual"] for s in stats),
                 "preconditioner": {"levels": info["levels"], "n_dense": info["n_dense"], "nnz_L": info["nnz_L"],
                                    "fill": info["fill"], "n_2x2": info["n_2x2"]},
-                "fp64": fp64, "e2e": e2e, "roofline": roofline,
+                "fp64": fp64, "e2e": e2e, "roofline": roofline, "serving": serving,
                 "stencil_fp32": {"calls": stencil_calls, "avg_ms": stencil_ms / stencil_calls if stencil_calls else None,
                                  "achieved_GBps": 12 * n / (stencil_ms / stencil_calls / 1e3) / 1e9 if stencil_calls else None},
                 "cpu_baseline": cpu, "clocks": clocks,

@@ -47,6 +47,7 @@ extern "C" {
 #define JD_EBREAKDOWN (-4)  /* persistent Krylov breakdown                    */
 #define JD_EDEVICE (-5)     /* CUDA error or a device-side wait that timed out*/
 #define JD_ESETUP (-6)      /* preconditioner construction failed             */
+#define JD_EAGAIN (-7)      /* jd_poll: the request is queued or running      */
 
 /* ---- boundary conditions and precisions -------------------------------- */
 #define JD_PERIODIC 0 /* x_{M+1} = x_1 (the default of every table)           */
@@ -383,6 +384,79 @@ int jd_solve(anderson_t h, double sigma, int k, double tol, const jd_params* p, 
 int jd_solve_batch(const anderson_t* hs, int nprob, const double* sigma, const int* k, double tol,
                    const jd_params* p, double* const* evals, double* const* evecs, jd_stats* stats,
                    int setup_threads, void* stream);
+
+/* ------------------------------------------------------------------ serving
+ * A request loop for many independent eigensolves of different sizes (the
+ * paper's physics needs many lattices, disorder strengths and energies,
+ * Sections 3 and 8; it has no serving layer of its own).  Requests are
+ * admitted in arrival order while the device memory they are estimated to
+ * need fits the budget; `setup_threads` host threads build their potentials
+ * and preconditioners, and `slots` host threads solve admitted problems
+ * concurrently, each on its own CUDA stream, so that the device work of
+ * several requests overlaps (continuous batching: a request starts as soon
+ * as a build finishes and a slot is free, not when a batch fills).  The
+ * grid-wide preconditioner applies of concurrent solves are ordered on the
+ * device one after another; all other kernels overlap.  Each request is the
+ * computation jd_solve does for (anderson_create(L, W, seed, bc), sigma, k,
+ * tol) with the server's jd_params, so its result does not depend on what
+ * else is running.
+ */
+typedef struct jd_server_s* jd_server_t;
+
+typedef struct {
+  size_t hbm_budget;  /* bytes of device memory the requests may hold at once
+                         (estimated per request, see jd_server_estimate);
+                         0 = 80% of the free device memory at creation */
+  int slots;          /* concurrent solves, 1..64 (0 = 4) */
+  int setup_threads;  /* concurrent preconditioner builds, 1..64 (0 = 2) */
+  jd_params solve;    /* parameters of every solve; solve.precond must be NULL */
+} jd_server_params;
+
+#define JD_SUBMIT_VECTORS 1 /* keep the eigenvectors for jd_poll */
+
+typedef struct {
+  int64_t submitted, completed, failed; /* requests */
+  int queued, building, ready, solving; /* requests in each state now */
+  int peak_solving;                     /* most solves that ran at once */
+  size_t hbm_budget, reserved_bytes, peak_reserved_bytes;
+} jd_server_info;
+
+/* Defaults as documented above (solve = jd_params_default). */
+int jd_server_params_default(jd_server_params* p);
+
+/* Device-memory estimate that admission charges a request of an L^3 lattice
+ * with k eigenpairs: potential, the three device copies of a factor of
+ * typical fill (and its dense tail), and the solver's search space.  */
+int jd_server_estimate(int L, int k, size_t* bytes);
+
+/* Start the worker threads on the current device.  Errors: JD_EINVAL (bad
+ * parameters), JD_EDEVICE. */
+int jd_server_create(const jd_server_params* p, jd_server_t* out);
+
+/* Queue a request; *ticket identifies it in jd_poll/jd_wait.  Arguments are
+ * checked as by anderson_create and jd_solve (JD_EINVAL); a request whose
+ * estimate exceeds the whole budget is rejected with JD_ENOMEM. */
+int jd_submit(jd_server_t srv, int L, double W, uint64_t seed, int bc, double sigma, int k, double tol, int flags,
+              uint64_t* ticket);
+
+/* JD_EAGAIN while the request is queued, building or solving.  Otherwise
+ * the request's own status (JD_OK, JD_ENOCONV with the converged prefix,
+ * or an error) is returned, evals[k] (caller buffer, may be NULL), evecs
+ * (n x k column-major, caller buffer, only with JD_SUBMIT_VECTORS, may be
+ * NULL), *st and *latency_ms (submission to completion, may be NULL) are
+ * filled, and the ticket is retired.  Unknown ticket: JD_EINVAL. */
+int jd_poll(jd_server_t srv, uint64_t ticket, double* evals, double* evecs, jd_stats* st, double* latency_ms);
+
+/* jd_poll that blocks until the request completes or timeout_s seconds
+ * pass (JD_EAGAIN then); timeout_s < 0 waits without limit. */
+int jd_wait(jd_server_t srv, uint64_t ticket, double* evals, double* evecs, jd_stats* st, double* latency_ms,
+            double timeout_s);
+
+int jd_server_info_get(jd_server_t srv, jd_server_info* info);
+
+/* Stop: queued requests are dropped, solves in flight finish, every handle
+ * and buffer of the server is released.  NULL is a no-op. */
+int jd_server_destroy(jd_server_t srv);
 
 #ifdef __cplusplus
 }

@@ -11,10 +11,11 @@ import ctypes
 import numpy as np
 
 from . import _ffi
-from ._ffi import (JD_EBREAKDOWN, JD_EDEVICE, JD_EINVAL, JD_ENOCONV, JD_ENOMEM, JD_ESETUP, JD_FP32,
-                   JD_FP64, JD_HARDWALL, JD_MIXED, JD_OK, JD_PERIODIC, JDError)
+from ._ffi import (JD_EAGAIN, JD_EBREAKDOWN, JD_EDEVICE, JD_EINVAL, JD_ENOCONV, JD_ENOMEM, JD_ESETUP, JD_FP32,
+                   JD_FP64, JD_HARDWALL, JD_MIXED, JD_OK, JD_PERIODIC, JD_SUBMIT_VECTORS, JDError)
 
-__all__ = ["Anderson", "Preconditioner", "ildl_params", "jd_params", "solve", "JDError", "JD_PERIODIC", "JD_HARDWALL", "JD_FP64", "JD_FP32", "JD_MIXED", "library_path"]
+__all__ = ["Anderson", "Preconditioner", "Server", "ildl_params", "jd_params", "solve", "solve_batch", "JDError",
+           "JD_PERIODIC", "JD_HARDWALL", "JD_FP64", "JD_FP32", "JD_MIXED", "library_path"]
 
 
 def library_path():
@@ -316,3 +317,85 @@ def solve_batch(lattices, sigmas, ks, tol, precision=JD_FP64, vectors=True, setu
         stats["status"] = JD_OK if stats["nconv"] >= kk[i] else JD_ENOCONV
         out.append((evs[i], (Xs[i].T if vectors else None), stats))
     return out
+
+
+class Server:
+    """The request loop of ``jd_server_*``: submit eigensolves of any size,
+    poll or wait for each result.  ``slots`` solves run concurrently on
+    their own CUDA streams, ``setup_threads`` host threads build the
+    preconditioners, and requests are admitted while their estimated device
+    memory fits ``hbm_budget`` bytes (0: 80% of the free memory).  Keyword
+    arguments other than these go to :func:`jd_params` (for every solve)."""
+
+    def __init__(self, hbm_budget=0, slots=4, setup_threads=2, precision=JD_FP64, **params):
+        p = _ffi.JdServerParams()
+        _ffi.call("jd_server_params_default", ctypes.byref(p))
+        p.hbm_budget = int(hbm_budget)
+        p.slots = int(slots)
+        p.setup_threads = int(setup_threads)
+        p.solve = jd_params(precision=precision, **params)
+        h = ctypes.c_void_p()
+        _ffi.call("jd_server_create", ctypes.byref(p), ctypes.byref(h))
+        self._h = h
+        self._meta = {}
+
+    @staticmethod
+    def estimate(L, k):
+        b = ctypes.c_size_t()
+        _ffi.call("jd_server_estimate", int(L), int(k), ctypes.byref(b))
+        return b.value
+
+    def submit(self, L, W, seed, sigma, k, tol, bc=JD_PERIODIC, vectors=False):
+        t = ctypes.c_uint64()
+        _ffi.call("jd_submit", self._h, int(L), float(W), int(seed), int(bc), float(sigma), int(k), float(tol),
+                  JD_SUBMIT_VECTORS if vectors else 0, ctypes.byref(t))
+        self._meta[t.value] = (int(L) ** 3, int(k), bool(vectors))
+        return t.value
+
+    def _result(self, fn, ticket, *extra, raise_on_error=True):
+        n, k, vec = self._meta[ticket]
+        ev = np.zeros(k)
+        X = np.zeros((k, n)) if vec else None
+        st = _ffi.JdStats()
+        lat = ctypes.c_double()
+        vp = ctypes.c_void_p
+        rc = getattr(_ffi.lib(), fn)(self._h, ticket, ev.ctypes.data_as(vp), X.ctypes.data_as(vp) if vec else None,
+                                     ctypes.byref(st), ctypes.byref(lat), *extra)
+        if rc == JD_EAGAIN:
+            return None
+        del self._meta[ticket]
+        if rc != JD_OK and (rc != JD_ENOCONV or raise_on_error):
+            _ffi.check(rc, fn)
+        stats = _stats_dict(st)
+        stats["status"] = rc
+        stats["latency_ms"] = lat.value
+        return ev, (X.T if vec else None), stats
+
+    def poll(self, ticket, raise_on_error=True):
+        """(evals, evecs or None, stats) once done, else None."""
+        return self._result("jd_poll", ticket, raise_on_error=raise_on_error)
+
+    def wait(self, ticket, timeout=-1.0, raise_on_error=True):
+        return self._result("jd_wait", ticket, ctypes.c_double(timeout), raise_on_error=raise_on_error)
+
+    def info(self):
+        i = _ffi.JdServerInfo()
+        _ffi.call("jd_server_info_get", self._h, ctypes.byref(i))
+        return {f: getattr(i, f) for f, _ in i._fields_}
+
+    def close(self):
+        if self._h is not None:
+            _ffi.lib().jd_server_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

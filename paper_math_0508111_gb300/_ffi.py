@@ -14,11 +14,14 @@ c_int, c_double, c_void_p, c_int64, c_uint64 = (ctypes.c_int, ctypes.c_double, c
 P = ctypes.POINTER
 
 JD_OK, JD_EINVAL, JD_ENOMEM, JD_ENOCONV, JD_EBREAKDOWN, JD_EDEVICE, JD_ESETUP = 0, -1, -2, -3, -4, -5, -6
+JD_EAGAIN = -7
+JD_SUBMIT_VECTORS = 1
 JD_PERIODIC, JD_HARDWALL = 0, 1
 JD_FP64, JD_FP32, JD_MIXED = 0, 1, 2
 
 ERROR_NAMES = {JD_EINVAL: "JD_EINVAL", JD_ENOMEM: "JD_ENOMEM", JD_ENOCONV: "JD_ENOCONV",
-               JD_EBREAKDOWN: "JD_EBREAKDOWN", JD_EDEVICE: "JD_EDEVICE", JD_ESETUP: "JD_ESETUP"}
+               JD_EBREAKDOWN: "JD_EBREAKDOWN", JD_EDEVICE: "JD_EDEVICE", JD_ESETUP: "JD_ESETUP",
+               JD_EAGAIN: "JD_EAGAIN"}
 
 
 class JDError(RuntimeError):
@@ -52,6 +55,17 @@ class JdStats(ctypes.Structure):
                 ("precond_calls", c_int), ("precond_ms", c_double), ("stencil_calls", c_int), ("stencil_ms", c_double)]
 
 
+class JdServerParams(ctypes.Structure):
+    _fields_ = [("hbm_budget", ctypes.c_size_t), ("slots", c_int), ("setup_threads", c_int), ("solve", JdParams)]
+
+
+class JdServerInfo(ctypes.Structure):
+    _fields_ = [("submitted", c_int64), ("completed", c_int64), ("failed", c_int64), ("queued", c_int),
+                ("building", c_int), ("ready", c_int), ("solving", c_int), ("peak_solving", c_int),
+                ("hbm_budget", ctypes.c_size_t), ("reserved_bytes", ctypes.c_size_t),
+                ("peak_reserved_bytes", ctypes.c_size_t)]
+
+
 # (name, restype, argtypes) of every exported function
 SIGNATURES = [
     ("jd_last_error", ctypes.c_char_p, []),
@@ -75,6 +89,15 @@ SIGNATURES = [
     ("jd_params_default", c_int, [P(JdParams)]),
     ("jd_solve", c_int, [c_void_p, c_double, c_int, c_double, P(JdParams), c_void_p, c_void_p, P(JdStats),
                          c_void_p]),
+    ("jd_server_params_default", c_int, [P(JdServerParams)]),
+    ("jd_server_estimate", c_int, [c_int, c_int, P(ctypes.c_size_t)]),
+    ("jd_server_create", c_int, [P(JdServerParams), P(c_void_p)]),
+    ("jd_submit", c_int, [c_void_p, c_int, c_double, c_uint64, c_int, c_double, c_int, c_double, c_int,
+                          P(c_uint64)]),
+    ("jd_poll", c_int, [c_void_p, c_uint64, c_void_p, c_void_p, P(JdStats), P(c_double)]),
+    ("jd_wait", c_int, [c_void_p, c_uint64, c_void_p, c_void_p, P(JdStats), P(c_double), c_double]),
+    ("jd_server_info_get", c_int, [c_void_p, P(JdServerInfo)]),
+    ("jd_server_destroy", c_int, [c_void_p]),
     ("jd_solve_batch", c_int, [c_void_p, c_int, c_void_p, c_void_p, c_double, P(JdParams), c_void_p, c_void_p,
                                c_void_p, c_int, c_void_p]),
 ]

@@ -22,6 +22,7 @@
 
 #include "anderson_impl.cuh"
 #include "ildl_impl.cuh"
+#include "jd_impl.cuh"
 #include "ildl_setup.h"
 
 namespace ajd {
@@ -488,7 +489,13 @@ int upload_factor(const HostFactor& F, DevFactor<T>& d, cudaStream_t st) {
   return JD_OK;
 }
 
+thread_local bool tl_serialize_applies = false;
+std::mutex g_chain_mu;
+cudaEvent_t g_chain_last = nullptr;  // completion of the last serialised apply
+
 }  // namespace
+
+void set_apply_serialization(bool on) { tl_serialize_applies = on; }
 
 // One persistent apply with factor values V, work vectors X, caller vectors IO.
 template <typename V, typename X, typename IO>
@@ -510,8 +517,23 @@ int launch_apply(const ildl_s* f, const DevFactor<V>& d, X* w, X* z, const IO* b
   unsigned long long* stamps = nullptr;
   if (timing) AJD_CUDA(cudaMalloc(&stamps, (np + 1) * sizeof(unsigned long long)));
   void* args[] = {&a, &ph, &np, &cnt, &gen, &err, &stamps};
-  AJD_CUDA(cudaLaunchCooperativeKernel((void*)ildl_apply_persistent_kernel<V, X, IO>, dim3(d.grid),
-                                       dim3(kPersistThreads), args, 0, s));
+  if (tl_serialize_applies) {
+    // concurrent solvers: this apply starts on the device only after the
+    // previous serialised apply (of any thread) has finished, so no two of
+    // these grid-wide cooperative kernels ever run at the same time
+    std::lock_guard<std::mutex> lk(g_chain_mu);
+    if (g_chain_last) AJD_CUDA(cudaStreamWaitEvent(s, g_chain_last, 0));
+    AJD_CUDA(cudaLaunchCooperativeKernel((void*)ildl_apply_persistent_kernel<V, X, IO>, dim3(d.grid),
+                                         dim3(kPersistThreads), args, 0, s));
+    cudaEvent_t ev = nullptr;
+    AJD_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    AJD_CUDA(cudaEventRecord(ev, s));
+    if (g_chain_last) cudaEventDestroy(g_chain_last);  // released once it has completed
+    g_chain_last = ev;
+  } else {
+    AJD_CUDA(cudaLaunchCooperativeKernel((void*)ildl_apply_persistent_kernel<V, X, IO>, dim3(d.grid),
+                                         dim3(kPersistThreads), args, 0, s));
+  }
   count_launches(2);
   if (timing) {
     std::vector<unsigned long long> t(np + 1);

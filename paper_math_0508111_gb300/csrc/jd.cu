@@ -796,12 +796,10 @@ int JdSolver::cgs2(int kc, int m, double* t, double* nrm_host) {
 int JdSolver::rr(int m) {
   const int mp = (m + 1) & ~1;
   const size_t sm = sizeof(double) * (2 * mp * mp + mp) + sizeof(int) * mp;
-  static bool attr = false;
-  if (!attr) {
-    AJD_CUDA(cudaFuncSetAttribute(rr_eig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)(sizeof(double) * (2 * kMaxM * kMaxM + kMaxM) + sizeof(int) * kMaxM)));
-    attr = true;
-  }
+  static const cudaError_t attr = cudaFuncSetAttribute(  // once per process (thread-safe static init)
+      rr_eig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      (int)(sizeof(double) * (2 * kMaxM * kMaxM + kMaxM) + sizeof(int) * kMaxM));
+  AJD_CUDA(attr);
   rr_eig_kernel<<<1, kThreads, sm, s_>>>(H_, kMaxM, m, sigma_, theta_, Y_, kMaxM); count_launches();
   AJD_CHECK_LAUNCH();
   return JD_OK;
@@ -1307,6 +1305,14 @@ int JdSolver::finalize(int kc, double* lam, double* evals, double* evecs, jd_sta
   return JD_OK;
 }
 
+int normalize_jd_params(const jd_params* p, jd_params& prm);
+
+int solve_problem(anderson_s* h, ildl_s* pc, const jd_params& prm, double sigma, int k, double tol, double* evals,
+                  double* evecs, jd_stats* st, cudaStream_t s) {
+  JdSolver solver(h, pc, prm, sigma, k, tol, s);
+  return solver.run(evals, evecs, st);
+}
+
 }  // namespace ajd
 
 using namespace ajd;
@@ -1327,6 +1333,7 @@ extern "C" int jd_params_default(jd_params* p) {
 }
 
 static int normalize_params(const jd_params* p, jd_params& prm);
+int ajd::normalize_jd_params(const jd_params* p, jd_params& prm) { return normalize_params(p, prm); }
 
 extern "C" int jd_solve(anderson_t h, double sigma, int k, double tol, const jd_params* p, double* evals,
                         double* evecs, jd_stats* st, void* stream) {

@@ -71,3 +71,25 @@ def test_batch_argument_validation_without_gpu(built_lib):
     ev = (ctypes.c_void_p * 1)(None)
     assert L.jd_solve_batch(hs, 1, sig, kk, 1e-8, None, ev, None, None, 0, None) == _ffi.JD_EINVAL
     assert b"problem 0" in L.jd_last_error()
+
+
+def test_server_argument_validation_without_gpu(built_lib):
+    """The request loop rejects bad arguments before touching a device."""
+    from paper_math_0508111_gb300 import _ffi
+    L = _ffi.lib()
+    p = _ffi.JdServerParams()
+    assert L.jd_server_params_default(ctypes.byref(p)) == _ffi.JD_OK
+    assert p.slots == 4 and p.setup_threads == 2 and p.hbm_budget == 0
+    h = ctypes.c_void_p()
+    p.slots = 100
+    assert L.jd_server_create(ctypes.byref(p), ctypes.byref(h)) == _ffi.JD_EINVAL
+    t = ctypes.c_uint64()
+    assert L.jd_submit(None, 10, 16.5, 1, 0, 0.0, 5, 1e-8, 0, ctypes.byref(t)) == _ffi.JD_EINVAL
+    assert L.jd_poll(None, 1, None, None, None, None) == _ffi.JD_EINVAL
+    assert L.jd_server_destroy(None) == _ffi.JD_OK
+    # the admission estimate grows with the lattice and covers the factor
+    b = [ctypes.c_size_t() for _ in range(3)]
+    for x, Lx in zip(b, [10, 50, 100]):
+        assert L.jd_server_estimate(Lx, 5, ctypes.byref(x)) == _ffi.JD_OK
+    assert b[0].value < b[1].value < b[2].value
+    assert b[2].value > 56 * 56 * 10 ** 6  # three copies of ~57 entries per row at L = 100
