@@ -135,22 +135,46 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def apply_bytes(info, elem):
-    """Algorithmic bytes of one preconditioner application x = K^{-1} b:
-    every stored entry of L read once in the forward and once in the backward
-    sweep (value + int32 column), both row-pointer arrays, and per position
-    the gather/scatter vectors (perm, scale twice, b, out), the work vectors
-    w and z (written once, read once), the 2x2 pivot data (diagonal,
-    off-diagonal, partner) and the dense trailing inverse.  Gathers of
-    earlier solution entries through the column indices are cache traffic
-    and not counted."""
+def apply_bytes(info, val, vec):
+    """Algorithmic bytes of one preconditioner application x = K^{-1} b with
+    `val`-byte factor values and `vec`-byte vectors: every stored entry of L
+    read once in the forward and once in the backward sweep (value + int32
+    column), both row-pointer arrays, and per position the gather/scatter
+    data (perm twice, scale twice, b, out), the work vectors w and z
+    (written once, read once), the 2x2 pivot data (diagonal, off-diagonal,
+    partner) and the dense trailing inverse.  Gathers of earlier solution
+    entries through the column indices are cache traffic and not counted."""
     n, nnz, nd = info["n"], info["nnz_L"], info["n_dense"]
     idx = 4
-    return (2 * nnz * (elem + idx) + 2 * (n + 1) * idx
-            + n * (2 * idx + 2 * elem + 2 * elem)      # perm x2, scale x2, b, out
-            + n * (4 * elem)                          # w write/read, z write/read
-            + (n - nd) * (2 * elem + idx)             # D^{-1} diagonal, off-diagonal, partner
-            + nd * nd * elem)
+    return (2 * nnz * (val + idx) + 2 * (n + 1) * idx
+            + n * (2 * idx + 2 * val + 2 * vec)       # perm x2, scale x2, b, out
+            + n * (4 * vec)                           # w write/read, z write/read
+            + (n - nd) * (2 * val + idx)              # D^{-1} diagonal, off-diagonal, partner
+            + nd * nd * val)
+
+
+def kernel_source_hash():
+    """SHA-1 of the apply kernel's source file: DRAM counters recorded for an
+    older source no longer describe the kernel that runs."""
+    import hashlib
+    with open(os.path.join(ROOT, "paper_math_0508111_gb300", "csrc", "ildl.cu"), "rb") as f:
+        return hashlib.sha1(f.read()).hexdigest()
+
+
+def measured_traffic(precision, info):
+    """DRAM bytes per apply from the committed ncu summary of this kernel
+    (profiles/ildl_apply_<precision>_traffic.json), scaled from the captured
+    lattice to this factor by the ratio of algorithmic bytes; None when no
+    capture exists or the kernel source changed since it was taken."""
+    path = os.path.join(ROOT, "profiles", "ildl_apply_%s_traffic.json" % precision)
+    try:
+        with open(path) as f:
+            d = json.load(f)
+    except Exception:
+        return None
+    if d.get("source_sha1") != kernel_source_hash():
+        return None
+    return d["dram_bytes_per_apply"] * apply_bytes(info, *d["val_vec_bytes"]) / d["algorithmic_bytes_per_apply"]
 
 
 def serving_sample(ajd, args, precision):
@@ -379,15 +403,10 @@ def main():
     calls = sum(s["precond_calls"] for s in stats)
     ms = sum(s["precond_ms"] for s in stats)
     info = stats[-1]["ildl"]
-    bytes_per = apply_bytes(info, 8 if args.precision == "fp64" else 4)
+    val_b, vec_b = {"fp64": (8, 8), "fp32": (4, 4), "mixed": (4, 8)}[args.precision]
+    bytes_per = apply_bytes(info, val_b, vec_b)
     achieved = bytes_per / (ms / calls / 1e3) / 1e9 if calls else 0.0
-    traffic = None
-    prof = os.path.join(ROOT, "profiles", "ildl_apply_fp32_traffic.json")
-    if os.path.exists(prof):
-        try:
-            traffic = json.load(open(prof)).get("dram_bytes_per_apply_scaled_to_L100")
-        except Exception:
-            traffic = None
+    traffic = measured_traffic(args.precision, info)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "kernel": "ildl_apply_persistent_kernel (one cooperative launch: gather, "
                                                "forward level sweeps, dense tail, backward level sweeps)",

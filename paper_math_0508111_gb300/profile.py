@@ -1,12 +1,13 @@
 """Small, repeatable workloads for timing and profiling single kernels.
 
-    python -m paper_math_0508111_gb300.profile apply   [--L 70] [--reps 5]
+    python -m paper_math_0508111_gb300.profile apply   [--L 70] [--reps 5] [--only fp32|fp64|mixed]
     python -m paper_math_0508111_gb300.profile stencil [--L 256] [--reps 20]
 
 ``apply`` builds the preconditioner of A - 0 I for an L^3 lattice (W = 16.5,
-seed 1) and times its application in binary32, binary32-with-binary64
-vectors and binary64 (3 warm-up applications each, then ``reps`` timed ones,
-CUDA events on the current stream).  ``stencil`` times y = A x in binary64
+seed 1) and times its application in binary32, binary64 and the mixed form
+(factor values as rounded upper words, binary64 vectors and sums): 3 warm-up
+applications each, then ``reps`` timed ones, CUDA events on the current
+stream.  ``stencil`` times y = A x in binary64
 and binary32 with the L2 flushed before every repetition.  Both print one
 JSON line per case.  Run them under ncu with ``-k regex:persistent`` or
 ``-k regex:stencil`` to capture the kernel of interest.
@@ -36,24 +37,21 @@ def _time(fn, reps, flush=None):
     return ts[len(ts) // 2]
 
 
-def apply_case(L, reps):
+def apply_case(L, reps, only=None):
     h = ajd.Anderson(L, 16.5, 1)
     P = ajd.Preconditioner.from_lattice(h, 0.0)
     info = P.info()
     print(json.dumps({"case": "setup", "L": L, **info}), flush=True)
-    for name, dt in [("fp32", torch.float32), ("fp64", torch.float64)]:
+    for name, dt, mixed in [("fp32", torch.float32, False), ("fp64", torch.float64, False),
+                            ("mixed", torch.float64, True)]:
+        if only and name != only:
+            continue
         b = torch.randn(h.n, device="cuda", dtype=dt)
         x = torch.empty_like(b)
         for _ in range(3):
-            P.apply(b, out=x)
-        ms = _time(lambda: P.apply(b, out=x), reps)
+            P.apply(b, out=x, mixed=mixed)
+        ms = _time(lambda: P.apply(b, out=x, mixed=mixed), reps)
         print(json.dumps({"case": "apply", "precision": name, "L": L, "ms": ms}), flush=True)
-    b = torch.randn(h.n, device="cuda", dtype=torch.float64)
-    x = torch.empty_like(b)
-    for _ in range(3):
-        P.apply(b, out=x, mixed=True)
-    ms = _time(lambda: P.apply(b, out=x, mixed=True), reps)
-    print(json.dumps({"case": "apply", "precision": "mixed", "L": L, "ms": ms}), flush=True)
 
 
 def stencil_case(L, reps):
@@ -74,9 +72,10 @@ def main():
     ap.add_argument("what", choices=["apply", "stencil"])
     ap.add_argument("--L", type=int, default=None)
     ap.add_argument("--reps", type=int, default=None)
+    ap.add_argument("--only", choices=["fp32", "fp64", "mixed"], default=None)
     a = ap.parse_args()
     if a.what == "apply":
-        apply_case(a.L or 70, a.reps or 5)
+        apply_case(a.L or 70, a.reps or 5, a.only)
     else:
         stencil_case(a.L or 256, a.reps or 20)
 
