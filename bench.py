@@ -279,7 +279,8 @@ def main():
     import paper_math_0508111_gb300 as ajd
     L, W, k, tol, sigma = args.L, args.W, args.k, args.tol, args.sigma
     nwarm, nsteps = args.warmup, args.steps
-    seeds = [1 + 100000 * rank + i for i in range(nwarm + nsteps)]
+    from paper_math_0508111_gb300 import replicas
+    seeds = replicas.realisation_seeds(nwarm + nsteps, rank)
     lattices = [ajd.Anderson(L, W, s) for s in seeds]  # potentials resident before timing
     n = lattices[0].n
     flush = torch.empty(256 * 1024 * 1024 // 4, device="cuda", dtype=torch.float32)
@@ -340,12 +341,7 @@ def main():
     torch.cuda.synchronize()
     barrier()
     clocks = sampler.stop()
-    elapsed = e0.elapsed_time(e1) / 1e3
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([elapsed], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed = float(t.item())
+    elapsed = replicas.max_over_ranks(e0.elapsed_time(e1) / 1e3)  # the slowest rank's time
     value = world * nsteps * k / elapsed
     setup_s = sum(s["setup_ms"] for s in stats) / 1e3
     solve_s = sum(s["solve_ms"] for s in stats) / 1e3
