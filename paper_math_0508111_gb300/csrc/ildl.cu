@@ -209,22 +209,27 @@ __device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned* gen, uns
   return failed == 0;
 }
 
+// Final value of row p of a sweep, given the row's dot product `acc` with
+// the solution entries it depends on (and, forward, its right-hand side).
+template <typename V, typename X, typename IO>
+__device__ __forceinline__ void finish_value(const ApplyArgs<V, X, IO>& a, int kind, int p, X acc, X rhs) {
+  if (kind == PH_FWD) {
+    __stcg(a.w + p, rhs - acc);  // rhs = s[p] b[perm[p]], stored in w by the gather phase
+  } else {
+    const int pp = __ldg(a.partner + p);
+    X d = ldw<X>(a.dd + p) * __ldcg(a.w + p);
+    if (pp >= 0) d += ldw<X>(a.dof + p) * __ldcg(a.w + pp);
+    const X zp = d - acc;
+    __stcg(a.z + p, zp);
+    a.out[__ldg(a.perm + p)] = (IO)(ldw<X>(a.scale + p) * zp);
+  }
+}
+
 template <typename V, typename X, typename IO, int G>
 __device__ __forceinline__ void finish_row(const ApplyArgs<V, X, IO>& a, int kind, int p, X acc, int lane, X rhs) {
 #pragma unroll
   for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, G);
-  if (p >= 0 && lane == 0) {
-    if (kind == PH_FWD) {
-      __stcg(a.w + p, rhs - acc);  // rhs = s[p] b[perm[p]], stored in w by the gather phase
-    } else {
-      const int pp = __ldg(a.partner + p);
-      X d = ldw<X>(a.dd + p) * __ldcg(a.w + p);
-      if (pp >= 0) d += ldw<X>(a.dof + p) * __ldcg(a.w + pp);
-      const X zp = d - acc;
-      __stcg(a.z + p, zp);
-      a.out[__ldg(a.perm + p)] = (IO)(ldw<X>(a.scale + p) * zp);
-    }
-  }
+  if (p >= 0 && lane == 0) finish_value(a, kind, p, acc, rhs);
 }
 
 // Rows of one level, G threads per row; each group handles two rows at a
@@ -290,6 +295,62 @@ __device__ __forceinline__ void level_rows(const ApplyArgs<V, X, IO>& a, int kin
     accb += accb2;
     finish_row<V, X, IO, G>(a, kind, pa, acca, lane, ra_rhs);
     finish_row<V, X, IO, G>(a, kind, pb, accb, lane, rb_rhs);
+  }
+}
+
+// Rows of one level with G = 64..512 threads per row (G / 32 warps, 512 / G
+// rows per CTA): for few, long rows, such as the deepest levels, whose rows
+// collect the fill of every earlier level.  Warp partial sums meet in
+// shared memory.  The row loop is uniform across the CTA (it depends on the
+// block index only), as the CTA barriers inside it require.
+template <typename V, typename X, typename IO, int G>
+__device__ __forceinline__ void level_rows_wide(const ApplyArgs<V, X, IO>& a, int kind, int p0, int p1) {
+  constexpr int W = G / 32;                 // warps per row
+  constexpr int RPC = kPersistThreads / G;  // rows per CTA and pass
+  constexpr int B = 8;                      // entries per thread and batch
+  __shared__ X part[kPersistThreads / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int slot = threadIdx.x / G, t = threadIdx.x % G;
+  const int* ptr = kind == PH_FWD ? a.Lptr : a.Uptr;
+  const int* col = kind == PH_FWD ? a.Lcol : a.Ucol;
+  const V* val = kind == PH_FWD ? a.Lval : a.Uval;
+  const X* x = kind == PH_FWD ? a.w : a.z;
+  for (int64_t base = p0 + (int64_t)blockIdx.x * RPC; base < p1; base += (int64_t)gridDim.x * RPC) {
+    const int p = base + slot < p1 ? (int)(base + slot) : -1;
+    X acc = X(0), acc2 = X(0);
+    if (p >= 0) {
+      int q = __ldg(ptr + p) + t;
+      const int e = __ldg(ptr + p + 1);
+      for (; q < e; q += B * G) {
+        int c[B];
+        X v[B];
+#pragma unroll
+        for (int i = 0; i < B; ++i) {
+          const bool o = q + i * G < e;
+          c[i] = o ? __ldg(col + q + i * G) : -1;
+          v[i] = o ? ldw<X>(val + q + i * G) : X(0);
+        }
+#pragma unroll
+        for (int i = 0; i < B; i += 2) {
+          const X x0 = c[i] >= 0 ? __ldcg(x + c[i]) : X(0);
+          const X x1 = c[i + 1] >= 0 ? __ldcg(x + c[i + 1]) : X(0);
+          acc += v[i] * x0;
+          acc2 += v[i + 1] * x1;
+        }
+      }
+    }
+    acc += acc2;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) part[warp] = acc;
+    __syncthreads();
+    if (p >= 0 && t == 0) {
+      X sum = X(0);
+#pragma unroll
+      for (int j = 0; j < W; ++j) sum += part[slot * W + j];
+      finish_value(a, kind, p, sum, kind == PH_FWD ? __ldcg(a.w + p) : X(0));
+    }
+    __syncthreads();  // part[] is reused by the next pass
   }
 }
 
@@ -363,11 +424,15 @@ ildl_apply_persistent_kernel(ApplyArgs<V, X, IO> a, const int4* __restrict__ pha
         }
       }
     } else {
-      switch (G) {
+      switch (G) {  // threads per row, fixed per phase at upload
         case 4: level_rows<V, X, IO, 4>(a, kind, p0, p1); break;
         case 8: level_rows<V, X, IO, 8>(a, kind, p0, p1); break;
         case 16: level_rows<V, X, IO, 16>(a, kind, p0, p1); break;
-        default: level_rows<V, X, IO, 32>(a, kind, p0, p1); break;
+        case 32: level_rows<V, X, IO, 32>(a, kind, p0, p1); break;
+        case 64: level_rows_wide<V, X, IO, 64>(a, kind, p0, p1); break;
+        case 128: level_rows_wide<V, X, IO, 128>(a, kind, p0, p1); break;
+        case 256: level_rows_wide<V, X, IO, 256>(a, kind, p0, p1); break;
+        default: level_rows_wide<V, X, IO, 512>(a, kind, p0, p1); break;
       }
     }
     if (ph + 1 < nphase) prefetch_phase<V, X, IO>(a, Pn);
@@ -452,7 +517,15 @@ int upload_factor(const HostFactor& F, DevFactor<T>& d, cudaStream_t st) {
   std::vector<int4> ph;
   const std::vector<int>& lvp = F.level_ptr;
   const int nl = F.nlev;
-  auto pick_g = [](double avg) { return avg > 48 ? 32 : avg > 16 ? 16 : avg > 6 ? 8 : 4; };
+  // threads per row: enough rows in flight to cover the grid, and about four
+  // stored entries per thread of a row (a power of two in 4..512)
+  const double threads_total = (double)sm_count() * kPersistThreads;
+  auto pick_g = [&](int rows, double avg) {
+    const double want = std::min(threads_total / std::max(rows, 1), avg / 4.0);
+    int g = 4;
+    while (g < 512 && 2 * g <= want) g *= 2;
+    return g;
+  };
   // the gather phase writes s[p] b[perm[p]] into w for every position; level
   // 0 rows are then final and later rows read their right-hand side from w
   ph.push_back(make_int4(PH_GATHER, 0, F.n, 1));
@@ -460,14 +533,14 @@ int upload_factor(const HostFactor& F, DevFactor<T>& d, cudaStream_t st) {
     const int p0 = lvp[l], p1 = lvp[l + 1];
     if (p1 <= p0) continue;
     const double avg = (double)(F.Lptr[p1] - F.Lptr[p0]) / (p1 - p0);
-    ph.push_back(make_int4(PH_FWD, p0, p1, pick_g(avg)));
+    ph.push_back(make_int4(PH_FWD, p0, p1, pick_g(p1 - p0, avg)));
   }
   if (F.n_dense > 0) ph.push_back(make_int4(PH_DENSE, lvp[nl], lvp[nl + 1], 32));
   for (int l = nl - 1; l >= 0; --l) {
     const int p0 = lvp[l], p1 = lvp[l + 1];
     if (p1 <= p0) continue;
     const double avg = (double)(F.Uptr[p1] - F.Uptr[p0]) / (p1 - p0);
-    ph.push_back(make_int4(PH_BWD, p0, p1, pick_g(avg)));
+    ph.push_back(make_int4(PH_BWD, p0, p1, pick_g(p1 - p0, avg)));
   }
   d.nphase = (int)ph.size();
   AJD_CUDA(cudaMalloc(&d.phases, std::max<size_t>(1, ph.size()) * sizeof(int4)));

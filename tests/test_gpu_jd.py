@@ -37,6 +37,23 @@ def test_ildl_apply_matches_oracle(ajd, L, bc, sigma, nd):
         P.close()
 
 
+def test_ildl_apply_wide_rows(ajd):
+    """A factor without dropping has few, long rows on its deepest levels:
+    those phases run with 64..512 threads per row (CTA-wide rows with a
+    shared-memory reduction) and must still equal the oracle's apply."""
+    with ajd.Anderson(22, 16.5, 1) as h:
+        P = ajd.Preconditioner.from_lattice(h, 0.3, n_dense=200, drop=0.0)
+        F = P.export()
+        assert P.info()["nnz_L"] > 5 * 10 ** 6  # deep rows of several hundred to thousands of entries
+        b = np.random.default_rng(3).standard_normal(h.n)
+        want = matching.apply_factor(F, b)
+        scale = np.abs(want).max()
+        for dt, mixed, tol in [(torch.float64, False, 1e-12), (torch.float32, False, 1e-3), (torch.float64, True, 1e-3)]:
+            x = P.apply(torch.tensor(b, device="cuda", dtype=dt), mixed=mixed).double().cpu().numpy()
+            assert np.abs(x - want).max() <= tol * scale, (dt, mixed)
+        P.close()
+
+
 @pytest.mark.parametrize("L,bc,sigma,nd", [(12, 1, -1.0, 200), (20, 0, 0.3, 1000)])
 def test_ildl_apply_no_read_before_write(ajd, monkeypatch, L, bc, sigma, nd):
     """Work vectors filled with NaN before the first apply (AJD_POISON_ALLOC):
