@@ -210,26 +210,29 @@ __device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned* gen, uns
 }
 
 // Final value of row p of a sweep, given the row's dot product `acc` with
-// the solution entries it depends on (and, forward, its right-hand side).
+// the solution entries it depends on, its right-hand side (forward) and its
+// 2x2 partner and permutation entry (backward; loaded before the row's
+// entries so that their latency overlaps the gathers).
 template <typename V, typename X, typename IO>
-__device__ __forceinline__ void finish_value(const ApplyArgs<V, X, IO>& a, int kind, int p, X acc, X rhs) {
+__device__ __forceinline__ void finish_value(const ApplyArgs<V, X, IO>& a, int kind, int p, X acc, X rhs, int pp,
+                                             int perm) {
   if (kind == PH_FWD) {
     __stcg(a.w + p, rhs - acc);  // rhs = s[p] b[perm[p]], stored in w by the gather phase
   } else {
-    const int pp = __ldg(a.partner + p);
     X d = ldw<X>(a.dd + p) * __ldcg(a.w + p);
     if (pp >= 0) d += ldw<X>(a.dof + p) * __ldcg(a.w + pp);
     const X zp = d - acc;
     __stcg(a.z + p, zp);
-    a.out[__ldg(a.perm + p)] = (IO)(ldw<X>(a.scale + p) * zp);
+    a.out[perm] = (IO)(ldw<X>(a.scale + p) * zp);
   }
 }
 
 template <typename V, typename X, typename IO, int G>
-__device__ __forceinline__ void finish_row(const ApplyArgs<V, X, IO>& a, int kind, int p, X acc, int lane, X rhs) {
+__device__ __forceinline__ void finish_row(const ApplyArgs<V, X, IO>& a, int kind, int p, X acc, int lane, X rhs,
+                                           int pp, int perm) {
 #pragma unroll
   for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, G);
-  if (p >= 0 && lane == 0) finish_value(a, kind, p, acc, rhs);
+  if (p >= 0 && lane == 0) finish_value(a, kind, p, acc, rhs, pp, perm);
 }
 
 // Rows of one level, G threads per row; each group handles two rows at a
@@ -244,22 +247,29 @@ __device__ __forceinline__ void level_rows(const ApplyArgs<V, X, IO>& a, int kin
   const int* col = kind == PH_FWD ? a.Lcol : a.Ucol;
   const V* val = kind == PH_FWD ? a.Lval : a.Uval;
   const X* x = kind == PH_FWD ? a.w : a.z;  // vector read through the columns
-  constexpr int B = G >= 32 ? 8 : 4;        // entries per lane and row per batch
+  constexpr int B = 8;                      // entries per lane and row per batch
   for (int64_t base = p0; base < p1; base += 2 * groups) {
     const int64_t ra = base + g0, rb = base + groups + g0;
     const int pa = ra < p1 ? (int)ra : -1;
     const int pb = rb < p1 ? (int)rb : -1;
     int qa = 0, ea = 0, qb = 0, eb = 0;
     X ra_rhs = X(0), rb_rhs = X(0);
+    int ppa = -1, ppb = -1, pma = 0, pmb = 0;
     if (pa >= 0) {
       qa = __ldg(ptr + pa) + lane;
       ea = __ldg(ptr + pa + 1);
-      if (kind == PH_FWD && lane == 0) ra_rhs = __ldcg(a.w + pa);
+      if (lane == 0) {
+        if (kind == PH_FWD) ra_rhs = __ldcg(a.w + pa);
+        else { ppa = __ldg(a.partner + pa); pma = __ldg(a.perm + pa); }
+      }
     }
     if (pb >= 0) {
       qb = __ldg(ptr + pb) + lane;
       eb = __ldg(ptr + pb + 1);
-      if (kind == PH_FWD && lane == 0) rb_rhs = __ldcg(a.w + pb);
+      if (lane == 0) {
+        if (kind == PH_FWD) rb_rhs = __ldcg(a.w + pb);
+        else { ppb = __ldg(a.partner + pb); pmb = __ldg(a.perm + pb); }
+      }
     }
     // two partial sums per row halve the dependent chain of FMAs
     X acca = X(0), accb = X(0), acca2 = X(0), accb2 = X(0);
@@ -293,8 +303,8 @@ __device__ __forceinline__ void level_rows(const ApplyArgs<V, X, IO>& a, int kin
     }
     acca += acca2;
     accb += accb2;
-    finish_row<V, X, IO, G>(a, kind, pa, acca, lane, ra_rhs);
-    finish_row<V, X, IO, G>(a, kind, pb, accb, lane, rb_rhs);
+    finish_row<V, X, IO, G>(a, kind, pa, acca, lane, ra_rhs, ppa, pma);
+    finish_row<V, X, IO, G>(a, kind, pb, accb, lane, rb_rhs, ppb, pmb);
   }
 }
 
@@ -317,7 +327,12 @@ __device__ __forceinline__ void level_rows_wide(const ApplyArgs<V, X, IO>& a, in
   const X* x = kind == PH_FWD ? a.w : a.z;
   for (int64_t base = p0 + (int64_t)blockIdx.x * RPC; base < p1; base += (int64_t)gridDim.x * RPC) {
     const int p = base + slot < p1 ? (int)(base + slot) : -1;
-    X acc = X(0), acc2 = X(0);
+    X acc = X(0), acc2 = X(0), rhs = X(0);
+    int pp = -1, pm = 0;
+    if (p >= 0 && t == 0) {
+      if (kind == PH_FWD) rhs = __ldcg(a.w + p);
+      else { pp = __ldg(a.partner + p); pm = __ldg(a.perm + p); }
+    }
     if (p >= 0) {
       int q = __ldg(ptr + p) + t;
       const int e = __ldg(ptr + p + 1);
@@ -348,7 +363,7 @@ __device__ __forceinline__ void level_rows_wide(const ApplyArgs<V, X, IO>& a, in
       X sum = X(0);
 #pragma unroll
       for (int j = 0; j < W; ++j) sum += part[slot * W + j];
-      finish_value(a, kind, p, sum, kind == PH_FWD ? __ldcg(a.w + p) : X(0));
+      finish_value(a, kind, p, sum, rhs, pp, pm);
     }
     __syncthreads();  // part[] is reused by the next pass
   }
@@ -521,7 +536,9 @@ int upload_factor(const HostFactor& F, DevFactor<T>& d, cudaStream_t st) {
   // stored entries per thread of a row (a power of two in 4..512)
   const double threads_total = (double)sm_count() * kPersistThreads;
   auto pick_g = [&](int rows, double avg) {
-    const double want = std::min(threads_total / std::max(rows, 1), avg / 4.0);
+    // (a phase of many long rows keeps up to a warp per row: each thread then
+    // works through several rows, eight entries per batch)
+    const double want = std::max(std::min(threads_total / std::max(rows, 1), avg / 4.0), std::min(avg / 8.0, 32.0));
     int g = 4;
     while (g < 512 && 2 * g <= want) g *= 2;
     return g;

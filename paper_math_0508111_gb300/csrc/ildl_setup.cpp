@@ -107,8 +107,25 @@ int max_product_matching(const SymCsr& A, std::vector<int>& match_col, std::vect
   }
   match_col.assign(n, -1);
   std::vector<int> match_row(n, -1);
-  // greedy start on zero reduced costs, preferring the diagonal
+  // greedy start on zero reduced costs: first every row whose diagonal has
+  // zero reduced cost takes it (rows are independent: no conflicts), then
+  // the other rows take a free zero-reduced-cost column in row order
+  auto zero_rc = [&](int i, int64_t p) {
+    const int j = A.col[p];
+    return cost[p] < kInf && cost[p] - u[i] - v[j] <= 1e-13 * (1.0 + std::fabs(u[i]) + std::fabs(v[j]));
+  };
+#pragma omp parallel for schedule(static)
+  for (int i = 0; i < n; ++i)
+    for (int64_t p = A.ptr[i]; p < A.ptr[i + 1]; ++p)
+      if (A.col[p] == i) {
+        if (zero_rc(i, p)) {
+          match_row[i] = i;
+          match_col[i] = i;
+        }
+        break;
+      }
   for (int i = 0; i < n; ++i) {
+    if (match_row[i] >= 0) continue;
     int best = -1;
     for (int64_t p = A.ptr[i]; p < A.ptr[i + 1]; ++p) {
       const int j = A.col[p];
@@ -297,6 +314,91 @@ struct Trip {
   double v;
 };
 
+// Stable parallel bucket scatter: items 0..N-1, taken in order, go to the
+// buckets key(i) in [0, nb) so that every bucket keeps its items in item
+// order.  The items are cut into contiguous chunks; per-chunk counts give
+// every (chunk, bucket) pair its own run of slots.  On return ptr holds the
+// nb + 1 bucket offsets and emit(i, slot) has been called once per item.
+template <class Key, class Emit>
+void stable_scatter(int64_t N, int nb, Key key, std::vector<int64_t>& ptr, Emit emit) {
+  const int T = (int)std::max<int64_t>(1, std::min<int64_t>(omp_get_max_threads(), N / 16384));
+  std::vector<unsigned> cnt((size_t)T * nb, 0u);
+#pragma omp parallel for schedule(static)
+  for (int t = 0; t < T; ++t) {
+    unsigned* c = cnt.data() + (size_t)t * nb;
+    for (int64_t i = N * t / T; i < N * (t + 1) / T; ++i) ++c[key(i)];
+  }
+  ptr.assign((size_t)nb + 1, 0);
+#pragma omp parallel for schedule(static)
+  for (int b = 0; b < nb; ++b) {
+    unsigned run = 0;  // offsets within the bucket, by chunk
+    for (int t = 0; t < T; ++t) {
+      const unsigned c = cnt[(size_t)t * nb + b];
+      cnt[(size_t)t * nb + b] = run;
+      run += c;
+    }
+    ptr[(size_t)b + 1] = run;
+  }
+  for (int b = 0; b < nb; ++b) ptr[(size_t)b + 1] += ptr[b];
+#pragma omp parallel for schedule(static)
+  for (int t = 0; t < T; ++t) {
+    unsigned* c = cnt.data() + (size_t)t * nb;
+    for (int64_t i = N * t / T; i < N * (t + 1) / T; ++i) {
+      const int b = key(i);
+      emit(i, ptr[b] + c[b]++);
+    }
+  }
+}
+
+// Stable parallel transpose of a CSR block (rows 0..nr-1, columns
+// 0..nc-1): row c of the result lists (r, val) for every entry (r, c), in
+// increasing r; entries with keep(r, c) false are left out.  Rows are cut
+// into chunks of about equal entry counts.
+template <class Keep>
+void stable_transpose(int nr, int nc, const std::vector<int64_t>& ptr, const std::vector<int>& col,
+                      const std::vector<double>& val, Keep keep, std::vector<int64_t>& tptr, std::vector<int>& tcol,
+                      std::vector<double>& tval) {
+  const int64_t nnz = ptr[nr];
+  const int T = (int)std::max<int64_t>(1, std::min<int64_t>(omp_get_max_threads(), nnz / 16384));
+  std::vector<int> rcut(T + 1, nr);
+  rcut[0] = 0;
+  for (int t = 1; t < T; ++t)
+    rcut[t] = (int)(std::lower_bound(ptr.begin(), ptr.begin() + nr + 1, nnz * t / T) - ptr.begin());
+  std::vector<unsigned> cnt((size_t)T * nc, 0u);
+#pragma omp parallel for schedule(static)
+  for (int t = 0; t < T; ++t) {
+    unsigned* c = cnt.data() + (size_t)t * nc;
+    for (int r = rcut[t]; r < rcut[t + 1]; ++r)
+      for (int64_t q = ptr[r]; q < ptr[r + 1]; ++q)
+        if (keep(r, col[q])) ++c[col[q]];
+  }
+  tptr.assign((size_t)nc + 1, 0);
+#pragma omp parallel for schedule(static)
+  for (int b = 0; b < nc; ++b) {
+    unsigned run = 0;
+    for (int t = 0; t < T; ++t) {
+      const unsigned c = cnt[(size_t)t * nc + b];
+      cnt[(size_t)t * nc + b] = run;
+      run += c;
+    }
+    tptr[(size_t)b + 1] = run;
+  }
+  for (int b = 0; b < nc; ++b) tptr[(size_t)b + 1] += tptr[b];
+  tcol.resize(tptr[nc]);
+  tval.resize(tptr[nc]);
+#pragma omp parallel for schedule(static)
+  for (int t = 0; t < T; ++t) {
+    unsigned* c = cnt.data() + (size_t)t * nc;
+    for (int r = rcut[t]; r < rcut[t + 1]; ++r)
+      for (int64_t q = ptr[r]; q < ptr[r + 1]; ++q)
+        if (keep(r, col[q])) {
+          const int64_t slot = tptr[col[q]] + c[col[q]]++;
+          tcol[slot] = r;
+          tval[slot] = val[q];
+        }
+  }
+}
+
 // Gauss–Jordan inverse with partial pivoting (row-major, in place on a copy).
 bool dense_inverse(int m, std::vector<double>& M, std::vector<double>& inv) {
   inv.assign((size_t)m * m, 0.0);
@@ -432,11 +534,16 @@ int build_ildl(const SymCsr& A, const ildl_params& prm, HostFactor& F, bool dens
       offsum[i] = o;
     }
     auto d1_of = [&](int i) { return diag[i] != 0.0 ? offsum[i] / std::fabs(diag[i]) : kInf; };
-    std::vector<Cand> cands;
-    cands.reserve(m);
-    for (const auto& g : groups) {
+    // one or two candidates per group, computed in parallel and compacted in
+    // group order (the same list a sequential pass produces)
+    const int ng = (int)groups.size();
+    std::vector<Cand> g1(ng), g2(ng);
+    std::vector<char> gcount(ng, 1);
+#pragma omp parallel for schedule(dynamic, 1024)
+    for (int gi = 0; gi < ng; ++gi) {
+      const auto& g = groups[gi];
       if (g.second < 0) {
-        cands.push_back({g.first, -1, d1_of(g.first)});
+        g1[gi] = {g.first, -1, d1_of(g.first)};
         continue;
       }
       const int i = g.first, j = g.second;
@@ -469,11 +576,18 @@ int build_ildl(const SymCsr& A, const ildl_params& prm, HostFactor& F, bool dens
         }
       }
       if (use2) {
-        cands.push_back({i, j, q2});
+        g1[gi] = {i, j, q2};
       } else {
-        cands.push_back({i, -1, d1_of(i)});
-        cands.push_back({j, -1, d1_of(j)});
+        g1[gi] = {i, -1, d1_of(i)};
+        g2[gi] = {j, -1, d1_of(j)};
+        gcount[gi] = 2;
       }
+    }
+    std::vector<Cand> cands;
+    cands.reserve(m);
+    for (int gi = 0; gi < ng; ++gi) {
+      cands.push_back(g1[gi]);
+      if (gcount[gi] == 2) cands.push_back(g2[gi]);
     }
     __gnu_parallel::stable_sort(cands.begin(), cands.end(), [](const Cand& x, const Cand& y) {
       if (x.q != y.q) return x.q < y.q;
@@ -616,10 +730,14 @@ int build_ildl(const SymCsr& A, const ildl_params& prm, HostFactor& F, bool dens
         lval.insert(lval.end(), cv[ch].begin(), cv[ch].end());
       }
     }
-    for (int r = 0; r < mc_n; ++r) {
-      const int k = cnodes[r];
-      for (int64_t p = lptr[r]; p < lptr[r + 1]; ++p)
-        trips.push_back({gid[k], gid[lnode[p]], lval[p] / cum[k]});
+    {
+      const size_t base = trips.size();
+      trips.resize(base + (size_t)lptr[mc_n]);
+#pragma omp parallel for schedule(static)
+      for (int r = 0; r < mc_n; ++r) {
+        const int k = cnodes[r];
+        for (int64_t p = lptr[r]; p < lptr[r + 1]; ++p) trips[base + p] = {gid[k], gid[lnode[p]], lval[p] / cum[k]};
+      }
     }
 
     const double tl_ms = ms_since(t_lf);
@@ -662,6 +780,7 @@ int build_ildl(const SymCsr& A, const ildl_params& prm, HostFactor& F, bool dens
       c1.swap(c12);
       c2.swap(c22);
     }
+    const double ts_rec = ms_since(t_schur);
     SymCsr U;  // upper triangle of S'
     U.n = mc_n;
     U.ptr.assign(mc_n + 1, 0);
@@ -750,33 +869,33 @@ int build_ildl(const SymCsr& A, const ildl_params& prm, HostFactor& F, bool dens
         U.val.insert(U.val.end(), uval[ch].begin(), uval[ch].end());
       }
     }
-    // mirror U into a full symmetric CSR
+    const double ts_num = ms_since(t_schur) - ts_rec;
+    // mirror U into a full symmetric CSR: row c holds the lower entries
+    // (r, c), r < c, in increasing r (a stable transpose of the strictly
+    // upper part), then its own upper entries
     SymCsr Sn;
     Sn.n = mc_n;
-    Sn.ptr.assign(mc_n + 1, 0);
-    for (int r = 0; r < mc_n; ++r)
-      for (int64_t p = U.ptr[r]; p < U.ptr[r + 1]; ++p) {
-        Sn.ptr[r + 1]++;
-        if (U.col[p] != r) Sn.ptr[U.col[p] + 1]++;
-      }
-    for (int r = 0; r < mc_n; ++r) Sn.ptr[r + 1] += Sn.ptr[r];
-    Sn.col.resize(Sn.ptr[mc_n]);
-    Sn.val.resize(Sn.ptr[mc_n]);
     {
-      std::vector<int64_t> fp(Sn.ptr.begin(), Sn.ptr.end() - 1);
-      // lower entries first (rows ascending give ascending columns), then upper
-      for (int r = 0; r < mc_n; ++r)
-        for (int64_t p = U.ptr[r]; p < U.ptr[r + 1]; ++p)
-          if (U.col[p] != r) {
-            const int c = U.col[p];
-            Sn.col[fp[c]] = r;
-            Sn.val[fp[c]++] = U.val[p];
-          }
-      for (int r = 0; r < mc_n; ++r)
-        for (int64_t p = U.ptr[r]; p < U.ptr[r + 1]; ++p) {
-          Sn.col[fp[r]] = U.col[p];
-          Sn.val[fp[r]++] = U.val[p];
+      std::vector<int64_t> lptr2;
+      std::vector<int> lcol2;
+      std::vector<double> lval2;
+      stable_transpose(mc_n, mc_n, U.ptr, U.col, U.val, [](int r, int c) { return c != r; }, lptr2, lcol2, lval2);
+      Sn.ptr.assign(mc_n + 1, 0);
+      for (int r = 0; r < mc_n; ++r) Sn.ptr[r + 1] = Sn.ptr[r] + (lptr2[r + 1] - lptr2[r]) + (U.ptr[r + 1] - U.ptr[r]);
+      Sn.col.resize(Sn.ptr[mc_n]);
+      Sn.val.resize(Sn.ptr[mc_n]);
+#pragma omp parallel for schedule(dynamic, 1024)
+      for (int r = 0; r < mc_n; ++r) {
+        int64_t o = Sn.ptr[r];
+        for (int64_t q = lptr2[r]; q < lptr2[r + 1]; ++q, ++o) {
+          Sn.col[o] = lcol2[q];
+          Sn.val[o] = lval2[q];
         }
+        for (int64_t q = U.ptr[r]; q < U.ptr[r + 1]; ++q, ++o) {
+          Sn.col[o] = U.col[q];
+          Sn.val[o] = U.val[q];
+        }
+      }
     }
     // next level's numbering
     std::vector<int> gid2(mc_n);
@@ -788,9 +907,9 @@ int build_ildl(const SymCsr& A, const ildl_params& prm, HostFactor& F, bool dens
     gid.swap(gid2);
     cum.swap(cum2);
     if (verbose)
-      std::fprintf(stderr, "ildl level %d: m=%d B=%zu C=%d nnzS'/row=%.1f nnzLF=%zu | match %.1f cand %.1f LF %.1f schur %.1f total %.1f ms\n",
+      std::fprintf(stderr, "ildl level %d: m=%d B=%zu C=%d nnzS'/row=%.1f nnzLF=%zu | match %.1f cand %.1f LF %.1f schur %.1f (records %.1f numeric %.1f) total %.1f ms\n",
                    level, m, acc.size(), mc_n, mc_n ? (double)Sn.col.size() / mc_n : 0.0, lnode.size(), tm_ms, tc_ms, tl_ms,
-                   ms_since(t_schur), ms_since(t_level));
+                   ms_since(t_schur), ts_rec, ts_num, ms_since(t_level));
     S = std::move(Sn);
   }
   const int nlev = level;
@@ -818,58 +937,39 @@ int build_ildl(const SymCsr& A, const ildl_params& prm, HostFactor& F, bool dens
   level_ptr.push_back((int)order.size());
   if ((int)order.size() != n) return fail(JD_ESETUP, "ildl: internal error, %zu of %d rows ordered", order.size(), n);
 
-  // global assembly in position space
+  // global assembly in position space (parallel counting and scattering;
+  // every row is sorted afterwards, so the result does not depend on the
+  // scatter order)
+  const auto t_asm = Clock::now();
   std::vector<int> pos(n);
+#pragma omp parallel for schedule(static)
   for (int p = 0; p < n; ++p) pos[order[p]] = p;
   F.nlev = nlev;
   F.n_dense = nd;
   F.perm = order;
   F.scale.resize(n);
+#pragma omp parallel for schedule(static)
   for (int p = 0; p < n; ++p) F.scale[p] = sc[order[p]];
   F.level_ptr = level_ptr;
-  F.Lptr.assign(n + 1, 0);
-  for (const Trip& t : trips) F.Lptr[pos[t.r] + 1]++;
-  for (int p = 0; p < n; ++p) F.Lptr[p + 1] += F.Lptr[p];
-  F.Lcol.resize(trips.size());
-  F.Lval.resize(trips.size());
-  {
-    std::vector<int64_t> fp(F.Lptr.begin(), F.Lptr.end() - 1);
-    for (const Trip& t : trips) {
-      const int r = pos[t.r];
-      F.Lcol[fp[r]] = pos[t.c];
-      F.Lval[fp[r]++] = t.v * sc[t.r];
-    }
-    std::vector<std::pair<int, double>> tmp;
-    for (int r = 0; r < n; ++r) {
-      tmp.clear();
-      for (int64_t q = F.Lptr[r]; q < F.Lptr[r + 1]; ++q) tmp.push_back({F.Lcol[q], F.Lval[q]});
-      std::sort(tmp.begin(), tmp.end());
-      for (size_t k = 0; k < tmp.size(); ++k) {
-        F.Lcol[F.Lptr[r] + k] = tmp[k].first;
-        F.Lval[F.Lptr[r] + k] = tmp[k].second;
-      }
-    }
-  }
+  // L rows: the triplets of a row were appended level by level, and within
+  // a level in increasing pivot position, so a stable scatter leaves every
+  // row sorted by column
+  const int64_t nt = (int64_t)trips.size();
+  F.Lcol.resize(nt);
+  F.Lval.resize(nt);
+  stable_scatter(nt, n, [&](int64_t q) { return pos[trips[q].r]; }, F.Lptr, [&](int64_t q, int64_t slot) {
+    const Trip& t = trips[q];
+    F.Lcol[slot] = pos[t.c];
+    F.Lval[slot] = t.v * sc[t.r];
+  });
   trips.clear();
   trips.shrink_to_fit();
   // transpose (rows of L^T = columns of L), entries ordered by row
-  F.Uptr.assign(n + 1, 0);
-  for (int64_t q = 0; q < (int64_t)F.Lcol.size(); ++q) F.Uptr[F.Lcol[q] + 1]++;
-  for (int p = 0; p < n; ++p) F.Uptr[p + 1] += F.Uptr[p];
-  F.Ucol.resize(F.Lcol.size());
-  F.Uval.resize(F.Lcol.size());
-  {
-    std::vector<int64_t> fp(F.Uptr.begin(), F.Uptr.end() - 1);
-    for (int r = 0; r < n; ++r)
-      for (int64_t q = F.Lptr[r]; q < F.Lptr[r + 1]; ++q) {
-        const int c = F.Lcol[q];
-        F.Ucol[fp[c]] = r;
-        F.Uval[fp[c]++] = F.Lval[q];
-      }
-  }
+  stable_transpose(n, n, F.Lptr, F.Lcol, F.Lval, [](int, int) { return true; }, F.Uptr, F.Ucol, F.Uval);
   F.dinv_d.assign(n, 0.0);
   F.dinv_o.assign(n, 0.0);
   F.partner.assign(n, -1);
+#pragma omp parallel for schedule(static)
   for (int p = 0; p < n - nd; ++p) {
     const int o = order[p];
     F.dinv_d[p] = dd[o];
@@ -877,8 +977,11 @@ int build_ildl(const SymCsr& A, const ildl_params& prm, HostFactor& F, bool dens
     F.partner[p] = part[o] >= 0 ? pos[part[o]] : -1;
   }
   F.dense_inv.swap(dense_inv);
-  F.max_abs_L = 0.0;
-  for (double v : F.Lval) F.max_abs_L = std::max(F.max_abs_L, std::fabs(v));
+  double mx = 0.0;
+#pragma omp parallel for reduction(max : mx) schedule(static)
+  for (int64_t q = 0; q < nt; ++q) mx = std::max(mx, std::fabs(F.Lval[q]));
+  F.max_abs_L = mx;
+  if (verbose) std::fprintf(stderr, "ildl global assembly: %.1f ms\n", ms_since(t_asm));
   F.t_match_ms = t_match;
   F.t_total_ms = ms_since(t_start);
   F.t_factor_ms = F.t_total_ms - t_match;
