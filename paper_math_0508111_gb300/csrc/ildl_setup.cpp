@@ -59,6 +59,38 @@ double lookup(const SymCsr& S, int i, int j) {
 
 }  // namespace
 
+// Natural logarithm of a positive finite double: x = m 2^e with m in
+// [sqrt(1/2), sqrt(2)), ln x = e ln 2 + 2 atanh(s), s = (m - 1) / (m + 1),
+// |s| < 0.1716, and atanh(s) = s + s^3/3 + s^5/5 + ... summed to s^19 (the
+// first omitted term is below 1e-16 relative).  A few times cheaper than the
+// library call; the matching only needs one consistent logarithm.
+inline double log_pos(double x) {
+  uint64_t b;
+  std::memcpy(&b, &x, sizeof(b));
+  const int ef = (int)((b >> 52) & 0x7ff);
+  if (ef == 0 || ef == 0x7ff) return std::log(x);  // subnormal, inf, nan
+  int e = ef - 1023;
+  b = (b & 0x000fffffffffffffull) | 0x3ff0000000000000ull;  // mantissa in [1, 2)
+  double m;
+  std::memcpy(&m, &b, sizeof(m));
+  if (m > 1.4142135623730951) {
+    m *= 0.5;
+    ++e;
+  }
+  const double s = (m - 1.0) / (m + 1.0), s2 = s * s;
+  double t = 1.0 / 19.0;
+  t = t * s2 + 1.0 / 17.0;
+  t = t * s2 + 1.0 / 15.0;
+  t = t * s2 + 1.0 / 13.0;
+  t = t * s2 + 1.0 / 11.0;
+  t = t * s2 + 1.0 / 9.0;
+  t = t * s2 + 1.0 / 7.0;
+  t = t * s2 + 1.0 / 5.0;
+  t = t * s2 + 1.0 / 3.0;
+  t = t * s2 + 1.0;
+  return (double)e * 0.6931471805599453 + 2.0 * s * t;
+}
+
 // ---------------------------------------------------------------------------
 // Section 5.1: maximise prod_i |a_{sigma(i) i}| <=> minimise sum c_{sigma(i) i}
 // with c_ij = log a_i - log |a_ij|, a_i = max_j |a_ij|.  Sparse Kuhn–Munkres:
@@ -76,7 +108,7 @@ int max_product_matching(const SymCsr& A, std::vector<int>& match_col, std::vect
     for (int64_t p = A.ptr[i]; p < A.ptr[i + 1]; ++p) r = std::max(r, std::fabs(A.val[p]));
     if (r == 0.0) r = 1.0;
     rowmax[i] = r;
-    logmax[i] = std::log(r);
+    logmax[i] = log_pos(r);
   }
   // cost of entry p (row i, column col[p]); +inf for explicit zeros
   std::vector<double> cost(A.val.size()), loga(A.val.size());
@@ -84,7 +116,7 @@ int max_product_matching(const SymCsr& A, std::vector<int>& match_col, std::vect
   for (int i = 0; i < n; ++i)
     for (int64_t p = A.ptr[i]; p < A.ptr[i + 1]; ++p) {
       const double a = std::fabs(A.val[p]);
-      loga[p] = a > 0.0 ? std::log(a) : -kInf;
+      loga[p] = a > 0.0 ? log_pos(a) : -kInf;
       cost[p] = a > 0.0 ? logmax[i] - loga[p] : kInf;
     }
   // v_j = min_i c_ij: by symmetry column j's entries are row j's entries,
@@ -124,97 +156,175 @@ int max_product_matching(const SymCsr& A, std::vector<int>& match_col, std::vect
         }
         break;
       }
-  for (int i = 0; i < n; ++i) {
-    if (match_row[i] >= 0) continue;
-    int best = -1;
-    for (int64_t p = A.ptr[i]; p < A.ptr[i + 1]; ++p) {
-      const int j = A.col[p];
-      if (match_col[j] >= 0 || cost[p] == kInf) continue;
-      if (cost[p] - u[i] - v[j] <= 1e-13 * (1.0 + std::fabs(u[i]) + std::fabs(v[j]))) {
-        if (best < 0 || j == i) best = j;
-        if (j == i) break;
+  {
+    // rounds: every open row proposes its first free zero-reduced-cost
+    // column (in parallel); in row order a proposal wins if its column is
+    // still free; the losers propose again; rows without a proposal stop
+    std::vector<int> todo;
+    for (int i = 0; i < n; ++i)
+      if (match_row[i] < 0) todo.push_back(i);
+    std::vector<int> prop, next;
+    while (!todo.empty()) {
+      prop.assign(todo.size(), -1);
+#pragma omp parallel for schedule(dynamic, 256)
+      for (size_t t = 0; t < todo.size(); ++t) {
+        const int i = todo[t];
+        for (int64_t p = A.ptr[i]; p < A.ptr[i + 1]; ++p)
+          if (match_col[A.col[p]] < 0 && zero_rc(i, p)) {
+            prop[t] = A.col[p];
+            break;
+          }
       }
-    }
-    if (best >= 0) {
-      match_row[i] = best;
-      match_col[best] = i;
+      next.clear();
+      for (size_t t = 0; t < todo.size(); ++t) {
+        const int j = prop[t];
+        if (j < 0) continue;
+        if (match_col[j] < 0) {
+          match_row[todo[t]] = j;
+          match_col[j] = todo[t];
+        } else {
+          next.push_back(todo[t]);
+        }
+      }
+      todo.swap(next);
     }
   }
-  // shortest augmenting paths
-  std::vector<double> dist(n, kInf);
-  std::vector<int> pred(n, -1);
-  std::vector<char> scanned(n, 0);
-  std::vector<int> touched, scanned_list, tree_rows;
-  std::vector<double> tree_d;
-  using Item = std::pair<double, int>;
-  std::priority_queue<Item, std::vector<Item>, std::greater<Item>> heap;
-  int unmatched = 0;
-  for (int s = 0; s < n; ++s) {
-    if (match_row[s] >= 0) continue;
-    touched.clear();
-    scanned_list.clear();
-    tree_rows.clear();
-    tree_d.clear();
-    while (!heap.empty()) heap.pop();
-    int i = s;
+  // shortest augmenting paths (Dijkstra over reduced costs), run in batches:
+  // the searches of a batch run in parallel on the same state; then, in row
+  // order, a search is applied if nothing it read (its tree rows and every
+  // column it touched) was written by a search applied before it in this
+  // batch, and is otherwise run again in the next batch.  Batches depend
+  // only on the row order and size, not on the thread count.
+  struct Search {
+    int s = -1, sink = -1;
+    double D = 0.0;
+    std::vector<int> touched, scanned, tree_rows, path;  // path: (row, col) pairs from the sink back
+    std::vector<double> tree_d, scanned_d;
+  };
+  struct Work {
+    std::vector<double> dist;
+    std::vector<int> pred;
+    std::vector<char> done;
+  };
+  const int nthreads = std::max(1, omp_get_max_threads());
+  std::vector<Work> work(nthreads);
+  auto search = [&](Work& W, Search& R) {
+    if (W.dist.empty()) {
+      W.dist.assign(n, kInf);
+      W.pred.assign(n, -1);
+      W.done.assign(n, 0);
+    }
+    using Item = std::pair<double, int>;
+    std::priority_queue<Item, std::vector<Item>, std::greater<Item>> heap;
+    R.touched.clear();
+    R.scanned.clear();
+    R.tree_rows.clear();
+    R.tree_d.clear();
+    R.scanned_d.clear();
+    R.path.clear();
+    R.sink = -1;
+    int i = R.s;
     double di = 0.0;
-    tree_rows.push_back(s);
-    tree_d.push_back(0.0);
-    int sink = -1;
+    R.tree_rows.push_back(i);
+    R.tree_d.push_back(0.0);
     for (;;) {
       for (int64_t p = A.ptr[i]; p < A.ptr[i + 1]; ++p) {
         const int j = A.col[p];
-        if (scanned[j] || cost[p] == kInf) continue;
+        if (W.done[j] || cost[p] == kInf) continue;
         const double nd = di + std::max(0.0, cost[p] - u[i] - v[j]);
-        if (nd < dist[j]) {
-          if (dist[j] == kInf) touched.push_back(j);
-          dist[j] = nd;
-          pred[j] = i;
+        if (nd < W.dist[j]) {
+          if (W.dist[j] == kInf) R.touched.push_back(j);
+          W.dist[j] = nd;
+          W.pred[j] = i;
           heap.push({nd, j});
         }
       }
       int jmin = -1;
       while (!heap.empty()) {
-        Item it = heap.top();
+        const Item it = heap.top();
         heap.pop();
-        if (!scanned[it.second] && it.first == dist[it.second]) {
+        if (!W.done[it.second] && it.first == W.dist[it.second]) {
           jmin = it.second;
           break;
         }
       }
       if (jmin < 0) break;  // no augmenting path from s
-      scanned[jmin] = 1;
-      scanned_list.push_back(jmin);
+      W.done[jmin] = 1;
+      R.scanned.push_back(jmin);
+      R.scanned_d.push_back(W.dist[jmin]);
       if (match_col[jmin] < 0) {
-        sink = jmin;
+        R.sink = jmin;
         break;
       }
       i = match_col[jmin];
-      di = dist[jmin];
-      tree_rows.push_back(i);
-      tree_d.push_back(di);
+      di = W.dist[jmin];
+      R.tree_rows.push_back(i);
+      R.tree_d.push_back(di);
     }
-    if (sink >= 0) {
-      const double D = dist[sink];
-      for (size_t t = 0; t < tree_rows.size(); ++t) u[tree_rows[t]] += D - tree_d[t];
-      for (int j : scanned_list) v[j] += dist[j] - D;
-      int j = sink;
-      for (;;) {
-        const int r = pred[j];
-        const int jprev = match_row[r];
-        match_row[r] = j;
-        match_col[j] = r;
-        if (r == s) break;
-        j = jprev;
+    if (R.sink >= 0) {
+      R.D = W.dist[R.sink];
+      for (int j = R.sink;;) {  // alternating path back to s
+        const int r = W.pred[j];
+        R.path.push_back(r);
+        R.path.push_back(j);
+        if (r == R.s) break;
+        j = match_row[r];
       }
-    } else {
-      ++unmatched;
     }
-    for (int j : touched) {
-      dist[j] = kInf;
-      pred[j] = -1;
+    for (int j : R.touched) {
+      W.dist[j] = kInf;
+      W.pred[j] = -1;
+      W.done[j] = 0;
     }
-    for (int j : scanned_list) scanned[j] = 0;
+  };
+  std::vector<int> open;
+  for (int i = 0; i < n; ++i)
+    if (match_row[i] < 0) open.push_back(i);
+  int unmatched = 0;
+  std::vector<int> wrow(n, -1), wcol(n, -1);  // batch that last wrote a row / column
+  std::vector<Search> batch;
+  std::vector<int> retry;
+  const size_t K = (size_t)std::max(8, std::min(1024, n / 2000));
+  int epoch = 0;
+  size_t head = 0;
+  while (head < open.size() || !retry.empty()) {
+    // next batch: rows to run again first, then fresh rows
+    std::vector<int> rows;
+    rows.swap(retry);
+    while (rows.size() < K && head < open.size()) rows.push_back(open[head++]);
+    batch.resize(rows.size());
+#pragma omp parallel for schedule(dynamic, 1)
+    for (size_t t = 0; t < rows.size(); ++t) {
+      batch[t].s = rows[t];
+      search(work[omp_get_thread_num()], batch[t]);
+    }
+    ++epoch;
+    for (size_t t = 0; t < rows.size(); ++t) {
+      Search& R = batch[t];
+      bool clash = false;
+      for (int r : R.tree_rows) clash = clash || wrow[r] == epoch;
+      for (int j : R.touched) clash = clash || wcol[j] == epoch;
+      if (clash) {
+        retry.push_back(R.s);
+        continue;
+      }
+      if (R.sink < 0) {
+        ++unmatched;
+        continue;
+      }
+      for (size_t q = 0; q < R.tree_rows.size(); ++q) {
+        u[R.tree_rows[q]] += R.D - R.tree_d[q];
+        wrow[R.tree_rows[q]] = epoch;
+      }
+      for (size_t q = 0; q < R.scanned.size(); ++q) {
+        v[R.scanned[q]] += R.scanned_d[q] - R.D;
+        wcol[R.scanned[q]] = epoch;
+      }
+      for (size_t q = 0; q < R.path.size(); q += 2) {
+        match_row[R.path[q]] = R.path[q + 1];
+        match_col[R.path[q + 1]] = R.path[q];
+      }
+    }
   }
   if (unmatched) {
     // structurally singular: pair the leftover rows and columns in index
