@@ -335,9 +335,11 @@ def main():
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("bench_timed")  # ncu --nvtx --nvtx-include bench_timed/ captures this region only
     e0.record(stream)
     stats = batch([h.handle for h in lattices[nwarm:]], head, ev_ptrs, x_ptrs)
     e1.record(stream)
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     barrier()
     clocks = sampler.stop()

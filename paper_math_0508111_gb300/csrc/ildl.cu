@@ -28,104 +28,6 @@
 namespace ajd {
 namespace {
 
-// ---- Gauss–Jordan inversion of the dense trailing block (setup) ----
-// A and X are m x m row-major binary64; X starts as I and ends as A^{-1}.
-// Pivot c: argmax_{r >= c} |A[r][c]| (ties: smallest r).
-__global__ void gj_pivot_kernel(const double* __restrict__ A, int m, int c, int* piv, double* pval, int* bad) {
-  __shared__ double bv[1024];
-  __shared__ int bi[1024];
-  double best = -1.0;
-  int arg = c;
-  for (int r = c + threadIdx.x; r < m; r += blockDim.x) {
-    const double a = fabs(A[(int64_t)r * m + c]);
-    if (a > best) { best = a; arg = r; }
-  }
-  bv[threadIdx.x] = best;
-  bi[threadIdx.x] = arg;
-  __syncthreads();
-  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-    if (threadIdx.x < o) {
-      const double b2 = bv[threadIdx.x + o];
-      const int i2 = bi[threadIdx.x + o];
-      if (b2 > bv[threadIdx.x] || (b2 == bv[threadIdx.x] && i2 < bi[threadIdx.x])) {
-        bv[threadIdx.x] = b2;
-        bi[threadIdx.x] = i2;
-      }
-    }
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) {
-    *piv = bi[0];
-    *pval = A[(int64_t)bi[0] * m + c];
-    if (!(bv[0] > 0.0) || !isfinite(bv[0])) *bad = 1;
-  }
-}
-
-// swap rows c and piv, scale the new row c by 1/pivot; f[r] = A[r][c] after
-// the swap (f[c] = 1)
-__global__ void gj_swap_scale_kernel(double* __restrict__ A, double* __restrict__ X, int m, int c,
-                                     const int* __restrict__ piv, const double* __restrict__ pval) {
-  const int p = *piv;
-  const double inv = 1.0 / *pval;
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < m; k += gridDim.x * blockDim.x) {
-    const double ac = A[(int64_t)c * m + k], ap = A[(int64_t)p * m + k];
-    const double xc = X[(int64_t)c * m + k], xp = X[(int64_t)p * m + k];
-    A[(int64_t)c * m + k] = ap * inv;
-    X[(int64_t)c * m + k] = xp * inv;
-    if (p != c) {
-      A[(int64_t)p * m + k] = ac;
-      X[(int64_t)p * m + k] = xc;
-    }
-  }
-}
-
-__global__ void gj_save_col_kernel(const double* __restrict__ A, int m, int c, double* __restrict__ f) {
-  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < m; r += gridDim.x * blockDim.x) f[r] = A[(int64_t)r * m + c];
-}
-
-// rows r != c: A[r][k] -= f[r] A[c][k] for k > c (A[r][c] becomes 0) and
-// X[r][k] -= f[r] X[c][k] for all k.  Columns k < c of A are unit columns
-// untouched by the (row >= c) swaps, so they are skipped; X is updated in
-// full because row swaps move entries into its later columns.
-// (flattened grid-stride loop over all (r, j), j < 2m - c)
-__global__ void gj_eliminate_kernel(double* __restrict__ A, double* __restrict__ X, int m, int c,
-                                    const double* __restrict__ f) {
-  const int64_t w = (int64_t)(m - c) + m;
-  const int64_t total = (int64_t)m * w;
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
-    const int r = (int)(t / w);
-    const int j = (int)(t - (int64_t)r * w);
-    if (r == c) continue;
-    const double fr = f[r];
-    if (fr == 0.0) continue;
-    if (j < m - c) {  // A columns c .. m-1
-      const int k = c + j;
-      if (k == c) A[(int64_t)r * m + k] = 0.0;
-      else A[(int64_t)r * m + k] -= fr * A[(int64_t)c * m + k];
-    } else {          // X columns 0 .. m-1
-      const int k = j - (m - c);
-      X[(int64_t)r * m + k] -= fr * X[(int64_t)c * m + k];
-    }
-  }
-}
-
-__global__ void gj_symmetrize_kernel(double* __restrict__ X, int m) {
-  const int64_t total = (int64_t)m * m;
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
-    const int i = (int)(t / m), j = (int)(t % m);
-    if (j <= i) continue;
-    const double s = 0.5 * (X[(int64_t)i * m + j] + X[(int64_t)j * m + i]);
-    X[(int64_t)i * m + j] = s;
-    X[(int64_t)j * m + i] = s;
-  }
-}
-
-__global__ void identity_kernel(double* __restrict__ X, int m) {
-  const int64_t total = (int64_t)m * m;
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x)
-    X[t] = (t / m == t % m) ? 1.0 : 0.0;
-}
-
 // ---- persistent apply: all phases of K^{-1} b in one cooperative launch ----
 // Phase kinds: gather (level 0), forward level, dense trailing block,
 // backward level.  Phases run in order; a grid-wide barrier separates them
@@ -177,11 +79,11 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
   return v;
 }
 
-// Grid barrier number `ph` (0-based) of one apply: every CTA adds one
-// arrival to `count`; the last arrival of this barrier publishes generation
-// ph + 1 in `gen` (a different cache line), which the other CTAs poll.  Polls
-// are bounded: after kSpinLimit of them the CTA records a timeout in `err`
-// and the whole apply returns early.
+// Grid barrier number `ph` (0-based) of one cooperative launch: every CTA
+// adds one arrival to `count` (release) and polls it (acquire) until all
+// CTAs of barriers 0..ph have arrived.  Polls are bounded: after kSpinLimit
+// of them the CTA records a timeout in `err` and the kernel returns early;
+// the other CTAs see the flag and return too.
 __device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned* gen, unsigned ph, int* err) {
   (void)gen;
   __syncthreads();
@@ -213,6 +115,120 @@ __device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned* gen, uns
 // the solution entries it depends on, its right-hand side (forward) and its
 // 2x2 partner and permutation entry (backward; loaded before the row's
 // entries so that their latency overlaps the gathers).
+// ---- Gauss–Jordan inversion of the dense trailing block (setup) ----
+// X = A^{-1} for the m x m row-major binary64 matrix A (overwritten), with
+// partial pivoting, in one cooperative launch: for every column c three
+// phases separated by grid barriers --
+//   1. each CTA finds the largest |A[r][c]|, r >= c, over its share of the
+//      rows (partials: value with sign, row);
+//   2. every CTA reduces the partials (largest modulus, lowest row on ties),
+//      swaps rows c and piv of A (columns >= c) and of X, scales the new row
+//      c by 1/pivot, and records the multipliers f[r] = A[r][c];
+//   3. rows r != c: A[r][k] -= f[r] A[c][k] (k >= c) and X[r][k] -= f[r] X[c][k]
+//      (all k: the swaps move entries of X into every column).
+// X starts as I and ends symmetrised ((X + X^T)/2).  A zero or non-finite
+// pivot sets *bad.  Bounded barrier waits set *err, and the kernel returns.
+constexpr int kGjThreads = 512;
+
+__global__ void __launch_bounds__(kGjThreads, 1)
+gj_invert_kernel(double* __restrict__ A, double* __restrict__ X, int m, double* __restrict__ part_v,
+                 int* __restrict__ part_i, double* __restrict__ f, double* __restrict__ acc_old, unsigned* count,
+                 int* err, int* bad) {
+  // every read of data another CTA may have written goes through L2 (__ldcg)
+  __shared__ double sv[kGjThreads / 32];
+  __shared__ int si[kGjThreads / 32];
+  __shared__ int s_piv;
+  __shared__ double s_pval;
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t nth = (int64_t)gridDim.x * blockDim.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned ph = 0;
+  for (int64_t t = tid; t < (int64_t)m * m; t += nth) X[t] = (t / m == t % m) ? 1.0 : 0.0;
+  if (!grid_barrier(count, nullptr, ph++, err)) return;
+  for (int c = 0; c < m; ++c) {
+    // 1. partial pivot search (largest modulus, lowest row on ties; the
+    //    partial keeps the signed value)
+    double bv = 0.0;
+    int bi = m;
+    for (int64_t r = c + tid; r < m; r += nth) {
+      const double a = __ldcg(A + r * m + c);
+      if (bi == m || fabs(a) > fabs(bv)) { bv = a; bi = (int)r; }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      const double v2 = __shfl_xor_sync(0xffffffffu, bv, o);
+      const int i2 = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (i2 < m && (bi == m || fabs(v2) > fabs(bv) || (fabs(v2) == fabs(bv) && i2 < bi))) { bv = v2; bi = i2; }
+    }
+    if (lane == 0) { sv[warp] = bv; si[warp] = bi; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int w = 0;
+      for (int j = 1; j < kGjThreads / 32; ++j)
+        if (si[j] < m && (si[w] == m || fabs(sv[j]) > fabs(sv[w]) || (fabs(sv[j]) == fabs(sv[w]) && si[j] < si[w])))
+          w = j;
+      part_i[blockIdx.x] = si[w];
+      part_v[blockIdx.x] = sv[w];
+      if (blockIdx.x == 0) *acc_old = __ldcg(A + (int64_t)c * m + c);
+    }
+    if (!grid_barrier(count, nullptr, ph++, err)) return;
+    // 2. reduce the partials (every CTA, same order), swap, scale, multipliers
+    if (threadIdx.x == 0) {
+      int w = 0;
+      for (int j = 1; j < (int)gridDim.x; ++j) {
+        const int ij = __ldcg(part_i + j), iw = __ldcg(part_i + w);
+        const double vj = fabs(__ldcg(part_v + j)), vw = fabs(__ldcg(part_v + w));
+        if (ij < m && (iw == m || vj > vw || (vj == vw && ij < iw))) w = j;
+      }
+      const int pw = __ldcg(part_i + w);
+      s_piv = pw < m ? pw : c;
+      s_pval = pw < m ? __ldcg(part_v + w) : 0.0;
+      if (!(fabs(s_pval) > 0.0) || !isfinite(s_pval)) *bad = 1;
+    }
+    __syncthreads();
+    const int piv = s_piv;
+    const double inv = 1.0 / s_pval;
+    const double aold = __ldcg(acc_old);
+    // multipliers first: rows other than c and piv are not written in this
+    // phase; f[piv] is the old A[c][c], which the swap moves to row piv
+    for (int64_t r = tid; r < m; r += nth) f[r] = r == c ? 0.0 : (r == piv ? aold : __ldcg(A + r * m + c));
+    for (int64_t k = tid; k < m; k += nth) {
+      const double xc = __ldcg(X + (int64_t)c * m + k), xp = __ldcg(X + (int64_t)piv * m + k);
+      X[(int64_t)c * m + k] = xp * inv;
+      if (piv != c) X[(int64_t)piv * m + k] = xc;
+      if (k >= c) {
+        const double ac = __ldcg(A + (int64_t)c * m + k), ap = __ldcg(A + (int64_t)piv * m + k);
+        A[(int64_t)c * m + k] = ap * inv;
+        if (piv != c) A[(int64_t)piv * m + k] = ac;
+      }
+    }
+    if (!grid_barrier(count, nullptr, ph++, err)) return;
+    // 3. eliminate column c from every other row (f[c] = 0 skips row c)
+    const int64_t w = (int64_t)(m - c) + m;
+    for (int64_t t = tid; t < (int64_t)m * w; t += nth) {
+      const int r = (int)(t / w);
+      const int j = (int)(t - (int64_t)r * w);
+      const double fr = __ldcg(f + r);
+      if (fr == 0.0) continue;
+      if (j < m - c) {
+        const int k = c + j;
+        if (k == c) A[(int64_t)r * m + k] = 0.0;
+        else A[(int64_t)r * m + k] = __ldcg(A + (int64_t)r * m + k) - fr * __ldcg(A + (int64_t)c * m + k);
+      } else {
+        const int k = j - (m - c);
+        X[(int64_t)r * m + k] = __ldcg(X + (int64_t)r * m + k) - fr * __ldcg(X + (int64_t)c * m + k);
+      }
+    }
+    if (!grid_barrier(count, nullptr, ph++, err)) return;
+  }
+  for (int64_t t = tid; t < (int64_t)m * m; t += nth) {
+    const int i = (int)(t / m), j = (int)(t % m);
+    if (j <= i) continue;
+    const double sym = 0.5 * (__ldcg(X + (int64_t)i * m + j) + __ldcg(X + (int64_t)j * m + i));
+    X[(int64_t)i * m + j] = sym;
+    X[(int64_t)j * m + i] = sym;
+  }
+}
+
 template <typename V, typename X, typename IO>
 __device__ __forceinline__ void finish_value(const ApplyArgs<V, X, IO>& a, int kind, int p, X acc, X rhs, int pp,
                                              int perm) {
@@ -680,44 +696,48 @@ template int ildl_apply_dev<float>(const ildl_s*, const float*, float*, cudaStre
 // current device.
 int invert_dense_on_device(std::vector<double>& M, int m, cudaStream_t st) {
   if (m == 0) return JD_OK;
-  double *A = nullptr, *X = nullptr, *f = nullptr, *pv = nullptr;
-  int *piv = nullptr, *bad = nullptr;
   const size_t bytes = (size_t)m * m * sizeof(double);
+  const int grid = sm_count();
+  double *A = nullptr, *X = nullptr, *f = nullptr, *pv = nullptr;
+  int* pi = nullptr;
+  unsigned* bar = nullptr;  // [0] arrivals, [32] timeout flag, [64] singular flag, [96..97] old pivot-row entry
   cudaError_t e = cudaMalloc(&A, bytes);
   if (e == cudaSuccess) e = cudaMalloc(&X, bytes);
-  if (e == cudaSuccess) e = cudaMalloc(&f, m * sizeof(double));
-  if (e == cudaSuccess) e = cudaMalloc(&pv, sizeof(double));
-  if (e == cudaSuccess) e = cudaMalloc(&piv, sizeof(int));
-  if (e == cudaSuccess) e = cudaMalloc(&bad, sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&f, (size_t)m * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&pv, (size_t)grid * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&pi, (size_t)grid * sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&bar, 128 * sizeof(unsigned));
   int rc = JD_OK;
   if (e == cudaSuccess) e = cudaMemcpyAsync(A, M.data(), bytes, cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(bad, 0, sizeof(int), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(bar, 0, 128 * sizeof(unsigned), st);
   if (e == cudaSuccess) {
-    const int gb = std::max(1, std::min(ceil_div((int64_t)m * m, 256), 8 * sm_count()));
-    identity_kernel<<<gb, 256, 0, st>>>(X, m);
-    const int cb = ceil_div(m, 256);
-    for (int c = 0; c < m; ++c) {
-      gj_pivot_kernel<<<1, 1024, 0, st>>>(A, m, c, piv, pv, bad);
-      gj_swap_scale_kernel<<<cb, 256, 0, st>>>(A, X, m, c, piv, pv);
-      gj_save_col_kernel<<<cb, 256, 0, st>>>(A, m, c, f);
-      gj_eliminate_kernel<<<gb, 256, 0, st>>>(A, X, m, c, f);
-    }
-    gj_symmetrize_kernel<<<gb, 256, 0, st>>>(X, m);
-    count_launches(4 * m + 2);
-    e = cudaGetLastError();
-    int hbad = 0;
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, st);
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gj_invert_kernel, kGjThreads, 0);
+    if (e == cudaSuccess && per_sm < 1) e = cudaErrorInvalidConfiguration;
+  }
+  if (e == cudaSuccess) {
+    unsigned* cnt = bar;
+    int* err = reinterpret_cast<int*>(bar + 32);
+    int* bad = reinterpret_cast<int*>(bar + 64);
+    double* acc_old = reinterpret_cast<double*>(bar + 96);
+    void* args[] = {&A, &X, &m, &pv, &pi, &f, &acc_old, &cnt, &err, &bad};
+    e = cudaLaunchCooperativeKernel((void*)gj_invert_kernel, dim3(grid), dim3(kGjThreads), args, 0, st);
+    count_launches();
+    int flags[2] = {0, 0};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&flags[0], err, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&flags[1], bad, sizeof(int), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(M.data(), X, bytes, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (e == cudaSuccess && hbad) rc = fail(JD_ESETUP, "ildl: the final dense block (%d rows) is singular", m);
+    if (e == cudaSuccess && flags[0]) rc = fail(JD_EDEVICE, "ildl dense inverse: a device-side barrier timed out");
+    else if (e == cudaSuccess && flags[1]) rc = fail(JD_ESETUP, "ildl: the final dense block (%d rows) is singular", m);
   }
   if (e != cudaSuccess) rc = fail(JD_EDEVICE, "ildl dense inverse: %s", cudaGetErrorString(e));
   cudaFree(A);
   cudaFree(X);
   cudaFree(f);
   cudaFree(pv);
-  cudaFree(piv);
-  cudaFree(bad);
+  cudaFree(pi);
+  cudaFree(bar);
   return rc;
 }
 
