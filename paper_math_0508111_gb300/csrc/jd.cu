@@ -107,14 +107,27 @@ shifted_dots_kernel(const double* __restrict__ V, const double* __restrict__ AV,
   }
 }
 
-// out[j] = sum_b partial[b*ncols + j] (fixed order, deterministic)
-__global__ void reduce_partials_kernel(const double* __restrict__ partial, int nblocks, int ncols,
-                                       double* __restrict__ out, const int* done) {
+// out[j] = sum_b partial[b*ncols + j]: one warp per column, lanes striding
+// over the blocks, then a shuffle tree (fixed order, deterministic)
+constexpr int kRedThreads = 256;
+
+__device__ __forceinline__ double warp_sum_partials(const double* __restrict__ partial, int nblocks, int stride,
+                                                    int j) {
+  const int lane = threadIdx.x & 31;
+  double s = 0.0;
+  for (int b = lane; b < nblocks; b += 32) s += partial[(int64_t)b * stride + j];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  return s;
+}
+
+__global__ void __launch_bounds__(kRedThreads)
+reduce_partials_kernel(const double* __restrict__ partial, int nblocks, int ncols, double* __restrict__ out,
+                       const int* done) {
   if (done && *done) return;
-  for (int j = threadIdx.x; j < ncols; j += blockDim.x) {
-    double s = 0.0;
-    for (int b = 0; b < nblocks; ++b) s += partial[(int64_t)b * ncols + j];
-    out[j] = s;
+  const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int j = warp; j < ncols; j += nw) {
+    const double s = warp_sum_partials(partial, nblocks, ncols, j);
+    if ((threadIdx.x & 31) == 0) out[j] = s;
   }
 }
 
@@ -347,8 +360,8 @@ __global__ void sqmr_scalar_theta_kernel(const double* __restrict__ partial, int
                                          const double* __restrict__ dots, int c, double* __restrict__ scal,
                                          int* done, int* breakdown) {
   if (*done) return;
-  double rr = 0.0;
-  for (int b = 0; b < nblocks; ++b) rr += partial[b];
+  const double rr = warp_sum_partials(partial, nblocks, 1, 0);  // one warp; lane 0 goes on
+  if (threadIdx.x != 0) return;
   const double sigma = dots[c];
   if (sigma == 0.0 || !isfinite(sigma)) {
     *breakdown = 1;
@@ -424,8 +437,8 @@ sqmr_update_u_kernel(Cols<T> W, const double* __restrict__ gg, const T* __restri
 __global__ void sqmr_scalar_beta_kernel(const double* __restrict__ partial, int nblocks, double* __restrict__ scal,
                                         int first, int* done, int* breakdown) {
   if (*done) return;
-  double rho = 0.0;
-  for (int b = 0; b < nblocks; ++b) rho += partial[b];
+  const double rho = warp_sum_partials(partial, nblocks, 1, 0);  // one warp; lane 0 goes on
+  if (threadIdx.x != 0) return;
   if (first) {
     scal[S_BETA] = 0.0;
   } else {
@@ -476,8 +489,8 @@ sqmr_init_kernel(const T* __restrict__ b, T* __restrict__ r, T* __restrict__ x, 
 
 __global__ void sqmr_scalar_init_kernel(const double* __restrict__ partial, int nblocks, double* __restrict__ scal,
                                         double rel_tol, int* done, int* breakdown) {
-  double rr = 0.0;
-  for (int b = 0; b < nblocks; ++b) rr += partial[b];
+  const double rr = warp_sum_partials(partial, nblocks, 1, 0);  // one warp; lane 0 goes on
+  if (threadIdx.x != 0) return;
   const double bn = sqrt(rr);
   for (int i = 0; i < S_NSCAL; ++i) scal[i] = 0.0;
   scal[S_TAU] = bn;
@@ -773,7 +786,7 @@ int JdSolver::dot_cols(Cols<double> X1, Cols<double> X2, const double* extra, co
   const int nc = X1.c + X2.c + (extra ? 1 : 0);
   if (nc == 0) return JD_OK;
   multidot_kernel<double><<<nb_, kThreads, 0, s_>>>(X1, X2, extra, v, n_, partial_, nc, nullptr); count_launches();
-  reduce_partials_kernel<<<1, 128, 0, s_>>>(partial_, nb_, nc, out, nullptr); count_launches();
+  reduce_partials_kernel<<<1, kRedThreads, 0, s_>>>(partial_, nb_, nc, out, nullptr); count_launches();
   AJD_CHECK_LAUNCH();
   return JD_OK;
 }
@@ -826,7 +839,7 @@ int JdSolver::cache_lock_column(int kc) {
   AJD_TRY((apply_k<T, P>(Qt + (int64_t)kc * ld_, W + (int64_t)kc * ld_)));
   multidot_kernel<T><<<nb_, kThreads, 0, s_>>>(Cols<T>{Qt, ld_, c}, Cols<T>{}, nullptr, W + (int64_t)kc * ld_, n_,
                                                partial_, c, nullptr); count_launches();
-  reduce_partials_kernel<<<1, 128, 0, s_>>>(partial_, nb_, c, dots_, nullptr); count_launches();
+  reduce_partials_kernel<<<1, kRedThreads, 0, s_>>>(partial_, nb_, c, dots_, nullptr); count_launches();
   std::vector<double> col(c);
   AJD_TRY(sync_read(dots_, c, col.data()));
   std::vector<double> Mn((size_t)c * c);
@@ -857,7 +870,7 @@ int JdSolver::correction(int kc, double theta_hat, double rel_tol, int* its) {
   {
     multidot_kernel<T><<<bl, kThreads, 0, s_>>>(Cols<T>{Qt, ld_, c}, Cols<T>{}, nullptr, W + (int64_t)kc * ld_, n_,
                                                 partial_, c, nullptr); count_launches();
-    reduce_partials_kernel<<<1, 128, 0, s_>>>(partial_, bl, c, dots_, nullptr); count_launches();
+    reduce_partials_kernel<<<1, kRedThreads, 0, s_>>>(partial_, bl, c, dots_, nullptr); count_launches();
     std::vector<double> col(c);
     AJD_TRY(sync_read(dots_, c, col.data()));
     // assemble M (host) from the cached Q block and the new column, invert
@@ -902,20 +915,20 @@ int JdSolver::correction(int kc, double theta_hat, double rel_tol, int* its) {
   Cols<T> QtC{Qt, ld_, c}, WC{W, ld_, c};
   // init: r = b, x = d = 0, tau = ||b||; u = P b; q = u; rho = r^T u
   sqmr_init_kernel<T><<<bl, kThreads, 0, s_>>>(b, r, x, d, q, n_, partial_); count_launches();
-  sqmr_scalar_init_kernel<<<1, 1, 0, s_>>>(partial_, bl, scal_, rel_tol, done, brk); count_launches();
+  sqmr_scalar_init_kernel<<<1, 32, 0, s_>>>(partial_, bl, scal_, rel_tol, done, brk); count_launches();
   auto precond = [&]() -> int {
     const bool timed = nevp_ < kEv;
     if (timed) AJD_CUDA(cudaEventRecord(evp_[2 * nevp_], s_));
     AJD_TRY((apply_k<T, P>(r, y)));
     if (timed) AJD_CUDA(cudaEventRecord(evp_[2 * nevp_++ + 1], s_));
     multidot_kernel<T><<<bl, kThreads, 0, s_>>>(QtC, Cols<T>{}, nullptr, y, n_, partial_, c, done); count_launches();
-    reduce_partials_kernel<<<1, 128, 0, s_>>>(partial_, bl, c, dots_, done); count_launches();
+    reduce_partials_kernel<<<1, kRedThreads, 0, s_>>>(partial_, bl, c, dots_, done); count_launches();
     small_matvec_kernel<<<1, 64, 0, s_>>>(Minv_, c, dots_, gg_, done); count_launches();
     sqmr_update_u_kernel<T><<<bl, kThreads, 0, s_>>>(WC, gg_, y, r, u, n_, partial_, done); count_launches();
     return JD_OK;
   };
   AJD_TRY(precond());
-  sqmr_scalar_beta_kernel<<<1, 1, 0, s_>>>(partial_, bl, scal_, 1, done, brk); count_launches();
+  sqmr_scalar_beta_kernel<<<1, 32, 0, s_>>>(partial_, bl, scal_, 1, done, brk); count_launches();
   sqmr_update_q_kernel<T><<<bl, kThreads, 0, s_>>>(u, q, n_, scal_, done); count_launches();  // q = u (beta = 0)
   const int maxit = p_.max_inner;
   int it = 0;
@@ -928,13 +941,13 @@ int JdSolver::correction(int kc, double theta_hat, double rel_tol, int* its) {
       AJD_TRY(stencil_apply<T>(h_, (T)theta_hat, q, t, 1, s_));
       if (timed) AJD_CUDA(cudaEventRecord(evs_[2 * nevs_++ + 1], s_));
       multidot_kernel<T><<<bl, kThreads, 0, s_>>>(QtC, Cols<T>{}, q, t, n_, partial_, c + 1, done); count_launches();
-      reduce_partials_kernel<<<1, 128, 0, s_>>>(partial_, bl, c + 1, dots_, done); count_launches();
+      reduce_partials_kernel<<<1, kRedThreads, 0, s_>>>(partial_, bl, c + 1, dots_, done); count_launches();
       sqmr_update_r_kernel<T><<<bl, kThreads, 0, s_>>>(QtC, dots_, t, r, n_, scal_, partial_, done); count_launches();
-      sqmr_scalar_theta_kernel<<<1, 1, 0, s_>>>(partial_, bl, dots_, c, scal_, done, brk); count_launches();
+      sqmr_scalar_theta_kernel<<<1, 32, 0, s_>>>(partial_, bl, dots_, c, scal_, done, brk); count_launches();
       sqmr_update_dx_kernel<T><<<bl, kThreads, 0, s_>>>(d, x, q, n_, scal_, done); count_launches();
       sqmr_mark_done_kernel<<<1, 1, 0, s_>>>(done); count_launches();
       AJD_TRY(precond());
-      sqmr_scalar_beta_kernel<<<1, 1, 0, s_>>>(partial_, bl, scal_, 0, done, brk); count_launches();
+      sqmr_scalar_beta_kernel<<<1, 32, 0, s_>>>(partial_, bl, scal_, 0, done, brk); count_launches();
       sqmr_update_q_kernel<T><<<bl, kThreads, 0, s_>>>(u, q, n_, scal_, done); count_launches();
     }
     AJD_CHECK_LAUNCH();
@@ -1108,7 +1121,7 @@ int JdSolver::run(double* evals, double* evecs, jd_stats* st) {
     AJD_TRY(stencil_apply<double>(h_, 0.0, V_ + (int64_t)m * ld_, AV_ + (int64_t)m * ld_, 1, s_));
     AJD_TRY(dot_cols(Cols<double>{V_, ld_, m + 1}, Cols<double>{}, nullptr, AV_ + (int64_t)m * ld_, dots_));
     shifted_dots_kernel<<<nb_, kThreads, 0, s_>>>(V_, AV_, ld_, m + 1, sigma_, n, partial_); count_launches();
-    reduce_partials_kernel<<<1, 128, 0, s_>>>(partial_, nb_, m + 1, dots_ + (m + 1), nullptr); count_launches();
+    reduce_partials_kernel<<<1, kRedThreads, 0, s_>>>(partial_, nb_, m + 1, dots_ + (m + 1), nullptr); count_launches();
     double d[2 * kMaxM + 2];
     AJD_TRY(sync_read(dots_, 2 * (m + 1), d));
     for (int i = 0; i <= m; ++i) {
