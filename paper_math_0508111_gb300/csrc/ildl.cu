@@ -503,11 +503,19 @@ template <typename S, typename D>
 int upload(D** dst, const std::vector<S>& src, cudaStream_t st) {
   *dst = nullptr;
   if (src.empty()) return JD_OK;
-  std::vector<D> tmp(src.begin(), src.end());
-  cudaError_t e = cudaMalloc(dst, tmp.size() * sizeof(D));
+  const size_t n = src.size();
+  cudaError_t e = cudaMalloc(dst, n * sizeof(D));
   if (e != cudaSuccess) return fail(e == cudaErrorMemoryAllocation ? JD_ENOMEM : JD_EDEVICE, "ildl upload: %s", cudaGetErrorString(e));
-  AJD_CUDA(cudaMemcpyAsync(*dst, tmp.data(), tmp.size() * sizeof(D), cudaMemcpyHostToDevice, st));
-  AJD_CUDA(cudaStreamSynchronize(st));  // tmp is released on return
+  if constexpr (std::is_same<S, D>::value) {
+    AJD_CUDA(cudaMemcpyAsync(*dst, src.data(), n * sizeof(D), cudaMemcpyHostToDevice, st));
+    AJD_CUDA(cudaStreamSynchronize(st));
+  } else {
+    std::vector<D> tmp(n);
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < (int64_t)n; ++i) tmp[i] = D(src[i]);
+    AJD_CUDA(cudaMemcpyAsync(*dst, tmp.data(), n * sizeof(D), cudaMemcpyHostToDevice, st));
+    AJD_CUDA(cudaStreamSynchronize(st));  // tmp is released on return
+  }
   return JD_OK;
 }
 
@@ -741,14 +749,14 @@ int invert_dense_on_device(std::vector<double>& M, int m, cudaStream_t st) {
   return rc;
 }
 
-int ildl_upload_all(ildl_s* f, cudaStream_t st) {
+int ildl_upload_all(ildl_s* f, cudaStream_t st, int copies) {
   if (f->F.dense_is_matrix) {
     AJD_TRY(invert_dense_on_device(f->F.dense_inv, f->F.n_dense, st));
     f->F.dense_is_matrix = false;
   }
-  AJD_TRY(upload_factor<double>(f->F, f->d64, st));
-  AJD_TRY(upload_factor<float>(f->F, f->d32, st));
-  AJD_TRY(upload_factor<hi32_t>(f->F, f->dh, st));
+  if (copies & kCopyF64) AJD_TRY(upload_factor<double>(f->F, f->d64, st));
+  if (copies & kCopyF32) AJD_TRY(upload_factor<float>(f->F, f->d32, st));
+  if (copies & kCopyMixed) AJD_TRY(upload_factor<hi32_t>(f->F, f->dh, st));
   return JD_OK;
 }
 
@@ -920,7 +928,8 @@ extern "C" int ildl_matching(int n, const int64_t* rowptr, const int* col, const
 namespace ajd {
 // ildl_create with the device work (potential download, dense inverse,
 // upload) on `st`
-int ildl_create_on_stream(anderson_t h, double sigma, const ildl_params* p, ildl_t* out, cudaStream_t st) {
+int ildl_create_on_stream(anderson_t h, double sigma, const ildl_params* p, ildl_t* out, cudaStream_t st,
+                          int copies) {
   if (!out || !h) return fail(JD_EINVAL, "ildl_create: NULL argument");
   *out = nullptr;
   if (!std::isfinite(sigma)) return fail(JD_EINVAL, "ildl_create: sigma must be finite");
@@ -936,7 +945,7 @@ int ildl_create_on_stream(anderson_t h, double sigma, const ildl_params* p, ildl
     f->device = h->device;
     const auto t0 = std::chrono::steady_clock::now();
     int rc = build_ildl(A, prm, f->F, /*dense_on_host=*/false);
-    if (rc == JD_OK) rc = ildl_upload_all(f, st);
+    if (rc == JD_OK) rc = ildl_upload_all(f, st, copies);
     f->F.t_total_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     if (rc != JD_OK) {
       ildl_free_device(f);
@@ -952,7 +961,7 @@ int ildl_create_on_stream(anderson_t h, double sigma, const ildl_params* p, ildl
 }  // namespace ajd
 
 extern "C" int ildl_create(anderson_t h, double sigma, const ildl_params* p, ildl_t* out) {
-  return ajd::ildl_create_on_stream(h, sigma, p, out, 0);
+  return ajd::ildl_create_on_stream(h, sigma, p, out, 0, ajd::kCopyAll);
 }
 
 extern "C" int ildl_info(ildl_t f, ildl_info_t* info) {

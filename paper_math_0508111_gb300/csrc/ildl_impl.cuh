@@ -74,8 +74,18 @@ int ildl_apply_dev(const ildl_s* f, const T* b, T* out, cudaStream_t stream);
 // and sums.
 int ildl_apply_dev_mixed(const ildl_s* f, const double* b, double* out, cudaStream_t stream);
 
-// ildl_create with its device work on stream `st`.
-int ildl_create_on_stream(anderson_t h, double sigma, const ildl_params* p, ildl_t* out, cudaStream_t st);
+// Device copies of a factor: binary64, binary32, mixed (hi32_t values).
+constexpr int kCopyF64 = 1, kCopyF32 = 2, kCopyMixed = 4, kCopyAll = 7;
+
+// The copy a solve in `precision` (JD_FP64, JD_FP32, JD_MIXED) applies.
+inline int copy_for_precision(int precision) {
+  return precision == JD_FP32 ? kCopyF32 : precision == JD_MIXED ? kCopyMixed : kCopyF64;
+}
+
+// ildl_create with its device work on stream `st`, uploading only the
+// device copies in `copies`.
+int ildl_create_on_stream(anderson_t h, double sigma, const ildl_params* p, ildl_t* out, cudaStream_t st,
+                          int copies = kCopyAll);
 
 // JD_EDEVICE if a device-side wait of an apply timed out (reads a flag).
 int ildl_check_device_error(const ildl_s* f);

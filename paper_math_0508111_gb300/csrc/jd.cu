@@ -1362,7 +1362,8 @@ extern "C" int jd_solve(anderson_t h, double sigma, int k, double tol, const jd_
   ildl_t pc = prm.precond;
   bool own = false;
   if (!pc) {
-    AJD_TRY(ildl_create(h, sigma, &prm.ildl, &pc));
+    AJD_TRY(ildl_create_on_stream(h, sigma, &prm.ildl, &pc, reinterpret_cast<cudaStream_t>(stream),
+                                  copy_for_precision(prm.precision)));
     own = true;
   }
   if (st) {
@@ -1449,7 +1450,7 @@ extern "C" int jd_solve_batch(const anderson_t* hs, int nprob, const double* sig
       }
       const auto t0 = std::chrono::steady_clock::now();
       ildl_t pc = nullptr;
-      const int rc = ildl_create_on_stream(hs[i], sigma[i], &prm.ildl, &pc, st);
+      const int rc = ildl_create_on_stream(hs[i], sigma[i], &prm.ildl, &pc, st, copy_for_precision(prm.precision));
       const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
       std::lock_guard<std::mutex> lk(mu);
       pcs[i] = pc;

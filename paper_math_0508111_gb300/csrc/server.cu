@@ -49,7 +49,7 @@ size_t estimate_bytes(int L, int k, const jd_params& p) {
   const int jmin = p.jmin > 0 ? p.jmin : std::max(2 * kint, 10);
   const int jmax = std::min(64, p.jmax > 0 ? p.jmax : jmin + 15);
   const double per_row = 12.0                      // potential, binary64 + binary32
-                         + 160.0 + 56.0 * fill     // three device copies of the factor
+                         + 160.0 + 56.0 * fill     // device copies of the factor (bound: all three)
                          + 8.0 * (4.0 * jmax + kint + 4) + 8.0 * (2.0 * (kint + 1) + 8);  // solver
   return (size_t)(n * per_row + nd * nd * 16.0) + ((size_t)64 << 20);
 }
@@ -113,7 +113,8 @@ void build_loop(jd_server_s* S, int omp_threads) {
     anderson_t h = nullptr;
     ildl_t pc = nullptr;
     int rc = anderson_create(r->L, r->W, r->seed, r->bc, &h);
-    if (rc == JD_OK) rc = ildl_create_on_stream(h, r->sigma, &S->prm.solve.ildl, &pc, st);
+    if (rc == JD_OK)
+      rc = ildl_create_on_stream(h, r->sigma, &S->prm.solve.ildl, &pc, st, copy_for_precision(S->prm.solve.precision));
     const std::string msg = rc == JD_OK ? std::string() : std::string(jd_last_error());
     const double ms = std::chrono::duration<double, std::milli>(Clock::now() - t0).count();
     std::lock_guard<std::mutex> lk(S->mu);
