@@ -154,10 +154,11 @@ def apply_bytes(info, val, vec):
 
 
 def kernel_source_hash():
-    """SHA-1 of the apply kernel's source file: DRAM counters recorded for an
-    older source no longer describe the kernel that runs."""
+    """SHA-1 of the apply kernel's source (csrc/ildl_apply_kernel.cuh): DRAM
+    counters recorded for an older source no longer describe the kernel that
+    runs."""
     import hashlib
-    with open(os.path.join(ROOT, "paper_math_0508111_gb300", "csrc", "ildl.cu"), "rb") as f:
+    with open(os.path.join(ROOT, "paper_math_0508111_gb300", "csrc", "ildl_apply_kernel.cuh"), "rb") as f:
         return hashlib.sha1(f.read()).hexdigest()
 
 
