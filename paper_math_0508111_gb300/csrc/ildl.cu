@@ -470,7 +470,7 @@ extern "C" int ildl_params_default(ildl_params* p) {
   p->drop = -1.0;
   p->gamma = -1.0;
   p->max_levels = 256;
-  p->n_dense = 6000;
+  p->n_dense = 0;
   p->matching = -1;
   return JD_OK;
 }
@@ -481,8 +481,8 @@ static int check_params(const ildl_params* p, ildl_params& out) {
   if (!(out.kappa > 1.0)) return fail(JD_EINVAL, "ildl: kappa must be > 1");
   if (!std::isfinite(out.drop) && out.drop > 0) return fail(JD_EINVAL, "ildl: drop must be finite");
   if (out.gamma >= 1.0 || std::isnan(out.gamma)) return fail(JD_EINVAL, "ildl: gamma must be < 1");
-  if (out.max_levels < 1 || out.n_dense < 1 || out.n_dense > 8000)
-    return fail(JD_EINVAL, "ildl: max_levels >= 1 and 1 <= n_dense <= 8000 required");
+  if (out.max_levels < 1 || out.n_dense < 0 || out.n_dense > 8000)
+    return fail(JD_EINVAL, "ildl: max_levels >= 1 and 0 <= n_dense <= 8000 required");
   return JD_OK;
 }
 

@@ -566,7 +566,9 @@ int build_ildl(const SymCsr& A, const ildl_params& prm, HostFactor& F, bool dens
   // at n = 10^6 while 5/sqrt(n) keeps it)
   const double gamma = prm.gamma < 0.0 ? std::min(0.02, 5.0 / std::sqrt((double)n)) : prm.gamma;
   const int max_levels = prm.max_levels > 0 ? prm.max_levels : 64;
-  const int n_dense = prm.n_dense > 0 ? prm.n_dense : 1000;
+  // dense tail: the given size, else n/16 clamped to 1000..6000 (the
+  // O(n_dense^3) inversion stays small for small lattices)
+  const int n_dense = prm.n_dense > 0 ? prm.n_dense : std::max(1000, std::min(6000, n / 16));
   constexpr int kDenseHardMax = 8000;
 
   F = HostFactor();
