@@ -53,6 +53,9 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain binary64 comparison")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--workload", default="headline", choices=["headline", "batch"],
+                    help="headline: the L = 100 realisations; batch: the 256-problem batch through jd_server")
+    ap.add_argument("--batch-problems", type=int, default=256)
     ap.add_argument("--serve-requests", type=int, default=32,
                     help="requests of the serving sample (0 skips it)")
     ap.add_argument("--serve-rate", type=float, default=1.5, help="Poisson arrival rate of the serving sample, 1/s")
@@ -178,29 +181,20 @@ def measured_traffic(precision, info):
     return d["dram_bytes_per_apply"] * apply_bytes(info, *d["val_vec_bytes"]) / d["algorithmic_bytes_per_apply"]
 
 
-def serving_sample(ajd, args, precision):
-    """Requests arriving as a Poisson stream (driver seed 7): L uniform in
-    {16..serve_lmax}, W uniform in [8, 24], sigma uniform in [-2, 2], k in
-    {1, 5, 10}, request r on disorder seed 10^6 + r, periodic, tol as the
-    headline.  Each is submitted to a jd_server at its arrival time and
-    polled until done; reports eigenpairs/s over the whole sample and the
-    latency percentiles (submission to completion)."""
+def run_requests(ajd, args, precision, reqs, slots, setup_threads):
+    """Submit each request to a jd_server at its arrival time ("t", seconds
+    from the start) and poll until all are done.  Returns eigenpairs/s over
+    the whole run and the latency percentiles (submission to completion)."""
     import numpy as np
-    g = np.random.default_rng(7)
-    reqs, t = [], 0.0
-    for r in range(args.serve_requests):
-        t += g.exponential(1.0 / args.serve_rate)
-        reqs.append((t, int(g.integers(16, args.serve_lmax + 1)), float(g.uniform(8.0, 24.0)), 10 ** 6 + r,
-                     float(g.uniform(-2.0, 2.0)), int(g.choice([1, 5, 10]))))
     lat, pairs, failed = [], 0, 0
-    with ajd.Server(slots=args.serve_slots, setup_threads=args.serve_setup_threads, precision=precision) as srv:
+    with ajd.Server(slots=slots, setup_threads=setup_threads, precision=precision) as srv:
         start = time.perf_counter()
         pending, i = {}, 0
         while i < len(reqs) or pending:
             now = time.perf_counter() - start
-            while i < len(reqs) and reqs[i][0] <= now:
-                _, L, W, seed, sigma, k = reqs[i]
-                pending[srv.submit(L, W, seed, sigma, k, args.tol)] = k
+            while i < len(reqs) and reqs[i]["t"] <= now:
+                r = reqs[i]
+                pending[srv.submit(r["L"], r["W"], r["seed"], r["sigma"], r["k"], args.tol, bc=r["bc"])] = r["k"]
                 i += 1
             for tk in list(pending):
                 out = srv.poll(tk, raise_on_error=False)
@@ -214,13 +208,49 @@ def serving_sample(ajd, args, precision):
         elapsed = time.perf_counter() - start
         info = srv.info()
     lat = np.sort(np.array(lat))
-    return {"value": pairs / elapsed, "unit": UNIT, "requests": len(reqs), "failed": failed,
+    return {"value": pairs / elapsed, "unit": UNIT, "requests": len(reqs), "failed": failed, "eigenpairs": pairs,
             "p50_latency_ms": float(np.percentile(lat, 50)), "p99_latency_ms": float(np.percentile(lat, 99)),
             "max_latency_ms": float(lat[-1]), "seconds": elapsed, "peak_concurrent_solves": info["peak_solving"],
-            "slots": args.serve_slots, "setup_threads": args.serve_setup_threads,
-            "sample": "%d Poisson arrivals at %.2f/s, L~U{16..%d}, W~U[8,24], sigma~U[-2,2], k in {1,5,10}, seeds "
-                      "1e6+r, tol %g (a bounded sample of the 4096-request L<=120 stream)"
-                      % (len(reqs), args.serve_rate, args.serve_lmax, args.tol)}
+            "slots": slots, "setup_threads": setup_threads}
+
+
+def serving_sample(ajd, args, precision):
+    """The serving workload (workloads.serve_recipe: Poisson arrivals, L
+    uniform in 16..serve_lmax, W in [8, 24], sigma in [-2, 2], k in
+    {1, 5, 10}, request r on disorder seed 10^6 + r, driver seed 7), bounded
+    to serve_requests requests."""
+    import workloads
+    reqs = workloads.serve_recipe(args.serve_requests, args.serve_rate, seed=7, lmax=args.serve_lmax)
+    out = run_requests(ajd, args, precision, reqs, args.serve_slots, args.serve_setup_threads)
+    out["sample"] = ("%d Poisson arrivals at %.2f/s, L~U{16..%d}, W~U[8,24], sigma~U[-2,2], k in {1,5,10}, seeds "
+                     "1e6+r, tol %g (a bounded sample of the 4096-request L<=120 stream)"
+                     % (len(reqs), args.serve_rate, args.serve_lmax, args.tol))
+    return out
+
+
+def run_batch_workload(args):
+    """--workload batch: the 256-problem batch (workloads.batch_recipe: L in
+    {20,30,40,50}, W in {12,16.5,20}, sigma in {-1,0,1}, k = 5, seeds 1000 + p)
+    submitted at once to a jd_server; one JSON line."""
+    import torch
+    import paper_math_0508111_gb300 as ajd
+    import workloads
+    head = {"mixed": ajd.JD_MIXED, "fp32": ajd.JD_FP32, "fp64": ajd.JD_FP64}[args.precision]
+    reqs = [dict(r, t=0.0) for r in workloads.batch_recipe(args.batch_problems, seed=42)]
+    warm = [dict(r, t=0.0, seed=r["seed"] + 10 ** 5) for r in workloads.batch_recipe(max(args.warmup, 1), seed=43)]
+    run_requests(ajd, args, head, warm, args.serve_slots, args.serve_setup_threads)
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
+    out = run_requests(ajd, args, head, reqs, args.serve_slots, args.serve_setup_threads)
+    clocks = sampler.stop()
+    line = {"metric": "eigenpairs/s, batch of %d Anderson problems (L in {20,30,40,50}), resid<=%g" % (len(reqs), args.tol),
+            "value": out["value"], "unit": UNIT, "n_gpus": 1, "steps": 1, "warmup": len(warm),
+            "ms_per_step": 1e3 * out["seconds"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": {"mixed": "f32+f64", "fp32": "f32+f64", "fp64": "f64"}[args.precision], "data": "synthetic",
+            "config": {"workload": "batch-%d-L20..50-W12..20-sigma-1..1-k5" % len(reqs), "precision": args.precision,
+                       "submission": "all requests at t = 0 to one jd_server"},
+            "batch": out, "clocks": clocks}
+    print(json.dumps(line), flush=True)
 
 
 def cpu_baseline(W, sigma, k, L_sample=30):
@@ -270,6 +300,9 @@ def main():
     rank, world, local = dist_env()
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.workload == "batch":
+        run_batch_workload(args)
         return
     import numpy as np
     import torch

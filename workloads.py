@@ -51,13 +51,14 @@ def batch_recipe(nprob=256, seed=42):
                  seed=1000 + p, bc=0) for p in range(nprob)]
 
 
-def serve_recipe(nreq=4096, rate_per_s=1.0, seed=7):
+def serve_recipe(nreq=4096, rate_per_s=1.0, seed=7, lmax=120):
     """Request stream of the serving workload: dicts with arrival time
-    (seconds, Poisson process of the given rate), L, W, sigma, k, seed."""
+    (seconds, Poisson process of the given rate), L, W, sigma, k, seed.
+    ``lmax`` < 120 gives a bounded sample (L uniform in 16..lmax)."""
     rng = np.random.default_rng(seed)
     gaps = rng.exponential(1.0 / rate_per_s, size=nreq)
     t = np.cumsum(gaps)
-    Ls = rng.integers(16, 121, size=nreq)
+    Ls = rng.integers(16, lmax + 1, size=nreq)
     Ws = rng.uniform(8.0, 24.0, size=nreq)
     ss = rng.uniform(-2.0, 2.0, size=nreq)
     ks = rng.choice([1, 5, 10], size=nreq)
