@@ -160,6 +160,170 @@ stencil_kernel(const T* __restrict__ eps, const T* __restrict__ xin, T* __restri
   }
 }
 
+// Plane-tile stencil for rows whose length in bytes is a multiple of 16 (L a
+// multiple of 4 in binary32, of 2 in binary64) and 16-byte aligned vectors.
+// A CTA of 8 warps owns 8 consecutive y-rows of one x-segment (32 lanes x
+// VW sites, VW = 16 B / element) and walks a chunk of z-planes.  Per step:
+// every lane loads its VW sites with one 16-byte load (plane z+2 and the
+// potential of plane z+1 are in flight while plane z is computed); the
+// segment's 8 rows and the two halo rows y0-1, y0+8 pass through a
+// shared-memory plane tile for the y-neighbours; x-neighbours come from the
+// neighbouring lanes by shuffles (global loads only at segment ends); z-
+// neighbours stay in registers.  DRAM traffic per site: x once (plus the
+// halo rows, 2/8, mostly L2 hits), the potential once, y once.
+template <typename T>
+struct Vec16;
+template <>
+struct Vec16<float> {
+  using type = float4;
+  static constexpr int n = 4;
+};
+template <>
+struct Vec16<double> {
+  using type = double2;
+  static constexpr int n = 2;
+};
+
+template <typename T>
+__device__ __forceinline__ void vload(const T* __restrict__ p, bool ok, T (&v)[Vec16<T>::n]) {
+  using V = typename Vec16<T>::type;
+  if (ok) {
+    const V q = __ldg(reinterpret_cast<const V*>(p));
+    const T* e = reinterpret_cast<const T*>(&q);
+#pragma unroll
+    for (int i = 0; i < Vec16<T>::n; ++i) v[i] = e[i];
+  } else {
+#pragma unroll
+    for (int i = 0; i < Vec16<T>::n; ++i) v[i] = T(0);
+  }
+}
+
+constexpr int kTileRows = 8;
+
+template <typename T>
+__global__ void __launch_bounds__(32 * kTileRows)
+stencil_tile_kernel(const T* __restrict__ eps, const T* __restrict__ xin, T* __restrict__ yout, int L, int nseg,
+                    int zchunk, T shift, T hop, int periodic_i, int64_t n) {
+  constexpr int VW = Vec16<T>::n;
+  using V = typename Vec16<T>::type;
+  __shared__ V tile[kTileRows + 2][32];
+  const bool periodic = periodic_i != 0;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int seg = blockIdx.x % nseg, ytile = blockIdx.x / nseg;
+  const int y = ytile * kTileRows + warp;
+  const int xs = seg * 32 * VW + VW * lane;  // first site of this lane
+  const bool lane_ok = xs < L;               // L is a multiple of VW
+  const bool own_ok = lane_ok && y < L;      // rows this warp writes
+  // rows of the last tile beyond L hold the wrapped rows (periodic) or zeros,
+  // so that row L-1 finds its y+1 neighbour in the tile
+  const int yl = y < L ? y : (periodic ? y - L : -1);
+  const bool load_ok = lane_ok && yl >= 0;
+  const int z0 = blockIdx.y * zchunk;
+  const int z1 = min(z0 + zchunk, L);
+  const int64_t LL = (int64_t)L * L;
+  const T* __restrict__ x = xin + (int64_t)blockIdx.z * n;
+  T* __restrict__ yo = yout + (int64_t)blockIdx.z * n;
+  // halo rows of this tile (loaded by warps 0 and kTileRows-1)
+  int yh = -1;
+  bool halo_ok = false;
+  if (warp == 0 || warp == kTileRows - 1) {
+    yh = warp == 0 ? ytile * kTileRows - 1 : ytile * kTileRows + kTileRows;
+    halo_ok = periodic || (yh >= 0 && yh < L);
+    if (yh < 0) yh += L;
+    if (yh >= L) yh -= L;
+    halo_ok = halo_ok && lane_ok && yh < L;
+  }
+  auto plane_ok = [&](int z, int& zz) {
+    zz = z;
+    if (zz < 0) zz += L;
+    if (zz >= L) zz -= L;
+    return periodic || (z >= 0 && z < L);
+  };
+  const bool last_lane = xs + VW >= L || lane == 31;  // its right neighbour lies in another segment
+  T xm[VW], xc[VW], xp[VW], xq[VW], ec[VW], en[VW], hc[VW], hn[VW];
+  {
+    int za, zb;
+    const bool oa = plane_ok(z0 - 1, za), ob = plane_ok(z0 + 1, zb);
+    const int64_t r = (int64_t)(load_ok ? yl : 0) * L + xs;
+    vload(x + (int64_t)za * LL + r, load_ok && oa, xm);
+    vload(x + (int64_t)z0 * LL + r, load_ok, xc);
+    vload(x + (int64_t)zb * LL + r, load_ok && ob, xp);
+    vload(eps + (int64_t)z0 * LL + r, own_ok, ec);
+    vload(x + (int64_t)z0 * LL + (int64_t)yh * L + xs, halo_ok, hc);
+  }
+  for (int z = z0; z < z1; ++z) {
+    // loads for the next steps: x of plane z+2, eps and halo of plane z+1
+    int zq, ze;
+    const bool oq = plane_ok(z + 2, zq), oe = plane_ok(z + 1, ze);
+    const bool more = z + 1 < z1;
+    const int64_t r = (int64_t)(load_ok ? yl : 0) * L + xs;
+    vload(x + (int64_t)zq * LL + r, load_ok && oq && z + 2 <= z1, xq);
+    vload(eps + (int64_t)ze * LL + r, own_ok && more, en);
+    vload(x + (int64_t)ze * LL + (int64_t)yh * L + xs, halo_ok && more, hn);
+    // x-neighbours at the segment ends (global, usually L1/L2 hits)
+    const int64_t row = (int64_t)z * LL + (int64_t)y * L;
+    T left_g = T(0), right_g = T(0);
+    if (own_ok && lane == 0) {
+      const int xl = xs - 1;
+      if (xl >= 0) left_g = x[row + xl];
+      else if (periodic) left_g = x[row + L - 1];
+    }
+    if (own_ok && last_lane) {
+      const int xr = xs + VW;
+      if (xr < L) right_g = x[row + xr];
+      else if (periodic) right_g = x[row];
+    }
+    // y-neighbours through the plane tile
+    __syncthreads();  // the previous step's readers are done
+    {
+      V v;
+      T* e = reinterpret_cast<T*>(&v);
+#pragma unroll
+      for (int i = 0; i < VW; ++i) e[i] = xc[i];
+      tile[warp + 1][lane] = v;
+      if (warp == 0 || warp == kTileRows - 1) {
+#pragma unroll
+        for (int i = 0; i < VW; ++i) e[i] = hc[i];
+        tile[warp == 0 ? 0 : kTileRows + 1][lane] = v;
+      }
+    }
+    __syncthreads();
+    const V vm = tile[warp][lane], vp = tile[warp + 2][lane];
+    const T* ym = reinterpret_cast<const T*>(&vm);
+    const T* yp = reinterpret_cast<const T*>(&vp);
+    // rows y-1 / y+1 outside a hard wall are zero
+    const bool okym = periodic || y - 1 >= 0;
+    const bool okyp = periodic || y + 1 < L;
+    T left = __shfl_up_sync(0xffffffffu, xc[VW - 1], 1);
+    T right = __shfl_down_sync(0xffffffffu, xc[0], 1);
+    if (lane == 0) left = left_g;
+    if (last_lane) right = right_g;
+    if (own_ok) {
+      T out[VW];
+#pragma unroll
+      for (int i = 0; i < VW; ++i) {
+        const T l = i == 0 ? left : xc[i - 1];
+        const T rr = i == VW - 1 ? right : xc[i + 1];
+        const T nb = (l + rr) + ((okym ? ym[i] : T(0)) + (okyp ? yp[i] : T(0))) + (xm[i] + xp[i]);
+        out[i] = (ec[i] - shift) * xc[i] + hop * nb;
+      }
+      V o;
+      T* oe = reinterpret_cast<T*>(&o);
+#pragma unroll
+      for (int i = 0; i < VW; ++i) oe[i] = out[i];
+      *reinterpret_cast<V*>(yo + row + xs) = o;
+    }
+#pragma unroll
+    for (int i = 0; i < VW; ++i) {
+      xm[i] = xc[i];
+      xc[i] = xp[i];
+      xp[i] = xq[i];
+      ec[i] = en[i];
+      hc[i] = hn[i];
+    }
+  }
+}
+
 }  // namespace
 
 template <typename T, int V>
@@ -182,6 +346,23 @@ static void launch_stencil(const T* eps, const T* x, T* y, int L, int m, T shift
 }
 
 template <typename T>
+static void launch_stencil_tile(const T* eps, const T* x, T* y, int L, int m, T shift, T hop, int periodic,
+                                int64_t n, cudaStream_t stream) {
+  constexpr int VW = Vec16<T>::n;
+  const int nseg = ceil_div(L, 32 * VW);
+  const int bx = nseg * ceil_div(L, kTileRows);
+  // z-chunks: enough CTAs for several per SM, each chunk at least 8 planes
+  const int target = 8 * sm_count();
+  int nchunk = ceil_div(target, (int64_t)bx * m);
+  nchunk = std::max(1, std::min(nchunk, std::max(1, L / 8)));
+  const int zchunk = ceil_div(L, nchunk);
+  nchunk = ceil_div(L, zchunk);
+  dim3 grid(bx, nchunk, m);
+  stencil_tile_kernel<T><<<grid, 32 * kTileRows, 0, stream>>>(eps, x, y, L, nseg, zchunk, shift, hop, periodic, n);
+  count_launches();
+}
+
+template <typename T>
 int stencil_apply(const anderson_s* h, T shift, const T* x, T* y, int m, cudaStream_t stream) {
   if (m == 0) return JD_OK;
   if (m > 65535) return fail(JD_EINVAL, "anderson_apply: at most 65535 vectors per call");
@@ -190,6 +371,15 @@ int stencil_apply(const anderson_s* h, T shift, const T* x, T* y, int m, cudaStr
   else eps = reinterpret_cast<const T*>(h->eps32);
   const int L = h->L, per = h->bc == JD_PERIODIC ? 1 : 0;
   const T hop = (T)h->hop;
+  // 16-byte rows and 16-byte aligned vectors: the plane-tile kernel
+  constexpr int VW = Vec16<T>::n;
+  const bool aligned = ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(y) |
+                         reinterpret_cast<uintptr_t>(eps)) % 16) == 0;
+  if (L % VW == 0 && aligned && L >= 8) {
+    launch_stencil_tile<T>(eps, x, y, L, m, shift, hop, per, h->n, stream);
+    AJD_CHECK_LAUNCH();
+    return JD_OK;
+  }
   if (L <= 32) launch_stencil<T, 1>(eps, x, y, L, m, shift, hop, per, h->n, stream);
   else if (L <= 64) launch_stencil<T, 2>(eps, x, y, L, m, shift, hop, per, h->n, stream);
   else if (L <= 96) launch_stencil<T, 3>(eps, x, y, L, m, shift, hop, per, h->n, stream);

@@ -50,7 +50,10 @@ def _check_stencil(ajd, L, W, seed, bc, shift, m, dtype):
         assert err <= tol, (L, bc, err)
 
 
-@pytest.mark.parametrize("L,bc", [(3, 0), (4, 0), (5, 1), (10, 0), (10, 1), (33, 0), (37, 1), (64, 0)])
+@pytest.mark.parametrize("L,bc", [(3, 0), (4, 0), (5, 1), (10, 0), (10, 1), (33, 0), (37, 1), (64, 0),
+                                  # plane-tile kernel: 16-byte rows, tiles past L (L % 8 != 0), hard walls,
+                                  # several x-segments per row (L > 128 binary32, > 64 binary64)
+                                  (8, 0), (12, 1), (20, 1), (24, 0), (132, 1), (136, 0)])
 @pytest.mark.parametrize("dtype_name", ["float64", "float32"])
 def test_stencil_matches_oracle(ajd, L, bc, dtype_name):
     _check_stencil(ajd, L, 16.5, 3, bc, 0.37, 1, getattr(torch, dtype_name))
@@ -62,6 +65,8 @@ def test_stencil_block_and_edge_sizes(ajd, dtype_name):
     _check_stencil(ajd, 1, 16.5, 3, 1, 0.0, 2, dt)  # single site, no neighbours
     _check_stencil(ajd, 2, 16.5, 3, 1, -1.0, 3, dt)
     _check_stencil(ajd, 21, 12.0, 4, 0, 1.5, 4, dt)
+    _check_stencil(ajd, 12, 12.0, 4, 1, 0.7, 3, dt)  # several vectors on the plane-tile kernel
+    _check_stencil(ajd, 16, 12.0, 5, 0, -0.3, 2, dt)
 
 
 def test_stencil_full_size_L100(ajd):
