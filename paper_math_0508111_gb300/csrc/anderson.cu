@@ -351,7 +351,9 @@ static void launch_stencil_tile(const T* eps, const T* x, T* y, int L, int m, T 
   constexpr int VW = Vec16<T>::n;
   const int nseg = ceil_div(L, 32 * VW);
   const int bx = nseg * ceil_div(L, kTileRows);
-  // z-chunks: enough CTAs for several per SM, each chunk at least 8 planes
+  // z-chunks: about eight CTAs per SM (measured at L = 256 against 2, 4 and
+  // 16 per SM and 4- or 16-row tiles: 4.4 TB/s versus 2.7-4.2), each chunk
+  // at least 8 planes
   const int target = 8 * sm_count();
   int nchunk = ceil_div(target, (int64_t)bx * m);
   nchunk = std::max(1, std::min(nchunk, std::max(1, L / 8)));
@@ -375,7 +377,7 @@ int stencil_apply(const anderson_s* h, T shift, const T* x, T* y, int m, cudaStr
   constexpr int VW = Vec16<T>::n;
   const bool aligned = ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(y) |
                          reinterpret_cast<uintptr_t>(eps)) % 16) == 0;
-  if (L % VW == 0 && aligned && L >= 8) {
+  if (L % VW == 0 && aligned && L >= 16) {
     launch_stencil_tile<T>(eps, x, y, L, m, shift, hop, per, h->n, stream);
     AJD_CHECK_LAUNCH();
     return JD_OK;
