@@ -111,7 +111,7 @@ int max_product_matching(const SymCsr& A, std::vector<int>& match_col, std::vect
     logmax[i] = log_pos(r);
   }
   // cost of entry p (row i, column col[p]); +inf for explicit zeros
-  std::vector<double> cost(A.val.size()), loga(A.val.size());
+  dvec<double> cost(A.val.size()), loga(A.val.size());  // filled (first touched) in parallel below
 #pragma omp parallel for schedule(static)
   for (int i = 0; i < n; ++i)
     for (int64_t p = A.ptr[i]; p < A.ptr[i + 1]; ++p) {
@@ -464,10 +464,9 @@ void stable_scatter(int64_t N, int nb, Key key, std::vector<int64_t>& ptr, Emit 
 // 0..nc-1): row c of the result lists (r, val) for every entry (r, c), in
 // increasing r; entries with keep(r, c) false are left out.  Rows are cut
 // into chunks of about equal entry counts.
-template <class Keep>
-void stable_transpose(int nr, int nc, const std::vector<int64_t>& ptr, const std::vector<int>& col,
-                      const std::vector<double>& val, Keep keep, std::vector<int64_t>& tptr, std::vector<int>& tcol,
-                      std::vector<double>& tval) {
+template <class Keep, class ColIn, class ValIn, class ColOut, class ValOut>
+void stable_transpose(int nr, int nc, const std::vector<int64_t>& ptr, const ColIn& col, const ValIn& val, Keep keep,
+                      std::vector<int64_t>& tptr, ColOut& tcol, ValOut& tval) {
   const int64_t nnz = ptr[nr];
   const int T = (int)std::max<int64_t>(1, std::min<int64_t>(omp_get_max_threads(), nnz / 16384));
   std::vector<int> rcut(T + 1, nr);
@@ -789,8 +788,8 @@ int build_ildl(const SymCsr& A, const ildl_params& prm, HostFactor& F, bool dens
     // 6. L_F = F D_B^{-1} row by row (rows: C nodes), dropped at tau.
     // Entries: (C row, B node, value) with the B node's block.
     std::vector<int64_t> lptr(mc_n + 1, 0);
-    std::vector<int> lnode;    // B node (local index)
-    std::vector<double> lval;
+    dvec<int> lnode;    // B node (local index)
+    dvec<double> lval;
     const int nchunk = std::max(1, std::min(mc_n, 8 * omp_get_max_threads()));
     {
       std::vector<std::vector<int>> cn(nchunk);
@@ -835,11 +834,15 @@ int build_ildl(const SymCsr& A, const ildl_params& prm, HostFactor& F, bool dens
         }
       }
       for (int r = 0; r < mc_n; ++r) lptr[r + 1] = lptr[r] + rowcnt[r];
-      lnode.reserve(lptr[mc_n]);
-      lval.reserve(lptr[mc_n]);
+      // chunks hold consecutive rows, so chunk ch starts at the row pointer of
+      // its first row; copied in parallel
+      lnode.resize(lptr[mc_n]);
+      lval.resize(lptr[mc_n]);
+#pragma omp parallel for schedule(dynamic, 1)
       for (int ch = 0; ch < nchunk; ++ch) {
-        lnode.insert(lnode.end(), cn[ch].begin(), cn[ch].end());
-        lval.insert(lval.end(), cv[ch].begin(), cv[ch].end());
+        const int r0 = (int)((int64_t)mc_n * ch / nchunk);
+        std::copy(cn[ch].begin(), cn[ch].end(), lnode.begin() + lptr[r0]);
+        std::copy(cv[ch].begin(), cv[ch].end(), lval.begin() + lptr[r0]);
       }
     }
     {
@@ -974,11 +977,13 @@ int build_ildl(const SymCsr& A, const ildl_params& prm, HostFactor& F, bool dens
         }
       }
       for (int r = 0; r < mc_n; ++r) U.ptr[r + 1] = U.ptr[r] + rowcnt[r];
-      U.col.reserve(U.ptr[mc_n]);
-      U.val.reserve(U.ptr[mc_n]);
+      U.col.resize(U.ptr[mc_n]);
+      U.val.resize(U.ptr[mc_n]);
+#pragma omp parallel for schedule(dynamic, 1)
       for (int ch = 0; ch < nchunk; ++ch) {
-        U.col.insert(U.col.end(), ucol[ch].begin(), ucol[ch].end());
-        U.val.insert(U.val.end(), uval[ch].begin(), uval[ch].end());
+        const int r0 = (int)((int64_t)mc_n * ch / nchunk);
+        std::copy(ucol[ch].begin(), ucol[ch].end(), U.col.begin() + U.ptr[r0]);
+        std::copy(uval[ch].begin(), uval[ch].end(), U.val.begin() + U.ptr[r0]);
       }
     }
     const double ts_num = ms_since(t_schur) - ts_rec;
@@ -989,8 +994,8 @@ int build_ildl(const SymCsr& A, const ildl_params& prm, HostFactor& F, bool dens
     Sn.n = mc_n;
     {
       std::vector<int64_t> lptr2;
-      std::vector<int> lcol2;
-      std::vector<double> lval2;
+      dvec<int> lcol2;
+      dvec<double> lval2;
       stable_transpose(mc_n, mc_n, U.ptr, U.col, U.val, [](int r, int c) { return c != r; }, lptr2, lcol2, lval2);
       Sn.ptr.assign(mc_n + 1, 0);
       for (int r = 0; r < mc_n; ++r) Sn.ptr[r + 1] = Sn.ptr[r] + (lptr2[r + 1] - lptr2[r]) + (U.ptr[r + 1] - U.ptr[r]);

@@ -2,19 +2,45 @@
 // (Sections 5 and 6).  Pure C++ (no CUDA), so it also runs without a GPU.
 #pragma once
 #include <cstdint>
+#include <memory>
+#include <utility>
 #include <vector>
 
 #include "anderson_jd.h"
 
 namespace ajd {
 
+// std::allocator that leaves elements default-initialised (no zero fill on
+// resize): the large per-level arrays of the setup are then first touched
+// by the parallel loops that fill them, not by a serial memset.
+template <class T>
+struct default_init_allocator : std::allocator<T> {
+  template <class U>
+  struct rebind {
+    using other = default_init_allocator<U>;
+  };
+  default_init_allocator() = default;
+  template <class U>
+  default_init_allocator(const default_init_allocator<U>&) noexcept {}
+  template <class U>
+  void construct(U* p) noexcept {
+    ::new (static_cast<void*>(p)) U;
+  }
+  template <class U, class... Args>
+  void construct(U* p, Args&&... args) {
+    ::new (static_cast<void*>(p)) U(std::forward<Args>(args)...);
+  }
+};
+template <class T>
+using dvec = std::vector<T, default_init_allocator<T>>;
+
 // Symmetric sparse matrix, both triangles stored, rows sorted by column,
 // diagonal entry always present (possibly zero).
 struct SymCsr {
   int n = 0;
   std::vector<int64_t> ptr;
-  std::vector<int> col;
-  std::vector<double> val;
+  dvec<int> col;
+  dvec<double> val;
 };
 
 // The factor in global (level-ordered) position space:
