@@ -68,6 +68,38 @@ def assemble(L, eps, bc=PERIODIC, t=-1.0, shift=0.0):
     return sp.csr_matrix((vals, (rows, cols)), shape=(n, n))
 
 
+def assemble_offdiag(L, diag, hop, bc=PERIODIC, shift=0.0):
+    """Sparse CSR matrix A - shift*I of the off-diagonal Anderson model
+    (Section 7): diagonal ``diag`` (a scalar or an array of n values) and the
+    hopping hop[s, d] on the bond from site s to its +x/+y/+z neighbour
+    (d = 0/1/2), the same graph as Eq. (1).  Hard walls drop the bonds that
+    would leave the cube (their hop entries are not used).  FP64."""
+    n = L ** 3
+    if bc == PERIODIC and L < 3:
+        raise ValueError("periodic lattice needs L >= 3")
+    hop = np.asarray(hop, dtype=np.float64)
+    assert hop.shape == (n, 3)
+    d_all = np.broadcast_to(np.asarray(diag, dtype=np.float64), (n,))
+    idx, x, y, z = _coords(L)
+    rows, cols, vals = [np.arange(n)], [np.arange(n)], [d_all - shift]
+    for d in range(3):
+        c = (x, y, z)[d]
+        keep = c < L - 1 if bc == HARDWALL else np.ones(n, dtype=bool)
+        step = L ** d
+        nb = np.where(c == L - 1, idx - (L - 1) * step, idx + step)  # the +d neighbour, wrapped
+        a, b, t = idx[keep], nb[keep], hop[keep, d]
+        rows += [a, b]
+        cols += [b, a]
+        vals += [t, t]
+    return sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=(n, n))
+
+
+def norm_bound_offdiag(diag, hop):
+    """Gershgorin bound max|diag| + 6 max|t| of the off-diagonal model (the
+    relative tolerances use it as ||A||; with t = -1 it is norm_bound)."""
+    return float(np.max(np.abs(diag))) + 6.0 * float(np.max(np.abs(hop)))
+
+
 def dense(L, eps, bc=PERIODIC, t=-1.0, shift=0.0):
     return assemble(L, eps, bc, t, shift).toarray()
 

@@ -52,3 +52,15 @@ def potential(L, W, seed):
     n = int(L) ** 3
     u = uniform01(seed, n)
     return np.float64(W) * (u - 0.5)
+
+
+def hoppings(L, seed, width=1.0):
+    """Random hopping amplitudes of the off-diagonal Anderson model (Section
+    7, Table 6: the randomness moved from the diagonal to the off-diagonal
+    entries, uniform on [-1/2, 1/2] for width 1).  Reading: the bond from
+    site s to its +x, +y, +z neighbour (d = 0, 1, 2) gets
+    t[s, d] = width * (u_{3s+d} - 1/2), u the same SplitMix64 stream as
+    `potential`, indexed 3s + d.  FP64, shape (L**3, 3)."""
+    n = int(L) ** 3
+    u = uniform01(seed, 3 * n)
+    return (np.float64(width) * (u - 0.5)).reshape(n, 3)

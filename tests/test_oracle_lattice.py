@@ -96,3 +96,58 @@ def test_matvec_block_and_shift():
     Y = lattice.matvec(L, eps, X, shift=0.7)
     D = lattice.dense(L, eps) - 0.7 * np.eye(L ** 3)
     assert np.allclose(Y, D @ X, atol=1e-13)
+
+
+# ---- off-diagonal Anderson model (Section 7, Table 6) ----
+
+@pytest.mark.parametrize("L,bc", [(3, 0), (4, 1), (5, 0), (6, 1)])
+def test_offdiag_constant_hopping_is_eq1(L, bc):
+    """Equal hopping on every bond and the potential on the diagonal give
+    exactly the matrix of Eq. (1) (assemble, pinned by the closed form)."""
+    eps = rng.potential(L, 16.5, 4)
+    for t in (-1.0, 0.7):
+        A = lattice.assemble(L, eps, bc, t=t, shift=0.3)
+        B = lattice.assemble_offdiag(L, eps, np.full((L ** 3, 3), t), bc, shift=0.3)
+        assert abs(A - B).max() == 0.0
+
+
+def test_offdiag_hard_wall_ignores_outer_bonds():
+    L = 5
+    hop = rng.hoppings(L, 3)
+    A = lattice.assemble_offdiag(L, 1.28, hop, lattice.HARDWALL)
+    _, x, y, z = np.arange(L ** 3), *(np.arange(L ** 3) % L, (np.arange(L ** 3) // L) % L, np.arange(L ** 3) // L ** 2)
+    hop2 = hop.copy()
+    hop2[x == L - 1, 0] = 99.0
+    hop2[y == L - 1, 1] = 99.0
+    hop2[z == L - 1, 2] = 99.0
+    assert abs(A - lattice.assemble_offdiag(L, 1.28, hop2, lattice.HARDWALL)).max() == 0.0
+    # ... while a periodic lattice uses them
+    assert abs(lattice.assemble_offdiag(L, 1.28, hop, 0) - lattice.assemble_offdiag(L, 1.28, hop2, 0)).max() > 1.0
+
+
+@pytest.mark.parametrize("L,bc", [(4, 0), (5, 1)])
+def test_offdiag_invariants(L, bc):
+    """Symmetry, trace, Frobenius norm (every kept bond twice) and the
+    Gershgorin bound of the spectrum."""
+    n = L ** 3
+    hop = rng.hoppings(L, 9)
+    A = lattice.assemble_offdiag(L, 1.28, hop, bc)
+    Ad = A.toarray()
+    assert np.array_equal(Ad, Ad.T)
+    assert np.trace(Ad) == pytest.approx(1.28 * n)
+    nbonds = 3 * n if bc == 0 else 3 * L * L * (L - 1)
+    assert A.nnz == n + 2 * nbonds
+    off = Ad - np.diag(np.diag(Ad))
+    assert np.sum(off ** 2) == pytest.approx(2 * (np.sum(hop ** 2) if bc == 0 else np.sum(off[np.triu_indices(n, 1)] ** 2)))
+    w = np.linalg.eigvalsh(Ad)
+    r = lattice.norm_bound_offdiag(1.28, hop)
+    assert w.min() >= 1.28 - 6 * np.abs(hop).max() - 1e-12 and w.max() <= r + 1e-12
+
+
+def test_hoppings_range_and_stream():
+    L = 6
+    h = rng.hoppings(L, 11, width=1.0)
+    assert h.shape == (L ** 3, 3)
+    assert h.min() >= -0.5 and h.max() < 0.5
+    # the same stream as the potential, read at 3s + d
+    assert np.array_equal(h.ravel(), rng.uniform01(11, 3 * L ** 3) - 0.5)
