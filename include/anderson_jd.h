@@ -103,6 +103,27 @@ int anderson_create(int L, double W, uint64_t seed, int bc, anderson_t* out);
  */
 int anderson_create_from_potential(int L, const double* eps_host, int bc, anderson_t* out);
 
+/*
+ * anderson_create_offdiag -- the off-diagonal ("inverse") Anderson model of
+ * Section 7 (Table 6): the same nearest-neighbour graph as Eq. (1), a
+ * constant diagonal `diag` (1.28 at the transition the paper studies) and
+ * random hopping on every bond: the bond from site s to its +x, +y, +z
+ * neighbour (d = 0, 1, 2) gets t = width * (u_{3s+d} - 1/2) with u_i the
+ * i-th value of the SplitMix64 stream of anderson_create (uniform on
+ * [-width/2, width/2); width 1 in the paper).  Hard walls drop the bonds
+ * that leave the cube.  anderson_norm returns the Gershgorin bound
+ * |diag| + 6 max|t| used as ||A|| by jd_solve's tolerance.
+ *   L, seed, bc as for anderson_create (3 L^3 < 2^31); diag finite;
+ *   width finite, >= 0.
+ * Errors: JD_EINVAL, JD_ENOMEM / JD_EDEVICE.  Synchronous.
+ */
+int anderson_create_offdiag(int L, double diag, double width, uint64_t seed, int bc, anderson_t* out);
+
+/* Copy the hoppings t[3s + d] (binary64, 3 L^3 values, 0 for bonds a hard
+ * wall removes) to the caller's host buffer.  JD_EINVAL for a lattice of
+ * Eq. (1) (constant hopping -1). */
+int anderson_bonds(anderson_t h, double* bonds_host);
+
 /* Release the handle and its device memory.  NULL is a no-op. */
 int anderson_destroy(anderson_t h);
 

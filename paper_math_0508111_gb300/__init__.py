@@ -72,6 +72,28 @@ class Anderson:
         _ffi.call("anderson_size", self._h, ctypes.byref(n))
         self.n = n.value
 
+    @classmethod
+    def offdiag(cls, L, seed, diag=1.28, width=1.0, bc=JD_PERIODIC):
+        """The off-diagonal Anderson model of Section 7 (anderson_create_offdiag):
+        constant diagonal ``diag``, bond hoppings uniform on
+        [-width/2, width/2)."""
+        self = cls.__new__(cls)
+        h = ctypes.c_void_p()
+        _ffi.call("anderson_create_offdiag", int(L), float(diag), float(width),
+                  ctypes.c_uint64(int(seed) & (2 ** 64 - 1)), int(bc), ctypes.byref(h))
+        self._h = h
+        self.L, self.W, self.seed, self.bc = int(L), float(width), int(seed), int(bc)
+        n = ctypes.c_int64()
+        _ffi.call("anderson_size", self._h, ctypes.byref(n))
+        self.n = n.value
+        return self
+
+    def bonds(self):
+        """Hoppings t[s, d] of an off-diagonal lattice, shape (n, 3)."""
+        out = np.empty(3 * self.n, dtype=np.float64)
+        _ffi.call("anderson_bonds", self.handle, out.ctypes.data_as(ctypes.c_void_p))
+        return out.reshape(self.n, 3)
+
     @property
     def handle(self):
         if self._h is None:

@@ -72,6 +72,8 @@ SIGNATURES = [
     ("jd_version", c_int, []),
     ("anderson_create", c_int, [c_int, c_double, c_uint64, c_int, P(c_void_p)]),
     ("anderson_create_from_potential", c_int, [c_int, c_void_p, c_int, P(c_void_p)]),
+    ("anderson_create_offdiag", c_int, [c_int, c_double, c_double, c_uint64, c_int, P(c_void_p)]),
+    ("anderson_bonds", c_int, [c_void_p, c_void_p]),
     ("anderson_destroy", c_int, [c_void_p]),
     ("anderson_size", c_int, [c_void_p, P(c_int64)]),
     ("anderson_potential", c_int, [c_void_p, c_void_p]),

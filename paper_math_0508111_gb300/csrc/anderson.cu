@@ -54,6 +54,63 @@ __global__ void max_abs_kernel(const double* __restrict__ v, int64_t n,
   if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(m));
 }
 
+// Off-diagonal model (Section 7): bond (s, d) from site s to its +d
+// neighbour gets t = width (u_{3s+d} - 1/2), u from the same SplitMix64
+// stream as the potential; hard walls zero the bonds that leave the cube.
+__global__ void bond_kernel(double* __restrict__ b64, float* __restrict__ b32, int L, int64_t n, uint64_t seed,
+                            double width, int periodic) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < 3 * n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t s = i / 3;
+    const int d = (int)(i - 3 * s);
+    const int64_t c = d == 0 ? s % L : d == 1 ? (s / L) % L : s / ((int64_t)L * L);
+    double t = 0.0;
+    if (periodic || c < L - 1) {
+      const uint64_t z = splitmix64_at(seed, (uint64_t)i);
+      const double u = __dmul_rn((double)(z >> 11), 0x1.0p-53);
+      t = __dmul_rn(width, __dsub_rn(u, 0.5));
+    }
+    b64[i] = t;
+    b32[i] = (float)t;
+  }
+}
+
+__global__ void fill_kernel(double* __restrict__ e64, float* __restrict__ e32, int64_t n, double v) {
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x) {
+    e64[s] = v;
+    e32[s] = (float)v;
+  }
+}
+
+// y = (A - shift I) x for the off-diagonal model: one thread per site, the
+// six neighbours weighted by their bonds (own +d bonds at [3s + d], the -d
+// bonds stored at the neighbour).  Neighbour values and bonds are reused
+// through the caches.
+template <typename T>
+__global__ void stencil_bond_kernel(const T* __restrict__ diag, const T* __restrict__ bond, const T* __restrict__ xin,
+                                    T* __restrict__ yout, int L, T shift, int periodic, int64_t n) {
+  const T* __restrict__ x = xin + (int64_t)blockIdx.y * n;
+  T* __restrict__ y = yout + (int64_t)blockIdx.y * n;
+  const int64_t LL = (int64_t)L * L;
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c[3] = {s % L, (s / L) % L, s / LL};
+    const int64_t step[3] = {1, L, LL};
+    T acc = (__ldg(diag + s) - shift) * __ldg(x + s);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      // +d neighbour through the own bond
+      if (c[d] < L - 1) acc += __ldg(bond + 3 * s + d) * __ldg(x + s + step[d]);
+      else if (periodic) acc += __ldg(bond + 3 * s + d) * __ldg(x + s - (L - 1) * step[d]);
+      // -d neighbour through its bond
+      if (c[d] > 0) acc += __ldg(bond + 3 * (s - step[d]) + d) * __ldg(x + s - step[d]);
+      else if (periodic) {
+        const int64_t sn = s + (L - 1) * step[d];
+        acc += __ldg(bond + 3 * sn + d) * __ldg(x + sn);
+      }
+    }
+    y[s] = acc;
+  }
+}
+
 // Row-marching stencil.  A warp owns one x-segment of 32*V sites of a lattice
 // row (fixed y) and walks a chunk of z-planes, keeping the segment's values at
 // z-1, z and z+1 in registers; lane l holds sites seg*32V + l + 32v, so every
@@ -372,6 +429,16 @@ int stencil_apply(const anderson_s* h, T shift, const T* x, T* y, int m, cudaStr
   if constexpr (sizeof(T) == 8) eps = reinterpret_cast<const T*>(h->eps64);
   else eps = reinterpret_cast<const T*>(h->eps32);
   const int L = h->L, per = h->bc == JD_PERIODIC ? 1 : 0;
+  if (h->bond64) {  // off-diagonal model
+    const T* bond = nullptr;
+    if constexpr (sizeof(T) == 8) bond = reinterpret_cast<const T*>(h->bond64);
+    else bond = reinterpret_cast<const T*>(h->bond32);
+    const int blocks = (int)std::min<int64_t>((h->n + 255) / 256, 16 * sm_count());
+    stencil_bond_kernel<T><<<dim3(blocks, m), 256, 0, stream>>>(eps, bond, x, y, L, shift, per, h->n);
+    count_launches();
+    AJD_CHECK_LAUNCH();
+    return JD_OK;
+  }
   const T hop = (T)h->hop;
   // 16-byte rows and 16-byte aligned vectors: the plane-tile kernel
   constexpr int VW = Vec16<T>::n;
@@ -484,6 +551,58 @@ extern "C" int anderson_create_from_potential(int L, const double* eps_host, int
   return JD_OK;
 }
 
+extern "C" int anderson_create_offdiag(int L, double diag, double width, uint64_t seed, int bc, anderson_t* out) {
+  if (!out) return fail(JD_EINVAL, "anderson_create_offdiag: out is NULL");
+  *out = nullptr;
+  if (bc != JD_PERIODIC && bc != JD_HARDWALL) return fail(JD_EINVAL, "anderson_create_offdiag: bad bc");
+  if (bc == JD_PERIODIC && L < 3) return fail(JD_EINVAL, "anderson_create_offdiag: periodic lattice needs L >= 3");
+  if (L < 1 || (int64_t)L * L * L >= ((int64_t)1 << 31) / 3) return fail(JD_EINVAL, "anderson_create_offdiag: bad L");
+  if (!std::isfinite(diag) || !(width >= 0.0) || !std::isfinite(width))
+    return fail(JD_EINVAL, "anderson_create_offdiag: diag must be finite and width finite and >= 0");
+  anderson_s* h = new (std::nothrow) anderson_s();
+  if (!h) return fail(JD_ENOMEM, "anderson_create_offdiag: host allocation failed");
+  h->L = L;
+  h->n = (int64_t)L * L * L;
+  h->W = width;
+  h->seed = seed;
+  h->bc = bc;
+  h->max_abs_eps = std::fabs(diag);
+  cudaGetDevice(&h->device);
+  const int64_t n = h->n;
+  unsigned long long* dmax = nullptr;
+  cudaError_t e = cudaMalloc(&h->eps64, n * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&h->eps32, n * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&h->bond64, 3 * n * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&h->bond32, 3 * n * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&dmax, sizeof(unsigned long long));
+  if (e == cudaSuccess) {
+    const int blocks = (int)std::min<int64_t>((3 * n + 255) / 256, 16 * sm_count());
+    fill_kernel<<<blocks, 256>>>(h->eps64, h->eps32, n, diag);
+    bond_kernel<<<blocks, 256>>>(h->bond64, h->bond32, L, n, seed, width, bc == JD_PERIODIC ? 1 : 0);
+    cudaMemsetAsync(dmax, 0, sizeof(unsigned long long), 0);
+    max_abs_kernel<<<blocks, 256>>>(h->bond64, 3 * n, dmax);
+    count_launches(3);
+    unsigned long long bits = 0;
+    e = cudaMemcpy(&bits, dmax, sizeof(bits), cudaMemcpyDeviceToHost);
+    std::memcpy(&h->max_abs_bond, &bits, sizeof(double));
+  }
+  cudaFree(dmax);
+  if (e != cudaSuccess) {
+    anderson_destroy(h);
+    return fail(e == cudaErrorMemoryAllocation ? JD_ENOMEM : JD_EDEVICE, "anderson_create_offdiag: %s",
+                cudaGetErrorString(e));
+  }
+  *out = h;
+  return JD_OK;
+}
+
+extern "C" int anderson_bonds(anderson_t h, double* bonds_host) {
+  if (!h || !bonds_host) return fail(JD_EINVAL, "anderson_bonds: NULL argument");
+  if (!h->bond64) return fail(JD_EINVAL, "anderson_bonds: the lattice has constant hopping (Eq. (1))");
+  AJD_CUDA(cudaMemcpy(bonds_host, h->bond64, 3 * h->n * sizeof(double), cudaMemcpyDeviceToHost));
+  return JD_OK;
+}
+
 extern "C" int anderson_destroy(anderson_t h) {
   if (!h) return JD_OK;
   int dev = 0;
@@ -491,6 +610,8 @@ extern "C" int anderson_destroy(anderson_t h) {
   cudaSetDevice(h->device);
   cudaFree(h->eps64);
   cudaFree(h->eps32);
+  cudaFree(h->bond64);
+  cudaFree(h->bond32);
   cudaSetDevice(dev);
   delete h;
   return JD_OK;
@@ -510,7 +631,7 @@ extern "C" int anderson_potential(anderson_t h, double* eps_host) {
 
 extern "C" int anderson_norm(anderson_t h, double* norm) {
   if (!h || !norm) return fail(JD_EINVAL, "anderson_norm: NULL argument");
-  *norm = 6.0 + h->max_abs_eps;
+  *norm = h->norm_bound();
   return JD_OK;
 }
 

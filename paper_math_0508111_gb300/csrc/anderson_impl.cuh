@@ -14,6 +14,15 @@ struct anderson_s {
   double* eps64 = nullptr;  // on-site energies, binary64, device
   float* eps32 = nullptr;   // binary32 copy, device
   double max_abs_eps = 0.0;
+  // off-diagonal model (Section 7): hopping of the bond from site s to its
+  // +x/+y/+z neighbour at [3s + d] (0 for bonds a hard wall removes);
+  // nullptr for Eq. (1), whose hopping is `hop` on every bond
+  double* bond64 = nullptr;
+  float* bond32 = nullptr;
+  double max_abs_bond = 1.0;
+  // Gershgorin bound max|diagonal| + 6 max|hopping|: the ||A|| of the
+  // relative tolerances (6 + max|eps| for Eq. (1))
+  double norm_bound() const { return max_abs_eps + 6.0 * max_abs_bond; }
 };
 
 namespace ajd {

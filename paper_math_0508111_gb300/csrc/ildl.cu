@@ -409,7 +409,8 @@ void ildl_free_device(ildl_s* f) {
 }
 
 // CSR of A - sigma I for a lattice (host, from the binary64 potential).
-int lattice_csr(const anderson_s* h, const std::vector<double>& eps, double sigma, SymCsr& A) {
+int lattice_csr(const anderson_s* h, const std::vector<double>& eps, const std::vector<double>& bonds, double sigma,
+                SymCsr& A) {
   const int L = h->L;
   const int64_t n = h->n;
   const bool per = h->bc == JD_PERIODIC;
@@ -424,7 +425,9 @@ int lattice_csr(const anderson_s* h, const std::vector<double>& eps, double sigm
   for (int64_t s = 0; s < n; ++s) {
     const int x = (int)(s % L), y = (int)((s / L) % L), z = (int)(s / ((int64_t)L * L));
     int k = 0;
-    auto add = [&](int xx, int yy, int zz) {
+    // neighbour (xx, yy, zz) across the bond of direction d stored at site
+    // `lower` (the site it leaves in the +d direction)
+    auto add = [&](int xx, int yy, int zz, int d, bool minus) {
       if (per) {
         xx = (xx + L) % L;
         yy = (yy + L) % L;
@@ -432,16 +435,17 @@ int lattice_csr(const anderson_s* h, const std::vector<double>& eps, double sigm
       } else if (xx < 0 || xx >= L || yy < 0 || yy >= L || zz < 0 || zz >= L) {
         return;
       }
-      nb[k] = (int)(xx + (int64_t)L * (yy + (int64_t)L * zz));
-      nv[k] = h->hop;
+      const int64_t t = xx + (int64_t)L * (yy + (int64_t)L * zz);
+      nb[k] = (int)t;
+      nv[k] = bonds.empty() ? h->hop : bonds[3 * (minus ? t : s) + d];
       ++k;
     };
-    add(x - 1, y, z);
-    add(x + 1, y, z);
-    add(x, y - 1, z);
-    add(x, y + 1, z);
-    add(x, y, z - 1);
-    add(x, y, z + 1);
+    add(x - 1, y, z, 0, true);
+    add(x + 1, y, z, 0, false);
+    add(x, y - 1, z, 1, true);
+    add(x, y + 1, z, 1, false);
+    add(x, y, z - 1, 2, true);
+    add(x, y, z + 1, 2, false);
     nb[k] = (int)s;
     nv[k] = eps[s] - sigma;
     ++k;
@@ -578,11 +582,13 @@ int ildl_create_on_stream(anderson_t h, double sigma, const ildl_params* p, ildl
   ildl_params prm;
   AJD_TRY(check_params(p, prm));
   try {
-    std::vector<double> eps(h->n);
+    std::vector<double> eps(h->n), bonds(h->bond64 ? 3 * h->n : 0);
     AJD_CUDA(cudaMemcpyAsync(eps.data(), h->eps64, h->n * sizeof(double), cudaMemcpyDeviceToHost, st));
+    if (h->bond64)
+      AJD_CUDA(cudaMemcpyAsync(bonds.data(), h->bond64, 3 * h->n * sizeof(double), cudaMemcpyDeviceToHost, st));
     AJD_CUDA(cudaStreamSynchronize(st));
     SymCsr A;
-    lattice_csr(h, eps, sigma, A);
+    lattice_csr(h, eps, bonds, sigma, A);
     ildl_s* f = new ildl_s();
     f->device = h->device;
     const auto t0 = std::chrono::steady_clock::now();

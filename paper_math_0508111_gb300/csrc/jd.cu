@@ -976,7 +976,7 @@ int JdSolver::correction(int kc, double theta_hat, double rel_tol, int* its) {
 int JdSolver::run(double* evals, double* evecs, jd_stats* st) {
   using Clock = std::chrono::steady_clock;
   const auto t0 = Clock::now();
-  normA_ = 6.0 + h_->max_abs_eps;
+  normA_ = h_->norm_bound();
   const int64_t n = h_->n;
   const int guard = p_.guard < 0 ? 0 : (p_.guard == 0 ? 2 : p_.guard);
   kint_ = (int)std::min<int64_t>(k_ + guard, n / 2 > k_ ? n / 2 : k_);

@@ -1,0 +1,72 @@
+"""GPU parity of the off-diagonal ("inverse") Anderson model of Section 7
+(Table 6): bonds bit-exact against the oracle, the bond-weighted stencil
+against the oracle's matrix, and Jacobi-Davidson pairs against the dense
+oracle."""
+import numpy as np
+import pytest
+
+from oracle import eig, lattice, rng
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def ajd():
+    import paper_math_0508111_gb300 as ajd
+    assert torch.cuda.is_available()
+    return ajd
+
+
+@pytest.mark.parametrize("L,bc", [(3, 0), (5, 1), (8, 0), (13, 1)])
+def test_bonds_bit_exact(ajd, L, bc):
+    with ajd.Anderson.offdiag(L, 7, diag=1.28, width=1.0, bc=bc) as h:
+        got = h.bonds()
+        want = rng.hoppings(L, 7, 1.0)
+        if bc == 1:
+            idx = np.arange(L ** 3)
+            c = np.stack([idx % L, (idx // L) % L, idx // L ** 2], axis=1)
+            want = np.where(c < L - 1, want, 0.0)
+        assert np.array_equal(got, want)
+        assert np.array_equal(h.potential(), np.full(L ** 3, 1.28))
+        assert h.norm() == pytest.approx(1.28 + 6 * np.abs(want).max(), abs=0)
+
+
+@pytest.mark.parametrize("L,bc", [(3, 0), (4, 1), (9, 0), (16, 1), (33, 0)])
+@pytest.mark.parametrize("dt", ["float64", "float32"])
+def test_offdiag_stencil_matches_oracle(ajd, L, bc, dt):
+    dtype = getattr(torch, dt)
+    with ajd.Anderson.offdiag(L, 3, bc=bc) as h:
+        X = np.random.default_rng(L).standard_normal((2, h.n))
+        y = h.apply(torch.tensor(X, device="cuda", dtype=dtype), shift=0.4).double().cpu().numpy()
+        A = lattice.assemble_offdiag(L, 1.28, rng.hoppings(L, 3), bc, shift=0.4)
+        want = (A @ X.T).T
+        tol = 1e-14 if dt == "float64" else 2e-6
+        assert np.abs(y - want).max() <= tol * 5 * np.abs(X).max()
+
+
+@pytest.mark.parametrize("L,bc,sigma,k,prec", [(8, 0, 0.0, 5, 0), (9, 1, 0.0, 4, 2), (10, 0, 0.5, 3, 1)])
+def test_offdiag_jd_matches_dense_oracle(ajd, L, bc, sigma, k, prec):
+    """Eigenpairs nearest sigma (the paper's target is 0 with the diagonal at
+    1.28) against the dense oracle."""
+    tol = 1e-11 if prec == 0 else 1e-10
+    hop = rng.hoppings(L, 5)
+    A = lattice.assemble_offdiag(L, 1.28, hop, bc)
+    nA = lattice.norm_bound_offdiag(1.28, hop)
+    with ajd.Anderson.offdiag(L, 5, bc=bc) as h:
+        assert h.norm() == pytest.approx(nA if bc == 0 else 1.28 + 6 * np.abs(h.bonds()).max())
+        ev, X, st = ajd.solve(h, sigma, k, tol, precision=prec)
+    w, V = np.linalg.eigh(A.toarray())
+    o = eig.order_nearest(w, sigma)
+    assert st["nconv"] == k
+    assert np.abs(ev - w[o[:k]]).max() <= 1e-10 * nA
+    assert np.linalg.norm(A @ X - X * ev, axis=0).max() <= 2 * tol * nA
+    assert np.abs(X.T @ X - np.eye(k)).max() <= 1e-12
+    Vk = V[:, o[:k]]
+    for j in range(k):  # eigenvector angles (clusters are split by the disorder)
+        gaps = np.abs(w - w[o[j]])
+        gaps[o[j]] = np.inf
+        res = np.linalg.norm(A @ X[:, j] - ev[j] * X[:, j])
+        sin = np.sqrt(max(0.0, 1 - min(1.0, abs(X[:, j] @ Vk[:, j])) ** 2))
+        assert sin <= max(1e-6, 2 * res / gaps.min())
