@@ -69,7 +69,7 @@ def parse():
     ap.add_argument("--serve-lmax", type=int, default=48, help="largest lattice of the serving sample")
     ap.add_argument("--serve-slots", type=int, default=4)
     ap.add_argument("--serve-setup-threads", type=int, default=3)
-    ap.add_argument("--setup-threads", type=int, default=4,
+    ap.add_argument("--setup-threads", type=int, default=2,
                     help="concurrent preconditioner builds in the pipelined batch")
     return ap.parse_args()
 
