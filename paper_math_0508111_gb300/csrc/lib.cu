@@ -1,3 +1,4 @@
+#include <atomic>
 // Library-wide helpers: error strings, version, device properties.
 #include "common.cuh"
 
@@ -25,16 +26,17 @@ int fail(int code, const char* fmt, ...) {
 }
 
 int sm_count() {
-  static int cached = 0;
-  if (cached == 0) {
-    int dev = 0, v = 0;
-    if (cudaGetDevice(&dev) == cudaSuccess &&
-        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0)
-      cached = v;
-    else
-      return 148;
+  // SMs of the current device, queried once per device (threads may ask
+  // concurrently: relaxed atomics, every writer stores the same value)
+  static std::atomic<int> cached[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
+  int v = cached[dev].load(std::memory_order_relaxed);
+  if (v == 0) {
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) return 148;
+    cached[dev].store(v, std::memory_order_relaxed);
   }
-  return cached;
+  return v;
 }
 
 int64_t& launch_counter() {
