@@ -388,6 +388,26 @@ int jd_solve(anderson_t h, double sigma, int k, double tol, const jd_params* p, 
              double* evecs, jd_stats* st, void* stream);
 
 /*
+ * jd_lanczos_solve -- the same problem as jd_solve by the paper's other
+ * method (Section 4.1): shift-and-invert Lanczos, the Lanczos vectors of
+ * (A - sigma I)^{-1} (Eq. (4.2)), each product a preconditioned SQMR solve
+ * with the same multilevel ILDL^T (Section 7: stopped at relative residual
+ * 1e-10).  Full reorthogonalisation replaces implicit restarts: at most
+ * p->jmax (<= 64; 0 = 64) Lanczos vectors.  k + guard Ritz pairs with the
+ * largest |nu| (lambda = sigma + 1/nu) are taken once their residual
+ * estimates fall below tol ||A||, then pass the final Rayleigh-Ritz and the
+ * explicit residual check of jd_solve; outputs, ordering and conventions as
+ * jd_solve (k <= 60).  Uses from *p: precision (of the inner solve), seed,
+ * guard, jmax, max_inner (at least 2000 here), inner_floor (the inner
+ * relative tolerance; 0 = 1e-10), ildl, precond.  jd_stats: outer_its =
+ * Lanczos steps, inner_its = SQMR iterations.  JD_ENOCONV when the Ritz
+ * estimates did not converge within jmax steps (outputs hold the best
+ * pairs).
+ */
+int jd_lanczos_solve(anderson_t h, double sigma, int k, double tol, const jd_params* p, double* evals,
+                     double* evecs, jd_stats* st, void* stream);
+
+/*
  * jd_solve_batch -- jd_solve for nprob independent problems (disorder
  * realisations, shifts, k; the paper's physics needs "many realizations",
  * Section 3), pipelined: `setup_threads` host threads build the

@@ -289,8 +289,12 @@ def _stats_dict(st):
     return d
 
 
-def solve(lattice, sigma, k, tol, precision=JD_FP64, vectors=True, stream=None, raise_on_noconv=True, **params):
-    """The k eigenpairs of the lattice's matrix nearest sigma (jd_solve).
+def solve(lattice, sigma, k, tol, precision=JD_FP64, vectors=True, stream=None, raise_on_noconv=True,
+          method="jd", **params):
+    """The k eigenpairs of the lattice's matrix nearest sigma: by
+    Jacobi-Davidson (jd_solve, ``method="jd"``) or by shift-and-invert
+    Lanczos over the same preconditioned SQMR (jd_lanczos_solve,
+    ``method="lanczos"``).
 
     Returns (evals, evecs, stats): evals has shape (k,), evecs shape (n, k)
     (numpy, host), stats a dict of the solver counters.  Extra keyword
@@ -300,11 +304,12 @@ def solve(lattice, sigma, k, tol, precision=JD_FP64, vectors=True, stream=None, 
     X = np.zeros((int(k), lattice.n)) if vectors else None
     st = _ffi.JdStats()
     vp = ctypes.c_void_p
-    rc = _ffi.lib().jd_solve(lattice.handle, float(sigma), int(k), float(tol), ctypes.byref(p),
+    fn = {"jd": "jd_solve", "lanczos": "jd_lanczos_solve"}[method]
+    rc = getattr(_ffi.lib(), fn)(lattice.handle, float(sigma), int(k), float(tol), ctypes.byref(p),
                              ev.ctypes.data_as(vp), X.ctypes.data_as(vp) if vectors else None, ctypes.byref(st),
                              _stream_handle(stream) if stream is not None else None)
     if rc != JD_OK and (rc != JD_ENOCONV or raise_on_noconv):
-        _ffi.check(rc, "jd_solve")
+        _ffi.check(rc, fn)
     stats = _stats_dict(st)
     stats["status"] = rc
     return ev, (X.T if vectors else None), stats

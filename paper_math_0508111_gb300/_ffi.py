@@ -91,6 +91,8 @@ SIGNATURES = [
     ("jd_params_default", c_int, [P(JdParams)]),
     ("jd_solve", c_int, [c_void_p, c_double, c_int, c_double, P(JdParams), c_void_p, c_void_p, P(JdStats),
                          c_void_p]),
+    ("jd_lanczos_solve", c_int, [c_void_p, c_double, c_int, c_double, P(JdParams), c_void_p, c_void_p, P(JdStats),
+                                 c_void_p]),
     ("jd_server_params_default", c_int, [P(JdServerParams)]),
     ("jd_server_estimate", c_int, [c_int, c_int, P(ctypes.c_size_t)]),
     ("jd_server_create", c_int, [P(JdServerParams), P(c_void_p)]),

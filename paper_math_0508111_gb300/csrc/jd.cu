@@ -648,6 +648,9 @@ class JdSolver {
   ~JdSolver() { release(); }
 
   int run(double* evals, double* evecs, jd_stats* st);
+  // shift-and-invert Lanczos (Section 4.1) over the same preconditioned
+  // SQMR: the alternative to run()
+  int lanczos(double* evals, double* evecs, jd_stats* st);
 
  private:
   anderson_s* h_;
@@ -692,6 +695,9 @@ class JdSolver {
   int rr(int m);
   template <typename T, typename P>
   int correction(int kc, double theta_hat, double rel_tol, int* its);
+  template <typename T, typename P>
+  int sqmr_core(int c, double shift, const double* rhs, double sign, double rel_tol, int maxit, double* xout,
+                int* its);
   // out = K^{-1} in with vectors in T and the preconditioner applied in P
   template <typename T, typename P>
   int apply_k(const T* in, T* out);
@@ -910,8 +916,29 @@ int JdSolver::correction(int kc, double theta_hat, double rel_tol, int* its) {
     }
     AJD_CUDA(cudaMemcpyAsync(Minv_, Mi.data(), sizeof(double) * c * c, cudaMemcpyHostToDevice, s_));
   }
-  // rhs b = -r (binary64 residual, already orthogonal to Q and u)
-  convert_kernel<double, T><<<bl, kThreads, 0, s_>>>(r_, b, n_, -1.0); count_launches();
+  // rhs b = -r (binary64 residual, already orthogonal to Q and u); the
+  // solution goes to t_ (binary64), which the caller orthogonalises
+  return sqmr_core<T, P>(c, theta_hat, r_, -1.0, rel_tol, p_.max_inner, t_, its);
+}
+
+// Preconditioned SQMR for (P (A - shift I) P) x = P b with b = sign * rhs and
+// P the projection against the first c columns of Q~ (the projected
+// preconditioner K^{-1} - W M^{-1} W^T of the correction equation); c = 0
+// is the plain preconditioned solve of (A - shift I) x = b.  Stops when the
+// quasi-residual estimate falls below rel_tol ||b|| or after maxit
+// iterations; x goes to xout (binary64).
+template <typename T, typename P>
+int JdSolver::sqmr_core(int c, double shift, const double* rhs, double sign, double rel_tol, int maxit, double* xout,
+                        int* its) {
+  T* Qt = static_cast<T*>(Qt_);
+  T* W = static_cast<T*>(W_);
+  T *x = static_cast<T*>(xb_), *r = static_cast<T*>(rb_), *q = static_cast<T*>(qb_), *d = static_cast<T*>(db_);
+  T *t = static_cast<T*>(tb_), *y = static_cast<T*>(yb_), *u = static_cast<T*>(ub_), *b = static_cast<T*>(bb_);
+  int* done = flags_;
+  int* brk = flags_ + 1;
+  const int bl = nb_;
+  const double theta_hat = shift;
+  convert_kernel<double, T><<<bl, kThreads, 0, s_>>>(rhs, b, n_, sign); count_launches();
   Cols<T> QtC{Qt, ld_, c}, WC{W, ld_, c};
   // init: r = b, x = d = 0, tau = ||b||; u = P b; q = u; rho = r^T u
   sqmr_init_kernel<T><<<bl, kThreads, 0, s_>>>(b, r, x, d, q, n_, partial_); count_launches();
@@ -930,7 +957,6 @@ int JdSolver::correction(int kc, double theta_hat, double rel_tol, int* its) {
   AJD_TRY(precond());
   sqmr_scalar_beta_kernel<<<1, 32, 0, s_>>>(partial_, bl, scal_, 1, done, brk); count_launches();
   sqmr_update_q_kernel<T><<<bl, kThreads, 0, s_>>>(u, q, n_, scal_, done); count_launches();  // q = u (beta = 0)
-  const int maxit = p_.max_inner;
   int it = 0;
   const int chunk = 4;
   while (it < maxit) {
@@ -967,8 +993,7 @@ int JdSolver::correction(int kc, double theta_hat, double rel_tol, int* its) {
   }
   *its = it;
   AJD_TRY(ildl_check_device_error(pc_));
-  // t (binary64) = x, then the caller orthogonalises it
-  convert_kernel<T, double><<<bl, kThreads, 0, s_>>>(x, t_, n_, 1.0); count_launches();
+  convert_kernel<T, double><<<bl, kThreads, 0, s_>>>(x, xout, n_, 1.0); count_launches();
   AJD_CHECK_LAUNCH();
   return JD_OK;
 }
@@ -1251,6 +1276,117 @@ int JdSolver::run(double* evals, double* evecs, jd_stats* st) {
   return status;
 }
 
+// Shift-and-invert Lanczos (Section 4.1, Eq. (4.2)): Lanczos vectors of
+// (A - sigma I)^{-1}, each product a preconditioned SQMR solve (the same
+// ILDL^T and kernels as the correction equation, no projection) to
+// relative residual inner_floor (default 1e-10, the paper's stopping rule
+// for this mode).  Full reorthogonalisation (CGS2) instead of implicit
+// restarts: at most jmax (<= 64) Lanczos vectors.  The Ritz values nu of the
+// tridiagonal T give lambda = sigma + 1/nu; the k + guard largest |nu| are
+// taken when their residual estimates ||A - sigma I|| beta |z_last| / |nu|
+// fall below tol ||A||, their Ritz vectors go through the same final
+// Rayleigh-Ritz, residual check and ordering as run().
+int JdSolver::lanczos(double* evals, double* evecs, jd_stats* st) {
+  using Clock = std::chrono::steady_clock;
+  const auto t0 = Clock::now();
+  normA_ = h_->norm_bound();
+  const int64_t n = h_->n;
+  const int guard = p_.guard < 0 ? 0 : (p_.guard == 0 ? 2 : p_.guard);
+  kint_ = (int)std::min<int64_t>(k_ + guard, n - 1);
+  jmax_ = (int)std::min<int64_t>(p_.jmax > 0 ? std::min(p_.jmax, kMaxM) : kMaxM, n);
+  if (jmax_ < kint_ + 1) jmax_ = std::min<int64_t>(kint_ + 1, n);
+  jmin_ = 1;
+  if (kint_ < 1 || jmax_ < kint_) return fail(JD_EINVAL, "jd_lanczos_solve: lattice too small for k = %d", k_);
+  AJD_TRY(alloc());
+  launches0_ = launch_counter();
+  const uint64_t seed = p_.seed ? p_.seed : (h_->seed ^ 0xD1B54A32D192ED03ull);
+  random_kernel<<<nb_, kThreads, 0, s_>>>(t_, n, seed); count_launches();
+  double nrm = 0.0;
+  AJD_TRY(cgs2(0, 0, t_, &nrm));
+  if (!(nrm > 0.0)) return fail(JD_EBREAKDOWN, "jd_lanczos_solve: zero start vector");
+  scale_copy_kernel<<<nb_, kThreads, 0, s_>>>(t_, V_, n, scal_, 0, 1); count_launches();
+  const double inner_tol = p_.inner_floor > 0.0 ? p_.inner_floor : 1e-10;
+  const int maxit = std::max(p_.max_inner, 2000);
+  const double op_norm = normA_ + std::fabs(sigma_);  // bound on ||A - sigma I||
+  std::vector<double> alpha, beta, w, Z;
+  std::vector<int> order;
+  int m = 0, steps = 0;
+  bool converged = false;
+  double worst = 0.0;
+  for (int j = 0; j < jmax_; ++j) {
+    int its = 0;
+    double* vj = V_ + (int64_t)j * ld_;
+    if (p_.precision == JD_FP32) AJD_TRY((sqmr_core<float, float>(0, sigma_, vj, 1.0, inner_tol, maxit, t_, &its)));
+    else if (p_.precision == JD_MIXED) AJD_TRY((sqmr_core<double, float>(0, sigma_, vj, 1.0, inner_tol, maxit, t_, &its)));
+    else AJD_TRY((sqmr_core<double, double>(0, sigma_, vj, 1.0, inner_tol, maxit, t_, &its)));
+    inner_total_ += its;
+    ++steps;
+    // alpha_j = v_j^T w, then w orthogonalised against v_0..v_j (twice)
+    AJD_TRY(dot_cols(Cols<double>{vj, ld_, 1}, Cols<double>{}, nullptr, t_, scal_ + 2));
+    double aj;
+    AJD_TRY(sync_read(scal_ + 2, 1, &aj));
+    AJD_TRY(cgs2(0, j + 1, t_, &nrm));
+    alpha.push_back(aj);
+    m = j + 1;
+    // Ritz values of T_m
+    std::vector<double> T((size_t)m * m, 0.0);
+    for (int i = 0; i < m; ++i) {
+      T[(size_t)i * m + i] = alpha[i];
+      if (i + 1 < m) T[(size_t)i * m + i + 1] = T[(size_t)(i + 1) * m + i] = beta[i];
+    }
+    hostla::jacobi_eig(m, T, w, Z);
+    order.resize(m);
+    for (int i = 0; i < m; ++i) order[i] = i;
+    std::sort(order.begin(), order.end(), [&](int a, int b) { return std::fabs(w[a]) > std::fabs(w[b]); });
+    if (m >= kint_) {
+      worst = 0.0;
+      for (int q = 0; q < kint_; ++q) {
+        const int i = order[q];
+        const double est = op_norm * nrm * std::fabs(Z[(size_t)i * m + (m - 1)]) / std::max(std::fabs(w[i]), 1e-300);
+        worst = std::max(worst, est);
+      }
+      if (trace_) std::fprintf(stderr, "lanczos step %d: beta %.3e worst estimate %.3e (inner its %d)\n", j, nrm,
+                               worst / normA_, its);
+      if (worst <= tol_ * normA_) {
+        converged = true;
+        break;
+      }
+    }
+    if (!(nrm > 1e-14 * std::fabs(aj)) || m == jmax_) break;  // invariant subspace, or no room
+    beta.push_back(nrm);
+    scale_copy_kernel<<<nb_, kThreads, 0, s_>>>(t_, V_ + (int64_t)(j + 1) * ld_, n, scal_, 0, 1); count_launches();
+  }
+  // Ritz vectors of the kint largest |nu| into Q
+  const int kc = std::min(kint_, m);
+  {
+    std::vector<double> up((size_t)kMaxM * kc, 0.0);
+    for (int q = 0; q < kc; ++q)
+      for (int i = 0; i < m; ++i) up[(size_t)q * kMaxM + i] = Z[(size_t)order[q] * m + i];
+    AJD_CUDA(cudaMemcpyAsync(Y_, up.data(), sizeof(double) * kMaxM * kc, cudaMemcpyHostToDevice, s_));
+    lincomb_kernel<<<nb_, kThreads, 0, s_>>>(V_, ld_, m, Y_, kMaxM, kc, Q_, ld_, n); count_launches();
+    AJD_CUDA(cudaStreamSynchronize(s_));
+  }
+  if (st) {
+    st->outer_its = steps;
+    st->inner_its = inner_total_;
+    st->restarts = 0;
+  }
+  const int rc = finalize(kc, nullptr, evals, evecs, st);
+  if (st) {
+    st->solve_ms = std::chrono::duration<double, std::milli>(Clock::now() - t0).count();
+    st->kernel_launches = launch_counter() - launches0_;
+    st->precond_calls = precond_calls_;
+    st->precond_ms = precond_ms_;
+    st->stencil_calls = stencil_calls_;
+    st->stencil_ms = stencil_ms_;
+  }
+  if (rc != JD_OK) return rc;
+  if (!converged)
+    return fail(JD_ENOCONV, "jd_lanczos_solve: Ritz estimates %.3e after %d Lanczos steps (tol %.1e)", worst / normA_,
+                steps, tol_);
+  return JD_OK;
+}
+
 // Final Rayleigh–Ritz on the locked vectors, residuals, ordering, signs,
 // copy-out.
 int JdSolver::finalize(int kc, double* lam, double* evals, double* evecs, jd_stats* st) {
@@ -1374,6 +1510,37 @@ extern "C" int jd_solve(anderson_t h, double sigma, int k, double tol, const jd_
   {
     JdSolver solver(h, pc, prm, sigma, k, tol, reinterpret_cast<cudaStream_t>(stream));
     rc = solver.run(evals, evecs, st);
+  }
+  if (own) ildl_destroy(pc);
+  return rc;
+}
+
+extern "C" int jd_lanczos_solve(anderson_t h, double sigma, int k, double tol, const jd_params* p, double* evals,
+                                double* evecs, jd_stats* st, void* stream) {
+  if (!h || !evals) return fail(JD_EINVAL, "jd_lanczos_solve: NULL handle or evals");
+  if (!std::isfinite(sigma)) return fail(JD_EINVAL, "jd_lanczos_solve: sigma must be finite");
+  if (k < 1 || k > 60 || (int64_t)k >= h->n) return fail(JD_EINVAL, "jd_lanczos_solve: need 1 <= k <= 60 and k < n");
+  if (!(tol > 0.0)) return fail(JD_EINVAL, "jd_lanczos_solve: tol must be > 0");
+  jd_params prm;
+  AJD_TRY(normalize_params(p, prm));
+  if (st) std::memset(st, 0, sizeof(*st));
+  using Clock = std::chrono::steady_clock;
+  const auto t0 = Clock::now();
+  ildl_t pc = prm.precond;
+  bool own = false;
+  if (!pc) {
+    AJD_TRY(ildl_create_on_stream(h, sigma, &prm.ildl, &pc, reinterpret_cast<cudaStream_t>(stream),
+                                  copy_for_precision(prm.precision)));
+    own = true;
+  }
+  if (st) {
+    st->setup_ms = std::chrono::duration<double, std::milli>(Clock::now() - t0).count();
+    ildl_info(pc, &st->ildl);
+  }
+  int rc;
+  {
+    JdSolver solver(h, pc, prm, sigma, k, tol, reinterpret_cast<cudaStream_t>(stream));
+    rc = solver.lanczos(evals, evecs, st);
   }
   if (own) ildl_destroy(pc);
   return rc;

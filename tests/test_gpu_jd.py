@@ -250,3 +250,29 @@ def test_jd_full_size_certificate(ajd, L):
         assert X[i, j] > 0
     # the two solves find the same eigenvalues (both converged to 1e-8 ||A||)
     assert np.abs(ev - ev64).max() <= 1e-10 * nA
+
+
+@pytest.mark.parametrize("L,W,seed,bc,sigma,k,prec", [
+    (10, 16.5, 1, 0, 0.0, 5, 0),
+    (9, 12.0, 3, 1, -0.5, 4, 2),
+    (12, 16.5, 8, 0, 1.0, 3, 1),
+])
+def test_lanczos_matches_dense_oracle(ajd, L, W, seed, bc, sigma, k, prec):
+    """Shift-and-invert Lanczos over the preconditioned SQMR (Section 4.1)
+    reaches the pairs of the dense oracle."""
+    tol = 1e-11 if prec == 0 else 1e-10
+    with ajd.Anderson(L, W, seed, bc) as h:
+        ev, X, st = ajd.solve(h, sigma, k, tol, precision=prec, method="lanczos", ildl={"n_dense": 300})
+    _check_pairs(L, W, seed, bc, sigma, k, ev, X, st, tol)
+    assert st["outer_its"] <= 64 and st["inner_its"] > 0
+
+
+def test_lanczos_agrees_with_jd_mid_size(ajd):
+    """At L = 24 (several levels, dense tail 1000) both methods give the same
+    eigenvalues, checked against the shift-invert oracle."""
+    L, W, seed, sigma, k, tol = 24, 16.5, 4, 0.0, 5, 1e-10
+    with ajd.Anderson(L, W, seed) as h:
+        ev_l, X_l, st_l = ajd.solve(h, sigma, k, tol, method="lanczos", precision=2)
+        ev_j, _, _ = ajd.solve(h, sigma, k, tol, precision=2, vectors=False)
+    _check_pairs(L, W, seed, 0, sigma, k, ev_l, X_l, st_l, tol, oracle="lanczos")
+    assert np.abs(ev_l - ev_j).max() <= 1e-10 * (6 + W / 2)
