@@ -400,7 +400,9 @@ int jd_solve(anderson_t h, double sigma, int k, double tol, const jd_params* p, 
  * jd_solve (k <= 60).  Uses from *p: precision (of the inner solve), seed,
  * guard, jmax, max_inner (at least 2000 here), inner_floor (the inner
  * relative tolerance; 0 = 1e-10), ildl, precond.  jd_stats: outer_its =
- * Lanczos steps, inner_its = SQMR iterations.  JD_ENOCONV when the Ritz
+ * Lanczos steps, inner_its = SQMR iterations.  With JD_FP32 the inner
+ * tolerance defaults to 1e-6 (binary32 SQMR stalls there), which bounds the
+ * attainable accuracy; use JD_FP64 or JD_MIXED.  JD_ENOCONV when the Ritz
  * estimates did not converge within jmax steps (outputs hold the best
  * pairs).
  */

@@ -1305,7 +1305,9 @@ int JdSolver::lanczos(double* evals, double* evecs, jd_stats* st) {
   AJD_TRY(cgs2(0, 0, t_, &nrm));
   if (!(nrm > 0.0)) return fail(JD_EBREAKDOWN, "jd_lanczos_solve: zero start vector");
   scale_copy_kernel<<<nb_, kThreads, 0, s_>>>(t_, V_, n, scal_, 0, 1); count_launches();
-  const double inner_tol = p_.inner_floor > 0.0 ? p_.inner_floor : 1e-10;
+  // the paper's 1e-10; a binary32 inner solve cannot get below ~1e-6 (its
+  // Lanczos operator is then only that accurate)
+  const double inner_tol = p_.inner_floor > 0.0 ? p_.inner_floor : (p_.precision == JD_FP32 ? 1e-6 : 1e-10);
   const int maxit = std::max(p_.max_inner, 2000);
   const double op_norm = normA_ + std::fabs(sigma_);  // bound on ||A - sigma I||
   std::vector<double> alpha, beta, w, Z;
