@@ -55,6 +55,9 @@ def parse():
                     help="diagonal disorder of Eq. (1), or the off-diagonal model of Section 7 (diagonal 1.28, "
                          "hoppings uniform on [-1/2, 1/2])")
     ap.add_argument("--bc", default="periodic", choices=["periodic", "hardwall"])
+    ap.add_argument("--method", default="jd", choices=["jd", "lanczos"],
+                    help="jd: pipelined jd_solve_batch; lanczos: shift-and-invert Lanczos (jd_lanczos_solve), "
+                         "one realisation after another")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp32", "fp64"],
                     help="inner-solve precision of the headline form")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain binary64 comparison")
@@ -347,10 +350,22 @@ def main():
         return ajd._stats_dict(st)
 
     def batch(handles, precision, ev_bufs, x_bufs):
-        """jd_solve_batch over the given problems; ev_bufs/x_bufs are raw
-        pointers (host or device)."""
+        """jd_solve_batch over the given problems (or, with --method lanczos,
+        jd_lanczos_solve one after another); ev_bufs/x_bufs are raw pointers
+        (host or device)."""
         m = len(handles)
         vp = ajd.ctypes.c_void_p
+        if args.method == "lanczos":
+            out = []
+            for i in range(m):
+                p = ajd.jd_params(precision=precision)
+                st = ajd._ffi.JdStats()
+                hv = handles[i] if isinstance(handles[i], vp) else vp(handles[i])
+                rc = ajd._ffi.lib().jd_lanczos_solve(hv, sigma, k, tol, ajd.ctypes.byref(p), vp(ev_bufs[i]),
+                                                     vp(x_bufs[i]), ajd.ctypes.byref(st), vp(stream.cuda_stream))
+                ajd._ffi.check(rc, "jd_lanczos_solve")
+                out.append(ajd._stats_dict(st))
+            return out
         hs = (vp * m)(*handles)
         sig = (ajd.ctypes.c_double * m)(*([sigma] * m))
         kk = (ajd.ctypes.c_int * m)(*([k] * m))
