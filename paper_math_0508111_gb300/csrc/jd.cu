@@ -705,6 +705,11 @@ class JdSolver {
   int cache_lock_column(int kc);
   int finalize(int kc, double* lam, double* evals, double* evecs, jd_stats* st);
   int sync_read(const double* dev, int cnt, double* host);
+  // wait for the work queued on s_ by blocking on an event: the waiting
+  // thread yields its core (setup threads of a batch or a server share the
+  // host cores with the solving threads)
+  int wait_stream();
+  cudaEvent_t sync_ev_ = nullptr;
 };
 
 int JdSolver::alloc() {
@@ -770,6 +775,8 @@ void JdSolver::harvest_events() {
 }
 
 void JdSolver::release() {
+  if (sync_ev_) cudaEventDestroy(sync_ev_);
+  sync_ev_ = nullptr;
   for (auto& e : evp_) if (e) cudaEventDestroy(e);
   for (auto& e : evs_) if (e) cudaEventDestroy(e);
   for (void* p : {(void*)V_, (void*)AV_, (void*)Vt_, (void*)AVt_, (void*)Q_, (void*)t_, (void*)u_, (void*)Au_,
@@ -781,9 +788,16 @@ void JdSolver::release() {
   host_ = nullptr;
 }
 
+int JdSolver::wait_stream() {
+  if (!sync_ev_) AJD_CUDA(cudaEventCreateWithFlags(&sync_ev_, cudaEventDisableTiming | cudaEventBlockingSync));
+  AJD_CUDA(cudaEventRecord(sync_ev_, s_));
+  AJD_CUDA(cudaEventSynchronize(sync_ev_));
+  return JD_OK;
+}
+
 int JdSolver::sync_read(const double* dev, int cnt, double* host) {
   AJD_CUDA(cudaMemcpyAsync(host_, dev, sizeof(double) * cnt, cudaMemcpyDeviceToHost, s_));
-  AJD_CUDA(cudaStreamSynchronize(s_));
+  AJD_TRY(wait_stream());
   std::memcpy(host, host_, sizeof(double) * cnt);
   return JD_OK;
 }
@@ -982,7 +996,7 @@ int JdSolver::sqmr_core(int c, double shift, const double* rhs, double sign, dou
     int fl[2];
     AJD_CUDA(cudaMemcpyAsync(host_, scal_, sizeof(double) * S_NSCAL, cudaMemcpyDeviceToHost, s_));
     AJD_CUDA(cudaMemcpyAsync(host_ + S_NSCAL, flags_, sizeof(int) * 2, cudaMemcpyDeviceToHost, s_));
-    AJD_CUDA(cudaStreamSynchronize(s_));
+    AJD_TRY(wait_stream());
     std::memcpy(sc, host_, sizeof(sc));
     std::memcpy(fl, host_ + S_NSCAL, sizeof(fl));
     harvest_events();
@@ -1050,7 +1064,7 @@ int JdSolver::run(double* evals, double* evecs, jd_stats* st) {
     std::swap(AV_, AVt_);
     expand_h(Hh, hostla::congruence(m, c, compact(Hh, m), Qy), c);
     expand_h(Gh, hostla::congruence(m, c, compact(Gh, m), Qy), c);
-    AJD_CUDA(cudaStreamSynchronize(s_));  // Y_ is reused by the next upload
+    AJD_TRY(wait_stream());  // Y_ is reused by the next upload
     return JD_OK;
   };
   // Ritz extraction on the current basis: coefficient vectors Yc (m x m,
@@ -1366,7 +1380,7 @@ int JdSolver::lanczos(double* evals, double* evecs, jd_stats* st) {
       for (int i = 0; i < m; ++i) up[(size_t)q * kMaxM + i] = Z[(size_t)order[q] * m + i];
     AJD_CUDA(cudaMemcpyAsync(Y_, up.data(), sizeof(double) * kMaxM * kc, cudaMemcpyHostToDevice, s_));
     lincomb_kernel<<<nb_, kThreads, 0, s_>>>(V_, ld_, m, Y_, kMaxM, kc, Q_, ld_, n); count_launches();
-    AJD_CUDA(cudaStreamSynchronize(s_));
+    AJD_TRY(wait_stream());
   }
   if (st) {
     st->outer_its = steps;
@@ -1435,7 +1449,7 @@ int JdSolver::finalize(int kc, double* lam, double* evals, double* evecs, jd_sta
     double* x = Vt_ + (int64_t)j * ld_;
     AJD_CUDA(cudaMemcpyAsync(scal_ + 8, &signs[j], sizeof(double), cudaMemcpyHostToDevice, s_));
     scale_copy_kernel<<<nb_, kThreads, 0, s_>>>(x, x, n, scal_, 8, 0); count_launches();
-    AJD_CUDA(cudaStreamSynchronize(s_));
+    AJD_TRY(wait_stream());
   }
   double orth = 0.0;
   for (int j = 0; j < kout; ++j) {
@@ -1448,7 +1462,7 @@ int JdSolver::finalize(int kc, double* lam, double* evals, double* evecs, jd_sta
     for (int j = 0; j < kout; ++j)
       AJD_CUDA(cudaMemcpyAsync(evecs + (int64_t)j * n, Vt_ + (int64_t)j * ld_, sizeof(double) * n, cudaMemcpyDefault, s_));
   }
-  AJD_CUDA(cudaStreamSynchronize(s_));
+  AJD_TRY(wait_stream());
   if (st) {
     st->max_residual = max_res;
     st->orth_error = orth;
