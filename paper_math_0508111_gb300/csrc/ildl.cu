@@ -147,8 +147,8 @@ void free_dev(DevFactor<T>& d) {
   cudaFree(d.z);
   cudaFree(d.phases);
   cudaFree(d.bar);
-  cudaFree(d.w64);
-  cudaFree(d.z64);
+  cudaFree(d.wdf);
+  cudaFree(d.zdf);
   d = DevFactor<T>();
 }
 
@@ -190,19 +190,18 @@ int upload_factor(const HostFactor& F, DevFactor<T>& d, cudaStream_t st) {
   AJD_TRY(upload(&d.dense, F.dense_inv, st));
   const size_t nb = std::max<size_t>(1, F.n);
   const bool poison = std::getenv("AJD_POISON_ALLOC") != nullptr;  // NaN-filled work vectors (tests)
-  if constexpr (std::is_same<T, hi32_t>::value) {  // binary64 work vectors of the mixed apply
-    AJD_CUDA(cudaMalloc(&d.w64, nb * sizeof(double)));
-    AJD_CUDA(cudaMalloc(&d.z64, nb * sizeof(double)));
+  AJD_CUDA(cudaMalloc(&d.w, nb * sizeof(T)));
+  AJD_CUDA(cudaMalloc(&d.z, nb * sizeof(T)));
+  if (poison) {
+    AJD_CUDA(cudaMemsetAsync(d.w, 0xFF, nb * sizeof(T), st));
+    AJD_CUDA(cudaMemsetAsync(d.z, 0xFF, nb * sizeof(T), st));
+  }
+  if (sizeof(T) == 4) {  // float-float work vectors of the mixed apply
+    AJD_CUDA(cudaMalloc(&d.wdf, nb * sizeof(float2)));
+    AJD_CUDA(cudaMalloc(&d.zdf, nb * sizeof(float2)));
     if (poison) {
-      AJD_CUDA(cudaMemsetAsync(d.w64, 0xFF, nb * sizeof(double), st));
-      AJD_CUDA(cudaMemsetAsync(d.z64, 0xFF, nb * sizeof(double), st));
-    }
-  } else {
-    AJD_CUDA(cudaMalloc(&d.w, nb * sizeof(T)));
-    AJD_CUDA(cudaMalloc(&d.z, nb * sizeof(T)));
-    if (poison) {
-      AJD_CUDA(cudaMemsetAsync(d.w, 0xFF, nb * sizeof(T), st));
-      AJD_CUDA(cudaMemsetAsync(d.z, 0xFF, nb * sizeof(T), st));
+      AJD_CUDA(cudaMemsetAsync(d.wdf, 0xFF, nb * sizeof(float2), st));
+      AJD_CUDA(cudaMemsetAsync(d.zdf, 0xFF, nb * sizeof(float2), st));
     }
   }
   // phase list of the persistent apply
@@ -248,8 +247,7 @@ int upload_factor(const HostFactor& F, DevFactor<T>& d, cudaStream_t st) {
   AJD_CUDA(cudaMemsetAsync(d.bar, 0, 96 * sizeof(unsigned), st));
   AJD_CUDA(cudaStreamSynchronize(st));
   int per_sm = 0;
-  using XT = typename std::conditional<std::is_same<T, hi32_t>::value, double, T>::type;
-  AJD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ildl_apply_persistent_kernel<T, XT, XT>, kPersistThreads, 0));
+  AJD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ildl_apply_persistent_kernel<T, T, T>, kPersistThreads, 0));
   if (per_sm < 1) return fail(JD_EDEVICE, "ildl: persistent apply kernel cannot be resident");
   d.grid = sm_count();  // one CTA per SM
   d.ready = true;
@@ -332,16 +330,17 @@ int ildl_apply_dev(const ildl_s* f, const T* b, T* out, cudaStream_t s) {
 }
 
 int ildl_apply_dev_mixed(const ildl_s* f, const double* b, double* out, cudaStream_t s) {
-  const DevFactor<hi32_t>& d = f->dh;
-  if (!d.w64) return fail(JD_EINVAL, "ildl_apply: no mixed-precision work vectors");
-  return launch_apply<hi32_t, double, double>(f, d, d.w64, d.z64, b, out, s);
+  const DevFactor<float>& d = f->d32;
+  if (!d.wdf) return fail(JD_EINVAL, "ildl_apply: no mixed-precision work vectors");
+  return launch_apply<float, df64, double>(f, d, reinterpret_cast<df64*>(d.wdf), reinterpret_cast<df64*>(d.zdf), b,
+                                           out, s);
 }
 
 // Timeout flag of the persistent apply (sticky until cleared): JD_EDEVICE if
 // a grid barrier gave up.
 int ildl_check_device_error(const ildl_s* f) {
-  for (int prec = 0; prec < 3; ++prec) {
-    const unsigned* bar = prec == 0 ? f->d64.bar : prec == 1 ? f->d32.bar : f->dh.bar;
+  for (int prec = 0; prec < 2; ++prec) {
+    const unsigned* bar = prec == 0 ? f->d64.bar : f->d32.bar;
     if (!bar) continue;
     int e = 0;
     AJD_CUDA(cudaMemcpy(&e, bar + 64, sizeof(int), cudaMemcpyDeviceToHost));
@@ -398,14 +397,12 @@ int ildl_upload_all(ildl_s* f, cudaStream_t st, int copies) {
   }
   if (copies & kCopyF64) AJD_TRY(upload_factor<double>(f->F, f->d64, st));
   if (copies & kCopyF32) AJD_TRY(upload_factor<float>(f->F, f->d32, st));
-  if (copies & kCopyMixed) AJD_TRY(upload_factor<hi32_t>(f->F, f->dh, st));
   return JD_OK;
 }
 
 void ildl_free_device(ildl_s* f) {
   free_dev(f->d64);
   free_dev(f->d32);
-  free_dev(f->dh);
 }
 
 // CSR of A - sigma I for a lattice (host, from the binary64 potential).
@@ -664,7 +661,7 @@ extern "C" int ildl_destroy(ildl_t f) {
   if (!f) return JD_OK;
   int dev = 0;
   cudaGetDevice(&dev);
-  if (f->d64.ready || f->d32.ready || f->dh.ready) {
+  if (f->d64.ready || f->d32.ready) {
     cudaSetDevice(f->device);
     ildl_free_device(f);
     cudaSetDevice(dev);
@@ -772,8 +769,8 @@ extern "C" int ildl_apply_noalloc(ildl_t f, const void* b, void* x, int precisio
                                              scratch, s);
   }
   if (precision == JD_MIXED) {
-    if (!f->dh.ready) return fail(JD_EINVAL, "ildl_apply_noalloc: factor has no device copy");
-    return launch_apply_static<hi32_t, double, double>(f, f->dh, static_cast<const double*>(b), static_cast<double*>(x),
+    if (!f->d32.ready) return fail(JD_EINVAL, "ildl_apply_noalloc: factor has no device copy");
+    return launch_apply_static<float, df64, double>(f, f->d32, static_cast<const double*>(b), static_cast<double*>(x),
                                               scratch, s);
   }
   return fail(JD_EINVAL, "ildl_apply_noalloc: unknown precision %d", precision);

@@ -7,22 +7,6 @@
 
 namespace ajd {
 
-// A binary64 value stored as its upper 32 bits (sign, 11-bit exponent, 20
-// mantissa bits), rounded to nearest-even from the full value: half the
-// bytes of a binary64 entry, the full binary64 range, 21 significant bits,
-// and widening back to binary64 is a register move (no conversion
-// instruction).  Used for the factor values of the mixed apply.
-struct hi32_t {
-  unsigned u = 0;
-  hi32_t() = default;
-  explicit hi32_t(double x) {
-    uint64_t b;
-    std::memcpy(&b, &x, sizeof(b));
-    b += 0x7FFFFFFFull + ((b >> 32) & 1ull);  // round the dropped low word, ties to even
-    u = (unsigned)(b >> 32);
-  }
-};
-
 // Device copy of a HostFactor in one precision.
 template <typename T>
 struct DevFactor {
@@ -45,8 +29,8 @@ struct DevFactor {
   int nphase = 0;
   unsigned* bar = nullptr;  // [0] arrivals, [32] generation, [64] timeout flag
   int grid = 0;
-  double* w64 = nullptr;  // binary64 work vectors of the mixed apply (hi32_t factor)
-  double* z64 = nullptr;
+  float2* wdf = nullptr;  // float-float work vectors of the mixed apply (binary32 copy only)
+  float2* zdf = nullptr;
 };
 
 }  // namespace ajd
@@ -55,8 +39,7 @@ struct ildl_s {
   ajd::HostFactor F;
   int device = 0;
   ajd::DevFactor<double> d64;
-  ajd::DevFactor<float> d32;
-  ajd::DevFactor<ajd::hi32_t> dh;  // mixed apply: binary64 sums over hi32_t values
+  ajd::DevFactor<float> d32;  // also the mixed apply (float-float work vectors)
   template <typename T>
   const ajd::DevFactor<T>& dev() const {
     if constexpr (sizeof(T) == 8) return d64;
@@ -70,16 +53,17 @@ namespace ajd {
 template <typename T>
 int ildl_apply_dev(const ildl_s* f, const T* b, T* out, cudaStream_t stream);
 
-// x = K^{-1} b with the factor values stored as hi32_t, binary64 vectors
-// and sums.
+// x = K^{-1} b with the binary32 factor, float-float work vectors and
+// sums, binary64 b and x.
 int ildl_apply_dev_mixed(const ildl_s* f, const double* b, double* out, cudaStream_t stream);
 
-// Device copies of a factor: binary64, binary32, mixed (hi32_t values).
-constexpr int kCopyF64 = 1, kCopyF32 = 2, kCopyMixed = 4, kCopyAll = 7;
+// Device copies of a factor: binary64, binary32 (which the mixed apply
+// shares: binary32 values, float-float work vectors).
+constexpr int kCopyF64 = 1, kCopyF32 = 2, kCopyAll = 3;
 
 // The copy a solve in `precision` (JD_FP64, JD_FP32, JD_MIXED) applies.
 inline int copy_for_precision(int precision) {
-  return precision == JD_FP32 ? kCopyF32 : precision == JD_MIXED ? kCopyMixed : kCopyF64;
+  return precision == JD_FP32 || precision == JD_MIXED ? kCopyF32 : kCopyF64;
 }
 
 // ildl_create with its device work on stream `st`, uploading only the
