@@ -506,7 +506,8 @@ def main():
                 "config": {"workload": workload, "model": args.model,
                            "L": L, "W": W if args.model == "diagonal" else None, "k": k, "sigma": sigma, "tol": tol,
                            "bc": args.bc,
-                           "precision": {"mixed": "mixed: binary32 preconditioner, binary64 vectors/stencil/outer",
+                           "precision": {"mixed": "mixed: binary32 factor applied with float-float sums, binary64 "
+                                                  "SQMR vectors/stencil/outer",
                                          "fp32": "binary32 inner solve (stencil, preconditioner, SQMR), binary64 outer",
                                          "fp64": "binary64 throughout"}[args.precision],
                            "step": "one realisation solved completely (preconditioner setup + Jacobi-Davidson); "

@@ -55,8 +55,9 @@ extern "C" {
 
 #define JD_FP64 0  /* arithmetic in binary64                                  */
 #define JD_FP32 1  /* arithmetic in binary32 (vectors and potential in FP32)  */
-#define JD_MIXED 2 /* jd_solve only: binary32 preconditioner application,
-                      binary64 everything else                                */
+#define JD_MIXED 2 /* binary32 factor values applied with float-float
+                      (hi + lo, ~48-bit) work vectors and sums; SQMR vectors,
+                      stencil and everything else binary64                    */
 
 /* Message of the last failing call on this thread ("" if none). */
 const char* jd_last_error(void);
@@ -260,8 +261,8 @@ int ildl_export(ildl_t f, int* perm, double* scale, int* level_ptr, int64_t* Lpt
  * diagonal and dense solves, one parallel step per level of L^T (backward),
  * and one scatter/scale pass.
  *   b, x       device pointers, n elements each, distinct; binary64 for
- *              JD_FP64 and JD_MIXED (binary32 factor, binary64 vectors and
- *              sums), binary32 for JD_FP32.
+ *              JD_FP64 and JD_MIXED (binary32 factor, float-float work
+ *              vectors and sums), binary32 for JD_FP32.
  * Errors: JD_EINVAL (no device copy, bad precision), JD_EDEVICE.
  */
 int ildl_apply(ildl_t f, const void* b, void* x, int precision, void* stream);
@@ -312,8 +313,9 @@ typedef struct {
                          the Ritz value theta afterwards [1e-3]                */
   int precision;      /* inner solve: JD_FP64 (all binary64), JD_FP32
                          (stencil, preconditioner and SQMR in binary32) or
-                         JD_MIXED (preconditioner in binary32, SQMR vectors
-                         and stencil in binary64); the outer residual, Ritz
+                         JD_MIXED (binary32 factor applied with float-float
+                         sums; SQMR vectors and stencil in binary64); the
+                         outer residual, Ritz
                          projection and orthogonalisation are always
                          binary64 [JD_FP64]                                   */
   uint64_t seed;      /* start vector seed (0 = derived from the lattice seed)*/

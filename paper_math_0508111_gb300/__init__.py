@@ -232,8 +232,8 @@ class Preconditioner:
 
     def apply(self, b, out=None, stream=None, mixed=False):
         """x = K^{-1} b for a CUDA tensor b (float64 or float32, length n).
-        ``mixed=True`` (float64 b) applies the binary32 factor with binary64
-        vectors and sums."""
+        ``mixed=True`` (float64 b) applies the binary32 factor with
+        float-float (about 48-bit) work vectors and sums."""
         import torch
         if out is None:
             out = torch.empty_like(b)

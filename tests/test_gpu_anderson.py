@@ -51,8 +51,9 @@ def _check_stencil(ajd, L, W, seed, bc, shift, m, dtype):
 
 
 @pytest.mark.parametrize("L,bc", [(3, 0), (4, 0), (5, 1), (10, 0), (10, 1), (33, 0), (37, 1), (64, 0),
-                                  # plane-tile kernel: 16-byte rows, tiles past L (L % 8 != 0), hard walls,
-                                  # several x-segments per row (L > 128 binary32, > 64 binary64)
+                                  # L >= 16 with 16-byte rows runs the plane-tile kernel: tiles past L
+                                  # (L % 8 != 0), hard walls, several x-segments per row (L > 128 binary32,
+                                  # > 64 binary64); L = 8, 12 exercise the row-marching kernel
                                   (8, 0), (12, 1), (20, 1), (24, 0), (132, 1), (136, 0)])
 @pytest.mark.parametrize("dtype_name", ["float64", "float32"])
 def test_stencil_matches_oracle(ajd, L, bc, dtype_name):
