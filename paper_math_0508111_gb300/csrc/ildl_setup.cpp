@@ -860,41 +860,51 @@ int build_ildl(const SymCsr& A, const ildl_params& prm, HostFactor& F, bool dens
     // 7. Schur complement S' = S_CC - L_F D_B L_F^T (upper triangle, then
     // mirrored so that S' is exactly symmetric), dropped at tau off the
     // diagonal.  Column access to L_F per B block:
-    std::vector<int64_t> cptr(acc.size() + 1, 0);
-    for (int64_t p = 0; p < (int64_t)lnode.size(); ++p) cptr[blk_of[lnode[p]] + 1]++;
-    for (size_t b = 0; b < acc.size(); ++b) cptr[b + 1] += cptr[b];
-    std::vector<int> crow(lnode.size());
-    std::vector<double> c1(lnode.size(), 0.0), c2(lnode.size(), 0.0);
-    {
-      // one record per (block, C row): values for node a and node b
-      std::vector<int64_t> fillp(cptr.begin(), cptr.end() - 1);
-      std::vector<int64_t> last_slot(acc.size(), -1);
-      std::vector<int> last_row(acc.size(), -1);
-      for (int r = 0; r < mc_n; ++r)
-        for (int64_t p = lptr[r]; p < lptr[r + 1]; ++p) {
-          const int b = blk_of[lnode[p]];
-          int64_t slot;
-          if (last_row[b] == r) slot = last_slot[b];
-          else { slot = fillp[b]++; last_row[b] = r; last_slot[b] = slot; crow[slot] = r; }
-          if (lnode[p] == cands[acc[b]].a) c1[slot] = lval[p];
-          else c2[slot] = lval[p];
-        }
-      // compact: records per block are fillp[b] - cptr[b]
-      std::vector<int64_t> nptr(acc.size() + 1, 0);
-      for (size_t b = 0; b < acc.size(); ++b) nptr[b + 1] = nptr[b] + (fillp[b] - cptr[b]);
-      std::vector<int> crow2(nptr.back());
-      std::vector<double> c12(nptr.back()), c22(nptr.back());
-      for (size_t b = 0; b < acc.size(); ++b)
-        for (int64_t t = 0; t < fillp[b] - cptr[b]; ++t) {
-          crow2[nptr[b] + t] = crow[cptr[b] + t];
-          c12[nptr[b] + t] = c1[cptr[b] + t];
-          c22[nptr[b] + t] = c2[cptr[b] + t];
-        }
-      cptr.swap(nptr);
-      crow.swap(crow2);
-      c1.swap(c12);
-      c2.swap(c22);
+    // One record per (block, C row) -- the row's L_F values for the block's
+    // nodes a and b -- grouped by block with rows ascending: the entries of
+    // a row are ordered by block (a block's one or two nodes adjacent), so
+    // the records are the runs of equal block; built per row in parallel and
+    // grouped by a stable parallel scatter.
+    std::vector<int64_t> rrec(mc_n + 1, 0);
+#pragma omp parallel for schedule(static)
+    for (int r = 0; r < mc_n; ++r) {
+      int cnt = 0, last = -1;
+      for (int64_t p = lptr[r]; p < lptr[r + 1]; ++p) {
+        const int b = blk_of[lnode[p]];
+        if (b != last) { ++cnt; last = b; }
+      }
+      rrec[r + 1] = cnt;
     }
+    for (int r = 0; r < mc_n; ++r) rrec[r + 1] += rrec[r];
+    const int64_t nrec = rrec[mc_n];
+    dvec<int> rec_row(nrec), rec_blk(nrec);
+    dvec<double> rec_a(nrec), rec_b(nrec);
+#pragma omp parallel for schedule(static)
+    for (int r = 0; r < mc_n; ++r) {
+      int64_t q = rrec[r] - 1;
+      int last = -1;
+      for (int64_t p = lptr[r]; p < lptr[r + 1]; ++p) {
+        const int b = blk_of[lnode[p]];
+        if (b != last) {
+          ++q;
+          last = b;
+          rec_row[q] = r;
+          rec_blk[q] = b;
+          rec_a[q] = 0.0;
+          rec_b[q] = 0.0;
+        }
+        if (lnode[p] == cands[acc[b]].a) rec_a[q] = lval[p];
+        else rec_b[q] = lval[p];
+      }
+    }
+    std::vector<int64_t> cptr;
+    dvec<int> crow(nrec);
+    dvec<double> c1(nrec), c2(nrec);
+    stable_scatter(nrec, (int)acc.size(), [&](int64_t i) { return rec_blk[i]; }, cptr, [&](int64_t i, int64_t slot) {
+      crow[slot] = rec_row[i];
+      c1[slot] = rec_a[i];
+      c2[slot] = rec_b[i];
+    });
     const double ts_rec = ms_since(t_schur);
     SymCsr U;  // upper triangle of S'
     U.n = mc_n;
@@ -961,14 +971,22 @@ int build_ildl(const SymCsr& A, const ildl_params& prm, HostFactor& F, bool dens
                 accv[q] -= wa * c1[t] + wb * c2[t];
               }
             }
+            // drop first, then sort only the entries that stay
+            size_t keep = 0;
+            for (int c : cols) {
+              if (c == r || std::fabs(accv[c]) >= tau) {
+                cols[keep++] = c;
+              } else {
+                accv[c] = 0.0;
+                mark[c] = 0;
+              }
+            }
+            cols.resize(keep);
             std::sort(cols.begin(), cols.end());
             const size_t before = ucol[ch].size();
             for (int c : cols) {
-              const double val = accv[c];
-              if (c == r || std::fabs(val) >= tau) {
-                ucol[ch].push_back(c);
-                uval[ch].push_back(val);
-              }
+              ucol[ch].push_back(c);
+              uval[ch].push_back(accv[c]);
               accv[c] = 0.0;
               mark[c] = 0;
             }
