@@ -585,7 +585,11 @@ int build_ildl(const SymCsr& A, const ildl_params& prm, HostFactor& F, bool dens
   std::vector<double> dd(n, 0.0), dof(n, 0.0);
   std::vector<int> part(n, -1);    // partner original id
   std::vector<double> sc(n, 1.0);  // final scaling of each original node
-  std::vector<Trip> trips;
+  // entries of L as (row, column, value) in original numbering, appended
+  // level by level; room for a typical fill is reserved up front (pages are
+  // only touched when written) so that growing it rarely copies
+  dvec<Trip> trips;
+  trips.reserve((size_t)n * 64);
   double t_match = 0.0;
 
   const bool verbose = std::getenv("AJD_SETUP_VERBOSE") != nullptr;
