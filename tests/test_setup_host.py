@@ -132,3 +132,26 @@ def test_setup_rejects_bad_input(ajd):
         ajd.Preconditioner.from_csr(np.array([0, 1]), np.array([0]), np.array([1.0]), kappa=0.5)
     with pytest.raises(ajd.JDError):
         ajd.Preconditioner.from_csr(np.array([0, 2, 3]), np.array([1, 0, 1]), np.array([1.0, 2.0, 1.0]))
+
+
+def test_setup_independent_of_thread_count(ajd):
+    """The parallel setup (matching searches in batches, parallel scatters,
+    per-chunk rows) gives the same factor, bit for bit, with 1 and 4 host
+    threads."""
+    import ctypes
+    import ctypes.util
+    gomp = ctypes.CDLL(ctypes.util.find_library("gomp") or "libgomp.so.1")
+    A, _ = _csr(14, 12.0, 6, PERIODIC, 0.2)
+    out = []
+    try:
+        for t in (1, 4):
+            gomp.omp_set_num_threads(t)
+            out.append(ajd.Preconditioner.from_csr(A.indptr, A.indices, A.data, n_dense=200).export())
+    finally:
+        gomp.omp_set_num_threads(max(1, __import__("os").cpu_count() or 1))
+    assert out[0]["levels"] >= 3
+    for key in out[0]:
+        if key.endswith("_ms"):  # timings
+            continue
+        a, b = np.asarray(out[0][key]), np.asarray(out[1][key])
+        assert a.shape == b.shape and np.array_equal(a, b), key
