@@ -904,10 +904,12 @@ int build_ildl(const SymCsr& A, const ildl_params& prm, HostFactor& F, bool dens
     std::vector<int64_t> cptr;
     dvec<int> crow(nrec);
     dvec<double> c1(nrec), c2(nrec);
+    dvec<int64_t> rec_slot(nrec);  // where record i (row order) sits in its block's list
     stable_scatter(nrec, (int)acc.size(), [&](int64_t i) { return rec_blk[i]; }, cptr, [&](int64_t i, int64_t slot) {
       crow[slot] = rec_row[i];
       c1[slot] = rec_a[i];
       c2[slot] = rec_b[i];
+      rec_slot[i] = slot;
     });
     const double ts_rec = ms_since(t_schur);
     SymCsr U;  // upper triangle of S'
@@ -922,7 +924,6 @@ int build_ildl(const SymCsr& A, const ildl_params& prm, HostFactor& F, bool dens
         std::vector<double> accv(mc_n, 0.0);
         std::vector<char> mark(mc_n, 0);
         std::vector<int> cols;
-        std::vector<int> rowblocks;
 #pragma omp for schedule(dynamic, 1)
         for (int ch = 0; ch < nchunk; ++ch) {
           const int r0 = (int)((int64_t)mc_n * ch / nchunk), r1 = (int)((int64_t)mc_n * (ch + 1) / nchunk);
@@ -951,17 +952,12 @@ int build_ildl(const SymCsr& A, const ildl_params& prm, HostFactor& F, bool dens
               accv[c] += S.val[p];
             }
             if (!mark[r]) { mark[r] = 1; cols.push_back(r); }
-            // blocks in row r of L_F with their (l_a, l_b) values
-            rowblocks.clear();
-            for (int64_t p = lptr[r]; p < lptr[r + 1]; ++p) {
-              const int b = blk_of[lnode[p]];
-              if (rowblocks.empty() || rowblocks.back() != b) rowblocks.push_back(b);
-            }
-            for (int b : rowblocks) {
-              // this row's record in block b's column list (rows ascending)
-              const int* cb = crow.data() + cptr[b];
-              const int* ce = crow.data() + cptr[b + 1];
-              const int64_t me = std::lower_bound(cb, ce, r) - crow.data();
+            // the blocks of row r of L_F (its records, in block order) with
+            // their (l_a, l_b) values; `me` is the row's record in the
+            // block's column list (rows ascending)
+            for (int64_t i = rrec[r]; i < rrec[r + 1]; ++i) {
+              const int b = rec_blk[i];
+              const int64_t me = rec_slot[i];
               const double la = c1[me], lb = c2[me];
               double wa, wb;  // (l_a, l_b) * D_b
               if (cands[acc[b]].b < 0) { wa = la * bmat[3 * b]; wb = 0.0; }
