@@ -5,7 +5,7 @@
 
 ``apply`` builds the preconditioner of A - 0 I for an L^3 lattice (W = 16.5,
 seed 1) and times its application in binary32, binary64 and the mixed form
-(factor values as rounded upper words, binary64 vectors and sums): 3 warm-up
+(binary32 factor values, float-float work vectors and sums): 3 warm-up
 applications each, then ``reps`` timed ones, CUDA events on the current
 stream.  ``stencil`` times y = A x in binary64
 and binary32 with the L2 flushed before every repetition.  Both print one
