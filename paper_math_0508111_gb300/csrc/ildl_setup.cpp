@@ -28,6 +28,7 @@
 #include <cmath>
 #include <cstring>
 #include <limits>
+#include <memory>
 #include <numeric>
 #include <queue>
 #include <utility>
@@ -49,6 +50,15 @@ double ms_since(Clock::time_point t0) {
 }
 
 constexpr double kInf = std::numeric_limits<double>::infinity();
+
+// Resize a buffer whose contents are about to be overwritten: within its
+// capacity nothing moves; beyond it the old block is released first (no
+// copy of stale contents, no second block alive at once).
+template <class V>
+void resize_discard(V& v, size_t n) {
+  if (n > v.capacity()) V().swap(v);
+  v.resize(n);
+}
 
 double lookup(const SymCsr& S, int i, int j) {
   const int* b = S.col.data() + S.ptr[i];
@@ -98,7 +108,9 @@ inline double log_pos(double x) {
 // path per unmatched row over reduced costs c_ij - u_i - v_j >= 0.
 // ---------------------------------------------------------------------------
 int max_product_matching(const SymCsr& A, std::vector<int>& match_col, std::vector<double>& u,
-                         std::vector<double>& v, std::vector<double>& rowmax) {
+                         std::vector<double>& v, std::vector<double>& rowmax, MatchWork* work) {
+  MatchWork local;
+  MatchWork& mw = work ? *work : local;
   const int n = A.n;
   rowmax.assign(n, 0.0);
   std::vector<double> logmax(n);
@@ -111,7 +123,10 @@ int max_product_matching(const SymCsr& A, std::vector<int>& match_col, std::vect
     logmax[i] = log_pos(r);
   }
   // cost of entry p (row i, column col[p]); +inf for explicit zeros
-  dvec<double> cost(A.val.size()), loga(A.val.size());  // filled (first touched) in parallel below
+  dvec<double>& cost = mw.cost;  // filled (first touched) in parallel below
+  dvec<double>& loga = mw.loga;
+  resize_discard(cost, A.val.size());
+  resize_discard(loga, A.val.size());
 #pragma omp parallel for schedule(static)
   for (int i = 0; i < n; ++i)
     for (int64_t p = A.ptr[i]; p < A.ptr[i + 1]; ++p) {
@@ -201,18 +216,15 @@ int max_product_matching(const SymCsr& A, std::vector<int>& match_col, std::vect
     std::vector<int> touched, scanned, tree_rows, path;  // path: (row, col) pairs from the sink back
     std::vector<double> tree_d, scanned_d;
   };
-  struct Work {
-    std::vector<double> dist;
-    std::vector<int> pred;
-    std::vector<char> done;
-  };
+  using Work = MatchWork::Search;
   const int nthreads = std::max(1, omp_get_max_threads());
-  std::vector<Work> work(nthreads);
+  if ((int)mw.threads.size() < nthreads) mw.threads.resize(nthreads);
+  std::vector<Work>& tw = mw.threads;
   auto search = [&](Work& W, Search& R) {
-    if (W.dist.empty()) {
-      W.dist.assign(n, kInf);
-      W.pred.assign(n, -1);
-      W.done.assign(n, 0);
+    if (W.dist.size() < (size_t)n) {  // grown entries start at rest
+      W.dist.resize(n, kInf);
+      W.pred.resize(n, -1);
+      W.done.resize(n, 0);
     }
     using Item = std::pair<double, int>;
     std::priority_queue<Item, std::vector<Item>, std::greater<Item>> heap;
@@ -296,7 +308,7 @@ int max_product_matching(const SymCsr& A, std::vector<int>& match_col, std::vect
 #pragma omp parallel for schedule(dynamic, 1)
     for (size_t t = 0; t < rows.size(); ++t) {
       batch[t].s = rows[t];
-      search(work[omp_get_thread_num()], batch[t]);
+      search(tw[omp_get_thread_num()], batch[t]);
     }
     ++epoch;
     for (size_t t = 0; t < rows.size(); ++t) {
@@ -592,6 +604,27 @@ int build_ildl(const SymCsr& A, const ildl_params& prm, HostFactor& F, bool dens
   trips.reserve((size_t)n * 64);
   double t_match = 0.0;
 
+  // per-level scratch kept across levels: the levels shrink, so after the
+  // first few every buffer is reused from memory that is already mapped
+  // (fresh large blocks would fault in every page again at every level)
+  MatchWork mwork;
+  SymCsr Snext;                                      // next level's S
+  dvec<int> lnode;                                   // L_F: B node (local index)
+  dvec<double> lval;
+  std::vector<std::vector<int>> cn, ucol;            // per-chunk row output
+  std::vector<std::vector<double>> cv, uval;
+  dvec<int> rec_row, rec_blk, crow;                  // Schur records
+  dvec<double> rec_a, rec_b, c1, c2;
+  dvec<int64_t> rec_slot;
+  std::vector<unsigned> mirror_cnt;
+  struct RowWork {                                   // per thread; accv and mark all zero at rest
+    std::vector<double> accv;
+    std::vector<char> mark;
+    std::unique_ptr<int[]> cols;                      // uninitialised
+    int cap = 0;
+  };
+  std::vector<RowWork> rwork(std::max(1, omp_get_max_threads()));
+
   const bool verbose = std::getenv("AJD_SETUP_VERBOSE") != nullptr;
   int level = 0;
   for (;; ++level) {
@@ -609,7 +642,7 @@ int build_ildl(const SymCsr& A, const ildl_params& prm, HostFactor& F, bool dens
     std::vector<std::pair<int, int>> groups;
     const bool use_matching = prm.matching != 0 && (prm.matching < 0 || level < prm.matching);
     if (use_matching) {
-      max_product_matching(S, mc, u, v, rmax);
+      max_product_matching(S, mc, u, v, rmax, &mwork);
       for (int i = 0; i < m; ++i) d[i] = std::sqrt(std::exp(u[i] + v[i]) / rmax[i]);
       if (level == 0)
         for (int j = 0; j < m; ++j) F.n_matched_offdiag += (mc[j] != j);
@@ -792,12 +825,14 @@ int build_ildl(const SymCsr& A, const ildl_params& prm, HostFactor& F, bool dens
     // 6. L_F = F D_B^{-1} row by row (rows: C nodes), dropped at tau.
     // Entries: (C row, B node, value) with the B node's block.
     std::vector<int64_t> lptr(mc_n + 1, 0);
-    dvec<int> lnode;    // B node (local index)
-    dvec<double> lval;
     const int nchunk = std::max(1, std::min(mc_n, 8 * omp_get_max_threads()));
+    if ((int)cn.size() < nchunk) {
+      cn.resize(nchunk);
+      cv.resize(nchunk);
+      ucol.resize(nchunk);
+      uval.resize(nchunk);
+    }
     {
-      std::vector<std::vector<int>> cn(nchunk);
-      std::vector<std::vector<double>> cv(nchunk);
       std::vector<int> rowcnt(mc_n, 0);
 #pragma omp parallel
       {
@@ -806,6 +841,8 @@ int build_ildl(const SymCsr& A, const ildl_params& prm, HostFactor& F, bool dens
 #pragma omp for schedule(dynamic, 1)
         for (int ch = 0; ch < nchunk; ++ch) {
           const int r0 = (int)((int64_t)mc_n * ch / nchunk), r1 = (int)((int64_t)mc_n * (ch + 1) / nchunk);
+          cn[ch].clear();
+          cv[ch].clear();
           for (int r = r0; r < r1; ++r) {
             const int k = cnodes[r];
             touched.clear();
@@ -840,8 +877,8 @@ int build_ildl(const SymCsr& A, const ildl_params& prm, HostFactor& F, bool dens
       for (int r = 0; r < mc_n; ++r) lptr[r + 1] = lptr[r] + rowcnt[r];
       // chunks hold consecutive rows, so chunk ch starts at the row pointer of
       // its first row; copied in parallel
-      lnode.resize(lptr[mc_n]);
-      lval.resize(lptr[mc_n]);
+      resize_discard(lnode, lptr[mc_n]);
+      resize_discard(lval, lptr[mc_n]);
 #pragma omp parallel for schedule(dynamic, 1)
       for (int ch = 0; ch < nchunk; ++ch) {
         const int r0 = (int)((int64_t)mc_n * ch / nchunk);
@@ -881,8 +918,10 @@ int build_ildl(const SymCsr& A, const ildl_params& prm, HostFactor& F, bool dens
     }
     for (int r = 0; r < mc_n; ++r) rrec[r + 1] += rrec[r];
     const int64_t nrec = rrec[mc_n];
-    dvec<int> rec_row(nrec), rec_blk(nrec);
-    dvec<double> rec_a(nrec), rec_b(nrec);
+    resize_discard(rec_row, nrec);
+    resize_discard(rec_blk, nrec);
+    resize_discard(rec_a, nrec);
+    resize_discard(rec_b, nrec);
 #pragma omp parallel for schedule(static)
     for (int r = 0; r < mc_n; ++r) {
       int64_t q = rrec[r] - 1;
@@ -902,9 +941,10 @@ int build_ildl(const SymCsr& A, const ildl_params& prm, HostFactor& F, bool dens
       }
     }
     std::vector<int64_t> cptr;
-    dvec<int> crow(nrec);
-    dvec<double> c1(nrec), c2(nrec);
-    dvec<int64_t> rec_slot(nrec);  // where record i (row order) sits in its block's list
+    resize_discard(crow, nrec);
+    resize_discard(c1, nrec);
+    resize_discard(c2, nrec);
+    resize_discard(rec_slot, nrec);  // where record i (row order) sits in its block's list
     stable_scatter(nrec, (int)acc.size(), [&](int64_t i) { return rec_blk[i]; }, cptr, [&](int64_t i, int64_t slot) {
       crow[slot] = rec_row[i];
       c1[slot] = rec_a[i];
@@ -912,21 +952,34 @@ int build_ildl(const SymCsr& A, const ildl_params& prm, HostFactor& F, bool dens
       rec_slot[i] = slot;
     });
     const double ts_rec = ms_since(t_schur);
-    SymCsr U;  // upper triangle of S'
-    U.n = mc_n;
-    U.ptr.assign(mc_n + 1, 0);
+    // upper triangle of S', row by row: chunk ch holds the rows of its row
+    // range in order; rowcnt[r] entries per row (diagonal included)
+    std::vector<int> rowcnt(mc_n, 0);
+    // a new row is typically as long as the old ones: room for about 3/4 of
+    // an old row per upper row, so that the chunk buffers rarely grow
+    const double upper_guess = 0.75 * (double)S.ptr[m] / m + 8.0;
     {
-      std::vector<std::vector<int>> ucol(nchunk);
-      std::vector<std::vector<double>> uval(nchunk);
-      std::vector<int> rowcnt(mc_n, 0);
 #pragma omp parallel
       {
-        std::vector<double> accv(mc_n, 0.0);
-        std::vector<char> mark(mc_n, 0);
-        std::vector<int> cols;
+        RowWork& rw = rwork[omp_get_thread_num()];
+        if (rw.cap < mc_n) {
+          rw.accv.assign(mc_n, 0.0);
+          rw.mark.assign(mc_n, 0);
+          // the row's columns in first-touch order; never more than mc_n,
+          // and written ahead of the count (below), so left uninitialised
+          rw.cols.reset(new int[(size_t)mc_n + 1]);
+          rw.cap = mc_n;
+        }
+        double* const accv = rw.accv.data();
+        char* const mark = rw.mark.data();
+        int* const cols = rw.cols.get();
 #pragma omp for schedule(dynamic, 1)
         for (int ch = 0; ch < nchunk; ++ch) {
           const int r0 = (int)((int64_t)mc_n * ch / nchunk), r1 = (int)((int64_t)mc_n * (ch + 1) / nchunk);
+          ucol[ch].clear();
+          uval[ch].clear();
+          ucol[ch].reserve((size_t)((r1 - r0) * upper_guess));
+          uval[ch].reserve((size_t)((r1 - r0) * upper_guess));
           for (int r = r0; r < r1; ++r) {
             const int k = cnodes[r];
             if (lptr[r] == lptr[r + 1]) {
@@ -944,14 +997,14 @@ int build_ildl(const SymCsr& A, const ildl_params& prm, HostFactor& F, bool dens
               rowcnt[r] = (int)(ucol[ch].size() - before);
               continue;
             }
-            cols.clear();
+            int nc = 0;
             for (int64_t p = S.ptr[k]; p < S.ptr[k + 1]; ++p) {
               const int c = cidx[S.col[p]];
               if (c < r) continue;  // B columns have cidx -1
-              if (!mark[c]) { mark[c] = 1; cols.push_back(c); }
+              if (!mark[c]) { mark[c] = 1; cols[nc++] = c; }
               accv[c] += S.val[p];
             }
-            if (!mark[r]) { mark[r] = 1; cols.push_back(r); }
+            if (!mark[r]) { mark[r] = 1; cols[nc++] = r; }
             // the blocks of row r of L_F (its records, in block order) with
             // their (l_a, l_b) values; `me` is the row's record in the
             // block's column list (rows ascending)
@@ -965,26 +1018,34 @@ int build_ildl(const SymCsr& A, const ildl_params& prm, HostFactor& F, bool dens
                 wa = la * bmat[3 * b] + lb * bmat[3 * b + 1];
                 wb = la * bmat[3 * b + 1] + lb * bmat[3 * b + 2];
               }
-              for (int64_t t = me; t < cptr[b + 1]; ++t) {
+              // about half the updates reach a column for the first time:
+              // the column is stored unconditionally and counted only then
+              // (no unpredictable branch)
+              const int64_t te = cptr[b + 1];
+              for (int64_t t = me; t < te; ++t) {
                 const int q = crow[t];  // q >= r because rows are ascending
-                if (!mark[q]) { mark[q] = 1; cols.push_back(q); }
+                cols[nc] = q;
+                nc += !mark[q];
+                mark[q] = 1;
                 accv[q] -= wa * c1[t] + wb * c2[t];
               }
             }
-            // drop first, then sort only the entries that stay
-            size_t keep = 0;
-            for (int c : cols) {
-              if (c == r || std::fabs(accv[c]) >= tau) {
-                cols[keep++] = c;
-              } else {
-                accv[c] = 0.0;
-                mark[c] = 0;
-              }
+            // drop first (branch-free: a dropped column is cleared, a kept
+            // one rewritten unchanged), then sort only the entries that stay
+            int keep = 0;
+            for (int x = 0; x < nc; ++x) {
+              const int c = cols[x];
+              const double a = accv[c];
+              const bool kept = c == r || std::fabs(a) >= tau;
+              cols[keep] = c;
+              keep += kept;
+              accv[c] = kept ? a : 0.0;
+              mark[c] = kept;
             }
-            cols.resize(keep);
-            std::sort(cols.begin(), cols.end());
+            std::sort(cols, cols + keep);
             const size_t before = ucol[ch].size();
-            for (int c : cols) {
+            for (int x = 0; x < keep; ++x) {
+              const int c = cols[x];
               ucol[ch].push_back(c);
               uval[ch].push_back(accv[c]);
               accv[c] = 0.0;
@@ -994,41 +1055,72 @@ int build_ildl(const SymCsr& A, const ildl_params& prm, HostFactor& F, bool dens
           }
         }
       }
-      for (int r = 0; r < mc_n; ++r) U.ptr[r + 1] = U.ptr[r] + rowcnt[r];
-      U.col.resize(U.ptr[mc_n]);
-      U.val.resize(U.ptr[mc_n]);
-#pragma omp parallel for schedule(dynamic, 1)
-      for (int ch = 0; ch < nchunk; ++ch) {
-        const int r0 = (int)((int64_t)mc_n * ch / nchunk);
-        std::copy(ucol[ch].begin(), ucol[ch].end(), U.col.begin() + U.ptr[r0]);
-        std::copy(uval[ch].begin(), uval[ch].end(), U.val.begin() + U.ptr[r0]);
-      }
     }
     const double ts_num = ms_since(t_schur) - ts_rec;
-    // mirror U into a full symmetric CSR: row c holds the lower entries
-    // (r, c), r < c, in increasing r (a stable transpose of the strictly
-    // upper part), then its own upper entries
-    SymCsr Sn;
+    // mirror the upper triangle into a full symmetric CSR, straight from the
+    // chunk buffers: row c holds its lower entries (r, c), r < c, in
+    // increasing r, then its own upper entries.  Groups of consecutive
+    // chunks count their lower entries per column; a group's entries of
+    // column c then take the slots after those of the groups before it, so
+    // the order is increasing r whatever the number of groups.
+    SymCsr& Sn = Snext;
     Sn.n = mc_n;
     {
-      std::vector<int64_t> lptr2;
-      dvec<int> lcol2;
-      dvec<double> lval2;
-      stable_transpose(mc_n, mc_n, U.ptr, U.col, U.val, [](int r, int c) { return c != r; }, lptr2, lcol2, lval2);
-      Sn.ptr.assign(mc_n + 1, 0);
-      for (int r = 0; r < mc_n; ++r) Sn.ptr[r + 1] = Sn.ptr[r] + (lptr2[r + 1] - lptr2[r]) + (U.ptr[r + 1] - U.ptr[r]);
-      Sn.col.resize(Sn.ptr[mc_n]);
-      Sn.val.resize(Sn.ptr[mc_n]);
-#pragma omp parallel for schedule(dynamic, 1024)
-      for (int r = 0; r < mc_n; ++r) {
-        int64_t o = Sn.ptr[r];
-        for (int64_t q = lptr2[r]; q < lptr2[r + 1]; ++q, ++o) {
-          Sn.col[o] = lcol2[q];
-          Sn.val[o] = lval2[q];
+      const int64_t nup = [&] {
+        int64_t s = 0;
+        for (int ch = 0; ch < nchunk; ++ch) s += (int64_t)ucol[ch].size();
+        return s;
+      }();
+      const int G = (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)omp_get_max_threads(), (int64_t)nchunk, nup / 16384}));
+      auto chunk_row0 = [&](int ch) { return (int)((int64_t)mc_n * ch / nchunk); };
+      std::vector<unsigned>& cnt = mirror_cnt;
+      cnt.assign((size_t)G * mc_n, 0u);
+#pragma omp parallel for schedule(static)
+      for (int g = 0; g < G; ++g) {
+        unsigned* c = cnt.data() + (size_t)g * mc_n;
+        for (int ch = nchunk * g / G; ch < nchunk * (g + 1) / G; ++ch) {
+          const int* col = ucol[ch].data();
+          int64_t q = 0;
+          for (int r = chunk_row0(ch); r < chunk_row0(ch + 1); ++r)
+            for (const int64_t e = q + rowcnt[r]; q < e; ++q)
+              if (col[q] != r) ++c[col[q]];
         }
-        for (int64_t q = U.ptr[r]; q < U.ptr[r + 1]; ++q, ++o) {
-          Sn.col[o] = U.col[q];
-          Sn.val[o] = U.val[q];
+      }
+      std::vector<int> lowcnt(mc_n);
+#pragma omp parallel for schedule(static)
+      for (int c = 0; c < mc_n; ++c) {
+        unsigned run = 0;  // offsets within the column's lower entries, by group
+        for (int g = 0; g < G; ++g) {
+          const unsigned k = cnt[(size_t)g * mc_n + c];
+          cnt[(size_t)g * mc_n + c] = run;
+          run += k;
+        }
+        lowcnt[c] = (int)run;
+      }
+      Sn.ptr.assign(mc_n + 1, 0);
+      for (int r = 0; r < mc_n; ++r) Sn.ptr[r + 1] = Sn.ptr[r] + lowcnt[r] + rowcnt[r];
+      resize_discard(Sn.col, Sn.ptr[mc_n]);
+      resize_discard(Sn.val, Sn.ptr[mc_n]);
+#pragma omp parallel for schedule(static)
+      for (int g = 0; g < G; ++g) {
+        unsigned* c = cnt.data() + (size_t)g * mc_n;
+        for (int ch = nchunk * g / G; ch < nchunk * (g + 1) / G; ++ch) {
+          const int* col = ucol[ch].data();
+          const double* val = uval[ch].data();
+          int64_t q = 0;
+          for (int r = chunk_row0(ch); r < chunk_row0(ch + 1); ++r) {
+            int64_t o = Sn.ptr[r] + lowcnt[r];
+            for (const int64_t e = q + rowcnt[r]; q < e; ++q, ++o) {
+              const int cc = col[q];
+              Sn.col[o] = cc;
+              Sn.val[o] = val[q];
+              if (cc != r) {
+                const int64_t slot = Sn.ptr[cc] + c[cc]++;
+                Sn.col[slot] = r;
+                Sn.val[slot] = val[q];
+              }
+            }
+          }
         }
       }
     }
@@ -1045,7 +1137,7 @@ int build_ildl(const SymCsr& A, const ildl_params& prm, HostFactor& F, bool dens
       std::fprintf(stderr, "ildl level %d: m=%d B=%zu C=%d nnzS'/row=%.1f nnzLF=%zu | match %.1f cand %.1f LF %.1f schur %.1f (records %.1f numeric %.1f) total %.1f ms\n",
                    level, m, acc.size(), mc_n, mc_n ? (double)Sn.col.size() / mc_n : 0.0, lnode.size(), tm_ms, tc_ms, tl_ms,
                    ms_since(t_schur), ts_rec, ts_num, ms_since(t_level));
-    S = std::move(Sn);
+    std::swap(S, Snext);
   }
   const int nlev = level;
   const int nd = S.n;

@@ -87,8 +87,20 @@ int build_ildl(const SymCsr& A, const ildl_params& p, HostFactor& F, bool dense_
 // potentials of the assignment problem with costs c_ij = log a_i - log|a_ij|,
 // a_i = max_j |a_ij|.  Returns the number of unmatched columns (0 when a
 // perfect matching exists).
+// `work` (optional) holds the scratch arrays between calls, so that a caller
+// matching a sequence of matrices (the levels of the factorization) reuses
+// memory that is already mapped instead of faulting in fresh pages per call.
+struct MatchWork {
+  dvec<double> cost, loga;  // per stored entry
+  struct Search {           // per OpenMP thread; at rest: dist = inf, pred = -1, done = 0
+    std::vector<double> dist;
+    std::vector<int> pred;
+    std::vector<char> done;
+  };
+  std::vector<Search> threads;
+};
 int max_product_matching(const SymCsr& A, std::vector<int>& match_col, std::vector<double>& u,
-                         std::vector<double>& v, std::vector<double>& rowmax);
+                         std::vector<double>& v, std::vector<double>& rowmax, MatchWork* work = nullptr);
 
 // Split the cycles of the permutation j -> match_col[j] into 1- and 2-cycles
 // (Section 5.2).  `sdiag` and the scaled matrix decide the splits.  Returns
