@@ -617,6 +617,7 @@ int build_ildl(const SymCsr& A, const ildl_params& prm, HostFactor& F, bool dens
   dvec<double> rec_a, rec_b, c1, c2;
   dvec<int64_t> rec_slot;
   std::vector<unsigned> mirror_cnt;
+  dvec<Trip> mirror_tmp;                             // lower entries bucketed by column block
   struct RowWork {                                   // per thread; accv and mark all zero at rest
     std::vector<double> accv;
     std::vector<char> mark;
@@ -1057,12 +1058,15 @@ int build_ildl(const SymCsr& A, const ildl_params& prm, HostFactor& F, bool dens
       }
     }
     const double ts_num = ms_since(t_schur) - ts_rec;
-    // mirror the upper triangle into a full symmetric CSR, straight from the
-    // chunk buffers: row c holds its lower entries (r, c), r < c, in
-    // increasing r, then its own upper entries.  Groups of consecutive
-    // chunks count their lower entries per column; a group's entries of
-    // column c then take the slots after those of the groups before it, so
-    // the order is increasing r whatever the number of groups.
+    // mirror the upper triangle into a full symmetric CSR: row c holds its
+    // lower entries (r, c), r < c, in increasing r, then its own upper
+    // entries.  Scattering the lower entries straight into their rows would
+    // miss the cache on almost every write, so they go through a bucket
+    // pass: (1) groups of consecutive chunks (increasing r) copy their upper
+    // rows and append each lower entry to the bucket of its column block,
+    // behind the entries of the groups before them; (2) each block, small
+    // enough to stay in cache, moves its bucket into the rows in bucket
+    // order.  Both keep increasing r per column whatever the group count.
     SymCsr& Sn = Snext;
     Sn.n = mc_n;
     {
@@ -1072,8 +1076,10 @@ int build_ildl(const SymCsr& A, const ildl_params& prm, HostFactor& F, bool dens
         return s;
       }();
       const int G = (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)omp_get_max_threads(), (int64_t)nchunk, nup / 16384}));
+      constexpr int kBlkShift = 8;  // 256 columns per block
+      const int nblk = (mc_n >> kBlkShift) + 1;
       auto chunk_row0 = [&](int ch) { return (int)((int64_t)mc_n * ch / nchunk); };
-      std::vector<unsigned>& cnt = mirror_cnt;
+      std::vector<unsigned>& cnt = mirror_cnt;  // per group: lower entries per column
       cnt.assign((size_t)G * mc_n, 0u);
 #pragma omp parallel for schedule(static)
       for (int g = 0; g < G; ++g) {
@@ -1087,23 +1093,33 @@ int build_ildl(const SymCsr& A, const ildl_params& prm, HostFactor& F, bool dens
         }
       }
       std::vector<int> lowcnt(mc_n);
+      std::vector<int64_t> boff((size_t)G * nblk);  // per group: its first slot in each bucket
+      std::vector<int64_t> bptr(nblk + 1, 0);       // bucket b = lower entries of columns [256 b, 256 b + 256)
 #pragma omp parallel for schedule(static)
-      for (int c = 0; c < mc_n; ++c) {
-        unsigned run = 0;  // offsets within the column's lower entries, by group
+      for (int b = 0; b < nblk; ++b) {
+        const int c0 = b << kBlkShift, c1 = std::min(mc_n, c0 + (1 << kBlkShift));
+        int64_t run = 0;
         for (int g = 0; g < G; ++g) {
-          const unsigned k = cnt[(size_t)g * mc_n + c];
-          cnt[(size_t)g * mc_n + c] = run;
-          run += k;
+          boff[(size_t)g * nblk + b] = run;
+          for (int c = c0; c < c1; ++c) run += cnt[(size_t)g * mc_n + c];
         }
-        lowcnt[c] = (int)run;
+        for (int c = c0; c < c1; ++c) {
+          unsigned k = 0;
+          for (int g = 0; g < G; ++g) k += cnt[(size_t)g * mc_n + c];
+          lowcnt[c] = (int)k;
+        }
+        bptr[b + 1] = run;
       }
+      for (int b = 0; b < nblk; ++b) bptr[b + 1] += bptr[b];
       Sn.ptr.assign(mc_n + 1, 0);
       for (int r = 0; r < mc_n; ++r) Sn.ptr[r + 1] = Sn.ptr[r] + lowcnt[r] + rowcnt[r];
       resize_discard(Sn.col, Sn.ptr[mc_n]);
       resize_discard(Sn.val, Sn.ptr[mc_n]);
+      resize_discard(mirror_tmp, bptr[nblk]);
 #pragma omp parallel for schedule(static)
       for (int g = 0; g < G; ++g) {
-        unsigned* c = cnt.data() + (size_t)g * mc_n;
+        int64_t* bo = boff.data() + (size_t)g * nblk;
+        for (int b = 0; b < nblk; ++b) bo[b] += bptr[b];
         for (int ch = nchunk * g / G; ch < nchunk * (g + 1) / G; ++ch) {
           const int* col = ucol[ch].data();
           const double* val = uval[ch].data();
@@ -1114,13 +1130,21 @@ int build_ildl(const SymCsr& A, const ildl_params& prm, HostFactor& F, bool dens
               const int cc = col[q];
               Sn.col[o] = cc;
               Sn.val[o] = val[q];
-              if (cc != r) {
-                const int64_t slot = Sn.ptr[cc] + c[cc]++;
-                Sn.col[slot] = r;
-                Sn.val[slot] = val[q];
-              }
+              if (cc != r) mirror_tmp[bo[cc >> kBlkShift]++] = {r, cc, val[q]};
             }
           }
+        }
+      }
+#pragma omp parallel for schedule(dynamic, 16)
+      for (int b = 0; b < nblk; ++b) {
+        const int c0 = b << kBlkShift, c1 = std::min(mc_n, c0 + (1 << kBlkShift));
+        int64_t next[1 << kBlkShift];  // write position of each column of the block
+        for (int c = c0; c < c1; ++c) next[c - c0] = Sn.ptr[c];
+        for (int64_t t = bptr[b]; t < bptr[b + 1]; ++t) {
+          const Trip& e = mirror_tmp[t];
+          const int64_t slot = next[e.c - c0]++;
+          Sn.col[slot] = e.r;
+          Sn.val[slot] = e.v;
         }
       }
     }
