@@ -67,19 +67,15 @@ double lookup(const SymCsr& S, int i, int j) {
   return (p != e && *p == j) ? S.val[p - S.col.data()] : 0.0;
 }
 
-}  // namespace
-
-// Natural logarithm of a positive finite double: x = m 2^e with m in
-// [sqrt(1/2), sqrt(2)), ln x = e ln 2 + 2 atanh(s), s = (m - 1) / (m + 1),
-// |s| < 0.1716, and atanh(s) = s + s^3/3 + s^5/5 + ... summed to s^19 (the
-// first omitted term is below 1e-16 relative).  A few times cheaper than the
-// library call; the matching only needs one consistent logarithm.
-inline double log_pos(double x) {
+// Natural logarithm of a positive normal double by the atanh series:
+// x = m 2^e with m in [sqrt(1/2), sqrt(2)), ln x = e ln 2 + 2 atanh(s),
+// s = (m - 1) / (m + 1), |s| < 0.1716, atanh(s) = s + s^3/3 + ... summed to
+// s^19 (the first omitted term is below 1e-16 relative).  Used only to build
+// the table of log_pos.
+double log_series(double x) {
   uint64_t b;
   std::memcpy(&b, &x, sizeof(b));
-  const int ef = (int)((b >> 52) & 0x7ff);
-  if (ef == 0 || ef == 0x7ff) return std::log(x);  // subnormal, inf, nan
-  int e = ef - 1023;
+  int e = (int)((b >> 52) & 0x7ff) - 1023;
   b = (b & 0x000fffffffffffffull) | 0x3ff0000000000000ull;  // mantissa in [1, 2)
   double m;
   std::memcpy(&m, &b, sizeof(m));
@@ -89,17 +85,56 @@ inline double log_pos(double x) {
   }
   const double s = (m - 1.0) / (m + 1.0), s2 = s * s;
   double t = 1.0 / 19.0;
-  t = t * s2 + 1.0 / 17.0;
-  t = t * s2 + 1.0 / 15.0;
-  t = t * s2 + 1.0 / 13.0;
-  t = t * s2 + 1.0 / 11.0;
-  t = t * s2 + 1.0 / 9.0;
-  t = t * s2 + 1.0 / 7.0;
-  t = t * s2 + 1.0 / 5.0;
-  t = t * s2 + 1.0 / 3.0;
-  t = t * s2 + 1.0;
+  for (int k = 17; k >= 1; k -= 2) t = t * s2 + 1.0 / k;
   return (double)e * 0.6931471805599453 + 2.0 * s * t;
 }
+
+// Table of the division-free logarithm: the mantissa range [1, 2) is cut
+// into 128 intervals [c_k, c_k + 1/128), c_k = 1 + k/128, with 1/c_k and
+// ln c_k stored (computed once, by IEEE division and the series above, so
+// the table is the same on every machine).
+struct LogTable {
+  double inv[128], logc[128];
+  LogTable() {
+    for (int k = 0; k < 128; ++k) {
+      const double c = 1.0 + k / 128.0;
+      inv[k] = 1.0 / c;
+      logc[k] = k == 0 ? 0.0 : log_series(c);
+    }
+  }
+};
+const LogTable g_log_table;
+
+// Natural logarithm of a positive finite double without a division (the
+// matching takes one per stored entry): x = m 2^e, m in [1, 2) falls in the
+// interval k of the table, r = m / c_k - 1 in [0, 1/128) (exact for k = 0,
+// so ln 1 = 0 and ln 2^e = e ln 2), and ln x = e ln 2 + ln c_k + ln(1 + r)
+// with ln(1 + r) = r - r^2/2 + ... + r^9/9 (first omitted term below
+// 1e-20).  Error a few units in the last place; the matching only needs one
+// consistent logarithm, and nothing here depends on the host's libm.
+inline double log_pos(double x) {
+  uint64_t b;
+  std::memcpy(&b, &x, sizeof(b));
+  const int ef = (int)((b >> 52) & 0x7ff);
+  if (ef == 0 || ef == 0x7ff) return std::log(x);  // subnormal, inf, nan
+  const int k = (int)((b >> 45) & 127);            // top 7 bits of the mantissa
+  const uint64_t mb = (b & 0x000fffffffffffffull) | 0x3ff0000000000000ull;
+  double m;
+  std::memcpy(&m, &mb, sizeof(m));
+  const double r = k == 0 ? m - 1.0 : m * g_log_table.inv[k] - 1.0;
+  double t = 1.0 / 9.0;
+  t = t * r - 1.0 / 8.0;
+  t = t * r + 1.0 / 7.0;
+  t = t * r - 1.0 / 6.0;
+  t = t * r + 1.0 / 5.0;
+  t = t * r - 1.0 / 4.0;
+  t = t * r + 1.0 / 3.0;
+  t = t * r - 1.0 / 2.0;
+  t = t * r + 1.0;
+  return (double)(ef - 1023) * 0.6931471805599453 + (g_log_table.logc[k] + r * t);
+}
+
+}  // namespace
 
 // ---------------------------------------------------------------------------
 // Section 5.1: maximise prod_i |a_{sigma(i) i}| <=> minimise sum c_{sigma(i) i}
