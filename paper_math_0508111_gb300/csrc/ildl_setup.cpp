@@ -157,34 +157,34 @@ int max_product_matching(const SymCsr& A, std::vector<int>& match_col, std::vect
     rowmax[i] = r;
     logmax[i] = log_pos(r);
   }
-  // cost of entry p (row i, column col[p]); +inf for explicit zeros
-  dvec<double>& cost = mw.cost;  // filled (first touched) in parallel below
-  dvec<double>& loga = mw.loga;
-  resize_discard(cost, A.val.size());
+  // log|a| of every stored entry (-inf for explicit zeros); the cost of
+  // entry p in row i is c_i,col[p] = logmax[i] - loga[p] (+inf for zeros),
+  // formed where it is used rather than stored.  v_j = min_i c_ij: by
+  // symmetry column j's entries are row j's entries, with the cost taken in
+  // the row of the other index, so v comes out of the same pass.
+  dvec<double>& loga = mw.loga;  // filled (first touched) in parallel below
   resize_discard(loga, A.val.size());
-#pragma omp parallel for schedule(static)
-  for (int i = 0; i < n; ++i)
-    for (int64_t p = A.ptr[i]; p < A.ptr[i + 1]; ++p) {
-      const double a = std::fabs(A.val[p]);
-      loga[p] = a > 0.0 ? log_pos(a) : -kInf;
-      cost[p] = a > 0.0 ? logmax[i] - loga[p] : kInf;
-    }
-  // v_j = min_i c_ij: by symmetry column j's entries are row j's entries,
-  // with the cost taken in the row of the other index.
+  auto cost = [&](int i, int64_t p) { return logmax[i] - loga[p]; };
   v.assign(n, kInf);
 #pragma omp parallel for schedule(static)
   for (int j = 0; j < n; ++j) {
     double best = kInf;
-    for (int64_t p = A.ptr[j]; p < A.ptr[j + 1]; ++p)
-      if (loga[p] > -kInf) best = std::min(best, logmax[A.col[p]] - loga[p]);
+    for (int64_t p = A.ptr[j]; p < A.ptr[j + 1]; ++p) {
+      const double a = std::fabs(A.val[p]);
+      const double la = a > 0.0 ? log_pos(a) : -kInf;
+      loga[p] = la;
+      if (la > -kInf) best = std::min(best, logmax[A.col[p]] - la);
+    }
     v[j] = best == kInf ? 0.0 : best;
   }
   u.assign(n, kInf);
 #pragma omp parallel for schedule(static)
   for (int i = 0; i < n; ++i) {
     double best = kInf;
-    for (int64_t p = A.ptr[i]; p < A.ptr[i + 1]; ++p)
-      if (cost[p] < kInf) best = std::min(best, cost[p] - v[A.col[p]]);
+    for (int64_t p = A.ptr[i]; p < A.ptr[i + 1]; ++p) {
+      const double c = cost(i, p);
+      if (c < kInf) best = std::min(best, c - v[A.col[p]]);
+    }
     u[i] = best == kInf ? 0.0 : best;
   }
   match_col.assign(n, -1);
@@ -194,7 +194,8 @@ int max_product_matching(const SymCsr& A, std::vector<int>& match_col, std::vect
   // the other rows take a free zero-reduced-cost column in row order
   auto zero_rc = [&](int i, int64_t p) {
     const int j = A.col[p];
-    return cost[p] < kInf && cost[p] - u[i] - v[j] <= 1e-13 * (1.0 + std::fabs(u[i]) + std::fabs(v[j]));
+    const double c = cost(i, p);
+    return c < kInf && c - u[i] - v[j] <= 1e-13 * (1.0 + std::fabs(u[i]) + std::fabs(v[j]));
   };
 #pragma omp parallel for schedule(static)
   for (int i = 0; i < n; ++i)
@@ -277,8 +278,9 @@ int max_product_matching(const SymCsr& A, std::vector<int>& match_col, std::vect
     for (;;) {
       for (int64_t p = A.ptr[i]; p < A.ptr[i + 1]; ++p) {
         const int j = A.col[p];
-        if (W.done[j] || cost[p] == kInf) continue;
-        const double nd = di + std::max(0.0, cost[p] - u[i] - v[j]);
+        const double c = cost(i, p);
+        if (W.done[j] || c == kInf) continue;
+        const double nd = di + std::max(0.0, c - u[i] - v[j]);
         if (nd < W.dist[j]) {
           if (W.dist[j] == kInf) R.touched.push_back(j);
           W.dist[j] = nd;
@@ -1058,12 +1060,24 @@ int build_ildl(const SymCsr& A, const ildl_params& prm, HostFactor& F, bool dens
               // the column is stored unconditionally and counted only then
               // (no unpredictable branch)
               const int64_t te = cptr[b + 1];
-              for (int64_t t = me; t < te; ++t) {
-                const int q = crow[t];  // q >= r because rows are ascending
-                cols[nc] = q;
-                nc += !mark[q];
-                mark[q] = 1;
-                accv[q] -= wa * c1[t] + wb * c2[t];
+              if (cands[acc[b]].b < 0) {
+                // 1x1 block: wb = 0 and every c2 is 0, so wb * c2 is +0 (the
+                // same sum as the general form, without the second operand)
+                for (int64_t t = me; t < te; ++t) {
+                  const int q = crow[t];  // q >= r because rows are ascending
+                  cols[nc] = q;
+                  nc += !mark[q];
+                  mark[q] = 1;
+                  accv[q] -= wa * c1[t] + 0.0;
+                }
+              } else {
+                for (int64_t t = me; t < te; ++t) {
+                  const int q = crow[t];
+                  cols[nc] = q;
+                  nc += !mark[q];
+                  mark[q] = 1;
+                  accv[q] -= wa * c1[t] + wb * c2[t];
+                }
               }
             }
             // drop first (branch-free: a dropped column is cleared, a kept

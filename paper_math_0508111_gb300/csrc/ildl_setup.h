@@ -91,7 +91,7 @@ int build_ildl(const SymCsr& A, const ildl_params& p, HostFactor& F, bool dense_
 // matching a sequence of matrices (the levels of the factorization) reuses
 // memory that is already mapped instead of faulting in fresh pages per call.
 struct MatchWork {
-  dvec<double> cost, loga;  // per stored entry
+  dvec<double> loga;        // log|a| per stored entry
   struct Search {           // per OpenMP thread; at rest: dist = inf, pred = -1, done = 0
     std::vector<double> dist;
     std::vector<int> pred;
