@@ -60,6 +60,22 @@ void resize_discard(V& v, size_t n) {
   v.resize(n);
 }
 
+// Ascending sort of a short int array: insertion sort up to `small`
+// entries (few moves on nearly sorted input, no mispredicted partitions),
+// std::sort above.
+void sort_ints(int* a, int n, int small) {
+  if (n > small) {
+    std::sort(a, a + n);
+    return;
+  }
+  for (int x = 1; x < n; ++x) {
+    const int c = a[x];
+    int y = x;
+    for (; y > 0 && a[y - 1] > c; --y) a[y] = a[y - 1];
+    a[y] = c;
+  }
+}
+
 double lookup(const SymCsr& S, int i, int j) {
   const int* b = S.col.data() + S.ptr[i];
   const int* e = S.col.data() + S.ptr[i + 1];
@@ -893,7 +909,7 @@ int build_ildl(const SymCsr& A, const ildl_params& prm, HostFactor& F, bool dens
               if (x == cd.a) fa[b] += S.val[p];
               else fb[b] += S.val[p];
             }
-            std::sort(touched.begin(), touched.end());
+            sort_ints(touched.data(), (int)touched.size(), 32);
             const size_t before = cn[ch].size();
             for (int b : touched) {
               const Cand& cd = cands[acc[b]];
@@ -1092,7 +1108,11 @@ int build_ildl(const SymCsr& A, const ildl_params& prm, HostFactor& F, bool dens
               accv[c] = kept ? a : 0.0;
               mark[c] = kept;
             }
-            std::sort(cols, cols + keep);
+            // the columns arrive as a few ascending runs (the old row, then
+            // the new columns of each block in row order): insertion sort
+            // moves little on such input and beats a general sort up to a
+            // few hundred entries
+            sort_ints(cols, keep, 256);
             const size_t before = ucol[ch].size();
             for (int x = 0; x < keep; ++x) {
               const int c = cols[x];
