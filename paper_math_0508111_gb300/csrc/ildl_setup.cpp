@@ -697,6 +697,7 @@ int build_ildl(const SymCsr& A, const ildl_params& prm, HostFactor& F, bool dens
     const bool use_matching = prm.matching != 0 && (prm.matching < 0 || level < prm.matching);
     if (use_matching) {
       max_product_matching(S, mc, u, v, rmax, &mwork);
+#pragma omp parallel for schedule(static)
       for (int i = 0; i < m; ++i) d[i] = std::sqrt(std::exp(u[i] + v[i]) / rmax[i]);
       if (level == 0)
         for (int j = 0; j < m; ++j) F.n_matched_offdiag += (mc[j] != j);
