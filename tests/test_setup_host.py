@@ -137,16 +137,18 @@ def test_setup_rejects_bad_input(ajd):
 def test_setup_independent_of_thread_count(ajd):
     """The parallel setup (matching searches in batches, parallel scatters,
     per-chunk rows) gives the same factor, bit for bit, with 1 and 4 host
-    threads."""
+    threads.  L = 24 is large enough that the scatters and the Schur mirror
+    split their work into several thread groups (at least 16384 entries
+    per group)."""
     import ctypes
     import ctypes.util
     gomp = ctypes.CDLL(ctypes.util.find_library("gomp") or "libgomp.so.1")
-    A, _ = _csr(14, 12.0, 6, PERIODIC, 0.2)
+    A, _ = _csr(24, 12.0, 6, PERIODIC, 0.2)
     out = []
     try:
         for t in (1, 4):
             gomp.omp_set_num_threads(t)
-            out.append(ajd.Preconditioner.from_csr(A.indptr, A.indices, A.data, n_dense=200).export())
+            out.append(ajd.Preconditioner.from_csr(A.indptr, A.indices, A.data, n_dense=300).export())
     finally:
         gomp.omp_set_num_threads(max(1, __import__("os").cpu_count() or 1))
     assert out[0]["levels"] >= 3
