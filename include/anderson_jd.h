@@ -179,6 +179,14 @@ typedef struct {
                      cycle split and symmetric dual scaling (Sections 5.1,
                      5.2); deeper levels use row-max scaling and 1x1
                      candidates; 0 = none, < 0 = every level [-1]            */
+  double aggressive; /* tau of the aggressive dropping of Section 6.3: an
+                     entry l_ij of a level's column block of L is dropped
+                     when |l_ij| <= tau / #(nonzeros of column j of the
+                     block); the paper's norm estimate nu_i of L^{-1} e_i is
+                     exactly 1 for every row of a level's block.  Applied
+                     as soon as the block is computed, so the Schur
+                     complement is formed from the sparsified block.
+                     0 = off, else 0 < tau < 1 (the paper suggests 0.1) [0] */
 } ildl_params;
 
 /* Fill *p with the defaults above. */
@@ -199,6 +207,8 @@ typedef struct {
   int relaxed_levels;/* levels where fewer than 0.5% of the rows met kappa and
                         the bound was widened (at most 64 kappa)            */
   double max_abs_L;  /* largest |entry| of L (after the global scaling)     */
+  int64_t aggressive_dropped; /* entries removed by aggressive dropping
+                        (ildl_params.aggressive; 0 when off)                */
 } ildl_info_t;
 
 /*

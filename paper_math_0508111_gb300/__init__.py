@@ -147,7 +147,8 @@ class Anderson:
 
 def ildl_params(**kw):
     """Preconditioner parameters (defaults of ildl_params_default) with
-    keyword overrides: kappa, drop, gamma, max_levels, n_dense, matching."""
+    keyword overrides: kappa, drop, gamma, max_levels, n_dense, matching,
+    aggressive (tau of the aggressive dropping of Section 6.3; 0 = off)."""
     p = _ffi.IldlParams()
     _ffi.call("ildl_params_default", ctypes.byref(p))
     for k, v in kw.items():

@@ -473,6 +473,7 @@ extern "C" int ildl_params_default(ildl_params* p) {
   p->max_levels = 256;
   p->n_dense = 0;
   p->matching = -1;
+  p->aggressive = 0.0;
   return JD_OK;
 }
 
@@ -482,6 +483,8 @@ static int check_params(const ildl_params* p, ildl_params& out) {
   if (!(out.kappa > 1.0)) return fail(JD_EINVAL, "ildl: kappa must be > 1");
   if (!std::isfinite(out.drop) && out.drop > 0) return fail(JD_EINVAL, "ildl: drop must be finite");
   if (out.gamma >= 1.0 || std::isnan(out.gamma)) return fail(JD_EINVAL, "ildl: gamma must be < 1");
+  if (!(out.aggressive >= 0.0 && out.aggressive < 1.0))
+    return fail(JD_EINVAL, "ildl: aggressive dropping tau must be in [0, 1)");
   if (out.max_levels < 1 || out.n_dense < 0 || out.n_dense > 8000)
     return fail(JD_EINVAL, "ildl: max_levels >= 1 and 0 <= n_dense <= 8000 required");
   return JD_OK;
@@ -624,6 +627,7 @@ extern "C" int ildl_info(ildl_t f, ildl_info_t* info) {
   info->match_ms = F.t_match_ms;
   info->relaxed_levels = F.n_relaxed;
   info->max_abs_L = F.max_abs_L;
+  info->aggressive_dropped = F.n_aggressive;
   return JD_OK;
 }
 

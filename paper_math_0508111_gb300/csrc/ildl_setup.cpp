@@ -624,6 +624,7 @@ int build_ildl(const SymCsr& A, const ildl_params& prm, HostFactor& F, bool dens
   const double kappa = prm.kappa > 1.0 ? prm.kappa : 5.0;
   const double eps_drop = prm.drop < 0.0 ? 1.0 / std::sqrt((double)n) : prm.drop;
   const double tau = eps_drop / kappa;
+  const double agg_tau = prm.aggressive > 0.0 ? prm.aggressive : 0.0;  // Section 6.3, 0 = off
 
   // weak-coupling threshold of the independent sets; by default it shrinks
   // with the drop tolerance (measured: a fixed 0.02 loses the preconditioner
@@ -664,6 +665,8 @@ int build_ildl(const SymCsr& A, const ildl_params& prm, HostFactor& F, bool dens
   SymCsr Snext;                                      // next level's S
   dvec<int> lnode;                                   // L_F: B node (local index)
   dvec<double> lval;
+  dvec<int> agg_node;                                // L_F after aggressive dropping
+  dvec<double> agg_val;
   std::vector<std::vector<int>> cn, ucol;            // per-chunk row output
   std::vector<std::vector<double>> cv, uval;
   dvec<int> rec_row, rec_blk, crow;                  // Schur records
@@ -940,6 +943,42 @@ int build_ildl(const SymCsr& A, const ildl_params& prm, HostFactor& F, bool dens
         std::copy(cn[ch].begin(), cn[ch].end(), lnode.begin() + lptr[r0]);
         std::copy(cv[ch].begin(), cv[ch].end(), lval.begin() + lptr[r0]);
       }
+    }
+    if (agg_tau > 0.0 && lptr[mc_n] > 0) {
+      // 6b. aggressive dropping (Section 6.3): l_ij goes when |l_ij| <=
+      // tau / (nu_i * #column j), nu_i = ||L_level^{-1} e_i||, which is 1 for
+      // every row i of the block (the level's L is [I 0; L_F I]).  Done
+      // before the Schur complement, which is then formed from the sparser
+      // block.
+      std::vector<int> ccount(m, 0);
+#pragma omp parallel for schedule(static)
+      for (int64_t p = 0; p < lptr[mc_n]; ++p) {
+#pragma omp atomic
+        ++ccount[lnode[p]];
+      }
+      std::vector<int64_t> nptr(mc_n + 1, 0);
+#pragma omp parallel for schedule(static)
+      for (int r = 0; r < mc_n; ++r) {
+        int64_t k = 0;
+        for (int64_t p = lptr[r]; p < lptr[r + 1]; ++p) k += std::fabs(lval[p]) > agg_tau / ccount[lnode[p]];
+        nptr[r + 1] = k;
+      }
+      for (int r = 0; r < mc_n; ++r) nptr[r + 1] += nptr[r];
+      resize_discard(agg_node, nptr[mc_n]);
+      resize_discard(agg_val, nptr[mc_n]);
+#pragma omp parallel for schedule(static)
+      for (int r = 0; r < mc_n; ++r) {
+        int64_t o = nptr[r];
+        for (int64_t p = lptr[r]; p < lptr[r + 1]; ++p)
+          if (std::fabs(lval[p]) > agg_tau / ccount[lnode[p]]) {
+            agg_node[o] = lnode[p];
+            agg_val[o++] = lval[p];
+          }
+      }
+      F.n_aggressive += lptr[mc_n] - nptr[mc_n];
+      lptr.swap(nptr);
+      lnode.swap(agg_node);
+      lval.swap(agg_val);
     }
     {
       const size_t base = trips.size();

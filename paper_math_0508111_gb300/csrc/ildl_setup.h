@@ -70,6 +70,7 @@ struct HostFactor {
   int n_2x2 = 0;
   int n_matched_offdiag = 0;      // rows matched off the diagonal at level 0
   int n_relaxed = 0;              // levels where pivot acceptance was relaxed
+  int64_t n_aggressive = 0;       // entries removed by aggressive dropping
   double max_abs_L = 0.0;         // largest |entry| of the global L
   int64_t nnz_A = 0;
   double t_match_ms = 0, t_factor_ms = 0, t_total_ms = 0;

@@ -1574,7 +1574,11 @@ static int normalize_params(const jd_params* p, jd_params& prm) {
     if (!(prm.inner_floor >= 0.0)) prm.inner_floor = d.inner_floor;
     if (prm.extraction != 0 && prm.extraction != 1) prm.extraction = d.extraction;
     if (!(prm.switch_tol > 0.0)) prm.switch_tol = d.switch_tol;
-    if (prm.ildl.kappa == 0.0 && prm.ildl.max_levels == 0 && prm.ildl.n_dense == 0) prm.ildl = d.ildl;
+    if (prm.ildl.kappa == 0.0 && prm.ildl.max_levels == 0 && prm.ildl.n_dense == 0) {
+      const double aggressive = prm.ildl.aggressive;  // the one field whose default is 0
+      prm.ildl = d.ildl;
+      prm.ildl.aggressive = aggressive;
+    }
   }
   if (prm.precision != JD_FP64 && prm.precision != JD_FP32 && prm.precision != JD_MIXED)
     return fail(JD_EINVAL, "jd_solve: unknown precision");

@@ -138,6 +138,18 @@ def test_jd_shift_invert_oracle(ajd, L, sigma, prec):
     _check_pairs(L, W, seed, 0, sigma, k, ev, X, st, tol, oracle="lanczos")
 
 
+@pytest.mark.parametrize("prec", [0, 2])
+def test_jd_with_aggressive_dropping(ajd, prec):
+    """Jacobi-Davidson preconditioned by a factor with Section 6.3's
+    aggressive dropping (tau = 0.1) reaches the dense oracle's pairs."""
+    L, W, seed, sigma, k = 14, 16.5, 3, 0.0, 5
+    tol = 1e-11 if prec == 0 else 1e-10
+    with ajd.Anderson(L, W, seed) as h:
+        ev, X, st = ajd.solve(h, sigma, k, tol, precision=prec, ildl=dict(aggressive=0.1, n_dense=300))
+    assert st["ildl"]["aggressive_dropped"] > 0
+    _check_pairs(L, W, seed, 0, sigma, k, ev, X, st, tol)
+
+
 @pytest.mark.parametrize("extraction", [0, 1])
 def test_jd_extraction_modes(ajd, extraction):
     """Harmonic (default) and standard Ritz extraction reach the same pairs."""

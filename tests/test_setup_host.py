@@ -157,3 +157,60 @@ def test_setup_independent_of_thread_count(ajd):
             continue
         a, b = np.asarray(out[0][key]), np.asarray(out[1][key])
         assert a.shape == b.shape and np.array_equal(a, b), key
+
+
+def test_aggressive_dropping_rule(ajd):
+    """Section 6.3's aggressive dropping on a one-level factor (the rest of
+    the matrix goes to the dense block), where the exported L is exactly the
+    level's scaled column block: an entry l_ij of the default factor is
+    removed iff |l_ij| <= tau / #(entries of column j); the pivots,
+    ordering, scaling and D are unchanged and the kept entries are the same
+    numbers.  tau = 0 gives the default factor bit for bit.  (The first
+    level's entries are large, so a large tau is taken to make it drop.)"""
+    A, _ = _csr(10, 16.5, 5, PERIODIC, 0.0)
+    kw = dict(max_levels=1, n_dense=100)
+    F0 = ajd.Preconditioner.from_csr(A.indptr, A.indices, A.data, **kw).export()
+    Fz = ajd.Preconditioner.from_csr(A.indptr, A.indices, A.data, aggressive=0.0, **kw).export()
+    tau = 0.9
+    Fa = ajd.Preconditioner.from_csr(A.indptr, A.indices, A.data, aggressive=tau, **kw).export()
+    for key in F0:
+        if not key.endswith("_ms"):
+            assert np.array_equal(np.asarray(F0[key]), np.asarray(Fz[key])), key
+    assert F0["levels"] == Fa["levels"] == 1 and F0["aggressive_dropped"] == 0
+    for key in ("perm", "scale", "level_ptr", "dinv_d", "dinv_o", "partner"):
+        assert np.array_equal(F0[key], Fa[key]), key
+    n = A.shape[0]
+    L0 = [(r, c, v) for r in range(n) for c, v in zip(F0["Lcol"][F0["Lptr"][r]:F0["Lptr"][r + 1]],
+                                                        F0["Lval"][F0["Lptr"][r]:F0["Lptr"][r + 1]])]
+    count = np.bincount([c for _, c, _ in L0], minlength=n)
+    want = {(r, c): v for r, c, v in L0 if abs(v) > tau / count[c]}
+    got = {(r, c): v for r in range(n) for c, v in zip(Fa["Lcol"][Fa["Lptr"][r]:Fa["Lptr"][r + 1]],
+                                                         Fa["Lval"][Fa["Lptr"][r]:Fa["Lptr"][r + 1]])}
+    assert got == want
+    assert Fa["aggressive_dropped"] == len(L0) - len(want) > 0
+
+
+def test_aggressive_dropping_quality(ajd):
+    """A multilevel factor with aggressive dropping (tau = 0.1, the value the
+    paper suggests) is sparser and still a good preconditioner: oracle SQMR
+    on (A - sigma I) x = b needs at most twice the default factor's
+    iterations."""
+    A, _ = _csr(14, 16.5, 1, PERIODIC, 0.0)
+    b = np.random.default_rng(4).standard_normal(A.shape[0])
+    its = {}
+    nnz = {}
+    for tau in (0.0, 0.1):
+        F = ajd.Preconditioner.from_csr(A.indptr, A.indices, A.data, n_dense=300, aggressive=tau).export()
+        assert F["levels"] >= 3
+        x, its[tau], _ = krylov.sqmr(lambda v: A @ v, lambda v: matching.apply_factor(F, v), b, 1e-8, 400)
+        assert np.linalg.norm(A @ x - b) <= 1e-7 * np.linalg.norm(b)
+        nnz[tau] = F["nnz_L"]
+    assert nnz[0.1] < nnz[0.0]
+    assert its[0.1] <= 2 * its[0.0]
+
+
+def test_aggressive_dropping_rejects_bad_tau(ajd):
+    A, _ = _csr(6, 16.5, 1, PERIODIC, 0.0)
+    for tau in (-0.1, 1.0, float("nan")):
+        with pytest.raises(ajd.JDError):
+            ajd.Preconditioner.from_csr(A.indptr, A.indices, A.data, aggressive=tau)
