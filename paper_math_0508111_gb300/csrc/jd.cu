@@ -218,14 +218,6 @@ __global__ void set_h_column_kernel(double* __restrict__ H, int ldh, int col, co
   }
 }
 
-// H = diag(theta[sel[0..m)])
-__global__ void set_h_diag_kernel(double* __restrict__ H, int ldh, int m, const double* __restrict__ theta, int off) {
-  for (int t = threadIdx.x; t < m * m; t += blockDim.x) {
-    const int i = t % m, j = t / m;
-    H[(int64_t)j * ldh + i] = (i == j) ? theta[off + i] : 0.0;
-  }
-}
-
 // Symmetric eigenproblem of H (m x m, m <= kMaxM) by the cyclic Jacobi method
 // with the round-robin (tournament) ordering, m/2 rotations per round applied
 // in parallel.  Output: theta[j] and Y[:, j] ordered by |theta - sigma|
@@ -878,10 +870,6 @@ int JdSolver::correction(int kc, double theta_hat, double rel_tol, int* its) {
   const int c = kc + 1;
   T* Qt = static_cast<T*>(Qt_);
   T* W = static_cast<T*>(W_);
-  T *x = static_cast<T*>(xb_), *r = static_cast<T*>(rb_), *q = static_cast<T*>(qb_), *d = static_cast<T*>(db_);
-  T *t = static_cast<T*>(tb_), *y = static_cast<T*>(yb_), *u = static_cast<T*>(ub_), *b = static_cast<T*>(bb_);
-  int* done = flags_;
-  int* brk = flags_ + 1;
   const int bl = nb_;
   // Qt[:, kc] = u, W[:, kc] = K^{-1} u  (Q columns and their W are cached)
   convert_kernel<double, T><<<bl, kThreads, 0, s_>>>(u_, Qt + (int64_t)kc * ld_, n_, 1.0); count_launches();
