@@ -31,6 +31,7 @@
 #include <memory>
 #include <numeric>
 #include <queue>
+#include <type_traits>
 #include <utility>
 #include <cstdio>
 #include <cstdlib>
@@ -525,51 +526,64 @@ void stable_scatter(int64_t N, int nb, Key key, std::vector<int64_t>& ptr, Emit 
   }
 }
 
-// Stable parallel transpose of a CSR block (rows 0..nr-1, columns
-// 0..nc-1): row c of the result lists (r, val) for every entry (r, c), in
-// increasing r; entries with keep(r, c) false are left out.  Rows are cut
-// into chunks of about equal entry counts.
-template <class Keep, class ColIn, class ValIn, class ColOut, class ValOut>
-void stable_transpose(int nr, int nc, const std::vector<int64_t>& ptr, const ColIn& col, const ValIn& val, Keep keep,
-                      std::vector<int64_t>& tptr, ColOut& tcol, ValOut& tval) {
-  const int64_t nnz = ptr[nr];
-  const int T = (int)std::max<int64_t>(1, std::min<int64_t>(omp_get_max_threads(), nnz / 16384));
-  std::vector<int> rcut(T + 1, nr);
-  rcut[0] = 0;
-  for (int t = 1; t < T; ++t)
-    rcut[t] = (int)(std::lower_bound(ptr.begin(), ptr.begin() + nr + 1, nnz * t / T) - ptr.begin());
-  std::vector<unsigned> cnt((size_t)T * nc, 0u);
+// Stable placement of items into the rows of a CSR array, in two passes
+// that keep the writes inside the cache.  produce(g, f) calls f(item) for
+// the items of group g (g = 0..G-1, each group a contiguous run of the item
+// order); item.r is the destination row in [0, nr), item.c and item.v the
+// stored column and value.  On return row r holds its items in item order
+// at ptr[r] .. ptr[r + 1] of (col, val), whatever G is.  Pass 1 moves the
+// items, group by group, into buckets of 256 consecutive rows (few write
+// streams); pass 2 places each bucket's items into its rows.
+template <class Produce, class ColOut, class ValOut>
+void stable_place(int G, int nr, Produce produce, std::vector<int64_t>& ptr, dvec<Trip>& tmp, ColOut& col,
+                  ValOut& val) {
+  constexpr int kShift = 8;
+  const int nblk = (nr >> kShift) + 1;
+  std::vector<unsigned> cnt((size_t)G * nr, 0u);
 #pragma omp parallel for schedule(static)
-  for (int t = 0; t < T; ++t) {
-    unsigned* c = cnt.data() + (size_t)t * nc;
-    for (int r = rcut[t]; r < rcut[t + 1]; ++r)
-      for (int64_t q = ptr[r]; q < ptr[r + 1]; ++q)
-        if (keep(r, col[q])) ++c[col[q]];
+  for (int g = 0; g < G; ++g) {
+    unsigned* c = cnt.data() + (size_t)g * nr;
+    produce(g, [&](const Trip& t) { ++c[t.r]; });
   }
-  tptr.assign((size_t)nc + 1, 0);
+  std::vector<int64_t> boff((size_t)G * nblk), bptr(nblk + 1, 0);
+  ptr.assign((size_t)nr + 1, 0);
 #pragma omp parallel for schedule(static)
-  for (int b = 0; b < nc; ++b) {
-    unsigned run = 0;
-    for (int t = 0; t < T; ++t) {
-      const unsigned c = cnt[(size_t)t * nc + b];
-      cnt[(size_t)t * nc + b] = run;
-      run += c;
+  for (int b = 0; b < nblk; ++b) {
+    const int r0 = b << kShift, r1 = std::min(nr, r0 + (1 << kShift));
+    int64_t run = 0;
+    for (int g = 0; g < G; ++g) {
+      boff[(size_t)g * nblk + b] = run;
+      for (int r = r0; r < r1; ++r) run += cnt[(size_t)g * nr + r];
     }
-    tptr[(size_t)b + 1] = run;
+    for (int r = r0; r < r1; ++r) {
+      int64_t k = 0;
+      for (int g = 0; g < G; ++g) k += cnt[(size_t)g * nr + r];
+      ptr[(size_t)r + 1] = k;
+    }
+    bptr[b + 1] = run;
   }
-  for (int b = 0; b < nc; ++b) tptr[(size_t)b + 1] += tptr[b];
-  tcol.resize(tptr[nc]);
-  tval.resize(tptr[nc]);
+  for (int r = 0; r < nr; ++r) ptr[(size_t)r + 1] += ptr[r];
+  for (int b = 0; b < nblk; ++b) bptr[b + 1] += bptr[b];
+  resize_discard(tmp, bptr[nblk]);
+  col.resize(ptr[nr]);
+  val.resize(ptr[nr]);
 #pragma omp parallel for schedule(static)
-  for (int t = 0; t < T; ++t) {
-    unsigned* c = cnt.data() + (size_t)t * nc;
-    for (int r = rcut[t]; r < rcut[t + 1]; ++r)
-      for (int64_t q = ptr[r]; q < ptr[r + 1]; ++q)
-        if (keep(r, col[q])) {
-          const int64_t slot = tptr[col[q]] + c[col[q]]++;
-          tcol[slot] = r;
-          tval[slot] = val[q];
-        }
+  for (int g = 0; g < G; ++g) {
+    int64_t* bo = boff.data() + (size_t)g * nblk;
+    for (int b = 0; b < nblk; ++b) bo[b] += bptr[b];
+    produce(g, [&](const Trip& t) { tmp[bo[t.r >> kShift]++] = t; });
+  }
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int b = 0; b < nblk; ++b) {
+    const int r0 = b << kShift, r1 = std::min(nr, r0 + (1 << kShift));
+    int64_t next[1 << kShift];
+    for (int r = r0; r < r1; ++r) next[r - r0] = ptr[r];
+    for (int64_t q = bptr[b]; q < bptr[b + 1]; ++q) {
+      const Trip& t = tmp[q];
+      const int64_t slot = next[t.r - r0]++;
+      col[slot] = t.c;
+      val[slot] = t.v;
+    }
   }
 }
 
@@ -1274,6 +1288,34 @@ int build_ildl(const SymCsr& A, const ildl_params& prm, HostFactor& F, bool dens
   }
   const int nlev = level;
   const int nd = S.n;
+  {
+    // the level scratch is not needed any more: release it before the
+    // global assembly allocates the factor
+    auto release = [](auto& v) { std::remove_reference_t<decltype(v)>().swap(v); };
+    release(mwork.loga);
+    release(mwork.threads);
+    release(Snext.ptr);
+    release(Snext.col);
+    release(Snext.val);
+    release(lnode);
+    release(lval);
+    release(agg_node);
+    release(agg_val);
+    release(cn);
+    release(ucol);
+    release(cv);
+    release(uval);
+    release(rec_row);
+    release(rec_blk);
+    release(crow);
+    release(rec_a);
+    release(rec_b);
+    release(c1);
+    release(c2);
+    release(rec_slot);
+    release(mirror_cnt);
+    release(rwork);
+  }
   // trailing dense block
   std::vector<double> dense_inv;
   if (nd > 0) {
@@ -1315,17 +1357,37 @@ int build_ildl(const SymCsr& A, const ildl_params& prm, HostFactor& F, bool dens
   // a level in increasing pivot position, so a stable scatter leaves every
   // row sorted by column
   const int64_t nt = (int64_t)trips.size();
-  F.Lcol.resize(nt);
-  F.Lval.resize(nt);
-  stable_scatter(nt, n, [&](int64_t q) { return pos[trips[q].r]; }, F.Lptr, [&](int64_t q, int64_t slot) {
-    const Trip& t = trips[q];
-    F.Lcol[slot] = pos[t.c];
-    F.Lval[slot] = t.v * sc[t.r];
-  });
+  {
+    const int G = (int)std::max<int64_t>(1, std::min<int64_t>(omp_get_max_threads(), nt / 16384));
+    stable_place(
+        G, n,
+        [&](int g, auto&& emit) {
+          for (int64_t q = nt * g / G; q < nt * (g + 1) / G; ++q) {
+            const Trip& t = trips[q];
+            emit(Trip{pos[t.r], pos[t.c], t.v * sc[t.r]});
+          }
+        },
+        F.Lptr, mirror_tmp, F.Lcol, F.Lval);
+  }
   trips.clear();
   trips.shrink_to_fit();
-  // transpose (rows of L^T = columns of L), entries ordered by row
-  stable_transpose(n, n, F.Lptr, F.Lcol, F.Lval, [](int, int) { return true; }, F.Uptr, F.Ucol, F.Uval);
+  {
+    // transpose (rows of L^T = columns of L), entries ordered by row: row
+    // groups of about equal entry counts, in row order
+    const int G = (int)std::max<int64_t>(1, std::min<int64_t>(omp_get_max_threads(), nt / 16384));
+    std::vector<int> rcut(G + 1, n);
+    rcut[0] = 0;
+    for (int g = 1; g < G; ++g)
+      rcut[g] = (int)(std::lower_bound(F.Lptr.begin(), F.Lptr.end(), nt * g / G) - F.Lptr.begin());
+    stable_place(
+        G, n,
+        [&](int g, auto&& emit) {
+          for (int r = rcut[g]; r < rcut[g + 1]; ++r)
+            for (int64_t q = F.Lptr[r]; q < F.Lptr[r + 1]; ++q) emit(Trip{F.Lcol[q], r, F.Lval[q]});
+        },
+        F.Uptr, mirror_tmp, F.Ucol, F.Uval);
+  }
+  dvec<Trip>().swap(mirror_tmp);
   F.dinv_d.assign(n, 0.0);
   F.dinv_o.assign(n, 0.0);
   F.partner.assign(n, -1);
