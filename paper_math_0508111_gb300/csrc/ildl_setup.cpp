@@ -30,7 +30,7 @@
 #include <limits>
 #include <memory>
 #include <numeric>
-#include <queue>
+#include <functional>
 #include <type_traits>
 #include <utility>
 #include <cstdio>
@@ -215,15 +215,16 @@ int max_product_matching(const SymCsr& A, std::vector<int>& match_col, std::vect
     return c < kInf && c - u[i] - v[j] <= 1e-13 * (1.0 + std::fabs(u[i]) + std::fabs(v[j]));
   };
 #pragma omp parallel for schedule(static)
-  for (int i = 0; i < n; ++i)
-    for (int64_t p = A.ptr[i]; p < A.ptr[i + 1]; ++p)
-      if (A.col[p] == i) {
-        if (zero_rc(i, p)) {
-          match_row[i] = i;
-          match_col[i] = i;
-        }
-        break;
-      }
+  for (int i = 0; i < n; ++i) {
+    // rows are sorted by column: the diagonal by binary search
+    const int* b = A.col.data() + A.ptr[i];
+    const int* e = A.col.data() + A.ptr[i + 1];
+    const int* d = std::lower_bound(b, e, i);
+    if (d != e && *d == i && zero_rc(i, d - A.col.data())) {
+      match_row[i] = i;
+      match_col[i] = i;
+    }
+  }
   {
     // rounds: every open row proposes its first free zero-reduced-cost
     // column (in parallel); in row order a proposal wins if its column is
@@ -279,8 +280,12 @@ int max_product_matching(const SymCsr& A, std::vector<int>& match_col, std::vect
       W.pred.resize(n, -1);
       W.done.resize(n, 0);
     }
+    // min-heap of (distance, column) with lazy deletion, kept in the
+    // thread's scratch so that searches do not allocate
     using Item = std::pair<double, int>;
-    std::priority_queue<Item, std::vector<Item>, std::greater<Item>> heap;
+    std::vector<Item>& heap = W.heap;
+    heap.clear();
+    const std::greater<Item> later;
     R.touched.clear();
     R.scanned.clear();
     R.tree_rows.clear();
@@ -302,13 +307,15 @@ int max_product_matching(const SymCsr& A, std::vector<int>& match_col, std::vect
           if (W.dist[j] == kInf) R.touched.push_back(j);
           W.dist[j] = nd;
           W.pred[j] = i;
-          heap.push({nd, j});
+          heap.push_back({nd, j});
+          std::push_heap(heap.begin(), heap.end(), later);
         }
       }
       int jmin = -1;
       while (!heap.empty()) {
-        const Item it = heap.top();
-        heap.pop();
+        std::pop_heap(heap.begin(), heap.end(), later);
+        const Item it = heap.back();
+        heap.pop_back();
         if (!W.done[it.second] && it.first == W.dist[it.second]) {
           jmin = it.second;
           break;

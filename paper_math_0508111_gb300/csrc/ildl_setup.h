@@ -97,6 +97,7 @@ struct MatchWork {
     std::vector<double> dist;
     std::vector<int> pred;
     std::vector<char> done;
+    std::vector<std::pair<double, int>> heap;
   };
   std::vector<Search> threads;
 };
