@@ -93,3 +93,33 @@ def test_server_argument_validation_without_gpu(built_lib):
         assert L.jd_server_estimate(Lx, 5, ctypes.byref(x)) == _ffi.JD_OK
     assert b[0].value < b[1].value < b[2].value
     assert b[2].value > 56 * 56 * 10 ** 6  # three copies of ~57 entries per row at L = 100
+
+
+def test_binding_struct_layout_matches_header(tmp_path):
+    """Every parameter and statistics struct of the binding has the size and
+    field offsets that a C compiler gives the header's struct (a C program
+    built against include/ prints sizeof and offsetof)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    from paper_math_0508111_gb300 import _ffi
+    structs = {"ildl_params": _ffi.IldlParams, "ildl_info_t": _ffi.IldlInfo, "jd_params": _ffi.JdParams,
+               "jd_stats": _ffi.JdStats, "jd_server_params": _ffi.JdServerParams,
+               "jd_server_info": _ffi.JdServerInfo}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "anderson_jd.h"', "int main(void) {"]
+    want = []
+    for cname, py in structs.items():
+        lines.append('  printf("%%zu\\n", sizeof(%s));' % cname)
+        want.append(ctypes.sizeof(py))
+        for field, _ in py._fields_:
+            lines.append('  printf("%%zu\\n", offsetof(%s, %s));' % (cname, field))
+            want.append(getattr(py, field).offset)
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = [int(x) for x in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()]
+    assert got == want
