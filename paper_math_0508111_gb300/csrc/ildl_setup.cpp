@@ -732,10 +732,22 @@ int build_ildl(const SymCsr& A, const ildl_params& prm, HostFactor& F, bool dens
         d[i] = r > 0.0 ? 1.0 / std::sqrt(r) : 1.0;
       }
     }
+    // scale, and in the same pass collect what the candidates need:
+    // d1 = sum_{k != i} |s_ki| / |s_ii| (the 1-norm of the would-be L column)
+    std::vector<double> diag(m), offsum(m);
 #pragma omp parallel for schedule(static)
     for (int i = 0; i < m; ++i) {
       cum[i] *= d[i];
-      for (int64_t p = S.ptr[i]; p < S.ptr[i + 1]; ++p) S.val[p] *= d[i] * d[S.col[p]];
+      double o = 0.0, dg = 0.0;
+      for (int64_t p = S.ptr[i]; p < S.ptr[i + 1]; ++p) {
+        const int c = S.col[p];
+        const double sv = S.val[p] * (d[i] * d[c]);
+        S.val[p] = sv;
+        if (c == i) dg = sv;
+        else o += std::fabs(sv);
+      }
+      diag[i] = dg;
+      offsum[i] = o;
     }
     if (use_matching) {
       split_cycles(S, mc, groups);
@@ -747,19 +759,8 @@ int build_ildl(const SymCsr& A, const ildl_params& prm, HostFactor& F, bool dens
     t_match += tm_ms;
     const auto t_cand = Clock::now();
 
-    // 3. candidates: d1 = sum_{k != i} |s_ki| / |s_ii| (the 1-norm of the
-    // would-be L column); d2 = sum_k ||(s_ki, s_kj) B^{-1}||_1 for a 2x2 block
-    std::vector<double> diag(m), offsum(m);
-#pragma omp parallel for schedule(static)
-    for (int i = 0; i < m; ++i) {
-      double o = 0.0, dg = 0.0;
-      for (int64_t p = S.ptr[i]; p < S.ptr[i + 1]; ++p) {
-        if (S.col[p] == i) dg = S.val[p];
-        else o += std::fabs(S.val[p]);
-      }
-      diag[i] = dg;
-      offsum[i] = o;
-    }
+    // 3. candidates: d1 from the scaling pass above; d2 = sum_k
+    // ||(s_ki, s_kj) B^{-1}||_1 for a 2x2 block
     auto d1_of = [&](int i) { return diag[i] != 0.0 ? offsum[i] / std::fabs(diag[i]) : kInf; };
     // one or two candidates per group, computed in parallel and compacted in
     // group order (the same list a sequential pass produces)
