@@ -214,3 +214,101 @@ def test_aggressive_dropping_rejects_bad_tau(ajd):
     for tau in (-0.1, 1.0, float("nan")):
         with pytest.raises(ajd.JDError):
             ajd.Preconditioner.from_csr(A.indptr, A.indices, A.data, aggressive=tau)
+
+
+def _random_symmetric(n, seed, per_row=6):
+    """Sparse symmetric test matrix with entries over four decades (so that
+    the drop rule and 2x2 pivots come into play)."""
+    import scipy.sparse as sparse
+    g = np.random.default_rng(seed)
+    r, c = g.integers(0, n, n * per_row), g.integers(0, n, n * per_row)
+    v = g.choice([-1.0, 1.0], n * per_row) * 10.0 ** g.uniform(-4, 0, n * per_row)
+    M = sparse.coo_matrix((v, (r, c)), shape=(n, n)).tocsr()
+    M = (M + M.T + sparse.diags(g.choice([-1.0, 1.0], n) * 10.0 ** g.uniform(-1, 0.5, n))).tocsr()
+    M.sort_indices()
+    M.eliminate_zeros()
+    return M
+
+
+@pytest.mark.parametrize("case", [("lattice", 8, 16.5, 3, 0.0), ("lattice", 9, 12.0, 4, 0.4),
+                                  ("lattice", 8, 21.0, 6, -0.7), ("lattice", 8, 1.0, 3, 0.0),
+                                  ("random", 500, 1), ("random", 400, 3)])
+def test_one_level_factor_matches_oracle(ajd, case):
+    """A factor with one sparse level (the rest goes to the dense block),
+    element by element against the oracle's block elimination (Sections
+    6.2-6.3) on the same scaled matrix and pivots: D_B^{-1}, the column
+    block L_F of L with its drops, and the dense block's inverse against the
+    oracle's Schur complement.  The library's pivot choice is checked against
+    its rules: every 1x1 pivot meets 1 + d1 <= kappa, every 2x2 pivot
+    d2 < d1 and 1 + (largest column sum of its L block) <= kappa, and pivots
+    of the level are coupled by at most gamma.  Lattices (one with many 2x2
+    pivots and a relaxed level) and random sparse matrices whose entries span
+    four decades (many drops in L_F)."""
+    from oracle import ildl
+    if case[0] == "lattice":
+        A, _ = _csr(*case[1:3], case[3], PERIODIC, case[4])
+    else:
+        A = _random_symmetric(case[1], case[2])
+    n = A.shape[0]
+    F = ajd.Preconditioner.from_csr(A.indptr, A.indices, A.data, max_levels=1, n_dense=100).export()
+    assert F["levels"] == 1
+    perm, lp, pt = F["perm"], F["level_ptr"], F["partner"]
+    nb = int(lp[1])
+    s = np.empty(n)
+    s[perm] = F["scale"]
+    As = s[:, None] * A.toarray() * s[None, :]
+    blocks, p = [], 0
+    while p < nb:  # the pivot blocks in elimination order
+        if pt[p] >= 0:
+            assert pt[p] == p + 1 and pt[p + 1] == p
+            blocks.append([int(perm[p]), int(perm[p + 1])])
+            p += 2
+        else:
+            blocks.append([int(perm[p])])
+            p += 1
+    tau = 1.0 / (5.0 * np.sqrt(n))  # epsilon / kappa, epsilon = 1/sqrt(n)
+    B, C, D, LF, S = ildl.eliminate_level(As, blocks, tau)
+    assert list(perm[:nb]) == B and list(perm[nb:]) == C
+    # no entry within rounding of the drop threshold (so both sides must
+    # take the same drop decisions)
+    _, _, _, LF0, _ = ildl.eliminate_level(As, blocks, 0.0)
+    assert not np.any(np.abs(np.abs(LF0) - tau) <= 1e-9 * tau)
+    # D^{-1} per position
+    Dinv = np.linalg.inv(D)
+    for q in range(nb):
+        assert abs(F["dinv_d"][q] - Dinv[q, q]) <= 1e-12 * abs(Dinv[q, q])
+        if pt[q] >= 0:
+            assert abs(F["dinv_o"][q] - Dinv[q, pt[q]]) <= 1e-12 * np.abs(Dinv).max()
+    # L: only the block (C rows, B columns), same pattern and values
+    import scipy.sparse as sparse
+    Lx = sparse.csr_matrix((F["Lval"], F["Lcol"], F["Lptr"]), shape=(n, n)).toarray()
+    assert not Lx[:nb].any() and not Lx[nb:, nb:].any()
+    got = Lx[nb:, :nb]
+    assert np.array_equal(got != 0, LF != 0)
+    assert np.abs(got - LF).max() <= 1e-12 * np.abs(LF).max()
+    # dense block: the inverse of the oracle's Schur complement
+    Sd = S[np.ix_(range(len(C)), range(len(C)))]
+    off = ~np.eye(len(C), dtype=bool)
+    S0 = As[np.ix_(C, C)] - LF @ D @ LF.T
+    assert not np.any(off & (np.abs(np.abs(S0) - tau) <= 1e-9 * tau))
+    assert np.abs(F["dense_inv"] @ Sd - np.eye(len(C))).max() <= 1e-8
+    # the pivot rules
+    # a relaxed level widens the bound step by step, at most to 64 kappa
+    kappa, gamma = (5.0 if F["relaxed_levels"] == 0 else 320.0), min(0.02, 5.0 / np.sqrt(n))
+    absA = np.abs(As)
+    d1 = (absA.sum(axis=0) - np.diag(absA)) / np.abs(np.diag(As))
+    owner = {i: k for k, b in enumerate(blocks) for i in b}
+    for b in blocks:
+        if len(b) == 1:
+            assert 1.0 + d1[b[0]] <= kappa * (1 + 1e-12)
+        else:
+            i, j = b
+            R = As[:, b] @ np.linalg.inv(As[np.ix_(b, b)])
+            R[b] = 0.0
+            cs = np.abs(R).sum(axis=0)
+            assert cs.sum() < min(d1[i], d1[j])
+            assert 1.0 + cs.max() <= kappa * (1 + 1e-12)
+    for x in B:
+        for y in B:
+            if owner[x] != owner[y]:
+                assert absA[x, y] <= gamma
