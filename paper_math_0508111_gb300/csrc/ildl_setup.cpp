@@ -16,9 +16,10 @@
 //      pivots is then block diagonal, so every level is ONE parallel step of
 //      the triangular solves on the GPU;
 //   5. the level's column block of L is dropped at epsilon/kappa (Section
-//      6.2) and the Schur complement S = C - L D L^T formed explicitly and
-//      dropped the same way; the recursion continues on S until it is small
-//      enough to be factored densely.
+//      6.2), optionally sparsified further by the aggressive dropping of
+//      Section 6.3, and the Schur complement S = C - L D L^T formed
+//      explicitly and dropped at epsilon/kappa; the recursion continues on S
+//      until it is small enough to be factored densely.
 // The levels are finally concatenated into one global unit lower triangular
 // L (rows ordered level by level), one block diagonal D and one scaling.
 #include "ildl_setup.h"
