@@ -829,8 +829,7 @@ int build_ildl(const SymCsr& A, const ildl_params& prm, HostFactor& F, bool dens
     std::vector<int> acc;  // indices into cands
     auto block_nbrs = [&](int x) {
       blocked[x] = 1;
-      for (int64_t p = S.ptr[x]; p < S.ptr[x + 1]; ++p)
-        if (std::fabs(S.val[p]) > gamma) blocked[S.col[p]] = 1;
+      for (int64_t p = S.ptr[x]; p < S.ptr[x + 1]; ++p) blocked[S.col[p]] |= (char)(std::fabs(S.val[p]) > gamma);
     };
     auto try_accept = [&](double qmax) {
       for (size_t t = 0; t < cands.size(); ++t) {
