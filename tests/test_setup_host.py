@@ -312,3 +312,76 @@ def test_one_level_factor_matches_oracle(ajd, case):
         for y in B:
             if owner[x] != owner[y]:
                 assert absA[x, y] <= gamma
+
+
+def _pivot_blocks(F, lo, hi):
+    """Pivot blocks (lists of positions) of the positions [lo, hi)."""
+    pt, blocks, p = F["partner"], [], lo
+    while p < hi:
+        if pt[p] >= 0:
+            assert pt[p] == p + 1 and pt[p + 1] == p
+            blocks.append([p, p + 1])
+            p += 2
+        else:
+            blocks.append([p])
+            p += 1
+    return blocks
+
+
+@pytest.mark.parametrize("case", [("lattice", 8, 16.5, 3, 0.0), ("lattice", 9, 12.0, 5, 0.3), ("random", 500, 2)])
+def test_two_level_factor_matches_oracle(ajd, case):
+    """The composition of levels, element by element: a factor with two
+    sparse levels against the oracle's block elimination applied twice.
+    Level 1 works on the oracle's Schur complement of level 0, scaled by the
+    library's matching of that matrix (``ildl_matching``); the stored scaling
+    of a level-1 node is the product of its two scalings, a level-0 column of
+    L seen from a later row carries that row's second scaling, and the dense
+    block inverts the oracle's second Schur complement."""
+    import scipy.sparse as sparse
+    from oracle import ildl
+    if case[0] == "lattice":
+        A, _ = _csr(*case[1:3], case[3], PERIODIC, case[4])
+    else:
+        A = _random_symmetric(case[1], case[2])
+    n = A.shape[0]
+    tau = 1.0 / (5.0 * np.sqrt(n))
+    F = ajd.Preconditioner.from_csr(A.indptr, A.indices, A.data, max_levels=2, n_dense=100).export()
+    assert F["levels"] == 2
+    perm, lp, sc = F["perm"], F["level_ptr"], F["scale"]
+    n0, n1 = int(lp[1]), int(lp[2])
+    # level 0 on the library's scaling of A
+    _, s1, _ = ajd.matching(A.indptr, A.indices, A.data)
+    assert np.array_equal(sc[:n0], s1[perm[:n0]])
+    As1 = s1[:, None] * A.toarray() * s1[None, :]
+    blocks0 = [[int(perm[q]) for q in b] for b in _pivot_blocks(F, 0, n0)]
+    B0, C0, D0, LF0, S1 = ildl.eliminate_level(As1, blocks0, tau)
+    assert list(perm[:n0]) == B0
+    # level 1 on the oracle's Schur complement, scaled by the library's matching of it
+    S1c = sparse.csr_matrix(S1)
+    S1c.sort_indices()
+    assert all(S1c[i, i] != 0 for i in range(S1.shape[0]))
+    _, s2, _ = ajd.matching(S1c.indptr, S1c.indices, S1c.data)
+    loc = {g: k for k, g in enumerate(C0)}
+    later = np.array([loc[int(g)] for g in perm[n0:]])  # local index in level 1 of positions n0..n-1
+    assert np.allclose(sc[n0:], s1[perm[n0:]] * s2[later], rtol=1e-12, atol=0)
+    As2 = s2[:, None] * S1 * s2[None, :]
+    blocks1 = [[int(later[q - n0]) for q in b] for b in _pivot_blocks(F, n0, n1)]
+    B1, C1, D1, LF1, S2 = ildl.eliminate_level(As2, blocks1, tau)
+    assert list(later[:n1 - n0]) == B1 and list(later[n1 - n0:]) == C1
+    for As_, blocks_ in ((As1, blocks0), (As2, blocks1)):  # no entry within rounding of the drop threshold
+        _, _, _, LFx, _ = ildl.eliminate_level(As_, blocks_, 0.0)
+        assert not np.any(np.abs(np.abs(LFx) - tau) <= 1e-9 * tau)
+    # D^{-1} of both levels
+    Dinv = np.zeros(n)
+    Dinv[:n0] = np.diag(np.linalg.inv(D0))
+    Dinv[n0:n1] = np.diag(np.linalg.inv(D1))
+    assert np.allclose(F["dinv_d"][:n1], Dinv[:n1], rtol=1e-11, atol=0)
+    # L: level-0 columns (rows n0.., times the row's level-1 scaling), level-1 columns (dense rows)
+    Lx = sparse.csr_matrix((F["Lval"], F["Lcol"], F["Lptr"]), shape=(n, n)).toarray()
+    want = np.zeros((n, n))
+    want[n0:, :n0] = LF0[later] * s2[later][:, None]
+    want[n1:, n0:n1] = LF1
+    assert np.array_equal(Lx != 0, want != 0)
+    assert np.abs(Lx - want).max() <= 1e-11 * np.abs(want).max()
+    # dense block: inverse of the second Schur complement
+    assert np.abs(F["dense_inv"] @ S2 - np.eye(S2.shape[0])).max() <= 1e-8
