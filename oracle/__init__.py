@@ -28,6 +28,9 @@ matching   maximum-product transversal (Eqs. (5.1)-(5.2)) by a dense
 krylov     plain restatements of the Krylov pieces of the hot path: the
            simplified QMR recurrences (Section 4.2), classical Gram–Schmidt
            with reorthogonalisation, and the Rayleigh–Ritz step.
+ildl       one level of the incomplete block LDL^T (Sections 6.2-6.3):
+           pivot blocks, L_F = F D_B^{-1} and the Schur complement with the
+           drop rule, densely.
 
 Every function says which passage it follows.  Pins that tie the oracle to
 something other than itself live in ``tests/test_oracle_*.py``.
