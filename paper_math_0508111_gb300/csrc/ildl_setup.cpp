@@ -573,8 +573,8 @@ void stable_place(int G, int nr, Produce produce, std::vector<int64_t>& ptr, dve
   for (int r = 0; r < nr; ++r) ptr[(size_t)r + 1] += ptr[r];
   for (int b = 0; b < nblk; ++b) bptr[b + 1] += bptr[b];
   resize_discard(tmp, bptr[nblk]);
-  col.resize(ptr[nr]);
-  val.resize(ptr[nr]);
+  resize_discard(col, ptr[nr]);
+  resize_discard(val, ptr[nr]);
 #pragma omp parallel for schedule(static)
   for (int g = 0; g < G; ++g) {
     int64_t* bo = boff.data() + (size_t)g * nblk;
@@ -689,8 +689,8 @@ int build_ildl(const SymCsr& A, const ildl_params& prm, HostFactor& F, bool dens
   dvec<double> lval;
   dvec<int> agg_node;                                // L_F after aggressive dropping
   dvec<double> agg_val;
-  std::vector<std::vector<int>> cn, ucol;            // per-chunk row output
-  std::vector<std::vector<double>> cv, uval;
+  std::vector<std::vector<int>> ucol;                // per-chunk row output
+  std::vector<std::vector<double>> uval;
   dvec<int> rec_row, rec_blk, crow;                  // Schur records
   dvec<double> rec_a, rec_b, c1, c2;
   dvec<int64_t> rec_slot;
@@ -902,69 +902,53 @@ int build_ildl(const SymCsr& A, const ildl_params& prm, HostFactor& F, bool dens
     for (int i = 0; i < m; ++i)
       if (!inB[i]) { cidx[i] = mc_n++; cnodes.push_back(i); }
 
-    // 6. L_F = F D_B^{-1} row by row (rows: C nodes), dropped at tau.
-    // Entries: (C row, B node, value) with the B node's block.
-    std::vector<int64_t> lptr(mc_n + 1, 0);
-    const int nchunk = std::max(1, std::min(mc_n, 8 * omp_get_max_threads()));
-    if ((int)cn.size() < nchunk) {
-      cn.resize(nchunk);
-      cv.resize(nchunk);
-      ucol.resize(nchunk);
-      uval.resize(nchunk);
-    }
+    // 6. L_F = F D_B^{-1}, dropped at tau, built from the pivot blocks' own
+    // rows: S is symmetric, so row a of S holds column a of F.  Each block
+    // emits (C row, node, value) for the C rows its nodes reach, blocks in
+    // elimination order (node a before node b), and a stable placement by C
+    // row lists every row's entries by block -- the rows that a pass over
+    // all C rows gives, at the cost of the pivot rows alone.
+    std::vector<int64_t> lptr;
     {
-      std::vector<int> rowcnt(mc_n, 0);
-#pragma omp parallel
-      {
-        std::vector<double> fa(acc.size(), 0.0), fb(acc.size(), 0.0);
-        std::vector<int> touched;
-#pragma omp for schedule(dynamic, 1)
-        for (int ch = 0; ch < nchunk; ++ch) {
-          const int r0 = (int)((int64_t)mc_n * ch / nchunk), r1 = (int)((int64_t)mc_n * (ch + 1) / nchunk);
-          cn[ch].clear();
-          cv[ch].clear();
-          for (int r = r0; r < r1; ++r) {
-            const int k = cnodes[r];
-            touched.clear();
-            for (int64_t p = S.ptr[k]; p < S.ptr[k + 1]; ++p) {
-              const int x = S.col[p];
-              if (!inB[x]) continue;
-              const int b = blk_of[x];
-              const Cand& cd = cands[acc[b]];
-              if (fa[b] == 0.0 && fb[b] == 0.0) touched.push_back(b);
-              if (x == cd.a) fa[b] += S.val[p];
-              else fb[b] += S.val[p];
+      const int nacc = (int)acc.size();
+      const int G = std::max(1, std::min(omp_get_max_threads(), nacc / 256));
+      auto produce = [&](int g, auto&& emit) {
+        const int b0 = (int)((int64_t)nacc * g / G), b1 = (int)((int64_t)nacc * (g + 1) / G);
+        for (int b = b0; b < b1; ++b) {
+          const Cand& cd = cands[acc[b]];
+          if (cd.b < 0) {
+            for (int64_t p = S.ptr[cd.a]; p < S.ptr[cd.a + 1]; ++p) {
+              const int r = cidx[S.col[p]];
+              if (r < 0) continue;  // B nodes
+              const double l = S.val[p] * binv[3 * b];
+              if (std::fabs(l) >= tau && l != 0.0) emit(Trip{r, cd.a, l});
             }
-            sort_ints(touched.data(), (int)touched.size(), 32);
-            const size_t before = cn[ch].size();
-            for (int b : touched) {
-              const Cand& cd = cands[acc[b]];
-              if (cd.b < 0) {
-                const double l = fa[b] * binv[3 * b];
-                if (std::fabs(l) >= tau && l != 0.0) { cn[ch].push_back(cd.a); cv[ch].push_back(l); }
-              } else {
-                const double l1 = fa[b] * binv[3 * b] + fb[b] * binv[3 * b + 1];
-                const double l2 = fa[b] * binv[3 * b + 1] + fb[b] * binv[3 * b + 2];
-                if (std::fabs(l1) >= tau && l1 != 0.0) { cn[ch].push_back(cd.a); cv[ch].push_back(l1); }
-                if (std::fabs(l2) >= tau && l2 != 0.0) { cn[ch].push_back(cd.b); cv[ch].push_back(l2); }
-              }
-              fa[b] = fb[b] = 0.0;
-            }
-            rowcnt[r] = (int)(cn[ch].size() - before);
+            continue;
+          }
+          // 2x2: (s_ka, s_kb) for every row k that rows a and b reach
+          int64_t pa = S.ptr[cd.a], pb = S.ptr[cd.b];
+          const int64_t ea = S.ptr[cd.a + 1], eb = S.ptr[cd.b + 1];
+          while (pa < ea || pb < eb) {
+            int k;
+            double fa = 0.0, fb = 0.0;
+            if (pb >= eb || (pa < ea && S.col[pa] < S.col[pb])) { k = S.col[pa]; fa = S.val[pa++]; }
+            else if (pa >= ea || S.col[pb] < S.col[pa]) { k = S.col[pb]; fb = S.val[pb++]; }
+            else { k = S.col[pa]; fa = S.val[pa++]; fb = S.val[pb++]; }
+            const int r = cidx[k];
+            if (r < 0) continue;
+            const double l1 = fa * binv[3 * b] + fb * binv[3 * b + 1];
+            const double l2 = fa * binv[3 * b + 1] + fb * binv[3 * b + 2];
+            if (std::fabs(l1) >= tau && l1 != 0.0) emit(Trip{r, cd.a, l1});
+            if (std::fabs(l2) >= tau && l2 != 0.0) emit(Trip{r, cd.b, l2});
           }
         }
-      }
-      for (int r = 0; r < mc_n; ++r) lptr[r + 1] = lptr[r] + rowcnt[r];
-      // chunks hold consecutive rows, so chunk ch starts at the row pointer of
-      // its first row; copied in parallel
-      resize_discard(lnode, lptr[mc_n]);
-      resize_discard(lval, lptr[mc_n]);
-#pragma omp parallel for schedule(dynamic, 1)
-      for (int ch = 0; ch < nchunk; ++ch) {
-        const int r0 = (int)((int64_t)mc_n * ch / nchunk);
-        std::copy(cn[ch].begin(), cn[ch].end(), lnode.begin() + lptr[r0]);
-        std::copy(cv[ch].begin(), cv[ch].end(), lval.begin() + lptr[r0]);
-      }
+      };
+      stable_place(G, mc_n, produce, lptr, mirror_tmp, lnode, lval);
+    }
+    const int nchunk = std::max(1, std::min(mc_n, 8 * omp_get_max_threads()));
+    if ((int)ucol.size() < nchunk) {
+      ucol.resize(nchunk);
+      uval.resize(nchunk);
     }
     if (agg_tau > 0.0 && lptr[mc_n] > 0) {
       // 6b. aggressive dropping (Section 6.3): l_ij goes when |l_ij| <=
@@ -1309,9 +1293,7 @@ int build_ildl(const SymCsr& A, const ildl_params& prm, HostFactor& F, bool dens
     release(lval);
     release(agg_node);
     release(agg_val);
-    release(cn);
     release(ucol);
-    release(cv);
     release(uval);
     release(rec_row);
     release(rec_blk);
