@@ -134,7 +134,8 @@ def test_setup_rejects_bad_input(ajd):
         ajd.Preconditioner.from_csr(np.array([0, 2, 3]), np.array([1, 0, 1]), np.array([1.0, 2.0, 1.0]))
 
 
-def test_setup_independent_of_thread_count(ajd):
+@pytest.mark.parametrize("aggressive", [0.0, 0.1])
+def test_setup_independent_of_thread_count(ajd, aggressive):
     """The parallel setup (matching searches in batches, parallel scatters,
     per-chunk rows) gives the same factor, bit for bit, with 1 and 4 host
     threads.  L = 24 is large enough that the scatters and the Schur mirror
@@ -148,7 +149,8 @@ def test_setup_independent_of_thread_count(ajd):
     try:
         for t in (1, 4):
             gomp.omp_set_num_threads(t)
-            out.append(ajd.Preconditioner.from_csr(A.indptr, A.indices, A.data, n_dense=300).export())
+            out.append(ajd.Preconditioner.from_csr(A.indptr, A.indices, A.data, n_dense=300,
+                                                   aggressive=aggressive).export())
     finally:
         gomp.omp_set_num_threads(max(1, __import__("os").cpu_count() or 1))
     assert out[0]["levels"] >= 3
