@@ -2,6 +2,7 @@
 
     python -m paper_math_0508111_gb300.profile apply   [--L 70] [--reps 5] [--only fp32|fp64|mixed]
     python -m paper_math_0508111_gb300.profile stencil [--L 256] [--reps 20] [--vectors 1]
+    python -m paper_math_0508111_gb300.profile setup   [--L 100] [--threads 16,7]
 
 ``apply`` builds the preconditioner of A - 0 I for an L^3 lattice (W = 16.5,
 seed 1) and times its application in binary32, binary64 and the mixed form
@@ -10,7 +11,10 @@ applications each, then ``reps`` timed ones, CUDA events on the current
 stream.  ``stencil`` times y = A x in binary64
 and binary32 with the L2 flushed before every repetition.  Both print one
 JSON line per case.  Run them under ncu with ``-k regex:persistent`` or
-``-k regex:stencil`` to capture the kernel of interest.
+``-k regex:stencil`` to capture the kernel of interest.  ``setup`` times the
+whole construction of the preconditioner of A - 0 I for an L^3 lattice
+(host setup, dense-tail inversion on the device, upload) once per host
+thread count, with the OpenMP thread count set through libgomp.
 """
 import argparse
 import json
@@ -70,16 +74,37 @@ def stencil_case(L, reps, m=1):
                           "GBps": nbytes * h.n * m / (ms * 1e-3) / 1e9}), flush=True)
 
 
+def setup_case(L, threads):
+    import ctypes
+    import ctypes.util
+    import time
+    gomp = ctypes.CDLL(ctypes.util.find_library("gomp") or "libgomp.so.1")
+    with ajd.Anderson(L, 16.5, 1) as h:
+        for t in threads:
+            gomp.omp_set_num_threads(int(t))
+            t0 = time.perf_counter()
+            P = ajd.Preconditioner.from_lattice(h, 0.0)
+            wall = time.perf_counter() - t0
+            inf = P.info()
+            print(json.dumps({"case": "setup", "L": L, "threads": int(t), "wall_s": wall, "setup_ms": inf["setup_ms"],
+                              "match_ms": inf["match_ms"], "levels": inf["levels"], "nnz_L": inf["nnz_L"]}),
+                  flush=True)
+            P.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("what", choices=["apply", "stencil"])
+    ap.add_argument("what", choices=["apply", "stencil", "setup"])
     ap.add_argument("--L", type=int, default=None)
     ap.add_argument("--reps", type=int, default=None)
     ap.add_argument("--only", choices=["fp32", "fp64", "mixed"], default=None)
     ap.add_argument("--vectors", type=int, default=1, help="stencil: vectors per launch")
+    ap.add_argument("--threads", default="16,7", help="setup: host thread counts, comma separated")
     a = ap.parse_args()
     if a.what == "apply":
         apply_case(a.L or 70, a.reps or 5, a.only)
+    elif a.what == "setup":
+        setup_case(a.L or 100, [int(t) for t in a.threads.split(",")])
     else:
         stencil_case(a.L or 256, a.reps or 20, a.vectors)
 
