@@ -430,8 +430,6 @@ void split_cycles(const SymCsr& S, const std::vector<int>& match_col,
                   std::vector<std::pair<int, int>>& groups) {
   const int n = S.n;
   groups.clear();
-  std::vector<char> seen(n, 0);
-  std::vector<int> cyc;
   auto union_nnz = [&](int a, int b) {
     int64_t pa = S.ptr[a], pb = S.ptr[b], cnt = 0;
     while (pa < S.ptr[a + 1] || pb < S.ptr[b + 1]) {
@@ -442,20 +440,14 @@ void split_cycles(const SymCsr& S, const std::vector<int>& match_col,
     }
     return cnt;
   };
-  for (int j0 = 0; j0 < n; ++j0) {
-    if (seen[j0]) continue;
-    cyc.clear();
-    int j = j0;
-    do {
-      seen[j] = 1;
-      cyc.push_back(j);
-      j = match_col[j];
-    } while (j != j0 && j >= 0 && !seen[j]);
+  // the groups of one cycle (members in cycle order, starting at its
+  // smallest index), appended to `out`
+  auto split = [&](const std::vector<int>& cyc, std::vector<std::pair<int, int>>& out) {
     const int len = (int)cyc.size();
     if (len == 1) {
-      groups.push_back({cyc[0], -1});
+      out.push_back({cyc[0], -1});
     } else if (len == 2) {
-      groups.push_back({std::min(cyc[0], cyc[1]), std::max(cyc[0], cyc[1])});
+      out.push_back({std::min(cyc[0], cyc[1]), std::max(cyc[0], cyc[1])});
     } else if (len % 2 == 0) {
       double score[2] = {0.0, 0.0};
       int64_t nnz[2] = {0, 0};
@@ -469,7 +461,7 @@ void split_cycles(const SymCsr& S, const std::vector<int>& match_col,
       if (score[1] > score[0] || (score[1] == score[0] && nnz[1] < nnz[0])) opt = 1;
       for (int k = opt; k < len + opt; k += 2) {
         const int a = cyc[k % len], b = cyc[(k + 1) % len];
-        groups.push_back({std::min(a, b), std::max(a, b)});
+        out.push_back({std::min(a, b), std::max(a, b)});
       }
     } else {
       int t = 0;
@@ -477,12 +469,75 @@ void split_cycles(const SymCsr& S, const std::vector<int>& match_col,
         const double dk = std::fabs(lookup(S, cyc[k], cyc[k])), dt = std::fabs(lookup(S, cyc[t], cyc[t]));
         if (dk > dt || (dk == dt && cyc[k] < cyc[t])) t = k;
       }
-      groups.push_back({cyc[t], -1});
+      out.push_back({cyc[t], -1});
       for (int k = 1; k < len; k += 2) {
         const int a = cyc[(t + k) % len], b = cyc[(t + k + 1) % len];
-        groups.push_back({std::min(a, b), std::max(a, b)});
+        out.push_back({std::min(a, b), std::max(a, b)});
       }
     }
+  };
+  std::vector<char> seen(n, 0);
+  std::vector<int> cyc;
+  bool perm = true;
+  for (int j = 0; j < n && perm; ++j) perm = match_col[j] >= 0;
+  if (!perm) {
+    // a partial matching (chains as well as cycles): one walk per unseen
+    // index, in index order
+    for (int j0 = 0; j0 < n; ++j0) {
+      if (seen[j0]) continue;
+      cyc.clear();
+      int j = j0;
+      do {
+        seen[j] = 1;
+        cyc.push_back(j);
+        j = match_col[j];
+      } while (j != j0 && j >= 0 && !seen[j]);
+      split(cyc, groups);
+    }
+    return;
+  }
+  // a permutation: every cycle is emitted at its smallest member, in index
+  // order.  Fixed points and 2-cycles (nearly all of them) are placed in
+  // parallel; longer cycles are walked in index order and their groups
+  // copied into place.
+  std::vector<int> ng(n + 1, 0);  // groups emitted at index j, then offsets
+#pragma omp parallel for schedule(static)
+  for (int j = 0; j < n; ++j) {
+    const int k = match_col[j];
+    if (k == j) ng[j + 1] = 1;
+    else if (match_col[k] == j) ng[j + 1] = j < k ? 1 : 0;
+    else ng[j + 1] = -1;  // in a longer cycle
+  }
+  std::vector<std::pair<int, int>> longg;          // groups of the longer cycles
+  std::vector<std::pair<int, int64_t>> longat;     // (leader, first group in longg)
+  for (int j0 = 0; j0 < n; ++j0) {
+    if (ng[j0 + 1] >= 0 || seen[j0]) continue;
+    cyc.clear();
+    int j = j0;
+    do {
+      seen[j] = 1;
+      cyc.push_back(j);
+      j = match_col[j];
+    } while (j != j0);
+    const size_t before = longg.size();
+    split(cyc, longg);
+    longat.push_back({j0, (int64_t)before});
+    for (size_t q = 1; q < cyc.size(); ++q) ng[cyc[q] + 1] = 0;
+    ng[j0 + 1] = (int)(longg.size() - before);
+  }
+  for (int j = 0; j < n; ++j) ng[j + 1] += ng[j];
+  groups.resize(ng[n]);
+#pragma omp parallel for schedule(static)
+  for (int j = 0; j < n; ++j) {
+    const int k = match_col[j];
+    if (k == j) groups[ng[j]] = {j, -1};
+    else if (match_col[k] == j && j < k) groups[ng[j]] = {j, k};
+  }
+#pragma omp parallel for schedule(dynamic, 64)
+  for (size_t c = 0; c < longat.size(); ++c) {
+    const int j0 = longat[c].first;
+    const int64_t from = longat[c].second;
+    for (int q = 0; q < ng[j0 + 1] - ng[j0]; ++q) groups[ng[j0] + q] = longg[from + q];
   }
 }
 
@@ -854,26 +909,34 @@ int build_ildl(const SymCsr& A, const ildl_params& prm, HostFactor& F, bool dens
 
     const double tc_ms = ms_since(t_cand);
     const auto t_lf = Clock::now();
-    // 5. local numbering: B in accepted order, C in index order
+    // 5. local numbering: B in accepted order, C in index order (both
+    // built in parallel: block positions and C indices from prefix sums)
+    const int nacc_blocks = (int)acc.size();
     std::vector<int> blk_of(m, -1), cidx(m, -1);
     std::vector<double> binv(3 * acc.size());  // symmetric 2x2 (or 1x1) inverse per block
     std::vector<double> bmat(3 * acc.size());
     const int level_start = (int)order.size();
-    for (size_t b = 0; b < acc.size(); ++b) {
+    std::vector<int> bpos(nacc_blocks + 1, 0);  // first position of each block in the level
+    for (int b = 0; b < nacc_blocks; ++b) bpos[b + 1] = bpos[b] + (cands[acc[b]].b < 0 ? 1 : 2);
+    order.resize((size_t)level_start + bpos[nacc_blocks]);
+    int n2 = 0;
+#pragma omp parallel for schedule(static) reduction(+ : n2)
+    for (int b = 0; b < nacc_blocks; ++b) {
       const Cand& cd = cands[acc[b]];
-      blk_of[cd.a] = (int)b;
+      const int o = level_start + bpos[b];
+      blk_of[cd.a] = b;
       if (cd.b < 0) {
         const double piv = diag[cd.a];
         bmat[3 * b] = piv;
         binv[3 * b] = 1.0 / piv;
         binv[3 * b + 1] = binv[3 * b + 2] = 0.0;
-        order.push_back(gid[cd.a]);
+        order[o] = gid[cd.a];
         sc[gid[cd.a]] = cum[cd.a];
         dd[gid[cd.a]] = 1.0 / piv;
         dof[gid[cd.a]] = 0.0;
         part[gid[cd.a]] = -1;
       } else {
-        blk_of[cd.b] = (int)b;
+        blk_of[cd.b] = b;
         const double a = diag[cd.a], c = diag[cd.b];
         const double s = 0.5 * (lookup(S, cd.a, cd.b) + lookup(S, cd.b, cd.a));
         const double det = a * c - s * s;
@@ -883,8 +946,8 @@ int build_ildl(const SymCsr& A, const ildl_params& prm, HostFactor& F, bool dens
         binv[3 * b] = c / det;
         binv[3 * b + 1] = -s / det;
         binv[3 * b + 2] = a / det;
-        order.push_back(gid[cd.a]);
-        order.push_back(gid[cd.b]);
+        order[o] = gid[cd.a];
+        order[o + 1] = gid[cd.b];
         sc[gid[cd.a]] = cum[cd.a];
         sc[gid[cd.b]] = cum[cd.b];
         dd[gid[cd.a]] = c / det;
@@ -892,15 +955,37 @@ int build_ildl(const SymCsr& A, const ildl_params& prm, HostFactor& F, bool dens
         dof[gid[cd.a]] = dof[gid[cd.b]] = -s / det;
         part[gid[cd.a]] = gid[cd.b];
         part[gid[cd.b]] = gid[cd.a];
-        ++F.n_2x2;
+        ++n2;
       }
     }
+    F.n_2x2 += n2;
     level_ptr.push_back((int)order.size());
     F.level_sizes.push_back((int)order.size() - level_start);
-    int mc_n = 0;
+    // C nodes in index order: per-chunk counts, then each chunk numbers its own
     std::vector<int> cnodes;
-    for (int i = 0; i < m; ++i)
-      if (!inB[i]) { cidx[i] = mc_n++; cnodes.push_back(i); }
+    int mc_n = 0;
+    {
+      const int T = std::max(1, std::min(omp_get_max_threads(), m / 16384));
+      std::vector<int> ccnt(T + 1, 0);
+#pragma omp parallel for schedule(static)
+      for (int t = 0; t < T; ++t) {
+        int k = 0;
+        for (int i = (int)((int64_t)m * t / T); i < (int)((int64_t)m * (t + 1) / T); ++i) k += !inB[i];
+        ccnt[t + 1] = k;
+      }
+      for (int t = 0; t < T; ++t) ccnt[t + 1] += ccnt[t];
+      mc_n = ccnt[T];
+      cnodes.resize(mc_n);
+#pragma omp parallel for schedule(static)
+      for (int t = 0; t < T; ++t) {
+        int k = ccnt[t];
+        for (int i = (int)((int64_t)m * t / T); i < (int)((int64_t)m * (t + 1) / T); ++i)
+          if (!inB[i]) {
+            cidx[i] = k;
+            cnodes[k++] = i;
+          }
+      }
+    }
 
     // 6. L_F = F D_B^{-1}, dropped at tau, built from the pivot blocks' own
     // rows: S is symmetric, so row a of S holds column a of F.  Each block
@@ -1266,6 +1351,7 @@ int build_ildl(const SymCsr& A, const ildl_params& prm, HostFactor& F, bool dens
     // next level's numbering
     std::vector<int> gid2(mc_n);
     std::vector<double> cum2(mc_n);
+#pragma omp parallel for schedule(static)
     for (int r = 0; r < mc_n; ++r) {
       gid2[r] = gid[cnodes[r]];
       cum2[r] = cum[cnodes[r]];
