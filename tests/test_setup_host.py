@@ -387,3 +387,58 @@ def test_two_level_factor_matches_oracle(ajd, case):
     assert np.abs(Lx - want).max() <= 1e-11 * np.abs(want).max()
     # dense block: inverse of the second Schur complement
     assert np.abs(F["dense_inv"] @ S2 - np.eye(S2.shape[0])).max() <= 1e-8
+
+
+def _off_diagonal_dominant(n, seed):
+    """Sparse symmetric matrix with tiny diagonal: the matching goes off the
+    diagonal, mostly in 2-cycles, with a few long cycles."""
+    import scipy.sparse as sparse
+    g = np.random.default_rng(seed)
+    r, c = g.integers(0, n, n * 4), g.integers(0, n, n * 4)
+    v = g.choice([-1.0, 1.0], n * 4) * 10.0 ** g.uniform(-2, 0, n * 4)
+    M = sparse.coo_matrix((v, (r, c)), shape=(n, n)).tocsr()
+    M = (M + M.T + sparse.diags(g.choice([-1.0, 1.0], n) * 10.0 ** g.uniform(-4, -2, n))).tocsr()
+    M.sort_indices()
+    M.eliminate_zeros()
+    return M
+
+
+@pytest.mark.parametrize("seed", [1, 2, 5, 14])
+def test_cycle_split_rules(ajd, seed):
+    """The 1x1/2x2 groups of the library's matching follow the cycle-split
+    readings of Section 5.2 on matrices with long cycles: an odd cycle keeps
+    its member of largest |diagonal| (scaled matrix) as the 1x1 and pairs
+    the rest in cycle order; an even cycle takes the split with the larger
+    sum of log|off-diagonal| (ties: fewer nonzeros in the merged rows).  The
+    seeds give odd cycles of length 3 to 93; even cycles longer than 2 only
+    arise from ties (for a symmetric matrix the product along an even cycle
+    is the geometric mean of its two splits, so one split is at least as
+    good), and the rule for them is checked wherever one appears."""
+    A = _off_diagonal_dominant(3000, seed)
+    mc, sc, pt = ajd.matching(A.indptr, A.indices, A.data)
+    S = (sc[:, None] * A.toarray()) * sc[None, :]
+    pattern = [set(A.indices[A.indptr[i]:A.indptr[i + 1]]) for i in range(A.shape[0])]
+    long_cycles = 0
+    for cyc in matching.cycles(mc):
+        m = len(cyc)
+        if m == 1:
+            want = matching.split_cycle(cyc, 0)
+        elif m % 2 == 0:
+            def score(s):
+                return sum(np.log(abs(S[a, b]) + 1e-300) for a, b in matching.split_cycle(cyc, s))
+
+            def nnz(s):
+                return sum(len(pattern[a] | pattern[b]) for a, b in matching.split_cycle(cyc, s))
+            s = 1 if (score(1) > score(0) or (score(1) == score(0) and nnz(1) < nnz(0))) else 0
+            want = matching.split_cycle(cyc, s)
+        else:
+            d = np.abs(S[cyc, cyc])
+            t = max(range(m), key=lambda k: (d[k], -cyc[k]))
+            want = matching.split_cycle(cyc, t)
+        long_cycles += m > 2
+        for grp in want:
+            if len(grp) == 1:
+                assert pt[grp[0]] == -1
+            else:
+                assert pt[grp[0]] == grp[1] and pt[grp[1]] == grp[0]
+    assert long_cycles >= 1
