@@ -300,9 +300,17 @@ def test_one_level_factor_matches_oracle(ajd, case):
     absA = np.abs(As)
     d1 = (absA.sum(axis=0) - np.diag(absA)) / np.abs(np.diag(As))
     owner = {i: k for k, b in enumerate(blocks) for i in b}
+    _, _, pt0 = ajd.matching(A.indptr, A.indices, A.data)  # the level's matched pairs
     for b in blocks:
         if len(b) == 1:
             assert 1.0 + d1[b[0]] <= kappa * (1 + 1e-12)
+            x, y = b[0], pt0[b[0]]
+            if y >= 0:  # a matched pair taken apart: its 2x2 form was not better (d2 >= d1)
+                Bxy = As[np.ix_([x, y], [x, y])]
+                if abs(np.linalg.det(Bxy)) > 1e-300:
+                    R = As[:, [x, y]] @ np.linalg.inv(Bxy)
+                    R[[x, y]] = 0.0
+                    assert np.abs(R).sum() >= min(d1[x], d1[y]) * (1 - 1e-12)
         else:
             i, j = b
             R = As[:, b] @ np.linalg.inv(As[np.ix_(b, b)])
