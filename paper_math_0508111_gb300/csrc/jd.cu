@@ -1595,7 +1595,9 @@ extern "C" int jd_solve_batch(const anderson_t* hs, int nprob, const double* sig
   if (stats) std::memset(stats, 0, sizeof(jd_stats) * nprob);
   const int nthr = std::max(1, std::min(setup_threads > 0 ? setup_threads : 2, nprob));
   const int omp_total = std::max(1, omp_get_max_threads());
-  const int omp_each = std::max(1, (omp_total - 1) / nthr);  // one core stays with the solving thread
+  // the host cores are shared by the setups: the solving thread waits on
+  // the device in blocking synchronisation and needs almost no CPU
+  const int omp_each = std::max(1, omp_total / nthr);
   int dev = 0;
   AJD_CUDA(cudaGetDevice(&dev));
 
