@@ -152,8 +152,8 @@ void free_dev(DevFactor<T>& d) {
   d = DevFactor<T>();
 }
 
-template <typename S, typename D>
-int upload(D** dst, const std::vector<S>& src, cudaStream_t st) {
+template <typename S, typename D, class Alloc>
+int upload(D** dst, const std::vector<S, Alloc>& src, cudaStream_t st) {
   *dst = nullptr;
   if (src.empty()) return JD_OK;
   const size_t n = src.size();
@@ -163,7 +163,7 @@ int upload(D** dst, const std::vector<S>& src, cudaStream_t st) {
     AJD_CUDA(cudaMemcpyAsync(*dst, src.data(), n * sizeof(D), cudaMemcpyHostToDevice, st));
     AJD_CUDA(cudaStreamSynchronize(st));
   } else {
-    std::vector<D> tmp(n);
+    dvec<D> tmp(n);  // first touched by the parallel conversion
 #pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < (int64_t)n; ++i) tmp[i] = D(src[i]);
     AJD_CUDA(cudaMemcpyAsync(*dst, tmp.data(), n * sizeof(D), cudaMemcpyHostToDevice, st));
@@ -354,7 +354,7 @@ template int ildl_apply_dev<float>(const ildl_s*, const float*, float*, cudaStre
 
 // Invert the dense trailing block (host matrix in, host inverse out) on the
 // current device.
-int invert_dense_on_device(std::vector<double>& M, int m, cudaStream_t st) {
+int invert_dense_on_device(dvec<double>& M, int m, cudaStream_t st) {
   if (m == 0) return JD_OK;
   const size_t bytes = (size_t)m * m * sizeof(double);
   double *A = nullptr, *X = nullptr, *f = nullptr;

@@ -651,7 +651,7 @@ void stable_place(int G, int nr, Produce produce, std::vector<int64_t>& ptr, dve
 }
 
 // Gauss–Jordan inverse with partial pivoting (row-major, in place on a copy).
-bool dense_inverse(int m, std::vector<double>& M, std::vector<double>& inv) {
+bool dense_inverse(int m, dvec<double>& M, dvec<double>& inv) {
   inv.assign((size_t)m * m, 0.0);
   for (int i = 0; i < m; ++i) inv[(size_t)i * m + i] = 1.0;
   for (int c = 0; c < m; ++c) {
@@ -1393,11 +1393,15 @@ int build_ildl(const SymCsr& A, const ildl_params& prm, HostFactor& F, bool dens
     release(rwork);
   }
   // trailing dense block
-  std::vector<double> dense_inv;
+  dvec<double> dense_inv;
   if (nd > 0) {
-    std::vector<double> M((size_t)nd * nd, 0.0);
-    for (int i = 0; i < nd; ++i)
-      for (int64_t p = S.ptr[i]; p < S.ptr[i + 1]; ++p) M[(size_t)i * nd + S.col[p]] = S.val[p];
+    dvec<double> M((size_t)nd * nd);  // rows zeroed and filled in parallel
+#pragma omp parallel for schedule(static)
+    for (int i = 0; i < nd; ++i) {
+      double* row = M.data() + (size_t)i * nd;
+      std::fill(row, row + nd, 0.0);
+      for (int64_t p = S.ptr[i]; p < S.ptr[i + 1]; ++p) row[S.col[p]] = S.val[p];
+    }
     const auto t_dense = Clock::now();
     if (dense_on_host) {
       if (!dense_inverse(nd, M, dense_inv))

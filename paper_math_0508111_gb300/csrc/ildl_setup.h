@@ -64,7 +64,7 @@ struct HostFactor {
   std::vector<double> dinv_d;     // per position: diagonal of D^{-1} block
   std::vector<double> dinv_o;     // per position: off-diagonal of D^{-1} block
   std::vector<int> partner;       // per position: 2x2 partner position or -1
-  std::vector<double> dense_inv;  // n_dense^2, row-major, symmetric
+  dvec<double> dense_inv;         // n_dense^2, row-major, symmetric
   bool dense_is_matrix = false;   // dense_inv still holds the block itself
   // statistics
   int n_2x2 = 0;
