@@ -56,11 +56,11 @@ struct HostFactor {
   std::vector<double> scale;      // S
   std::vector<int> level_ptr;     // nlev + 2 entries: sparse levels, then the dense block
   std::vector<int64_t> Lptr;      // strictly lower part of L, CSR by rows
-  std::vector<int> Lcol;
-  std::vector<double> Lval;
+  dvec<int> Lcol;
+  dvec<double> Lval;
   std::vector<int64_t> Uptr;      // L^T, CSR by rows (= L by columns)
-  std::vector<int> Ucol;
-  std::vector<double> Uval;
+  dvec<int> Ucol;
+  dvec<double> Uval;
   std::vector<double> dinv_d;     // per position: diagonal of D^{-1} block
   std::vector<double> dinv_o;     // per position: off-diagonal of D^{-1} block
   std::vector<int> partner;       // per position: 2x2 partner position or -1
