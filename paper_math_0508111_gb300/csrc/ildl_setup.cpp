@@ -602,10 +602,11 @@ void stable_place(int G, int nr, Produce produce, std::vector<int64_t>& ptr, dve
                   ValOut& val) {
   constexpr int kShift = 8;
   const int nblk = (nr >> kShift) + 1;
-  std::vector<unsigned> cnt((size_t)G * nr, 0u);
+  dvec<unsigned> cnt((size_t)G * nr);  // each group zeroes its own counts
 #pragma omp parallel for schedule(static)
   for (int g = 0; g < G; ++g) {
     unsigned* c = cnt.data() + (size_t)g * nr;
+    std::fill(c, c + nr, 0u);
     produce(g, [&](const Trip& t) { ++c[t.r]; });
   }
   std::vector<int64_t> boff((size_t)G * nblk), bptr(nblk + 1, 0);
@@ -749,7 +750,7 @@ int build_ildl(const SymCsr& A, const ildl_params& prm, HostFactor& F, bool dens
   dvec<int> rec_row, rec_blk, crow;                  // Schur records
   dvec<double> rec_a, rec_b, c1, c2;
   dvec<int64_t> rec_slot;
-  std::vector<unsigned> mirror_cnt;
+  dvec<unsigned> mirror_cnt;
   dvec<Trip> mirror_tmp;                             // lower entries bucketed by column block
   struct RowWork {                                   // per thread; accv and mark all zero at rest
     std::vector<double> accv;
@@ -1279,11 +1280,12 @@ int build_ildl(const SymCsr& A, const ildl_params& prm, HostFactor& F, bool dens
       constexpr int kBlkShift = 8;  // 256 columns per block
       const int nblk = (mc_n >> kBlkShift) + 1;
       auto chunk_row0 = [&](int ch) { return (int)((int64_t)mc_n * ch / nchunk); };
-      std::vector<unsigned>& cnt = mirror_cnt;  // per group: lower entries per column
-      cnt.assign((size_t)G * mc_n, 0u);
+      dvec<unsigned>& cnt = mirror_cnt;  // per group: lower entries per column
+      resize_discard(cnt, (size_t)G * mc_n);
 #pragma omp parallel for schedule(static)
       for (int g = 0; g < G; ++g) {
         unsigned* c = cnt.data() + (size_t)g * mc_n;
+        std::fill(c, c + mc_n, 0u);
         for (int ch = nchunk * g / G; ch < nchunk * (g + 1) / G; ++ch) {
           const int* col = ucol[ch].data();
           int64_t q = 0;
