@@ -248,7 +248,9 @@ extern "C" int jd_server_create(const jd_server_params* p, jd_server_t* out) {
   S->prm = prm;
   S->device = dev;
   const int hw = std::max(1, omp_get_max_threads());
-  const int omp_each = std::max(1, (hw - prm.slots) / prm.setup_threads);
+  // the solving threads wait on the device in blocking synchronisation and
+  // need almost no CPU: the host cores go to the setups
+  const int omp_each = std::max(1, hw / prm.setup_threads);
   try {
     for (int t = 0; t < prm.setup_threads; ++t) S->workers.emplace_back(build_loop, S, omp_each);
     for (int t = 0; t < prm.slots; ++t) S->workers.emplace_back(solve_loop, S);
