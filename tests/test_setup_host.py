@@ -450,3 +450,13 @@ def test_cycle_split_rules(ajd, seed):
             else:
                 assert pt[grp[0]] == grp[1] and pt[grp[1]] == grp[0]
     assert long_cycles >= 1
+
+
+def test_dense_only_factor(ajd):
+    """Degenerate case: a matrix no larger than the dense block gets no sparse
+    level, an empty L, and K = A - sigma I exactly (the dense inverse)."""
+    A, _ = _csr(5, 16.5, 2, PERIODIC, 0.3)
+    F = ajd.Preconditioner.from_csr(A.indptr, A.indices, A.data, n_dense=200).export()
+    assert F["levels"] == 0 and F["nnz_L"] == 0 and F["n_dense"] == A.shape[0]
+    b = np.random.default_rng(0).standard_normal(A.shape[0])
+    assert np.abs(matching.apply_factor(F, A @ b) - b).max() <= 1e-12 * np.abs(b).max()
