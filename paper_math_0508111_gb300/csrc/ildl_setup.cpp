@@ -167,10 +167,15 @@ int max_product_matching(const SymCsr& A, std::vector<int>& match_col, std::vect
   const int n = A.n;
   rowmax.assign(n, 0.0);
   std::vector<double> logmax(n);
+  const bool known = mw.rowmax_in.size() == (size_t)n;
 #pragma omp parallel for schedule(static)
   for (int i = 0; i < n; ++i) {
     double r = 0.0;
-    for (int64_t p = A.ptr[i]; p < A.ptr[i + 1]; ++p) r = std::max(r, std::fabs(A.val[p]));
+    if (known) {
+      r = mw.rowmax_in[i];
+    } else {
+      for (int64_t p = A.ptr[i]; p < A.ptr[i + 1]; ++p) r = std::max(r, std::fabs(A.val[p]));
+    }
     if (r == 0.0) r = 1.0;
     rowmax[i] = r;
     logmax[i] = log_pos(r);
@@ -1270,6 +1275,8 @@ int build_ildl(const SymCsr& A, const ildl_params& prm, HostFactor& F, bool dens
     // order.  Both keep increasing r per column whatever the group count.
     SymCsr& Sn = Snext;
     Sn.n = mc_n;
+    std::vector<double>& next_rowmax = mwork.rowmax_in;  // filled by the mirror below
+    next_rowmax.resize(mc_n);
     {
       const int64_t nup = [&] {
         int64_t s = 0;
@@ -1328,12 +1335,15 @@ int build_ildl(const SymCsr& A, const ildl_params& prm, HostFactor& F, bool dens
           int64_t q = 0;
           for (int r = chunk_row0(ch); r < chunk_row0(ch + 1); ++r) {
             int64_t o = Sn.ptr[r] + lowcnt[r];
+            double mx = 0.0;  // max |entry| of the row's upper part
             for (const int64_t e = q + rowcnt[r]; q < e; ++q, ++o) {
               const int cc = col[q];
               Sn.col[o] = cc;
               Sn.val[o] = val[q];
+              mx = std::max(mx, std::fabs(val[q]));
               if (cc != r) mirror_tmp[bo[cc >> kBlkShift]++] = {r, cc, val[q]};
             }
+            next_rowmax[r] = mx;
           }
         }
       }
@@ -1341,13 +1351,21 @@ int build_ildl(const SymCsr& A, const ildl_params& prm, HostFactor& F, bool dens
       for (int b = 0; b < nblk; ++b) {
         const int c0 = b << kBlkShift, c1 = std::min(mc_n, c0 + (1 << kBlkShift));
         int64_t next[1 << kBlkShift];  // write position of each column of the block
-        for (int c = c0; c < c1; ++c) next[c - c0] = Sn.ptr[c];
+        double mx[1 << kBlkShift];     // max |entry| of the column's lower part
+        for (int c = c0; c < c1; ++c) {
+          next[c - c0] = Sn.ptr[c];
+          mx[c - c0] = 0.0;
+        }
         for (int64_t t = bptr[b]; t < bptr[b + 1]; ++t) {
           const Trip& e = mirror_tmp[t];
           const int64_t slot = next[e.c - c0]++;
           Sn.col[slot] = e.r;
           Sn.val[slot] = e.v;
+          mx[e.c - c0] = std::max(mx[e.c - c0], std::fabs(e.v));
         }
+        // row maxima of S' for the next level's matching (max is exact, so
+        // the same as a pass over the finished rows)
+        for (int c = c0; c < c1; ++c) next_rowmax[c] = std::max(next_rowmax[c], mx[c - c0]);
       }
     }
     // next level's numbering
@@ -1374,6 +1392,7 @@ int build_ildl(const SymCsr& A, const ildl_params& prm, HostFactor& F, bool dens
     auto release = [](auto& v) { std::remove_reference_t<decltype(v)>().swap(v); };
     release(mwork.loga);
     release(mwork.threads);
+    release(mwork.rowmax_in);
     release(Snext.ptr);
     release(Snext.col);
     release(Snext.val);

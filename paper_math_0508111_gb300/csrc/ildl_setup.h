@@ -100,6 +100,9 @@ struct MatchWork {
     std::vector<std::pair<double, int>> heap;
   };
   std::vector<Search> threads;
+  // optional: max |a_ij| of every row of the next matrix, when the caller
+  // has it already (one pass over the matrix fewer); used if it has n entries
+  std::vector<double> rowmax_in;
 };
 int max_product_matching(const SymCsr& A, std::vector<int>& match_col, std::vector<double>& u,
                          std::vector<double>& v, std::vector<double>& rowmax, MatchWork* work = nullptr);
