@@ -460,3 +460,30 @@ def test_dense_only_factor(ajd):
     assert F["levels"] == 0 and F["nnz_L"] == 0 and F["n_dense"] == A.shape[0]
     b = np.random.default_rng(0).standard_normal(A.shape[0])
     assert np.abs(matching.apply_factor(F, A @ b) - b).max() <= 1e-12 * np.abs(b).max()
+
+
+def test_concurrent_setups_match_sequential(ajd):
+    """The host setup holds no shared state: two setups running at once on
+    two host threads (as in the batch and the server) give the same factors,
+    bit for bit, as one after the other."""
+    import threading
+    mats = [_csr(16, 16.5, s, PERIODIC, 0.1)[0] for s in (7, 8)]
+
+    def build(A):
+        return ajd.Preconditioner.from_csr(A.indptr, A.indices, A.data, n_dense=200).export()
+
+    seq = [build(A) for A in mats]
+    out = [None, None]
+
+    def run(i):
+        out[i] = build(mats[i])
+
+    ts = [threading.Thread(target=run, args=(i,)) for i in range(2)]
+    for t in ts:
+        t.start()
+    for t in ts:
+        t.join()
+    for a, b in zip(seq, out):
+        for key in a:
+            if not key.endswith("_ms"):
+                assert np.array_equal(np.asarray(a[key]), np.asarray(b[key])), key
