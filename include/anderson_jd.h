@@ -169,7 +169,8 @@ typedef struct {
                      ignored when each level's independent set of pivots is
                      chosen, and dropped between pivots of the same level;
                      0 = exact independence; < 0 selects
-                     min(0.02, 5/sqrt(n)) [-1]                               */
+                     min(0.02, 5/sqrt(n)), and min(0.02, 1/sqrt(n)) for the
+                     lattices of anderson_create_offdiag [-1]                */
   int max_levels; /* maximum number of sparse levels [256]                    */
   int n_dense;    /* the remaining Schur complement is factored densely once
                      it has at most this many rows (at most 8000); 0 = n/16
