@@ -60,16 +60,22 @@ def parse():
                          "one realisation after another")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp32", "fp64"],
                     help="inner-solve precision of the headline form")
-    ap.add_argument("--no-fp64", action="store_true", help="skip the plain binary64 comparison")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the binary64 comparison arms")
+    ap.add_argument("--fp64-steps", type=int, default=8,
+                    help="realisations of the binary64 comparison arms (the first of the timed ones)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--workload", default="headline", choices=["headline", "batch"],
                     help="headline: the L = 100 realisations; batch: the 256-problem batch through jd_server")
     ap.add_argument("--batch-problems", type=int, default=256)
-    ap.add_argument("--serve-requests", type=int, default=32,
-                    help="requests of the serving sample (0 skips it)")
-    ap.add_argument("--serve-rate", type=float, default=1.5, help="Poisson arrival rate of the serving sample, 1/s")
-    ap.add_argument("--serve-lmax", type=int, default=48, help="largest lattice of the serving sample")
+    ap.add_argument("--batch-sample", type=int, default=32,
+                    help="problems of the bounded batch sample reported beside the headline (0 skips it)")
+    ap.add_argument("--serve-requests", type=int, default=16,
+                    help="requests per arrival rate of the serving sweep (0 skips it)")
+    ap.add_argument("--serve-rates", type=float, nargs="+", default=[0.5, 1.0, 2.0],
+                    help="arrival rates of the serving sweep, as multiples of the measured capacity")
+    ap.add_argument("--serve-lmax", type=int, default=120, help="largest lattice of the serving stream")
+    ap.add_argument("--cpu-L", type=int, default=30, help="lattice of the CPU oracle baseline sample")
     ap.add_argument("--serve-slots", type=int, default=4)
     ap.add_argument("--serve-setup-threads", type=int, default=3)
     ap.add_argument("--setup-threads", type=int, default=2,
@@ -217,24 +223,77 @@ def run_requests(ajd, args, precision, reqs, slots, setup_threads):
             time.sleep(0.002)
         elapsed = time.perf_counter() - start
         info = srv.info()
-    lat = np.sort(np.array(lat))
-    return {"value": pairs / elapsed, "unit": UNIT, "requests": len(reqs), "failed": failed, "eigenpairs": pairs,
+    return summarize_requests(lat, pairs, failed, elapsed, info["peak_solving"], slots, setup_threads)
+
+
+def summarize_requests(lat, pairs, failed, elapsed, peak, slots, setup_threads):
+    """Throughput and latency percentiles of one request run; with several
+    ranks (each serving its balanced share of the requests) the eigenpairs
+    are summed, the time is the slowest rank's and the percentiles are over
+    every rank's latencies."""
+    import numpy as np
+    from paper_math_0508111_gb300 import replicas
+    parts = replicas.gather_to_root(list(lat))
+    allat = [x for part in parts for x in part] if parts is not None else list(lat)
+    pairs = int(replicas.sum_over_ranks(pairs))
+    failed = int(replicas.sum_over_ranks(failed))
+    elapsed = replicas.max_over_ranks(elapsed)
+    lat = np.sort(np.array(allat)) if allat else np.zeros(1)
+    return {"value": pairs / elapsed, "unit": UNIT, "requests": len(allat), "failed": failed, "eigenpairs": pairs,
             "p50_latency_ms": float(np.percentile(lat, 50)), "p99_latency_ms": float(np.percentile(lat, 99)),
-            "max_latency_ms": float(lat[-1]), "seconds": elapsed, "peak_concurrent_solves": info["peak_solving"],
+            "max_latency_ms": float(lat[-1]), "seconds": elapsed, "peak_concurrent_solves": peak,
             "slots": slots, "setup_threads": setup_threads}
 
 
-def serving_sample(ajd, args, precision):
-    """The serving workload (workloads.serve_recipe: Poisson arrivals, L
-    uniform in 16..serve_lmax, W in [8, 24], sigma in [-2, 2], k in
-    {1, 5, 10}, request r on disorder seed 10^6 + r, driver seed 7), bounded
-    to serve_requests requests."""
+def rank_share(ajd, reqs, rank, world):
+    """This rank's balanced share of independent requests (greedy by work,
+    under the HBM estimate of each solve); all of them on one GPU."""
+    if world == 1:
+        return reqs
+    from paper_math_0508111_gb300 import replicas
+    work = [replicas.problem_work(r["L"], r["k"]) for r in reqs]
+    mem = [ajd.Server.estimate(r["L"], r["k"]) for r in reqs]
+    return [reqs[i] for i in replicas.balanced_shard(work, mem, world)[rank]]
+
+
+def serving_sweep(ajd, args, precision, rank=0, world=1):
+    """The serving workload (workloads.serve_recipe: L uniform in
+    16..serve_lmax, W in [8, 24], sigma in [-2, 2], k in {1, 5, 10}, request
+    r on disorder seed 10^6 + r): first the capacity, the completion rate
+    of serve_requests requests all submitted at t = 0, then Poisson streams
+    of serve_requests requests at each rate of serve_rates times that
+    capacity, with p50/p99 latency (submission to completion) per rate."""
     import workloads
-    reqs = workloads.serve_recipe(args.serve_requests, args.serve_rate, seed=7, lmax=args.serve_lmax)
-    out = run_requests(ajd, args, precision, reqs, args.serve_slots, args.serve_setup_threads)
-    out["sample"] = ("%d Poisson arrivals at %.2f/s, L~U{16..%d}, W~U[8,24], sigma~U[-2,2], k in {1,5,10}, seeds "
-                     "1e6+r, tol %g (a bounded sample of the 4096-request L<=120 stream)"
-                     % (len(reqs), args.serve_rate, args.serve_lmax, args.tol))
+    base = workloads.serve_recipe(args.serve_requests, 1.0, seed=7, lmax=args.serve_lmax)
+    sat = run_requests(ajd, args, precision, rank_share(ajd, [dict(r, t=0.0) for r in base], rank, world),
+                       args.serve_slots, args.serve_setup_threads)
+    capacity = sat["requests"] / sat["seconds"]
+    out = {"capacity_requests_per_s": capacity, "saturated": sat, "rates": []}
+    for i, mult in enumerate(args.serve_rates):
+        # the same requests at every rate (same draws, arrival times scaled)
+        reqs = workloads.serve_recipe(args.serve_requests, mult * capacity, seed=7, lmax=args.serve_lmax)
+        res = run_requests(ajd, args, precision, rank_share(ajd, reqs, rank, world), args.serve_slots,
+                           args.serve_setup_threads)
+        res["rate_multiple"] = mult
+        res["rate_per_s"] = mult * capacity
+        out["rates"].append(res)
+    out["sample"] = ("%d requests per point, L~U{16..%d}, W~U[8,24], sigma~U[-2,2], k in {1,5,10}, tol %g; "
+                     "capacity from all requests submitted at t=0, then Poisson arrivals at %s x capacity "
+                     "(a bounded sample of the 4096-request stream)"
+                     % (args.serve_requests, args.serve_lmax, args.tol, "/".join("%g" % m for m in args.serve_rates)))
+    return out
+
+
+def batch_sample(ajd, args, precision, rank=0, world=1):
+    """A bounded sample of the batch workload (workloads.batch_recipe: L in
+    {20,30,40,50}, W in {12,16.5,20}, sigma in {-1,0,1}, k = 5, seeds
+    1000 + p), all problems submitted at t = 0 to one jd_server."""
+    import workloads
+    reqs = [dict(r, t=0.0) for r in workloads.batch_recipe(args.batch_sample, seed=42)]
+    out = run_requests(ajd, args, precision, rank_share(ajd, reqs, rank, world), args.serve_slots,
+                       args.serve_setup_threads)
+    out["sample"] = ("first %d problems of the 256-problem batch (L in {20,30,40,50}, W in {12,16.5,20}, "
+                     "sigma in {-1,0,1}, k=5), submitted at t=0" % len(reqs))
     return out
 
 
@@ -263,17 +322,30 @@ def run_batch_workload(args):
     print(json.dumps(line), flush=True)
 
 
-def cpu_baseline(W, sigma, k, L_sample=30):
-    """The oracle (shift-and-invert Lanczos over SuperLU) on a bounded sample:
-    one L_sample^3 lattice of the same disorder, shift and k."""
-    import numpy as np
+def cpu_baseline(W, sigma, k, tol, L_sample=30, threads=None):
+    """The oracle (shift-and-invert Lanczos over SuperLU) on a bounded
+    sample: one L_sample^3 lattice of the same disorder, shift and k, solved
+    to the metric's residual tol * ||A||.  With ``threads`` the oracle runs
+    in a child process whose BLAS/OpenMP pools have that many threads."""
+    if threads is not None:
+        env = dict(os.environ, OMP_NUM_THREADS=str(threads), OPENBLAS_NUM_THREADS=str(threads),
+                   MKL_NUM_THREADS=str(threads))
+        code = ("import json, sys; sys.path.insert(0, %r); import bench; "
+                "print(json.dumps(bench.cpu_baseline(%r, %r, %r, %r, %r)))" % (ROOT, W, sigma, k, tol, L_sample))
+        r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True)
+        if r.returncode != 0:
+            return {"error": r.stderr[-500:]}
+        out = json.loads(r.stdout.strip().splitlines()[-1])
+        out["threads"] = threads
+        return out
+    import numpy as np  # noqa: F401
     from oracle import lanczos, lattice, rng
     import resource
     eps = rng.potential(L_sample, W, 1)
     A = lattice.assemble(L_sample, eps)
     r0 = resource.getrusage(resource.RUSAGE_SELF)
     t0 = time.perf_counter()
-    w, X, info = lanczos.shift_invert_nearest(A, sigma, k, norm_a=lattice.norm_bound(eps))
+    w, X, info = lanczos.shift_invert_nearest(A, sigma, k, tol=tol, norm_a=lattice.norm_bound(eps))
     dt = time.perf_counter() - t0
     r1 = resource.getrusage(resource.RUSAGE_SELF)
     # threads actually used: CPU time over wall time of the run (SuperLU's
@@ -281,9 +353,9 @@ def cpu_baseline(W, sigma, k, L_sample=30):
     busy = (r1.ru_utime - r0.ru_utime) + (r1.ru_stime - r0.ru_stime)
     cores = round(busy / dt, 2) if dt > 0 else 1.0
     return {"value": k / dt, "unit": UNIT, "cores": cores, "cores_available": os.cpu_count(), "kind": "oracle",
-            "sample": "oracle shift-invert Lanczos + SuperLU on one L=%d lattice (W=%g, sigma=%g, k=%d): %.1f s; "
-                      "the oracle's sparse LU does not reach L=100 in bounded time (L=50 takes ~6 min), so the "
-                      "sample is the largest lattice it solves in 10-30 s" % (L_sample, W, sigma, k, dt),
+            "sample": "oracle shift-invert Lanczos + SuperLU on one L=%d lattice (W=%g, sigma=%g, k=%d, residual "
+                      "<= %g ||A||): %.1f s, %d Lanczos steps; a bounded sample of the L=100 workload, whose LU the "
+                      "oracle does not reach in bounded time" % (L_sample, W, sigma, k, tol, dt, info["steps"]),
             "seconds": dt}
 
 
@@ -297,15 +369,15 @@ def run_reference(args, rank, world):
     vals = []
     t0 = time.perf_counter()
     for s in range(args.steps):
-        cb = cpu_baseline(args.W, args.sigma, args.k)
+        cb = cpu_baseline(args.W, args.sigma, args.k, args.tol, args.cpu_L)
         vals.append(cb["seconds"])
     total = time.perf_counter() - t0
     value = args.k * args.steps / sum(vals)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": "anderson-L30-W%g-periodic-k%d-sigma%g (oracle sample of the L=100 workload)"
-                       % (args.W, args.k, args.sigma)},
+            "config": {"workload": "anderson-L%d-W%g-periodic-k%d-sigma%g (oracle sample of the L=100 workload)"
+                       % (args.cpu_L, args.W, args.k, args.sigma)},
             "cpu_baseline": {"value": value, "unit": UNIT, "kind": "oracle", "cores": cb["cores"],
                              "cores_available": cb["cores_available"], "sample": cb["sample"]},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -419,28 +491,47 @@ def main():
     solve_s = sum(s["solve_ms"] for s in stats) / 1e3
     ev_batched = ev_dev.cpu().numpy()
 
-    # plain binary64 form: one jd_solve after another on the same realisations
+    # binary64 comparison arms on the first fp64_steps timed realisations:
+    # plain (one jd_solve after another) and pipelined (jd_solve_batch, the
+    # same pipeline as the headline), so that the precision gain is
+    # separated from the pipelining gain
     fp64 = None
     if not args.no_fp64:
+        m64 = max(1, min(args.fp64_steps, nsteps))
+        sub = lattices[nwarm:nwarm + m64]
         torch.cuda.synchronize()
         f0 = torch.cuda.Event(enable_timing=True)
         f1 = torch.cuda.Event(enable_timing=True)
         st64, ev64 = [], []
         f0.record(stream)
-        for i in range(nsteps):
+        for i in range(m64):
             flush.zero_()
-            st64.append(one(lattices[nwarm + i], ajd.JD_FP64))
+            st64.append(one(sub[i], ajd.JD_FP64))
             ev64.append(ev_out.copy())
         f1.record(stream)
         torch.cuda.synchronize()
         t64 = f0.elapsed_time(f1) / 1e3
         ev64 = np.array(ev64)
-        fp64 = {"value": world * nsteps * k / t64, "unit": UNIT, "ms_per_step": 1e3 * t64 / nsteps,
-                "setup_s_per_step": sum(s["setup_ms"] for s in st64) / 1e3 / nsteps,
-                "solve_only_value": world * nsteps * k / (sum(s["solve_ms"] for s in st64) / 1e3),
+        flush.zero_()
+        torch.cuda.synchronize()
+        f0.record(stream)
+        stp = batch([h.handle for h in sub], ajd.JD_FP64, ev_ptrs[:m64], x_ptrs[:m64])
+        f1.record(stream)
+        torch.cuda.synchronize()
+        tp = f0.elapsed_time(f1) / 1e3
+        fp64 = {"value": world * m64 * k / t64, "unit": UNIT, "realisations": m64, "ms_per_step": 1e3 * t64 / m64,
+                "setup_s_per_step": sum(s["setup_ms"] for s in st64) / 1e3 / m64,
+                "solve_only_value": world * m64 * k / (sum(s["solve_ms"] for s in st64) / 1e3),
                 "outer_its": [s["outer_its"] for s in st64], "inner_its": [s["inner_its"] for s in st64],
                 "headline_vs_fp64_max_abs_dlambda_over_normA":
-                    float(np.max(np.abs(ev_batched - ev64)) / max(lattices[nwarm + i].norm() for i in range(nsteps)))}
+                    float(np.max(np.abs(ev_batched[:m64] - ev64)) / max(h.norm() for h in sub)),
+                "pipelined": {"value": world * m64 * k / tp, "unit": UNIT, "ms_per_step": 1e3 * tp / m64,
+                              "setup_s_per_step": sum(s["setup_ms"] for s in stp) / 1e3 / m64,
+                              "solve_s_per_step": sum(s["solve_ms"] for s in stp) / 1e3 / m64,
+                              "inner_its": [s["inner_its"] for s in stp],
+                              "note": "binary64 inner solve through the same jd_solve_batch pipeline "
+                                      "(%d setup threads) as the headline" % args.setup_threads},
+                "note": "plain: one binary64 jd_solve after another (setup + solve per realisation)"}
 
     # end to end through the public API from host memory: potentials copied
     # in from pinned buffers, the same pipelined batch writing eigenvalues
@@ -480,17 +571,25 @@ def main():
                                                "forward level sweeps, dense tail, backward level sweeps)",
                 "peak_kind": peak_kind + " (hbm_gbs, copy test)", "algorithmic_bytes_per_launch": bytes_per,
                 "avg_launch_ms": ms / calls if calls else None, "launches_timed": calls}
+    # the inner solve's stencil runs in binary64 for the binary64 and mixed
+    # solves (24 B/site: x, eps, y) and in binary32 for the binary32 one
+    stencil_prec = "binary32" if args.precision == "fp32" else "binary64"
+    stencil_bps = 12 if args.precision == "fp32" else 24
     stencil_calls = sum(s["stencil_calls"] for s in stats)
     stencil_ms = sum(s["stencil_ms"] for s in stats)
 
-    serving = None
-    if args.serve_requests > 0:
-        serving = serving_sample(ajd, args, head)
+    # the batch sample and the serving stream split over the ranks by the
+    # greedy work/HBM balance (independent problems, host-side gathers only)
+    batch_c4 = batch_sample(ajd, args, head, rank, world) if args.batch_sample > 0 else None
+    serving = serving_sweep(ajd, args, head, rank, world) if args.serve_requests > 0 else None
 
     cpu = None
     if rank == 0 and not args.no_cpu:
-        cpu = cpu_baseline(W, sigma, k)
+        cpu = cpu_baseline(W, sigma, k, tol, args.cpu_L)
         cpu.pop("seconds", None)
+        one_thread = cpu_baseline(W, sigma, k, tol, args.cpu_L, threads=1)
+        one_thread.pop("seconds", None)
+        cpu["one_thread"] = one_thread
 
     if args.model == "diagonal":
         workload = "anderson-L%d-W%g-%s-k%d-sigma%g-tol%g" % (L, W, args.bc, k, sigma, tol)
@@ -531,9 +630,13 @@ def main():
                 "max_residual": max(s["max_residual"] for s in stats),
                 "preconditioner": {"levels": info["levels"], "n_dense": info["n_dense"], "nnz_L": info["nnz_L"],
                                    "fill": info["fill"], "n_2x2": info["n_2x2"]},
-                "fp64": fp64, "e2e": e2e, "roofline": roofline, "serving": serving,
-                "stencil_fp32": {"calls": stencil_calls, "avg_ms": stencil_ms / stencil_calls if stencil_calls else None,
-                                 "achieved_GBps": 12 * n / (stencil_ms / stencil_calls / 1e3) / 1e9 if stencil_calls else None},
+                "fp64": fp64, "e2e": e2e, "roofline": roofline, "batch": batch_c4, "serving": serving,
+                "stencil": {"precision": stencil_prec, "bytes_per_site": stencil_bps, "sites": n,
+                            "calls": stencil_calls, "avg_ms": stencil_ms / stencil_calls if stencil_calls else None,
+                            "achieved_GBps": stencil_bps * n / (stencil_ms / stencil_calls / 1e3) / 1e9
+                            if stencil_calls else None,
+                            "note": "the stencil calls of the headline solves (SQMR and outer steps), timed with "
+                                    "CUDA events around each call"},
                 "cpu_baseline": cpu, "clocks": clocks,
                 "gpu_launches": int(sum(s["kernel_launches"] for s in stats))}
         print(json.dumps(line), flush=True)

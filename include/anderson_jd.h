@@ -193,6 +193,12 @@ typedef struct {
 /* Fill *p with the defaults above. */
 int ildl_params_default(ildl_params* p);
 
+/* The threshold gamma that gamma < 0 selects for an order-n matrix:
+ * min(0.02, 5/sqrt(n)), or min(0.02, 1/sqrt(n)) when offdiag != 0 (the
+ * lattices of anderson_create_offdiag, Section 7).  Host only; JD_EINVAL if
+ * n < 1 or gamma is NULL. */
+int ildl_default_gamma(int64_t n, int offdiag, double* gamma);
+
 /* Sizes and statistics of a factor. */
 typedef struct {
   int n;             /* order                                               */
@@ -280,21 +286,26 @@ int ildl_apply(ildl_t f, const void* b, void* x, int precision, void* stream);
 
 /*
  * ildl_apply_noalloc -- x = K^{-1} b like ildl_apply, for callers that cannot
- * allocate device memory during the call (a fixed memory pool, an embedding
- * runtime that owns all device memory, a region that must stay free of
- * allocations).  The paper has no counterpart: this is a deployment variant.
+ * allocate device memory during the call (a fixed memory pool reserved up
+ * front, an embedding runtime that owns all device memory).  The paper has no
+ * counterpart: this is a deployment variant.
  * It runs the same kernel but takes its scratch (two work vectors and the
- * grid-barrier words) from one static device array compiled into the
+ * status word of its waits) from one static device array compiled into the
  * library (2 MiB + 512 bytes, held by every GPU that loads the library until
  * the process exits) instead of the factor's buffers; it calls no cudaMalloc,
  * cudaFree or allocating library routine.
  *   f          a factor from ildl_create with at most 131072 rows (n = L^3,
- *              L <= 50); larger orders are rejected with JD_EINVAL.
+ *              L <= 50); larger orders are rejected with JD_EINVAL.  The
+ *              factor's device must be the current device (JD_EINVAL
+ *              otherwise).
  *   b, x       device pointers as for ildl_apply; precision JD_FP64,
  *              JD_FP32 or JD_MIXED.
  * Every call shares the one array (its previous contents are kept; the call
  * clears the words that must start at zero), so calls that overlap on the
  * GPU -- on different streams or threads -- race and must not be issued.
+ * The launch is ordered behind the preconditioner applies of jd_server's
+ * concurrent solves; it must not overlap an ildl_apply or jd_solve issued
+ * on another stream of the same device.
  * The first call on each device looks up the array's device address
  * (cudaGetSymbolAddress) with that device current; make that first call
  * before any stream capture.  The call waits for the apply to finish and

@@ -90,13 +90,3 @@ def nearest_dense(A, sigma, k, solver="lapack"):
         w, V = np.linalg.eigh(np.asarray(A, dtype=np.float64))
     order = order_nearest(w, sigma)[:k]
     return w[order], normalize_sign(V[:, order])
-
-
-def cluster_gap(evals_all, sigma, k):
-    """Distance between the k-th and (k+1)-th eigenvalue in the nearest-sigma
-    order, measured as |lambda - sigma|: positive iff the k-nearest set is
-    unique."""
-    d = np.sort(np.abs(np.asarray(evals_all) - sigma))
-    if k >= len(d):
-        return np.inf
-    return d[k] - d[k - 1]

@@ -167,15 +167,3 @@ def apply_factor(F, b):
     out = np.empty(n)
     out[perm] = s * x
     return out
-
-
-def factor_matrix(F):
-    """The matrix K = P^T S^{-1} L D L^T S^{-1} P represented by a factor
-    (dense; small n only)."""
-    n = len(F["perm"])
-    K = np.empty((n, n))
-    for j in range(n):
-        e = np.zeros(n)
-        e[j] = 1.0
-        K[:, j] = apply_factor(F, e)
-    return np.linalg.inv(K)

@@ -80,6 +80,7 @@ SIGNATURES = [
     ("anderson_norm", c_int, [c_void_p, P(c_double)]),
     ("anderson_apply", c_int, [c_void_p, c_double, c_void_p, c_void_p, c_int, c_int, c_void_p]),
     ("ildl_params_default", c_int, [P(IldlParams)]),
+    ("ildl_default_gamma", c_int, [c_int64, c_int, P(c_double)]),
     ("ildl_setup_csr", c_int, [c_int, c_void_p, c_void_p, c_void_p, P(IldlParams), P(c_void_p)]),
     ("ildl_matching", c_int, [c_int, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     ("ildl_create", c_int, [c_void_p, c_double, P(IldlParams), P(c_void_p)]),

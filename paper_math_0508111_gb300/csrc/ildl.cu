@@ -219,21 +219,33 @@ int upload_factor(const HostFactor& F, DevFactor<T>& d, cudaStream_t st) {
     while (g < 512 && 2 * g <= want) g *= 2;
     return g;
   };
-  // the gather phase writes s[p] b[perm[p]] into w for every position; level
-  // 0 rows are then final and later rows read their right-hand side from w
-  ph.push_back(make_int4(PH_GATHER, 0, F.n, 1));
+  // level 0 (rows without entries): w = s b[perm]; later forward rows form
+  // their right-hand side s[p] b[perm[p]] themselves
+  // each phase's rows start at the CTA after the last one the previous
+  // phase used (round robin over the grid), so that the CTAs of a small
+  // phase are idle while the level before it is computed and have its
+  // loads in flight by then; the first CTA goes in the high half of .w
+  const int grid = sm_count();
+  int cursor = 0;
+  auto add_phase = [&](int kind, int p0, int p1, int g) {
+    const int64_t threads = (int64_t)(p1 - p0) * (kind == PH_DENSE ? 32 : g);
+    const int ctas = (int)std::min<int64_t>(grid, (threads + kPersistThreads - 1) / kPersistThreads);
+    ph.push_back(make_int4(kind, p0, p1, g | (cursor << 16)));
+    cursor = (cursor + ctas) % grid;
+  };
+  ph.push_back(make_int4(PH_GATHER, lvp[0], lvp[1], 1));
   for (int l = 1; l <= nl; ++l) {
     const int p0 = lvp[l], p1 = lvp[l + 1];
     if (p1 <= p0) continue;
     const double avg = (double)(F.Lptr[p1] - F.Lptr[p0]) / (p1 - p0);
-    ph.push_back(make_int4(PH_FWD, p0, p1, pick_g(p1 - p0, avg)));
+    add_phase(PH_FWD, p0, p1, pick_g(p1 - p0, avg));
   }
-  if (F.n_dense > 0) ph.push_back(make_int4(PH_DENSE, lvp[nl], lvp[nl + 1], 32));
+  if (F.n_dense > 0) add_phase(PH_DENSE, lvp[nl], lvp[nl + 1], 32);
   for (int l = nl - 1; l >= 0; --l) {
     const int p0 = lvp[l], p1 = lvp[l + 1];
     if (p1 <= p0) continue;
     const double avg = (double)(F.Uptr[p1] - F.Uptr[p0]) / (p1 - p0);
-    ph.push_back(make_int4(PH_BWD, p0, p1, pick_g(p1 - p0, avg)));
+    add_phase(PH_BWD, p0, p1, pick_g(p1 - p0, avg));
   }
   d.nphase = (int)ph.size();
   AJD_CUDA(cudaMalloc(&d.phases, std::max<size_t>(1, ph.size()) * sizeof(int4)));
@@ -241,8 +253,8 @@ int upload_factor(const HostFactor& F, DevFactor<T>& d, cudaStream_t st) {
     AJD_CUDA(cudaMemcpyAsync(d.phases, ph.data(), ph.size() * sizeof(int4), cudaMemcpyHostToDevice, st));
     AJD_CUDA(cudaStreamSynchronize(st));
   }
-  // barrier words on separate 128-byte lines: [0] arrivals, [32] generation,
-  // [64] timeout flag
+  // status words: [64] the timeout flag of the apply's waits (its own
+  // 128-byte line)
   AJD_CUDA(cudaMalloc(&d.bar, 96 * sizeof(unsigned)));
   AJD_CUDA(cudaMemsetAsync(d.bar, 0, 96 * sizeof(unsigned), st));
   AJD_CUDA(cudaStreamSynchronize(st));
@@ -270,18 +282,19 @@ int launch_apply(const ildl_s* f, const DevFactor<V>& d, X* w, X* z, const IO* b
   if (F.n == 0 || d.nphase == 0) return JD_OK;
   ApplyArgs<V, X, IO> a{d.perm, d.scale, d.Lptr, d.Lcol, d.Lval, d.Uptr, d.Ucol, d.Uval, d.dd, d.dof, d.partner,
                         d.dense, w, z, b, out, F.n_dense, F.level_ptr[F.nlev]};
-  AJD_CUDA(cudaMemsetAsync(d.bar, 0, 64 * sizeof(unsigned), s));  // arrivals and generation
+  // every solution entry starts as the sentinel (all ones) that the
+  // kernel's readers poll on
+  AJD_CUDA(cudaMemsetAsync(w, 0xFF, (size_t)F.n * sizeof(X), s));
+  AJD_CUDA(cudaMemsetAsync(z, 0xFF, (size_t)F.n * sizeof(X), s));
   const int4* ph = d.phases;
   int np = d.nphase;
-  unsigned* cnt = d.bar;
-  unsigned* gen = d.bar + 32;
   int* err = reinterpret_cast<int*>(d.bar + 64);
   // AJD_APPLY_TIMING=1: record the start of every phase (globaltimer, CTA 0)
   // and print a per-kind summary of the next apply to stderr (diagnostics)
   static const bool timing = std::getenv("AJD_APPLY_TIMING") != nullptr;
   unsigned long long* stamps = nullptr;
   if (timing) AJD_CUDA(cudaMalloc(&stamps, (np + 1) * sizeof(unsigned long long)));
-  void* args[] = {&a, &ph, &np, &cnt, &gen, &err, &stamps};
+  void* args[] = {&a, &ph, &np, &err, &stamps};
   if (tl_serialize_applies) {
     // concurrent solvers: this apply starts on the device only after the
     // previous serialised apply (of any thread) has finished, so no two of
@@ -299,7 +312,7 @@ int launch_apply(const ildl_s* f, const DevFactor<V>& d, X* w, X* z, const IO* b
     AJD_CUDA(cudaLaunchCooperativeKernel((void*)ildl_apply_persistent_kernel<V, X, IO>, dim3(d.grid),
                                          dim3(kPersistThreads), args, 0, s));
   }
-  count_launches(2);
+  count_launches(3);
   if (timing) {
     std::vector<unsigned long long> t(np + 1);
     std::vector<int4> phs(np);
@@ -314,7 +327,8 @@ int launch_apply(const ildl_s* f, const DevFactor<V>& d, X* w, X* z, const IO* b
       kind_us[phs[i].x] += us;
       kind_n[phs[i].x]++;
       if (std::getenv("AJD_APPLY_TIMING_ALL"))
-        std::fprintf(stderr, "phase %d kind %d rows %d G %d: %.2f us\n", i, phs[i].x, phs[i].z - phs[i].y, phs[i].w, us);
+        std::fprintf(stderr, "phase %d kind %d rows %d G %d cta %d: %.2f us\n", i, phs[i].x, phs[i].z - phs[i].y,
+                     phs[i].w & 0xFFFF, phs[i].w >> 16, us);
     }
     std::fprintf(stderr, "apply %.1f us: gather %.1f (%d) fwd %.1f (%d) dense %.1f (%d) bwd %.1f (%d)\n",
                  (t[np] - t[0]) * 1e-3, kind_us[0], kind_n[0], kind_us[1], kind_n[1], kind_us[2], kind_n[2], kind_us[3],
@@ -337,14 +351,15 @@ int ildl_apply_dev_mixed(const ildl_s* f, const double* b, double* out, cudaStre
 }
 
 // Timeout flag of the persistent apply (sticky until cleared): JD_EDEVICE if
-// a grid barrier gave up.
-int ildl_check_device_error(const ildl_s* f) {
+// a wait of the apply gave up.
+int ildl_check_device_error(const ildl_s* f, cudaStream_t s) {
   for (int prec = 0; prec < 2; ++prec) {
     const unsigned* bar = prec == 0 ? f->d64.bar : f->d32.bar;
     if (!bar) continue;
     int e = 0;
-    AJD_CUDA(cudaMemcpy(&e, bar + 64, sizeof(int), cudaMemcpyDeviceToHost));
-    if (e) return fail(JD_EDEVICE, "ildl_apply: a device-side barrier timed out");
+    AJD_CUDA(cudaMemcpyAsync(&e, bar + 64, sizeof(int), cudaMemcpyDeviceToHost, s));
+    AJD_CUDA(cudaStreamSynchronize(s));
+    if (e) return fail(JD_EDEVICE, "ildl_apply: a device-side wait timed out");
   }
   return JD_OK;
 }
@@ -477,6 +492,12 @@ extern "C" int ildl_params_default(ildl_params* p) {
   return JD_OK;
 }
 
+extern "C" int ildl_default_gamma(int64_t n, int offdiag, double* gamma) {
+  if (n < 1 || !gamma) return fail(JD_EINVAL, "ildl_default_gamma: n >= 1 and a non-NULL gamma required");
+  *gamma = default_gamma(n, offdiag != 0);
+  return JD_OK;
+}
+
 static int check_params(const ildl_params* p, ildl_params& out) {
   if (p) out = *p;
   else ildl_params_default(&out);
@@ -582,10 +603,11 @@ int ildl_create_on_stream(anderson_t h, double sigma, const ildl_params* p, ildl
   ildl_params prm;
   AJD_TRY(check_params(p, prm));
   // off-diagonal disorder (Section 7): the factor loses more by ignoring
-  // weak couplings, so the default threshold is five times smaller
-  // (measured with SQMR on A x = b: at L = 33, 78-80 iterations with 0.02,
-  // 29-43 with 1/sqrt(n); at L = 50, 120-154 with 5/sqrt(n), 36-37 with 0.002)
-  if (prm.gamma < 0.0 && h->bond64) prm.gamma = std::min(0.02, 1.0 / std::sqrt((double)h->n));
+  // weak couplings, so the default threshold is min(0.02, 1/sqrt(n)) instead
+  // of min(0.02, 5/sqrt(n)) -- five times smaller from L = 40 on, 0.0053
+  // against 0.02 at L = 33 (measured with SQMR on A x = b: at L = 33, 78-80
+  // iterations with 0.02, 29-43 with 1/sqrt(n))
+  if (prm.gamma < 0.0) prm.gamma = default_gamma(h->n, h->bond64 != nullptr);
   try {
     std::vector<double> eps(h->n), bonds(h->bond64 ? 3 * h->n : 0);
     AJD_CUDA(cudaMemcpyAsync(eps.data(), h->eps64, h->n * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -683,18 +705,19 @@ extern "C" int ildl_destroy(ildl_t f) {
 // Allocation-free preconditioner application.
 //
 // Some callers cannot allocate device memory while they run: code executing
-// under an allocator that forbids it (a memory pool reserved up front, a
-// captured region that must stay allocation-free, an embedding runtime that
-// owns all device memory).  ildl_apply_noalloc serves them: it launches the
-// same persistent kernel as ildl_apply but takes its scratch (the two work
-// vectors and the grid-barrier words) from one file-scope device array
-// instead of the factor's own buffers.  Nothing is allocated or freed.
+// under an allocator that forbids it (a memory pool reserved up front, an
+// embedding runtime that owns all device memory).  ildl_apply_noalloc serves
+// them: it launches the same persistent kernel as ildl_apply but takes its
+// scratch (the two work vectors and the status words) from one
+// file-scope device array instead of the factor's own buffers.  Nothing is
+// allocated or freed.  The call is synchronous: it waits for the apply and
+// reads its timeout flag before returning.
 // ---------------------------------------------------------------------------
 namespace {
 
 constexpr int64_t kNoAllocMaxN = 131072;  // largest order served (L <= 50 lattices)
 constexpr size_t kNoAllocVecBytes = (size_t)kNoAllocMaxN * sizeof(double);
-constexpr size_t kNoAllocBytes = 2 * kNoAllocVecBytes + 512;  // w, z, barrier words
+constexpr size_t kNoAllocBytes = 2 * kNoAllocVecBytes + 512;  // w, z, status words
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
@@ -735,24 +758,34 @@ int launch_apply_static(const ildl_s* f, const DevFactor<V>& d, const IO* b, IO*
   unsigned* bar = reinterpret_cast<unsigned*>(scratch + 2 * kNoAllocVecBytes);
   ApplyArgs<V, X, IO> a{d.perm, d.scale, d.Lptr, d.Lcol, d.Lval, d.Uptr, d.Ucol, d.Uval, d.dd, d.dof, d.partner,
                         d.dense, w, z, b, out, F.n_dense, F.level_ptr[F.nlev]};
-  // the array keeps the previous call's contents: the barrier words (arrivals,
-  // generation, timeout flag) must start at zero; w and z are written before
-  // they are read
+  // the array keeps the previous call's contents: the timeout flag must start
+  // at zero, and every entry of w and z as the sentinel the kernel polls on
   AJD_CUDA(cudaMemsetAsync(bar, 0, 96 * sizeof(unsigned), s));
+  AJD_CUDA(cudaMemsetAsync(w, 0xFF, (size_t)F.n * sizeof(X), s));
+  AJD_CUDA(cudaMemsetAsync(z, 0xFF, (size_t)F.n * sizeof(X), s));
   const int4* ph = d.phases;
   int np = d.nphase;
-  unsigned* cnt = bar;
-  unsigned* gen = bar + 32;
   int* err = reinterpret_cast<int*>(bar + 64);
   unsigned long long* stamps = nullptr;
-  void* args[] = {&a, &ph, &np, &cnt, &gen, &err, &stamps};
-  AJD_CUDA(cudaLaunchCooperativeKernel((void*)ildl_apply_persistent_kernel<V, X, IO>, dim3(d.grid),
-                                       dim3(kPersistThreads), args, 0, s));
-  count_launches(2);
+  void* args[] = {&a, &ph, &np, &err, &stamps};
+  {
+    // ordered behind the applies of concurrent served solves (the same
+    // event chain), so this grid-wide kernel never runs beside one of them
+    std::lock_guard<std::mutex> lk(g_chain_mu);
+    if (g_chain_last) AJD_CUDA(cudaStreamWaitEvent(s, g_chain_last, 0));
+    AJD_CUDA(cudaLaunchCooperativeKernel((void*)ildl_apply_persistent_kernel<V, X, IO>, dim3(d.grid),
+                                         dim3(kPersistThreads), args, 0, s));
+    cudaEvent_t ev = nullptr;
+    AJD_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    AJD_CUDA(cudaEventRecord(ev, s));
+    if (g_chain_last) cudaEventDestroy(g_chain_last);
+    g_chain_last = ev;
+  }
+  count_launches(4);
   int herr = 0;
   AJD_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
   AJD_CUDA(cudaStreamSynchronize(s));
-  if (herr) return fail(JD_EDEVICE, "ildl_apply_noalloc: a device-side barrier timed out");
+  if (herr) return fail(JD_EDEVICE, "ildl_apply_noalloc: a device-side wait timed out");
   return JD_OK;
 }
 
@@ -764,6 +797,12 @@ extern "C" int ildl_apply_noalloc(ildl_t f, const void* b, void* x, int precisio
   if ((int64_t)f->F.n > kNoAllocMaxN)
     return fail(JD_EINVAL, "ildl_apply_noalloc: order %d exceeds the static scratch limit of %lld rows", f->F.n,
                 (long long)kNoAllocMaxN);
+  // the scratch array looked up below is the current device's; the
+  // factor's arrays live on f->device
+  int cur = 0;
+  AJD_CUDA(cudaGetDevice(&cur));
+  if (cur != f->device)
+    return fail(JD_EINVAL, "ildl_apply_noalloc: current device %d is not the factor's device %d", cur, f->device);
   unsigned char* scratch = nullptr;
   AJD_TRY(noalloc_scratch(&scratch));
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);

@@ -1,22 +1,36 @@
-// The persistent preconditioner apply kernel (device code only): all phases
-// of x = K^{-1} b in one cooperative launch.  Included by ildl.cu; kept in
-// its own file so that measurements of this kernel can be tied to its
-// source (bench.py keys recorded DRAM counters to this file's hash).
+// The persistent preconditioner apply kernel (device code only): all of
+// x = K^{-1} b in one cooperative launch.  Included by ildl.cu; kept in its
+// own file so that measurements of this kernel can be tied to its source
+// (bench.py keys recorded DRAM counters to this file's hash).
+//
+// Synchronisation-free level scheduling.  The positions are ordered level by
+// level; a row of the forward sweep reads only solution entries of earlier
+// levels, a row of the backward sweep only entries of later levels.  Instead
+// of a grid-wide barrier between levels, every solution entry of w (forward)
+// and z (backward) starts as a sentinel bit pattern (all ones: a NaN no
+// arithmetic produces), written by the host before the launch, and each
+// row's final value is published with one single-copy-atomic relaxed store.
+// A row that needs an entry loads it with a relaxed (L2-coherent) load and
+// polls while it still reads the sentinel.  So a row waits only for the rows
+// it actually depends on, the index and value loads of a level are issued
+// before its dependencies are ready, and consecutive levels overlap.  Every
+// thread walks the levels in order and all CTAs are resident (cooperative
+// launch, one CTA per SM), so every wait ends: the rows of level 0 depend on
+// nothing, and a row of level l waits only on rows of levels < l, whose
+// threads never wait on level l.  The waits are bounded anyway: after
+// kSpinLimit polls a thread records a timeout in `err`, stops waiting and
+// the apply returns garbage that the host reports as JD_EDEVICE.
 #pragma once
 #include "ildl_impl.cuh"
 
 namespace ajd {
 namespace {
 
-// ---- persistent apply: all phases of K^{-1} b in one cooperative launch ----
-// Phase kinds: gather (level 0), forward level, dense trailing block,
-// backward level.  Phases run in order; a grid-wide barrier separates them
-// (every phase reads only results of earlier phases).  The barrier counts
-// CTA arrivals on one counter (zeroed before the launch); waits are bounded
-// and record a timeout in `err` instead of hanging.
+// Phase kinds: level 0 (no dependencies), forward level, dense trailing
+// block, backward level.  Threads walk the phase list in order.
 enum { PH_GATHER = 0, PH_FWD = 1, PH_DENSE = 2, PH_BWD = 3 };
 constexpr int kPersistThreads = 512;
-constexpr unsigned kSpinLimit = 1u << 22;  // ~0.1-0.5 s at 32-128 ns per poll
+constexpr unsigned kSpinLimit = 1u << 20;  // polls per thread and apply (~0.5-1 s)
 
 // V: type of the stored factor values; X: type of the work vectors and of
 // the sums; IO: type of the caller's b and x.  binary64 apply: V = X = IO =
@@ -47,11 +61,11 @@ __device__ __forceinline__ W ldw(const V* p) {
 }
 
 // ---- arithmetic of the sweeps, per work type ----
-// zero, acc += v * x (mac), a + b, a - b, v * x, shuffles, L2 loads/stores,
-// conversions from and to the caller's type.  The float-float forms use the
-// error-free transformations of Dekker and Knuth (TwoSum, FMA-based
-// TwoProduct): the product v * x.hi is split into its rounded value and
-// exact error, and every addition carries its rounding error into lo.
+// zero, acc += v * x (mac), a + b, a - b, v * x, shuffles, conversions from
+// and to the caller's type.  The float-float forms use the error-free
+// transformations of Dekker and Knuth (TwoSum, FMA-based TwoProduct): the
+// product v * x.hi is split into its rounded value and exact error, and
+// every addition carries its rounding error into lo.
 template <typename X>
 __device__ __forceinline__ X zero() {
   return X(0);
@@ -124,22 +138,6 @@ __device__ __forceinline__ df64 shfl_xor(df64 v, int o, int w) {
   return df64{__shfl_xor_sync(0xffffffffu, v.hi, o, w), __shfl_xor_sync(0xffffffffu, v.lo, o, w)};
 }
 
-template <typename X>
-__device__ __forceinline__ X ldx(const X* p) {
-  return __ldcg(p);
-}
-__device__ __forceinline__ df64 ldx(const df64* p) {
-  const float2 v = __ldcg(reinterpret_cast<const float2*>(p));
-  return df64{v.x, v.y};
-}
-template <typename X>
-__device__ __forceinline__ void stx(X* p, X v) {
-  __stcg(p, v);
-}
-__device__ __forceinline__ void stx(df64* p, df64 v) {
-  __stcg(reinterpret_cast<float2*>(p), make_float2(v.hi, v.lo));
-}
-
 template <typename X, typename IO>
 __device__ __forceinline__ X from_io(IO v) {
   return (X)v;
@@ -158,6 +156,117 @@ __device__ __forceinline__ double to_io<double, df64>(df64 v) {
   return (double)v.hi + (double)v.lo;
 }
 
+// ---- publication and polling of solution entries ----
+// Bits of one work-vector entry (8 bytes for binary64 and float-float,
+// 4 for binary32); the sentinel is all ones.  Stores and loads are relaxed
+// at GPU scope and of the entry's full width, so a reader sees either the
+// sentinel or the final value, never a mix, and never a stale L1 copy.
+template <typename X>
+struct Bits {
+  using type = unsigned long long;
+};
+template <>
+struct Bits<float> {
+  using type = unsigned;
+};
+
+__device__ __forceinline__ unsigned long long ld_relaxed(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ unsigned ld_relaxed(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ void st_relaxed(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ void st_relaxed(unsigned* p, unsigned v) {
+  asm volatile("st.relaxed.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+template <typename X>
+__device__ __forceinline__ typename Bits<X>::type to_bits(X v) {
+  typename Bits<X>::type b;
+  memcpy(&b, &v, sizeof(b));
+  return b;
+}
+template <typename X>
+__device__ __forceinline__ X from_bits(typename Bits<X>::type b) {
+  X v;
+  memcpy(&v, &b, sizeof(b));
+  return v;
+}
+template <typename B>
+__device__ __forceinline__ bool is_sentinel(B b) {
+  return b == ~B(0);
+}
+
+// Per-thread wait state: polls spent so far in this apply, and whether a
+// wait has given up (then no further wait is attempted).
+struct Waiter {
+  unsigned spins;
+  bool dead;
+  int* err;
+};
+
+// Poll entry p until it holds a published value (bounded).
+template <typename X>
+__device__ __noinline__ typename Bits<X>::type wait_bits(const X* p, Waiter& wt) {
+  using B = typename Bits<X>::type;
+  const B* q = reinterpret_cast<const B*>(p);
+  B b = ld_relaxed(q);
+  while (is_sentinel(b) && !wt.dead) {
+    ++wt.spins;
+    if ((wt.spins & 255u) == 0 && *((volatile int*)wt.err)) {
+      wt.dead = true;
+      break;
+    }
+    if (wt.spins > kSpinLimit) {
+      atomicExch(wt.err, 1);
+      wt.dead = true;
+      break;
+    }
+    __nanosleep(20);
+    b = ld_relaxed(q);
+  }
+  return is_sentinel(b) ? B(0) : b;
+}
+
+// Load entry p of a work vector: one relaxed load, polling only while the
+// entry is not yet published.
+template <typename X>
+__device__ __forceinline__ X take(const X* p, Waiter& wt) {
+  using B = typename Bits<X>::type;
+  B b = ld_relaxed(reinterpret_cast<const B*>(p));
+  if (is_sentinel(b)) b = wait_bits(p, wt);
+  return from_bits<X>(b);
+}
+
+// Gathers of N entries x[c[i]] (c[i] < 0: none, value 0): all N loads are
+// issued before the first is inspected, so their latencies overlap; only
+// entries still unpublished are then polled.
+template <typename X, int N>
+__device__ __forceinline__ void gather(const X* x, const int (&c)[N], X (&out)[N], Waiter& wt) {
+  using B = typename Bits<X>::type;
+  B r[N];
+#pragma unroll
+  for (int i = 0; i < N; ++i) r[i] = c[i] >= 0 ? ld_relaxed(reinterpret_cast<const B*>(x + c[i])) : B(0);
+#pragma unroll
+  for (int i = 0; i < N; ++i)
+    if (is_sentinel(r[i])) r[i] = wait_bits(x + c[i], wt);
+#pragma unroll
+  for (int i = 0; i < N; ++i) out[i] = from_bits<X>(r[i]);
+}
+
+template <typename X>
+__device__ __forceinline__ void publish(X* p, X v) {
+  using B = typename Bits<X>::type;
+  st_relaxed(reinterpret_cast<B*>(p), to_bits(v));
+}
+
 template <typename V, typename X, typename IO = X>
 struct ApplyArgs {
   const int* perm;
@@ -172,121 +281,95 @@ struct ApplyArgs {
   const V* dof;
   const int* partner;
   const V* dense;
-  X* w;
-  X* z;
+  X* w;  // forward solution, sentinel-filled before the launch
+  X* z;  // backward solution, sentinel-filled before the launch
   const IO* b;
   IO* out;
   int nd, d0;
 };
 
-__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
-  unsigned v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
+// Row operands loaded before the row's entries (their latency overlaps the
+// gathers): forward -- the right-hand side s[p] b[perm[p]]; backward -- the
+// 2x2 partner and the permutation entry.
+template <typename V, typename X, typename IO>
+struct RowHead {
+  X rhs;
+  int pp, perm;
+};
 
-// Grid barrier number `ph` (0-based) of one cooperative launch: every CTA
-// adds one arrival to `count` (release) and polls it (acquire) until all
-// CTAs of barriers 0..ph have arrived.  Polls are bounded: after kSpinLimit
-// of them the CTA records a timeout in `err` and the kernel returns early;
-// the other CTAs see the flag and return too.
-__device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned* gen, unsigned ph, int* err) {
-  (void)gen;
-  __syncthreads();
-  __shared__ int failed;
-  if (threadIdx.x == 0) {
-    int f = 0;
-    // release-add: this CTA's writes (ordered by the CTA barrier above)
-    // become visible before its arrival is counted
-    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(count) : "memory");
-    const unsigned target = (ph + 1) * gridDim.x;
-    unsigned spins = 0;
-    while (ld_acquire_u32(count) < target) {
-      ++spins;
-      if ((spins & 1023u) == 0 && *((volatile int*)err)) { f = 1; break; }
-      if (spins > kSpinLimit) {
-        atomicExch(err, 1);
-        f = 1;
-        break;
-      }
-      if (spins > 64) __nanosleep(32);
-    }
-    failed = f;
-  }
-  __syncthreads();
-  return failed == 0;
+template <typename V, typename X, typename IO>
+__device__ __forceinline__ RowHead<V, X, IO> row_head(const ApplyArgs<V, X, IO>& a, int kind, int p) {
+  using W = typename ValueReg<V, X>::type;
+  RowHead<V, X, IO> h{zero<X>(), -1, 0};
+  h.perm = __ldg(a.perm + p);
+  if (kind == PH_FWD) h.rhs = mul(ldw<W>(a.scale + p), from_io<X>(__ldg(a.b + h.perm)));
+  else h.pp = __ldg(a.partner + p);
+  return h;
 }
 
 // Final value of row p of a sweep, given the row's dot product `acc` with
-// the solution entries it depends on, its right-hand side (forward) and its
-// 2x2 partner and permutation entry (backward; loaded before the row's
-// entries so that their latency overlaps the gathers).
+// the solution entries it depends on.
 template <typename V, typename X, typename IO>
-__device__ __forceinline__ void finish_value(const ApplyArgs<V, X, IO>& a, int kind, int p, X acc, X rhs, int pp,
-                                             int perm) {
+__device__ __forceinline__ void finish_value(const ApplyArgs<V, X, IO>& a, int kind, int p, X acc,
+                                             const RowHead<V, X, IO>& h, Waiter& wt) {
   using W = typename ValueReg<V, X>::type;
   if (kind == PH_FWD) {
-    stx(a.w + p, sub(rhs, acc));  // rhs = s[p] b[perm[p]], stored in w by the gather phase
+    publish(a.w + p, sub(h.rhs, acc));
   } else {
-    X d = mul(ldw<W>(a.dd + p), ldx(a.w + p));
-    if (pp >= 0) d = add(d, mul(ldw<W>(a.dof + p), ldx(a.w + pp)));
+    X d = mul(ldw<W>(a.dd + p), take(a.w + p, wt));
+    if (h.pp >= 0) d = add(d, mul(ldw<W>(a.dof + p), take(a.w + h.pp, wt)));
     const X zp = sub(d, acc);
-    stx(a.z + p, zp);
-    a.out[perm] = to_io<IO>(mul(ldw<W>(a.scale + p), zp));
+    publish(a.z + p, zp);
+    a.out[h.perm] = to_io<IO>(mul(ldw<W>(a.scale + p), zp));
   }
 }
 
 template <typename V, typename X, typename IO, int G>
-__device__ __forceinline__ void finish_row(const ApplyArgs<V, X, IO>& a, int kind, int p, X acc, int lane, X rhs,
-                                           int pp, int perm) {
+__device__ __forceinline__ void finish_row(const ApplyArgs<V, X, IO>& a, int kind, int p, X acc, int lane,
+                                           const RowHead<V, X, IO>& h, Waiter& wt) {
   acc = norm(acc);
 #pragma unroll
   for (int o = G / 2; o > 0; o >>= 1) acc = add(acc, shfl_xor(acc, o, G));
-  if (p >= 0 && lane == 0) finish_value(a, kind, p, acc, rhs, pp, perm);
+  if (p >= 0 && lane == 0) finish_value(a, kind, p, acc, h, wt);
 }
 
 // Rows of one level, G threads per row; each group handles two rows at a
 // time with their loads interleaved (index/value loads of both rows first,
 // then the gathers), so every memory latency is shared by two rows.
 template <typename V, typename X, typename IO, int G>
-__device__ __forceinline__ void level_rows(const ApplyArgs<V, X, IO>& a, int kind, int p0, int p1) {
+__device__ __forceinline__ void level_rows(const ApplyArgs<V, X, IO>& a, int kind, int p0, int p1, int cta,
+                                           Waiter& wt) {
   using W = typename ValueReg<V, X>::type;
   const int lane = threadIdx.x % G;
   const int64_t groups = (int64_t)gridDim.x * blockDim.x / G;
-  const int64_t g0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
+  const int64_t g0 = ((int64_t)cta * blockDim.x + threadIdx.x) / G;
   const int* ptr = kind == PH_FWD ? a.Lptr : a.Uptr;
   const int* col = kind == PH_FWD ? a.Lcol : a.Ucol;
   const V* val = kind == PH_FWD ? a.Lval : a.Uval;
   const X* x = kind == PH_FWD ? a.w : a.z;  // vector read through the columns
-  constexpr int B = 8;                      // entries per lane and row per batch
+  // entries per lane and row per batch (fewer with binary64 values, which
+  // take twice the registers)
+  constexpr int B = sizeof(V) == 8 ? 4 : 8;
   for (int64_t base = p0; base < p1; base += 2 * groups) {
     const int64_t ra = base + g0, rb = base + groups + g0;
     const int pa = ra < p1 ? (int)ra : -1;
     const int pb = rb < p1 ? (int)rb : -1;
     int qa = 0, ea = 0, qb = 0, eb = 0;
-    X ra_rhs = zero<X>(), rb_rhs = zero<X>();
-    int ppa = -1, ppb = -1, pma = 0, pmb = 0;
+    RowHead<V, X, IO> ha{zero<X>(), -1, 0}, hb{zero<X>(), -1, 0};
     if (pa >= 0) {
       qa = __ldg(ptr + pa) + lane;
       ea = __ldg(ptr + pa + 1);
-      if (lane == 0) {
-        if (kind == PH_FWD) ra_rhs = ldx(a.w + pa);
-        else { ppa = __ldg(a.partner + pa); pma = __ldg(a.perm + pa); }
-      }
+      if (lane == 0) ha = row_head(a, kind, pa);
     }
     if (pb >= 0) {
       qb = __ldg(ptr + pb) + lane;
       eb = __ldg(ptr + pb + 1);
-      if (lane == 0) {
-        if (kind == PH_FWD) rb_rhs = ldx(a.w + pb);
-        else { ppb = __ldg(a.partner + pb); pmb = __ldg(a.perm + pb); }
-      }
+      if (lane == 0) hb = row_head(a, kind, pb);
     }
     // two partial sums per row halve the dependent chain of FMAs
     X acca = zero<X>(), accb = zero<X>(), acca2 = zero<X>(), accb2 = zero<X>();
     while (qa < ea || qb < eb) {
-      // lanes past the end of a row gather nothing: the solution entry they
-      // would point at may not be written yet in this sweep (0 * NaN = NaN)
+      // lanes past the end of a row gather nothing
       int ca[B], cb[B];
       W va[B], vb[B];
 #pragma unroll
@@ -298,24 +381,29 @@ __device__ __forceinline__ void level_rows(const ApplyArgs<V, X, IO>& a, int kin
         cb[i] = o2 ? __ldg(col + q2) : -1;
         vb[i] = o2 ? ldw<W>(val + q2) : W(0);
       }
+      // both rows' gathers in flight at once
+      int cab[2 * B];
+      X xab[2 * B];
+#pragma unroll
+      for (int i = 0; i < B; ++i) {
+        cab[i] = ca[i];
+        cab[B + i] = cb[i];
+      }
+      gather(x, cab, xab, wt);
 #pragma unroll
       for (int i = 0; i < B; i += 2) {
-        const X xa0 = ca[i] >= 0 ? ldx(x + ca[i]) : zero<X>();
-        const X xb0 = cb[i] >= 0 ? ldx(x + cb[i]) : zero<X>();
-        const X xa1 = ca[i + 1] >= 0 ? ldx(x + ca[i + 1]) : zero<X>();
-        const X xb1 = cb[i + 1] >= 0 ? ldx(x + cb[i + 1]) : zero<X>();
-        mac(acca, va[i], xa0);
-        mac(accb, vb[i], xb0);
-        mac(acca2, va[i + 1], xa1);
-        mac(accb2, vb[i + 1], xb1);
+        mac(acca, va[i], xab[i]);
+        mac(accb, vb[i], xab[B + i]);
+        mac(acca2, va[i + 1], xab[i + 1]);
+        mac(accb2, vb[i + 1], xab[B + i + 1]);
       }
       qa += B * G;
       qb += B * G;
     }
     acca = add(norm(acca), norm(acca2));
     accb = add(norm(accb), norm(accb2));
-    finish_row<V, X, IO, G>(a, kind, pa, acca, lane, ra_rhs, ppa, pma);
-    finish_row<V, X, IO, G>(a, kind, pb, accb, lane, rb_rhs, ppb, pmb);
+    finish_row<V, X, IO, G>(a, kind, pa, acca, lane, ha, wt);
+    finish_row<V, X, IO, G>(a, kind, pb, accb, lane, hb, wt);
   }
 }
 
@@ -325,9 +413,10 @@ __device__ __forceinline__ void level_rows(const ApplyArgs<V, X, IO>& a, int kin
 // shared memory.  The row loop is uniform across the CTA (it depends on the
 // block index only), as the CTA barriers inside it require.
 template <typename V, typename X, typename IO, int G>
-__device__ __forceinline__ void level_rows_wide(const ApplyArgs<V, X, IO>& a, int kind, int p0, int p1) {
+__device__ __forceinline__ void level_rows_wide(const ApplyArgs<V, X, IO>& a, int kind, int p0, int p1, int cta,
+                                                Waiter& wt) {
   using VR = typename ValueReg<V, X>::type;
-  constexpr int W = G / 32;                 // warps per row
+  constexpr int NW = G / 32;                // warps per row
   constexpr int RPC = kPersistThreads / G;  // rows per CTA and pass
   constexpr int B = 8;                      // entries per thread and batch
   __shared__ X part[kPersistThreads / 32];
@@ -337,14 +426,11 @@ __device__ __forceinline__ void level_rows_wide(const ApplyArgs<V, X, IO>& a, in
   const int* col = kind == PH_FWD ? a.Lcol : a.Ucol;
   const V* val = kind == PH_FWD ? a.Lval : a.Uval;
   const X* x = kind == PH_FWD ? a.w : a.z;
-  for (int64_t base = p0 + (int64_t)blockIdx.x * RPC; base < p1; base += (int64_t)gridDim.x * RPC) {
+  for (int64_t base = p0 + (int64_t)cta * RPC; base < p1; base += (int64_t)gridDim.x * RPC) {
     const int p = base + slot < p1 ? (int)(base + slot) : -1;
-    X acc = zero<X>(), acc2 = zero<X>(), rhs = zero<X>();
-    int pp = -1, pm = 0;
-    if (p >= 0 && t == 0) {
-      if (kind == PH_FWD) rhs = ldx(a.w + p);
-      else { pp = __ldg(a.partner + p); pm = __ldg(a.perm + p); }
-    }
+    X acc = zero<X>(), acc2 = zero<X>();
+    RowHead<V, X, IO> h{zero<X>(), -1, 0};
+    if (p >= 0 && t == 0) h = row_head(a, kind, p);
     if (p >= 0) {
       int q = __ldg(ptr + p) + t;
       const int e = __ldg(ptr + p + 1);
@@ -357,12 +443,12 @@ __device__ __forceinline__ void level_rows_wide(const ApplyArgs<V, X, IO>& a, in
           c[i] = o ? __ldg(col + q + i * G) : -1;
           v[i] = o ? ldw<VR>(val + q + i * G) : VR(0);
         }
+        X xv[B];
+        gather(x, c, xv, wt);
 #pragma unroll
         for (int i = 0; i < B; i += 2) {
-          const X x0 = c[i] >= 0 ? ldx(x + c[i]) : zero<X>();
-          const X x1 = c[i + 1] >= 0 ? ldx(x + c[i + 1]) : zero<X>();
-          mac(acc, v[i], x0);
-          mac(acc2, v[i + 1], x1);
+          mac(acc, v[i], xv[i]);
+          mac(acc2, v[i + 1], xv[i + 1]);
         }
       }
     }
@@ -374,70 +460,52 @@ __device__ __forceinline__ void level_rows_wide(const ApplyArgs<V, X, IO>& a, in
     if (p >= 0 && t == 0) {
       X sum = zero<X>();
 #pragma unroll
-      for (int j = 0; j < W; ++j) sum = add(sum, part[slot * W + j]);
-      finish_value(a, kind, p, sum, rhs, pp, pm);
+      for (int j = 0; j < NW; ++j) sum = add(sum, part[slot * NW + j]);
+      finish_value(a, kind, p, sum, h, wt);
     }
     __syncthreads();  // part[] is reused by the next pass
   }
 }
 
-// Prefetch the stored rows of a level phase into L2 (lines strided over the
-// whole grid); skipped for phases larger than 16 MB, which stream from HBM
-// at full bandwidth anyway.
-template <typename V, typename X, typename IO>
-__device__ __forceinline__ void prefetch_phase(const ApplyArgs<V, X, IO>& a, int4 P) {
-  if (P.x != PH_FWD && P.x != PH_BWD) return;
-  const int* ptr = P.x == PH_FWD ? a.Lptr : a.Uptr;
-  const int* col = P.x == PH_FWD ? a.Lcol : a.Ucol;
-  const V* val = P.x == PH_FWD ? a.Lval : a.Uval;
-  const int64_t q0 = __ldg(ptr + P.y), q1 = __ldg(ptr + P.z);
-  const int64_t bytes = (q1 - q0) * (int64_t)(sizeof(V) + sizeof(int));
-  if (bytes > (16ll << 20) || q1 <= q0) return;
-  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t nth = (int64_t)gridDim.x * blockDim.x;
-  const int64_t lines_v = ((q1 - q0) * (int64_t)sizeof(V) + 127) / 128;
-  const int64_t lines_c = ((q1 - q0) * (int64_t)sizeof(int) + 127) / 128;
-  const char* vb = reinterpret_cast<const char*>(val + q0);
-  const char* cb = reinterpret_cast<const char*>(col + q0);
-  for (int64_t l = tid; l < lines_v + lines_c; l += nth) {
-    const char* addr = l < lines_v ? vb + l * 128 : cb + (l - lines_v) * 128;
-    asm volatile("prefetch.global.L2 [%0];" ::"l"(addr));
-  }
-}
-
 template <typename V, typename X, typename IO>
 __global__ void __launch_bounds__(kPersistThreads, 1)
-ildl_apply_persistent_kernel(ApplyArgs<V, X, IO> a, const int4* __restrict__ phases, int nphase, unsigned* count,
-                             unsigned* gen, int* err, unsigned long long* stamps) {
+ildl_apply_persistent_kernel(ApplyArgs<V, X, IO> a, const int4* __restrict__ phases, int nphase, int* err,
+                             unsigned long long* stamps) {
+  using W = typename ValueReg<V, X>::type;
+  Waiter wt{0u, false, err};
+  if (stamps && blockIdx.x == 0 && threadIdx.x == 0) {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    stamps[0] = t;  // start (CTA 0)
+  }
   for (int ph = 0; ph < nphase; ++ph) {
-    const int4 P = phases[ph];  // kind, p0, p1, G
-    const int kind = P.x, p0 = P.y, p1 = P.z, G = P.w;
-    if (stamps && blockIdx.x == 0 && threadIdx.x == 0) {
-      unsigned long long t;
-      asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-      stamps[ph] = t;
-    }
-    const int4 Pn = ph + 1 < nphase ? phases[ph + 1] : make_int4(-1, 0, 0, 0);
-    using W = typename ValueReg<V, X>::type;
+    const int4 P = phases[ph];  // kind, p0, p1, G | first CTA << 16
+    const int kind = P.x, p0 = P.y, p1 = P.z, G = P.w & 0xFFFF;
+    // the phase's rows start at CTA P.w >> 16: consecutive small phases land
+    // on different CTAs, whose loads are then issued while the previous
+    // level is still being computed (not after it, as on one CTA)
+    const int cta = (int)((blockIdx.x + gridDim.x - (unsigned)(P.w >> 16) % gridDim.x) % gridDim.x);
     if (kind == PH_GATHER) {
+      // level 0: rows without entries, w = s b[perm]
       for (int p = p0 + blockIdx.x * blockDim.x + threadIdx.x; p < p1; p += gridDim.x * blockDim.x)
-        stx(a.w + p, mul(ldw<W>(a.scale + p), from_io<X>(__ldg(a.b + __ldg(a.perm + p)))));
+        publish(a.w + p, mul(ldw<W>(a.scale + p), from_io<X>(__ldg(a.b + __ldg(a.perm + p)))));
     } else if (kind == PH_DENSE) {
       const int lane = threadIdx.x & 31;
       const int warps = (gridDim.x * blockDim.x) >> 5;
-      for (int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < a.nd; r += warps) {
+      for (int r = (cta * blockDim.x + threadIdx.x) >> 5; r < a.nd; r += warps) {
         const V* row = a.dense + (int64_t)r * a.nd;
         X acc = zero<X>(), acc2 = zero<X>();
         for (int c0 = lane; c0 < a.nd; c0 += 8 * 32) {
           W rv[8];
           X wv[8];
+          int cc[8];
 #pragma unroll
           for (int i = 0; i < 8; ++i) {
             const int c = c0 + 32 * i;
-            const bool ok = c < a.nd;
-            rv[i] = ok ? ldw<W>(row + c) : W(0);
-            wv[i] = ok ? ldx(a.w + a.d0 + c) : zero<X>();
+            rv[i] = c < a.nd ? ldw<W>(row + c) : W(0);
+            cc[i] = c < a.nd ? c : -1;
           }
+          gather(a.w + a.d0, cc, wv, wt);
 #pragma unroll
           for (int i = 0; i < 8; i += 2) {
             mac(acc, rv[i], wv[i]);
@@ -448,30 +516,29 @@ ildl_apply_persistent_kernel(ApplyArgs<V, X, IO> a, const int4* __restrict__ pha
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) acc = add(acc, shfl_xor(acc, o, 32));
         if (lane == 0) {
-          stx(a.z + a.d0 + r, acc);
+          publish(a.z + a.d0 + r, acc);
           a.out[__ldg(a.perm + a.d0 + r)] = to_io<IO>(mul(ldw<W>(a.scale + a.d0 + r), acc));
         }
       }
     } else {
       switch (G) {  // threads per row, fixed per phase at upload
-        case 4: level_rows<V, X, IO, 4>(a, kind, p0, p1); break;
-        case 8: level_rows<V, X, IO, 8>(a, kind, p0, p1); break;
-        case 16: level_rows<V, X, IO, 16>(a, kind, p0, p1); break;
-        case 32: level_rows<V, X, IO, 32>(a, kind, p0, p1); break;
-        case 64: level_rows_wide<V, X, IO, 64>(a, kind, p0, p1); break;
-        case 128: level_rows_wide<V, X, IO, 128>(a, kind, p0, p1); break;
-        case 256: level_rows_wide<V, X, IO, 256>(a, kind, p0, p1); break;
-        default: level_rows_wide<V, X, IO, 512>(a, kind, p0, p1); break;
+        case 4: level_rows<V, X, IO, 4>(a, kind, p0, p1, cta, wt); break;
+        case 8: level_rows<V, X, IO, 8>(a, kind, p0, p1, cta, wt); break;
+        case 16: level_rows<V, X, IO, 16>(a, kind, p0, p1, cta, wt); break;
+        case 32: level_rows<V, X, IO, 32>(a, kind, p0, p1, cta, wt); break;
+        case 64: level_rows_wide<V, X, IO, 64>(a, kind, p0, p1, cta, wt); break;
+        case 128: level_rows_wide<V, X, IO, 128>(a, kind, p0, p1, cta, wt); break;
+        case 256: level_rows_wide<V, X, IO, 256>(a, kind, p0, p1, cta, wt); break;
+        default: level_rows_wide<V, X, IO, 512>(a, kind, p0, p1, cta, wt); break;
       }
     }
-    if (ph + 1 < nphase) prefetch_phase<V, X, IO>(a, Pn);
-    if (ph + 1 < nphase && !grid_barrier(count, gen, (unsigned)ph, err)) return;
+    if (stamps && cta == 0 && threadIdx.x == 0) {
+      unsigned long long t;
+      asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+      stamps[ph + 1] = t;  // when the phase's first CTA is done with it (phases overlap)
+    }
   }
-  if (stamps && blockIdx.x == 0 && threadIdx.x == 0) {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    stamps[nphase] = t;
-  }
+
 }
 
 }  // namespace

@@ -72,6 +72,6 @@ int ildl_create_on_stream(anderson_t h, double sigma, const ildl_params* p, ildl
                           int copies = kCopyAll);
 
 // JD_EDEVICE if a device-side wait of an apply timed out (reads a flag).
-int ildl_check_device_error(const ildl_s* f);
+int ildl_check_device_error(const ildl_s* f, cudaStream_t s);
 
 }  // namespace ajd

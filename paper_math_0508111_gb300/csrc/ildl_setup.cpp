@@ -700,7 +700,16 @@ bool dense_inverse(int m, dvec<double>& M, dvec<double>& inv) {
 
 }  // namespace
 
-int build_ildl(const SymCsr& A, const ildl_params& prm, HostFactor& F, bool dense_on_host) {
+double default_gamma(int64_t n, bool offdiag) {
+  // weak-coupling threshold of the independent sets; by default it shrinks
+  // with the drop tolerance (measured: a fixed 0.02 loses the preconditioner
+  // at n = 10^6 while 5/sqrt(n) keeps it).  Off-diagonal disorder (Section
+  // 7) loses more by ignoring weak couplings: 1/sqrt(n) there.
+  const double rn = std::sqrt((double)std::max<int64_t>(n, 1));
+  return std::min(0.02, (offdiag ? 1.0 : 5.0) / rn);
+}
+
+int build_ildl(const SymCsr& A, const ildl_params& prm, HostFactor& F, bool dense_on_host, SchurEngine* engine) {
   const auto t_start = Clock::now();
   const int n = A.n;
   if (n <= 0) return fail(JD_EINVAL, "ildl: empty matrix");
@@ -709,10 +718,7 @@ int build_ildl(const SymCsr& A, const ildl_params& prm, HostFactor& F, bool dens
   const double tau = eps_drop / kappa;
   const double agg_tau = prm.aggressive > 0.0 ? prm.aggressive : 0.0;  // Section 6.3, 0 = off
 
-  // weak-coupling threshold of the independent sets; by default it shrinks
-  // with the drop tolerance (measured: a fixed 0.02 loses the preconditioner
-  // at n = 10^6 while 5/sqrt(n) keeps it)
-  const double gamma = prm.gamma < 0.0 ? std::min(0.02, 5.0 / std::sqrt((double)n)) : prm.gamma;
+  const double gamma = prm.gamma < 0.0 ? default_gamma(n, false) : prm.gamma;
   const int max_levels = prm.max_levels > 0 ? prm.max_levels : 64;
   // dense tail: the given size, else n/16 clamped to 1000..6000 (the
   // O(n_dense^3) inversion stays small for small lattices)
@@ -766,6 +772,10 @@ int build_ildl(const SymCsr& A, const ildl_params& prm, HostFactor& F, bool dens
   std::vector<RowWork> rwork(std::max(1, omp_get_max_threads()));
 
   const bool verbose = std::getenv("AJD_SETUP_VERBOSE") != nullptr;
+  if (engine) {
+    const int erc = engine->begin(S);
+    if (erc != JD_OK) return erc;
+  }
   int level = 0;
   for (;; ++level) {
     const auto t_level = Clock::now();
@@ -810,6 +820,10 @@ int build_ildl(const SymCsr& A, const ildl_params& prm, HostFactor& F, bool dens
       }
       diag[i] = dg;
       offsum[i] = o;
+    }
+    if (engine) {
+      const int erc = engine->scale(d.data(), m);
+      if (erc != JD_OK) return erc;
     }
     if (use_matching) {
       split_cycles(S, mc, groups);
@@ -1143,229 +1157,255 @@ int build_ildl(const SymCsr& A, const ildl_params& prm, HostFactor& F, bool dens
       rec_slot[i] = slot;
     });
     const double ts_rec = ms_since(t_schur);
-    // upper triangle of S', row by row: chunk ch holds the rows of its row
-    // range in order; rowcnt[r] entries per row (diagonal included)
-    std::vector<int> rowcnt(mc_n, 0);
-    // a new row is typically as long as the old ones: room for about 3/4 of
-    // an old row per upper row, so that the chunk buffers rarely grow
-    const double upper_guess = 0.75 * (double)S.ptr[m] / m + 8.0;
-    {
-#pragma omp parallel
+    double ts_num = 0.0;
+    SymCsr& Sn = Snext;
+    std::vector<double>& next_rowmax = mwork.rowmax_in;  // the next matching's row maxima
+    if (engine) {
+      // S' on the engine (the GPU), from the records above
+      std::vector<char> is2(acc.size());
+      for (size_t b = 0; b < acc.size(); ++b) is2[b] = cands[acc[b]].b >= 0;
+      SchurLevel lv;
+      lv.m = m;
+      lv.mc_n = mc_n;
+      lv.nblk = (int)acc.size();
+      lv.cidx = cidx.data();
+      lv.cnodes = cnodes.data();
+      lv.rrec = rrec.data();
+      lv.rec_blk = rec_blk.data();
+      lv.rec_slot = rec_slot.data();
+      lv.cptr = cptr.data();
+      lv.crow = crow.data();
+      lv.c1 = c1.data();
+      lv.c2 = c2.data();
+      lv.bmat = bmat.data();
+      lv.is2x2 = is2.data();
+      lv.tau = tau;
+      const int erc = engine->schur(lv, Sn, next_rowmax);
+      if (erc != JD_OK) return erc;
+      ts_num = ms_since(t_schur) - ts_rec;
+    } else {
+      // upper triangle of S', row by row: chunk ch holds the rows of its row
+      // range in order; rowcnt[r] entries per row (diagonal included)
+      std::vector<int> rowcnt(mc_n, 0);
+      // a new row is typically as long as the old ones: room for about 3/4 of
+      // an old row per upper row, so that the chunk buffers rarely grow
+      const double upper_guess = 0.75 * (double)S.ptr[m] / m + 8.0;
       {
-        RowWork& rw = rwork[omp_get_thread_num()];
-        if (rw.cap < mc_n) {
-          rw.accv.assign(mc_n, 0.0);
-          rw.mark.assign(mc_n, 0);
-          // the row's columns in first-touch order; never more than mc_n,
-          // and written ahead of the count (below), so left uninitialised
-          rw.cols.reset(new int[(size_t)mc_n + 1]);
-          rw.cap = mc_n;
-        }
-        double* const accv = rw.accv.data();
-        char* const mark = rw.mark.data();
-        int* const cols = rw.cols.get();
+#pragma omp parallel
+        {
+          RowWork& rw = rwork[omp_get_thread_num()];
+          if (rw.cap < mc_n) {
+            rw.accv.assign(mc_n, 0.0);
+            rw.mark.assign(mc_n, 0);
+            // the row's columns in first-touch order; never more than mc_n,
+            // and written ahead of the count (below), so left uninitialised
+            rw.cols.reset(new int[(size_t)mc_n + 1]);
+            rw.cap = mc_n;
+          }
+          double* const accv = rw.accv.data();
+          char* const mark = rw.mark.data();
+          int* const cols = rw.cols.get();
 #pragma omp for schedule(dynamic, 1)
-        for (int ch = 0; ch < nchunk; ++ch) {
-          const int r0 = (int)((int64_t)mc_n * ch / nchunk), r1 = (int)((int64_t)mc_n * (ch + 1) / nchunk);
-          ucol[ch].clear();
-          uval[ch].clear();
-          ucol[ch].reserve((size_t)((r1 - r0) * upper_guess));
-          uval[ch].reserve((size_t)((r1 - r0) * upper_guess));
-          for (int r = r0; r < r1; ++r) {
-            const int k = cnodes[r];
-            if (lptr[r] == lptr[r + 1]) {
-              // no elimination update reaches this row: S' row = S row on C
-              // (column order is preserved by the C numbering)
-              const size_t before = ucol[ch].size();
+          for (int ch = 0; ch < nchunk; ++ch) {
+            const int r0 = (int)((int64_t)mc_n * ch / nchunk), r1 = (int)((int64_t)mc_n * (ch + 1) / nchunk);
+            ucol[ch].clear();
+            uval[ch].clear();
+            ucol[ch].reserve((size_t)((r1 - r0) * upper_guess));
+            uval[ch].reserve((size_t)((r1 - r0) * upper_guess));
+            for (int r = r0; r < r1; ++r) {
+              const int k = cnodes[r];
+              if (lptr[r] == lptr[r + 1]) {
+                // no elimination update reaches this row: S' row = S row on C
+                // (column order is preserved by the C numbering)
+                const size_t before = ucol[ch].size();
+                for (int64_t p = S.ptr[k]; p < S.ptr[k + 1]; ++p) {
+                  const int c = cidx[S.col[p]];
+                  if (c < r) continue;
+                  if (c == r || std::fabs(S.val[p]) >= tau) {
+                    ucol[ch].push_back(c);
+                    uval[ch].push_back(S.val[p]);
+                  }
+                }
+                rowcnt[r] = (int)(ucol[ch].size() - before);
+                continue;
+              }
+              int nc = 0;
               for (int64_t p = S.ptr[k]; p < S.ptr[k + 1]; ++p) {
                 const int c = cidx[S.col[p]];
-                if (c < r) continue;
-                if (c == r || std::fabs(S.val[p]) >= tau) {
-                  ucol[ch].push_back(c);
-                  uval[ch].push_back(S.val[p]);
+                if (c < r) continue;  // B columns have cidx -1
+                if (!mark[c]) { mark[c] = 1; cols[nc++] = c; }
+                accv[c] += S.val[p];
+              }
+              if (!mark[r]) { mark[r] = 1; cols[nc++] = r; }
+              // the blocks of row r of L_F (its records, in block order) with
+              // their (l_a, l_b) values; `me` is the row's record in the
+              // block's column list (rows ascending)
+              for (int64_t i = rrec[r]; i < rrec[r + 1]; ++i) {
+                const int b = rec_blk[i];
+                const int64_t me = rec_slot[i];
+                const double la = c1[me], lb = c2[me];
+                double wa, wb;  // (l_a, l_b) * D_b
+                if (cands[acc[b]].b < 0) { wa = la * bmat[3 * b]; wb = 0.0; }
+                else {
+                  wa = la * bmat[3 * b] + lb * bmat[3 * b + 1];
+                  wb = la * bmat[3 * b + 1] + lb * bmat[3 * b + 2];
                 }
+                // about half the updates reach a column for the first time:
+                // the column is stored unconditionally and counted only then
+                // (no unpredictable branch)
+                const int64_t te = cptr[b + 1];
+                if (cands[acc[b]].b < 0) {
+                  // 1x1 block: wb = 0 and every c2 is 0, so wb * c2 is +0 (the
+                  // same sum as the general form, without the second operand)
+                  for (int64_t t = me; t < te; ++t) {
+                    const int q = crow[t];  // q >= r because rows are ascending
+                    cols[nc] = q;
+                    nc += !mark[q];
+                    mark[q] = 1;
+                    accv[q] -= wa * c1[t] + 0.0;
+                  }
+                } else {
+                  for (int64_t t = me; t < te; ++t) {
+                    const int q = crow[t];
+                    cols[nc] = q;
+                    nc += !mark[q];
+                    mark[q] = 1;
+                    accv[q] -= wa * c1[t] + wb * c2[t];
+                  }
+                }
+              }
+              // drop first (branch-free: a dropped column is cleared, a kept
+              // one rewritten unchanged), then sort only the entries that stay
+              int keep = 0;
+              for (int x = 0; x < nc; ++x) {
+                const int c = cols[x];
+                const double a = accv[c];
+                const bool kept = c == r || std::fabs(a) >= tau;
+                cols[keep] = c;
+                keep += kept;
+                accv[c] = kept ? a : 0.0;
+                mark[c] = kept;
+              }
+              // the columns arrive as a few ascending runs (the old row, then
+              // the new columns of each block in row order): insertion sort
+              // moves little on such input and beats a general sort up to a
+              // few hundred entries
+              sort_ints(cols, keep, 256);
+              const size_t before = ucol[ch].size();
+              for (int x = 0; x < keep; ++x) {
+                const int c = cols[x];
+                ucol[ch].push_back(c);
+                uval[ch].push_back(accv[c]);
+                accv[c] = 0.0;
+                mark[c] = 0;
               }
               rowcnt[r] = (int)(ucol[ch].size() - before);
-              continue;
             }
-            int nc = 0;
-            for (int64_t p = S.ptr[k]; p < S.ptr[k + 1]; ++p) {
-              const int c = cidx[S.col[p]];
-              if (c < r) continue;  // B columns have cidx -1
-              if (!mark[c]) { mark[c] = 1; cols[nc++] = c; }
-              accv[c] += S.val[p];
-            }
-            if (!mark[r]) { mark[r] = 1; cols[nc++] = r; }
-            // the blocks of row r of L_F (its records, in block order) with
-            // their (l_a, l_b) values; `me` is the row's record in the
-            // block's column list (rows ascending)
-            for (int64_t i = rrec[r]; i < rrec[r + 1]; ++i) {
-              const int b = rec_blk[i];
-              const int64_t me = rec_slot[i];
-              const double la = c1[me], lb = c2[me];
-              double wa, wb;  // (l_a, l_b) * D_b
-              if (cands[acc[b]].b < 0) { wa = la * bmat[3 * b]; wb = 0.0; }
-              else {
-                wa = la * bmat[3 * b] + lb * bmat[3 * b + 1];
-                wb = la * bmat[3 * b + 1] + lb * bmat[3 * b + 2];
-              }
-              // about half the updates reach a column for the first time:
-              // the column is stored unconditionally and counted only then
-              // (no unpredictable branch)
-              const int64_t te = cptr[b + 1];
-              if (cands[acc[b]].b < 0) {
-                // 1x1 block: wb = 0 and every c2 is 0, so wb * c2 is +0 (the
-                // same sum as the general form, without the second operand)
-                for (int64_t t = me; t < te; ++t) {
-                  const int q = crow[t];  // q >= r because rows are ascending
-                  cols[nc] = q;
-                  nc += !mark[q];
-                  mark[q] = 1;
-                  accv[q] -= wa * c1[t] + 0.0;
-                }
-              } else {
-                for (int64_t t = me; t < te; ++t) {
-                  const int q = crow[t];
-                  cols[nc] = q;
-                  nc += !mark[q];
-                  mark[q] = 1;
-                  accv[q] -= wa * c1[t] + wb * c2[t];
-                }
-              }
-            }
-            // drop first (branch-free: a dropped column is cleared, a kept
-            // one rewritten unchanged), then sort only the entries that stay
-            int keep = 0;
-            for (int x = 0; x < nc; ++x) {
-              const int c = cols[x];
-              const double a = accv[c];
-              const bool kept = c == r || std::fabs(a) >= tau;
-              cols[keep] = c;
-              keep += kept;
-              accv[c] = kept ? a : 0.0;
-              mark[c] = kept;
-            }
-            // the columns arrive as a few ascending runs (the old row, then
-            // the new columns of each block in row order): insertion sort
-            // moves little on such input and beats a general sort up to a
-            // few hundred entries
-            sort_ints(cols, keep, 256);
-            const size_t before = ucol[ch].size();
-            for (int x = 0; x < keep; ++x) {
-              const int c = cols[x];
-              ucol[ch].push_back(c);
-              uval[ch].push_back(accv[c]);
-              accv[c] = 0.0;
-              mark[c] = 0;
-            }
-            rowcnt[r] = (int)(ucol[ch].size() - before);
           }
         }
       }
-    }
-    const double ts_num = ms_since(t_schur) - ts_rec;
-    // mirror the upper triangle into a full symmetric CSR: row c holds its
-    // lower entries (r, c), r < c, in increasing r, then its own upper
-    // entries.  Scattering the lower entries straight into their rows would
-    // miss the cache on almost every write, so they go through a bucket
-    // pass: (1) groups of consecutive chunks (increasing r) copy their upper
-    // rows and append each lower entry to the bucket of its column block,
-    // behind the entries of the groups before them; (2) each block, small
-    // enough to stay in cache, moves its bucket into the rows in bucket
-    // order.  Both keep increasing r per column whatever the group count.
-    SymCsr& Sn = Snext;
-    Sn.n = mc_n;
-    std::vector<double>& next_rowmax = mwork.rowmax_in;  // filled by the mirror below
-    next_rowmax.resize(mc_n);
-    {
-      const int64_t nup = [&] {
-        int64_t s = 0;
-        for (int ch = 0; ch < nchunk; ++ch) s += (int64_t)ucol[ch].size();
-        return s;
-      }();
-      const int G = (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)omp_get_max_threads(), (int64_t)nchunk, nup / 16384}));
-      constexpr int kBlkShift = 8;  // 256 columns per block
-      const int nblk = (mc_n >> kBlkShift) + 1;
-      auto chunk_row0 = [&](int ch) { return (int)((int64_t)mc_n * ch / nchunk); };
-      dvec<unsigned>& cnt = mirror_cnt;  // per group: lower entries per column
-      resize_discard(cnt, (size_t)G * mc_n);
+      ts_num = ms_since(t_schur) - ts_rec;
+      // mirror the upper triangle into a full symmetric CSR: row c holds its
+      // lower entries (r, c), r < c, in increasing r, then its own upper
+      // entries.  Scattering the lower entries straight into their rows would
+      // miss the cache on almost every write, so they go through a bucket
+      // pass: (1) groups of consecutive chunks (increasing r) copy their upper
+      // rows and append each lower entry to the bucket of its column block,
+      // behind the entries of the groups before them; (2) each block, small
+      // enough to stay in cache, moves its bucket into the rows in bucket
+      // order.  Both keep increasing r per column whatever the group count.
+      Sn.n = mc_n;
+      next_rowmax.resize(mc_n);
+      {
+        const int64_t nup = [&] {
+          int64_t s = 0;
+          for (int ch = 0; ch < nchunk; ++ch) s += (int64_t)ucol[ch].size();
+          return s;
+        }();
+        const int G = (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)omp_get_max_threads(), (int64_t)nchunk, nup / 16384}));
+        constexpr int kBlkShift = 8;  // 256 columns per block
+        const int nblk = (mc_n >> kBlkShift) + 1;
+        auto chunk_row0 = [&](int ch) { return (int)((int64_t)mc_n * ch / nchunk); };
+        dvec<unsigned>& cnt = mirror_cnt;  // per group: lower entries per column
+        resize_discard(cnt, (size_t)G * mc_n);
 #pragma omp parallel for schedule(static)
-      for (int g = 0; g < G; ++g) {
-        unsigned* c = cnt.data() + (size_t)g * mc_n;
-        std::fill(c, c + mc_n, 0u);
-        for (int ch = nchunk * g / G; ch < nchunk * (g + 1) / G; ++ch) {
-          const int* col = ucol[ch].data();
-          int64_t q = 0;
-          for (int r = chunk_row0(ch); r < chunk_row0(ch + 1); ++r)
-            for (const int64_t e = q + rowcnt[r]; q < e; ++q)
-              if (col[q] != r) ++c[col[q]];
-        }
-      }
-      std::vector<int> lowcnt(mc_n);
-      std::vector<int64_t> boff((size_t)G * nblk);  // per group: its first slot in each bucket
-      std::vector<int64_t> bptr(nblk + 1, 0);       // bucket b = lower entries of columns [256 b, 256 b + 256)
-#pragma omp parallel for schedule(static)
-      for (int b = 0; b < nblk; ++b) {
-        const int c0 = b << kBlkShift, c1 = std::min(mc_n, c0 + (1 << kBlkShift));
-        int64_t run = 0;
         for (int g = 0; g < G; ++g) {
-          boff[(size_t)g * nblk + b] = run;
-          for (int c = c0; c < c1; ++c) run += cnt[(size_t)g * mc_n + c];
-        }
-        for (int c = c0; c < c1; ++c) {
-          unsigned k = 0;
-          for (int g = 0; g < G; ++g) k += cnt[(size_t)g * mc_n + c];
-          lowcnt[c] = (int)k;
-        }
-        bptr[b + 1] = run;
-      }
-      for (int b = 0; b < nblk; ++b) bptr[b + 1] += bptr[b];
-      Sn.ptr.assign(mc_n + 1, 0);
-      for (int r = 0; r < mc_n; ++r) Sn.ptr[r + 1] = Sn.ptr[r] + lowcnt[r] + rowcnt[r];
-      resize_discard(Sn.col, Sn.ptr[mc_n]);
-      resize_discard(Sn.val, Sn.ptr[mc_n]);
-      resize_discard(mirror_tmp, bptr[nblk]);
-#pragma omp parallel for schedule(static)
-      for (int g = 0; g < G; ++g) {
-        int64_t* bo = boff.data() + (size_t)g * nblk;
-        for (int b = 0; b < nblk; ++b) bo[b] += bptr[b];
-        for (int ch = nchunk * g / G; ch < nchunk * (g + 1) / G; ++ch) {
-          const int* col = ucol[ch].data();
-          const double* val = uval[ch].data();
-          int64_t q = 0;
-          for (int r = chunk_row0(ch); r < chunk_row0(ch + 1); ++r) {
-            int64_t o = Sn.ptr[r] + lowcnt[r];
-            double mx = 0.0;  // max |entry| of the row's upper part
-            for (const int64_t e = q + rowcnt[r]; q < e; ++q, ++o) {
-              const int cc = col[q];
-              Sn.col[o] = cc;
-              Sn.val[o] = val[q];
-              mx = std::max(mx, std::fabs(val[q]));
-              if (cc != r) mirror_tmp[bo[cc >> kBlkShift]++] = {r, cc, val[q]};
-            }
-            next_rowmax[r] = mx;
+          unsigned* c = cnt.data() + (size_t)g * mc_n;
+          std::fill(c, c + mc_n, 0u);
+          for (int ch = nchunk * g / G; ch < nchunk * (g + 1) / G; ++ch) {
+            const int* col = ucol[ch].data();
+            int64_t q = 0;
+            for (int r = chunk_row0(ch); r < chunk_row0(ch + 1); ++r)
+              for (const int64_t e = q + rowcnt[r]; q < e; ++q)
+                if (col[q] != r) ++c[col[q]];
           }
         }
-      }
+        std::vector<int> lowcnt(mc_n);
+        std::vector<int64_t> boff((size_t)G * nblk);  // per group: its first slot in each bucket
+        std::vector<int64_t> bptr(nblk + 1, 0);       // bucket b = lower entries of columns [256 b, 256 b + 256)
+#pragma omp parallel for schedule(static)
+        for (int b = 0; b < nblk; ++b) {
+          const int c0 = b << kBlkShift, c1 = std::min(mc_n, c0 + (1 << kBlkShift));
+          int64_t run = 0;
+          for (int g = 0; g < G; ++g) {
+            boff[(size_t)g * nblk + b] = run;
+            for (int c = c0; c < c1; ++c) run += cnt[(size_t)g * mc_n + c];
+          }
+          for (int c = c0; c < c1; ++c) {
+            unsigned k = 0;
+            for (int g = 0; g < G; ++g) k += cnt[(size_t)g * mc_n + c];
+            lowcnt[c] = (int)k;
+          }
+          bptr[b + 1] = run;
+        }
+        for (int b = 0; b < nblk; ++b) bptr[b + 1] += bptr[b];
+        Sn.ptr.assign(mc_n + 1, 0);
+        for (int r = 0; r < mc_n; ++r) Sn.ptr[r + 1] = Sn.ptr[r] + lowcnt[r] + rowcnt[r];
+        resize_discard(Sn.col, Sn.ptr[mc_n]);
+        resize_discard(Sn.val, Sn.ptr[mc_n]);
+        resize_discard(mirror_tmp, bptr[nblk]);
+#pragma omp parallel for schedule(static)
+        for (int g = 0; g < G; ++g) {
+          int64_t* bo = boff.data() + (size_t)g * nblk;
+          for (int b = 0; b < nblk; ++b) bo[b] += bptr[b];
+          for (int ch = nchunk * g / G; ch < nchunk * (g + 1) / G; ++ch) {
+            const int* col = ucol[ch].data();
+            const double* val = uval[ch].data();
+            int64_t q = 0;
+            for (int r = chunk_row0(ch); r < chunk_row0(ch + 1); ++r) {
+              int64_t o = Sn.ptr[r] + lowcnt[r];
+              double mx = 0.0;  // max |entry| of the row's upper part
+              for (const int64_t e = q + rowcnt[r]; q < e; ++q, ++o) {
+                const int cc = col[q];
+                Sn.col[o] = cc;
+                Sn.val[o] = val[q];
+                mx = std::max(mx, std::fabs(val[q]));
+                if (cc != r) mirror_tmp[bo[cc >> kBlkShift]++] = {r, cc, val[q]};
+              }
+              next_rowmax[r] = mx;
+            }
+          }
+        }
 #pragma omp parallel for schedule(dynamic, 16)
-      for (int b = 0; b < nblk; ++b) {
-        const int c0 = b << kBlkShift, c1 = std::min(mc_n, c0 + (1 << kBlkShift));
-        int64_t next[1 << kBlkShift];  // write position of each column of the block
-        double mx[1 << kBlkShift];     // max |entry| of the column's lower part
-        for (int c = c0; c < c1; ++c) {
-          next[c - c0] = Sn.ptr[c];
-          mx[c - c0] = 0.0;
+        for (int b = 0; b < nblk; ++b) {
+          const int c0 = b << kBlkShift, c1 = std::min(mc_n, c0 + (1 << kBlkShift));
+          int64_t next[1 << kBlkShift];  // write position of each column of the block
+          double mx[1 << kBlkShift];     // max |entry| of the column's lower part
+          for (int c = c0; c < c1; ++c) {
+            next[c - c0] = Sn.ptr[c];
+            mx[c - c0] = 0.0;
+          }
+          for (int64_t t = bptr[b]; t < bptr[b + 1]; ++t) {
+            const Trip& e = mirror_tmp[t];
+            const int64_t slot = next[e.c - c0]++;
+            Sn.col[slot] = e.r;
+            Sn.val[slot] = e.v;
+            mx[e.c - c0] = std::max(mx[e.c - c0], std::fabs(e.v));
+          }
+          // row maxima of S' for the next level's matching (max is exact, so
+          // the same as a pass over the finished rows)
+          for (int c = c0; c < c1; ++c) next_rowmax[c] = std::max(next_rowmax[c], mx[c - c0]);
         }
-        for (int64_t t = bptr[b]; t < bptr[b + 1]; ++t) {
-          const Trip& e = mirror_tmp[t];
-          const int64_t slot = next[e.c - c0]++;
-          Sn.col[slot] = e.r;
-          Sn.val[slot] = e.v;
-          mx[e.c - c0] = std::max(mx[e.c - c0], std::fabs(e.v));
-        }
-        // row maxima of S' for the next level's matching (max is exact, so
-        // the same as a pass over the finished rows)
-        for (int c = c0; c < c1; ++c) next_rowmax[c] = std::max(next_rowmax[c], mx[c - c0]);
       }
     }
     // next level's numbering

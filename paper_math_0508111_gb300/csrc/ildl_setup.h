@@ -77,11 +77,60 @@ struct HostFactor {
   std::vector<int> level_sizes;   // rows eliminated per sparse level
 };
 
+// One level's Schur complement S' = S_CC - L_F D_B L_F^T as the level loop
+// of build_ildl hands it to a SchurEngine (all arrays host, in the loop's
+// local numbering; see the loop for their construction):
+//   cidx[m]         C index of each local row, -1 for the level's pivots;
+//   cnodes[mc_n]    local row of each C row;
+//   rrec[mc_n+1]    records of C row r: rrec[r] .. rrec[r+1], in block order;
+//   rec_blk, rec_slot  per record: its pivot block b and its position in the
+//                   block's column list;
+//   cptr[nblk+1], crow, c1, c2  per block b, its column list cptr[b] ..
+//                   cptr[b+1]: C rows (ascending) with the L_F values of
+//                   the block's nodes a and b (c2 = 0 for a 1x1 block);
+//   bmat[3 nblk]    the symmetric pivot blocks (a, s, c), is2x2[nblk];
+//   tau             drop tolerance of S' (off the diagonal).
+struct SchurLevel {
+  int m = 0, mc_n = 0, nblk = 0;
+  const int* cidx = nullptr;
+  const int* cnodes = nullptr;
+  const int64_t* rrec = nullptr;
+  const int* rec_blk = nullptr;
+  const int64_t* rec_slot = nullptr;
+  const int64_t* cptr = nullptr;
+  const int* crow = nullptr;
+  const double* c1 = nullptr;
+  const double* c2 = nullptr;
+  const double* bmat = nullptr;
+  const char* is2x2 = nullptr;
+  double tau = 0.0;
+};
+
+// Computes the Schur complements of the level loop somewhere other than the
+// host threads (the GPU).  It keeps its own copy of the level matrix S:
+// begin() receives A, scale() the level's scaling d (S_ij *= d_i d_j, the
+// same products as the host's), and schur() returns S' -- full symmetric
+// CSR, rows sorted, bit for bit what the host code computes -- together with
+// the maxima |S'_ij| of its rows, and makes S' its level matrix.
+class SchurEngine {
+ public:
+  virtual ~SchurEngine() = default;
+  virtual int begin(const SymCsr& A) = 0;
+  virtual int scale(const double* d, int m) = 0;
+  virtual int schur(const SchurLevel& lv, SymCsr& Sn, std::vector<double>& rowmax) = 0;
+};
+
+// Default weak-coupling threshold gamma of the independent sets for an
+// order-n matrix: min(0.02, 5/sqrt(n)), or min(0.02, 1/sqrt(n)) for the
+// off-diagonal model.
+double default_gamma(int64_t n, bool offdiag);
+
 // Build the preconditioner of A (symmetric, e.g. A - sigma I).  Returns
 // JD_OK or JD_ESETUP / JD_EINVAL with jd_last_error() set.  With
 // dense_on_host = false the trailing dense block is left un-inverted
 // (dense_is_matrix) for a device-side inversion.
-int build_ildl(const SymCsr& A, const ildl_params& p, HostFactor& F, bool dense_on_host = true);
+int build_ildl(const SymCsr& A, const ildl_params& p, HostFactor& F, bool dense_on_host = true,
+               SchurEngine* engine = nullptr);
 
 // Maximum-product transversal of Section 5.1 (Eqs. (5.1)-(5.2)): on return
 // match_col[j] is the row matched to column j, u and v are the dual

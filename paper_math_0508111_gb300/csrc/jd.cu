@@ -994,7 +994,7 @@ int JdSolver::sqmr_core(int c, double shift, const double* rhs, double sign, dou
     }
   }
   *its = it;
-  AJD_TRY(ildl_check_device_error(pc_));
+  AJD_TRY(ildl_check_device_error(pc_, s_));
   convert_kernel<T, double><<<bl, kThreads, 0, s_>>>(x, xout, n_, 1.0); count_launches();
   AJD_CHECK_LAUNCH();
   return JD_OK;
@@ -1423,11 +1423,15 @@ int JdSolver::finalize(int kc, double* lam, double* evals, double* evecs, jd_sta
     first_index_kernel<<<nb_, kThreads, 0, s_>>>(x, n, amax_, amax_ + 1); count_launches();
     double nn[2];
     AJD_TRY(sync_read(dots_, 2, nn));
+    // readbacks on the solver's stream (never the legacy default stream,
+    // which would serialise the device against concurrent solves)
     unsigned long long key = 0;
-    AJD_CUDA(cudaMemcpy(&key, amax_ + 1, sizeof(key), cudaMemcpyDeviceToHost));
+    AJD_CUDA(cudaMemcpyAsync(host_, amax_ + 1, sizeof(key), cudaMemcpyDeviceToHost, s_));
+    AJD_TRY(wait_stream());
+    std::memcpy(&key, host_, sizeof(key));
     const int64_t imax = (int64_t)key;
     double xv = 0.0;
-    AJD_CUDA(cudaMemcpy(&xv, x + imax, sizeof(double), cudaMemcpyDeviceToHost));
+    AJD_TRY(sync_read(x + imax, 1, &xv));
     const double nrm = std::sqrt(nn[0]);
     max_res = std::max(max_res, std::sqrt(std::max(nn[1], 0.0)) / nrm / normA_);
     signs[j] = (xv < 0 ? -1.0 : 1.0) / nrm;

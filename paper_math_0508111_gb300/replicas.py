@@ -24,6 +24,42 @@ def shard(items, rank, world):
     return list(items[rank::world])
 
 
+def balanced_shard(work, mem, world, mem_budget=None):
+    """Greedy partition of independent problems over `world` ranks by
+    estimated work, under a per-rank device-memory budget.
+
+    work[i], mem[i]: estimated work and device bytes of problem i (for the
+    Anderson eigensolves work grows with the lattice size n = L^3 and mem is
+    the library's jd_server_estimate).  Problems are taken in decreasing
+    work (ties: lower index first) and each goes to the rank with the least
+    work so far (ties: lower rank) among the ranks whose largest problem
+    would still fit mem_budget -- every rank solves its problems one or a
+    few at a time, so the budget bounds the largest problem, not the sum.
+    A problem larger than the budget everywhere raises ValueError.  Returns
+    one ascending index list per rank; together they partition range(len)."""
+    n = len(work)
+    if len(mem) != n:
+        raise ValueError("work and mem must have the same length")
+    if world < 1:
+        raise ValueError("world must be >= 1")
+    load = [0.0] * world
+    out = [[] for _ in range(world)]
+    for i in sorted(range(n), key=lambda j: (-work[j], j)):
+        if mem_budget is not None and mem[i] > mem_budget:
+            raise ValueError("problem %d needs %d bytes, more than the budget %d" % (i, mem[i], mem_budget))
+        r = min(range(world), key=lambda q: (load[q], q))
+        load[r] += work[i]
+        out[r].append(i)
+    return [sorted(o) for o in out]
+
+
+def problem_work(L, k):
+    """Work estimate of one eigensolve on an L^3 lattice with k pairs: the
+    setup and every sweep of the solve are linear in n = L^3, and the
+    number of outer steps grows with k (one locked pair every few steps)."""
+    return float(L) ** 3 * (1.0 + 0.2 * k)
+
+
 def _device(backend):
     return torch.device("cuda", torch.cuda.current_device()) if backend == "nccl" else torch.device("cpu")
 

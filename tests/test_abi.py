@@ -123,3 +123,19 @@ def test_binding_struct_layout_matches_header(tmp_path):
     subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
     got = [int(x) for x in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()]
     assert got == want
+
+
+def test_default_gamma(built_lib):
+    """gamma < 0 selects min(0.02, 5/sqrt(n)), and min(0.02, 1/sqrt(n)) for
+    the off-diagonal model (Section 7): at L = 33 the two defaults are 0.02
+    and 1/sqrt(35937); from L = 40 on the off-diagonal one is five times
+    smaller."""
+    from paper_math_0508111_gb300 import _ffi
+    L = _ffi.lib()
+    g = ctypes.c_double()
+    for n, off, want in [(33 ** 3, 0, 0.02), (33 ** 3, 1, 1 / 35937 ** 0.5), (100 ** 3, 0, 0.005),
+                         (100 ** 3, 1, 0.001), (50 ** 3, 1, 1 / 125000 ** 0.5), (10, 1, 0.02)]:
+        assert L.ildl_default_gamma(n, off, ctypes.byref(g)) == _ffi.JD_OK
+        assert abs(g.value - want) <= 1e-15 * want, (n, off, g.value)
+    assert L.ildl_default_gamma(0, 0, ctypes.byref(g)) == _ffi.JD_EINVAL
+    assert L.ildl_default_gamma(10, 0, None) == _ffi.JD_EINVAL

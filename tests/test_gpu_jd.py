@@ -5,6 +5,7 @@ import pytest
 
 from oracle import eig, lanczos, lattice, matching, rng
 from pairs import check_pairs as _check_pairs
+from pairs import check_pairs_certified
 
 pytestmark = pytest.mark.gpu
 
@@ -18,22 +19,63 @@ def ajd():
     return ajd
 
 
+# Tolerances of the apply against the oracle, relative to max|x|.  The
+# binary32 and mixed applies use the factor's values rounded to binary32
+# (the device copy they read); the oracle applies that same rounded factor
+# in binary64, so what remains is the kernel's own arithmetic: binary64
+# sums, float-float sums (about 48 bits) and binary32 sums (24 bits,
+# with b rounded to binary32 as the kernel receives it).
+TOL_APPLY = {"fp64": 1e-12, "mixed": 1e-11, "fp32": 1e-5}
+# the same kernels against the unrounded binary64 factor: rounding the
+# stored values to binary32 is a small change of the preconditioner
+TOL_APPLY_UNROUNDED = 2e-5
+
+
+def rounded32(F):
+    """The factor with every stored value rounded to binary32 (scale, L, the
+    1x1/2x2 pivot inverses, the dense tail inverse), as on the device."""
+    G = dict(F)
+    for key in ["scale", "Lval", "dinv_d", "dinv_o", "dense_inv"]:
+        G[key] = np.asarray(F[key]).astype(np.float32).astype(np.float64)
+    return G
+
+
+def apply_errors(P, F, b):
+    """Relative max errors of the three device applies against the oracle on
+    the factor each one reads."""
+    want = matching.apply_factor(F, b)
+    F32 = rounded32(F)
+    want_m = matching.apply_factor(F32, b)
+    b32 = b.astype(np.float32)
+    want_32 = matching.apply_factor(F32, b32.astype(np.float64))
+    x64 = P.apply(torch.tensor(b, device="cuda")).cpu().numpy()
+    xm = P.apply(torch.tensor(b, device="cuda"), mixed=True).cpu().numpy()
+    x32 = P.apply(torch.tensor(b32, device="cuda")).double().cpu().numpy()
+    err = {"fp64": np.abs(x64 - want).max() / np.abs(want).max(),
+           "mixed": np.abs(xm - want_m).max() / np.abs(want_m).max(),
+           "fp32": np.abs(x32 - want_32).max() / np.abs(want_32).max(),
+           "mixed_unrounded": np.abs(xm - want).max() / np.abs(want).max(),
+           "fp32_unrounded": np.abs(x32 - want).max() / np.abs(want).max()}
+    assert all(np.isfinite(v) for v in err.values()), err
+    return err
+
+
+def check_apply_errors(err):
+    for key, tol in TOL_APPLY.items():
+        assert err[key] <= tol, (key, err)
+    assert err["mixed_unrounded"] <= TOL_APPLY_UNROUNDED, err
+    assert err["fp32_unrounded"] <= TOL_APPLY_UNROUNDED, err
+
+
 @pytest.mark.parametrize("L,bc,sigma,nd", [(10, 0, 0.0, 1000), (20, 0, 0.3, 1000), (33, 1, -0.5, 300), (16, 0, 1.0, 50)])
 def test_ildl_apply_matches_oracle(ajd, L, bc, sigma, nd):
     """x = K^{-1} b on the GPU equals the plain definition applied by the
-    oracle to the same factor (binary64 and binary32)."""
+    oracle to the same factor (binary64, mixed and binary32)."""
     with ajd.Anderson(L, 16.5, 1, bc) as h:
         P = ajd.Preconditioner.from_lattice(h, sigma, n_dense=nd)
         F = P.export()
         b = np.random.default_rng(0).standard_normal(h.n)
-        want = matching.apply_factor(F, b)
-        scale = np.abs(want).max()
-        x64 = P.apply(torch.tensor(b, device="cuda")).cpu().numpy()
-        assert np.abs(x64 - want).max() <= 1e-12 * scale
-        x32 = P.apply(torch.tensor(b, device="cuda", dtype=torch.float32)).double().cpu().numpy()
-        assert np.abs(x32 - want).max() <= 2e-5 * scale
-        xm = P.apply(torch.tensor(b, device="cuda"), mixed=True).cpu().numpy()
-        assert np.abs(xm - want).max() <= 2e-5 * scale
+        check_apply_errors(apply_errors(P, F, b))
         P.close()
 
 
@@ -46,11 +88,14 @@ def test_ildl_apply_wide_rows(ajd):
         F = P.export()
         assert P.info()["nnz_L"] > 5 * 10 ** 6  # deep rows of several hundred to thousands of entries
         b = np.random.default_rng(3).standard_normal(h.n)
-        want = matching.apply_factor(F, b)
-        scale = np.abs(want).max()
-        for dt, mixed, tol in [(torch.float64, False, 1e-12), (torch.float32, False, 1e-3), (torch.float64, True, 1e-3)]:
-            x = P.apply(torch.tensor(b, device="cuda", dtype=dt), mixed=mixed).double().cpu().numpy()
-            assert np.abs(x - want).max() <= tol * scale, (dt, mixed)
+        err = apply_errors(P, F, b)
+        # without dropping the deep rows are long and the factor's entries
+        # large: rounding the stored values moves K^{-1} b by more than the
+        # default factor's 2e-5, but the kernels' own arithmetic (against
+        # the rounded factor) stays at the usual bounds
+        for key, tol in TOL_APPLY.items():
+            assert err[key] <= tol, (key, err)
+        assert err["mixed_unrounded"] <= 1e-3 and err["fp32_unrounded"] <= 1e-3, err
         P.close()
 
 
@@ -63,13 +108,8 @@ def test_ildl_apply_no_read_before_write(ajd, monkeypatch, L, bc, sigma, nd):
     with ajd.Anderson(L, 12.0, 12, bc) as h:
         P = ajd.Preconditioner.from_lattice(h, sigma, n_dense=nd)
         assert P.info()["levels"] >= 2
-        want = matching.apply_factor(P.export(), np.random.default_rng(0).standard_normal(h.n))
         b = np.random.default_rng(0).standard_normal(h.n)
-        scale = np.abs(want).max()
-        for dt, mixed, tol in [(torch.float64, False, 1e-12), (torch.float32, False, 2e-5), (torch.float64, True, 2e-5)]:
-            x = P.apply(torch.tensor(b, device="cuda", dtype=dt), mixed=mixed).double().cpu().numpy()
-            assert np.isfinite(x).all()
-            assert np.abs(x - want).max() <= tol * scale
+        check_apply_errors(apply_errors(P, P.export(), b))
         P.close()
 
 
@@ -277,6 +317,19 @@ def test_lanczos_matches_dense_oracle(ajd, L, W, seed, bc, sigma, k, prec):
         ev, X, st = ajd.solve(h, sigma, k, tol, precision=prec, method="lanczos", ildl={"n_dense": 300})
     _check_pairs(L, W, seed, bc, sigma, k, ev, X, st, tol)
     assert st["outer_its"] <= 64 and st["inner_its"] > 0
+
+
+@pytest.mark.parametrize("L,W,seed,bc,sigma,k", [(12, 16.5, 8, 0, 1.0, 3), (9, 12.0, 3, 1, -0.5, 4)])
+def test_lanczos_binary32(ajd, L, W, seed, bc, sigma, k):
+    """Shift-and-invert Lanczos with a binary32 inner solve: each operator
+    application (A - sigma I)^{-1} v is only accurate to the binary32 SQMR
+    floor (1e-6 relative), so the pairs reach tol = 1e-5 and no further; the
+    eigenvalues are pinned to the dense oracle by the Kato-Temple bound of
+    each pair's explicit residual."""
+    tol = 1e-5
+    with ajd.Anderson(L, W, seed, bc) as h:
+        ev, X, st = ajd.solve(h, sigma, k, tol, precision=ajd.JD_FP32, method="lanczos", ildl={"n_dense": 300})
+    check_pairs_certified(L, W, seed, bc, sigma, k, ev, X, st, tol)
 
 
 def test_lanczos_agrees_with_jd_mid_size(ajd):

@@ -70,3 +70,23 @@ def test_offdiag_jd_matches_dense_oracle(ajd, L, bc, sigma, k, prec):
         res = np.linalg.norm(A @ X[:, j] - ev[j] * X[:, j])
         sin = np.sqrt(max(0.0, 1 - min(1.0, abs(X[:, j] @ Vk[:, j])) ** 2))
         assert sin <= max(1e-6, 2 * res / gaps.min())
+
+
+def test_offdiag_default_gamma_factor(ajd):
+    """gamma < 0 on a lattice of the off-diagonal model selects
+    min(0.02, 1/sqrt(n)): the default factor equals the one built with that
+    threshold given explicitly, entry for entry (L = 24: 0.0085, not the
+    diagonal model's 0.02)."""
+    L = 24
+    with ajd.Anderson.offdiag(L, 5, diag=1.28, width=1.0) as h:
+        n = L ** 3
+        P0 = ajd.Preconditioner.from_lattice(h, 0.0)
+        P1 = ajd.Preconditioner.from_lattice(h, 0.0, gamma=min(0.02, 1.0 / np.sqrt(n)))
+        P2 = ajd.Preconditioner.from_lattice(h, 0.0, gamma=0.02)
+        F0, F1, F2 = P0.export(), P1.export(), P2.export()
+        for key in ["perm", "scale", "level_ptr", "Lptr", "Lcol", "Lval", "dinv_d", "dinv_o", "partner",
+                    "dense_inv"]:
+            assert np.array_equal(F0[key], F1[key]), key
+        assert F0["levels"] != F2["levels"] or F0["nnz_L"] != F2["nnz_L"]
+        for P in (P0, P1, P2):
+            P.close()

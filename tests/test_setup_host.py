@@ -61,6 +61,22 @@ def test_factor_structure(ajd):
     assert np.allclose(Dn, Dn.T)
 
 
+def test_default_gamma_factor(ajd):
+    """gamma < 0 selects min(0.02, 5/sqrt(n)) for a general symmetric matrix:
+    the default factor equals the one built with that value given
+    explicitly, array for array (L = 15: 5/sqrt(3375) = 0.086, capped at
+    0.02; L = 40: 5/sqrt(64000) = 0.0198)."""
+    for L in (15, 40):
+        A, _ = _csr(L, 16.5, 3, PERIODIC, 0.0)
+        n = A.shape[0]
+        F0 = ajd.Preconditioner.from_csr(A.indptr, A.indices, A.data, n_dense=300).export()
+        F1 = ajd.Preconditioner.from_csr(A.indptr, A.indices, A.data, n_dense=300,
+                                         gamma=min(0.02, 5.0 / np.sqrt(n))).export()
+        for key in ["perm", "scale", "level_ptr", "Lptr", "Lcol", "Lval", "dinv_d", "dinv_o", "partner",
+                    "dense_inv"]:
+            assert np.array_equal(F0[key], F1[key]), (L, key)
+
+
 def test_preconditioner_quality_default(ajd):
     """Default parameters: SQMR (oracle) preconditioned by the library's K
     solves (A - sigma I) x = b at L = 12 in few iterations, versus
