@@ -201,8 +201,7 @@ def run_requests(ajd, args, precision, reqs, slots, setup_threads):
     """Submit each request to a jd_server at its arrival time ("t", seconds
     from the start) and poll until all are done.  Returns eigenpairs/s over
     the whole run and the latency percentiles (submission to completion)."""
-    import numpy as np
-    lat, pairs, failed = [], 0, 0
+    lat, pairs, failed, per = [], 0, 0, []
     with ajd.Server(slots=slots, setup_threads=setup_threads, precision=precision) as srv:
         start = time.perf_counter()
         pending, i = {}, 0
@@ -210,20 +209,25 @@ def run_requests(ajd, args, precision, reqs, slots, setup_threads):
             now = time.perf_counter() - start
             while i < len(reqs) and reqs[i]["t"] <= now:
                 r = reqs[i]
-                pending[srv.submit(r["L"], r["W"], r["seed"], r["sigma"], r["k"], args.tol, bc=r["bc"])] = r["k"]
+                pending[srv.submit(r["L"], r["W"], r["seed"], r["sigma"], r["k"], args.tol, bc=r["bc"])] = r
                 i += 1
             for tk in list(pending):
                 out = srv.poll(tk, raise_on_error=False)
                 if out is not None:
-                    st = out[2]
+                    st, r = out[2], pending.pop(tk)
                     lat.append(st["latency_ms"])
                     pairs += st["nconv"]
                     failed += st["status"] not in (0, ajd.JD_ENOCONV)
-                    del pending[tk]
+                    per.append([r["L"], round(r["W"], 2), round(r["sigma"], 3), r["k"], round(st["latency_ms"]),
+                                round(st["setup_ms"]), round(st["solve_ms"]), st["outer_its"], st["inner_its"],
+                                st["nconv"]])
             time.sleep(0.002)
         elapsed = time.perf_counter() - start
         info = srv.info()
-    return summarize_requests(lat, pairs, failed, elapsed, info["peak_solving"], slots, setup_threads)
+    out = summarize_requests(lat, pairs, failed, elapsed, info["peak_solving"], slots, setup_threads)
+    out["per_request"] = {"fields": ["L", "W", "sigma", "k", "latency_ms", "setup_ms", "solve_ms", "outer", "inner",
+                                     "nconv"], "rows": per}
+    return out
 
 
 def summarize_requests(lat, pairs, failed, elapsed, peak, slots, setup_threads):

@@ -188,6 +188,12 @@ typedef struct {
                      as soon as the block is computed, so the Schur
                      complement is formed from the sparsified block.
                      0 = off, else 0 < tau < 1 (the paper suggests 0.1) [0] */
+  int setup_device; /* where the levels' Schur complements S' = S_CC -
+                     L_F D_B L_F^T (Section 6.3) are formed: 1 = on the GPU
+                     (the lattice's device for ildl_create, the current
+                     device for ildl_setup_csr), 0 = on the host threads,
+                     < 0 = GPU for ildl_create and host for ildl_setup_csr.
+                     Both give the same factor bit for bit [-1]         */
 } ildl_params;
 
 /* Fill *p with the defaults above. */
@@ -289,13 +295,15 @@ int ildl_apply(ildl_t f, const void* b, void* x, int precision, void* stream);
  * allocate device memory during the call (a fixed memory pool reserved up
  * front, an embedding runtime that owns all device memory).  The paper has no
  * counterpart: this is a deployment variant.
- * It runs the same kernel but takes its scratch (two work vectors and the
- * status word of its waits) from one static device array compiled into the
- * library (2 MiB + 512 bytes, held by every GPU that loads the library until
- * the process exits) instead of the factor's buffers; it calls no cudaMalloc,
- * cudaFree or allocating library routine.
+ * It runs the same kernel but takes its scratch (two work vectors, the
+ * status word of its waits and the completion counters of its phases) from
+ * one static device array compiled into the library (2 MiB + 16.5 KiB, held
+ * by every GPU that loads the library until the process exits) instead of
+ * the factor's buffers; it calls no cudaMalloc, cudaFree or allocating
+ * library routine.
  *   f          a factor from ildl_create with at most 131072 rows (n = L^3,
- *              L <= 50); larger orders are rejected with JD_EINVAL.  The
+ *              L <= 50) and at most 4096 apply phases (two per sparse
+ *              level); larger factors are rejected with JD_EINVAL.  The
  *              factor's device must be the current device (JD_EINVAL
  *              otherwise).
  *   b, x       device pointers as for ildl_apply; precision JD_FP64,
@@ -352,7 +360,26 @@ typedef struct {
   ildl_t precond;     /* optional prebuilt preconditioner of A - sigma I
                          (from ildl_create with the same sigma); NULL = build
                          one inside the call and time it as setup           */
+  int gram;           /* first pass of the block Gram-Schmidt that extends
+                         the search space (Section 4.2): 1 = binary64 (both
+                         passes binary64), 2 = BF16 operands on the tensor
+                         cores with FP32 accumulation (second pass
+                         binary64); 0 = 2 for JD_MIXED and JD_FP32, 1 for
+                         JD_FP64 [0]                                         */
 } jd_params;
+
+/* jd_gram_bf16 -- out = BF16(X)^T BF16(t): the first pass of the block
+ * Gram-Schmidt of the search-space expansion (Section 4.2) on the tensor
+ * cores (tcgen05.mma, BF16 operands, FP32 accumulation per 64-row chunk and
+ * CTA, binary64 sum over CTAs), as jd_solve runs it with gram = 2.
+ *   X      device, n x c column-major binary64, leading dimension ldx >= n;
+ *          c <= 128 columns
+ *   t      device, n binary64
+ *   out    c binary64 (host or device pointer)
+ * Allocates and frees its own BF16 copy of X (c x n x 2 bytes).  JD_EINVAL
+ * for bad sizes, JD_EDEVICE on a CUDA error or a tensor-core wait that timed
+ * out. */
+int jd_gram_bf16(const double* X, int64_t ldx, int c, const double* t, int64_t n, double* out, void* stream);
 
 /* Counters of one solve (the observables of Tables 3-5). */
 typedef struct {
@@ -371,6 +398,8 @@ typedef struct {
   double precond_ms;   /* their device time (CUDA events on the stream)      */
   int stencil_calls;   /* inner-solve stencil applications                   */
   double stencil_ms;   /* their device time                                  */
+  double basis_orth_error; /* max |V^T V - I| over the final search space
+                              (jd_solve; 0 for jd_lanczos_solve)             */
 } jd_stats;
 
 /* Fill *p with the defaults (all fields zero except ildl = ildl defaults). */

@@ -32,7 +32,7 @@ class JDError(RuntimeError):
 
 class IldlParams(ctypes.Structure):
     _fields_ = [("kappa", c_double), ("drop", c_double), ("gamma", c_double), ("max_levels", c_int),
-                ("n_dense", c_int), ("matching", c_int), ("aggressive", c_double)]
+                ("n_dense", c_int), ("matching", c_int), ("aggressive", c_double), ("setup_device", c_int)]
 
 
 class IldlInfo(ctypes.Structure):
@@ -45,14 +45,15 @@ class JdParams(ctypes.Structure):
     _fields_ = [("jmin", c_int), ("jmax", c_int), ("max_outer", c_int), ("max_inner", c_int),
                 ("inner_decay", c_double), ("inner_floor", c_double), ("switch_tol", c_double),
                 ("precision", c_int), ("seed", c_uint64), ("extraction", c_int), ("guard", c_int), ("ildl", IldlParams),
-                ("precond", c_void_p)]
+                ("precond", c_void_p), ("gram", c_int)]
 
 
 class JdStats(ctypes.Structure):
     _fields_ = [("nconv", c_int), ("outer_its", c_int), ("inner_its", c_int), ("restarts", c_int),
                 ("setup_ms", c_double), ("solve_ms", c_double), ("max_residual", c_double),
                 ("orth_error", c_double), ("ildl", IldlInfo), ("kernel_launches", c_int64),
-                ("precond_calls", c_int), ("precond_ms", c_double), ("stencil_calls", c_int), ("stencil_ms", c_double)]
+                ("precond_calls", c_int), ("precond_ms", c_double), ("stencil_calls", c_int), ("stencil_ms", c_double),
+                ("basis_orth_error", c_double)]
 
 
 class JdServerParams(ctypes.Structure):
@@ -92,6 +93,7 @@ SIGNATURES = [
     ("jd_params_default", c_int, [P(JdParams)]),
     ("jd_solve", c_int, [c_void_p, c_double, c_int, c_double, P(JdParams), c_void_p, c_void_p, P(JdStats),
                          c_void_p]),
+    ("jd_gram_bf16", c_int, [c_void_p, c_int64, c_int, c_void_p, c_int64, c_void_p, c_void_p]),
     ("jd_lanczos_solve", c_int, [c_void_p, c_double, c_int, c_double, P(JdParams), c_void_p, c_void_p, P(JdStats),
                                  c_void_p]),
     ("jd_server_params_default", c_int, [P(JdServerParams)]),

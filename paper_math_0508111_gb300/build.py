@@ -21,7 +21,10 @@ BUILD = os.path.join(ROOT, "_build", "libanderson_jd")
 LIB = os.path.join(PKG, "libanderson_jd.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O3,-fopenmp",
+# host code: no contraction of a*b + c into fused multiply-adds (GCC's
+# default for C++ on Arm), so that the host setup gives the same bits on
+# every machine and the GPU engine of the setup reproduces them
+COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O3,-fopenmp,-ffp-contract=off",
           "-I", INCLUDE, "-I", CSRC, "--expt-relaxed-constexpr"]
 
 

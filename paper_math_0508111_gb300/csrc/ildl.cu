@@ -14,6 +14,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <memory>
 #include <mutex>
 #include <new>
 #include <cstdio>
@@ -25,6 +26,7 @@
 #include "jd_impl.cuh"
 #include "ildl_setup.h"
 #include "ildl_apply_kernel.cuh"
+#include "schur_gpu.h"
 
 namespace ajd {
 namespace {
@@ -147,6 +149,7 @@ void free_dev(DevFactor<T>& d) {
   cudaFree(d.z);
   cudaFree(d.phases);
   cudaFree(d.bar);
+  cudaFree(d.done);
   cudaFree(d.wdf);
   cudaFree(d.zdf);
   d = DevFactor<T>();
@@ -227,13 +230,15 @@ int upload_factor(const HostFactor& F, DevFactor<T>& d, cudaStream_t st) {
   // loads in flight by then; the first CTA goes in the high half of .w
   const int grid = sm_count();
   int cursor = 0;
+  // the CTAs that own rows of a phase (its participants, which signal its
+  // completion) go in the high bits of .x
   auto add_phase = [&](int kind, int p0, int p1, int g) {
     const int64_t threads = (int64_t)(p1 - p0) * (kind == PH_DENSE ? 32 : g);
     const int ctas = (int)std::min<int64_t>(grid, (threads + kPersistThreads - 1) / kPersistThreads);
-    ph.push_back(make_int4(kind, p0, p1, g | (cursor << 16)));
+    ph.push_back(make_int4(kind | (ctas << 8), p0, p1, g | (cursor << 16)));
     cursor = (cursor + ctas) % grid;
   };
-  ph.push_back(make_int4(PH_GATHER, lvp[0], lvp[1], 1));
+  add_phase(PH_GATHER, lvp[0], lvp[1], 1);
   for (int l = 1; l <= nl; ++l) {
     const int p0 = lvp[l], p1 = lvp[l + 1];
     if (p1 <= p0) continue;
@@ -254,8 +259,9 @@ int upload_factor(const HostFactor& F, DevFactor<T>& d, cudaStream_t st) {
     AJD_CUDA(cudaStreamSynchronize(st));
   }
   // status words: [64] the timeout flag of the apply's waits (its own
-  // 128-byte line)
+  // 128-byte line); completion counters of the phases
   AJD_CUDA(cudaMalloc(&d.bar, 96 * sizeof(unsigned)));
+  AJD_CUDA(cudaMalloc(&d.done, std::max<size_t>(1, ph.size()) * sizeof(unsigned)));
   AJD_CUDA(cudaMemsetAsync(d.bar, 0, 96 * sizeof(unsigned), st));
   AJD_CUDA(cudaStreamSynchronize(st));
   int per_sm = 0;
@@ -282,19 +288,18 @@ int launch_apply(const ildl_s* f, const DevFactor<V>& d, X* w, X* z, const IO* b
   if (F.n == 0 || d.nphase == 0) return JD_OK;
   ApplyArgs<V, X, IO> a{d.perm, d.scale, d.Lptr, d.Lcol, d.Lval, d.Uptr, d.Ucol, d.Uval, d.dd, d.dof, d.partner,
                         d.dense, w, z, b, out, F.n_dense, F.level_ptr[F.nlev]};
-  // every solution entry starts as the sentinel (all ones) that the
-  // kernel's readers poll on
-  AJD_CUDA(cudaMemsetAsync(w, 0xFF, (size_t)F.n * sizeof(X), s));
-  AJD_CUDA(cudaMemsetAsync(z, 0xFF, (size_t)F.n * sizeof(X), s));
+  // the phases' completion counters start at zero
+  AJD_CUDA(cudaMemsetAsync(d.done, 0, (size_t)d.nphase * sizeof(unsigned), s));
   const int4* ph = d.phases;
   int np = d.nphase;
+  unsigned* done = d.done;
   int* err = reinterpret_cast<int*>(d.bar + 64);
   // AJD_APPLY_TIMING=1: record the start of every phase (globaltimer, CTA 0)
   // and print a per-kind summary of the next apply to stderr (diagnostics)
   static const bool timing = std::getenv("AJD_APPLY_TIMING") != nullptr;
   unsigned long long* stamps = nullptr;
   if (timing) AJD_CUDA(cudaMalloc(&stamps, (np + 1) * sizeof(unsigned long long)));
-  void* args[] = {&a, &ph, &np, &err, &stamps};
+  void* args[] = {&a, &ph, &np, &done, &err, &stamps};
   if (tl_serialize_applies) {
     // concurrent solvers: this apply starts on the device only after the
     // previous serialised apply (of any thread) has finished, so no two of
@@ -312,7 +317,7 @@ int launch_apply(const ildl_s* f, const DevFactor<V>& d, X* w, X* z, const IO* b
     AJD_CUDA(cudaLaunchCooperativeKernel((void*)ildl_apply_persistent_kernel<V, X, IO>, dim3(d.grid),
                                          dim3(kPersistThreads), args, 0, s));
   }
-  count_launches(3);
+  count_launches(2);
   if (timing) {
     std::vector<unsigned long long> t(np + 1);
     std::vector<int4> phs(np);
@@ -324,11 +329,11 @@ int launch_apply(const ildl_s* f, const DevFactor<V>& d, X* w, X* z, const IO* b
     int kind_n[4] = {0, 0, 0, 0};
     for (int i = 0; i < np; ++i) {
       const double us = (t[i + 1] - t[i]) * 1e-3;
-      kind_us[phs[i].x] += us;
-      kind_n[phs[i].x]++;
+      kind_us[phs[i].x & 0xFF] += us;
+      kind_n[phs[i].x & 0xFF]++;
       if (std::getenv("AJD_APPLY_TIMING_ALL"))
-        std::fprintf(stderr, "phase %d kind %d rows %d G %d cta %d: %.2f us\n", i, phs[i].x, phs[i].z - phs[i].y,
-                     phs[i].w & 0xFFFF, phs[i].w >> 16, us);
+        std::fprintf(stderr, "phase %d kind %d rows %d G %d cta %d ctas %d: %.2f us\n", i, phs[i].x & 0xFF,
+                     phs[i].z - phs[i].y, phs[i].w & 0xFFFF, phs[i].w >> 16, phs[i].x >> 8, us);
     }
     std::fprintf(stderr, "apply %.1f us: gather %.1f (%d) fwd %.1f (%d) dense %.1f (%d) bwd %.1f (%d)\n",
                  (t[np] - t[0]) * 1e-3, kind_us[0], kind_n[0], kind_us[1], kind_n[1], kind_us[2], kind_n[2], kind_us[3],
@@ -489,6 +494,7 @@ extern "C" int ildl_params_default(ildl_params* p) {
   p->n_dense = 0;
   p->matching = -1;
   p->aggressive = 0.0;
+  p->setup_device = -1;
   return JD_OK;
 }
 
@@ -546,7 +552,9 @@ extern "C" int ildl_setup_csr(int n, const int64_t* rowptr, const int* col, cons
       B.ptr[i + 1] = (int64_t)B.col.size();
     }
     ildl_s* f = new ildl_s();
-    int rc = build_ildl(B, prm, f->F);
+    std::unique_ptr<SchurEngine> eng;
+    if (prm.setup_device > 0) eng = make_device_schur(0);
+    int rc = build_ildl(B, prm, f->F, true, eng.get());
     if (rc != JD_OK) {
       delete f;
       return rc;
@@ -619,7 +627,12 @@ int ildl_create_on_stream(anderson_t h, double sigma, const ildl_params* p, ildl
     ildl_s* f = new ildl_s();
     f->device = h->device;
     const auto t0 = std::chrono::steady_clock::now();
-    int rc = build_ildl(A, prm, f->F, /*dense_on_host=*/false);
+    // the levels' Schur complements on the lattice's device unless asked
+    // for on the host
+    std::unique_ptr<SchurEngine> eng;
+    if (prm.setup_device != 0) eng = make_device_schur(st);
+    int rc = build_ildl(A, prm, f->F, /*dense_on_host=*/false, eng.get());
+    eng.reset();
     if (rc == JD_OK) rc = ildl_upload_all(f, st, copies);
     f->F.t_total_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     if (rc != JD_OK) {
@@ -716,8 +729,10 @@ extern "C" int ildl_destroy(ildl_t f) {
 namespace {
 
 constexpr int64_t kNoAllocMaxN = 131072;  // largest order served (L <= 50 lattices)
+constexpr int kNoAllocMaxPhases = 4096;   // phase counters (2 per sparse level + 2 per factor)
 constexpr size_t kNoAllocVecBytes = (size_t)kNoAllocMaxN * sizeof(double);
-constexpr size_t kNoAllocBytes = 2 * kNoAllocVecBytes + 512;  // w, z, status words
+// w, z, status words, phase counters
+constexpr size_t kNoAllocBytes = 2 * kNoAllocVecBytes + 512 + kNoAllocMaxPhases * sizeof(unsigned);
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
@@ -758,16 +773,16 @@ int launch_apply_static(const ildl_s* f, const DevFactor<V>& d, const IO* b, IO*
   unsigned* bar = reinterpret_cast<unsigned*>(scratch + 2 * kNoAllocVecBytes);
   ApplyArgs<V, X, IO> a{d.perm, d.scale, d.Lptr, d.Lcol, d.Lval, d.Uptr, d.Ucol, d.Uval, d.dd, d.dof, d.partner,
                         d.dense, w, z, b, out, F.n_dense, F.level_ptr[F.nlev]};
-  // the array keeps the previous call's contents: the timeout flag must start
-  // at zero, and every entry of w and z as the sentinel the kernel polls on
-  AJD_CUDA(cudaMemsetAsync(bar, 0, 96 * sizeof(unsigned), s));
-  AJD_CUDA(cudaMemsetAsync(w, 0xFF, (size_t)F.n * sizeof(X), s));
-  AJD_CUDA(cudaMemsetAsync(z, 0xFF, (size_t)F.n * sizeof(X), s));
+  // the array keeps the previous call's contents: the timeout flag and the
+  // phase counters (behind the status words) must start at zero; w and z
+  // are written before they are read
+  unsigned* done = bar + 128;
+  AJD_CUDA(cudaMemsetAsync(bar, 0, 128 * sizeof(unsigned) + (size_t)d.nphase * sizeof(unsigned), s));
   const int4* ph = d.phases;
   int np = d.nphase;
   int* err = reinterpret_cast<int*>(bar + 64);
   unsigned long long* stamps = nullptr;
-  void* args[] = {&a, &ph, &np, &err, &stamps};
+  void* args[] = {&a, &ph, &np, &done, &err, &stamps};
   {
     // ordered behind the applies of concurrent served solves (the same
     // event chain), so this grid-wide kernel never runs beside one of them
@@ -781,7 +796,7 @@ int launch_apply_static(const ildl_s* f, const DevFactor<V>& d, const IO* b, IO*
     if (g_chain_last) cudaEventDestroy(g_chain_last);
     g_chain_last = ev;
   }
-  count_launches(4);
+  count_launches(2);
   int herr = 0;
   AJD_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
   AJD_CUDA(cudaStreamSynchronize(s));
@@ -797,6 +812,10 @@ extern "C" int ildl_apply_noalloc(ildl_t f, const void* b, void* x, int precisio
   if ((int64_t)f->F.n > kNoAllocMaxN)
     return fail(JD_EINVAL, "ildl_apply_noalloc: order %d exceeds the static scratch limit of %lld rows", f->F.n,
                 (long long)kNoAllocMaxN);
+  const int nphase = std::max(f->d64.nphase, f->d32.nphase);
+  if (nphase > kNoAllocMaxPhases)
+    return fail(JD_EINVAL, "ildl_apply_noalloc: %d phases exceed the static scratch limit of %d", nphase,
+                kNoAllocMaxPhases);
   // the scratch array looked up below is the current device's; the
   // factor's arrays live on f->device
   int cur = 0;

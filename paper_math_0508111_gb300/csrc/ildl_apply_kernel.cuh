@@ -3,23 +3,25 @@
 // own file so that measurements of this kernel can be tied to its source
 // (bench.py keys recorded DRAM counters to this file's hash).
 //
-// Synchronisation-free level scheduling.  The positions are ordered level by
-// level; a row of the forward sweep reads only solution entries of earlier
-// levels, a row of the backward sweep only entries of later levels.  Instead
-// of a grid-wide barrier between levels, every solution entry of w (forward)
-// and z (backward) starts as a sentinel bit pattern (all ones: a NaN no
-// arithmetic produces), written by the host before the launch, and each
-// row's final value is published with one single-copy-atomic relaxed store.
-// A row that needs an entry loads it with a relaxed (L2-coherent) load and
-// polls while it still reads the sentinel.  So a row waits only for the rows
-// it actually depends on, the index and value loads of a level are issued
-// before its dependencies are ready, and consecutive levels overlap.  Every
-// thread walks the levels in order and all CTAs are resident (cooperative
-// launch, one CTA per SM), so every wait ends: the rows of level 0 depend on
-// nothing, and a row of level l waits only on rows of levels < l, whose
-// threads never wait on level l.  The waits are bounded anyway: after
-// kSpinLimit polls a thread records a timeout in `err`, stops waiting and
-// the apply returns garbage that the host reports as JD_EDEVICE.
+// Level scheduling with per-phase completion counters.  The positions are
+// ordered level by level; a row of the forward sweep reads only solution
+// entries of earlier levels, a row of the backward sweep only entries of
+// later levels (and its own forward value).  The phase list (level 0, the
+// forward levels, the dense tail, the backward levels) is walked in order by
+// every CTA, but only the CTAs that own rows of a phase take part in it:
+// each of them, once its rows are written, adds one to the phase's counter
+// (release), and a CTA about to compute a phase first waits (one thread,
+// acquire polls) until every earlier phase's counter has reached its number
+// of participants.  The loads of the phase's row pointers, indices and
+// values are issued before that wait, so they are in flight while the
+// previous level is still being computed; only the gathers of solution
+// entries follow it.  Consecutive phases start on different CTAs (the
+// first CTA of each phase rotates round the grid), so the CTAs of a small
+// phase are idle, with their loads issued, when the level before completes.
+// All CTAs are resident (cooperative launch, one CTA per SM) and a phase
+// waits only on earlier phases, so every wait ends; the waits are bounded
+// anyway: after kSpinLimit polls the thread records a timeout in `err` and
+// its CTA returns (the host reports JD_EDEVICE).
 #pragma once
 #include "ildl_impl.cuh"
 
@@ -27,10 +29,12 @@ namespace ajd {
 namespace {
 
 // Phase kinds: level 0 (no dependencies), forward level, dense trailing
-// block, backward level.  Threads walk the phase list in order.
+// block, backward level.  A phase descriptor is the int4
+// (kind | participating CTAs << 8, first row, end row, threads per row |
+// first CTA << 16).
 enum { PH_GATHER = 0, PH_FWD = 1, PH_DENSE = 2, PH_BWD = 3 };
 constexpr int kPersistThreads = 512;
-constexpr unsigned kSpinLimit = 1u << 20;  // polls per thread and apply (~0.5-1 s)
+constexpr unsigned kSpinLimit = 1u << 22;  // polls of one wait (~0.2-1 s)
 
 // V: type of the stored factor values; X: type of the work vectors and of
 // the sums; IO: type of the caller's b and x.  binary64 apply: V = X = IO =
@@ -156,115 +160,20 @@ __device__ __forceinline__ double to_io<double, df64>(df64 v) {
   return (double)v.hi + (double)v.lo;
 }
 
-// ---- publication and polling of solution entries ----
-// Bits of one work-vector entry (8 bytes for binary64 and float-float,
-// 4 for binary32); the sentinel is all ones.  Stores and loads are relaxed
-// at GPU scope and of the entry's full width, so a reader sees either the
-// sentinel or the final value, never a mix, and never a stale L1 copy.
 template <typename X>
-struct Bits {
-  using type = unsigned long long;
-};
-template <>
-struct Bits<float> {
-  using type = unsigned;
-};
-
-__device__ __forceinline__ unsigned long long ld_relaxed(const unsigned long long* p) {
-  unsigned long long v;
-  asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p));
-  return v;
+__device__ __forceinline__ X ldx(const X* p) {
+  return __ldcg(p);
 }
-__device__ __forceinline__ unsigned ld_relaxed(const unsigned* p) {
-  unsigned v;
-  asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p));
-  return v;
-}
-__device__ __forceinline__ void st_relaxed(unsigned long long* p, unsigned long long v) {
-  asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
-__device__ __forceinline__ void st_relaxed(unsigned* p, unsigned v) {
-  asm volatile("st.relaxed.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
-template <typename X>
-__device__ __forceinline__ typename Bits<X>::type to_bits(X v) {
-  typename Bits<X>::type b;
-  memcpy(&b, &v, sizeof(b));
-  return b;
+__device__ __forceinline__ df64 ldx(const df64* p) {
+  const float2 v = __ldcg(reinterpret_cast<const float2*>(p));
+  return df64{v.x, v.y};
 }
 template <typename X>
-__device__ __forceinline__ X from_bits(typename Bits<X>::type b) {
-  X v;
-  memcpy(&v, &b, sizeof(b));
-  return v;
+__device__ __forceinline__ void stx(X* p, X v) {
+  __stcg(p, v);
 }
-template <typename B>
-__device__ __forceinline__ bool is_sentinel(B b) {
-  return b == ~B(0);
-}
-
-// Per-thread wait state: polls spent so far in this apply, and whether a
-// wait has given up (then no further wait is attempted).
-struct Waiter {
-  unsigned spins;
-  bool dead;
-  int* err;
-};
-
-// Poll entry p until it holds a published value (bounded).
-template <typename X>
-__device__ __noinline__ typename Bits<X>::type wait_bits(const X* p, Waiter& wt) {
-  using B = typename Bits<X>::type;
-  const B* q = reinterpret_cast<const B*>(p);
-  B b = ld_relaxed(q);
-  while (is_sentinel(b) && !wt.dead) {
-    ++wt.spins;
-    if ((wt.spins & 255u) == 0 && *((volatile int*)wt.err)) {
-      wt.dead = true;
-      break;
-    }
-    if (wt.spins > kSpinLimit) {
-      atomicExch(wt.err, 1);
-      wt.dead = true;
-      break;
-    }
-    __nanosleep(20);
-    b = ld_relaxed(q);
-  }
-  return is_sentinel(b) ? B(0) : b;
-}
-
-// Load entry p of a work vector: one relaxed load, polling only while the
-// entry is not yet published.
-template <typename X>
-__device__ __forceinline__ X take(const X* p, Waiter& wt) {
-  using B = typename Bits<X>::type;
-  B b = ld_relaxed(reinterpret_cast<const B*>(p));
-  if (is_sentinel(b)) b = wait_bits(p, wt);
-  return from_bits<X>(b);
-}
-
-// Gathers of N entries x[c[i]] (c[i] < 0: none, value 0): all N loads are
-// issued before the first is inspected, so their latencies overlap; only
-// entries still unpublished are then polled.
-template <typename X, int N>
-__device__ __forceinline__ void gather(const X* x, const int (&c)[N], X (&out)[N], Waiter& wt) {
-  using B = typename Bits<X>::type;
-  B r[N];
-#pragma unroll
-  for (int i = 0; i < N; ++i) r[i] = c[i] >= 0 ? ld_relaxed(reinterpret_cast<const B*>(x + c[i])) : B(0);
-#pragma unroll
-  for (int i = 0; i < N; ++i)
-    if (is_sentinel(r[i])) r[i] = wait_bits(x + c[i], wt);
-#pragma unroll
-  for (int i = 0; i < N; ++i) out[i] = from_bits<X>(r[i]);
-}
-
-template <typename X>
-__device__ __forceinline__ void publish(X* p, X v) {
-  using B = typename Bits<X>::type;
-  st_relaxed(reinterpret_cast<B*>(p), to_bits(v));
+__device__ __forceinline__ void stx(df64* p, df64 v) {
+  __stcg(reinterpret_cast<float2*>(p), make_float2(v.hi, v.lo));
 }
 
 template <typename V, typename X, typename IO = X>
@@ -281,16 +190,67 @@ struct ApplyArgs {
   const V* dof;
   const int* partner;
   const V* dense;
-  X* w;  // forward solution, sentinel-filled before the launch
-  X* z;  // backward solution, sentinel-filled before the launch
+  X* w;  // forward solution
+  X* z;  // backward solution
   const IO* b;
   IO* out;
   int nd, d0;
 };
 
-// Row operands loaded before the row's entries (their latency overlaps the
-// gathers): forward -- the right-hand side s[p] b[perm[p]]; backward -- the
-// 2x2 partner and the permutation entry.
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Completion bookkeeping of one CTA: counters of the phases, the number of
+// phases this CTA knows to be complete (all phases < known), the timeout
+// flag.  wait() is called by every thread of the CTA at the same point.
+struct Progress {
+  const int4* phases;
+  unsigned* done;
+  int* err;
+  int* known;   // shared
+  int* failed;  // shared
+
+  // every phase < ph complete; false after a timeout
+  __device__ __forceinline__ bool wait(int ph) {
+    if (threadIdx.x == 0) {
+      int r = *known;
+      while (r < ph && !*failed) {
+        const unsigned need = (unsigned)(phases[r].x >> 8);
+        unsigned spins = 0;
+        while (ld_acquire_u32(done + r) < need) {
+          ++spins;
+          if ((spins & 1023u) == 0 && *((volatile int*)err)) { *failed = 1; break; }
+          if (spins > kSpinLimit) {
+            atomicExch(err, 1);
+            *failed = 1;
+            break;
+          }
+          if (spins > 32) __nanosleep(32);
+        }
+        ++r;
+      }
+      *known = r;
+    }
+    __syncthreads();
+    return *failed == 0;
+  }
+
+  // this CTA's rows of phase ph are written
+  __device__ __forceinline__ void arrive(int ph) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(done + ph) : "memory");
+    }
+  }
+};
+
+// Row operands loaded before the row's entries: forward -- the right-hand
+// side s[p] b[perm[p]]; backward -- the 2x2 partner and the permutation
+// entry.
 template <typename V, typename X, typename IO>
 struct RowHead {
   X rhs;
@@ -311,35 +271,40 @@ __device__ __forceinline__ RowHead<V, X, IO> row_head(const ApplyArgs<V, X, IO>&
 // the solution entries it depends on.
 template <typename V, typename X, typename IO>
 __device__ __forceinline__ void finish_value(const ApplyArgs<V, X, IO>& a, int kind, int p, X acc,
-                                             const RowHead<V, X, IO>& h, Waiter& wt) {
+                                             const RowHead<V, X, IO>& h) {
   using W = typename ValueReg<V, X>::type;
   if (kind == PH_FWD) {
-    publish(a.w + p, sub(h.rhs, acc));
+    stx(a.w + p, sub(h.rhs, acc));
   } else {
-    X d = mul(ldw<W>(a.dd + p), take(a.w + p, wt));
-    if (h.pp >= 0) d = add(d, mul(ldw<W>(a.dof + p), take(a.w + h.pp, wt)));
+    X d = mul(ldw<W>(a.dd + p), ldx(a.w + p));
+    if (h.pp >= 0) d = add(d, mul(ldw<W>(a.dof + p), ldx(a.w + h.pp)));
     const X zp = sub(d, acc);
-    publish(a.z + p, zp);
+    stx(a.z + p, zp);
     a.out[h.perm] = to_io<IO>(mul(ldw<W>(a.scale + p), zp));
   }
 }
 
 template <typename V, typename X, typename IO, int G>
 __device__ __forceinline__ void finish_row(const ApplyArgs<V, X, IO>& a, int kind, int p, X acc, int lane,
-                                           const RowHead<V, X, IO>& h, Waiter& wt) {
+                                           const RowHead<V, X, IO>& h) {
   acc = norm(acc);
 #pragma unroll
   for (int o = G / 2; o > 0; o >>= 1) acc = add(acc, shfl_xor(acc, o, G));
-  if (p >= 0 && lane == 0) finish_value(a, kind, p, acc, h, wt);
+  if (p >= 0 && lane == 0) finish_value(a, kind, p, acc, h);
 }
 
 // Rows of one level, G threads per row; each group handles two rows at a
 // time with their loads interleaved (index/value loads of both rows first,
-// then the gathers), so every memory latency is shared by two rows.
+// then the gathers), so every memory latency is shared by two rows.  The
+// first row pair's pointers, heads and first batch of entries are loaded
+// before the wait for the earlier phases.
 template <typename V, typename X, typename IO, int G>
-__device__ __forceinline__ void level_rows(const ApplyArgs<V, X, IO>& a, int kind, int p0, int p1, int cta,
-                                           Waiter& wt) {
+__device__ __forceinline__ bool level_rows(const ApplyArgs<V, X, IO>& a, int kind, int p0, int p1, int cta,
+                                           Progress& pg, int ph) {
   using W = typename ValueReg<V, X>::type;
+  // entries per lane and row per batch (fewer with binary64 values, which
+  // take twice the registers)
+  constexpr int B = sizeof(V) == 8 ? 4 : 8;
   const int lane = threadIdx.x % G;
   const int64_t groups = (int64_t)gridDim.x * blockDim.x / G;
   const int64_t g0 = ((int64_t)cta * blockDim.x + threadIdx.x) / G;
@@ -347,15 +312,28 @@ __device__ __forceinline__ void level_rows(const ApplyArgs<V, X, IO>& a, int kin
   const int* col = kind == PH_FWD ? a.Lcol : a.Ucol;
   const V* val = kind == PH_FWD ? a.Lval : a.Uval;
   const X* x = kind == PH_FWD ? a.w : a.z;  // vector read through the columns
-  // entries per lane and row per batch (fewer with binary64 values, which
-  // take twice the registers)
-  constexpr int B = sizeof(V) == 8 ? 4 : 8;
-  for (int64_t base = p0; base < p1; base += 2 * groups) {
+  int64_t base = p0;
+  int pa = -1, pb = -1, qa = 0, ea = 0, qb = 0, eb = 0;
+  RowHead<V, X, IO> ha{zero<X>(), -1, 0}, hb{zero<X>(), -1, 0};
+  int ca[B], cb[B];
+  W va[B], vb[B];
+  // lanes past the end of a row gather nothing
+  auto load_batch = [&]() {
+#pragma unroll
+    for (int i = 0; i < B; ++i) {
+      const int q1 = qa + i * G, q2 = qb + i * G;
+      const bool o1 = q1 < ea, o2 = q2 < eb;
+      ca[i] = o1 ? __ldg(col + q1) : -1;
+      va[i] = o1 ? ldw<W>(val + q1) : W(0);
+      cb[i] = o2 ? __ldg(col + q2) : -1;
+      vb[i] = o2 ? ldw<W>(val + q2) : W(0);
+    }
+  };
+  auto load_pair = [&]() {
     const int64_t ra = base + g0, rb = base + groups + g0;
-    const int pa = ra < p1 ? (int)ra : -1;
-    const int pb = rb < p1 ? (int)rb : -1;
-    int qa = 0, ea = 0, qb = 0, eb = 0;
-    RowHead<V, X, IO> ha{zero<X>(), -1, 0}, hb{zero<X>(), -1, 0};
+    pa = ra < p1 ? (int)ra : -1;
+    pb = rb < p1 ? (int)rb : -1;
+    qa = ea = qb = eb = 0;
     if (pa >= 0) {
       qa = __ldg(ptr + pa) + lane;
       ea = __ldg(ptr + pa + 1);
@@ -366,55 +344,50 @@ __device__ __forceinline__ void level_rows(const ApplyArgs<V, X, IO>& a, int kin
       eb = __ldg(ptr + pb + 1);
       if (lane == 0) hb = row_head(a, kind, pb);
     }
+    load_batch();
+  };
+  load_pair();
+  if (!pg.wait(ph)) return false;
+  while (base < p1) {
     // two partial sums per row halve the dependent chain of FMAs
     X acca = zero<X>(), accb = zero<X>(), acca2 = zero<X>(), accb2 = zero<X>();
     while (qa < ea || qb < eb) {
-      // lanes past the end of a row gather nothing
-      int ca[B], cb[B];
-      W va[B], vb[B];
+      X xa[B], xb[B];
 #pragma unroll
-      for (int i = 0; i < B; ++i) {
-        const int q1 = qa + i * G, q2 = qb + i * G;
-        const bool o1 = q1 < ea, o2 = q2 < eb;
-        ca[i] = o1 ? __ldg(col + q1) : -1;
-        va[i] = o1 ? ldw<W>(val + q1) : W(0);
-        cb[i] = o2 ? __ldg(col + q2) : -1;
-        vb[i] = o2 ? ldw<W>(val + q2) : W(0);
+      for (int i = 0; i < B; ++i) {  // both rows' gathers in flight at once
+        xa[i] = ca[i] >= 0 ? ldx(x + ca[i]) : zero<X>();
+        xb[i] = cb[i] >= 0 ? ldx(x + cb[i]) : zero<X>();
       }
-      // both rows' gathers in flight at once
-      int cab[2 * B];
-      X xab[2 * B];
-#pragma unroll
-      for (int i = 0; i < B; ++i) {
-        cab[i] = ca[i];
-        cab[B + i] = cb[i];
-      }
-      gather(x, cab, xab, wt);
 #pragma unroll
       for (int i = 0; i < B; i += 2) {
-        mac(acca, va[i], xab[i]);
-        mac(accb, vb[i], xab[B + i]);
-        mac(acca2, va[i + 1], xab[i + 1]);
-        mac(accb2, vb[i + 1], xab[B + i + 1]);
+        mac(acca, va[i], xa[i]);
+        mac(accb, vb[i], xb[i]);
+        mac(acca2, va[i + 1], xa[i + 1]);
+        mac(accb2, vb[i + 1], xb[i + 1]);
       }
       qa += B * G;
       qb += B * G;
+      load_batch();
     }
     acca = add(norm(acca), norm(acca2));
     accb = add(norm(accb), norm(accb2));
-    finish_row<V, X, IO, G>(a, kind, pa, acca, lane, ha, wt);
-    finish_row<V, X, IO, G>(a, kind, pb, accb, lane, hb, wt);
+    finish_row<V, X, IO, G>(a, kind, pa, acca, lane, ha);
+    finish_row<V, X, IO, G>(a, kind, pb, accb, lane, hb);
+    base += 2 * groups;
+    if (base < p1) load_pair();
   }
+  return true;
 }
 
 // Rows of one level with G = 64..512 threads per row (G / 32 warps, 512 / G
 // rows per CTA): for few, long rows, such as the deepest levels, whose rows
 // collect the fill of every earlier level.  Warp partial sums meet in
 // shared memory.  The row loop is uniform across the CTA (it depends on the
-// block index only), as the CTA barriers inside it require.
+// block index only), as the CTA barriers inside it require.  The first
+// pass's row and first batch are loaded before the wait.
 template <typename V, typename X, typename IO, int G>
-__device__ __forceinline__ void level_rows_wide(const ApplyArgs<V, X, IO>& a, int kind, int p0, int p1, int cta,
-                                                Waiter& wt) {
+__device__ __forceinline__ bool level_rows_wide(const ApplyArgs<V, X, IO>& a, int kind, int p0, int p1, int cta,
+                                                Progress& pg, int ph) {
   using VR = typename ValueReg<V, X>::type;
   constexpr int NW = G / 32;                // warps per row
   constexpr int RPC = kPersistThreads / G;  // rows per CTA and pass
@@ -426,31 +399,44 @@ __device__ __forceinline__ void level_rows_wide(const ApplyArgs<V, X, IO>& a, in
   const int* col = kind == PH_FWD ? a.Lcol : a.Ucol;
   const V* val = kind == PH_FWD ? a.Lval : a.Uval;
   const X* x = kind == PH_FWD ? a.w : a.z;
-  for (int64_t base = p0 + (int64_t)cta * RPC; base < p1; base += (int64_t)gridDim.x * RPC) {
-    const int p = base + slot < p1 ? (int)(base + slot) : -1;
-    X acc = zero<X>(), acc2 = zero<X>();
-    RowHead<V, X, IO> h{zero<X>(), -1, 0};
-    if (p >= 0 && t == 0) h = row_head(a, kind, p);
+  int64_t base = p0 + (int64_t)cta * RPC;
+  int p = -1, q = 0, e = 0;
+  RowHead<V, X, IO> h{zero<X>(), -1, 0};
+  int c[B];
+  VR v[B];
+  auto load_batch = [&]() {
+#pragma unroll
+    for (int i = 0; i < B; ++i) {
+      const bool o = q + i * G < e;
+      c[i] = o ? __ldg(col + q + i * G) : -1;
+      v[i] = o ? ldw<VR>(val + q + i * G) : VR(0);
+    }
+  };
+  auto load_row = [&]() {
+    p = base + slot < p1 ? (int)(base + slot) : -1;
+    q = e = 0;
     if (p >= 0) {
-      int q = __ldg(ptr + p) + t;
-      const int e = __ldg(ptr + p + 1);
-      for (; q < e; q += B * G) {
-        int c[B];
-        VR v[B];
+      q = __ldg(ptr + p) + t;
+      e = __ldg(ptr + p + 1);
+      if (t == 0) h = row_head(a, kind, p);
+    }
+    load_batch();
+  };
+  load_row();
+  if (!pg.wait(ph)) return false;
+  for (; base < p1; base += (int64_t)gridDim.x * RPC) {
+    X acc = zero<X>(), acc2 = zero<X>();
+    while (q < e) {
+      X xv[B];
 #pragma unroll
-        for (int i = 0; i < B; ++i) {
-          const bool o = q + i * G < e;
-          c[i] = o ? __ldg(col + q + i * G) : -1;
-          v[i] = o ? ldw<VR>(val + q + i * G) : VR(0);
-        }
-        X xv[B];
-        gather(x, c, xv, wt);
+      for (int i = 0; i < B; ++i) xv[i] = c[i] >= 0 ? ldx(x + c[i]) : zero<X>();
 #pragma unroll
-        for (int i = 0; i < B; i += 2) {
-          mac(acc, v[i], xv[i]);
-          mac(acc2, v[i + 1], xv[i + 1]);
-        }
+      for (int i = 0; i < B; i += 2) {
+        mac(acc, v[i], xv[i]);
+        mac(acc2, v[i + 1], xv[i + 1]);
       }
+      q += B * G;
+      load_batch();
     }
     acc = add(norm(acc), norm(acc2));
 #pragma unroll
@@ -461,84 +447,119 @@ __device__ __forceinline__ void level_rows_wide(const ApplyArgs<V, X, IO>& a, in
       X sum = zero<X>();
 #pragma unroll
       for (int j = 0; j < NW; ++j) sum = add(sum, part[slot * NW + j]);
-      finish_value(a, kind, p, sum, h, wt);
+      finish_value(a, kind, p, sum, h);
     }
     __syncthreads();  // part[] is reused by the next pass
+    if (base + (int64_t)gridDim.x * RPC < p1) {
+      base += (int64_t)gridDim.x * RPC;
+      load_row();
+      base -= (int64_t)gridDim.x * RPC;
+    }
   }
+  return true;
+}
+
+// The dense trailing block: z_d = D^{-1} w_d with its stored inverse, one
+// warp per row; the first row's first chunk is loaded before the wait.
+template <typename V, typename X, typename IO>
+__device__ __forceinline__ bool dense_rows(const ApplyArgs<V, X, IO>& a, int cta, Progress& pg, int ph) {
+  using W = typename ValueReg<V, X>::type;
+  const int lane = threadIdx.x & 31;
+  const int warps = (gridDim.x * blockDim.x) >> 5;
+  int r = (cta * blockDim.x + threadIdx.x) >> 5;
+  W rv[8];
+  auto load_chunk = [&](int c0) {
+    const V* row = a.dense + (int64_t)r * a.nd;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int c = c0 + 32 * i;
+      rv[i] = (r < a.nd && c < a.nd) ? ldw<W>(row + c) : W(0);
+    }
+  };
+  load_chunk(lane);
+  if (!pg.wait(ph)) return false;
+  for (; r < a.nd; r += warps) {
+    X acc = zero<X>(), acc2 = zero<X>();
+    for (int c0 = lane; c0 < a.nd; c0 += 8 * 32) {
+      X wv[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int c = c0 + 32 * i;
+        wv[i] = c < a.nd ? ldx(a.w + a.d0 + c) : zero<X>();
+      }
+#pragma unroll
+      for (int i = 0; i < 8; i += 2) {
+        mac(acc, rv[i], wv[i]);
+        mac(acc2, rv[i + 1], wv[i + 1]);
+      }
+      if (c0 + 8 * 32 < a.nd) load_chunk(c0 + 8 * 32);
+    }
+    acc = add(norm(acc), norm(acc2));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc = add(acc, shfl_xor(acc, o, 32));
+    if (lane == 0) {
+      stx(a.z + a.d0 + r, acc);
+      a.out[__ldg(a.perm + a.d0 + r)] = to_io<IO>(mul(ldw<W>(a.scale + a.d0 + r), acc));
+    }
+    if (r + warps < a.nd) {
+      r += warps;
+      load_chunk(lane);
+      r -= warps;
+    }
+  }
+  return true;
 }
 
 template <typename V, typename X, typename IO>
 __global__ void __launch_bounds__(kPersistThreads, 1)
-ildl_apply_persistent_kernel(ApplyArgs<V, X, IO> a, const int4* __restrict__ phases, int nphase, int* err,
-                             unsigned long long* stamps) {
+ildl_apply_persistent_kernel(ApplyArgs<V, X, IO> a, const int4* __restrict__ phases, int nphase, unsigned* done,
+                             int* err, unsigned long long* stamps) {
   using W = typename ValueReg<V, X>::type;
-  Waiter wt{0u, false, err};
-  if (stamps && blockIdx.x == 0 && threadIdx.x == 0) {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    stamps[0] = t;  // start (CTA 0)
+  __shared__ int s_known, s_failed;
+  if (threadIdx.x == 0) {
+    s_known = 0;
+    s_failed = 0;
+    if (stamps && blockIdx.x == 0) {
+      unsigned long long t;
+      asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+      stamps[0] = t;  // start (CTA 0)
+    }
   }
+  __syncthreads();
+  Progress pg{phases, done, err, &s_known, &s_failed};
   for (int ph = 0; ph < nphase; ++ph) {
-    const int4 P = phases[ph];  // kind, p0, p1, G | first CTA << 16
-    const int kind = P.x, p0 = P.y, p1 = P.z, G = P.w & 0xFFFF;
-    // the phase's rows start at CTA P.w >> 16: consecutive small phases land
-    // on different CTAs, whose loads are then issued while the previous
-    // level is still being computed (not after it, as on one CTA)
+    const int4 P = phases[ph];
+    const int kind = P.x & 0xFF, parts = P.x >> 8, p0 = P.y, p1 = P.z, G = P.w & 0xFFFF;
+    // rotated CTA index: the phase's rows start at CTA P.w >> 16
     const int cta = (int)((blockIdx.x + gridDim.x - (unsigned)(P.w >> 16) % gridDim.x) % gridDim.x);
+    if (cta >= parts) continue;  // no rows of this phase here (uniform over the CTA)
+    bool ok = true;
     if (kind == PH_GATHER) {
-      // level 0: rows without entries, w = s b[perm]
-      for (int p = p0 + blockIdx.x * blockDim.x + threadIdx.x; p < p1; p += gridDim.x * blockDim.x)
-        publish(a.w + p, mul(ldw<W>(a.scale + p), from_io<X>(__ldg(a.b + __ldg(a.perm + p)))));
+      // level 0: rows without entries, w = s b[perm]; nothing to wait for
+      for (int p = p0 + cta * blockDim.x + threadIdx.x; p < p1; p += gridDim.x * blockDim.x)
+        stx(a.w + p, mul(ldw<W>(a.scale + p), from_io<X>(__ldg(a.b + __ldg(a.perm + p)))));
     } else if (kind == PH_DENSE) {
-      const int lane = threadIdx.x & 31;
-      const int warps = (gridDim.x * blockDim.x) >> 5;
-      for (int r = (cta * blockDim.x + threadIdx.x) >> 5; r < a.nd; r += warps) {
-        const V* row = a.dense + (int64_t)r * a.nd;
-        X acc = zero<X>(), acc2 = zero<X>();
-        for (int c0 = lane; c0 < a.nd; c0 += 8 * 32) {
-          W rv[8];
-          X wv[8];
-          int cc[8];
-#pragma unroll
-          for (int i = 0; i < 8; ++i) {
-            const int c = c0 + 32 * i;
-            rv[i] = c < a.nd ? ldw<W>(row + c) : W(0);
-            cc[i] = c < a.nd ? c : -1;
-          }
-          gather(a.w + a.d0, cc, wv, wt);
-#pragma unroll
-          for (int i = 0; i < 8; i += 2) {
-            mac(acc, rv[i], wv[i]);
-            mac(acc2, rv[i + 1], wv[i + 1]);
-          }
-        }
-        acc = add(norm(acc), norm(acc2));
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) acc = add(acc, shfl_xor(acc, o, 32));
-        if (lane == 0) {
-          publish(a.z + a.d0 + r, acc);
-          a.out[__ldg(a.perm + a.d0 + r)] = to_io<IO>(mul(ldw<W>(a.scale + a.d0 + r), acc));
-        }
-      }
+      ok = dense_rows(a, cta, pg, ph);
     } else {
       switch (G) {  // threads per row, fixed per phase at upload
-        case 4: level_rows<V, X, IO, 4>(a, kind, p0, p1, cta, wt); break;
-        case 8: level_rows<V, X, IO, 8>(a, kind, p0, p1, cta, wt); break;
-        case 16: level_rows<V, X, IO, 16>(a, kind, p0, p1, cta, wt); break;
-        case 32: level_rows<V, X, IO, 32>(a, kind, p0, p1, cta, wt); break;
-        case 64: level_rows_wide<V, X, IO, 64>(a, kind, p0, p1, cta, wt); break;
-        case 128: level_rows_wide<V, X, IO, 128>(a, kind, p0, p1, cta, wt); break;
-        case 256: level_rows_wide<V, X, IO, 256>(a, kind, p0, p1, cta, wt); break;
-        default: level_rows_wide<V, X, IO, 512>(a, kind, p0, p1, cta, wt); break;
+        case 4: ok = level_rows<V, X, IO, 4>(a, kind, p0, p1, cta, pg, ph); break;
+        case 8: ok = level_rows<V, X, IO, 8>(a, kind, p0, p1, cta, pg, ph); break;
+        case 16: ok = level_rows<V, X, IO, 16>(a, kind, p0, p1, cta, pg, ph); break;
+        case 32: ok = level_rows<V, X, IO, 32>(a, kind, p0, p1, cta, pg, ph); break;
+        case 64: ok = level_rows_wide<V, X, IO, 64>(a, kind, p0, p1, cta, pg, ph); break;
+        case 128: ok = level_rows_wide<V, X, IO, 128>(a, kind, p0, p1, cta, pg, ph); break;
+        case 256: ok = level_rows_wide<V, X, IO, 256>(a, kind, p0, p1, cta, pg, ph); break;
+        default: ok = level_rows_wide<V, X, IO, 512>(a, kind, p0, p1, cta, pg, ph); break;
       }
     }
+    if (!ok) return;  // a wait timed out (uniform over the CTA)
+    pg.arrive(ph);
     if (stamps && cta == 0 && threadIdx.x == 0) {
       unsigned long long t;
       asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
       stamps[ph + 1] = t;  // when the phase's first CTA is done with it (phases overlap)
     }
   }
-
 }
 
 }  // namespace

@@ -27,7 +27,8 @@ struct DevFactor {
   T* z = nullptr;
   int4* phases = nullptr;  // persistent-apply phase list (kind, p0, p1, G)
   int nphase = 0;
-  unsigned* bar = nullptr;  // [0] arrivals, [32] generation, [64] timeout flag
+  unsigned* bar = nullptr;   // [64] timeout flag of the apply's waits
+  unsigned* done = nullptr;  // completion counters of the apply's phases
   int grid = 0;
   float2* wdf = nullptr;  // float-float work vectors of the mixed apply (binary32 copy only)
   float2* zdf = nullptr;

@@ -1168,6 +1168,7 @@ int build_ildl(const SymCsr& A, const ildl_params& prm, HostFactor& F, bool dens
       lv.m = m;
       lv.mc_n = mc_n;
       lv.nblk = (int)acc.size();
+      lv.sptr = S.ptr.data();
       lv.cidx = cidx.data();
       lv.cnodes = cnodes.data();
       lv.rrec = rrec.data();

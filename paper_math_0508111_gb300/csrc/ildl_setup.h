@@ -92,6 +92,7 @@ struct HostFactor {
 //   tau             drop tolerance of S' (off the diagonal).
 struct SchurLevel {
   int m = 0, mc_n = 0, nblk = 0;
+  const int64_t* sptr = nullptr;  // row pointers of the level matrix S (m + 1)
   const int* cidx = nullptr;
   const int* cnodes = nullptr;
   const int64_t* rrec = nullptr;

@@ -30,6 +30,7 @@
 
 #include "anderson_impl.cuh"
 #include "ildl_impl.cuh"
+#include "gram_bf16.h"
 
 namespace ajd {
 namespace {
@@ -668,6 +669,13 @@ class JdSolver {
        *tb_ = nullptr, *yb_ = nullptr, *ub_ = nullptr, *bb_ = nullptr;
   double* host_ = nullptr;  // pinned readback area
   int nb_ = 0;              // blocks of vector kernels
+  // BF16 shadows of Q and V for the tensor-core first Gram-Schmidt pass:
+  // columns [0, qb_ok_) of Q and [0, vb_ok_) of V are current
+  bool gram_bf16_ = false;
+  void *Xbq_ = nullptr, *Xbv_ = nullptr;
+  int64_t ldb_ = 0;
+  int qb_ok_ = 0, vb_ok_ = 0;
+  int* gerr_ = nullptr;  // a tensor-core wait timed out
   std::vector<double> Mq_;  // cached Q^T W_Q block (host, kc x kc)
   int inner_total_ = 0;
   // CUDA events around the inner-loop preconditioner and stencil calls
@@ -746,6 +754,15 @@ int JdSolver::alloc() {
   AJD_TRY(A(&Qt_, pb * (kint_ + 1)));
   AJD_TRY(A(&W_, pb * (kint_ + 1)));
   for (void** b : {&xb_, &rb_, &qb_, &db_, &tb_, &yb_, &ub_, &bb_}) AJD_TRY(A(b, pb));
+  gram_bf16_ = (p_.gram == 2 || (p_.gram == 0 && p_.precision != JD_FP64)) && kint_ + jmax_ <= gram_bf16_max_cols();
+  if (gram_bf16_) {
+    ldb_ = gram_bf16_ld(n_);
+    AJD_TRY(A(&Xbq_, (size_t)ldb_ * 2 * kint_));
+    AJD_TRY(A(&Xbv_, (size_t)ldb_ * 2 * jmax_));
+    AJD_TRY(A((void**)&gerr_, sizeof(int)));
+    AJD_CUDA(cudaMemsetAsync(gerr_, 0, sizeof(int), s_));
+    qb_ok_ = vb_ok_ = 0;
+  }
   AJD_CUDA(cudaMallocHost(&host_, sizeof(double) * (kMaxM * kMaxM + 256)));
   for (auto& e : evp_) AJD_CUDA(cudaEventCreate(&e));
   for (auto& e : evs_) AJD_CUDA(cudaEventCreate(&e));
@@ -773,7 +790,8 @@ void JdSolver::release() {
   for (auto& e : evs_) if (e) cudaEventDestroy(e);
   for (void* p : {(void*)V_, (void*)AV_, (void*)Vt_, (void*)AVt_, (void*)Q_, (void*)t_, (void*)u_, (void*)Au_,
                   (void*)r_, (void*)H_, (void*)theta_, (void*)Y_, (void*)dots_, (void*)partial_, (void*)scal_,
-                  (void*)Minv_, (void*)gg_, (void*)flags_, (void*)amax_, Qt_, W_, xb_, rb_, qb_, db_, tb_, yb_, ub_, bb_})
+                  (void*)Minv_, (void*)gg_, (void*)flags_, (void*)amax_, Qt_, W_, xb_, rb_, qb_, db_, tb_, yb_, ub_, bb_,
+                  Xbq_, Xbv_, (void*)gerr_})
     if (p) cudaFree(p);
   if (host_) cudaFreeHost(host_);
   V_ = nullptr;
@@ -806,10 +824,39 @@ int JdSolver::dot_cols(Cols<double> X1, Cols<double> X2, const double* extra, co
 // t <- (I - [Q V][Q V]^T)^2 t; returns ||t|| (device scal[0] and host)
 int JdSolver::cgs2(int kc, int m, double* t, double* nrm_host) {
   Cols<double> Xq{Q_, ld_, kc}, Xv{V_, ld_, m};
-  for (int pass = 0; pass < 2; ++pass) {
-    if (kc + m == 0) break;
-    AJD_TRY(dot_cols(Xq, Xv, nullptr, t, dots_));
+  if (gram_bf16_ && kc + m > 0) {
+    // first pass: the projection c = X^T t on the tensor cores with the BF16
+    // shadows (brought up to date column by column), the update t -= X c
+    // with the binary64 columns -- so the BF16 error of c stays inside
+    // span(X), where the binary64 second pass removes it, and nothing is
+    // added to t's component outside span(X); if the second pass still
+    // removes more than 3/4 of ||t||^2 (Daniel-Gragg-Kaufman-Stewart
+    // criterion), one more binary64 pass
+    if (qb_ok_ < kc) AJD_TRY(gram_bf16_convert(Q_, ld_, qb_ok_, kc, Xbq_, ldb_, n_, s_));
+    if (vb_ok_ < m) AJD_TRY(gram_bf16_convert(V_, ld_, vb_ok_, m, Xbv_, ldb_, n_, s_));
+    qb_ok_ = kc;
+    vb_ok_ = m;
+    AJD_TRY(gram_bf16_dots(Xbq_, kc, Xbv_, m, ldb_, t, n_, partial_, nb_, dots_, gerr_, s_));
     multiaxpy_kernel<double><<<nb_, kThreads, 0, s_>>>(Xq, Xv, dots_, t, n_); count_launches();
+    AJD_TRY(dot_cols(Xq, Xv, t, t, dots_));  // projections and ||t||^2 before the pass
+    multiaxpy_kernel<double><<<nb_, kThreads, 0, s_>>>(Xq, Xv, dots_, t, n_); count_launches();
+    AJD_TRY(dot_cols(Cols<double>{t, ld_, 1}, Cols<double>{}, nullptr, t, scal_));
+    double nb[2];
+    AJD_CUDA(cudaMemcpyAsync(scal_ + 1, dots_ + kc + m, sizeof(double), cudaMemcpyDeviceToDevice, s_));
+    AJD_TRY(sync_read(scal_, 2, nb));
+    if (nb[0] < 0.25 * nb[1]) {
+      AJD_TRY(dot_cols(Xq, Xv, nullptr, t, dots_));
+      multiaxpy_kernel<double><<<nb_, kThreads, 0, s_>>>(Xq, Xv, dots_, t, n_); count_launches();
+    } else {
+      *nrm_host = std::sqrt(std::max(nb[0], 0.0));
+      return JD_OK;
+    }
+  } else {
+    for (int pass = 0; pass < 2; ++pass) {
+      if (kc + m == 0) break;
+      AJD_TRY(dot_cols(Xq, Xv, nullptr, t, dots_));
+      multiaxpy_kernel<double><<<nb_, kThreads, 0, s_>>>(Xq, Xv, dots_, t, n_); count_launches();
+    }
   }
   AJD_TRY(dot_cols(Cols<double>{t, ld_, 1}, Cols<double>{}, nullptr, t, scal_));
   double nn;
@@ -1050,6 +1097,7 @@ int JdSolver::run(double* evals, double* evecs, jd_stats* st) {
     lincomb_kernel<<<nb_, kThreads, 0, s_>>>(AV_, ld_, m, Y_, kMaxM, c, AVt_, ld_, n); count_launches();
     std::swap(V_, Vt_);
     std::swap(AV_, AVt_);
+    vb_ok_ = 0;  // every column of V changed
     expand_h(Hh, hostla::congruence(m, c, compact(Hh, m), Qy), c);
     expand_h(Gh, hostla::congruence(m, c, compact(Gh, m), Qy), c);
     AJD_TRY(wait_stream());  // Y_ is reused by the next upload
@@ -1145,6 +1193,7 @@ int JdSolver::run(double* evals, double* evecs, jd_stats* st) {
     }
     if (!(nrm > 0.0)) return fail(JD_EBREAKDOWN, "jd_solve: cannot expand the search space");
     scale_copy_kernel<<<nb_, kThreads, 0, s_>>>(t_, V_ + (int64_t)m * ld_, n, scal_, 0, 1); count_launches();
+    vb_ok_ = std::min(vb_ok_, m);
     AJD_TRY(stencil_apply<double>(h_, 0.0, V_ + (int64_t)m * ld_, AV_ + (int64_t)m * ld_, 1, s_));
     AJD_TRY(dot_cols(Cols<double>{V_, ld_, m + 1}, Cols<double>{}, nullptr, AV_ + (int64_t)m * ld_, dots_));
     shifted_dots_kernel<<<nb_, kThreads, 0, s_>>>(V_, AV_, ld_, m + 1, sigma_, n, partial_); count_launches();
@@ -1190,6 +1239,7 @@ int JdSolver::run(double* evals, double* evecs, jd_stats* st) {
       if (rnorm <= tol_ * normA_) {
         // lock u
         AJD_CUDA(cudaMemcpyAsync(Q_ + (int64_t)kc * ld_, u_, sizeof(double) * n, cudaMemcpyDeviceToDevice, s_));
+        qb_ok_ = std::min(qb_ok_, kc);
         lam.push_back(theta0);
         if (trace_) std::fprintf(stderr, "jd LOCK %d theta=%.15g res=%.3e at outer %d\n", kc, theta0, rnorm / normA_, outer);
         // cache W = K^{-1} q and the Q^T W block for the projected preconditioner
@@ -1260,6 +1310,24 @@ int JdSolver::run(double* evals, double* evecs, jd_stats* st) {
     ++steps_on_pair;
     if (trace_) std::fprintf(stderr, "   inner its %d (rel tol %.2e)\n", its, rel);
   }
+  // orthonormality of the final search-space basis, max |V^T V - I| (the
+  // Gram-Schmidt of every expansion, its BF16 first pass included)
+  {
+    double borth = 0.0;
+    for (int j = 0; j < m; ++j) {
+      AJD_TRY(dot_cols(Cols<double>{V_, ld_, m}, Cols<double>{}, nullptr, V_ + (int64_t)j * ld_, dots_));
+      double g[kMaxM];
+      AJD_TRY(sync_read(dots_, m, g));
+      for (int i = 0; i < m; ++i) borth = std::max(borth, std::fabs(g[i] - (i == j ? 1.0 : 0.0)));
+    }
+    if (st) st->basis_orth_error = borth;
+  }
+  if (gerr_) {
+    int ge = 0;
+    AJD_CUDA(cudaMemcpyAsync(&ge, gerr_, sizeof(int), cudaMemcpyDeviceToHost, s_));
+    AJD_TRY(wait_stream());
+    if (ge) return fail(JD_EDEVICE, "jd_solve: a tensor-core wait of the Gram-Schmidt timed out");
+  }
   if (st) {
     st->outer_its = outer;
     st->inner_its = inner_total_;
@@ -1307,6 +1375,7 @@ int JdSolver::lanczos(double* evals, double* evecs, jd_stats* st) {
   AJD_TRY(cgs2(0, 0, t_, &nrm));
   if (!(nrm > 0.0)) return fail(JD_EBREAKDOWN, "jd_lanczos_solve: zero start vector");
   scale_copy_kernel<<<nb_, kThreads, 0, s_>>>(t_, V_, n, scal_, 0, 1); count_launches();
+  vb_ok_ = 0;
   // the paper's 1e-10; a binary32 inner solve cannot get below ~1e-6 (its
   // Lanczos operator is then only that accurate)
   const double inner_tol = p_.inner_floor > 0.0 ? p_.inner_floor : (p_.precision == JD_FP32 ? 1e-6 : 1e-10);
@@ -1359,6 +1428,7 @@ int JdSolver::lanczos(double* evals, double* evecs, jd_stats* st) {
     if (!(nrm > 1e-14 * std::fabs(aj)) || m == jmax_) break;  // invariant subspace, or no room
     beta.push_back(nrm);
     scale_copy_kernel<<<nb_, kThreads, 0, s_>>>(t_, V_ + (int64_t)(j + 1) * ld_, n, scal_, 0, 1); count_launches();
+    vb_ok_ = std::min(vb_ok_, j + 1);
   }
   // Ritz vectors of the kint largest |nu| into Q
   const int kc = std::min(kint_, m);
@@ -1368,6 +1438,7 @@ int JdSolver::lanczos(double* evals, double* evecs, jd_stats* st) {
       for (int i = 0; i < m; ++i) up[(size_t)q * kMaxM + i] = Z[(size_t)order[q] * m + i];
     AJD_CUDA(cudaMemcpyAsync(Y_, up.data(), sizeof(double) * kMaxM * kc, cudaMemcpyHostToDevice, s_));
     lincomb_kernel<<<nb_, kThreads, 0, s_>>>(V_, ld_, m, Y_, kMaxM, kc, Q_, ld_, n); count_launches();
+    qb_ok_ = 0;
     AJD_TRY(wait_stream());
   }
   if (st) {
