@@ -70,10 +70,15 @@ def parse():
     ap.add_argument("--batch-problems", type=int, default=256)
     ap.add_argument("--batch-sample", type=int, default=32,
                     help="problems of the bounded batch sample reported beside the headline (0 skips it)")
-    ap.add_argument("--serve-requests", type=int, default=16,
+    ap.add_argument("--serve-requests", type=int, default=8,
                     help="requests per arrival rate of the serving sweep (0 skips it)")
+    ap.add_argument("--serve-max-outer", type=int, default=400,
+                    help="Jacobi-Davidson outer steps per served request before it returns its converged prefix "
+                         "(bounds the sample's run time; the weak-disorder requests of the stream converge slowly)")
     ap.add_argument("--serve-rates", type=float, nargs="+", default=[0.5, 1.0, 2.0],
                     help="arrival rates of the serving sweep, as multiples of the measured capacity")
+    ap.add_argument("--serve-budget-s", type=float, default=240.0,
+                    help="no further rate of the serving sweep is started once the sweep has run this long")
     ap.add_argument("--serve-lmax", type=int, default=120, help="largest lattice of the serving stream")
     ap.add_argument("--cpu-L", type=int, default=30, help="lattice of the CPU oracle baseline sample")
     ap.add_argument("--serve-slots", type=int, default=4)
@@ -81,6 +86,16 @@ def parse():
     ap.add_argument("--setup-threads", type=int, default=2,
                     help="concurrent preconditioner builds in the pipelined batch")
     return ap.parse_args()
+
+
+_T0 = time.perf_counter()
+
+
+def progress(msg):
+    """One line on stderr per stage (wall time since start), so a slow stage
+    shows in the log even when the run is cut short."""
+    sys.stderr.write("[bench %7.1f s] %s\n" % (time.perf_counter() - _T0, msg))
+    sys.stderr.flush()
 
 
 def dist_env():
@@ -202,7 +217,8 @@ def run_requests(ajd, args, precision, reqs, slots, setup_threads):
     from the start) and poll until all are done.  Returns eigenpairs/s over
     the whole run and the latency percentiles (submission to completion)."""
     lat, pairs, failed, per = [], 0, 0, []
-    with ajd.Server(slots=slots, setup_threads=setup_threads, precision=precision) as srv:
+    with ajd.Server(slots=slots, setup_threads=setup_threads, precision=precision,
+                    max_outer=args.serve_max_outer) as srv:
         start = time.perf_counter()
         pending, i = {}, 0
         while i < len(reqs) or pending:
@@ -227,6 +243,8 @@ def run_requests(ajd, args, precision, reqs, slots, setup_threads):
     out = summarize_requests(lat, pairs, failed, elapsed, info["peak_solving"], slots, setup_threads)
     out["per_request"] = {"fields": ["L", "W", "sigma", "k", "latency_ms", "setup_ms", "solve_ms", "outer", "inner",
                                      "nconv"], "rows": per}
+    out["unconverged"] = sum(1 for r in per if r[9] < r[3])
+    out["max_outer"] = args.serve_max_outer
     return out
 
 
@@ -268,12 +286,19 @@ def serving_sweep(ajd, args, precision, rank=0, world=1):
     of serve_requests requests at each rate of serve_rates times that
     capacity, with p50/p99 latency (submission to completion) per rate."""
     import workloads
+    t_start = time.perf_counter()
     base = workloads.serve_recipe(args.serve_requests, 1.0, seed=7, lmax=args.serve_lmax)
+    progress("serving: capacity run (%d requests at t = 0)" % len(base))
     sat = run_requests(ajd, args, precision, rank_share(ajd, [dict(r, t=0.0) for r in base], rank, world),
                        args.serve_slots, args.serve_setup_threads)
     capacity = sat["requests"] / sat["seconds"]
-    out = {"capacity_requests_per_s": capacity, "saturated": sat, "rates": []}
+    out = {"capacity_requests_per_s": capacity, "saturated": sat, "rates": [], "skipped_rates": []}
     for i, mult in enumerate(args.serve_rates):
+        elapsed = replicas_max(time.perf_counter() - t_start)
+        if elapsed > args.serve_budget_s:
+            out["skipped_rates"].append(mult)
+            continue
+        progress("serving: %g x capacity" % mult)
         # the same requests at every rate (same draws, arrival times scaled)
         reqs = workloads.serve_recipe(args.serve_requests, mult * capacity, seed=7, lmax=args.serve_lmax)
         res = run_requests(ajd, args, precision, rank_share(ajd, reqs, rank, world), args.serve_slots,
@@ -281,11 +306,18 @@ def serving_sweep(ajd, args, precision, rank=0, world=1):
         res["rate_multiple"] = mult
         res["rate_per_s"] = mult * capacity
         out["rates"].append(res)
-    out["sample"] = ("%d requests per point, L~U{16..%d}, W~U[8,24], sigma~U[-2,2], k in {1,5,10}, tol %g; "
-                     "capacity from all requests submitted at t=0, then Poisson arrivals at %s x capacity "
-                     "(a bounded sample of the 4096-request stream)"
-                     % (args.serve_requests, args.serve_lmax, args.tol, "/".join("%g" % m for m in args.serve_rates)))
+    out["sample"] = ("%d requests per point, L~U{16..%d}, W~U[8,24], sigma~U[-2,2], k in {1,5,10}, tol %g, at most "
+                     "%d outer steps per request; capacity from all requests submitted at t=0, then Poisson arrivals "
+                     "at %s x capacity, a rate skipped once the sweep has run %g s (a bounded sample of the "
+                     "4096-request stream)"
+                     % (args.serve_requests, args.serve_lmax, args.tol, args.serve_max_outer,
+                        "/".join("%g" % m for m in args.serve_rates), args.serve_budget_s))
     return out
+
+
+def replicas_max(x):
+    from paper_math_0508111_gb300 import replicas
+    return replicas.max_over_ranks(x)
 
 
 def batch_sample(ajd, args, precision, rank=0, world=1):
@@ -467,6 +499,7 @@ def main():
     ev_ptrs = [ev_dev[i].data_ptr() for i in range(nsteps)]
     x_ptrs = [X_all[i].data_ptr() for i in range(nsteps)]
     # warm-up: the same pipeline on the warm-up realisations
+    progress("warm-up: %d realisations" % nwarm)
     batch([h.handle for h in lattices[:nwarm]], head, ev_ptrs[:1] * nwarm, x_ptrs[:1] * nwarm)
 
     def barrier():
@@ -474,6 +507,7 @@ def main():
             import torch.distributed as dist
             dist.barrier()
 
+    progress("timed: %d realisations" % nsteps)
     sampler = ClockSampler(local)
     sampler.start()
     barrier()
@@ -502,6 +536,7 @@ def main():
     fp64 = None
     if not args.no_fp64:
         m64 = max(1, min(args.fp64_steps, nsteps))
+        progress("binary64 arms: %d realisations" % m64)
         sub = lattices[nwarm:nwarm + m64]
         torch.cuda.synchronize()
         f0 = torch.cuda.Event(enable_timing=True)
@@ -542,6 +577,7 @@ def main():
     # and eigenvectors into pinned host buffers
     e2e = None
     if not args.no_e2e and args.model == "diagonal":
+        progress("end to end through the C ABI from host buffers")
         pots = [torch.from_numpy(h.potential()).pin_memory() for h in lattices[nwarm:]]
         Xh = torch.empty((nsteps, k, n), dtype=torch.float64).pin_memory()
         evh = torch.empty((nsteps, k), dtype=torch.float64).pin_memory()
@@ -584,11 +620,14 @@ def main():
 
     # the batch sample and the serving stream split over the ranks by the
     # greedy work/HBM balance (independent problems, host-side gathers only)
+    if args.batch_sample > 0:
+        progress("batch sample: %d problems" % args.batch_sample)
     batch_c4 = batch_sample(ajd, args, head, rank, world) if args.batch_sample > 0 else None
     serving = serving_sweep(ajd, args, head, rank, world) if args.serve_requests > 0 else None
 
     cpu = None
     if rank == 0 and not args.no_cpu:
+        progress("CPU oracle baseline (L = %d)" % args.cpu_L)
         cpu = cpu_baseline(W, sigma, k, tol, args.cpu_L)
         cpu.pop("seconds", None)
         one_thread = cpu_baseline(W, sigma, k, tol, args.cpu_L, threads=1)

@@ -108,8 +108,12 @@ __global__ void gj_eliminate_kernel(double* __restrict__ A, double* __restrict__
       if (k == c) A[(int64_t)r * m + k] = 0.0;
       else A[(int64_t)r * m + k] -= fr * A[(int64_t)c * m + k];
     } else {
+      // row c of X is zero outside the columns that earlier steps filled
+      // (X starts as I), and a zero there leaves X[r][k] unchanged: skip
+      // the read-modify-write (about half of X's traffic over the inversion)
       const int k = j - (m - c);
-      X[(int64_t)r * m + k] -= fr * X[(int64_t)c * m + k];
+      const double xc = X[(int64_t)c * m + k];
+      if (xc != 0.0) X[(int64_t)r * m + k] -= fr * xc;
     }
   }
 }
@@ -212,13 +216,13 @@ int upload_factor(const HostFactor& F, DevFactor<T>& d, cudaStream_t st) {
   const std::vector<int>& lvp = F.level_ptr;
   const int nl = F.nlev;
   // threads per row: enough rows in flight to cover the grid, and about four
-  // stored entries per thread of a row (a power of two in 4..512)
+  // stored entries per thread of a row (a power of two in 1..512)
   const double threads_total = (double)sm_count() * kPersistThreads;
   auto pick_g = [&](int rows, double avg) {
     // (a phase of many long rows keeps up to a warp per row: each thread then
     // works through several rows, eight entries per batch)
     const double want = std::max(std::min(threads_total / std::max(rows, 1), avg / 4.0), std::min(avg / 8.0, 32.0));
-    int g = 4;
+    int g = 1;
     while (g < 512 && 2 * g <= want) g *= 2;
     return g;
   };

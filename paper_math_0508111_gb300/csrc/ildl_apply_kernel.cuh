@@ -248,23 +248,42 @@ struct Progress {
   }
 };
 
-// Row operands loaded before the row's entries: forward -- the right-hand
-// side s[p] b[perm[p]]; backward -- the 2x2 partner and the permutation
-// entry.
+// Row operands that do not depend on other rows, loaded before the row's
+// entries (and, for a phase's first rows, before the wait): the permutation
+// entry; forward -- the right-hand side s[p] b[perm[p]]; backward -- the
+// 2x2 partner, the row's entries of D^{-1} and its scale.  Backward rows
+// also need D^{-1} w, formed after the wait (bwd_rhs) while the entries'
+// gathers are in flight.
 template <typename V, typename X, typename IO>
 struct RowHead {
+  using W = typename ValueReg<V, X>::type;
   X rhs;
   int pp, perm;
+  W dd, dof, sc;
 };
 
 template <typename V, typename X, typename IO>
 __device__ __forceinline__ RowHead<V, X, IO> row_head(const ApplyArgs<V, X, IO>& a, int kind, int p) {
   using W = typename ValueReg<V, X>::type;
-  RowHead<V, X, IO> h{zero<X>(), -1, 0};
+  RowHead<V, X, IO> h{zero<X>(), -1, 0, W(0), W(0), W(0)};
   h.perm = __ldg(a.perm + p);
-  if (kind == PH_FWD) h.rhs = mul(ldw<W>(a.scale + p), from_io<X>(__ldg(a.b + h.perm)));
-  else h.pp = __ldg(a.partner + p);
+  if (kind == PH_FWD) {
+    h.rhs = mul(ldw<W>(a.scale + p), from_io<X>(__ldg(a.b + h.perm)));
+  } else {
+    h.pp = __ldg(a.partner + p);
+    h.dd = ldw<W>(a.dd + p);
+    h.dof = ldw<W>(a.dof + p);
+    h.sc = ldw<W>(a.scale + p);
+  }
   return h;
+}
+
+// backward row p: rhs = (D^{-1} w)_p, from the forward sweep's values
+template <typename V, typename X, typename IO>
+__device__ __forceinline__ void bwd_rhs(const ApplyArgs<V, X, IO>& a, int p, RowHead<V, X, IO>& h) {
+  X d = mul(h.dd, ldx(a.w + p));
+  if (h.pp >= 0) d = add(d, mul(h.dof, ldx(a.w + h.pp)));
+  h.rhs = d;
 }
 
 // Final value of row p of a sweep, given the row's dot product `acc` with
@@ -272,15 +291,12 @@ __device__ __forceinline__ RowHead<V, X, IO> row_head(const ApplyArgs<V, X, IO>&
 template <typename V, typename X, typename IO>
 __device__ __forceinline__ void finish_value(const ApplyArgs<V, X, IO>& a, int kind, int p, X acc,
                                              const RowHead<V, X, IO>& h) {
-  using W = typename ValueReg<V, X>::type;
+  const X v = sub(h.rhs, acc);
   if (kind == PH_FWD) {
-    stx(a.w + p, sub(h.rhs, acc));
+    stx(a.w + p, v);
   } else {
-    X d = mul(ldw<W>(a.dd + p), ldx(a.w + p));
-    if (h.pp >= 0) d = add(d, mul(ldw<W>(a.dof + p), ldx(a.w + h.pp)));
-    const X zp = sub(d, acc);
-    stx(a.z + p, zp);
-    a.out[h.perm] = to_io<IO>(mul(ldw<W>(a.scale + p), zp));
+    stx(a.z + p, v);
+    a.out[h.perm] = to_io<IO>(mul(h.sc, v));
   }
 }
 
@@ -297,14 +313,15 @@ __device__ __forceinline__ void finish_row(const ApplyArgs<V, X, IO>& a, int kin
 // time with their loads interleaved (index/value loads of both rows first,
 // then the gathers), so every memory latency is shared by two rows.  The
 // first row pair's pointers, heads and first batch of entries are loaded
-// before the wait for the earlier phases.
+// before the wait for the earlier phases; while a pair's entries are
+// gathered, the next pair's pointers and heads are already being loaded.
 template <typename V, typename X, typename IO, int G>
 __device__ __forceinline__ bool level_rows(const ApplyArgs<V, X, IO>& a, int kind, int p0, int p1, int cta,
                                            Progress& pg, int ph) {
   using W = typename ValueReg<V, X>::type;
-  // entries per lane and row per batch (fewer with binary64 values, which
-  // take twice the registers)
-  constexpr int B = sizeof(V) == 8 ? 4 : 8;
+  // entries per lane and row per batch (fewer with binary64 values or
+  // float-float work vectors, which take twice the registers)
+  constexpr int B = sizeof(V) == 8 ? 4 : (sizeof(X) == 8 ? 6 : 8);
   const int lane = threadIdx.x % G;
   const int64_t groups = (int64_t)gridDim.x * blockDim.x / G;
   const int64_t g0 = ((int64_t)cta * blockDim.x + threadIdx.x) / G;
@@ -314,7 +331,7 @@ __device__ __forceinline__ bool level_rows(const ApplyArgs<V, X, IO>& a, int kin
   const X* x = kind == PH_FWD ? a.w : a.z;  // vector read through the columns
   int64_t base = p0;
   int pa = -1, pb = -1, qa = 0, ea = 0, qb = 0, eb = 0;
-  RowHead<V, X, IO> ha{zero<X>(), -1, 0}, hb{zero<X>(), -1, 0};
+  RowHead<V, X, IO> ha{}, hb{};
   int ca[B], cb[B];
   W va[B], vb[B];
   // lanes past the end of a row gather nothing
@@ -329,26 +346,37 @@ __device__ __forceinline__ bool level_rows(const ApplyArgs<V, X, IO>& a, int kin
       vb[i] = o2 ? ldw<W>(val + q2) : W(0);
     }
   };
-  auto load_pair = [&]() {
-    const int64_t ra = base + g0, rb = base + groups + g0;
-    pa = ra < p1 ? (int)ra : -1;
-    pb = rb < p1 ? (int)rb : -1;
-    qa = ea = qb = eb = 0;
-    if (pa >= 0) {
-      qa = __ldg(ptr + pa) + lane;
-      ea = __ldg(ptr + pa + 1);
-      if (lane == 0) ha = row_head(a, kind, pa);
+  // pointers and heads of the pair at `at` (rows beyond p1: -1)
+  auto load_heads = [&](int64_t at, int& ra, int& rb, int& sa, int& ta, int& sb, int& tb, RowHead<V, X, IO>& h1,
+                        RowHead<V, X, IO>& h2) {
+    const int64_t r1 = at + g0, r2 = at + groups + g0;
+    ra = r1 < p1 ? (int)r1 : -1;
+    rb = r2 < p1 ? (int)r2 : -1;
+    sa = ta = sb = tb = 0;
+    if (ra >= 0) {
+      sa = __ldg(ptr + ra) + lane;
+      ta = __ldg(ptr + ra + 1);
+      if (lane == 0) h1 = row_head(a, kind, ra);
     }
-    if (pb >= 0) {
-      qb = __ldg(ptr + pb) + lane;
-      eb = __ldg(ptr + pb + 1);
-      if (lane == 0) hb = row_head(a, kind, pb);
+    if (rb >= 0) {
+      sb = __ldg(ptr + rb) + lane;
+      tb = __ldg(ptr + rb + 1);
+      if (lane == 0) h2 = row_head(a, kind, rb);
     }
-    load_batch();
   };
-  load_pair();
+  load_heads(base, pa, pb, qa, ea, qb, eb, ha, hb);
+  load_batch();
   if (!pg.wait(ph)) return false;
   while (base < p1) {
+    if (kind == PH_BWD && lane == 0) {
+      if (pa >= 0) bwd_rhs(a, pa, ha);
+      if (pb >= 0) bwd_rhs(a, pb, hb);
+    }
+    // the next pair's pointers and heads, in flight during this pair's work
+    const int64_t nbase = base + 2 * groups;
+    int npa = -1, npb = -1, nqa = 0, nea = 0, nqb = 0, neb = 0;
+    RowHead<V, X, IO> nha{}, nhb{};
+    if (nbase < p1) load_heads(nbase, npa, npb, nqa, nea, nqb, neb, nha, nhb);
     // two partial sums per row halve the dependent chain of FMAs
     X acca = zero<X>(), accb = zero<X>(), acca2 = zero<X>(), accb2 = zero<X>();
     while (qa < ea || qb < eb) {
@@ -373,8 +401,18 @@ __device__ __forceinline__ bool level_rows(const ApplyArgs<V, X, IO>& a, int kin
     accb = add(norm(accb), norm(accb2));
     finish_row<V, X, IO, G>(a, kind, pa, acca, lane, ha);
     finish_row<V, X, IO, G>(a, kind, pb, accb, lane, hb);
-    base += 2 * groups;
-    if (base < p1) load_pair();
+    base = nbase;
+    if (base < p1) {
+      pa = npa;
+      pb = npb;
+      qa = nqa;
+      ea = nea;
+      qb = nqb;
+      eb = neb;
+      ha = nha;
+      hb = nhb;
+      load_batch();
+    }
   }
   return true;
 }
@@ -401,7 +439,7 @@ __device__ __forceinline__ bool level_rows_wide(const ApplyArgs<V, X, IO>& a, in
   const X* x = kind == PH_FWD ? a.w : a.z;
   int64_t base = p0 + (int64_t)cta * RPC;
   int p = -1, q = 0, e = 0;
-  RowHead<V, X, IO> h{zero<X>(), -1, 0};
+  RowHead<V, X, IO> h{};
   int c[B];
   VR v[B];
   auto load_batch = [&]() {
@@ -425,6 +463,7 @@ __device__ __forceinline__ bool level_rows_wide(const ApplyArgs<V, X, IO>& a, in
   load_row();
   if (!pg.wait(ph)) return false;
   for (; base < p1; base += (int64_t)gridDim.x * RPC) {
+    if (kind == PH_BWD && p >= 0 && t == 0) bwd_rhs(a, p, h);
     X acc = zero<X>(), acc2 = zero<X>();
     while (q < e) {
       X xv[B];
@@ -542,6 +581,8 @@ ildl_apply_persistent_kernel(ApplyArgs<V, X, IO> a, const int4* __restrict__ pha
       ok = dense_rows(a, cta, pg, ph);
     } else {
       switch (G) {  // threads per row, fixed per phase at upload
+        case 1: ok = level_rows<V, X, IO, 1>(a, kind, p0, p1, cta, pg, ph); break;
+        case 2: ok = level_rows<V, X, IO, 2>(a, kind, p0, p1, cta, pg, ph); break;
         case 4: ok = level_rows<V, X, IO, 4>(a, kind, p0, p1, cta, pg, ph); break;
         case 8: ok = level_rows<V, X, IO, 8>(a, kind, p0, p1, cta, pg, ph); break;
         case 16: ok = level_rows<V, X, IO, 16>(a, kind, p0, p1, cta, pg, ph); break;

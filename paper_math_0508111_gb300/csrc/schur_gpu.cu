@@ -26,6 +26,8 @@
 #include <climits>
 #include <cstring>
 #include <memory>
+#include <mutex>
+#include <utility>
 #include <vector>
 
 #include <omp.h>
@@ -334,6 +336,60 @@ __global__ void scale_kernel(const int64_t* __restrict__ ptr, const int* __restr
   }
 }
 
+// ---- pinned host staging, pooled across setups ----
+// S' comes back through page-locked memory (a copy into fresh pageable pages
+// runs at a few GB/s); the buffers are kept for the next setup of the
+// process, since page-locking hundreds of MB per setup would cost more than
+// the copies it speeds up.
+struct PinnedPool {
+  std::mutex mu;
+  std::vector<std::pair<void*, size_t>> free;
+};
+PinnedPool& pinned_pool() {
+  static PinnedPool* p = new PinnedPool();  // never destroyed: setups may run until exit
+  return *p;
+}
+
+struct Pinned {
+  void* p = nullptr;
+  size_t cap = 0;
+  Pinned() = default;
+  Pinned(const Pinned&) = delete;
+  Pinned& operator=(const Pinned&) = delete;
+  ~Pinned() {
+    if (p) {
+      std::lock_guard<std::mutex> lk(pinned_pool().mu);
+      pinned_pool().free.push_back({p, cap});
+    }
+  }
+  int reserve(size_t bytes) {
+    if (bytes <= cap) return JD_OK;
+    {
+      std::lock_guard<std::mutex> lk(pinned_pool().mu);
+      auto& fl = pinned_pool().free;
+      for (size_t i = 0; i < fl.size(); ++i)
+        if (fl[i].second >= bytes) {
+          if (p) fl.push_back({p, cap});
+          p = fl[i].first;
+          cap = fl[i].second;
+          fl.erase(fl.begin() + i);
+          return JD_OK;
+        }
+    }
+    if (p) cudaFreeHost(p);
+    p = nullptr;
+    cap = 0;
+    const size_t want = std::max(bytes + bytes / 4, (size_t)64 << 20);
+    cudaError_t e = cudaMallocHost(&p, want);
+    if (e != cudaSuccess) {
+      p = nullptr;
+      return fail(JD_ENOMEM, "gpu schur: pinned staging: %s", cudaGetErrorString(e));
+    }
+    cap = want;
+    return JD_OK;
+  }
+};
+
 // ---- device buffers that grow as needed ----
 template <typename T>
 struct DBuf {
@@ -502,13 +558,34 @@ class DeviceSchur final : public SchurEngine {
     AJD_CHECK_LAUNCH();
     AJD_TRY(sync());
     t_k2 = ms();
+    // S' and its row maxima through the pinned staging, then into the
+    // host's arrays by all threads (which also spreads the first touch of
+    // their pages)
+    const size_t vbytes = nnz * sizeof(double), cbytes = nnz * sizeof(int), mbytes = mc * sizeof(double);
+    AJD_TRY(stage_.reserve(vbytes + cbytes + mbytes + 64));
+    char* hv = static_cast<char*>(stage_.p);
+    char* hc = hv + vbytes;
+    char* hm = hc + ((cbytes + 15) & ~(size_t)15);
+    AJD_CUDA(cudaMemcpyAsync(hv, nval_.p, vbytes, cudaMemcpyDeviceToHost, st_));
+    AJD_CUDA(cudaMemcpyAsync(hc, ncol_.p, cbytes, cudaMemcpyDeviceToHost, st_));
+    AJD_CUDA(cudaMemcpyAsync(hm, rowmax_.p, mbytes, cudaMemcpyDeviceToHost, st_));
     Sn.col.resize(nnz);
     Sn.val.resize(nnz);
     rowmax.resize(mc);
-    AJD_CUDA(cudaMemcpyAsync(Sn.col.data(), ncol_.p, nnz * sizeof(int), cudaMemcpyDeviceToHost, st_));
-    AJD_CUDA(cudaMemcpyAsync(Sn.val.data(), nval_.p, nnz * sizeof(double), cudaMemcpyDeviceToHost, st_));
-    AJD_CUDA(cudaMemcpyAsync(rowmax.data(), rowmax_.p, mc * sizeof(double), cudaMemcpyDeviceToHost, st_));
     AJD_TRY(sync());
+    {
+      const double* sv = reinterpret_cast<const double*>(hv);
+      const int* sc = reinterpret_cast<const int*>(hc);
+      double* dv = Sn.val.data();
+      int* dc = Sn.col.data();
+#pragma omp parallel for schedule(static)
+      for (int64_t b = 0; b < (nnz + 65535) / 65536; ++b) {
+        const int64_t i0 = b * 65536, i1 = std::min<int64_t>(nnz, i0 + 65536);
+        std::memcpy(dv + i0, sv + i0, (i1 - i0) * sizeof(double));
+        std::memcpy(dc + i0, sc + i0, (i1 - i0) * sizeof(int));
+      }
+      std::memcpy(rowmax.data(), hm, mbytes);
+    }
     if (verbose_)
       std::fprintf(stderr, "  gpu schur m=%d C=%d nnz'=%lld slots=%lld: bounds %.1f upload %.1f rows+count %.1f ptr %.1f "
                    "mirror %.1f download %.1f ms\n", lv.m, mc, (long long)nnz, (long long)off[mc], t_bounds,
@@ -536,6 +613,7 @@ class DeviceSchur final : public SchurEngine {
   DBuf<int> scol_, ncol_, cidx_, cnodes_, rblk_, crow_, gkeys_, ucol_, ucnt_, lowcnt_, cursor_;
   DBuf<double> sval_, nval_, dd_, c1_, c2_, bmat_, gvals_, uval_, rowmax_;
   DBuf<char> is2_;
+  Pinned stage_;
 };
 
 }  // namespace
