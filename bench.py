@@ -85,6 +85,8 @@ def parse():
     ap.add_argument("--serve-setup-threads", type=int, default=3)
     ap.add_argument("--setup-threads", type=int, default=2,
                     help="concurrent preconditioner builds in the pipelined batch")
+    ap.add_argument("--n-dense", type=int, default=0,
+                    help="rows of the preconditioner's dense tail (0: the library's default)")
     return ap.parse_args()
 
 
@@ -454,8 +456,10 @@ def main():
     ev_out = np.zeros(k)
     X_dev = torch.empty((k, n), device="cuda", dtype=torch.float64)
 
+    ildl_over = {"n_dense": args.n_dense} if args.n_dense > 0 else None
+
     def one(h, precision):
-        p = ajd.jd_params(precision=precision)
+        p = ajd.jd_params(precision=precision, ildl=ildl_over)
         st = ajd._ffi.JdStats()
         rc = ajd._ffi.lib().jd_solve(h.handle, sigma, k, tol, ajd.ctypes.byref(p),
                                      ev_out.ctypes.data_as(ajd.ctypes.c_void_p),
@@ -473,7 +477,7 @@ def main():
         if args.method == "lanczos":
             out = []
             for i in range(m):
-                p = ajd.jd_params(precision=precision)
+                p = ajd.jd_params(precision=precision, ildl=ildl_over)
                 st = ajd._ffi.JdStats()
                 hv = handles[i] if isinstance(handles[i], vp) else vp(handles[i])
                 rc = ajd._ffi.lib().jd_lanczos_solve(hv, sigma, k, tol, ajd.ctypes.byref(p), vp(ev_bufs[i]),
@@ -487,7 +491,7 @@ def main():
         ep = (vp * m)(*ev_bufs)
         xp = (vp * m)(*x_bufs)
         sts = (ajd._ffi.JdStats * m)()
-        p = ajd.jd_params(precision=precision)
+        p = ajd.jd_params(precision=precision, ildl=ildl_over)
         rc = ajd._ffi.lib().jd_solve_batch(hs, m, sig, kk, tol, ajd.ctypes.byref(p), ep, xp, sts,
                                            args.setup_threads, vp(stream.cuda_stream))
         ajd._ffi.check(rc, "jd_solve_batch")
@@ -672,7 +676,8 @@ def main():
                                "restarts": [s["restarts"] for s in stats]},
                 "max_residual": max(s["max_residual"] for s in stats),
                 "preconditioner": {"levels": info["levels"], "n_dense": info["n_dense"], "nnz_L": info["nnz_L"],
-                                   "fill": info["fill"], "n_2x2": info["n_2x2"]},
+                                   "fill": info["fill"], "n_2x2": info["n_2x2"],
+                                   "apply_threads_per_row_shift": [s["ildl"]["apply_shift"] for s in stats]},
                 "fp64": fp64, "e2e": e2e, "roofline": roofline, "batch": batch_c4, "serving": serving,
                 "stencil": {"precision": stencil_prec, "bytes_per_site": stencil_bps, "sites": n,
                             "calls": stencil_calls, "avg_ms": stencil_ms / stencil_calls if stencil_calls else None,

@@ -194,6 +194,10 @@ typedef struct {
                      device for ildl_setup_csr), 0 = on the host threads,
                      < 0 = GPU for ildl_create and host for ildl_setup_csr.
                      Both give the same factor bit for bit [-1]         */
+  int autotune;   /* ildl_create only: time the apply with the threads-per-
+                     row rule scaled by 1/2, 1 and 2 on the device and keep
+                     the fastest (factors of at least 200,000 rows; about a
+                     dozen applies); 0 = off, else on [-1]                   */
 } ildl_params;
 
 /* Fill *p with the defaults above. */
@@ -222,6 +226,8 @@ typedef struct {
   double max_abs_L;  /* largest |entry| of L (after the global scaling)     */
   int64_t aggressive_dropped; /* entries removed by aggressive dropping
                         (ildl_params.aggressive; 0 when off)                */
+  int apply_shift;   /* autotuned threads per row of the apply: the rule's
+                        choice times 2^apply_shift (-1, 0 or 1; 0 untuned) */
 } ildl_info_t;
 
 /*

@@ -103,6 +103,26 @@ gram_bf16_kernel(const __nv_bfloat16* __restrict__ X1, int c1, const __nv_bfloat
   const int64_t r0 = (int64_t)blockIdx.x * rows_per_cta;
   const int64_t r1 = std::min<int64_t>(n, r0 + rows_per_cta);
   const int nchunks = r1 > r0 ? (int)((r1 - r0 + kGramChunk - 1) / kGramChunk) : 0;
+  // the next chunk's operands are loaded into registers while the tensor
+  // cores work on the current one: A as 16-byte pieces (8 rows of one
+  // column of X; the shadow is zero-padded to ldb), B as one value of t
+  constexpr int kPieces = kGramM * 8 / kGramThreads;  // 16-byte pieces per thread
+  uint4 pre[kPieces];
+  double tv = 0.0;
+  auto load_chunk = [&](int k) {
+    const int64_t i0 = r0 + (int64_t)k * kGramChunk;
+#pragma unroll
+    for (int q = 0; q < kPieces; ++q) {
+      const int idx = tid + q * kGramThreads;
+      if (idx < c * 8) {
+        const int j = idx >> 3, kk = (idx & 7) * 8;
+        const __nv_bfloat16* col = j < c1 ? X1 + (int64_t)j * ldb : X2 + (int64_t)(j - c1) * ldb;
+        pre[q] = *reinterpret_cast<const uint4*>(col + i0 + kk);
+      }
+    }
+    if (tid < kGramChunk) tv = i0 + tid < n ? t[i0 + tid] : 0.0;
+  };
+  if (nchunks > 0) load_chunk(0);
   for (int k = 0; k < nchunks; ++k) {
     const int buf = k & 1;
     const uint32_t mb = buf ? mbar1 : mbar0;
@@ -111,24 +131,17 @@ gram_bf16_kernel(const __nv_bfloat16* __restrict__ X1, int c1, const __nv_bfloat
     }
     __syncthreads();
     if (s_fail) break;
-    const int64_t i0 = r0 + (int64_t)k * kGramChunk;
-    // A: column j of X, rows i0 .. i0 + 63, as row j of the tile (16-byte
-    // pieces: 8 rows of the column); the shadow is zero-padded to ldb
-    for (int idx = tid; idx < c * 8; idx += kGramThreads) {
-      const int j = idx >> 3, kk = (idx & 7) * 8;
-      const __nv_bfloat16* col = j < c1 ? X1 + (int64_t)j * ldb : X2 + (int64_t)(j - c1) * ldb;
-      const uint4 v = *reinterpret_cast<const uint4*>(col + i0 + kk);
-      *reinterpret_cast<uint4*>(&sA[buf][tile_off(j, kk)]) = v;
+    // A: column j of X, rows of the chunk, as row j of the tile; B: tb as row 0
+#pragma unroll
+    for (int q = 0; q < kPieces; ++q) {
+      const int idx = tid + q * kGramThreads;
+      if (idx < c * 8) *reinterpret_cast<uint4*>(&sA[buf][tile_off(idx >> 3, (idx & 7) * 8)]) = pre[q];
     }
-    // B: tb as row 0
-    if (tid < kGramChunk) {
-      const int64_t i = i0 + tid;
-      const __nv_bfloat16 v = __double2bfloat16(i < n ? t[i] : 0.0);
-      *reinterpret_cast<__nv_bfloat16*>(&sB[buf][tile_off(0, tid)]) = v;
-    }
+    if (tid < kGramChunk) *reinterpret_cast<__nv_bfloat16*>(&sB[buf][tile_off(0, tid)]) = __double2bfloat16(tv);
     // the generic-proxy writes above become visible to the tensor cores
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
+    if (k + 1 < nchunks) load_chunk(k + 1);
     if (tid == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint32_t a0 = (uint32_t)__cvta_generic_to_shared(&sA[buf][0]);
@@ -237,7 +250,7 @@ extern "C" int jd_gram_bf16(const double* X, int64_t ldx, int c, const double* t
   if (c == 0) return JD_OK;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const int64_t ldb = gram_bf16_ld(n);
-  const int nparts = 2 * sm_count();
+  const int nparts = 4 * sm_count();
   void* Xb = nullptr;
   double *partial = nullptr, *dout = nullptr;
   int* err = nullptr;

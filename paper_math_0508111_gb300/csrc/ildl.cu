@@ -179,6 +179,54 @@ int upload(D** dst, const std::vector<S, Alloc>& src, cudaStream_t st) {
   return JD_OK;
 }
 
+// Phase list of the persistent apply for factor F.  Threads per row: enough
+// rows in flight to cover the grid, and about four stored entries per thread
+// of a row (a power of two in 1..512), times 2^shift (the autotuner's knob).
+// Each phase's rows start at the CTA after the last one the previous phase
+// used (round robin over the grid), so that the CTAs of a small phase are
+// idle while the level before it is computed and have its loads in flight by
+// then; the first CTA goes in the high half of .w, the number of CTAs that
+// own rows (the phase's participants, which signal its completion) in the
+// high bits of .x.  Level 0 (rows without entries) only forms w = s b[perm];
+// later forward rows form their right-hand side s[p] b[perm[p]] themselves.
+std::vector<int4> build_phase_list(const HostFactor& F, int shift) {
+  std::vector<int4> ph;
+  const std::vector<int>& lvp = F.level_ptr;
+  const int nl = F.nlev;
+  const double threads_total = (double)sm_count() * kPersistThreads;
+  auto pick_g = [&](int rows, double avg) {
+    const double want = std::max(std::min(threads_total / std::max(rows, 1), avg / 4.0), std::min(avg / 8.0, 32.0));
+    int g = 1;
+    while (g < 512 && 2 * g <= want) g *= 2;
+    for (int i = 0; i < shift && g < 512; ++i) g *= 2;
+    for (int i = 0; i > shift && g > 1; --i) g /= 2;
+    return g;
+  };
+  const int grid = sm_count();
+  int cursor = 0;
+  auto add_phase = [&](int kind, int p0, int p1, int g) {
+    const int64_t threads = (int64_t)(p1 - p0) * (kind == PH_DENSE ? 32 : g);
+    const int ctas = (int)std::min<int64_t>(grid, (threads + kPersistThreads - 1) / kPersistThreads);
+    ph.push_back(make_int4(kind | (ctas << 8), p0, p1, g | (cursor << 16)));
+    cursor = (cursor + ctas) % grid;
+  };
+  add_phase(PH_GATHER, lvp[0], lvp[1], 1);
+  for (int l = 1; l <= nl; ++l) {
+    const int p0 = lvp[l], p1 = lvp[l + 1];
+    if (p1 <= p0) continue;
+    const double avg = (double)(F.Lptr[p1] - F.Lptr[p0]) / (p1 - p0);
+    add_phase(PH_FWD, p0, p1, pick_g(p1 - p0, avg));
+  }
+  if (F.n_dense > 0) add_phase(PH_DENSE, lvp[nl], lvp[nl + 1], 32);
+  for (int l = nl - 1; l >= 0; --l) {
+    const int p0 = lvp[l], p1 = lvp[l + 1];
+    if (p1 <= p0) continue;
+    const double avg = (double)(F.Uptr[p1] - F.Uptr[p0]) / (p1 - p0);
+    add_phase(PH_BWD, p0, p1, pick_g(p1 - p0, avg));
+  }
+  return ph;
+}
+
 template <typename T>
 int upload_factor(const HostFactor& F, DevFactor<T>& d, cudaStream_t st) {
   if (F.Lcol.size() >= (size_t)1 << 31) return fail(JD_ENOMEM, "ildl: factor has more than 2^31 entries");
@@ -211,51 +259,9 @@ int upload_factor(const HostFactor& F, DevFactor<T>& d, cudaStream_t st) {
       AJD_CUDA(cudaMemsetAsync(d.zdf, 0xFF, nb * sizeof(float2), st));
     }
   }
-  // phase list of the persistent apply
-  std::vector<int4> ph;
-  const std::vector<int>& lvp = F.level_ptr;
-  const int nl = F.nlev;
-  // threads per row: enough rows in flight to cover the grid, and about four
-  // stored entries per thread of a row (a power of two in 1..512)
-  const double threads_total = (double)sm_count() * kPersistThreads;
-  auto pick_g = [&](int rows, double avg) {
-    // (a phase of many long rows keeps up to a warp per row: each thread then
-    // works through several rows, eight entries per batch)
-    const double want = std::max(std::min(threads_total / std::max(rows, 1), avg / 4.0), std::min(avg / 8.0, 32.0));
-    int g = 1;
-    while (g < 512 && 2 * g <= want) g *= 2;
-    return g;
-  };
-  // level 0 (rows without entries): w = s b[perm]; later forward rows form
-  // their right-hand side s[p] b[perm[p]] themselves
-  // each phase's rows start at the CTA after the last one the previous
-  // phase used (round robin over the grid), so that the CTAs of a small
-  // phase are idle while the level before it is computed and have its
-  // loads in flight by then; the first CTA goes in the high half of .w
-  const int grid = sm_count();
-  int cursor = 0;
-  // the CTAs that own rows of a phase (its participants, which signal its
-  // completion) go in the high bits of .x
-  auto add_phase = [&](int kind, int p0, int p1, int g) {
-    const int64_t threads = (int64_t)(p1 - p0) * (kind == PH_DENSE ? 32 : g);
-    const int ctas = (int)std::min<int64_t>(grid, (threads + kPersistThreads - 1) / kPersistThreads);
-    ph.push_back(make_int4(kind | (ctas << 8), p0, p1, g | (cursor << 16)));
-    cursor = (cursor + ctas) % grid;
-  };
-  add_phase(PH_GATHER, lvp[0], lvp[1], 1);
-  for (int l = 1; l <= nl; ++l) {
-    const int p0 = lvp[l], p1 = lvp[l + 1];
-    if (p1 <= p0) continue;
-    const double avg = (double)(F.Lptr[p1] - F.Lptr[p0]) / (p1 - p0);
-    add_phase(PH_FWD, p0, p1, pick_g(p1 - p0, avg));
-  }
-  if (F.n_dense > 0) add_phase(PH_DENSE, lvp[nl], lvp[nl + 1], 32);
-  for (int l = nl - 1; l >= 0; --l) {
-    const int p0 = lvp[l], p1 = lvp[l + 1];
-    if (p1 <= p0) continue;
-    const double avg = (double)(F.Uptr[p1] - F.Uptr[p0]) / (p1 - p0);
-    add_phase(PH_BWD, p0, p1, pick_g(p1 - p0, avg));
-  }
+  // phase list of the persistent apply (threads-per-row rule unscaled; the
+  // autotuner may replace it once the factor is on the device)
+  const std::vector<int4> ph = build_phase_list(F, 0);
   d.nphase = (int)ph.size();
   AJD_CUDA(cudaMalloc(&d.phases, std::max<size_t>(1, ph.size()) * sizeof(int4)));
   if (!ph.empty()) {
@@ -283,6 +289,7 @@ cudaEvent_t g_chain_last = nullptr;  // completion of the last serialised apply
 }  // namespace
 
 void set_apply_serialization(bool on) { tl_serialize_applies = on; }
+bool apply_serialization() { return tl_serialize_applies; }
 
 // One persistent apply with factor values V, work vectors X, caller vectors IO.
 template <typename V, typename X, typename IO>
@@ -414,13 +421,109 @@ int invert_dense_on_device(dvec<double>& M, int m, cudaStream_t st) {
   return rc;
 }
 
-int ildl_upload_all(ildl_s* f, cudaStream_t st, int copies) {
+namespace {
+
+// Autotuning of the apply's threads per row, per factor: the rule's phase
+// list and the lists with every level's threads per row halved and doubled
+// are each timed on the device (CUDA events on the setup stream: one
+// warm-up and three timed applies of a zero vector, the apply's work does
+// not depend on the values) and the fastest is kept.  The timed applies join
+// the chain that orders the applies of concurrent solves, so they never run
+// beside one.  Only factors of at least kTuneMinRows rows are tuned (below,
+// a whole apply takes tens of microseconds and the choice matters little).
+constexpr int kTuneMinRows = 200000;
+
+template <typename T>
+int autotune_apply(ildl_s* f, DevFactor<T>& d, cudaStream_t st) {
+  const HostFactor& F = f->F;
+  if (F.n < kTuneMinRows || d.nphase == 0) return JD_OK;
+  double* b = nullptr;
+  double* x = nullptr;
+  int4* cand = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  const bool was = tl_serialize_applies;
+  tl_serialize_applies = true;
+  int rc = JD_OK;
+  auto run = [&](double* ms) -> int {
+    for (int rep = 0; rep < 4; ++rep) {
+      if (rep == 1) AJD_CUDA(cudaEventRecord(e0, st));
+      if constexpr (sizeof(T) == 8) {
+        AJD_TRY((launch_apply<double, double, double>(f, d, d.w, d.z, b, x, st)));
+      } else {
+        AJD_TRY((launch_apply<float, df64, double>(f, d, reinterpret_cast<df64*>(d.wdf), reinterpret_cast<df64*>(d.zdf),
+                                                   b, x, st)));
+      }
+    }
+    AJD_CUDA(cudaEventRecord(e1, st));
+    AJD_CUDA(cudaEventSynchronize(e1));
+    float t = 0.f;
+    AJD_CUDA(cudaEventElapsedTime(&t, e0, e1));
+    *ms = t / 3.0;
+    return JD_OK;
+  };
+  auto body = [&]() -> int {
+    AJD_CUDA(cudaMalloc(&b, sizeof(double) * (size_t)F.n));
+    AJD_CUDA(cudaMalloc(&x, sizeof(double) * (size_t)F.n));
+    AJD_CUDA(cudaMalloc(&cand, sizeof(int4) * (size_t)d.nphase));
+    AJD_CUDA(cudaMemsetAsync(b, 0, sizeof(double) * (size_t)F.n, st));
+    AJD_CUDA(cudaEventCreate(&e0));
+    AJD_CUDA(cudaEventCreate(&e1));
+    int best = 0;
+    double best_ms = 0.0;
+    AJD_TRY(run(&best_ms));
+    f->F.apply_tune_ms[1] = best_ms;
+    for (int shift : {-1, 1}) {
+      const std::vector<int4> ph = build_phase_list(F, shift);
+      AJD_CUDA(cudaMemcpyAsync(cand, ph.data(), ph.size() * sizeof(int4), cudaMemcpyHostToDevice, st));
+      std::swap(d.phases, cand);
+      double ms = 0.0;
+      const int r = run(&ms);
+      std::swap(d.phases, cand);
+      AJD_TRY(r);
+      f->F.apply_tune_ms[shift + 1] = ms;
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = shift;
+      }
+    }
+    if (best != 0) {
+      const std::vector<int4> ph = build_phase_list(F, best);
+      AJD_CUDA(cudaMemcpyAsync(d.phases, ph.data(), ph.size() * sizeof(int4), cudaMemcpyHostToDevice, st));
+    }
+    f->F.apply_shift = best;
+    AJD_CUDA(cudaStreamSynchronize(st));
+    return JD_OK;
+  };
+  rc = body();
+  tl_serialize_applies = was;
+  cudaFree(b);
+  cudaFree(x);
+  cudaFree(cand);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  return rc;
+}
+
+}  // namespace
+
+int ildl_upload_all(ildl_s* f, cudaStream_t st, int copies, bool tune) {
   if (f->F.dense_is_matrix) {
     AJD_TRY(invert_dense_on_device(f->F.dense_inv, f->F.n_dense, st));
     f->F.dense_is_matrix = false;
   }
   if (copies & kCopyF64) AJD_TRY(upload_factor<double>(f->F, f->d64, st));
   if (copies & kCopyF32) AJD_TRY(upload_factor<float>(f->F, f->d32, st));
+  if (tune) {
+    // tuned on the copy a solve uses first (binary32 for the mixed and
+    // binary32 solves); the other copy takes the same choice
+    if (copies & kCopyF32) AJD_TRY(autotune_apply<float>(f, f->d32, st));
+    else if (copies & kCopyF64) AJD_TRY(autotune_apply<double>(f, f->d64, st));
+    if ((copies & kCopyF32) && (copies & kCopyF64) && f->F.apply_shift != 0) {
+      const std::vector<int4> ph = build_phase_list(f->F, f->F.apply_shift);
+      AJD_CUDA(cudaMemcpyAsync(f->d64.phases, ph.data(), ph.size() * sizeof(int4), cudaMemcpyHostToDevice, st));
+      AJD_CUDA(cudaStreamSynchronize(st));
+    }
+  }
   return JD_OK;
 }
 
@@ -499,6 +602,7 @@ extern "C" int ildl_params_default(ildl_params* p) {
   p->matching = -1;
   p->aggressive = 0.0;
   p->setup_device = -1;
+  p->autotune = -1;
   return JD_OK;
 }
 
@@ -637,7 +741,7 @@ int ildl_create_on_stream(anderson_t h, double sigma, const ildl_params* p, ildl
     if (prm.setup_device != 0) eng = make_device_schur(st);
     int rc = build_ildl(A, prm, f->F, /*dense_on_host=*/false, eng.get());
     eng.reset();
-    if (rc == JD_OK) rc = ildl_upload_all(f, st, copies);
+    if (rc == JD_OK) rc = ildl_upload_all(f, st, copies, prm.autotune != 0);
     f->F.t_total_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     if (rc != JD_OK) {
       ildl_free_device(f);
@@ -672,6 +776,7 @@ extern "C" int ildl_info(ildl_t f, ildl_info_t* info) {
   info->relaxed_levels = F.n_relaxed;
   info->max_abs_L = F.max_abs_L;
   info->aggressive_dropped = F.n_aggressive;
+  info->apply_shift = F.apply_shift;
   return JD_OK;
 }
 

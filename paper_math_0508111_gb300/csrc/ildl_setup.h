@@ -74,6 +74,8 @@ struct HostFactor {
   double max_abs_L = 0.0;         // largest |entry| of the global L
   int64_t nnz_A = 0;
   double t_match_ms = 0, t_factor_ms = 0, t_total_ms = 0;
+  int apply_shift = 0;            // autotuned threads-per-row scale of the apply, log2
+  double apply_tune_ms[3] = {0, 0, 0};  // apply time with shift -1, 0, +1 (0 = not tuned)
   std::vector<int> level_sizes;   // rows eliminated per sparse level
 };
 

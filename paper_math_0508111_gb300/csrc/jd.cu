@@ -31,6 +31,7 @@
 #include "anderson_impl.cuh"
 #include "ildl_impl.cuh"
 #include "gram_bf16.h"
+#include "jd_impl.cuh"
 
 namespace ajd {
 namespace {
@@ -1719,6 +1720,14 @@ extern "C" int jd_solve_batch(const anderson_t* hs, int nprob, const double* sig
 
   int status = JD_OK;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  // this thread's applies join the chain that the setup threads' autotuning
+  // applies join too, so no two cooperative applies run at once
+  const bool serialized = apply_serialization();
+  set_apply_serialization(true);
+  struct Restore {
+    bool v;
+    ~Restore() { set_apply_serialization(v); }
+  } restore{serialized};
   for (int i = 0; i < nprob; ++i) {
     {
       std::unique_lock<std::mutex> lk(mu);

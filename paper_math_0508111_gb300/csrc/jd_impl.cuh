@@ -17,5 +17,6 @@ int solve_problem(anderson_s* h, ildl_s* pc, const jd_params& prm, double sigma,
 // thread with those of every other thread that set it (a device-side chain
 // of events): used by threads that solve concurrently on their own streams.
 void set_apply_serialization(bool on);
+bool apply_serialization();
 
 }  // namespace ajd

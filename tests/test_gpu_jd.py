@@ -79,6 +79,21 @@ def test_ildl_apply_matches_oracle(ajd, L, bc, sigma, nd):
         P.close()
 
 
+def test_ildl_apply_autotuned(ajd):
+    """A factor of more than 200,000 rows has its apply's threads per row
+    tuned on the device (the rule's choice times 1/2, 1 or 2, whichever
+    runs fastest); whatever the choice, the apply equals the oracle's."""
+    with ajd.Anderson(60, 16.5, 4) as h:
+        P = ajd.Preconditioner.from_lattice(h, 0.2)
+        assert P.info()["apply_shift"] in (-1, 0, 1)
+        b = np.random.default_rng(5).standard_normal(h.n)
+        check_apply_errors(apply_errors(P, P.export(), b))
+        P.close()
+        P0 = ajd.Preconditioner.from_lattice(h, 0.2, autotune=0)
+        assert P0.info()["apply_shift"] == 0
+        P0.close()
+
+
 def test_ildl_apply_wide_rows(ajd):
     """A factor without dropping has few, long rows on its deepest levels:
     those phases run with 64..512 threads per row (CTA-wide rows with a
