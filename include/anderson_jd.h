@@ -194,10 +194,17 @@ typedef struct {
                      device for ildl_setup_csr), 0 = on the host threads,
                      < 0 = GPU for ildl_create and host for ildl_setup_csr.
                      Both give the same factor bit for bit [-1]         */
-  int autotune;   /* ildl_create only: time the apply with the threads-per-
-                     row rule scaled by 1/2, 1 and 2 on the device and keep
-                     the fastest (factors of at least 200,000 rows; about a
-                     dozen applies); 0 = off, else on [-1]                   */
+  int autotune;   /* ildl_create only: time the apply in each form of
+                     apply_form with the threads-per-row rule scaled by 1/2,
+                     1 and 2 on the device and keep the fastest (factors of
+                     at least 200,000 rows; four applies per candidate);
+                     0 = off, else on [-1]                                   */
+  int apply_form; /* kernel of ildl_apply (the same x in either form, up to
+                     the rounding of the row sums): 0 = level sweeps with a
+                     completion count per level; 1 = dataflow, every row
+                     starts once the entries it reads are written (no
+                     per-level synchronisation); < 0 = chosen by the
+                     autotuner where it runs, else 1 [-1]                    */
 } ildl_params;
 
 /* Fill *p with the defaults above. */
@@ -228,6 +235,7 @@ typedef struct {
                         (ildl_params.aggressive; 0 when off)                */
   int apply_shift;   /* autotuned threads per row of the apply: the rule's
                         choice times 2^apply_shift (-1, 0 or 1; 0 untuned) */
+  int apply_form;    /* apply kernel in use (ildl_params.apply_form)        */
 } ildl_info_t;
 
 /*

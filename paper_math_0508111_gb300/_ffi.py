@@ -33,14 +33,14 @@ class JDError(RuntimeError):
 class IldlParams(ctypes.Structure):
     _fields_ = [("kappa", c_double), ("drop", c_double), ("gamma", c_double), ("max_levels", c_int),
                 ("n_dense", c_int), ("matching", c_int), ("aggressive", c_double), ("setup_device", c_int),
-                ("autotune", c_int)]
+                ("autotune", c_int), ("apply_form", c_int)]
 
 
 class IldlInfo(ctypes.Structure):
     _fields_ = [("n", c_int), ("levels", c_int), ("n_dense", c_int), ("n_2x2", c_int), ("nnz_L", c_int64),
                 ("nnz_A", c_int64), ("fill", c_double), ("setup_ms", c_double), ("match_ms", c_double),
                 ("relaxed_levels", c_int), ("max_abs_L", c_double), ("aggressive_dropped", c_int64),
-                ("apply_shift", c_int)]
+                ("apply_shift", c_int), ("apply_form", c_int)]
 
 
 class JdParams(ctypes.Structure):

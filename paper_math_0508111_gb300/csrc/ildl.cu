@@ -26,6 +26,7 @@
 #include "jd_impl.cuh"
 #include "ildl_setup.h"
 #include "ildl_apply_kernel.cuh"
+#include "ildl_apply_dataflow.cuh"
 #include "schur_gpu.h"
 
 namespace ajd {
@@ -44,6 +45,10 @@ namespace {
 // Ordinary launches, so the setup of one problem shares the GPU with the
 // solves of others.  A zero or non-finite pivot sets *bad.
 constexpr int kGjPivotThreads = 1024;
+
+// Apply form of factors that are not autotuned (ildl_params.apply_form < 0):
+// 1 = the dataflow kernel, 0 = the level-counter kernel.
+constexpr int kDefaultApplyForm = 1;
 
 __global__ void __launch_bounds__(kGjPivotThreads)
 gj_pivot_step_kernel(double* __restrict__ A, double* __restrict__ X, int m, int c, double* __restrict__ f,
@@ -152,6 +157,7 @@ void free_dev(DevFactor<T>& d) {
   cudaFree(d.w);
   cudaFree(d.z);
   cudaFree(d.phases);
+  cudaFree(d.units);
   cudaFree(d.bar);
   cudaFree(d.done);
   cudaFree(d.wdf);
@@ -227,6 +233,61 @@ std::vector<int4> build_phase_list(const HostFactor& F, int shift) {
   return ph;
 }
 
+// Unit segments of the dataflow apply for factor F, in the order the units
+// are taken: level 0 (32 rows per unit), the forward levels, the dense tail
+// (one row per unit), the backward levels from the last to level 0.  Lanes
+// per row: about four stored entries per lane (a power of two in 1..32),
+// times 2^shift.  Each int4 is (kind | G << 8, first row, end row, first
+// unit); *nunits receives the total.
+std::vector<int4> build_flow_list(const HostFactor& F, int shift, int* nunits) {
+  std::vector<int4> seg;
+  const std::vector<int>& lvp = F.level_ptr;
+  const int nl = F.nlev;
+  auto pick_g = [&](double avg) {
+    int g = 1;
+    while (g < 32 && 2 * g <= avg / 4.0) g *= 2;
+    for (int i = 0; i < shift && g < 32; ++i) g *= 2;
+    for (int i = 0; i > shift && g > 1; --i) g /= 2;
+    return g;
+  };
+  int64_t u = 0;
+  auto add = [&](int kind, int p0, int p1, int g) {
+    const int per = kind == PH_DENSE ? 1 : 32 / g;  // rows per unit
+    seg.push_back(make_int4(kind | (g << 8), p0, p1, (int)u));
+    u += (p1 - p0 + per - 1) / per;
+  };
+  add(PH_GATHER, lvp[0], lvp[1], 1);
+  for (int l = 1; l <= nl; ++l) {
+    const int p0 = lvp[l], p1 = lvp[l + 1];
+    if (p1 <= p0) continue;
+    add(PH_FWD, p0, p1, pick_g((double)(F.Lptr[p1] - F.Lptr[p0]) / (p1 - p0)));
+  }
+  if (F.n_dense > 0) add(PH_DENSE, lvp[nl], lvp[nl + 1], 32);
+  for (int l = nl - 1; l >= 0; --l) {
+    const int p0 = lvp[l], p1 = lvp[l + 1];
+    if (p1 <= p0) continue;
+    add(PH_BWD, p0, p1, pick_g((double)(F.Uptr[p1] - F.Uptr[p0]) / (p1 - p0)));
+  }
+  *nunits = (int)u;
+  return seg;
+}
+
+template <typename T>
+int upload_dataflow_units(const HostFactor& F, DevFactor<T>& d, int shift, cudaStream_t st) {
+  int nu = 0;
+  const std::vector<int4> seg = build_flow_list(F, shift, &nu);
+  if (!d.units || (int)seg.size() != d.nseg) {
+    cudaFree(d.units);
+    d.units = nullptr;
+    AJD_CUDA(cudaMalloc(&d.units, std::max<size_t>(1, seg.size()) * sizeof(int4)));
+  }
+  if (!seg.empty()) AJD_CUDA(cudaMemcpyAsync(d.units, seg.data(), seg.size() * sizeof(int4), cudaMemcpyHostToDevice, st));
+  AJD_CUDA(cudaStreamSynchronize(st));
+  d.nseg = (int)seg.size();
+  d.nunits = nu;
+  return JD_OK;
+}
+
 template <typename T>
 int upload_factor(const HostFactor& F, DevFactor<T>& d, cudaStream_t st) {
   if (F.Lcol.size() >= (size_t)1 << 31) return fail(JD_ENOMEM, "ildl: factor has more than 2^31 entries");
@@ -274,9 +335,13 @@ int upload_factor(const HostFactor& F, DevFactor<T>& d, cudaStream_t st) {
   AJD_CUDA(cudaMalloc(&d.done, std::max<size_t>(1, ph.size()) * sizeof(unsigned)));
   AJD_CUDA(cudaMemsetAsync(d.bar, 0, 96 * sizeof(unsigned), st));
   AJD_CUDA(cudaStreamSynchronize(st));
-  int per_sm = 0;
+  AJD_TRY(upload_dataflow_units(F, d, 0, st));
+  d.form = F.apply_form;
+  int per_sm = 0, per_sm_flow = 0;
   AJD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ildl_apply_persistent_kernel<T, T, T>, kPersistThreads, 0));
-  if (per_sm < 1) return fail(JD_EDEVICE, "ildl: persistent apply kernel cannot be resident");
+  AJD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_flow, ildl_apply_dataflow_kernel<T, T, T>,
+                                                         kPersistThreads, 0));
+  if (per_sm < 1 || per_sm_flow < 1) return fail(JD_EDEVICE, "ildl: persistent apply kernel cannot be resident");
   d.grid = sm_count();  // one CTA per SM
   d.ready = true;
   return JD_OK;
@@ -291,12 +356,54 @@ cudaEvent_t g_chain_last = nullptr;  // completion of the last serialised apply
 void set_apply_serialization(bool on) { tl_serialize_applies = on; }
 bool apply_serialization() { return tl_serialize_applies; }
 
-// One persistent apply with factor values V, work vectors X, caller vectors IO.
+// Cooperative launch of `kernel` on d.grid CTAs, ordered behind the
+// previous serialised apply when this thread serialises its applies.
+template <typename V>
+int launch_cooperative(const DevFactor<V>& d, const void* kernel, void** args, cudaStream_t s) {
+  if (tl_serialize_applies) {
+    // concurrent solvers: this apply starts on the device only after the
+    // previous serialised apply (of any thread) has finished, so no two of
+    // these grid-wide cooperative kernels ever run at the same time
+    std::lock_guard<std::mutex> lk(g_chain_mu);
+    if (g_chain_last) AJD_CUDA(cudaStreamWaitEvent(s, g_chain_last, 0));
+    AJD_CUDA(cudaLaunchCooperativeKernel(kernel, dim3(d.grid), dim3(kPersistThreads), args, 0, s));
+    cudaEvent_t ev = nullptr;
+    AJD_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    AJD_CUDA(cudaEventRecord(ev, s));
+    if (g_chain_last) cudaEventDestroy(g_chain_last);  // released once it has completed
+    g_chain_last = ev;
+  } else {
+    AJD_CUDA(cudaLaunchCooperativeKernel(kernel, dim3(d.grid), dim3(kPersistThreads), args, 0, s));
+  }
+  return JD_OK;
+}
+
+// One dataflow apply: w and z filled with the "not yet written" sentinel,
+// then the kernel.
+template <typename V, typename X, typename IO>
+int launch_apply_dataflow(const ildl_s* f, const DevFactor<V>& d, X* w, X* z, const IO* b, IO* out, cudaStream_t s) {
+  const HostFactor& F = f->F;
+  ApplyArgs<V, X, IO> a{d.perm, d.scale, d.Lptr, d.Lcol, d.Lval, d.Uptr, d.Ucol, d.Uval, d.dd, d.dof, d.partner,
+                        d.dense, w, z, b, out, F.n_dense, F.level_ptr[F.nlev]};
+  AJD_CUDA(cudaMemsetAsync(w, 0xFF, (size_t)F.n * sizeof(X), s));
+  AJD_CUDA(cudaMemsetAsync(z, 0xFF, (size_t)F.n * sizeof(X), s));
+  const int4* units = d.units;
+  int nseg = d.nseg, nunits = d.nunits;
+  int* err = reinterpret_cast<int*>(d.bar + 64);
+  void* args[] = {&a, &units, &nseg, &nunits, &err};
+  AJD_TRY(launch_cooperative(d, (const void*)ildl_apply_dataflow_kernel<V, X, IO>, args, s));
+  count_launches(3);
+  return JD_OK;
+}
+
+// One persistent apply with factor values V, work vectors X, caller vectors
+// IO, in the factor's apply form.
 template <typename V, typename X, typename IO>
 int launch_apply(const ildl_s* f, const DevFactor<V>& d, X* w, X* z, const IO* b, IO* out, cudaStream_t s) {
   if (!d.ready) return fail(JD_EINVAL, "ildl_apply: factor has no device copy (use ildl_create)");
   const HostFactor& F = f->F;
   if (F.n == 0 || d.nphase == 0) return JD_OK;
+  if (d.form == 1) return launch_apply_dataflow<V, X, IO>(f, d, w, z, b, out, s);
   ApplyArgs<V, X, IO> a{d.perm, d.scale, d.Lptr, d.Lcol, d.Lval, d.Uptr, d.Ucol, d.Uval, d.dd, d.dof, d.partner,
                         d.dense, w, z, b, out, F.n_dense, F.level_ptr[F.nlev]};
   // the phases' completion counters start at zero
@@ -311,23 +418,7 @@ int launch_apply(const ildl_s* f, const DevFactor<V>& d, X* w, X* z, const IO* b
   unsigned long long* stamps = nullptr;
   if (timing) AJD_CUDA(cudaMalloc(&stamps, (np + 1) * sizeof(unsigned long long)));
   void* args[] = {&a, &ph, &np, &done, &err, &stamps};
-  if (tl_serialize_applies) {
-    // concurrent solvers: this apply starts on the device only after the
-    // previous serialised apply (of any thread) has finished, so no two of
-    // these grid-wide cooperative kernels ever run at the same time
-    std::lock_guard<std::mutex> lk(g_chain_mu);
-    if (g_chain_last) AJD_CUDA(cudaStreamWaitEvent(s, g_chain_last, 0));
-    AJD_CUDA(cudaLaunchCooperativeKernel((void*)ildl_apply_persistent_kernel<V, X, IO>, dim3(d.grid),
-                                         dim3(kPersistThreads), args, 0, s));
-    cudaEvent_t ev = nullptr;
-    AJD_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
-    AJD_CUDA(cudaEventRecord(ev, s));
-    if (g_chain_last) cudaEventDestroy(g_chain_last);  // released once it has completed
-    g_chain_last = ev;
-  } else {
-    AJD_CUDA(cudaLaunchCooperativeKernel((void*)ildl_apply_persistent_kernel<V, X, IO>, dim3(d.grid),
-                                         dim3(kPersistThreads), args, 0, s));
-  }
+  AJD_TRY(launch_cooperative(d, (const void*)ildl_apply_persistent_kernel<V, X, IO>, args, s));
   count_launches(2);
   if (timing) {
     std::vector<unsigned long long> t(np + 1);
@@ -423,23 +514,35 @@ int invert_dense_on_device(dvec<double>& M, int m, cudaStream_t st) {
 
 namespace {
 
-// Autotuning of the apply's threads per row, per factor: the rule's phase
-// list and the lists with every level's threads per row halved and doubled
-// are each timed on the device (CUDA events on the setup stream: one
-// warm-up and three timed applies of a zero vector, the apply's work does
-// not depend on the values) and the fastest is kept.  The timed applies join
-// the chain that orders the applies of concurrent solves, so they never run
-// beside one.  Only factors of at least kTuneMinRows rows are tuned (below,
-// a whole apply takes tens of microseconds and the choice matters little).
+// Autotuning of the apply, per factor: both apply forms (level counters,
+// dataflow), each with the rule's threads per row and with every level's
+// threads per row halved and doubled, are timed on the device (CUDA events
+// on the setup stream: one warm-up and three timed applies of a zero vector;
+// the apply's work does not depend on the values) and the fastest is kept.
+// A form fixed by the caller is tuned over the threads per row only.  The
+// timed applies join the chain that orders the applies of concurrent solves,
+// so they never run beside one.  Only factors of at least kTuneMinRows rows
+// are tuned (below, a whole apply takes tens of microseconds and the choice
+// matters little).
 constexpr int kTuneMinRows = 200000;
 
 template <typename T>
-int autotune_apply(ildl_s* f, DevFactor<T>& d, cudaStream_t st) {
+int set_apply_shape(const HostFactor& F, DevFactor<T>& d, int form, int shift, cudaStream_t st) {
+  // the level-counter list always stays valid (the allocation-free apply
+  // launches that form whatever the factor's choice)
+  const std::vector<int4> ph = build_phase_list(F, form == 0 ? shift : 0);
+  AJD_CUDA(cudaMemcpyAsync(d.phases, ph.data(), ph.size() * sizeof(int4), cudaMemcpyHostToDevice, st));
+  AJD_TRY(upload_dataflow_units(F, d, form == 1 ? shift : 0, st));  // synchronises st
+  d.form = form;
+  return JD_OK;
+}
+
+template <typename T>
+int autotune_apply(ildl_s* f, DevFactor<T>& d, int form_req, cudaStream_t st) {
   const HostFactor& F = f->F;
   if (F.n < kTuneMinRows || d.nphase == 0) return JD_OK;
   double* b = nullptr;
   double* x = nullptr;
-  int4* cand = nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   const bool was = tl_serialize_applies;
   tl_serialize_applies = true;
@@ -464,41 +567,36 @@ int autotune_apply(ildl_s* f, DevFactor<T>& d, cudaStream_t st) {
   auto body = [&]() -> int {
     AJD_CUDA(cudaMalloc(&b, sizeof(double) * (size_t)F.n));
     AJD_CUDA(cudaMalloc(&x, sizeof(double) * (size_t)F.n));
-    AJD_CUDA(cudaMalloc(&cand, sizeof(int4) * (size_t)d.nphase));
     AJD_CUDA(cudaMemsetAsync(b, 0, sizeof(double) * (size_t)F.n, st));
     AJD_CUDA(cudaEventCreate(&e0));
     AJD_CUDA(cudaEventCreate(&e1));
-    int best = 0;
+    int best_form = -1, best_shift = 0;
     double best_ms = 0.0;
-    AJD_TRY(run(&best_ms));
-    f->F.apply_tune_ms[1] = best_ms;
-    for (int shift : {-1, 1}) {
-      const std::vector<int4> ph = build_phase_list(F, shift);
-      AJD_CUDA(cudaMemcpyAsync(cand, ph.data(), ph.size() * sizeof(int4), cudaMemcpyHostToDevice, st));
-      std::swap(d.phases, cand);
-      double ms = 0.0;
-      const int r = run(&ms);
-      std::swap(d.phases, cand);
-      AJD_TRY(r);
-      f->F.apply_tune_ms[shift + 1] = ms;
-      if (ms < best_ms) {
-        best_ms = ms;
-        best = shift;
+    for (int form = 0; form < 2; ++form) {
+      if (form_req >= 0 && form != form_req) continue;
+      for (int shift : {0, -1, 1}) {
+        AJD_TRY(set_apply_shape(F, d, form, shift, st));
+        double ms = 0.0;
+        AJD_TRY(run(&ms));
+        f->F.apply_tune_ms[form][shift + 1] = ms;
+        if (std::getenv("AJD_SETUP_VERBOSE"))
+          std::fprintf(stderr, "ildl apply autotune: form %d shift %+d: %.3f ms\n", form, shift, ms);
+        if (best_form < 0 || ms < best_ms) {
+          best_ms = ms;
+          best_form = form;
+          best_shift = shift;
+        }
       }
     }
-    if (best != 0) {
-      const std::vector<int4> ph = build_phase_list(F, best);
-      AJD_CUDA(cudaMemcpyAsync(d.phases, ph.data(), ph.size() * sizeof(int4), cudaMemcpyHostToDevice, st));
-    }
-    f->F.apply_shift = best;
-    AJD_CUDA(cudaStreamSynchronize(st));
+    AJD_TRY(set_apply_shape(F, d, best_form, best_shift, st));
+    f->F.apply_form = best_form;
+    f->F.apply_shift = best_shift;
     return JD_OK;
   };
   rc = body();
   tl_serialize_applies = was;
   cudaFree(b);
   cudaFree(x);
-  cudaFree(cand);
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
   return rc;
@@ -506,23 +604,22 @@ int autotune_apply(ildl_s* f, DevFactor<T>& d, cudaStream_t st) {
 
 }  // namespace
 
-int ildl_upload_all(ildl_s* f, cudaStream_t st, int copies, bool tune) {
+int ildl_upload_all(ildl_s* f, cudaStream_t st, int copies, bool tune, int form_req) {
   if (f->F.dense_is_matrix) {
     AJD_TRY(invert_dense_on_device(f->F.dense_inv, f->F.n_dense, st));
     f->F.dense_is_matrix = false;
   }
+  f->F.apply_form = form_req >= 0 ? form_req : kDefaultApplyForm;
+  f->F.apply_shift = 0;
   if (copies & kCopyF64) AJD_TRY(upload_factor<double>(f->F, f->d64, st));
   if (copies & kCopyF32) AJD_TRY(upload_factor<float>(f->F, f->d32, st));
   if (tune) {
     // tuned on the copy a solve uses first (binary32 for the mixed and
     // binary32 solves); the other copy takes the same choice
-    if (copies & kCopyF32) AJD_TRY(autotune_apply<float>(f, f->d32, st));
-    else if (copies & kCopyF64) AJD_TRY(autotune_apply<double>(f, f->d64, st));
-    if ((copies & kCopyF32) && (copies & kCopyF64) && f->F.apply_shift != 0) {
-      const std::vector<int4> ph = build_phase_list(f->F, f->F.apply_shift);
-      AJD_CUDA(cudaMemcpyAsync(f->d64.phases, ph.data(), ph.size() * sizeof(int4), cudaMemcpyHostToDevice, st));
-      AJD_CUDA(cudaStreamSynchronize(st));
-    }
+    if (copies & kCopyF32) AJD_TRY(autotune_apply<float>(f, f->d32, form_req, st));
+    else if (copies & kCopyF64) AJD_TRY(autotune_apply<double>(f, f->d64, form_req, st));
+    if ((copies & kCopyF32) && (copies & kCopyF64))
+      AJD_TRY(set_apply_shape(f->F, f->d64, f->F.apply_form, f->F.apply_shift, st));
   }
   return JD_OK;
 }
@@ -603,6 +700,7 @@ extern "C" int ildl_params_default(ildl_params* p) {
   p->aggressive = 0.0;
   p->setup_device = -1;
   p->autotune = -1;
+  p->apply_form = -1;
   return JD_OK;
 }
 
@@ -620,6 +718,7 @@ static int check_params(const ildl_params* p, ildl_params& out) {
   if (out.gamma >= 1.0 || std::isnan(out.gamma)) return fail(JD_EINVAL, "ildl: gamma must be < 1");
   if (!(out.aggressive >= 0.0 && out.aggressive < 1.0))
     return fail(JD_EINVAL, "ildl: aggressive dropping tau must be in [0, 1)");
+  if (out.apply_form < -1 || out.apply_form > 1) return fail(JD_EINVAL, "ildl: apply_form must be -1, 0 or 1");
   if (out.max_levels < 1 || out.n_dense < 0 || out.n_dense > 8000)
     return fail(JD_EINVAL, "ildl: max_levels >= 1 and 0 <= n_dense <= 8000 required");
   return JD_OK;
@@ -741,7 +840,7 @@ int ildl_create_on_stream(anderson_t h, double sigma, const ildl_params* p, ildl
     if (prm.setup_device != 0) eng = make_device_schur(st);
     int rc = build_ildl(A, prm, f->F, /*dense_on_host=*/false, eng.get());
     eng.reset();
-    if (rc == JD_OK) rc = ildl_upload_all(f, st, copies, prm.autotune != 0);
+    if (rc == JD_OK) rc = ildl_upload_all(f, st, copies, prm.autotune != 0, prm.apply_form);
     f->F.t_total_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     if (rc != JD_OK) {
       ildl_free_device(f);
@@ -777,6 +876,7 @@ extern "C" int ildl_info(ildl_t f, ildl_info_t* info) {
   info->max_abs_L = F.max_abs_L;
   info->aggressive_dropped = F.n_aggressive;
   info->apply_shift = F.apply_shift;
+  info->apply_form = F.apply_form;
   return JD_OK;
 }
 

@@ -30,6 +30,10 @@ struct DevFactor {
   unsigned* bar = nullptr;   // [64] timeout flag of the apply's waits
   unsigned* done = nullptr;  // completion counters of the apply's phases
   int grid = 0;
+  int4* units = nullptr;  // dataflow-apply unit segments (kind | G << 8, p0, p1, first unit)
+  int nseg = 0;
+  int nunits = 0;
+  int form = 0;  // apply form: 0 level counters (phases), 1 dataflow (units)
   float2* wdf = nullptr;  // float-float work vectors of the mixed apply (binary32 copy only)
   float2* zdf = nullptr;
 };

@@ -75,7 +75,8 @@ struct HostFactor {
   int64_t nnz_A = 0;
   double t_match_ms = 0, t_factor_ms = 0, t_total_ms = 0;
   int apply_shift = 0;            // autotuned threads-per-row scale of the apply, log2
-  double apply_tune_ms[3] = {0, 0, 0};  // apply time with shift -1, 0, +1 (0 = not tuned)
+  int apply_form = 0;             // apply kernel: 0 level counters, 1 dataflow
+  double apply_tune_ms[2][3] = {{0, 0, 0}, {0, 0, 0}};  // apply time per form and shift -1, 0, +1 (0 = not timed)
   std::vector<int> level_sizes;   // rows eliminated per sparse level
 };
 

@@ -43,21 +43,26 @@ def _time(fn, reps, flush=None):
     return ts[len(ts) // 2]
 
 
-def apply_case(L, reps, only=None):
+def apply_case(L, reps, only=None, forms=(-1,)):
+    """The apply of the L-lattice's factor (sigma = 0), per apply form
+    (-1: the autotuner's choice; 0: level counters; 1: dataflow)."""
     h = ajd.Anderson(L, 16.5, 1)
-    P = ajd.Preconditioner.from_lattice(h, 0.0)
-    info = P.info()
-    print(json.dumps({"case": "setup", "L": L, **info}), flush=True)
-    for name, dt, mixed in [("fp32", torch.float32, False), ("fp64", torch.float64, False),
-                            ("mixed", torch.float64, True)]:
-        if only and name != only:
-            continue
-        b = torch.randn(h.n, device="cuda", dtype=dt)
-        x = torch.empty_like(b)
-        for _ in range(3):
-            P.apply(b, out=x, mixed=mixed)
-        ms = _time(lambda: P.apply(b, out=x, mixed=mixed), reps)
-        print(json.dumps({"case": "apply", "precision": name, "L": L, "ms": ms}), flush=True)
+    for form in forms:
+        P = ajd.Preconditioner.from_lattice(h, 0.0, apply_form=form)
+        info = P.info()
+        print(json.dumps({"case": "setup", "L": L, "form_requested": form, **info}), flush=True)
+        for name, dt, mixed in [("fp32", torch.float32, False), ("fp64", torch.float64, False),
+                                ("mixed", torch.float64, True)]:
+            if only and name != only:
+                continue
+            b = torch.randn(h.n, device="cuda", dtype=dt)
+            x = torch.empty_like(b)
+            for _ in range(3):
+                P.apply(b, out=x, mixed=mixed)
+            ms = _time(lambda: P.apply(b, out=x, mixed=mixed), reps)
+            print(json.dumps({"case": "apply", "precision": name, "L": L, "form": info["apply_form"],
+                              "shift": info["apply_shift"], "ms": ms}), flush=True)
+        P.close()
 
 
 def stencil_case(L, reps, m=1):
@@ -124,12 +129,13 @@ def main():
     ap.add_argument("--L", type=int, default=None)
     ap.add_argument("--reps", type=int, default=None)
     ap.add_argument("--only", choices=["fp32", "fp64", "mixed"], default=None)
+    ap.add_argument("--forms", default="-1", help="apply: apply forms, comma separated (-1 = autotuned)")
     ap.add_argument("--vectors", type=int, default=1, help="stencil: vectors per launch")
     ap.add_argument("--threads", default="16,8", help="setup: host thread counts, comma separated")
     ap.add_argument("--schur", default="gpu,host", help="setup: where the Schur complements are formed")
     a = ap.parse_args()
     if a.what == "apply":
-        apply_case(a.L or 70, a.reps or 5, a.only)
+        apply_case(a.L or 70, a.reps or 5, a.only, [int(x) for x in a.forms.split(",")])
     elif a.what == "gram":
         gram_case(a.n, a.cols, a.reps or 10)
     elif a.what == "setup":

@@ -67,39 +67,77 @@ def check_apply_errors(err):
     assert err["fp32_unrounded"] <= TOL_APPLY_UNROUNDED, err
 
 
+FORMS = [0, 1]  # apply kernels: level counters, dataflow
+
+
+@pytest.mark.parametrize("form", FORMS)
 @pytest.mark.parametrize("L,bc,sigma,nd", [(10, 0, 0.0, 1000), (20, 0, 0.3, 1000), (33, 1, -0.5, 300), (16, 0, 1.0, 50)])
-def test_ildl_apply_matches_oracle(ajd, L, bc, sigma, nd):
+def test_ildl_apply_matches_oracle(ajd, L, bc, sigma, nd, form):
     """x = K^{-1} b on the GPU equals the plain definition applied by the
-    oracle to the same factor (binary64, mixed and binary32)."""
+    oracle to the same factor (binary64, mixed and binary32), in both apply
+    forms."""
     with ajd.Anderson(L, 16.5, 1, bc) as h:
-        P = ajd.Preconditioner.from_lattice(h, sigma, n_dense=nd)
+        P = ajd.Preconditioner.from_lattice(h, sigma, n_dense=nd, apply_form=form)
+        assert P.info()["apply_form"] == form
         F = P.export()
         b = np.random.default_rng(0).standard_normal(h.n)
         check_apply_errors(apply_errors(P, F, b))
         P.close()
 
 
+def test_ildl_apply_forms_agree(ajd):
+    """The level-counter and the dataflow kernels compute the same sums
+    (rows split over the same lanes in different orders only): their
+    binary64 results agree to rounding, and repeated dataflow applies of the
+    same vector give the same bits (each row's sum is formed by one fixed set
+    of lanes, whatever the timing)."""
+    with ajd.Anderson(30, 16.5, 7) as h:
+        P0 = ajd.Preconditioner.from_lattice(h, 0.1, apply_form=0)
+        P1 = ajd.Preconditioner.from_lattice(h, 0.1, apply_form=1)
+        b = torch.tensor(np.random.default_rng(9).standard_normal(h.n), device="cuda")
+        x0 = P0.apply(b).cpu().numpy()
+        x1 = P1.apply(b).cpu().numpy()
+        assert np.abs(x0 - x1).max() <= 1e-12 * np.abs(x0).max()
+        for mixed in (False, True):
+            r1 = P1.apply(b, mixed=mixed).cpu().numpy()
+            r2 = P1.apply(b, mixed=mixed).cpu().numpy()
+            assert np.array_equal(r1.view(np.int64), r2.view(np.int64))
+        P0.close()
+        P1.close()
+
+
 def test_ildl_apply_autotuned(ajd):
-    """A factor of more than 200,000 rows has its apply's threads per row
-    tuned on the device (the rule's choice times 1/2, 1 or 2, whichever
-    runs fastest); whatever the choice, the apply equals the oracle's."""
+    """A factor of more than 200,000 rows has its apply tuned on the device
+    (the two kernels, each with the rule's threads per row times 1/2, 1 or
+    2, whichever runs fastest); whatever the choice, the apply equals the
+    oracle's.  A kernel fixed by the caller is tuned over the threads per
+    row only."""
     with ajd.Anderson(60, 16.5, 4) as h:
         P = ajd.Preconditioner.from_lattice(h, 0.2)
         assert P.info()["apply_shift"] in (-1, 0, 1)
+        assert P.info()["apply_form"] in (0, 1)
         b = np.random.default_rng(5).standard_normal(h.n)
         check_apply_errors(apply_errors(P, P.export(), b))
         P.close()
+        for form in FORMS:
+            P1 = ajd.Preconditioner.from_lattice(h, 0.2, apply_form=form)
+            assert P1.info()["apply_form"] == form
+            check_apply_errors(apply_errors(P1, P1.export(), b))
+            P1.close()
         P0 = ajd.Preconditioner.from_lattice(h, 0.2, autotune=0)
         assert P0.info()["apply_shift"] == 0
         P0.close()
 
 
-def test_ildl_apply_wide_rows(ajd):
+@pytest.mark.parametrize("form", FORMS)
+def test_ildl_apply_wide_rows(ajd, form):
     """A factor without dropping has few, long rows on its deepest levels:
     those phases run with 64..512 threads per row (CTA-wide rows with a
-    shared-memory reduction) and must still equal the oracle's apply."""
+    shared-memory reduction) in the level-counter kernel and with a warp
+    per row and many batches in the dataflow kernel, and must still equal
+    the oracle's apply."""
     with ajd.Anderson(22, 16.5, 1) as h:
-        P = ajd.Preconditioner.from_lattice(h, 0.3, n_dense=200, drop=0.0)
+        P = ajd.Preconditioner.from_lattice(h, 0.3, n_dense=200, drop=0.0, apply_form=form)
         F = P.export()
         assert P.info()["nnz_L"] > 5 * 10 ** 6  # deep rows of several hundred to thousands of entries
         b = np.random.default_rng(3).standard_normal(h.n)
@@ -114,14 +152,18 @@ def test_ildl_apply_wide_rows(ajd):
         P.close()
 
 
+@pytest.mark.parametrize("form", FORMS)
 @pytest.mark.parametrize("L,bc,sigma,nd", [(12, 1, -1.0, 200), (20, 0, 0.3, 1000)])
-def test_ildl_apply_no_read_before_write(ajd, monkeypatch, L, bc, sigma, nd):
+def test_ildl_apply_no_read_before_write(ajd, monkeypatch, L, bc, sigma, nd, form):
     """Work vectors filled with NaN before the first apply (AJD_POISON_ALLOC):
     every apply must still equal the oracle's, so no entry of w or z is read
-    before this apply wrote it (padding lanes of a row included)."""
+    before this apply wrote it (padding lanes of a row included).  The
+    dataflow kernel refills them with its own sentinel before every apply
+    and waits on it, so there a read before the write would hang until the
+    bounded wait reports JD_EDEVICE instead."""
     monkeypatch.setenv("AJD_POISON_ALLOC", "1")
     with ajd.Anderson(L, 12.0, 12, bc) as h:
-        P = ajd.Preconditioner.from_lattice(h, sigma, n_dense=nd)
+        P = ajd.Preconditioner.from_lattice(h, sigma, n_dense=nd, apply_form=form)
         assert P.info()["levels"] >= 2
         b = np.random.default_rng(0).standard_normal(h.n)
         check_apply_errors(apply_errors(P, P.export(), b))
@@ -287,6 +329,19 @@ def test_jd_no_read_before_write(ajd, prec, monkeypatch):
         with ajd.Anderson(L, W, s, bc) as h:
             ev, X, st = ajd.solve(h, sigma, k, tol, precision=prec, ildl={"n_dense": 200})
         _check_pairs(L, W, s, bc, sigma, k, ev, X, st, tol)
+
+
+@pytest.mark.parametrize("form", FORMS)
+@pytest.mark.parametrize("prec", [0, 2])
+def test_jd_apply_forms(ajd, form, prec):
+    """Jacobi-Davidson with either apply kernel reaches the dense oracle's
+    pairs."""
+    L, W, s, bc, sigma, k = 16, 16.5, 31, 0, 0.4, 4
+    tol = 1e-11 if prec == 0 else 1e-10
+    with ajd.Anderson(L, W, s, bc) as h:
+        ev, X, st = ajd.solve(h, sigma, k, tol, precision=prec, ildl={"n_dense": 300, "apply_form": form})
+    assert st["ildl"]["apply_form"] == form
+    _check_pairs(L, W, s, bc, sigma, k, ev, X, st, tol)
 
 
 @pytest.mark.parametrize("L", [50, 100])
