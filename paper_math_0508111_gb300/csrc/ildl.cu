@@ -390,9 +390,42 @@ int launch_apply_dataflow(const ildl_s* f, const DevFactor<V>& d, X* w, X* z, co
   const int4* units = d.units;
   int nseg = d.nseg, nunits = d.nunits;
   int* err = reinterpret_cast<int*>(d.bar + 64);
-  void* args[] = {&a, &units, &nseg, &nunits, &err};
+  // AJD_APPLY_TIMING=1: record when each segment's last unit finished
+  // (globaltimer) and print a per-kind summary of the apply to stderr
+  static const bool timing = std::getenv("AJD_APPLY_TIMING") != nullptr;
+  unsigned long long* stamps = nullptr;
+  if (timing) {
+    AJD_CUDA(cudaMalloc(&stamps, (nseg + 1) * sizeof(unsigned long long)));
+    AJD_CUDA(cudaMemsetAsync(stamps, 0, (nseg + 1) * sizeof(unsigned long long), s));
+  }
+  void* args[] = {&a, &units, &nseg, &nunits, &err, &stamps};
   AJD_TRY(launch_cooperative(d, (const void*)ildl_apply_dataflow_kernel<V, X, IO>, args, s));
-  count_launches(3);
+  count_launches(timing ? 4 : 3);
+  if (timing) {
+    std::vector<unsigned long long> t(nseg + 1);
+    std::vector<int4> sg(nseg);
+    AJD_CUDA(cudaMemcpyAsync(t.data(), stamps, (nseg + 1) * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+    AJD_CUDA(cudaMemcpyAsync(sg.data(), d.units, nseg * sizeof(int4), cudaMemcpyDeviceToHost, s));
+    AJD_CUDA(cudaStreamSynchronize(s));
+    cudaFree(stamps);
+    // a segment's share: how far its completion moved the running maximum
+    double kind_us[4] = {0, 0, 0, 0};
+    int kind_n[4] = {0, 0, 0, 0};
+    unsigned long long last = t[0];
+    for (int i = 0; i < nseg; ++i) {
+      const unsigned long long ti = std::max(t[i + 1], last);
+      const double us = (ti - last) * 1e-3;
+      last = ti;
+      kind_us[sg[i].x & 0xFF] += us;
+      kind_n[sg[i].x & 0xFF]++;
+      if (std::getenv("AJD_APPLY_TIMING_ALL"))
+        std::fprintf(stderr, "segment %d kind %d rows %d G %d units from %d: done at %.2f us (+%.2f)\n", i,
+                     sg[i].x & 0xFF, sg[i].z - sg[i].y, sg[i].x >> 8, sg[i].w, (t[i + 1] - t[0]) * 1e-3, us);
+    }
+    std::fprintf(stderr, "dataflow apply %.1f us: gather %.1f (%d) fwd %.1f (%d) dense %.1f (%d) bwd %.1f (%d)\n",
+                 (last - t[0]) * 1e-3, kind_us[0], kind_n[0], kind_us[1], kind_n[1], kind_us[2], kind_n[2], kind_us[3],
+                 kind_n[3]);
+  }
   return JD_OK;
 }
 

@@ -115,6 +115,51 @@ __device__ __forceinline__ bool settle(const U* p, U& w, int* err) {
   return true;
 }
 
+// Wait until every gathered word of a batch is written.  A waiting warp
+// polls one address at a time: the lane that holds the warp's largest
+// pending column (the latest level's entry, usually the last to be written)
+// reloads it until it is written, then every lane reloads its own pending
+// entries once, and so on.  Thousands of lanes each polling their own entry
+// would crowd the few L2 lines that the level being finished writes.
+template <int B, typename U>
+__device__ __forceinline__ bool settle_batch(const U* xw, const int (&c)[B], U (&xv)[B], int* err) {
+  const int lane = threadIdx.x & 31;
+  unsigned spins = 0;
+  for (;;) {
+    int mine = -1;  // this lane's largest pending column
+#pragma unroll
+    for (int i = 0; i < B; ++i)
+      if (c[i] >= 0 && xv[i] == ~U(0)) mine = max(mine, c[i]);
+    int top = mine;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) top = max(top, __shfl_xor_sync(0xffffffffu, top, o));
+    if (top < 0) return true;
+    const int leader = __ffs(__ballot_sync(0xffffffffu, mine == top)) - 1;
+    int bad = 0;
+    if (lane == leader) {
+      U w = ld_flow(xw + top);
+      while (w == ~U(0)) {
+        ++spins;
+        if (spins > kSpinLimit) {
+          atomicExch(err, 1);
+          bad = 1;
+          break;
+        }
+        if ((spins & 255u) == 0 && *((volatile int*)err)) {
+          bad = 1;
+          break;
+        }
+        if (spins > 2) __nanosleep(32);
+        w = ld_flow(xw + top);
+      }
+    }
+    if (__shfl_sync(0xffffffffu, bad, leader)) return false;
+#pragma unroll
+    for (int i = 0; i < B; ++i)
+      if (c[i] >= 0 && xv[i] == ~U(0)) xv[i] = ld_flow(xw + c[i]);
+  }
+}
+
 // Unit descriptor (int4): kind | G << 8, first row, end row, first unit.
 template <typename V, typename X, typename IO, int G>
 __device__ __forceinline__ bool flow_rows(const ApplyArgs<V, X, IO>& a, int kind, int p0, int p1, int k, int* err) {
@@ -137,7 +182,7 @@ __device__ __forceinline__ bool flow_rows(const ApplyArgs<V, X, IO>& a, int kind
   }
   bool ok = true;
   X acc = zero<X>(), acc2 = zero<X>();
-  while (q < e) {
+  while (__any_sync(0xffffffffu, q < e)) {  // uniform over the warp (lanes past their row gather nothing)
     int c[B];
     W v[B];
     U xv[B];
@@ -149,16 +194,16 @@ __device__ __forceinline__ bool flow_rows(const ApplyArgs<V, X, IO>& a, int kind
     }
 #pragma unroll
     for (int i = 0; i < B; ++i) xv[i] = c[i] >= 0 ? ld_flow(xw + c[i]) : U(0);  // all-zero word: 0
-#pragma unroll
-    for (int i = 0; i < B; ++i)
-      if (ok && c[i] >= 0 && !settle(xw + c[i], xv[i], err)) ok = false;
+    if (!settle_batch<B>(xw, c, xv, err)) {
+      ok = false;
+      break;
+    }
 #pragma unroll
     for (int i = 0; i < B; i += 2) {
       mac(acc, v[i], word_value<X>(xv[i]));
       mac(acc2, v[i + 1], word_value<X>(xv[i + 1]));
     }
     q += B * G;
-    if (!ok) break;
   }
   // backward rows: rhs = (D^{-1} w)_p from the forward values of the row
   // and its 2x2 partner
@@ -196,28 +241,25 @@ __device__ __forceinline__ bool flow_dense_row(const ApplyArgs<V, X, IO>& a, int
   const int lane = threadIdx.x & 31;
   const V* row = a.dense + (int64_t)r * a.nd;
   const U* wd = words(a.w + a.d0);
-  bool ok = true;
   X acc = zero<X>(), acc2 = zero<X>();
-  for (int c0 = lane; c0 < a.nd; c0 += 32 * B) {
+  for (int base = 0; base < a.nd; base += 32 * B) {  // uniform over the warp
+    int c[B];
     W v[B];
     U xv[B];
 #pragma unroll
     for (int i = 0; i < B; ++i) {
-      const int c = c0 + 32 * i;
-      v[i] = c < a.nd ? ldw<W>(row + c) : W(0);
-      xv[i] = c < a.nd ? ld_flow(wd + c) : U(0);
+      const int col = base + lane + 32 * i;
+      c[i] = col < a.nd ? col : -1;
+      v[i] = col < a.nd ? ldw<W>(row + col) : W(0);
+      xv[i] = col < a.nd ? ld_flow(wd + col) : U(0);
     }
-#pragma unroll
-    for (int i = 0; i < B; ++i)
-      if (ok && c0 + 32 * i < a.nd && !settle(wd + c0 + 32 * i, xv[i], err)) ok = false;
+    if (!settle_batch<B>(wd, c, xv, err)) return false;
 #pragma unroll
     for (int i = 0; i < B; i += 2) {
       mac(acc, v[i], word_value<X>(xv[i]));
       mac(acc2, v[i + 1], word_value<X>(xv[i + 1]));
     }
-    if (!ok) break;
   }
-  if (__any_sync(0xffffffffu, !ok)) return false;
   acc = add(norm(acc), norm(acc2));
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) acc = add(acc, shfl_xor(acc, o, 32));
@@ -230,9 +272,15 @@ __device__ __forceinline__ bool flow_dense_row(const ApplyArgs<V, X, IO>& a, int
 
 template <typename V, typename X, typename IO>
 __global__ void __launch_bounds__(kPersistThreads, 1)
-ildl_apply_dataflow_kernel(ApplyArgs<V, X, IO> a, const int4* __restrict__ units, int nseg, int nunits, int* err) {
+ildl_apply_dataflow_kernel(ApplyArgs<V, X, IO> a, const int4* __restrict__ units, int nseg, int nunits, int* err,
+                           unsigned long long* stamps) {
   using W = typename ValueReg<V, X>::type;
   const int lane = threadIdx.x & 31;
+  if (stamps && blockIdx.x == 0 && threadIdx.x == 0) {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    stamps[0] = t;  // start (CTA 0)
+  }
   const int warps = (int)(gridDim.x * (blockDim.x >> 5));
   int sg = 0;
   for (int u = (int)((threadIdx.x >> 5) * gridDim.x + blockIdx.x); u < nunits; u += warps) {
@@ -257,6 +305,12 @@ ildl_apply_dataflow_kernel(ApplyArgs<V, X, IO> a, const int4* __restrict__ units
       }
     }
     if (!ok) return;  // a wait timed out (uniform over the warp)
+    if (stamps && lane == 0) {
+      // diagnostics: when the segment's last unit finished
+      unsigned long long t;
+      asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+      atomicMax(stamps + 1 + sg, t);
+    }
   }
 }
 
