@@ -236,8 +236,8 @@ std::vector<int4> build_phase_list(const HostFactor& F, int shift) {
 // Unit segments of the dataflow apply for factor F, in the order the units
 // are taken: level 0 (32 rows per unit), the forward levels, the dense tail
 // (one row per unit), the backward levels from the last to level 0.  Lanes
-// per row: about four stored entries per lane (a power of two in 1..32),
-// times 2^shift.  Each int4 is (kind | G << 8, first row, end row, first
+// per row: about six stored entries per lane, so that a lane's batch of
+// eight loads is mostly full (a power of two in 1..32), times 2^shift.  Each int4 is (kind | G << 8, first row, end row, first
 // unit); *nunits receives the total.
 std::vector<int4> build_flow_list(const HostFactor& F, int shift, int* nunits) {
   std::vector<int4> seg;
@@ -245,7 +245,7 @@ std::vector<int4> build_flow_list(const HostFactor& F, int shift, int* nunits) {
   const int nl = F.nlev;
   auto pick_g = [&](double avg) {
     int g = 1;
-    while (g < 32 && 2 * g <= avg / 4.0) g *= 2;
+    while (g < 32 && 2 * g <= avg / 6.0) g *= 2;
     for (int i = 0; i < shift && g < 32; ++i) g *= 2;
     for (int i = 0; i > shift && g > 1; --i) g /= 2;
     return g;

@@ -115,48 +115,62 @@ __device__ __forceinline__ bool settle(const U* p, U& w, int* err) {
   return true;
 }
 
-// Wait until every gathered word of a batch is written.  A waiting warp
-// polls one address at a time: the lane that holds the warp's largest
-// pending column (the latest level's entry, usually the last to be written)
-// reloads it until it is written, then every lane reloads its own pending
-// entries once, and so on.  Thousands of lanes each polling their own entry
-// would crowd the few L2 lines that the level being finished writes.
+// Wait until every gathered word of a batch is written.  While a warp waits
+// for the level before to finish, one lane polls one address: the lane that
+// holds the warp's largest pending column (an entry of the latest level)
+// reloads it until it is written; thousands of lanes each polling their own
+// entries would crowd the few L2 lines that the level being finished
+// writes.  Once it is written the level is nearly done, and every lane
+// reloads its pending entries together, round by round, until none is left.
 template <int B, typename U>
 __device__ __forceinline__ bool settle_batch(const U* xw, const int (&c)[B], U (&xv)[B], int* err) {
   const int lane = threadIdx.x & 31;
+  int mine = -1;  // this lane's largest pending column
+#pragma unroll
+  for (int i = 0; i < B; ++i)
+    if (c[i] >= 0 && xv[i] == ~U(0)) mine = max(mine, c[i]);
+  int top = mine;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) top = max(top, __shfl_xor_sync(0xffffffffu, top, o));
+  if (top < 0) return true;
   unsigned spins = 0;
-  for (;;) {
-    int mine = -1;  // this lane's largest pending column
-#pragma unroll
-    for (int i = 0; i < B; ++i)
-      if (c[i] >= 0 && xv[i] == ~U(0)) mine = max(mine, c[i]);
-    int top = mine;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) top = max(top, __shfl_xor_sync(0xffffffffu, top, o));
-    if (top < 0) return true;
-    const int leader = __ffs(__ballot_sync(0xffffffffu, mine == top)) - 1;
-    int bad = 0;
-    if (lane == leader) {
-      U w = ld_flow(xw + top);
-      while (w == ~U(0)) {
-        ++spins;
-        if (spins > kSpinLimit) {
-          atomicExch(err, 1);
-          bad = 1;
-          break;
-        }
-        if ((spins & 255u) == 0 && *((volatile int*)err)) {
-          bad = 1;
-          break;
-        }
-        if (spins > 2) __nanosleep(32);
-        w = ld_flow(xw + top);
+  const int leader = __ffs(__ballot_sync(0xffffffffu, mine == top)) - 1;
+  int bad = 0;
+  if (lane == leader) {
+    U w = ld_flow(xw + top);
+    while (w == ~U(0)) {
+      ++spins;
+      if (spins > kSpinLimit) {
+        atomicExch(err, 1);
+        bad = 1;
+        break;
       }
+      if ((spins & 255u) == 0 && *((volatile int*)err)) {
+        bad = 1;
+        break;
+      }
+      if (spins > 2) __nanosleep(32);
+      w = ld_flow(xw + top);
     }
-    if (__shfl_sync(0xffffffffu, bad, leader)) return false;
+  }
+  if (__shfl_sync(0xffffffffu, bad, leader)) return false;
+  spins = 0;
+  for (;;) {
+    bool pend = false;
 #pragma unroll
     for (int i = 0; i < B; ++i)
-      if (c[i] >= 0 && xv[i] == ~U(0)) xv[i] = ld_flow(xw + c[i]);
+      if (c[i] >= 0 && xv[i] == ~U(0)) {
+        xv[i] = ld_flow(xw + c[i]);
+        pend |= xv[i] == ~U(0);
+      }
+    if (!__any_sync(0xffffffffu, pend)) return true;
+    ++spins;
+    if (spins > kSpinLimit) {
+      if (lane == 0) atomicExch(err, 1);
+      return false;
+    }
+    if ((spins & 255u) == 0 && *((volatile int*)err)) return false;
+    __nanosleep(32);
   }
 }
 
@@ -175,10 +189,17 @@ __device__ __forceinline__ bool flow_rows(const ApplyArgs<V, X, IO>& a, int kind
   const U* xw = words(kind == PH_FWD ? a.w : a.z);  // vector read through the columns
   int q = 0, e = 0;
   RowHead<V, X, IO> h{};
+  U w0 = 0, w1 = 0;  // backward rows: the forward values of the row and its 2x2 partner
   if (live) {
     q = __ldg(ptr + p) + t;
     e = __ldg(ptr + p + 1);
-    if (t == 0) h = row_head(a, kind, p);
+    if (t == 0) {
+      h = row_head(a, kind, p);
+      if (kind == PH_BWD) {
+        w0 = ld_flow(words(a.w) + p);
+        if (h.pp >= 0) w1 = ld_flow(words(a.w) + h.pp);
+      }
+    }
   }
   bool ok = true;
   X acc = zero<X>(), acc2 = zero<X>();
@@ -209,8 +230,6 @@ __device__ __forceinline__ bool flow_rows(const ApplyArgs<V, X, IO>& a, int kind
   // and its 2x2 partner
   if (kind == PH_BWD && live && t == 0 && ok) {
     const U* ww = words(a.w);
-    U w0 = ld_flow(ww + p);
-    U w1 = h.pp >= 0 ? ld_flow(ww + h.pp) : U(0);
     if (!settle(ww + p, w0, err) || (h.pp >= 0 && !settle(ww + h.pp, w1, err))) ok = false;
     X d = mul(h.dd, word_value<X>(w0));
     if (h.pp >= 0) d = add(d, mul(h.dof, word_value<X>(w1)));
