@@ -189,27 +189,40 @@ def apply_bytes(info, val, vec):
             + nd * nd * val)
 
 
-def kernel_source_hash():
-    """SHA-1 of the apply kernel's source (csrc/ildl_apply_kernel.cuh): DRAM
-    counters recorded for an older source no longer describe the kernel that
-    runs."""
+APPLY_SOURCES = {0: ["ildl_apply_kernel.cuh"], 1: ["ildl_apply_kernel.cuh", "ildl_apply_dataflow.cuh"]}
+APPLY_KERNELS = {0: "ildl_apply_persistent_kernel (one cooperative launch; level sweeps with per-level completion "
+                    "counters: gather, forward levels, dense tail, backward levels)",
+                 1: "ildl_apply_dataflow_kernel (one cooperative launch; every row starts once the entries it "
+                    "reads are written: gather, forward levels, dense tail, backward levels)"}
+
+
+def kernel_source_hash(files):
+    """SHA-1 of the apply kernel's sources (csrc/<files>, concatenated):
+    DRAM counters recorded for an older source no longer describe the kernel
+    that runs."""
     import hashlib
-    with open(os.path.join(ROOT, "paper_math_0508111_gb300", "csrc", "ildl_apply_kernel.cuh"), "rb") as f:
-        return hashlib.sha1(f.read()).hexdigest()
+    h = hashlib.sha1()
+    for name in files:
+        with open(os.path.join(ROOT, "paper_math_0508111_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
 
 
-def measured_traffic(precision, info):
-    """DRAM bytes per apply from the committed ncu summary of this kernel
-    (profiles/ildl_apply_<precision>_traffic.json), scaled from the captured
-    lattice to this factor by the ratio of algorithmic bytes; None when no
-    capture exists or the kernel source changed since it was taken."""
-    path = os.path.join(ROOT, "profiles", "ildl_apply_%s_traffic.json" % precision)
+def measured_traffic(precision, info, form):
+    """DRAM bytes per apply from the committed ncu summary of the apply form
+    in use (profiles/ildl_apply_<precision>_traffic.json for the level-counter
+    kernel, profiles/ildl_apply_dataflow_<precision>_traffic.json for the
+    dataflow kernel), scaled from the captured lattice to this factor by the
+    ratio of algorithmic bytes; None when no capture exists or the kernel
+    source changed since it was taken."""
+    name = "ildl_apply_%s_traffic.json" % precision if form == 0 else "ildl_apply_dataflow_%s_traffic.json" % precision
     try:
-        with open(path) as f:
+        with open(os.path.join(ROOT, "profiles", name)) as f:
             d = json.load(f)
     except Exception:
         return None
-    if d.get("source_sha1") != kernel_source_hash():
+    files = d.get("source_files") or [os.path.basename(d.get("source_file", ""))]
+    if files != APPLY_SOURCES[form] or d.get("source_sha1") != kernel_source_hash(files):
         return None
     return d["dram_bytes_per_apply"] * apply_bytes(info, *d["val_vec_bytes"]) / d["algorithmic_bytes_per_apply"]
 
@@ -609,12 +622,17 @@ def main():
     val_b, vec_b = {"fp64": (8, 8), "fp32": (4, 4), "mixed": (4, 8)}[args.precision]
     bytes_per = apply_bytes(info, val_b, vec_b)
     achieved = bytes_per / (ms / calls / 1e3) / 1e9 if calls else 0.0
-    traffic = measured_traffic(args.precision, info)
+    forms = sorted({s["ildl"]["apply_form"] for s in stats})
+    form = forms[0] if len(forms) == 1 else None
+    traffic = measured_traffic(args.precision, info, form) if form is not None else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": traffic, "kernel": "ildl_apply_persistent_kernel (one cooperative launch: gather, "
-                                               "forward level sweeps, dense tail, backward level sweeps)",
+                "traffic": traffic,
+                "kernel": APPLY_KERNELS[form] if form is not None else
+                " / ".join(APPLY_KERNELS[f] for f in forms) + " (autotuned per factor)",
                 "peak_kind": peak_kind + " (hbm_gbs, copy test)", "algorithmic_bytes_per_launch": bytes_per,
-                "avg_launch_ms": ms / calls if calls else None, "launches_timed": calls}
+                "avg_launch_ms": ms / calls if calls else None, "launches_timed": calls,
+                "timed_as": "CUDA events around each ildl apply call on the solver's stream (the dataflow form's "
+                            "two sentinel fills of w and z included)"}
     # the inner solve's stencil runs in binary64 for the binary64 and mixed
     # solves (24 B/site: x, eps, y) and in binary32 for the binary32 one
     stencil_prec = "binary32" if args.precision == "fp32" else "binary64"
@@ -677,7 +695,8 @@ def main():
                 "max_residual": max(s["max_residual"] for s in stats),
                 "preconditioner": {"levels": info["levels"], "n_dense": info["n_dense"], "nnz_L": info["nnz_L"],
                                    "fill": info["fill"], "n_2x2": info["n_2x2"],
-                                   "apply_threads_per_row_shift": [s["ildl"]["apply_shift"] for s in stats]},
+                                   "apply_threads_per_row_shift": [s["ildl"]["apply_shift"] for s in stats],
+                                   "apply_form": [s["ildl"]["apply_form"] for s in stats]},
                 "fp64": fp64, "e2e": e2e, "roofline": roofline, "batch": batch_c4, "serving": serving,
                 "stencil": {"precision": stencil_prec, "bytes_per_site": stencil_bps, "sites": n,
                             "calls": stencil_calls, "avg_ms": stencil_ms / stencil_calls if stencil_calls else None,

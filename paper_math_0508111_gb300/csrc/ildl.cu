@@ -638,14 +638,24 @@ int autotune_apply(ildl_s* f, DevFactor<T>& d, int form_req, cudaStream_t st) {
 }  // namespace
 
 int ildl_upload_all(ildl_s* f, cudaStream_t st, int copies, bool tune, int form_req) {
+  using Clock = std::chrono::steady_clock;
+  auto ms_since = [](Clock::time_point t) {
+    return std::chrono::duration<double, std::milli>(Clock::now() - t).count();
+  };
+  const bool verbose = std::getenv("AJD_SETUP_VERBOSE") != nullptr;
+  auto t = Clock::now();
   if (f->F.dense_is_matrix) {
     AJD_TRY(invert_dense_on_device(f->F.dense_inv, f->F.n_dense, st));
     f->F.dense_is_matrix = false;
   }
+  if (verbose) std::fprintf(stderr, "ildl dense inverse on the device (%d rows): %.1f ms\n", f->F.n_dense, ms_since(t));
+  t = Clock::now();
   f->F.apply_form = form_req >= 0 ? form_req : kDefaultApplyForm;
   f->F.apply_shift = 0;
   if (copies & kCopyF64) AJD_TRY(upload_factor<double>(f->F, f->d64, st));
   if (copies & kCopyF32) AJD_TRY(upload_factor<float>(f->F, f->d32, st));
+  if (verbose) std::fprintf(stderr, "ildl upload (copies %d): %.1f ms\n", copies, ms_since(t));
+  t = Clock::now();
   if (tune) {
     // tuned on the copy a solve uses first (binary32 for the mixed and
     // binary32 solves); the other copy takes the same choice
@@ -653,6 +663,9 @@ int ildl_upload_all(ildl_s* f, cudaStream_t st, int copies, bool tune, int form_
     else if (copies & kCopyF64) AJD_TRY(autotune_apply<double>(f, f->d64, form_req, st));
     if ((copies & kCopyF32) && (copies & kCopyF64))
       AJD_TRY(set_apply_shape(f->F, f->d64, f->F.apply_form, f->F.apply_shift, st));
+    if (verbose)
+      std::fprintf(stderr, "ildl apply autotune (form %d shift %d): %.1f ms\n", f->F.apply_form, f->F.apply_shift,
+                   ms_since(t));
   }
   return JD_OK;
 }
@@ -873,6 +886,9 @@ int ildl_create_on_stream(anderson_t h, double sigma, const ildl_params* p, ildl
     if (prm.setup_device != 0) eng = make_device_schur(st);
     int rc = build_ildl(A, prm, f->F, /*dense_on_host=*/false, eng.get());
     eng.reset();
+    if (std::getenv("AJD_SETUP_VERBOSE"))
+      std::fprintf(stderr, "ildl host build: %.1f ms\n",
+                   std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count());
     if (rc == JD_OK) rc = ildl_upload_all(f, st, copies, prm.autotune != 0, prm.apply_form);
     f->F.t_total_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     if (rc != JD_OK) {

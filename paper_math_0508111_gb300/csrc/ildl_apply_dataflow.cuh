@@ -117,18 +117,21 @@ __device__ __forceinline__ bool settle(const U* p, U& w, int* err) {
 
 // Wait until every gathered word of a batch is written.  While a warp waits
 // for the level before to finish, one lane polls one address: the lane that
-// holds the warp's largest pending column (an entry of the latest level)
-// reloads it until it is written; thousands of lanes each polling their own
-// entries would crowd the few L2 lines that the level being finished
-// writes.  Once it is written the level is nearly done, and every lane
-// reloads its pending entries together, round by round, until none is left.
+// holds the warp's pending entry of the most recent level (the largest
+// column in a forward sweep, the smallest in a backward sweep, since
+// positions are ordered level by level) reloads it until it is written;
+// thousands of lanes each polling their own entries would crowd the few L2
+// lines that the level being finished writes.  Once it is written the level
+// is nearly done, and every lane reloads its pending entries together, round
+// by round, until none is left.
 template <int B, typename U>
-__device__ __forceinline__ bool settle_batch(const U* xw, const int (&c)[B], U (&xv)[B], int* err) {
+__device__ __forceinline__ bool settle_batch(const U* xw, const int (&c)[B], U (&xv)[B], int* err, bool backward) {
   const int lane = threadIdx.x & 31;
-  int mine = -1;  // this lane's largest pending column
+  // key of a pending column: larger = written later (-1: none pending)
+  int mine = -1;
 #pragma unroll
   for (int i = 0; i < B; ++i)
-    if (c[i] >= 0 && xv[i] == ~U(0)) mine = max(mine, c[i]);
+    if (c[i] >= 0 && xv[i] == ~U(0)) mine = max(mine, backward ? 0x7fffffff - c[i] : c[i]);
   int top = mine;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) top = max(top, __shfl_xor_sync(0xffffffffu, top, o));
@@ -137,7 +140,8 @@ __device__ __forceinline__ bool settle_batch(const U* xw, const int (&c)[B], U (
   const int leader = __ffs(__ballot_sync(0xffffffffu, mine == top)) - 1;
   int bad = 0;
   if (lane == leader) {
-    U w = ld_flow(xw + top);
+    const int col = backward ? 0x7fffffff - top : top;
+    U w = ld_flow(xw + col);
     while (w == ~U(0)) {
       ++spins;
       if (spins > kSpinLimit) {
@@ -150,7 +154,7 @@ __device__ __forceinline__ bool settle_batch(const U* xw, const int (&c)[B], U (
         break;
       }
       if (spins > 2) __nanosleep(32);
-      w = ld_flow(xw + top);
+      w = ld_flow(xw + col);
     }
   }
   if (__shfl_sync(0xffffffffu, bad, leader)) return false;
@@ -174,81 +178,111 @@ __device__ __forceinline__ bool settle_batch(const U* xw, const int (&c)[B], U (
   }
 }
 
-// Unit descriptor (int4): kind | G << 8, first row, end row, first unit.
+// Rows of one level, G lanes per row, 32/G rows per unit: this warp's units
+// k, k + kstep, ... below kend of the level, in order.  The next unit's row
+// pointers and heads are loaded before the current unit's gathers, and its
+// first batch of indices and values right after them, so a unit costs about
+// one memory round trip beyond the waits for its inputs.  Returns false
+// after a timeout (uniform over the warp).
 template <typename V, typename X, typename IO, int G>
-__device__ __forceinline__ bool flow_rows(const ApplyArgs<V, X, IO>& a, int kind, int p0, int p1, int k, int* err) {
+__device__ __forceinline__ bool flow_rows(const ApplyArgs<V, X, IO>& a, int kind, int p0, int p1, int k, int kstep,
+                                          int kend, int* err) {
   using W = typename ValueReg<V, X>::type;
   using U = typename FlowWord<X>::U;
   constexpr int B = 8;  // entries per lane and batch
-  const int lane = threadIdx.x & 31, t = lane % G;
-  const int p = p0 + k * (32 / G) + lane / G;
-  const bool live = p < p1;
-  const int* ptr = kind == PH_FWD ? a.Lptr : a.Uptr;
-  const int* col = kind == PH_FWD ? a.Lcol : a.Ucol;
-  const V* val = kind == PH_FWD ? a.Lval : a.Uval;
-  const U* xw = words(kind == PH_FWD ? a.w : a.z);  // vector read through the columns
-  int q = 0, e = 0;
+  constexpr int R = 32 / G;
+  const int lane = threadIdx.x & 31, t = lane % G, grp = lane / G;
+  const bool bwd = kind == PH_BWD;
+  const int* ptr = bwd ? a.Uptr : a.Lptr;
+  const int* col = bwd ? a.Ucol : a.Lcol;
+  const V* val = bwd ? a.Uval : a.Lval;
+  const U* xw = words(bwd ? a.z : a.w);  // vector read through the columns
+  const U* ww = words(a.w);
+  // row state: pointers, head, forward values (backward rows), one batch
+  int p = -1, q = 0, e = 0;
   RowHead<V, X, IO> h{};
-  U w0 = 0, w1 = 0;  // backward rows: the forward values of the row and its 2x2 partner
-  if (live) {
-    q = __ldg(ptr + p) + t;
-    e = __ldg(ptr + p + 1);
-    if (t == 0) {
-      h = row_head(a, kind, p);
-      if (kind == PH_BWD) {
-        w0 = ld_flow(words(a.w) + p);
-        if (h.pp >= 0) w1 = ld_flow(words(a.w) + h.pp);
+  U w0 = 0, w1 = 0;
+  int c[B];
+  W v[B];
+  int np = -1, nq = 0, ne = 0;
+  RowHead<V, X, IO> nh{};
+  U nw0 = 0, nw1 = 0;
+  auto start = [&](int kk, int& rp, int& rq, int& re, RowHead<V, X, IO>& rh, U& rw0, U& rw1) {
+    const int r = p0 + kk * R + grp;
+    rp = r < p1 ? r : -1;
+    rq = re = 0;
+    if (rp >= 0) {
+      rq = __ldg(ptr + rp) + t;
+      re = __ldg(ptr + rp + 1);
+      if (t == 0) {
+        rh = row_head(a, kind, rp);
+        if (bwd) {
+          rw0 = ld_flow(ww + rp);
+          if (rh.pp >= 0) rw1 = ld_flow(ww + rh.pp);
+        }
       }
     }
-  }
-  bool ok = true;
-  X acc = zero<X>(), acc2 = zero<X>();
-  while (__any_sync(0xffffffffu, q < e)) {  // uniform over the warp (lanes past their row gather nothing)
-    int c[B];
-    W v[B];
-    U xv[B];
+  };
+  auto batch = [&]() {
 #pragma unroll
     for (int i = 0; i < B; ++i) {
       const bool o = q + i * G < e;
       c[i] = o ? __ldg(col + q + i * G) : -1;
       v[i] = o ? ldw<W>(val + q + i * G) : W(0);
     }
+  };
+  start(k, p, q, e, h, w0, w1);
+  batch();
+  for (;;) {
+    const bool more = k + kstep < kend;
+    if (more) start(k + kstep, np, nq, ne, nh, nw0, nw1);  // in flight during this unit
+    X acc = zero<X>(), acc2 = zero<X>();
+    bool first = true;
+    while (__any_sync(0xffffffffu, q < e)) {  // uniform over the warp (lanes past their row gather nothing)
+      if (!first) batch();
+      first = false;
+      U xv[B];
 #pragma unroll
-    for (int i = 0; i < B; ++i) xv[i] = c[i] >= 0 ? ld_flow(xw + c[i]) : U(0);  // all-zero word: 0
-    if (!settle_batch<B>(xw, c, xv, err)) {
-      ok = false;
-      break;
-    }
+      for (int i = 0; i < B; ++i) xv[i] = c[i] >= 0 ? ld_flow(xw + c[i]) : U(0);  // all-zero word: 0
+      if (!settle_batch<B>(xw, c, xv, err, bwd)) return false;
 #pragma unroll
-    for (int i = 0; i < B; i += 2) {
-      mac(acc, v[i], word_value<X>(xv[i]));
-      mac(acc2, v[i + 1], word_value<X>(xv[i + 1]));
+      for (int i = 0; i < B; i += 2) {
+        mac(acc, v[i], word_value<X>(xv[i]));
+        mac(acc2, v[i + 1], word_value<X>(xv[i + 1]));
+      }
+      q += B * G;
     }
-    q += B * G;
-  }
-  // backward rows: rhs = (D^{-1} w)_p from the forward values of the row
-  // and its 2x2 partner
-  if (kind == PH_BWD && live && t == 0 && ok) {
-    const U* ww = words(a.w);
-    if (!settle(ww + p, w0, err) || (h.pp >= 0 && !settle(ww + h.pp, w1, err))) ok = false;
-    X d = mul(h.dd, word_value<X>(w0));
-    if (h.pp >= 0) d = add(d, mul(h.dof, word_value<X>(w1)));
-    h.rhs = d;
-  }
-  if (__any_sync(0xffffffffu, !ok)) return false;
-  acc = add(norm(acc), norm(acc2));
+    bool ok = true;
+    if (bwd && p >= 0 && t == 0) {
+      // rhs = (D^{-1} w)_p from the forward values of the row and its partner
+      if (!settle(ww + p, w0, err) || (h.pp >= 0 && !settle(ww + h.pp, w1, err))) ok = false;
+      X d = mul(h.dd, word_value<X>(w0));
+      if (h.pp >= 0) d = add(d, mul(h.dof, word_value<X>(w1)));
+      h.rhs = d;
+    }
+    if (__any_sync(0xffffffffu, !ok)) return false;
+    acc = add(norm(acc), norm(acc2));
 #pragma unroll
-  for (int o = G / 2; o > 0; o >>= 1) acc = add(acc, shfl_xor(acc, o, G));
-  if (live && t == 0) {
-    const X r = sub(h.rhs, acc);
-    if (kind == PH_FWD) {
-      put(a.w + p, r);
-    } else {
-      put(a.z + p, r);
-      a.out[h.perm] = to_io<IO>(mul(h.sc, r));
+    for (int o = G / 2; o > 0; o >>= 1) acc = add(acc, shfl_xor(acc, o, G));
+    if (p >= 0 && t == 0) {
+      const X r = sub(h.rhs, acc);
+      if (bwd) {
+        put(a.z + p, r);
+        a.out[h.perm] = to_io<IO>(mul(h.sc, r));
+      } else {
+        put(a.w + p, r);
+      }
     }
+    if (!more) return true;
+    k += kstep;
+    p = np;
+    q = nq;
+    e = ne;
+    h = nh;
+    w0 = nw0;
+    w1 = nw1;
+    batch();
   }
-  return true;
 }
 
 // Row r of the dense trailing block: z_d[r] = (D_d^{-1} w_d)[r], one warp.
@@ -272,7 +306,7 @@ __device__ __forceinline__ bool flow_dense_row(const ApplyArgs<V, X, IO>& a, int
       v[i] = col < a.nd ? ldw<W>(row + col) : W(0);
       xv[i] = col < a.nd ? ld_flow(wd + col) : U(0);
     }
-    if (!settle_batch<B>(wd, c, xv, err)) return false;
+    if (!settle_batch<B>(wd, c, xv, err, false)) return false;
 #pragma unroll
     for (int i = 0; i < B; i += 2) {
       mac(acc, v[i], word_value<X>(xv[i]));
@@ -306,6 +340,7 @@ ildl_apply_dataflow_kernel(ApplyArgs<V, X, IO> a, const int4* __restrict__ units
     while (sg + 1 < nseg && __ldg(&units[sg + 1].w) <= u) ++sg;
     const int4 S = __ldg(units + sg);
     const int kind = S.x & 0xFF, G = S.x >> 8, k = u - S.w;
+    const int kend = (sg + 1 < nseg ? __ldg(&units[sg + 1].w) : nunits) - S.w;  // units of the segment
     bool ok = true;
     if (kind == PH_GATHER) {
       // level 0: rows without entries, w = s b[perm]
@@ -314,14 +349,16 @@ ildl_apply_dataflow_kernel(ApplyArgs<V, X, IO> a, const int4* __restrict__ units
     } else if (kind == PH_DENSE) {
       ok = flow_dense_row(a, k, err);
     } else {
+      // all of this warp's units of the level at once (k, k + warps, ...)
       switch (G) {  // lanes per row, fixed per level at upload
-        case 1: ok = flow_rows<V, X, IO, 1>(a, kind, S.y, S.z, k, err); break;
-        case 2: ok = flow_rows<V, X, IO, 2>(a, kind, S.y, S.z, k, err); break;
-        case 4: ok = flow_rows<V, X, IO, 4>(a, kind, S.y, S.z, k, err); break;
-        case 8: ok = flow_rows<V, X, IO, 8>(a, kind, S.y, S.z, k, err); break;
-        case 16: ok = flow_rows<V, X, IO, 16>(a, kind, S.y, S.z, k, err); break;
-        default: ok = flow_rows<V, X, IO, 32>(a, kind, S.y, S.z, k, err); break;
+        case 1: ok = flow_rows<V, X, IO, 1>(a, kind, S.y, S.z, k, warps, kend, err); break;
+        case 2: ok = flow_rows<V, X, IO, 2>(a, kind, S.y, S.z, k, warps, kend, err); break;
+        case 4: ok = flow_rows<V, X, IO, 4>(a, kind, S.y, S.z, k, warps, kend, err); break;
+        case 8: ok = flow_rows<V, X, IO, 8>(a, kind, S.y, S.z, k, warps, kend, err); break;
+        case 16: ok = flow_rows<V, X, IO, 16>(a, kind, S.y, S.z, k, warps, kend, err); break;
+        default: ok = flow_rows<V, X, IO, 32>(a, kind, S.y, S.z, k, warps, kend, err); break;
       }
+      u += (kend - 1 - k) / warps * warps;  // the last of those units
     }
     if (!ok) return;  // a wait timed out (uniform over the warp)
     if (stamps && lane == 0) {
