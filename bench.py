@@ -83,7 +83,7 @@ def parse():
     ap.add_argument("--cpu-L", type=int, default=30, help="lattice of the CPU oracle baseline sample")
     ap.add_argument("--serve-slots", type=int, default=4)
     ap.add_argument("--serve-setup-threads", type=int, default=3)
-    ap.add_argument("--setup-threads", type=int, default=2,
+    ap.add_argument("--setup-threads", type=int, default=4,
                     help="concurrent preconditioner builds in the pipelined batch")
     ap.add_argument("--n-dense", type=int, default=0,
                     help="rows of the preconditioner's dense tail (0: the library's default)")

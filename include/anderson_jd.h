@@ -174,8 +174,8 @@ typedef struct {
   int max_levels; /* maximum number of sparse levels [256]                    */
   int n_dense;    /* the remaining Schur complement is factored densely once
                      it has at most this many rows (at most 8000); 0 = n/16
-                     clamped to 1000..6000 (6000 at n = 10^6; small
-                     lattices keep the dense inversion cheap) [0]           */
+                     clamped to 1000..3000 (3000 at n = 10^6: the inversion
+                     is O(n_dense^3) binary64 work on the device) [0]       */
   int matching;   /* levels that use the maximum-product matching, 1x1/2x2
                      cycle split and symmetric dual scaling (Sections 5.1,
                      5.2); deeper levels use row-max scaling and 1x1

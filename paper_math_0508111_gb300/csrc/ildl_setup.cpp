@@ -165,6 +165,8 @@ int max_product_matching(const SymCsr& A, std::vector<int>& match_col, std::vect
   MatchWork local;
   MatchWork& mw = work ? *work : local;
   const int n = A.n;
+  static const bool verbose = std::getenv("AJD_MATCH_VERBOSE") != nullptr;
+  const auto t_begin = Clock::now();
   rowmax.assign(n, 0.0);
   std::vector<double> logmax(n);
   const bool known = mw.rowmax_in.size() == (size_t)n;
@@ -210,6 +212,7 @@ int max_product_matching(const SymCsr& A, std::vector<int>& match_col, std::vect
     }
     u[i] = best == kInf ? 0.0 : best;
   }
+  const double ms_duals = ms_since(t_begin);
   match_col.assign(n, -1);
   std::vector<int> match_row(n, -1);
   // greedy start on zero reduced costs: first every row whose diagonal has
@@ -274,6 +277,7 @@ int max_product_matching(const SymCsr& A, std::vector<int>& match_col, std::vect
     int s = -1, sink = -1;
     double D = 0.0;
     std::vector<int> touched, scanned, tree_rows, path;  // path: (row, col) pairs from the sink back
+    std::vector<int> read;  // columns read but never given a distance (beyond the best sink)
     std::vector<double> tree_d, scanned_d;
   };
   using Work = MatchWork::Search;
@@ -298,43 +302,68 @@ int max_product_matching(const SymCsr& A, std::vector<int>& match_col, std::vect
     R.tree_d.clear();
     R.scanned_d.clear();
     R.path.clear();
+    R.read.clear();
     R.sink = -1;
     int i = R.s;
     double di = 0.0;
     R.tree_rows.push_back(i);
     R.tree_d.push_back(0.0);
+    // Columns leave the heap in (distance, index) order and the search ends
+    // at the first free column to leave it.  A free column is therefore
+    // kept aside as the best sink found so far (lsap, isap) instead of
+    // being pushed, and a column that would leave after it is never pushed:
+    // the same path and the same scanned columns as a search that pushes
+    // everything, with a heap a fraction of the size.  Such columns were
+    // still read; they are listed for the batch's conflict test.
+    double lsap = kInf;
+    int isap = -1;
+    auto after_sink = [&](double d, int j) { return d > lsap || (d == lsap && j > isap); };
     for (;;) {
       for (int64_t p = A.ptr[i]; p < A.ptr[i + 1]; ++p) {
         const int j = A.col[p];
         const double c = cost(i, p);
         if (W.done[j] || c == kInf) continue;
         const double nd = di + std::max(0.0, c - u[i] - v[j]);
+        if (isap >= 0 && after_sink(nd, j)) {
+          if (W.dist[j] == kInf) R.read.push_back(j);
+          continue;
+        }
         if (nd < W.dist[j]) {
           if (W.dist[j] == kInf) R.touched.push_back(j);
           W.dist[j] = nd;
           W.pred[j] = i;
-          heap.push_back({nd, j});
-          std::push_heap(heap.begin(), heap.end(), later);
+          if (match_col[j] < 0) {
+            lsap = nd;
+            isap = j;
+          } else {
+            heap.push_back({nd, j});
+            std::push_heap(heap.begin(), heap.end(), later);
+          }
         }
       }
       int jmin = -1;
       while (!heap.empty()) {
+        const Item top = heap.front();
+        if (isap >= 0 && after_sink(top.first, top.second)) break;
         std::pop_heap(heap.begin(), heap.end(), later);
-        const Item it = heap.back();
         heap.pop_back();
-        if (!W.done[it.second] && it.first == W.dist[it.second]) {
-          jmin = it.second;
+        if (!W.done[top.second] && top.first == W.dist[top.second]) {
+          jmin = top.second;
           break;
         }
       }
-      if (jmin < 0) break;  // no augmenting path from s
+      if (jmin < 0) {
+        if (isap >= 0) {  // the best free column leaves the heap next
+          W.done[isap] = 1;
+          R.scanned.push_back(isap);
+          R.scanned_d.push_back(lsap);
+          R.sink = isap;
+        }
+        break;  // else no augmenting path from s
+      }
       W.done[jmin] = 1;
       R.scanned.push_back(jmin);
       R.scanned_d.push_back(W.dist[jmin]);
-      if (match_col[jmin] < 0) {
-        R.sink = jmin;
-        break;
-      }
       i = match_col[jmin];
       di = W.dist[jmin];
       R.tree_rows.push_back(i);
@@ -356,9 +385,13 @@ int max_product_matching(const SymCsr& A, std::vector<int>& match_col, std::vect
       W.done[j] = 0;
     }
   };
+  const double ms_greedy = ms_since(t_begin) - ms_duals;
   std::vector<int> open;
   for (int i = 0; i < n; ++i)
     if (match_row[i] < 0) open.push_back(i);
+  int64_t n_searches = 0, n_scanned = 0;
+  int n_batches = 0;
+  double ms_par = 0.0;
   int unmatched = 0;
   std::vector<int> wrow(n, -1), wcol(n, -1);  // batch that last wrote a row / column
   std::vector<Search> batch;
@@ -372,17 +405,25 @@ int max_product_matching(const SymCsr& A, std::vector<int>& match_col, std::vect
     rows.swap(retry);
     while (rows.size() < K && head < open.size()) rows.push_back(open[head++]);
     batch.resize(rows.size());
+    const auto t_par = Clock::now();
 #pragma omp parallel for schedule(dynamic, 1)
     for (size_t t = 0; t < rows.size(); ++t) {
       batch[t].s = rows[t];
       search(tw[omp_get_thread_num()], batch[t]);
     }
     ++epoch;
+    if (verbose) ms_par += ms_since(t_par);
+    if (verbose) {
+      ++n_batches;
+      n_searches += (int64_t)rows.size();
+      for (size_t t = 0; t < rows.size(); ++t) n_scanned += (int64_t)batch[t].scanned.size();
+    }
     for (size_t t = 0; t < rows.size(); ++t) {
       Search& R = batch[t];
       bool clash = false;
       for (int r : R.tree_rows) clash = clash || wrow[r] == epoch;
       for (int j : R.touched) clash = clash || wcol[j] == epoch;
+      for (int j : R.read) clash = clash || wcol[j] == epoch;
       if (clash) {
         retry.push_back(R.s);
         continue;
@@ -405,6 +446,12 @@ int max_product_matching(const SymCsr& A, std::vector<int>& match_col, std::vect
       }
     }
   }
+  if (verbose)
+    std::fprintf(stderr,
+                 "  matching n=%d nnz=%lld: duals %.1f greedy %.1f searches %.1f ms (%zu open rows, %lld searches "
+                 "in %d batches, %lld columns scanned, parallel part %.1f ms)\n",
+                 n, (long long)A.ptr[n], ms_duals, ms_greedy, ms_since(t_begin) - ms_duals - ms_greedy, open.size(),
+                 (long long)n_searches, n_batches, (long long)n_scanned, ms_par);
   if (unmatched) {
     // structurally singular: pair the leftover rows and columns in index
     // order and give them neutral duals (scaling then reduces to 1/sqrt(a_i))
@@ -720,9 +767,13 @@ int build_ildl(const SymCsr& A, const ildl_params& prm, HostFactor& F, bool dens
 
   const double gamma = prm.gamma < 0.0 ? default_gamma(n, false) : prm.gamma;
   const int max_levels = prm.max_levels > 0 ? prm.max_levels : 64;
-  // dense tail: the given size, else n/16 clamped to 1000..6000 (the
-  // O(n_dense^3) inversion stays small for small lattices)
-  const int n_dense = prm.n_dense > 0 ? prm.n_dense : std::max(1000, std::min(6000, n / 16));
+  // dense tail: the given size, else n/16 clamped to 1000..3000.  Its
+  // Gauss-Jordan inversion costs O(n_dense^3) binary64 work on a GPU whose
+  // FP64 pipe is narrow (about 0.2 s at 3000 rows, 1.7 s at 6000), while the
+  // extra sparse levels that a smaller tail leaves cost little in the
+  // dataflow apply; the bound keeps the inversion short when setups share
+  // the device with solves
+  const int n_dense = prm.n_dense > 0 ? prm.n_dense : std::max(1000, std::min(3000, n / 16));
   constexpr int kDenseHardMax = 8000;
 
   F = HostFactor();
