@@ -205,7 +205,7 @@ typedef struct {
                      starts once the entries it reads are written (no
                      per-level synchronisation); < 0 = chosen by the
                      autotuner where it runs (1 unless 0 is faster by more
-                     than 5%), else 1 [-1]                                   */
+                     than 25%), else 1 [-1]                                   */
 } ildl_params;
 
 /* Fill *p with the defaults above. */

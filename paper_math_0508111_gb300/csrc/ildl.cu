@@ -154,14 +154,12 @@ void free_dev(DevFactor<T>& d) {
   cudaFree(d.dof);
   cudaFree(d.partner);
   cudaFree(d.dense);
-  cudaFree(d.w);
-  cudaFree(d.z);
+  cudaFree(d.w);  // z lies in the same allocation
   cudaFree(d.phases);
   cudaFree(d.units);
   cudaFree(d.bar);
   cudaFree(d.done);
-  cudaFree(d.wdf);
-  cudaFree(d.zdf);
+  cudaFree(d.wdf);  // and zdf in wdf's
   d = DevFactor<T>();
 }
 
@@ -306,19 +304,15 @@ int upload_factor(const HostFactor& F, DevFactor<T>& d, cudaStream_t st) {
   AJD_TRY(upload(&d.dense, F.dense_inv, st));
   const size_t nb = std::max<size_t>(1, F.n);
   const bool poison = std::getenv("AJD_POISON_ALLOC") != nullptr;  // NaN-filled work vectors (tests)
-  AJD_CUDA(cudaMalloc(&d.w, nb * sizeof(T)));
-  AJD_CUDA(cudaMalloc(&d.z, nb * sizeof(T)));
-  if (poison) {
-    AJD_CUDA(cudaMemsetAsync(d.w, 0xFF, nb * sizeof(T), st));
-    AJD_CUDA(cudaMemsetAsync(d.z, 0xFF, nb * sizeof(T), st));
-  }
+  // w and z adjacent (z = w + n), so that the dataflow apply fills both with
+  // its sentinel in one memset; z is not a separate allocation
+  AJD_CUDA(cudaMalloc(&d.w, 2 * nb * sizeof(T)));
+  d.z = d.w + nb;
+  if (poison) AJD_CUDA(cudaMemsetAsync(d.w, 0xFF, 2 * nb * sizeof(T), st));
   if (sizeof(T) == 4) {  // float-float work vectors of the mixed apply
-    AJD_CUDA(cudaMalloc(&d.wdf, nb * sizeof(float2)));
-    AJD_CUDA(cudaMalloc(&d.zdf, nb * sizeof(float2)));
-    if (poison) {
-      AJD_CUDA(cudaMemsetAsync(d.wdf, 0xFF, nb * sizeof(float2), st));
-      AJD_CUDA(cudaMemsetAsync(d.zdf, 0xFF, nb * sizeof(float2), st));
-    }
+    AJD_CUDA(cudaMalloc(&d.wdf, 2 * nb * sizeof(float2)));
+    d.zdf = d.wdf + nb;
+    if (poison) AJD_CUDA(cudaMemsetAsync(d.wdf, 0xFF, 2 * nb * sizeof(float2), st));
   }
   // phase list of the persistent apply (threads-per-row rule unscaled; the
   // autotuner may replace it once the factor is on the device)
@@ -385,8 +379,12 @@ int launch_apply_dataflow(const ildl_s* f, const DevFactor<V>& d, X* w, X* z, co
   const HostFactor& F = f->F;
   ApplyArgs<V, X, IO> a{d.perm, d.scale, d.Lptr, d.Lcol, d.Lval, d.Uptr, d.Ucol, d.Uval, d.dd, d.dof, d.partner,
                         d.dense, w, z, b, out, F.n_dense, F.level_ptr[F.nlev]};
-  AJD_CUDA(cudaMemsetAsync(w, 0xFF, (size_t)F.n * sizeof(X), s));
-  AJD_CUDA(cudaMemsetAsync(z, 0xFF, (size_t)F.n * sizeof(X), s));
+  if (z == w + F.n) {  // the factor's own work vectors: one fill
+    AJD_CUDA(cudaMemsetAsync(w, 0xFF, 2 * (size_t)F.n * sizeof(X), s));
+  } else {
+    AJD_CUDA(cudaMemsetAsync(w, 0xFF, (size_t)F.n * sizeof(X), s));
+    AJD_CUDA(cudaMemsetAsync(z, 0xFF, (size_t)F.n * sizeof(X), s));
+  }
   const int4* units = d.units;
   int nseg = d.nseg, nunits = d.nunits;
   int* err = reinterpret_cast<int*>(d.bar + 64);
@@ -552,7 +550,8 @@ namespace {
 // threads per row halved and doubled, are timed on the device (CUDA events
 // on the setup stream: one warm-up and the fastest of three timed applies of
 // a zero vector; the apply's work does not depend on the values) and the
-// fastest is kept, the level counters only when faster by more than 5%.
+// fastest is kept, the level counters only when faster by more than 25%
+// (the timings are taken while other setups may share the device).
 // A form fixed by the caller is tuned over the threads per row only.  The
 // timed applies join the chain that orders the applies of concurrent solves,
 // so they never run beside one.  Only factors of at least kTuneMinRows rows
@@ -609,9 +608,10 @@ int autotune_apply(ildl_s* f, DevFactor<T>& d, int form_req, cudaStream_t st) {
     AJD_CUDA(cudaEventCreate(&e0));
     AJD_CUDA(cudaEventCreate(&e1));
     // the dataflow form first; the level-counter form replaces it only when
-    // clearly faster (by more than kFormMargin), so that timing noise does
-    // not flip the choice
-    constexpr double kFormMargin = 0.05;
+    // clearly faster (by more than kFormMargin): alone on the device it is
+    // slower in every precision, and timing noise under load must not flip
+    // the choice
+    constexpr double kFormMargin = 0.25;
     int best_form = -1, best_shift = 0;
     double best_ms = 0.0;
     for (int form : {1, 0}) {
