@@ -154,6 +154,11 @@ inline double log_pos(double x) {
 
 }  // namespace
 
+void log_table_data(const double** inv, const double** logc) {
+  *inv = g_log_table.inv;
+  *logc = g_log_table.logc;
+}
+
 // ---------------------------------------------------------------------------
 // Section 5.1: maximise prod_i |a_{sigma(i) i}| <=> minimise sum c_{sigma(i) i}
 // with c_ij = log a_i - log |a_ij|, a_i = max_j |a_ij|.  Sparse Kuhn–Munkres:
@@ -186,31 +191,45 @@ int max_product_matching(const SymCsr& A, std::vector<int>& match_col, std::vect
   // entry p in row i is c_i,col[p] = logmax[i] - loga[p] (+inf for zeros),
   // formed where it is used rather than stored.  v_j = min_i c_ij: by
   // symmetry column j's entries are row j's entries, with the cost taken in
-  // the row of the other index, so v comes out of the same pass.
-  dvec<double>& loga = mw.loga;  // filled (first touched) in parallel below
-  resize_discard(loga, A.val.size());
-  auto cost = [&](int i, int64_t p) { return logmax[i] - loga[p]; };
-  v.assign(n, kInf);
+  // the row of the other index, so v comes out of the same pass.  When the
+  // initial potentials come with the matrix (u_in, v_in: formed on the GPU
+  // with the same logarithm and the same exact minima), only the entries
+  // that the greedy start and the searches read take a logarithm, here.
+  const bool given = known && mw.u_in.size() == (size_t)n && mw.v_in.size() == (size_t)n;
+  dvec<double>& loga = mw.loga;
+  auto entry_log = [&](int64_t p) {
+    const double a = std::fabs(A.val[p]);
+    return a > 0.0 ? log_pos(a) : -kInf;
+  };
+  auto cost = [&](int i, int64_t p) { return logmax[i] - (given ? entry_log(p) : loga[p]); };
+  if (given) {
+    u.swap(mw.u_in);
+    v.swap(mw.v_in);
+    mw.u_in.clear();
+    mw.v_in.clear();
+  } else {
+    resize_discard(loga, A.val.size());  // filled (first touched) in parallel below
+    v.assign(n, kInf);
 #pragma omp parallel for schedule(static)
-  for (int j = 0; j < n; ++j) {
-    double best = kInf;
-    for (int64_t p = A.ptr[j]; p < A.ptr[j + 1]; ++p) {
-      const double a = std::fabs(A.val[p]);
-      const double la = a > 0.0 ? log_pos(a) : -kInf;
-      loga[p] = la;
-      if (la > -kInf) best = std::min(best, logmax[A.col[p]] - la);
+    for (int j = 0; j < n; ++j) {
+      double best = kInf;
+      for (int64_t p = A.ptr[j]; p < A.ptr[j + 1]; ++p) {
+        const double la = entry_log(p);
+        loga[p] = la;
+        if (la > -kInf) best = std::min(best, logmax[A.col[p]] - la);
+      }
+      v[j] = best == kInf ? 0.0 : best;
     }
-    v[j] = best == kInf ? 0.0 : best;
-  }
-  u.assign(n, kInf);
+    u.assign(n, kInf);
 #pragma omp parallel for schedule(static)
-  for (int i = 0; i < n; ++i) {
-    double best = kInf;
-    for (int64_t p = A.ptr[i]; p < A.ptr[i + 1]; ++p) {
-      const double c = cost(i, p);
-      if (c < kInf) best = std::min(best, c - v[A.col[p]]);
+    for (int i = 0; i < n; ++i) {
+      double best = kInf;
+      for (int64_t p = A.ptr[i]; p < A.ptr[i + 1]; ++p) {
+        const double c = cost(i, p);
+        if (c < kInf) best = std::min(best, c - v[A.col[p]]);
+      }
+      u[i] = best == kInf ? 0.0 : best;
     }
-    u[i] = best == kInf ? 0.0 : best;
   }
   const double ms_duals = ms_since(t_begin);
   match_col.assign(n, -1);
@@ -1232,7 +1251,10 @@ int build_ildl(const SymCsr& A, const ildl_params& prm, HostFactor& F, bool dens
       lv.bmat = bmat.data();
       lv.is2x2 = is2.data();
       lv.tau = tau;
-      const int erc = engine->schur(lv, Sn, next_rowmax);
+      // the next level's matching potentials come with S' when it matches
+      const bool next_matches = prm.matching != 0 && (prm.matching < 0 || level + 1 < prm.matching);
+      const int erc = next_matches ? engine->schur(lv, Sn, next_rowmax, &mwork.u_in, &mwork.v_in)
+                                   : engine->schur(lv, Sn, next_rowmax, nullptr, nullptr);
       if (erc != JD_OK) return erc;
       ts_num = ms_since(t_schur) - ts_rec;
     } else {
@@ -1485,6 +1507,8 @@ int build_ildl(const SymCsr& A, const ildl_params& prm, HostFactor& F, bool dens
     release(mwork.loga);
     release(mwork.threads);
     release(mwork.rowmax_in);
+    release(mwork.u_in);
+    release(mwork.v_in);
     release(Snext.ptr);
     release(Snext.col);
     release(Snext.val);

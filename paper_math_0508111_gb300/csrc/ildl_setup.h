@@ -121,7 +121,11 @@ class SchurEngine {
   virtual ~SchurEngine() = default;
   virtual int begin(const SymCsr& A) = 0;
   virtual int scale(const double* d, int m) = 0;
-  virtual int schur(const SchurLevel& lv, SymCsr& Sn, std::vector<double>& rowmax) = 0;
+  // S' of the level, its row maxima and, when u and v are given, the
+  // matching's dual potentials of S' (as max_product_matching forms them
+  // before its searches: the same bits)
+  virtual int schur(const SchurLevel& lv, SymCsr& Sn, std::vector<double>& rowmax, std::vector<double>* u,
+                    std::vector<double>* v) = 0;
 };
 
 // Default weak-coupling threshold gamma of the independent sets for an
@@ -156,7 +160,16 @@ struct MatchWork {
   // optional: max |a_ij| of every row of the next matrix, when the caller
   // has it already (one pass over the matrix fewer); used if it has n entries
   std::vector<double> rowmax_in;
+  // optional, with rowmax_in: the initial dual potentials u, v of the next
+  // matrix, formed elsewhere (the GPU that formed the matrix) with the same
+  // arithmetic; the matching then takes log|a_ij| only of the entries its
+  // greedy start and searches read.  Used once if both have n entries.
+  std::vector<double> u_in, v_in;
 };
+
+// The table of the matching's division-free logarithm (128 values of 1/c_k
+// and of ln c_k, c_k = 1 + k/128), for a device copy of the same function.
+void log_table_data(const double** inv, const double** logc);
 int max_product_matching(const SymCsr& A, std::vector<int>& match_col, std::vector<double>& u,
                          std::vector<double>& v, std::vector<double>& rowmax, MatchWork* work = nullptr);
 

@@ -32,6 +32,8 @@
 
 #include <omp.h>
 
+#include <math_constants.h>
+
 #include "common.cuh"
 #include "ildl_setup.h"
 #include "schur_gpu.h"
@@ -336,6 +338,92 @@ __global__ void scale_kernel(const int64_t* __restrict__ ptr, const int* __restr
   }
 }
 
+// ---- the next level's matching potentials ----
+// The host matching (Section 5.1) starts from u_i = min_j (c_ij - v_j) and
+// v_j = min_i c_ij with c_ij = log a_i - log |a_ij|, a_i the row maximum.
+// Formed here from S' while it is on the device, with the host's
+// logarithm re-done step for step (the same table, every product and sum
+// rounded to nearest, no fused multiply-adds) and exact minima (order does
+// not matter), so the potentials are the host's bit for bit and the host
+// only takes logarithms of the entries its searches read.  Subnormal,
+// infinite or NaN arguments, which the host hands to its libm, go to the
+// device's log here (entries that small or large do not occur in S').
+__constant__ double c_log_inv[128];
+__constant__ double c_log_c[128];
+
+__device__ __forceinline__ double log_pos_dev(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int ef = (int)((b >> 52) & 0x7ff);
+  if (ef == 0 || ef == 0x7ff) return log(x);
+  const int k = (int)((b >> 45) & 127);
+  const double m = __longlong_as_double((long long)((b & 0x000fffffffffffffull) | 0x3ff0000000000000ull));
+  const double r = k == 0 ? __dsub_rn(m, 1.0) : __dsub_rn(__dmul_rn(m, c_log_inv[k]), 1.0);
+  double t = 1.0 / 9.0;
+  t = __dsub_rn(__dmul_rn(t, r), 1.0 / 8.0);
+  t = __dadd_rn(__dmul_rn(t, r), 1.0 / 7.0);
+  t = __dsub_rn(__dmul_rn(t, r), 1.0 / 6.0);
+  t = __dadd_rn(__dmul_rn(t, r), 1.0 / 5.0);
+  t = __dsub_rn(__dmul_rn(t, r), 1.0 / 4.0);
+  t = __dadd_rn(__dmul_rn(t, r), 1.0 / 3.0);
+  t = __dsub_rn(__dmul_rn(t, r), 1.0 / 2.0);
+  t = __dadd_rn(__dmul_rn(t, r), 1.0);
+  return __dadd_rn(__dmul_rn((double)(ef - 1023), 0.6931471805599453), __dadd_rn(c_log_c[k], __dmul_rn(r, t)));
+}
+
+__device__ __forceinline__ double entry_log_dev(double a) {
+  a = fabs(a);
+  return a > 0.0 ? log_pos_dev(a) : -CUDART_INF;
+}
+
+__device__ __forceinline__ double warp_min(double x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x = fmin(x, __shfl_xor_sync(0xffffffffu, x, o));
+  return x;
+}
+
+// logmax_i = log a_i (a_i = 1 for an empty row)
+__global__ void logmax_kernel(const double* __restrict__ rowmax, double* __restrict__ logmax, int m) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+    const double r = rowmax[i];
+    logmax[i] = log_pos_dev(r == 0.0 ? 1.0 : r);
+  }
+}
+
+// v_j = min over row j (= column j) of logmax[col] - log|a| (0 if none)
+__global__ void duals_v_kernel(const int64_t* __restrict__ ptr, const int* __restrict__ col,
+                               const double* __restrict__ val, const double* __restrict__ logmax,
+                               double* __restrict__ v, int m) {
+  const int lane = threadIdx.x & 31;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < m; j += nwarps) {
+    double best = CUDART_INF;
+    for (int64_t p = ptr[j] + lane; p < ptr[j + 1]; p += 32) {
+      const double la = entry_log_dev(val[p]);
+      if (la > -CUDART_INF) best = fmin(best, __dsub_rn(logmax[col[p]], la));
+    }
+    best = warp_min(best);
+    if (lane == 0) v[j] = best == CUDART_INF ? 0.0 : best;
+  }
+}
+
+// u_i = min over row i of (logmax_i - log|a|) - v[col] (0 if none)
+__global__ void duals_u_kernel(const int64_t* __restrict__ ptr, const int* __restrict__ col,
+                               const double* __restrict__ val, const double* __restrict__ logmax,
+                               const double* __restrict__ v, double* __restrict__ u, int m) {
+  const int lane = threadIdx.x & 31;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < m; i += nwarps) {
+    const double lm = logmax[i];
+    double best = CUDART_INF;
+    for (int64_t p = ptr[i] + lane; p < ptr[i + 1]; p += 32) {
+      const double c = __dsub_rn(lm, entry_log_dev(val[p]));
+      if (c < CUDART_INF) best = fmin(best, __dsub_rn(c, v[col[p]]));
+    }
+    best = warp_min(best);
+    if (lane == 0) u[i] = best == CUDART_INF ? 0.0 : best;
+  }
+}
+
 // ---- pinned host staging, pooled across setups ----
 // S' comes back through page-locked memory (a copy into fresh pageable pages
 // runs at a few GB/s); the buffers are kept for the next setup of the
@@ -419,7 +507,13 @@ struct DBuf {
 
 class DeviceSchur final : public SchurEngine {
  public:
-  explicit DeviceSchur(cudaStream_t st) : st_(st) {}
+  explicit DeviceSchur(cudaStream_t st) : st_(st) {
+    const double *inv = nullptr, *logc = nullptr;
+    log_table_data(&inv, &logc);
+    table_rc_ = cudaMemcpyToSymbolAsync(c_log_inv, inv, 128 * sizeof(double), 0, cudaMemcpyHostToDevice, st_);
+    if (table_rc_ == cudaSuccess)
+      table_rc_ = cudaMemcpyToSymbolAsync(c_log_c, logc, 128 * sizeof(double), 0, cudaMemcpyHostToDevice, st_);
+  }
 
   int begin(const SymCsr& A) override {
     m_ = A.n;
@@ -443,7 +537,11 @@ class DeviceSchur final : public SchurEngine {
     return JD_OK;  // ordered before the level's Schur complement on the stream
   }
 
-  int schur(const SchurLevel& lv, SymCsr& Sn, std::vector<double>& rowmax) override {
+  int schur(const SchurLevel& lv, SymCsr& Sn, std::vector<double>& rowmax, std::vector<double>* u,
+            std::vector<double>* v) override {
+    if (table_rc_ != cudaSuccess)
+      return fail(JD_EDEVICE, "gpu schur: logarithm table upload: %s", cudaGetErrorString(table_rc_));
+    const bool duals = u && v;
     const auto t0 = std::chrono::steady_clock::now();
     auto ms = [&]() { return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count(); };
     double t_bounds = 0, t_up = 0, t_k1 = 0, t_ptr = 0, t_k2 = 0;
@@ -555,6 +653,15 @@ class DeviceSchur final : public SchurEngine {
     sort_lower_kernel<<<gw, 32 * kWarpsPerCta, 0, st_>>>(lowcnt_.p, nptr_.p, ncol_.p, nval_.p, rowmax_.p, gkeys_.p,
                                                          gvals_.p, goff_.p, mc);
     count_launches(2);
+    if (duals) {
+      AJD_TRY(logmax_.reserve(mc));
+      AJD_TRY(du_.reserve(mc));
+      AJD_TRY(dv_.reserve(mc));
+      logmax_kernel<<<grid_for(mc), 256, 0, st_>>>(rowmax_.p, logmax_.p, mc);
+      duals_v_kernel<<<grid_for(mc), 256, 0, st_>>>(nptr_.p, ncol_.p, nval_.p, logmax_.p, dv_.p, mc);
+      duals_u_kernel<<<grid_for(mc), 256, 0, st_>>>(nptr_.p, ncol_.p, nval_.p, logmax_.p, dv_.p, du_.p, mc);
+      count_launches(3);
+    }
     AJD_CHECK_LAUNCH();
     AJD_TRY(sync());
     t_k2 = ms();
@@ -562,16 +669,26 @@ class DeviceSchur final : public SchurEngine {
     // host's arrays by all threads (which also spreads the first touch of
     // their pages)
     const size_t vbytes = nnz * sizeof(double), cbytes = nnz * sizeof(int), mbytes = mc * sizeof(double);
-    AJD_TRY(stage_.reserve(vbytes + cbytes + mbytes + 64));
+    AJD_TRY(stage_.reserve(vbytes + cbytes + 3 * mbytes + 64));
     char* hv = static_cast<char*>(stage_.p);
     char* hc = hv + vbytes;
     char* hm = hc + ((cbytes + 15) & ~(size_t)15);
+    char* hu = hm + mbytes;
+    char* hw = hu + mbytes;
     AJD_CUDA(cudaMemcpyAsync(hv, nval_.p, vbytes, cudaMemcpyDeviceToHost, st_));
     AJD_CUDA(cudaMemcpyAsync(hc, ncol_.p, cbytes, cudaMemcpyDeviceToHost, st_));
     AJD_CUDA(cudaMemcpyAsync(hm, rowmax_.p, mbytes, cudaMemcpyDeviceToHost, st_));
+    if (duals) {
+      AJD_CUDA(cudaMemcpyAsync(hu, du_.p, mbytes, cudaMemcpyDeviceToHost, st_));
+      AJD_CUDA(cudaMemcpyAsync(hw, dv_.p, mbytes, cudaMemcpyDeviceToHost, st_));
+    }
     Sn.col.resize(nnz);
     Sn.val.resize(nnz);
     rowmax.resize(mc);
+    if (duals) {
+      u->resize(mc);
+      v->resize(mc);
+    }
     AJD_TRY(sync());
     {
       const double* sv = reinterpret_cast<const double*>(hv);
@@ -585,6 +702,10 @@ class DeviceSchur final : public SchurEngine {
         std::memcpy(dc + i0, sc + i0, (i1 - i0) * sizeof(int));
       }
       std::memcpy(rowmax.data(), hm, mbytes);
+      if (duals) {
+        std::memcpy(u->data(), hu, mbytes);
+        std::memcpy(v->data(), hw, mbytes);
+      }
     }
     if (verbose_)
       std::fprintf(stderr, "  gpu schur m=%d C=%d nnz'=%lld slots=%lld: bounds %.1f upload %.1f rows+count %.1f ptr %.1f "
@@ -611,7 +732,8 @@ class DeviceSchur final : public SchurEngine {
   int64_t nnz_ = 0;
   DBuf<int64_t> sptr_, nptr_, rrec_, rslot_, cptr_, off_, hoff_, goff_;
   DBuf<int> scol_, ncol_, cidx_, cnodes_, rblk_, crow_, gkeys_, ucol_, ucnt_, lowcnt_, cursor_;
-  DBuf<double> sval_, nval_, dd_, c1_, c2_, bmat_, gvals_, uval_, rowmax_;
+  DBuf<double> sval_, nval_, dd_, c1_, c2_, bmat_, gvals_, uval_, rowmax_, logmax_, du_, dv_;
+  cudaError_t table_rc_ = cudaSuccess;
   DBuf<char> is2_;
   Pinned stage_;
 };
