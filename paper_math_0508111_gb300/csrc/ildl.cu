@@ -350,24 +350,38 @@ cudaEvent_t g_chain_last = nullptr;  // completion of the last serialised apply
 void set_apply_serialization(bool on) { tl_serialize_applies = on; }
 bool apply_serialization() { return tl_serialize_applies; }
 
-// Cooperative launch of `kernel` on d.grid CTAs, ordered behind the
-// previous serialised apply when this thread serialises its applies.
-template <typename V>
-int launch_cooperative(const DevFactor<V>& d, const void* kernel, void** args, cudaStream_t s) {
+// Events that the autotuner has recorded around the next apply of this
+// thread: `begin` after the apply has joined the chain of serialised
+// applies (so waiting for another solve's apply is not timed), `end` after
+// its kernel.
+thread_local cudaEvent_t tl_time_begin = nullptr, tl_time_end = nullptr;
+
+// Cooperative launch of `kernel` on d.grid CTAs after `pre` (the apply's
+// memsets), ordered behind the previous serialised apply when this thread
+// serialises its applies.
+template <typename V, typename Pre>
+int launch_cooperative(const DevFactor<V>& d, const void* kernel, void** args, cudaStream_t s, Pre&& pre) {
+  auto body = [&]() -> int {
+    if (tl_time_begin) AJD_CUDA(cudaEventRecord(tl_time_begin, s));
+    AJD_TRY(pre());
+    AJD_CUDA(cudaLaunchCooperativeKernel(kernel, dim3(d.grid), dim3(kPersistThreads), args, 0, s));
+    if (tl_time_end) AJD_CUDA(cudaEventRecord(tl_time_end, s));
+    return JD_OK;
+  };
   if (tl_serialize_applies) {
     // concurrent solvers: this apply starts on the device only after the
     // previous serialised apply (of any thread) has finished, so no two of
     // these grid-wide cooperative kernels ever run at the same time
     std::lock_guard<std::mutex> lk(g_chain_mu);
     if (g_chain_last) AJD_CUDA(cudaStreamWaitEvent(s, g_chain_last, 0));
-    AJD_CUDA(cudaLaunchCooperativeKernel(kernel, dim3(d.grid), dim3(kPersistThreads), args, 0, s));
+    AJD_TRY(body());
     cudaEvent_t ev = nullptr;
     AJD_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
     AJD_CUDA(cudaEventRecord(ev, s));
     if (g_chain_last) cudaEventDestroy(g_chain_last);  // released once it has completed
     g_chain_last = ev;
   } else {
-    AJD_CUDA(cudaLaunchCooperativeKernel(kernel, dim3(d.grid), dim3(kPersistThreads), args, 0, s));
+    AJD_TRY(body());
   }
   return JD_OK;
 }
@@ -379,12 +393,15 @@ int launch_apply_dataflow(const ildl_s* f, const DevFactor<V>& d, X* w, X* z, co
   const HostFactor& F = f->F;
   ApplyArgs<V, X, IO> a{d.perm, d.scale, d.Lptr, d.Lcol, d.Lval, d.Uptr, d.Ucol, d.Uval, d.dd, d.dof, d.partner,
                         d.dense, w, z, b, out, F.n_dense, F.level_ptr[F.nlev]};
-  if (z == w + F.n) {  // the factor's own work vectors: one fill
-    AJD_CUDA(cudaMemsetAsync(w, 0xFF, 2 * (size_t)F.n * sizeof(X), s));
-  } else {
-    AJD_CUDA(cudaMemsetAsync(w, 0xFF, (size_t)F.n * sizeof(X), s));
-    AJD_CUDA(cudaMemsetAsync(z, 0xFF, (size_t)F.n * sizeof(X), s));
-  }
+  auto fill = [&]() -> int {
+    if (z == w + F.n) {  // the factor's own work vectors: one fill
+      AJD_CUDA(cudaMemsetAsync(w, 0xFF, 2 * (size_t)F.n * sizeof(X), s));
+    } else {
+      AJD_CUDA(cudaMemsetAsync(w, 0xFF, (size_t)F.n * sizeof(X), s));
+      AJD_CUDA(cudaMemsetAsync(z, 0xFF, (size_t)F.n * sizeof(X), s));
+    }
+    return JD_OK;
+  };
   const int4* units = d.units;
   int nseg = d.nseg, nunits = d.nunits;
   int* err = reinterpret_cast<int*>(d.bar + 64);
@@ -397,7 +414,7 @@ int launch_apply_dataflow(const ildl_s* f, const DevFactor<V>& d, X* w, X* z, co
     AJD_CUDA(cudaMemsetAsync(stamps, 0, (nseg + 1) * sizeof(unsigned long long), s));
   }
   void* args[] = {&a, &units, &nseg, &nunits, &err, &stamps};
-  AJD_TRY(launch_cooperative(d, (const void*)ildl_apply_dataflow_kernel<V, X, IO>, args, s));
+  AJD_TRY(launch_cooperative(d, (const void*)ildl_apply_dataflow_kernel<V, X, IO>, args, s, fill));
   count_launches(timing ? 4 : 3);
   if (timing) {
     std::vector<unsigned long long> t(nseg + 1);
@@ -438,7 +455,10 @@ int launch_apply(const ildl_s* f, const DevFactor<V>& d, X* w, X* z, const IO* b
   ApplyArgs<V, X, IO> a{d.perm, d.scale, d.Lptr, d.Lcol, d.Lval, d.Uptr, d.Ucol, d.Uval, d.dd, d.dof, d.partner,
                         d.dense, w, z, b, out, F.n_dense, F.level_ptr[F.nlev]};
   // the phases' completion counters start at zero
-  AJD_CUDA(cudaMemsetAsync(d.done, 0, (size_t)d.nphase * sizeof(unsigned), s));
+  auto clear = [&]() -> int {
+    AJD_CUDA(cudaMemsetAsync(d.done, 0, (size_t)d.nphase * sizeof(unsigned), s));
+    return JD_OK;
+  };
   const int4* ph = d.phases;
   int np = d.nphase;
   unsigned* done = d.done;
@@ -449,7 +469,7 @@ int launch_apply(const ildl_s* f, const DevFactor<V>& d, X* w, X* z, const IO* b
   unsigned long long* stamps = nullptr;
   if (timing) AJD_CUDA(cudaMalloc(&stamps, (np + 1) * sizeof(unsigned long long)));
   void* args[] = {&a, &ph, &np, &done, &err, &stamps};
-  AJD_TRY(launch_cooperative(d, (const void*)ildl_apply_persistent_kernel<V, X, IO>, args, s));
+  AJD_TRY(launch_cooperative(d, (const void*)ildl_apply_persistent_kernel<V, X, IO>, args, s, clear));
   count_launches(2);
   if (timing) {
     std::vector<unsigned long long> t(np + 1);
@@ -586,14 +606,18 @@ int autotune_apply(ildl_s* f, DevFactor<T>& d, int form_req, cudaStream_t st) {
   auto run = [&](double* ms) -> int {
     *ms = 0.0;
     for (int rep = 0; rep < 4; ++rep) {
-      AJD_CUDA(cudaEventRecord(e0, st));
+      // events recorded inside the launch, after the wait for the chain
+      tl_time_begin = e0;
+      tl_time_end = e1;
+      int r;
       if constexpr (sizeof(T) == 8) {
-        AJD_TRY((launch_apply<double, double, double>(f, d, d.w, d.z, b, x, st)));
+        r = launch_apply<double, double, double>(f, d, d.w, d.z, b, x, st);
       } else {
-        AJD_TRY((launch_apply<float, df64, double>(f, d, reinterpret_cast<df64*>(d.wdf), reinterpret_cast<df64*>(d.zdf),
-                                                   b, x, st)));
+        r = launch_apply<float, df64, double>(f, d, reinterpret_cast<df64*>(d.wdf), reinterpret_cast<df64*>(d.zdf),
+                                              b, x, st);
       }
-      AJD_CUDA(cudaEventRecord(e1, st));
+      tl_time_begin = tl_time_end = nullptr;
+      AJD_TRY(r);
       AJD_CUDA(cudaEventSynchronize(e1));
       float t = 0.f;
       AJD_CUDA(cudaEventElapsedTime(&t, e0, e1));
