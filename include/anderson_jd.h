@@ -294,6 +294,27 @@ int ildl_export(ildl_t f, int* perm, double* scale, int* level_ptr, int64_t* Lpt
                 double* Lval, double* dinv_d, double* dinv_o, int* partner, double* dense_inv);
 
 /*
+ * ildl_dataflow_schedule -- the work units of the dataflow apply
+ * (ildl_params.apply_form = 1) for this factor with the threads-per-row
+ * rule scaled by 2^shift (shift in -1..1), for inspection and tests; host
+ * only, also for factors without a device copy.  The units form one
+ * sequence in segments, 5 ints per segment in seg[]:
+ *   kind        0 level 0 (32 rows per unit), 1 forward level, 2 dense tail
+ *               (one row per unit), 3 backward level
+ *   lanes       lanes per row G (1..32; 32/G rows per unit of a sparse level)
+ *   first, end  the positions [first, end) of the segment's rows
+ *   unit0       the first unit of the segment
+ * Segments come in the order the units are taken: level 0, forward levels
+ * 1..nl (the last one being the dense rows' L part), the dense tail,
+ * backward levels nl-1..0 (Section 6's forward and backward sweeps of the
+ * level-by-level L; the kernel's correctness rests on every unit reading
+ * only values written by earlier units).  cap is seg's capacity in
+ * segments; *nseg and *nunits receive the counts (*nseg even when cap is
+ * too small, which returns JD_EINVAL).
+ */
+int ildl_dataflow_schedule(ildl_t f, int shift, int* seg, int cap, int* nseg, int* nunits);
+
+/*
  * ildl_apply -- x = K^{-1} b on the device (created by ildl_create): one
  * gather/scale pass, one parallel step per level of L (forward), the block
  * diagonal and dense solves, one parallel step per level of L^T (backward),

@@ -89,6 +89,7 @@ SIGNATURES = [
     ("ildl_create", c_int, [c_void_p, c_double, P(IldlParams), P(c_void_p)]),
     ("ildl_info", c_int, [c_void_p, P(IldlInfo)]),
     ("ildl_export", c_int, [c_void_p] + [c_void_p] * 10),
+    ("ildl_dataflow_schedule", c_int, [c_void_p, c_int, c_void_p, c_int, c_void_p, c_void_p]),
     ("ildl_apply", c_int, [c_void_p, c_void_p, c_void_p, c_int, c_void_p]),
     ("ildl_apply_noalloc", c_int, [c_void_p, c_void_p, c_void_p, c_int, c_void_p]),
     ("ildl_destroy", c_int, [c_void_p]),

@@ -980,6 +980,26 @@ extern "C" int ildl_export(ildl_t f, int* perm, double* scale, int* level_ptr, i
   return JD_OK;
 }
 
+extern "C" int ildl_dataflow_schedule(ildl_t f, int shift, int* seg, int cap, int* nseg, int* nunits) {
+  if (!f || !nseg || !nunits) return fail(JD_EINVAL, "ildl_dataflow_schedule: NULL argument");
+  if (shift < -1 || shift > 1) return fail(JD_EINVAL, "ildl_dataflow_schedule: shift must be -1, 0 or 1");
+  int nu = 0;
+  const std::vector<int4> ph = build_flow_list(f->F, shift, &nu);
+  *nseg = (int)ph.size();
+  *nunits = nu;
+  if (cap < (int)ph.size() || (!seg && !ph.empty()))
+    return fail(JD_EINVAL, "ildl_dataflow_schedule: room for %d segments, %zu needed", cap, ph.size());
+  for (size_t i = 0; i < ph.size(); ++i) {
+    int* o = seg + 5 * i;
+    o[0] = ph[i].x & 0xFF;
+    o[1] = ph[i].x >> 8;
+    o[2] = ph[i].y;
+    o[3] = ph[i].z;
+    o[4] = ph[i].w;
+  }
+  return JD_OK;
+}
+
 extern "C" int ildl_apply(ildl_t f, const void* b, void* x, int precision, void* stream) {
   if (!f || !b || !x) return fail(JD_EINVAL, "ildl_apply: NULL argument");
   if (b == x) return fail(JD_EINVAL, "ildl_apply: b and x must be distinct");
