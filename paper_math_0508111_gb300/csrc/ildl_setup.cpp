@@ -192,16 +192,18 @@ int max_product_matching(const SymCsr& A, std::vector<int>& match_col, std::vect
   // formed where it is used rather than stored.  v_j = min_i c_ij: by
   // symmetry column j's entries are row j's entries, with the cost taken in
   // the row of the other index, so v comes out of the same pass.  When the
-  // initial potentials come with the matrix (u_in, v_in: formed on the GPU
-  // with the same logarithm and the same exact minima), only the entries
-  // that the greedy start and the searches read take a logarithm, here.
-  const bool given = known && mw.u_in.size() == (size_t)n && mw.v_in.size() == (size_t)n;
+  // logarithms and the initial potentials come with the matrix (loga_in,
+  // u_in, v_in: formed on the GPU with the same logarithm and the same exact
+  // minima), this pass is skipped.
+  const bool given = known && mw.loga_in && mw.u_in.size() == (size_t)n && mw.v_in.size() == (size_t)n &&
+                     mw.loga.size() == A.val.size();
+  mw.loga_in = false;
   dvec<double>& loga = mw.loga;
   auto entry_log = [&](int64_t p) {
     const double a = std::fabs(A.val[p]);
     return a > 0.0 ? log_pos(a) : -kInf;
   };
-  auto cost = [&](int i, int64_t p) { return logmax[i] - (given ? entry_log(p) : loga[p]); };
+  auto cost = [&](int i, int64_t p) { return logmax[i] - loga[p]; };
   if (given) {
     u.swap(mw.u_in);
     v.swap(mw.v_in);
@@ -1253,8 +1255,9 @@ int build_ildl(const SymCsr& A, const ildl_params& prm, HostFactor& F, bool dens
       lv.tau = tau;
       // the next level's matching potentials come with S' when it matches
       const bool next_matches = prm.matching != 0 && (prm.matching < 0 || level + 1 < prm.matching);
-      const int erc = next_matches ? engine->schur(lv, Sn, next_rowmax, &mwork.u_in, &mwork.v_in)
-                                   : engine->schur(lv, Sn, next_rowmax, nullptr, nullptr);
+      const int erc = next_matches ? engine->schur(lv, Sn, next_rowmax, &mwork.u_in, &mwork.v_in, &mwork.loga)
+                                   : engine->schur(lv, Sn, next_rowmax, nullptr, nullptr, nullptr);
+      mwork.loga_in = next_matches && erc == JD_OK;
       if (erc != JD_OK) return erc;
       ts_num = ms_since(t_schur) - ts_rec;
     } else {

@@ -121,11 +121,11 @@ class SchurEngine {
   virtual ~SchurEngine() = default;
   virtual int begin(const SymCsr& A) = 0;
   virtual int scale(const double* d, int m) = 0;
-  // S' of the level, its row maxima and, when u and v are given, the
-  // matching's dual potentials of S' (as max_product_matching forms them
-  // before its searches: the same bits)
+  // S' of the level, its row maxima and, when u, v and loga are given, the
+  // matching's dual potentials of S' and log |s'_ij| of every stored entry
+  // (as max_product_matching forms them before its searches: the same bits)
   virtual int schur(const SchurLevel& lv, SymCsr& Sn, std::vector<double>& rowmax, std::vector<double>* u,
-                    std::vector<double>* v) = 0;
+                    std::vector<double>* v, dvec<double>* loga) = 0;
 };
 
 // Default weak-coupling threshold gamma of the independent sets for an
@@ -161,10 +161,11 @@ struct MatchWork {
   // has it already (one pass over the matrix fewer); used if it has n entries
   std::vector<double> rowmax_in;
   // optional, with rowmax_in: the initial dual potentials u, v of the next
-  // matrix, formed elsewhere (the GPU that formed the matrix) with the same
-  // arithmetic; the matching then takes log|a_ij| only of the entries its
-  // greedy start and searches read.  Used once if both have n entries.
+  // matrix and log|a_ij| of its entries (in loga), formed elsewhere (the GPU
+  // that formed the matrix) with the same arithmetic.  Used once if u_in
+  // and v_in have n entries and loga_in is set.
   std::vector<double> u_in, v_in;
+  bool loga_in = false;
 };
 
 // The table of the matching's division-free logarithm (128 values of 1/c_k

@@ -389,16 +389,18 @@ __global__ void logmax_kernel(const double* __restrict__ rowmax, double* __restr
   }
 }
 
-// v_j = min over row j (= column j) of logmax[col] - log|a| (0 if none)
+// v_j = min over row j (= column j) of logmax[col] - log|a| (0 if none);
+// log|a| of every entry kept in loga for the host's searches
 __global__ void duals_v_kernel(const int64_t* __restrict__ ptr, const int* __restrict__ col,
                                const double* __restrict__ val, const double* __restrict__ logmax,
-                               double* __restrict__ v, int m) {
+                               double* __restrict__ v, double* __restrict__ loga, int m) {
   const int lane = threadIdx.x & 31;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
   for (int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < m; j += nwarps) {
     double best = CUDART_INF;
     for (int64_t p = ptr[j] + lane; p < ptr[j + 1]; p += 32) {
       const double la = entry_log_dev(val[p]);
+      loga[p] = la;
       if (la > -CUDART_INF) best = fmin(best, __dsub_rn(logmax[col[p]], la));
     }
     best = warp_min(best);
@@ -408,7 +410,7 @@ __global__ void duals_v_kernel(const int64_t* __restrict__ ptr, const int* __res
 
 // u_i = min over row i of (logmax_i - log|a|) - v[col] (0 if none)
 __global__ void duals_u_kernel(const int64_t* __restrict__ ptr, const int* __restrict__ col,
-                               const double* __restrict__ val, const double* __restrict__ logmax,
+                               const double* __restrict__ loga, const double* __restrict__ logmax,
                                const double* __restrict__ v, double* __restrict__ u, int m) {
   const int lane = threadIdx.x & 31;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -416,7 +418,7 @@ __global__ void duals_u_kernel(const int64_t* __restrict__ ptr, const int* __res
     const double lm = logmax[i];
     double best = CUDART_INF;
     for (int64_t p = ptr[i] + lane; p < ptr[i + 1]; p += 32) {
-      const double c = __dsub_rn(lm, entry_log_dev(val[p]));
+      const double c = __dsub_rn(lm, loga[p]);
       if (c < CUDART_INF) best = fmin(best, __dsub_rn(c, v[col[p]]));
     }
     best = warp_min(best);
@@ -538,10 +540,10 @@ class DeviceSchur final : public SchurEngine {
   }
 
   int schur(const SchurLevel& lv, SymCsr& Sn, std::vector<double>& rowmax, std::vector<double>* u,
-            std::vector<double>* v) override {
+            std::vector<double>* v, dvec<double>* loga) override {
     if (table_rc_ != cudaSuccess)
       return fail(JD_EDEVICE, "gpu schur: logarithm table upload: %s", cudaGetErrorString(table_rc_));
-    const bool duals = u && v;
+    const bool duals = u && v && loga;
     const auto t0 = std::chrono::steady_clock::now();
     auto ms = [&]() { return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count(); };
     double t_bounds = 0, t_up = 0, t_k1 = 0, t_ptr = 0, t_k2 = 0;
@@ -657,9 +659,10 @@ class DeviceSchur final : public SchurEngine {
       AJD_TRY(logmax_.reserve(mc));
       AJD_TRY(du_.reserve(mc));
       AJD_TRY(dv_.reserve(mc));
+      AJD_TRY(dloga_.reserve(nnz));
       logmax_kernel<<<grid_for(mc), 256, 0, st_>>>(rowmax_.p, logmax_.p, mc);
-      duals_v_kernel<<<grid_for(mc), 256, 0, st_>>>(nptr_.p, ncol_.p, nval_.p, logmax_.p, dv_.p, mc);
-      duals_u_kernel<<<grid_for(mc), 256, 0, st_>>>(nptr_.p, ncol_.p, nval_.p, logmax_.p, dv_.p, du_.p, mc);
+      duals_v_kernel<<<grid_for(mc), 256, 0, st_>>>(nptr_.p, ncol_.p, nval_.p, logmax_.p, dv_.p, dloga_.p, mc);
+      duals_u_kernel<<<grid_for(mc), 256, 0, st_>>>(nptr_.p, ncol_.p, dloga_.p, logmax_.p, dv_.p, du_.p, mc);
       count_launches(3);
     }
     AJD_CHECK_LAUNCH();
@@ -669,18 +672,23 @@ class DeviceSchur final : public SchurEngine {
     // host's arrays by all threads (which also spreads the first touch of
     // their pages)
     const size_t vbytes = nnz * sizeof(double), cbytes = nnz * sizeof(int), mbytes = mc * sizeof(double);
-    AJD_TRY(stage_.reserve(vbytes + cbytes + 3 * mbytes + 64));
+    const size_t lbytes = duals ? vbytes : 0;
+    AJD_TRY(stage_.reserve(vbytes + cbytes + 3 * mbytes + lbytes + 64));
     char* hv = static_cast<char*>(stage_.p);
     char* hc = hv + vbytes;
     char* hm = hc + ((cbytes + 15) & ~(size_t)15);
     char* hu = hm + mbytes;
     char* hw = hu + mbytes;
+    char* hl = hw + mbytes;
     AJD_CUDA(cudaMemcpyAsync(hv, nval_.p, vbytes, cudaMemcpyDeviceToHost, st_));
     AJD_CUDA(cudaMemcpyAsync(hc, ncol_.p, cbytes, cudaMemcpyDeviceToHost, st_));
     AJD_CUDA(cudaMemcpyAsync(hm, rowmax_.p, mbytes, cudaMemcpyDeviceToHost, st_));
     if (duals) {
       AJD_CUDA(cudaMemcpyAsync(hu, du_.p, mbytes, cudaMemcpyDeviceToHost, st_));
       AJD_CUDA(cudaMemcpyAsync(hw, dv_.p, mbytes, cudaMemcpyDeviceToHost, st_));
+      AJD_CUDA(cudaMemcpyAsync(hl, dloga_.p, lbytes, cudaMemcpyDeviceToHost, st_));
+      if ((size_t)nnz > loga->capacity()) dvec<double>().swap(*loga);  // no copy of stale contents
+      loga->resize(nnz);
     }
     Sn.col.resize(nnz);
     Sn.val.resize(nnz);
@@ -695,11 +703,14 @@ class DeviceSchur final : public SchurEngine {
       const int* sc = reinterpret_cast<const int*>(hc);
       double* dv = Sn.val.data();
       int* dc = Sn.col.data();
+      const double* sl = reinterpret_cast<const double*>(hl);
+      double* dl = duals ? loga->data() : nullptr;
 #pragma omp parallel for schedule(static)
       for (int64_t b = 0; b < (nnz + 65535) / 65536; ++b) {
         const int64_t i0 = b * 65536, i1 = std::min<int64_t>(nnz, i0 + 65536);
         std::memcpy(dv + i0, sv + i0, (i1 - i0) * sizeof(double));
         std::memcpy(dc + i0, sc + i0, (i1 - i0) * sizeof(int));
+        if (dl) std::memcpy(dl + i0, sl + i0, (i1 - i0) * sizeof(double));
       }
       std::memcpy(rowmax.data(), hm, mbytes);
       if (duals) {
@@ -732,7 +743,7 @@ class DeviceSchur final : public SchurEngine {
   int64_t nnz_ = 0;
   DBuf<int64_t> sptr_, nptr_, rrec_, rslot_, cptr_, off_, hoff_, goff_;
   DBuf<int> scol_, ncol_, cidx_, cnodes_, rblk_, crow_, gkeys_, ucol_, ucnt_, lowcnt_, cursor_;
-  DBuf<double> sval_, nval_, dd_, c1_, c2_, bmat_, gvals_, uval_, rowmax_, logmax_, du_, dv_;
+  DBuf<double> sval_, nval_, dd_, c1_, c2_, bmat_, gvals_, uval_, rowmax_, logmax_, du_, dv_, dloga_;
   cudaError_t table_rc_ = cudaSuccess;
   DBuf<char> is2_;
   Pinned stage_;
