@@ -331,8 +331,10 @@ int ildl_apply(ildl_t f, const void* b, void* x, int precision, void* stream);
  * allocate device memory during the call (a fixed memory pool reserved up
  * front, an embedding runtime that owns all device memory).  The paper has no
  * counterpart: this is a deployment variant.
- * It runs the same kernel but takes its scratch (two work vectors, the
- * status word of its waits and the completion counters of its phases) from
+ * It runs the level-counter form of the apply kernel (apply_form 0, whatever
+ * form the factor's own applies use; the result agrees with ildl_apply to
+ * rounding) and takes its scratch (two work vectors, the status word of its
+ * waits and the completion counters of its phases) from
  * one static device array compiled into the library (2 MiB + 16.5 KiB, held
  * by every GPU that loads the library until the process exits) instead of
  * the factor's buffers; it calls no cudaMalloc, cudaFree or allocating
