@@ -28,117 +28,14 @@
 #include "ildl_apply_kernel.cuh"
 #include "ildl_apply_dataflow.cuh"
 #include "schur_gpu.h"
+#include "dense_inverse.h"
 
 namespace ajd {
 namespace {
 
-// ---- Gauss–Jordan inversion of the dense trailing block (setup) ----
-// X = A^{-1} for the m x m row-major binary64 matrix A (overwritten), with
-// partial pivoting, two launches per column c:
-//   gj_pivot_step_kernel (one CTA): the largest |A[r][c]|, r >= c (lowest
-//     row on ties); rows c and piv swapped in A (columns >= c) and X (all
-//     columns); row c scaled by 1/pivot; multipliers f[r] = A[r][c] after
-//     the swap (f[c] = 0);
-//   gj_eliminate_kernel (grid): rows r != c: A[r][k] -= f[r] A[c][k] (k >= c),
-//     X[r][k] -= f[r] X[c][k] (all k: the swaps move entries of X into every
-//     column).
-// Ordinary launches, so the setup of one problem shares the GPU with the
-// solves of others.  A zero or non-finite pivot sets *bad.
-constexpr int kGjPivotThreads = 1024;
-
 // Apply form of factors that are not autotuned (ildl_params.apply_form < 0):
 // 1 = the dataflow kernel, 0 = the level-counter kernel.
 constexpr int kDefaultApplyForm = 1;
-
-__global__ void __launch_bounds__(kGjPivotThreads)
-gj_pivot_step_kernel(double* __restrict__ A, double* __restrict__ X, int m, int c, double* __restrict__ f,
-                     int* __restrict__ bad) {
-  __shared__ double sv[kGjPivotThreads / 32];
-  __shared__ int si[kGjPivotThreads / 32];
-  __shared__ int s_piv;
-  __shared__ double s_pval, s_aold;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  double bv = 0.0;
-  int bi = m;
-  for (int r = c + threadIdx.x; r < m; r += blockDim.x) {
-    const double a = A[(int64_t)r * m + c];
-    if (bi == m || fabs(a) > fabs(bv)) { bv = a; bi = r; }
-  }
-  for (int o = 16; o > 0; o >>= 1) {
-    const double v2 = __shfl_xor_sync(0xffffffffu, bv, o);
-    const int i2 = __shfl_xor_sync(0xffffffffu, bi, o);
-    if (i2 < m && (bi == m || fabs(v2) > fabs(bv) || (fabs(v2) == fabs(bv) && i2 < bi))) { bv = v2; bi = i2; }
-  }
-  if (lane == 0) { sv[warp] = bv; si[warp] = bi; }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int w = 0;
-    for (int j = 1; j < kGjPivotThreads / 32; ++j)
-      if (si[j] < m && (si[w] == m || fabs(sv[j]) > fabs(sv[w]) || (fabs(sv[j]) == fabs(sv[w]) && si[j] < si[w])))
-        w = j;
-    s_piv = si[w] < m ? si[w] : c;
-    s_pval = si[w] < m ? sv[w] : 0.0;
-    s_aold = A[(int64_t)c * m + c];
-    if (!(fabs(s_pval) > 0.0) || !isfinite(s_pval)) *bad = 1;
-  }
-  __syncthreads();
-  const int piv = s_piv;
-  const double inv = 1.0 / s_pval;
-  // the multipliers read rows other than c and piv, which the swap below
-  // does not touch; f[piv] is the old A[c][c] (moved to row piv)
-  for (int r = threadIdx.x; r < m; r += blockDim.x) f[r] = r == c ? 0.0 : (r == piv ? s_aold : A[(int64_t)r * m + c]);
-  for (int k = threadIdx.x; k < m; k += blockDim.x) {
-    const double xc = X[(int64_t)c * m + k], xp = X[(int64_t)piv * m + k];
-    X[(int64_t)c * m + k] = xp * inv;
-    if (piv != c) X[(int64_t)piv * m + k] = xc;
-    if (k >= c) {
-      const double ac = A[(int64_t)c * m + k], ap = A[(int64_t)piv * m + k];
-      A[(int64_t)c * m + k] = ap * inv;
-      if (piv != c) A[(int64_t)piv * m + k] = ac;
-    }
-  }
-}
-
-__global__ void gj_eliminate_kernel(double* __restrict__ A, double* __restrict__ X, int m, int c,
-                                    const double* __restrict__ f) {
-  const int64_t w = (int64_t)(m - c) + m;
-  const int64_t total = (int64_t)m * w;
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
-    const int r = (int)(t / w);
-    const int j = (int)(t - (int64_t)r * w);
-    const double fr = f[r];
-    if (fr == 0.0) continue;  // also row c (f[c] = 0)
-    if (j < m - c) {
-      const int k = c + j;
-      if (k == c) A[(int64_t)r * m + k] = 0.0;
-      else A[(int64_t)r * m + k] -= fr * A[(int64_t)c * m + k];
-    } else {
-      // row c of X is zero outside the columns that earlier steps filled
-      // (X starts as I), and a zero there leaves X[r][k] unchanged: skip
-      // the read-modify-write (about half of X's traffic over the inversion)
-      const int k = j - (m - c);
-      const double xc = X[(int64_t)c * m + k];
-      if (xc != 0.0) X[(int64_t)r * m + k] -= fr * xc;
-    }
-  }
-}
-
-__global__ void gj_identity_kernel(double* __restrict__ X, int m) {
-  const int64_t total = (int64_t)m * m;
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x)
-    X[t] = (t / m == t % m) ? 1.0 : 0.0;
-}
-
-__global__ void gj_symmetrize_kernel(double* __restrict__ X, int m) {
-  const int64_t total = (int64_t)m * m;
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
-    const int i = (int)(t / m), j = (int)(t % m);
-    if (j <= i) continue;
-    const double sym = 0.5 * (X[(int64_t)i * m + j] + X[(int64_t)j * m + i]);
-    X[(int64_t)i * m + j] = sym;
-    X[(int64_t)j * m + i] = sym;
-  }
-}
 
 template <typename T>
 void free_dev(DevFactor<T>& d) {
@@ -526,39 +423,31 @@ template int ildl_apply_dev<double>(const ildl_s*, const double*, double*, cudaS
 template int ildl_apply_dev<float>(const ildl_s*, const float*, float*, cudaStream_t);
 
 // Invert the dense trailing block (host matrix in, host inverse out) on the
-// current device.
+// current device (blocked Gauss-Jordan, csrc/dense_inverse.cu).
 int invert_dense_on_device(dvec<double>& M, int m, cudaStream_t st) {
   if (m == 0) return JD_OK;
   const size_t bytes = (size_t)m * m * sizeof(double);
-  double *A = nullptr, *X = nullptr, *f = nullptr;
+  double *A = nullptr, *X = nullptr;
   int* bad = nullptr;
   cudaError_t e = cudaMalloc(&A, bytes);
   if (e == cudaSuccess) e = cudaMalloc(&X, bytes);
-  if (e == cudaSuccess) e = cudaMalloc(&f, (size_t)m * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&bad, sizeof(int));
   int rc = JD_OK;
   if (e == cudaSuccess) e = cudaMemcpyAsync(A, M.data(), bytes, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(bad, 0, sizeof(int), st);
   if (e == cudaSuccess) {
-    const int gb = std::max(1, std::min(ceil_div((int64_t)m * m, 256), 8 * sm_count()));
-    gj_identity_kernel<<<gb, 256, 0, st>>>(X, m);
-    for (int c = 0; c < m; ++c) {
-      gj_pivot_step_kernel<<<1, kGjPivotThreads, 0, st>>>(A, X, m, c, f, bad);
-      gj_eliminate_kernel<<<gb, 256, 0, st>>>(A, X, m, c, f);
-    }
-    gj_symmetrize_kernel<<<gb, 256, 0, st>>>(X, m);
-    count_launches(2 * m + 2);
-    e = cudaGetLastError();
+    rc = dense_inverse_device(A, X, m, bad, st);
     int hbad = 0;
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(M.data(), X, bytes, cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (e == cudaSuccess && hbad) rc = fail(JD_ESETUP, "ildl: the final dense block (%d rows) is singular", m);
+    if (rc == JD_OK) {
+      e = cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, st);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(M.data(), X, bytes, cudaMemcpyDeviceToHost, st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+      if (e == cudaSuccess && hbad) rc = fail(JD_ESETUP, "ildl: the final dense block (%d rows) is singular", m);
+    }
   }
   if (e != cudaSuccess) rc = fail(JD_EDEVICE, "ildl dense inverse: %s", cudaGetErrorString(e));
   cudaFree(A);
   cudaFree(X);
-  cudaFree(f);
   cudaFree(bad);
   return rc;
 }

@@ -186,14 +186,19 @@ def test_dense_tail_inverse_is_exact(ajd, L, bc, sigma):
         P.close()
 
 
-def test_multilevel_factor_exact_on_device(ajd):
+@pytest.mark.parametrize("L,nd", [(10, 200), (12, 1100), (8, 512)])
+def test_multilevel_factor_exact_on_device(ajd, L, nd):
     """No dropping, exact independence, kappa = inf: the device apply of the
     multilevel factor (sparse levels + device-inverted dense tail) inverts
-    A - sigma I."""
-    L, sigma = 10, 0.3
+    A - sigma I.  The dense tails span one partial panel of the blocked
+    Gauss-Jordan inversion (200 rows: 7 panels of 32, the last of 8), many
+    panels over all eight row ranges of its cluster (1100 rows), and the
+    whole matrix (L = 8: 512 rows, no sparse level)."""
+    sigma = 0.3
     with ajd.Anderson(L, 16.5, 3) as h:
-        P = ajd.Preconditioner.from_lattice(h, sigma, drop=0.0, kappa=1e300, gamma=0.0, n_dense=200)
-        assert P.info()["levels"] >= 2
+        P = ajd.Preconditioner.from_lattice(h, sigma, drop=0.0, kappa=1e300, gamma=0.0, n_dense=nd)
+        if nd < h.n:
+            assert P.info()["levels"] >= 2
         A = lattice.assemble(L, rng.potential(L, 16.5, 3), 0, shift=sigma)
         x = np.random.default_rng(2).standard_normal(h.n)
         y = P.apply(torch.tensor(A @ x, device="cuda")).cpu().numpy()
