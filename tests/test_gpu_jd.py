@@ -86,11 +86,12 @@ def test_ildl_apply_matches_oracle(ajd, L, bc, sigma, nd, form):
 
 
 def test_ildl_apply_forms_agree(ajd):
-    """The level-counter and the dataflow kernels compute the same sums
-    (rows split over the same lanes in different orders only): their
-    binary64 results agree to rounding, and repeated dataflow applies of the
-    same vector give the same bits (each row's sum is formed by one fixed set
-    of lanes, whatever the timing)."""
+    """The level-counter and the dataflow kernels form the same products,
+    summed in different orders (their rows are split over different numbers
+    of lanes): their binary64 results agree to rounding, and repeated
+    dataflow applies of the same vector give the same bits (each row's sum
+    is formed by one fixed set of lanes in a fixed order, whatever the
+    timing)."""
     with ajd.Anderson(30, 16.5, 7) as h:
         P0 = ajd.Preconditioner.from_lattice(h, 0.1, apply_form=0)
         P1 = ajd.Preconditioner.from_lattice(h, 0.1, apply_form=1)
