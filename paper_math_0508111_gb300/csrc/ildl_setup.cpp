@@ -945,6 +945,9 @@ int build_ildl(const SymCsr& A, const ildl_params& prm, HostFactor& F, bool dens
           cs1 += std::fabs(r1);
           cs2 += std::fabs(r2);
           d2 += std::fabs(r1) + std::fabs(r2);
+          // the terms are non-negative: once d2 reaches d1 the block is not
+          // taken, whatever follows (same outcome as the full sum)
+          if (!(d2 < d1)) break;
         }
         if (d2 < d1) {  // Section 6.2: 2x2 update only if d2 < d1
           use2 = true;
@@ -959,6 +962,7 @@ int build_ildl(const SymCsr& A, const ildl_params& prm, HostFactor& F, bool dens
         gcount[gi] = 2;
       }
     }
+    const double tc_groups = ms_since(t_cand);
     std::vector<Cand> cands;
     cands.reserve(m);
     for (int gi = 0; gi < ng; ++gi) {
@@ -970,6 +974,7 @@ int build_ildl(const SymCsr& A, const ildl_params& prm, HostFactor& F, bool dens
       return x.a < y.a;
     });
 
+    const double tc_sort = ms_since(t_cand) - tc_groups;
     // 4. independent set of pivots, best first; inverse-based acceptance
     // 1 + q <= kappa (||L^{-1}||_1 of this level)
     std::vector<char> blocked(m, 0), inB(m, 0);
@@ -1000,6 +1005,9 @@ int build_ildl(const SymCsr& A, const ildl_params& prm, HostFactor& F, bool dens
     if (acc.empty()) return fail(JD_ESETUP, "ildl: no usable pivot at level %d (%d rows)", level, m);
 
     const double tc_ms = ms_since(t_cand);
+    if (verbose)
+      std::fprintf(stderr, "  candidates: groups %.1f sort %.1f independent set %.1f ms\n", tc_groups, tc_sort,
+                   tc_ms - tc_groups - tc_sort);
     const auto t_lf = Clock::now();
     // 5. local numbering: B in accepted order, C in index order (both
     // built in parallel: block positions and C indices from prefix sums)
