@@ -768,6 +768,13 @@ bool dense_inverse(int m, dvec<double>& M, dvec<double>& inv) {
 
 }  // namespace
 
+// Dense tail: n/16 clamped to 1000..3000 rows.  Its Gauss-Jordan inversion
+// costs O(n_dense^3) binary64 work on a GPU whose FP64 pipe is narrow (0.14 s
+// at 2946 rows in the blocked form), while the extra sparse levels that a
+// smaller tail leaves cost little in the dataflow apply; the bound keeps the
+// inversion short when setups share the device with solves.
+int default_n_dense(int64_t n) { return (int)std::max<int64_t>(1000, std::min<int64_t>(3000, n / 16)); }
+
 double default_gamma(int64_t n, bool offdiag) {
   // weak-coupling threshold of the independent sets; by default it shrinks
   // with the drop tolerance (measured: a fixed 0.02 loses the preconditioner
@@ -788,13 +795,7 @@ int build_ildl(const SymCsr& A, const ildl_params& prm, HostFactor& F, bool dens
 
   const double gamma = prm.gamma < 0.0 ? default_gamma(n, false) : prm.gamma;
   const int max_levels = prm.max_levels > 0 ? prm.max_levels : 64;
-  // dense tail: the given size, else n/16 clamped to 1000..3000.  Its
-  // Gauss-Jordan inversion costs O(n_dense^3) binary64 work on a GPU whose
-  // FP64 pipe is narrow (about 0.2 s at 3000 rows, 1.7 s at 6000), while the
-  // extra sparse levels that a smaller tail leaves cost little in the
-  // dataflow apply; the bound keeps the inversion short when setups share
-  // the device with solves
-  const int n_dense = prm.n_dense > 0 ? prm.n_dense : std::max(1000, std::min(3000, n / 16));
+  const int n_dense = prm.n_dense > 0 ? prm.n_dense : default_n_dense(n);
   constexpr int kDenseHardMax = 8000;
 
   F = HostFactor();

@@ -133,6 +133,9 @@ class SchurEngine {
 // off-diagonal model.
 double default_gamma(int64_t n, bool offdiag);
 
+// Default size of the dense trailing block for an order-n matrix (rows).
+int default_n_dense(int64_t n);
+
 // Build the preconditioner of A (symmetric, e.g. A - sigma I).  Returns
 // JD_OK or JD_ESETUP / JD_EINVAL with jd_last_error() set.  With
 // dense_on_host = false the trailing dense block is left un-inverted

@@ -43,7 +43,7 @@ struct Request {
 
 size_t estimate_bytes(int L, int k, const jd_params& p) {
   const double n = (double)L * L * L;
-  const double nd = std::min(n, (double)(p.ildl.n_dense > 0 ? p.ildl.n_dense : std::max(1000.0, std::min(6000.0, n / 16))));
+  const double nd = std::min(n, (double)(p.ildl.n_dense > 0 ? p.ildl.n_dense : default_n_dense((int64_t)n)));
   const double fill = n > nd ? 60.0 : 0.0;  // stored entries of L per row (56.6 measured at L = 100)
   const int kint = k + 2;
   const int jmin = p.jmin > 0 ? p.jmin : std::max(2 * kint, 10);
